@@ -1,0 +1,71 @@
+"""Mutation check of the oracle pins: each plausible mistake below is planted in
+a temporary copy of the oracle (on the CPU only) and the pin suite must fail on
+it. A mutant that survives means a part of the oracle is not pinned."""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+MUTANTS = {
+    "swap_dxdy": ("    dx = L[ys, xs + 1] - L[ys, xs - 1]\n    dy = L[ys + 1, xs] - L[ys - 1, xs]",
+                  "    dy = L[ys, xs + 1] - L[ys, xs - 1]\n    dx = L[ys + 1, xs] - L[ys - 1, xs]"),
+    "drop_dxy": ("    H = np.array([[dxx, dxy, dxs], [dxy, dyy, dys], [dxs, dys, dss]])",
+                 "    H = np.array([[dxx, 0.0, dxs], [0.0, dyy, dys], [dxs, dys, dss]])"),
+    "rotation_sign": ("    rx = (ct * ox + st * oy) / wbin\n    ry = (-st * ox + ct * oy) / wbin",
+                      "    rx = (ct * ox - st * oy) / wbin\n    ry = (st * ox + ct * oy) / wbin"),
+    "uv_transposed": ("                np.add.at(hist, (vv[inb], uu[inb], oo[inb])",
+                      "                np.add.at(hist, (uu[inb], vv[inb], oo[inb])"),
+    "relative_angle_sign": ("    phi = np.arctan2(dy, dx) - th", "    phi = th - np.arctan2(dy, dx)"),
+    "offset_sign": ("        delta = cramer_solve(H, -g)", "        delta = cramer_solve(H, g)"),
+    "contrast_no_half": ("    contrast = D[s, y, x] + 0.5 * float(g @ delta)",
+                         "    contrast = D[s, y, x] + float(g @ delta)"),
+    "kappa_linear": ("    return [math.sqrt(s[i] ** 2 - s[i - 1] ** 2) for i in range(1, len(s))]",
+                     "    return [s[i] - s[i - 1] for i in range(1, len(s))]"),
+    "edge_ratio_dropped": ("    lhs, rhs = tr * tr * r, (r + 1) ** 2 * det",
+                           "    lhs, rhs = tr * tr, (r + 1) ** 2 * det"),
+    "two_smoothing_passes": (
+        "    return 0.25 * np.roll(hist, 1) + 0.5 * hist + 0.25 * np.roll(hist, -1)",
+        "    h = 0.25 * np.roll(hist, 1) + 0.5 * hist + 0.25 * np.roll(hist, -1)\n"
+        "    return 0.25 * np.roll(h, 1) + 0.5 * h + 0.25 * np.roll(h, -1)"),
+    "parabola_sign": ("            kf = k + 0.5 * (hm - hp) / (hm - 2.0 * hk + hp)",
+                      "            kf = k - 0.5 * (hm - hp) / (hm - 2.0 * hk + hp)"),
+    "descriptor_window_sigma": (
+        "    wt = mag * np.exp(-(rx * rx + ry * ry) / (2.0 * (0.5 * d) ** 2))",
+        "    wt = mag * np.exp(-(rx * rx + ry * ry) / (2.0 * (0.5 * d)))"),
+    "decimate_odd_phase": ("    return img[0:2 * (h // 2):2, 0:2 * (w // 2):2].copy()",
+                           "    return img[1:2 * (h // 2):2, 1:2 * (w // 2):2].copy()"),
+    "upsample_no_average": ("        out[1::2] = 0.5 * (a + nxt)", "        out[1::2] = a"),
+    "border_off_by_one": (
+        "        if s < 1 or s > S or x < b or x >= w - b or y < b or y >= h - b:",
+        "        if s < 1 or s > S or x < b or x > w - b or y < b or y > h - b:"),
+    "orientation_window_sigma": ("    wt = np.exp(-(i * i + j * j) / (2.0 * sw * sw))",
+                                 "    wt = np.exp(-(i * i + j * j) / (2.0 * sw))"),
+    "clip_missing": ("    vec = np.minimum(vec / nrm, p.desc_clip)", "    vec = vec / nrm"),
+    "extremum_not_strict": ("        is_max = c > nmax\n        is_min = c < nmin",
+                            "        is_max = c >= nmax\n        is_min = c <= nmin"),
+    "nearest_bin_floor": (
+        "    bins = np.floor(n * th / (2 * math.pi) + 0.5).astype(np.int64) % n",
+        "    bins = np.floor(n * th / (2 * math.pi)).astype(np.int64) % n"),
+    "taps_not_normalised": ("    return r, w / w.sum()", "    return r, w / (math.sqrt(2 * math.pi) * sigma)"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, tmp_path):
+    before, after = MUTANTS[name]
+    src = open(os.path.join(ROOT, "oracle", "sift_oracle.py")).read()
+    assert before in src, "mutation anchor missing: " + name
+    for d in ("oracle", "workloads"):
+        shutil.copytree(os.path.join(ROOT, d), tmp_path / d,
+                        ignore=shutil.ignore_patterns("__pycache__"))
+    (tmp_path / "tests").mkdir()
+    for f in ("conftest.py", "test_oracle_pins.py"):
+        shutil.copy(os.path.join(ROOT, "tests", f), tmp_path / "tests" / f)
+    (tmp_path / "oracle" / "sift_oracle.py").write_text(src.replace(before, after))
+    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-q", "-x",
+                        "-p", "no:cacheprovider"], cwd=tmp_path, capture_output=True, text=True)
+    assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"

@@ -1,0 +1,471 @@
+"""Pins for the FP64 oracle: each check compares it with something other than
+itself (closed forms, brute force, invariants the mathematics fixes), chosen so
+that a dropped term, a wrong sign / index or a transposed operand fails one."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import sift_oracle as so
+from workloads import synth
+
+RNG = np.random.default_rng(1234)
+
+
+# ----------------------------------------------------------------- taps / blur
+
+@pytest.mark.parametrize("sigma", [0.8, 1.2263, 1.5199, 2.4525, 3.09])
+def test_taps_normalised_symmetric_second_moment(sigma):
+    r, w = so.gaussian_taps(sigma)
+    assert r == math.ceil(4 * sigma)
+    assert len(w) == 2 * r + 1
+    assert abs(w.sum() - 1.0) < 1e-15
+    np.testing.assert_array_equal(w, w[::-1])
+    k = np.arange(-r, r + 1)
+    var = float((k * k * w).sum())
+    # Truncation at 4 sigma can only remove tail variance, and removes < 2e-3 of it.
+    assert var <= sigma * sigma * (1 + 1e-12)
+    assert (sigma * sigma - var) / (sigma * sigma) < 2e-3
+    # Closed form of the sampled, untruncated taps: w_k proportional to exp(-k^2/2s^2).
+    np.testing.assert_allclose(w / w[r], np.exp(-(k * k) / (2 * sigma * sigma)), rtol=1e-14)
+
+
+def _refl(i, n):
+    while i < 0 or i >= n:
+        i = -i if i < 0 else 2 * (n - 1) - i
+    return i
+
+
+def _brute_blur(img, sigma):
+    r, w = so.gaussian_taps(sigma)
+    h, wd = img.shape
+    out = np.zeros((h, wd))
+    for y in range(h):
+        for x in range(wd):
+            acc = 0.0
+            for j in range(-r, r + 1):
+                for i in range(-r, r + 1):
+                    acc += w[j + r] * w[i + r] * img[_refl(y + j, h), _refl(x + i, wd)]
+            out[y, x] = acc
+    return out
+
+
+@pytest.mark.parametrize("shape,sigma", [((7, 9), 1.2), ((16, 13), 1.2263), ((33, 31), 1.5451),
+                                         ((20, 24), 3.09)])
+def test_separable_blur_equals_bruteforce_2d(shape, sigma):
+    r, _ = so.gaussian_taps(sigma)
+    if r >= min(shape):
+        sigma = (min(shape) - 1) / 4.0 - 0.01
+    img = RNG.random(shape)
+    np.testing.assert_allclose(so.blur(img, sigma), _brute_blur(img, sigma), atol=1e-12, rtol=0)
+
+
+def test_pyramid_impulse_variance_bookkeeping():
+    """Level i of octave 0 applied total variance sigma_i^2 - sigma_in^2 in each axis."""
+    p = so.Params()
+    n = 257
+    img = np.zeros((n, n))
+    img[128, 128] = 1.0
+    G = so.build_pyramid(img, p)[0]
+    k = np.arange(n) - 128.0
+    for i, sig in enumerate(so.level_sigmas(p)):
+        lv = G[i]
+        mass = lv.sum()
+        assert abs(mass - 1.0) < 1e-12
+        vx = float((lv.sum(axis=0) * k * k).sum())
+        vy = float((lv.sum(axis=1) * k * k).sum())
+        target = sig * sig - p.init_blur ** 2
+        assert abs(vx - target) / target < 2e-3
+        assert abs(vx - vy) < 1e-9
+
+
+def test_increment_sigmas_closed_form():
+    p = so.Params()
+    kap = so.increment_sigmas(p)
+    # kappa_i = sigma0 * 2^((i-1)/S) * sqrt(2^(2/S) - 1): geometric with ratio 2^(1/S).
+    expect = [1.6 * 2 ** ((i - 1) / 3) * math.sqrt(2 ** (2 / 3) - 1) for i in range(1, 6)]
+    np.testing.assert_allclose(kap, expect, rtol=1e-14)
+    assert [math.ceil(4 * k) for k in kap] == [5, 7, 8, 10, 13]
+    assert abs(so.base_sigma(p) - math.sqrt(1.6 ** 2 - 0.25)) < 1e-15
+    assert abs(so.base_sigma(so.Params(upsample=True)) - math.sqrt(1.6 ** 2 - 1.0)) < 1e-15
+
+
+# ------------------------------------------------------------ resampling
+
+def test_upsample_identities():
+    img = RNG.random((5, 7))
+    u = so.upsample2x(img)
+    assert u.shape == (10, 14)
+    np.testing.assert_array_equal(u[0::2, 0::2], img)
+    np.testing.assert_allclose(u[0::2, 1:-1:2], 0.5 * (img[:, :-1] + img[:, 1:]), rtol=1e-15)
+    np.testing.assert_allclose(u[1:-1:2, 0::2], 0.5 * (img[:-1] + img[1:]), rtol=1e-15)
+    np.testing.assert_allclose(u[1:-1:2, 1:-1:2],
+                               0.25 * (img[:-1, :-1] + img[:-1, 1:] + img[1:, :-1] + img[1:, 1:]),
+                               rtol=1e-14)
+    np.testing.assert_array_equal(u[-1, 0::2], img[-1])    # clamped last row
+    np.testing.assert_array_equal(u[0::2, -1], img[:, -1])  # clamped last column
+    np.testing.assert_array_equal(so.decimate(u), img)
+
+
+def test_decimate_floor_size_and_octaves():
+    img = RNG.random((31, 18))
+    d = so.decimate(img)
+    assert d.shape == (15, 9)
+    np.testing.assert_array_equal(d, img[0:30:2, 0:18:2])
+    assert so.octave_sizes(480, 640, so.Params()) == [(480, 640), (240, 320), (120, 160),
+                                                        (60, 80), (30, 40)]
+    assert len(so.octave_sizes(750, 1000, so.Params(upsample=True))) == 7
+    assert len(so.octave_sizes(1200, 1600, so.Params(upsample=True))) == 8
+
+
+# ------------------------------------------------------------------ extrema
+
+def _brute_candidates(D, p):
+    S, b = p.n_scales, p.border
+    _, h, w = D.shape
+    out = []
+    for s in range(1, S + 1):
+        for y in range(b, h - b):
+            for x in range(b, w - b):
+                c = D[s, y, x]
+                if not abs(c) > p.prefilter_ratio * p.contrast_thr:
+                    continue
+                nb = [D[s + a, y + bb, x + cc] for a in (-1, 0, 1) for bb in (-1, 0, 1)
+                      for cc in (-1, 0, 1) if (a, bb, cc) != (0, 0, 0)]
+                if all(c > v for v in nb) or all(c < v for v in nb):
+                    out.append((s, y, x))
+    return out
+
+
+def test_extrema_match_bruteforce_loop():
+    p = so.Params(contrast_thr=0.02)
+    D = RNG.normal(0, 0.02, size=(5, 23, 27))
+    D[2, 10, 12] = 0.3    # a planted maximum
+    D[1, 15, 7] = -0.3    # a planted minimum
+    D[3, 8, 20] = 0.3
+    D[3, 8, 21] = 0.3     # a plateau: strictness rejects both
+    cs, cy, cx, mg, me = so.find_candidates(D, p)
+    got = list(zip(cs.tolist(), cy.tolist(), cx.tolist()))
+    want = _brute_candidates(D, p)
+    assert got == want
+    assert (2, 10, 12) in got and (1, 15, 7) in got
+    assert (3, 8, 20) not in got and (3, 8, 21) not in got
+    assert np.all(mg > 0) and np.all(me > 0)
+
+
+def test_quadratic_dog_single_extremum_at_vertex():
+    p = so.Params(contrast_thr=0.001)
+    s_, y_, x_ = np.mgrid[0:5, 0:21, 0:21].astype(float)
+    D = 0.05 - 0.001 * ((x_ - 9) ** 2 + 2 * (y_ - 11) ** 2 + 3 * (s_ - 2) ** 2)
+    cs, cy, cx, _, _ = so.find_candidates(D, p)
+    assert list(zip(cs, cy, cx)) == [(2, 11, 9)]
+
+
+# --------------------------------------------------------------- refinement
+
+def _quadratic_stack(vertex, H, c0=0.04, shape=(5, 25, 25)):
+    s_, y_, x_ = np.mgrid[0:shape[0], 0:shape[1], 0:shape[2]].astype(float)
+    d = np.stack([x_ - vertex[0], y_ - vertex[1], s_ - vertex[2]])
+    q = np.einsum("i...,ij,j...->...", d, H, d)
+    return c0 + 0.5 * q
+
+
+def test_cramer_matches_linalg_solve():
+    for _ in range(50):
+        A = RNG.normal(size=(3, 3))
+        A = A @ A.T + 0.1 * np.eye(3)
+        bvec = RNG.normal(size=3)
+        np.testing.assert_allclose(so.cramer_solve(A, bvec), np.linalg.solve(A, bvec), rtol=1e-9)
+    assert so.cramer_solve(np.zeros((3, 3)), np.ones(3)) is None
+
+
+@pytest.mark.parametrize("off", [(0.3, -0.2, 0.1), (-0.45, 0.4, -0.35), (1.3, -0.2, 0.2),
+                                 (-2.2, 1.6, 0.3)])
+def test_refinement_recovers_quadratic_vertex(off):
+    """Central differences are exact on a quadratic, so the vertex is recovered
+    exactly, after one move per whole-pixel offset; the contrast is the vertex value."""
+    p = so.Params(contrast_thr=0.001)
+    H = -np.array([[0.010, 0.002, 0.001], [0.002, 0.012, -0.001], [0.001, -0.001, 0.02]])
+    v = (12 + off[0], 12 + off[1], 2 + off[2])
+    D = _quadratic_stack(v, H)
+    r = so.refine_candidate(D, 2, 12, 12, p)
+    assert r.code == so.KEEP
+    np.testing.assert_allclose([r.x + r.dx, r.y + r.dy, r.s + r.ds], v, atol=1e-10)
+    assert abs(r.response - 0.04) < 1e-12
+    assert max(abs(r.dx), abs(r.dy), abs(r.ds)) < 0.5
+
+
+def test_refinement_rejections():
+    p = so.Params(contrast_thr=0.001)
+    H = -np.diag([0.01, 0.01, 0.02])
+    D = _quadratic_stack((12.2, 12.1, 2.1), H, c0=0.0005)     # low contrast
+    assert so.refine_candidate(D, 2, 12, 12, p).code == so.REJ_CONTRAST
+    D = _quadratic_stack((12.2, 2.0, 2.1), H, shape=(5, 25, 25))  # vertex outside border
+    assert so.refine_candidate(D, 2, 6, 12, p).code == so.REJ_BOUNDS
+    D = np.zeros((5, 25, 25))
+    assert so.refine_candidate(D, 2, 12, 12, p).code == so.REJ_SINGULAR
+
+
+@pytest.mark.parametrize("a,b", [(1.0, 1.0), (1.0, 8.0), (1.0, 9.9), (1.0, 10.1), (1.0, 20.0),
+                                 (1.0, -1.0)])
+def test_edge_test_threshold(a, b):
+    """Spatial Hessian diag(a, b) is rejected iff (a+b)^2/(ab) >= (r+1)^2/r or ab <= 0."""
+    p = so.Params(contrast_thr=0.001, edge_ratio=10.0)
+    H = -0.001 * np.diag([a, b, 5.0])
+    D = _quadratic_stack((12.0, 12.0, 2.0), H)
+    r = so.refine_candidate(D, 2, 12, 12, p)
+    reject = a * b <= 0 or (a + b) ** 2 / (a * b) >= 121.0 / 10.0
+    assert (r.code == so.REJ_EDGE) == reject
+    if not reject:
+        assert r.code == so.KEEP
+
+
+# ------------------------------------------------------------------ blob scale
+
+@pytest.mark.parametrize("s", [3.0, 4.0, 6.0, 8.0, 11.0, 16.0])
+def test_blob_detected_at_predicted_scale(s):
+    """Continuous DoG of a Gaussian blob of width s between sigma and k*sigma peaks
+    at sigma* = sqrt(s^2 - sigma_in^2) / sqrt(k); the blob centre has dx = dy = 0."""
+    p = so.Params(contrast_thr=0.001)
+    n = 257 if s < 10 else 513
+    c = n // 2
+    Y, X = np.mgrid[0:n, 0:n]
+    img = 0.5 + 0.3 * np.exp(-((X - c) ** 2 + (Y - c) ** 2) / (2 * s * s))
+    r = so.extract(img, p, with_descriptors=False)
+    sel = (np.abs(r.x - c) < 1) & (np.abs(r.y - c) < 1)
+    assert sel.any()
+    pred = math.sqrt(s * s - p.init_blur ** 2) / math.sqrt(2 ** (1 / 3))
+    assert np.all(np.abs(r.sigma[sel] - pred) / pred < 1e-2)
+    assert np.all(np.abs(r.x[sel] - c) < 1e-9) and np.all(np.abs(r.y[sel] - c) < 1e-9)
+
+
+# ------------------------------------------------------------------ orientation
+
+@pytest.mark.parametrize("deg", [0.0, 30.0, 90.0, 200.0, 313.0, 47.0])
+def test_ramp_orientation(deg):
+    """A linear ramp has the same gradient everywhere: its orientation is the
+    nearest bin centre, exactly (the smoothed peak is symmetric)."""
+    p = so.Params()
+    th = math.radians(deg)
+    Y, X = np.mgrid[0:101, 0:101].astype(float)
+    L = 0.01 * (math.cos(th) * X + math.sin(th) * Y)
+    hist = so.orientation_histogram(L, 50, 50, 2.0, p)
+    nz = np.nonzero(hist)[0]
+    assert len(nz) == 1 and nz[0] == int(math.floor(deg / 10 + 0.5)) % 36
+    angles, _ = so.orientation_peaks(so.smooth_histogram(hist), p)
+    assert len(angles) == 1
+    assert abs(angles[0] - 10 * (int(math.floor(deg / 10 + 0.5)) % 36)) < 1e-9
+
+
+def test_smoothing_and_parabola():
+    h = np.zeros(36)
+    h[5] = 4.0
+    np.testing.assert_allclose(so.smooth_histogram(h)[[4, 5, 6]], [1.0, 2.0, 1.0])
+    assert so.smooth_histogram(h).sum() == pytest.approx(4.0)
+    # A parabola sampled at integer bins: refinement returns its exact vertex.
+    k = np.arange(36)
+    k0 = 17.3
+    hp = np.maximum(10.0 - (k - k0) ** 2, 0.0)
+    angles, _ = so.orientation_peaks(hp, so.Params())
+    assert len(angles) == 1 and abs(angles[0] - 10 * k0) < 1e-9
+    # Circular wrap: vertex at -0.2 reports 358 degrees.
+    hp = np.maximum(10.0 - ((k + 18) % 36 - 18 + 0.2) ** 2, 0.0)
+    angles, _ = so.orientation_peaks(hp, so.Params())
+    assert len(angles) == 1 and abs(angles[0] - 358.0) < 1e-9
+
+
+@pytest.mark.parametrize("ratio,npeaks", [(0.85, 2), (0.79, 1)])
+def test_secondary_peak_ratio(ratio, npeaks):
+    h = np.zeros(36)
+    h[3], h[20] = 1.0, ratio
+    angles, _ = so.orientation_peaks(h, so.Params())
+    assert len(angles) == npeaks
+    assert abs(angles[0] - 30.0) < 1e-9
+
+
+# ------------------------------------------------------------------ descriptor
+
+def test_descriptor_uniform_gradient_upright_two_bins():
+    """Upright on a uniform gradient at angle a: mass only in the two orientation
+    bins bracketing a*8/360; exactly one bin when a is a bin centre."""
+    p = so.Params()
+    Y, X = np.mgrid[0:121, 0:121].astype(float)
+    for deg, bins in ((100.0, {2, 3}), (45.0, {1}), (270.0, {6})):
+        th = math.radians(deg)
+        L = 0.01 * (math.cos(th) * X + math.sin(th) * Y)
+        d = so.descriptor(L, 60.3, 59.8, 60, 60, 2.5, 0.0, p).reshape(4, 4, 8)
+        assert abs(np.linalg.norm(d) - 1.0) < 1e-12
+        nz = set(np.nonzero(d.sum(axis=(0, 1)) > 1e-9)[0].tolist())
+        assert nz == bins
+
+
+def test_descriptor_clip_and_norm():
+    p = so.Params()
+    L = RNG.random((80, 80))
+    d = so.descriptor(L, 40.2, 39.7, 40, 40, 2.2, 37.0, p)
+    assert abs(np.linalg.norm(d) - 1.0) < 1e-12
+    assert np.all(d >= 0)
+    # Before the final renormalisation no entry exceeds the clip: after it, the
+    # largest entry is at most clip / ||clipped||.
+    assert d.max() <= 0.2 / np.linalg.norm(np.minimum(d, 0.2)) + 1e-12
+    assert np.all(so.descriptor(np.zeros((40, 40)), 20, 20, 20, 20, 2.0, 0.0, p) == 0)
+
+
+# ------------------------------------------------------------------ equivariance
+
+def _match_sets(a_keys, b_keys, tol):
+    a = np.asarray(a_keys)
+    b = np.asarray(b_keys)
+    used = np.zeros(len(b), bool)
+    pairs = []
+    for i in range(len(a)):
+        d = np.abs(b - a[i]).max(axis=1)
+        d[used] = np.inf
+        j = int(np.argmin(d))
+        if d[j] < tol:
+            used[j] = True
+            pairs.append((i, j))
+    return pairs
+
+
+def _angle_diff(a, b):
+    return np.abs((a - b + 180.0) % 360.0 - 180.0)
+
+
+def test_rot90_equivariance_octave0():
+    """Under a 90-degree counter-clockwise rotation (x, y) -> (y, W-1-x), octave-0
+    keypoints map one to one, the orientation shifts by -90 degrees and the
+    descriptor is unchanged (octave 0 involves no decimation, so it commutes)."""
+    p = so.Params()
+    img = synth.make_image(synth.rng_for(90, 0), 96, 112)
+    r0 = so.extract(img, p)
+    r1 = so.extract(np.rot90(img).copy(), p)
+    w = img.shape[1]
+    m0 = r0.octave == 0
+    m1 = r1.octave == 0
+    assert m0.sum() == m1.sum() and m0.sum() > 5
+    k0 = np.stack([r0.y[m0], w - 1 - r0.x[m0]], 1)
+    k1 = np.stack([r1.x[m1], r1.y[m1]], 1)
+    a0 = (r0.angle[m0] - 90.0) % 360.0
+    a1 = r1.angle[m1]
+    pairs = _match_sets(np.c_[k0, a0 / 1e3], np.c_[k1, a1 / 1e3], 1e-6)
+    assert len(pairs) == m0.sum()
+    d0 = r0.desc[m0]
+    d1 = r1.desc[m1]
+    for i, j in pairs:
+        assert _angle_diff(a0[i], a1[j]) < 1e-6
+        np.testing.assert_allclose(d0[i], d1[j], atol=1e-9)
+
+
+def test_rot90_upright_descriptor_permutation():
+    """Upright mode: rotating the image permutes the descriptor as
+    (v, u, o) -> (3 - u, v, o - 2 mod 8)."""
+    p = so.Params(upright=True)
+    img = synth.make_image(synth.rng_for(90, 1), 96, 96)
+    r0 = so.extract(img, p)
+    r1 = so.extract(np.rot90(img).copy(), p)
+    w = img.shape[1]
+    m0, m1 = r0.octave == 0, r1.octave == 0
+    k0 = np.stack([r0.y[m0], w - 1 - r0.x[m0]], 1)
+    k1 = np.stack([r1.x[m1], r1.y[m1]], 1)
+    pairs = _match_sets(k0, k1, 1e-6)
+    assert len(pairs) == m0.sum() == m1.sum() > 3
+    d0 = r0.desc[m0].reshape(-1, 4, 4, 8)
+    d1 = r1.desc[m1].reshape(-1, 4, 4, 8)
+    for i, j in pairs:
+        want = np.empty((4, 4, 8))
+        for v in range(4):
+            for u in range(4):
+                for o in range(8):
+                    want[3 - u, v, (o - 2) % 8] = d0[i, v, u, o]
+        np.testing.assert_allclose(d1[j], want, atol=1e-9)
+
+
+def test_transpose_equivariance_all_octaves():
+    """Transposing the image commutes with blur, decimation and upsampling, so every
+    keypoint maps (x, y) -> (y, x) with angle 90 - a, and the descriptor mirrors:
+    (v, u, o) -> (3 - v, u, -o mod 8)."""
+    p = so.Params(upsample=True)
+    img = synth.make_image(synth.rng_for(91, 0), 70, 90)
+    r0 = so.extract(img, p)
+    r1 = so.extract(img.T.copy(), p)
+    assert len(r0) == len(r1) > 10
+    assert set(r0.octave.tolist()) == set(r1.octave.tolist()) and r0.octave.max() >= 2
+    a0 = (90.0 - r0.angle) % 360.0
+    k0 = np.c_[r0.y, r0.x, r0.sigma, a0 / 1e3]
+    k1 = np.c_[r1.x, r1.y, r1.sigma, r1.angle / 1e3]
+    pairs = _match_sets(k0, k1, 1e-6)
+    assert len(pairs) == len(r0)
+    d0 = r0.desc.reshape(-1, 4, 4, 8)
+    d1 = r1.desc.reshape(-1, 4, 4, 8)
+    for i, j in pairs:
+        want = np.empty((4, 4, 8))
+        for v in range(4):
+            for u in range(4):
+                for o in range(8):
+                    want[3 - v, u, (-o) % 8] = d0[i, v, u, o]
+        np.testing.assert_allclose(d1[j], want, atol=1e-9)
+
+
+# ------------------------------------------------------------------ cap
+
+def test_cap_topk_bruteforce():
+    resp = RNG.integers(0, 20, size=200).astype(float)  # many ties
+    for k in (0, 1, 7, 50, 199, 200, 300):
+        got = so.cap_topk(resp, k)
+        if k <= 0 or k >= len(resp):
+            np.testing.assert_array_equal(got, np.arange(len(resp)))
+            continue
+        # Brute force: keep i iff fewer than k elements precede it in (-resp, index) order.
+        keep = [i for i in range(len(resp))
+                if sum(1 for j in range(len(resp))
+                       if (resp[j] > resp[i]) or (resp[j] == resp[i] and j < i)) < k]
+        np.testing.assert_array_equal(got, keep)
+
+
+def test_refinement_move_onto_border_is_rejected():
+    """A move that lands on x = W - b leaves the band [b, W - b) and is rejected;
+    one that lands on x = W - b - 1 is kept."""
+    p = so.Params(contrast_thr=0.001)
+    H = -np.diag([0.01, 0.012, 0.02])
+    w = 25
+    b = p.border
+    D = _quadratic_stack((w - b - 1 + 0.2, 12.0, 2.0), H)   # one move right, stays inside
+    r = so.refine_candidate(D, 2, 12, w - b - 2, p)
+    assert r.code == so.KEEP and r.x == w - b - 1
+    D = _quadratic_stack((w - b + 0.2, 12.0, 2.0), H)       # one move right, onto the edge
+    assert so.refine_candidate(D, 2, 12, w - b - 1, p).code == so.REJ_BOUNDS
+    D = _quadratic_stack((b - 1 + 0.1, 12.0, 2.0), H)       # one move left, onto b - 1
+    assert so.refine_candidate(D, 2, 12, b, p).code == so.REJ_BOUNDS
+
+
+@pytest.mark.parametrize("sigma_oct", [1.8, 2.5, 3.4])
+def test_orientation_window_mass_closed_form(sigma_oct):
+    """On a ramp every sample has the same magnitude, so the histogram's total is
+    m * (sum_k exp(-k^2 / (2 (1.5 sigma)^2)))^2 over k = -R..R, R = round(4.5 sigma)."""
+    p = so.Params()
+    Y, X = np.mgrid[0:121, 0:121].astype(float)
+    L = 0.003 * X + 0.004 * Y
+    m = 2.0 * math.hypot(0.003, 0.004)
+    hist = so.orientation_histogram(L, 60, 60, sigma_oct, p)
+    sw = 1.5 * sigma_oct
+    R = int(math.floor(4.5 * sigma_oct + 0.5))
+    k = np.arange(-R, R + 1)
+    want = m * np.exp(-(k * k) / (2 * sw * sw)).sum() ** 2
+    assert abs(hist.sum() - want) / want < 1e-12
+
+
+def test_descriptor_clip_is_active_on_concentrated_mass():
+    """Upright on a ramp along a bin centre: all mass sits in one orientation bin and
+    the central cells exceed 0.2 of the norm. After clipping, exactly those entries
+    are equal to the new maximum, which is below the unclipped maximum."""
+    Y, X = np.mgrid[0:121, 0:121].astype(float)
+    L = 0.01 * X   # gradient at 0 degrees
+    raw = so.descriptor(L, 60.0, 60.0, 60, 60, 2.5, 0.0, so.Params(desc_clip=1.0))
+    clp = so.descriptor(L, 60.0, 60.0, 60, 60, 2.5, 0.0, so.Params())
+    big = raw > 0.2
+    assert big.sum() >= 2 and raw.max() > 0.2
+    assert abs(np.linalg.norm(clp) - 1.0) < 1e-12
+    np.testing.assert_allclose(clp[big], clp.max(), rtol=1e-12)
+    assert np.all(clp[~big] < clp.max())
+    assert clp.max() < raw.max()
