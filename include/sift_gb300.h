@@ -1,0 +1,219 @@
+/*
+ * sift_gb300.h — C ABI of the GPU-resident, bitwise-deterministic SIFT extractor
+ * for NVIDIA GB300 (sm_103a).
+ *
+ * What it computes (PySIFT, arXiv 2605.17869, §3.2 "GPU Pipeline Stages" and
+ * Eq. 1): Gaussian scale-space pyramid built by separable blurs with 4-sigma
+ * truncation, difference of Gaussians, 3x3x3 extrema with a contrast gate,
+ * sub-pixel refinement solved by Cramer's rule (up to 5 iterations) with Hessian
+ * edge rejection, 36-bin orientation histograms smoothed with [1/4, 1/2, 1/4]
+ * and refined by a parabola, and 4x4x8 gradient descriptors with the 0.2 clip.
+ * Everything stays in device memory (§3.3): outputs are written into device
+ * buffers that callers wrap with DLPack.
+ *
+ * Determinism (§5, "Bitwise Deterministic GPU Execution"): no kernel uses
+ * atomics; histograms are per-lane private and merged in a fixed order, and
+ * keypoints are compacted by prefix scans in canonical order
+ * (octave, layer, row, column, orientation peak). An image's output is
+ * bit-identical whether it is extracted alone or inside any batch.
+ *
+ * Conventions
+ *  - Images are FP32 grayscale in [0, 1], row-major, with a row pitch given in
+ *    elements (pitch >= W). Image pointers are device pointers owned by the
+ *    caller; the extractor only reads them, and they must stay valid until the
+ *    work queued on the stream has run.
+ *  - Streams are passed as `void*` holding a cudaStream_t (NULL = legacy
+ *    default stream). Calls are asynchronous: they queue work and return
+ *    without waiting for the GPU. Argument errors are reported synchronously;
+ *    counts and truncation are device-side results.
+ *  - Output buffers are caller-owned device memory with capacity max_kpts
+ *    keypoints (descriptors: max_kpts x 128 floats, row-major).
+ *  - A handle owns its device workspace, plans and CUDA graphs. It is not
+ *    thread-safe: use one handle per host thread, and order calls on one
+ *    handle on a single stream (the workspace is reused by the next call).
+ *  - No entry point aborts; each returns a sift_status. sift_last_error()
+ *    gives a message for the last failure on a handle.
+ */
+#ifndef SIFT_GB300_H
+#define SIFT_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SIFT_OK = 0,
+  SIFT_W_TRUNCATED = 1,   /* a capacity was hit; output kept in canonical order */
+  SIFT_PENDING = 2,       /* serving: request not finished yet */
+  SIFT_E_INVALID = -1,    /* bad argument (null pointer, size < min_octave_side, ...) */
+  SIFT_E_OOM = -2,        /* device allocation failed */
+  SIFT_E_CUDA = -3,       /* a CUDA runtime call failed */
+  SIFT_E_BUDGET = -4,     /* serving: request can never fit the memory budget */
+  SIFT_E_TIMEOUT = -5,    /* a bounded wait ran out */
+  SIFT_E_NOTFOUND = -6    /* serving: unknown ticket */
+} sift_status;
+
+/* Extraction parameters. sift_params_default() gives plain SIFT as evaluated
+ * here: 3 scales per octave, sigma0 1.6, assumed input blur 0.5, no
+ * upsampling, octaves while min side >= 16, contrast threshold 0.04/3, edge
+ * ratio 10, border 5, 5 refinement iterations, pre-gate 0.5 x threshold,
+ * secondary orientation peaks at >= 0.8 of the maximum, no keypoint cap. */
+typedef struct {
+  int n_scales;          /* S: scales per octave (1..8) */
+  float sigma0;          /* base scale of each octave */
+  float init_blur;       /* blur already present in the input */
+  int upsample;          /* 1: first octave from the 2x bilinear magnified input */
+  int min_octave_side;   /* keep octaves while min(H_o, W_o) >= this (>= 16) */
+  float contrast_thr;    /* |interpolated DoG| must be >= this */
+  float edge_ratio;      /* principal curvature ratio limit r */
+  int border;            /* candidates need b <= x < W-b, b <= y < H-b */
+  int max_refine_iter;   /* refinement iterations (paper: 5) */
+  float prefilter_ratio; /* candidates need |D| > prefilter_ratio * contrast_thr */
+  float ori_peak_ratio;  /* orientation peaks >= ratio * histogram maximum */
+  int max_kpts;          /* output capacity and top-K cap (by response); > 0 */
+  int upright;           /* 1: orientation fixed to 0, one keypoint per extremum */
+  int dsp;               /* reserved (DSP-SIFT pooling, §3.2); must be 0 */
+  int rootsift;          /* 1: RootSIFT epilogue (L1 normalise, square root, §3.2) */
+} sift_params;
+
+/* Keypoint outputs: structure of arrays in device memory, capacity max_kpts.
+ * x, y, sigma are in input-image pixels (x right, y down); angle is in degrees
+ * in [0, 360), measured from +x towards +y; response is |interpolated DoG|;
+ * octave is the pyramid octave (0 = first, the magnified one when upsampling);
+ * layer is the DoG layer 1..S. */
+typedef struct {
+  float *x, *y, *sigma, *angle, *response;
+  int *octave, *layer;
+} sift_kpts_dev;
+
+typedef struct sift_handle sift_handle;
+typedef struct sift_server sift_server;
+
+/* Fill *p with the defaults above (max_kpts = 8192). */
+sift_status sift_params_default(sift_params *p);
+
+/* Create a handle. The handle copies *p; device workspace is allocated lazily
+ * on the first extraction and grown when a larger input arrives.
+ * Errors: SIFT_E_INVALID on a null or out-of-range parameter. */
+sift_status sift_create(const sift_params *p, sift_handle **out);
+
+/* Release a handle and all device memory, graphs and streams it owns. The
+ * caller must make sure no work queued by this handle is still running. */
+sift_status sift_destroy(sift_handle *h);
+
+/* Extract keypoints and descriptors of one image (Eq. 1, Pyr -> DoG -> Ext ->
+ * Ori -> Desc, all on the device).
+ *   img_dev      device pointer, H x W floats, row pitch pitch_elems (>= W)
+ *   stream       cudaStream_t the work is queued on
+ *   out_kpts     caller-owned SoA buffers, capacity max_kpts each
+ *   out_desc_dev caller-owned, max_kpts x 128 floats
+ *   out_count_dev caller-owned device int: number of keypoints written
+ * Keypoints beyond max_kpts are dropped keeping the largest responses (ties:
+ * canonical order); the kept ones are written in canonical order.
+ * Returns SIFT_OK once the work is queued; SIFT_E_INVALID for bad arguments
+ * (including min(H, W) below min_octave_side), SIFT_E_OOM / SIFT_E_CUDA on
+ * allocation or launch failure. */
+sift_status sift_extract(sift_handle *h, const float *img_dev, int H, int W, int pitch_elems,
+                         void *stream, sift_kpts_dev out_kpts, float *out_desc_dev,
+                         int *out_count_dev);
+
+/* Extract n images of arbitrary sizes in one pass: every stage runs as one
+ * persistent kernel per octave level over a flattened tile queue covering all
+ * images, captured in a CUDA graph. Each image's output is bit-identical to
+ * its sift_extract() output.
+ *   imgs_dev[i], H[i], W[i], pitch_elems[i]  host arrays describing image i
+ *   out_kpts[i], out_desc[i]                 host arrays of device buffers
+ *   out_counts_dev                           device int[n]
+ * Errors as sift_extract. */
+sift_status sift_extract_batch(sift_handle *h, int n, const float *const *imgs_dev,
+                               const int *H, const int *W, const int *pitch_elems, void *stream,
+                               const sift_kpts_dev *out_kpts, float *const *out_desc,
+                               int *out_counts_dev);
+
+/* Statistics of the last extraction on this handle, read after synchronising
+ * its stream. stats receives, per image i of the last call (up to max_images):
+ *   stats[4*i+0] candidates (extrema after the gate), stats[4*i+1] refined
+ *   keypoints, stats[4*i+2] oriented keypoints before the cap,
+ *   stats[4*i+3] truncation flags (bit 0 candidate capacity, bit 1 oriented
+ *   capacity, bit 2 top-K cap applied).
+ * Returns SIFT_W_TRUNCATED if any capacity was exceeded, else SIFT_OK. */
+sift_status sift_last_stats(sift_handle *h, int *stats, int max_images);
+
+/* Pyramid geometry for an H x W input under the handle's parameters:
+ * *n_octaves octaves; *total_elems floats for sift_build_pyramid's packed
+ * layout [octave][level 0..S+2][H_o][W_o] (no padding). */
+sift_status sift_pyramid_size(sift_handle *h, int H, int W, int *n_octaves, size_t *total_elems);
+
+/* Build the Gaussian pyramid of one image (the first stage of sift_extract,
+ * same kernels) and copy it, packed as above, into out_dev (capacity
+ * out_elems floats). For inspection and tests. */
+sift_status sift_build_pyramid(sift_handle *h, const float *img_dev, int H, int W,
+                               int pitch_elems, void *stream, float *out_dev, size_t out_elems);
+
+/* Per-kernel timing. When enabled, the graphs captured afterwards carry CUDA
+ * event nodes around the pyramid blur launches and the descriptor launch, and
+ * sift_kernel_times() returns, for the last extraction, the summed device time
+ * in milliseconds and launch count of each kernel class:
+ *   0 blur levels, 1 base level (blur of the input / magnified input),
+ *   2 DoG extrema scan, 3 keypoint stages (refine, orientation, compaction),
+ *   4 descriptor.
+ * Reading synchronises the handle's last stream. */
+sift_status sift_set_profiling(sift_handle *h, int enable);
+sift_status sift_kernel_times(sift_handle *h, double *ms, int *launches, int n_classes);
+
+/* Autotuner: time the blur and extrema kernels' tile shapes on a synthetic
+ * H x W workload on `stream` and keep the fastest. Tile shapes change only how
+ * work is distributed, never the arithmetic of any output, so tuned and
+ * untuned runs give bit-identical results. The choice can be saved and
+ * restored as a short JSON string. */
+sift_status sift_autotune(sift_handle *h, int H, int W, void *stream);
+sift_status sift_get_tuning(sift_handle *h, char *json, size_t len);
+sift_status sift_set_tuning(sift_handle *h, const char *json);
+
+/* ---------------------------------------------------------------- serving
+ * Continuous batching: a scheduler thread admits submitted requests while
+ * their device-memory estimate fits the budget and a slot is free, forms a
+ * step batch of everything admitted, and runs it on one of several worker
+ * streams, so steps overlap on the device. Requests that arrive while other
+ * steps are running join the next step. Pyramids and outputs stay on the
+ * device; results are library-owned until released. */
+typedef struct {
+  sift_status status;   /* SIFT_OK, SIFT_W_TRUNCATED or an error */
+  int count;            /* keypoints in the buffers below */
+  sift_kpts_dev kpts;   /* device buffers, valid until sift_serve_release */
+  float *desc;          /* device, count x 128 */
+  double submit_to_done_ms; /* host-measured latency of this request */
+} sift_result;
+
+/* mem_budget_bytes: device memory the server may use for in-flight requests;
+ * max_slots: most requests in flight at once. The server uses the handle's
+ * parameters; the handle itself must not be used while the server lives. */
+sift_status sift_serve_create(sift_handle *h, size_t mem_budget_bytes, int max_slots,
+                              sift_server **out);
+/* Queue one image. img_dev must stay valid until the request completes (poll
+ * returns something other than SIFT_PENDING). SIFT_E_BUDGET if the image
+ * alone exceeds the budget. */
+sift_status sift_serve_submit(sift_server *s, const float *img_dev, int H, int W, int pitch_elems,
+                              uint64_t *ticket);
+/* Non-blocking: SIFT_PENDING while queued or running; otherwise fills *out. */
+sift_status sift_serve_poll(sift_server *s, uint64_t ticket, sift_result *out);
+/* Block until the request is done or timeout_ms passes (SIFT_E_TIMEOUT). */
+sift_status sift_serve_wait(sift_server *s, uint64_t ticket, int timeout_ms, sift_result *out);
+/* Free a finished request's result buffers. */
+sift_status sift_serve_release(sift_server *s, uint64_t ticket);
+/* Stop the scheduler (waits for running steps) and free the server. */
+sift_status sift_serve_destroy(sift_server *s);
+
+/* Message describing the last error on the handle (never NULL). */
+const char *sift_last_error(sift_handle *h);
+
+/* Library version string. */
+const char *sift_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SIFT_GB300_H */

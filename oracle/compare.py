@@ -1,0 +1,90 @@
+"""Keypoint-set comparison between the CUDA extractor and the FP64 oracle
+(test infrastructure only).
+
+Outputs are compared as sets, never by index: FP32 rounding may flip a
+decision that sits within a hair of its threshold, which changes counts and
+therefore indices. The oracle records, for every keypoint, the smallest
+relative distance of any of its discrete decisions from the threshold; oracle
+keypoints closer than `margin_eps` (1e-4) to a threshold are excused.
+
+Tolerances (GPU FP32 vs oracle FP64): position within 0.01 px (input-image
+pixels), scale within 1e-3 relative, orientation within 0.5 degrees, and
+descriptor L2 difference at most 1e-3 on matched keypoints.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+POS_TOL = 0.01
+SIGMA_RTOL = 1e-3
+ANGLE_TOL = 0.5
+DESC_TOL = 1e-3
+MARGIN_EPS = 1e-4
+
+
+def angle_diff(a, b):
+    return np.abs((np.asarray(a) - np.asarray(b) + 180.0) % 360.0 - 180.0)
+
+
+@dataclass
+class Match:
+    n_oracle: int
+    n_eligible: int        # oracle keypoints not near a threshold
+    n_found: int           # eligible oracle keypoints matched by a GPU keypoint
+    n_gpu: int
+    n_gpu_unmatched: int   # GPU keypoints with no oracle keypoint at the same place
+    desc_max_l2: float
+    desc_pairs: int
+    worst: dict
+
+    @property
+    def found_frac(self):
+        return self.n_found / max(self.n_eligible, 1)
+
+
+def match(oracle_res, gpu: dict, margin_eps: float = MARGIN_EPS) -> Match:
+    """oracle_res: oracle Result; gpu: dict of numpy arrays (x, y, sigma, angle,
+    octave, layer, desc)."""
+    ox, oy, osig, oang = oracle_res.x, oracle_res.y, oracle_res.sigma, oracle_res.angle
+    ooct, olay = oracle_res.octave, oracle_res.layer
+    gx, gy, gsig, gang = (np.asarray(gpu[k], dtype=np.float64) for k in ("x", "y", "sigma", "angle"))
+    goct, glay = np.asarray(gpu["octave"]), np.asarray(gpu["layer"])
+    gdesc = np.asarray(gpu["desc"], dtype=np.float64)
+    eligible = oracle_res.margin >= margin_eps
+    n_found = 0
+    desc_max = 0.0
+    pairs = 0
+    worst = {"pos": 0.0, "sigma": 0.0, "angle": 0.0}
+    # Bucket GPU keypoints by (octave, layer) for the neighbour search.
+    buckets = {}
+    for i in range(len(gx)):
+        buckets.setdefault((int(goct[i]), int(glay[i])), []).append(i)
+    buckets = {k: np.array(v) for k, v in buckets.items()}
+    gpu_hit = np.zeros(len(gx), bool)
+    for i in range(len(ox)):
+        cand = buckets.get((int(ooct[i]), int(olay[i])))
+        if cand is None:
+            continue
+        dpos = np.maximum(np.abs(gx[cand] - ox[i]), np.abs(gy[cand] - oy[i]))
+        near = cand[dpos < POS_TOL]
+        if len(near) == 0:
+            continue
+        gpu_hit[near] = True
+        ds = np.abs(gsig[near] - osig[i]) / osig[i]
+        da = angle_diff(gang[near], oang[i])
+        ok = near[(ds < SIGMA_RTOL) & (da < ANGLE_TOL)]
+        if not eligible[i]:
+            continue
+        if len(ok):
+            n_found += 1
+            j = ok[np.argmin(angle_diff(gang[ok], oang[i]))]
+            worst["pos"] = max(worst["pos"], float(max(abs(gx[j] - ox[i]), abs(gy[j] - oy[i]))))
+            worst["sigma"] = max(worst["sigma"], float(abs(gsig[j] - osig[i]) / osig[i]))
+            worst["angle"] = max(worst["angle"], float(angle_diff(gang[j], oang[i])))
+            if len(oracle_res.desc) and len(gdesc):
+                desc_max = max(desc_max, float(np.linalg.norm(gdesc[j] - oracle_res.desc[i])))
+                pairs += 1
+    return Match(len(ox), int(eligible.sum()), n_found, len(gx), int((~gpu_hit).sum()),
+                 desc_max, pairs, worst)

@@ -1,0 +1,423 @@
+"""GPU-resident, bitwise-deterministic SIFT for NVIDIA GB300 (PySIFT, arXiv 2605.17869).
+
+Python binding of the C ABI in include/sift_gb300.h. Every function named
+`sift_*` here marshals its arguments into the library call of the same name;
+every step of the extraction runs in the library's CUDA kernels. PyTorch is
+used only to allocate device memory, name streams and hand results over by
+DLPack (§3.3). There is no CPU fallback: if the compiled library is missing,
+using this package raises.
+"""
+from __future__ import annotations
+
+import ctypes
+from ctypes import byref, c_double, c_int, c_size_t, c_uint64, c_void_p
+from dataclasses import dataclass
+
+from . import _abi
+from ._abi import (SIFT_E_BUDGET, SIFT_E_CUDA, SIFT_E_INVALID, SIFT_E_NOTFOUND, SIFT_E_OOM,
+                   SIFT_E_TIMEOUT, SIFT_OK, SIFT_PENDING, SIFT_W_TRUNCATED, STATUS_NAMES,
+                   SiftKptsDev, SiftParams, SiftResult)
+
+__all__ = [
+    "SiftError", "SiftParams", "SiftKptsDev", "SiftResult", "Features", "Extractor", "Server",
+    "sift_params_default", "sift_create", "sift_destroy", "sift_extract", "sift_extract_batch",
+    "sift_last_stats", "sift_pyramid_size", "sift_build_pyramid", "sift_set_profiling",
+    "sift_kernel_times", "sift_autotune", "sift_get_tuning", "sift_set_tuning",
+    "sift_serve_create", "sift_serve_submit", "sift_serve_poll", "sift_serve_wait",
+    "sift_serve_release", "sift_serve_destroy", "sift_last_error", "sift_version",
+    "SIFT_OK", "SIFT_W_TRUNCATED", "SIFT_PENDING", "SIFT_E_INVALID", "SIFT_E_OOM",
+    "SIFT_E_CUDA", "SIFT_E_BUDGET", "SIFT_E_TIMEOUT", "SIFT_E_NOTFOUND", "KERNEL_CLASSES",
+]
+
+KERNEL_CLASSES = ("blur", "base", "extrema", "decimate", "keypoint", "descriptor")
+
+
+class SiftError(RuntimeError):
+    def __init__(self, status: int, msg: str = ""):
+        self.status = status
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+
+
+def _lib():
+    return _abi.load()
+
+
+def _check(st: int, handle=None, what: str = "") -> int:
+    if st < 0:
+        msg = what
+        if handle is not None:
+            msg = f"{what}: {_lib().sift_last_error(handle).decode()}"
+        raise SiftError(st, msg)
+    return st
+
+
+# ------------------------------------------------------------ raw C ABI calls
+
+def sift_version() -> str:
+    return _lib().sift_version().decode()
+
+
+def sift_params_default() -> SiftParams:
+    p = SiftParams()
+    _check(_lib().sift_params_default(byref(p)))
+    return p
+
+
+def sift_create(params: SiftParams) -> c_void_p:
+    h = c_void_p()
+    _check(_lib().sift_create(byref(params), byref(h)), what="sift_create")
+    return h
+
+
+def sift_destroy(handle) -> None:
+    _check(_lib().sift_destroy(handle))
+
+
+def sift_last_error(handle) -> str:
+    return _lib().sift_last_error(handle).decode()
+
+
+def sift_extract(handle, img_ptr: int, H: int, W: int, pitch: int, stream: int,
+                 kpts: SiftKptsDev, desc_ptr: int, count_ptr: int) -> int:
+    return _check(_lib().sift_extract(handle, c_void_p(img_ptr), H, W, pitch, c_void_p(stream),
+                                      kpts, c_void_p(desc_ptr), c_void_p(count_ptr)),
+                  handle, "sift_extract")
+
+
+def sift_extract_batch(handle, img_ptrs, Hs, Ws, pitches, stream: int, kpts_list, desc_ptrs,
+                       counts_ptr: int) -> int:
+    n = len(img_ptrs)
+    return _check(_lib().sift_extract_batch(
+        handle, n, (c_void_p * n)(*img_ptrs), (c_int * n)(*Hs), (c_int * n)(*Ws),
+        (c_int * n)(*pitches), c_void_p(stream), (SiftKptsDev * n)(*kpts_list),
+        (c_void_p * n)(*desc_ptrs), c_void_p(counts_ptr)), handle, "sift_extract_batch")
+
+
+def sift_last_stats(handle, n_images: int):
+    buf = (c_int * (4 * n_images))()
+    st = _check(_lib().sift_last_stats(handle, buf, n_images), handle, "sift_last_stats")
+    rows = [tuple(buf[4 * i:4 * i + 4]) for i in range(n_images)]
+    return st, rows
+
+
+def sift_pyramid_size(handle, H: int, W: int):
+    no = c_int()
+    tot = c_size_t()
+    _check(_lib().sift_pyramid_size(handle, H, W, byref(no), byref(tot)), handle,
+           "sift_pyramid_size")
+    return no.value, tot.value
+
+
+def sift_build_pyramid(handle, img_ptr: int, H: int, W: int, pitch: int, stream: int,
+                       out_ptr: int, out_elems: int) -> int:
+    return _check(_lib().sift_build_pyramid(handle, c_void_p(img_ptr), H, W, pitch,
+                                            c_void_p(stream), c_void_p(out_ptr), out_elems),
+                  handle, "sift_build_pyramid")
+
+
+def sift_set_profiling(handle, enable: bool) -> None:
+    _check(_lib().sift_set_profiling(handle, int(bool(enable))), handle)
+
+
+def sift_kernel_times(handle):
+    n = len(KERNEL_CLASSES)
+    ms = (c_double * n)()
+    cnt = (c_int * n)()
+    _check(_lib().sift_kernel_times(handle, ms, cnt, n), handle, "sift_kernel_times")
+    return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+def sift_autotune(handle, H: int, W: int, stream: int) -> None:
+    _check(_lib().sift_autotune(handle, H, W, c_void_p(stream)), handle, "sift_autotune")
+
+
+def sift_get_tuning(handle) -> str:
+    buf = ctypes.create_string_buffer(512)
+    _check(_lib().sift_get_tuning(handle, buf, 512), handle, "sift_get_tuning")
+    return buf.value.decode()
+
+
+def sift_set_tuning(handle, js: str) -> None:
+    _check(_lib().sift_set_tuning(handle, js.encode()), handle, "sift_set_tuning")
+
+
+def sift_serve_create(handle, budget_bytes: int, max_slots: int) -> c_void_p:
+    s = c_void_p()
+    _check(_lib().sift_serve_create(handle, budget_bytes, max_slots, byref(s)), handle,
+           "sift_serve_create")
+    return s
+
+
+def sift_serve_submit(server, img_ptr: int, H: int, W: int, pitch: int) -> int:
+    t = c_uint64()
+    _check(_lib().sift_serve_submit(server, c_void_p(img_ptr), H, W, pitch, byref(t)),
+           what="sift_serve_submit")
+    return t.value
+
+
+def sift_serve_poll(server, ticket: int):
+    r = SiftResult()
+    st = _lib().sift_serve_poll(server, ticket, byref(r))
+    if st < 0:
+        raise SiftError(st, "sift_serve_poll")
+    return st, r
+
+
+def sift_serve_wait(server, ticket: int, timeout_ms: int = 60000):
+    r = SiftResult()
+    st = _lib().sift_serve_wait(server, ticket, timeout_ms, byref(r))
+    if st < 0:
+        raise SiftError(st, "sift_serve_wait")
+    return st, r
+
+
+def sift_serve_release(server, ticket: int) -> None:
+    _check(_lib().sift_serve_release(server, ticket), what="sift_serve_release")
+
+
+def sift_serve_destroy(server) -> None:
+    _check(_lib().sift_serve_destroy(server), what="sift_serve_destroy")
+
+
+# --------------------------------------------------------- torch-facing layer
+
+def _torch():
+    import torch  # noqa: PLC0415  (torch only provides memory, streams, DLPack)
+    return torch
+
+
+@dataclass
+class Features:
+    """Device-resident extraction result (torch CUDA tensors, length = count)."""
+    x: object
+    y: object
+    sigma: object
+    angle: object
+    response: object
+    octave: object
+    layer: object
+    desc: object
+    count: int
+
+    def as_numpy(self):
+        return {k: getattr(self, k).cpu().numpy() for k in
+                ("x", "y", "sigma", "angle", "response", "octave", "layer", "desc")}
+
+
+class OutputBuffers:
+    """Caller-owned output buffers for one image (capacity max_kpts)."""
+
+    def __init__(self, max_kpts: int, device):
+        torch = _torch()
+        self.K = max_kpts
+        f = dict(dtype=torch.float32, device=device)
+        i = dict(dtype=torch.int32, device=device)
+        self.x = torch.empty(max_kpts, **f)
+        self.y = torch.empty(max_kpts, **f)
+        self.sigma = torch.empty(max_kpts, **f)
+        self.angle = torch.empty(max_kpts, **f)
+        self.response = torch.empty(max_kpts, **f)
+        self.octave = torch.empty(max_kpts, **i)
+        self.layer = torch.empty(max_kpts, **i)
+        self.desc = torch.empty((max_kpts, 128), **f)
+
+    def kpts(self) -> SiftKptsDev:
+        return SiftKptsDev(self.x.data_ptr(), self.y.data_ptr(), self.sigma.data_ptr(),
+                           self.angle.data_ptr(), self.response.data_ptr(),
+                           self.octave.data_ptr(), self.layer.data_ptr())
+
+    def view(self, n: int) -> Features:
+        return Features(self.x[:n], self.y[:n], self.sigma[:n], self.angle[:n],
+                        self.response[:n], self.octave[:n], self.layer[:n], self.desc[:n], n)
+
+
+def params(**kw) -> SiftParams:
+    p = sift_params_default()
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise TypeError(f"unknown SIFT parameter {k!r}")
+        setattr(p, k, v)
+    return p
+
+
+class Extractor:
+    """One library handle plus reusable caller-owned output buffers.
+
+    extract(img) and extract_batch(imgs) take float32 CUDA tensors (H x W,
+    values in [0, 1]) and return device-resident Features. Work is queued on
+    the current torch stream; `sync=True` waits for the counts.
+    """
+
+    def __init__(self, **kw):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise SiftError(SIFT_E_CUDA, "no CUDA device: the extractor runs only on the GPU")
+        self.params = params(**kw)
+        self.handle = sift_create(self.params)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self._bufs = []
+        self._counts = None
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            _torch().cuda.synchronize()
+            sift_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _buffers(self, n: int):
+        torch = _torch()
+        while len(self._bufs) < n:
+            self._bufs.append(OutputBuffers(self.params.max_kpts, self.device))
+        if self._counts is None or self._counts.numel() < n:
+            self._counts = torch.zeros(max(n, 1), dtype=torch.int32, device=self.device)
+        return self._bufs[:n]
+
+    @staticmethod
+    def _check_img(img):
+        torch = _torch()
+        if not (img.is_cuda and img.dtype == torch.float32 and img.dim() == 2):
+            raise SiftError(SIFT_E_INVALID, "image must be a 2-D float32 CUDA tensor")
+        if img.stride(1) != 1:
+            raise SiftError(SIFT_E_INVALID, "image rows must be contiguous")
+        return img.shape[0], img.shape[1], img.stride(0)
+
+    def extract_async(self, img, stream=None):
+        """Queue one extraction; returns (buffers, counts tensor) without syncing."""
+        torch = _torch()
+        H, W, pitch = self._check_img(img)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        buf = self._buffers(1)[0]
+        sift_extract(self.handle, img.data_ptr(), H, W, pitch, s.cuda_stream, buf.kpts(),
+                     buf.desc.data_ptr(), self._counts.data_ptr())
+        return buf, self._counts[:1]
+
+    def extract(self, img, stream=None, copy: bool = True) -> Features:
+        buf, cnt = self.extract_async(img, stream)
+        n = int(cnt.item())
+        f = buf.view(n)
+        if copy:
+            f = Features(*(t.clone() for t in (f.x, f.y, f.sigma, f.angle, f.response,
+                                               f.octave, f.layer, f.desc)), n)
+        return f
+
+    def extract_batch_async(self, imgs, stream=None):
+        torch = _torch()
+        dims = [self._check_img(im) for im in imgs]
+        s = stream if stream is not None else torch.cuda.current_stream()
+        bufs = self._buffers(len(imgs))
+        sift_extract_batch(self.handle, [im.data_ptr() for im in imgs], [d[0] for d in dims],
+                           [d[1] for d in dims], [d[2] for d in dims], s.cuda_stream,
+                           [b.kpts() for b in bufs], [b.desc.data_ptr() for b in bufs],
+                           self._counts.data_ptr())
+        return bufs, self._counts[:len(imgs)]
+
+    def extract_batch(self, imgs, stream=None, copy: bool = True):
+        bufs, cnt = self.extract_batch_async(imgs, stream)
+        counts = cnt.tolist()
+        out = []
+        for b, n in zip(bufs, counts):
+            f = b.view(n)
+            if copy:
+                f = Features(*(t.clone() for t in (f.x, f.y, f.sigma, f.angle, f.response,
+                                                   f.octave, f.layer, f.desc)), n)
+            out.append(f)
+        return out
+
+    def stats(self, n_images: int = 1):
+        return sift_last_stats(self.handle, n_images)
+
+    def pyramid(self, img, stream=None):
+        """Gaussian pyramid as a list (per octave) of (S+3, H_o, W_o) tensors."""
+        torch = _torch()
+        H, W, pitch = self._check_img(img)
+        no, tot = sift_pyramid_size(self.handle, H, W)
+        out = torch.empty(tot, dtype=torch.float32, device=self.device)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        sift_build_pyramid(self.handle, img.data_ptr(), H, W, pitch, s.cuda_stream,
+                           out.data_ptr(), tot)
+        L = self.params.n_scales + 3
+        h = 2 * H if self.params.upsample else H
+        w = 2 * W if self.params.upsample else W
+        res, off = [], 0
+        for _ in range(no):
+            res.append(out[off:off + L * h * w].view(L, h, w))
+            off += L * h * w
+            h, w = h // 2, w // 2
+        return res
+
+    def set_profiling(self, on: bool):
+        sift_set_profiling(self.handle, on)
+
+    def kernel_times(self):
+        return sift_kernel_times(self.handle)
+
+    def autotune(self, H: int, W: int):
+        sift_autotune(self.handle, H, W, _torch().cuda.current_stream().cuda_stream)
+        return sift_get_tuning(self.handle)
+
+    def get_tuning(self) -> str:
+        return sift_get_tuning(self.handle)
+
+    def set_tuning(self, js: str):
+        sift_set_tuning(self.handle, js)
+
+
+# ----------------------------------------------------------------- serving
+
+class Server:
+    """Continuous-batching server over an Extractor's parameters.
+
+    submit() queues a device image and returns a ticket; result() waits and
+    returns Features whose tensors are zero-copy DLPack views of the server's
+    device buffers, valid until release(ticket).
+    """
+
+    def __init__(self, extractor: Extractor, budget_bytes: int = 8 << 30, max_slots: int = 64):
+        self.ex = extractor
+        self.K = extractor.params.max_kpts
+        self.srv = sift_serve_create(extractor.handle, budget_bytes, max_slots)
+
+    def submit(self, img) -> int:
+        H, W, pitch = Extractor._check_img(img)
+        return sift_serve_submit(self.srv, img.data_ptr(), H, W, pitch)
+
+    def poll(self, ticket: int):
+        st, r = sift_serve_poll(self.srv, ticket)
+        return None if st == SIFT_PENDING else self._features(r)
+
+    def result(self, ticket: int, timeout_ms: int = 60000):
+        st, r = sift_serve_wait(self.srv, ticket, timeout_ms)
+        return self._features(r), r.submit_to_done_ms, st
+
+    def _features(self, r: SiftResult) -> Features:
+        from ._dlpack import device_tensor
+        n = r.count
+        dev = self.ex.device.index
+        k = r.kpts
+        return Features(device_tensor(k.x, (n,), "f32", dev), device_tensor(k.y, (n,), "f32", dev),
+                        device_tensor(k.sigma, (n,), "f32", dev),
+                        device_tensor(k.angle, (n,), "f32", dev),
+                        device_tensor(k.response, (n,), "f32", dev),
+                        device_tensor(k.octave, (n,), "i32", dev),
+                        device_tensor(k.layer, (n,), "i32", dev),
+                        device_tensor(r.desc, (n, 128), "f32", dev), n)
+
+    def release(self, ticket: int):
+        sift_serve_release(self.srv, ticket)
+
+    def close(self):
+        if getattr(self, "srv", None) is not None:
+            sift_serve_destroy(self.srv)
+            self.srv = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

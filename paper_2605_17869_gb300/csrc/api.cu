@@ -1,0 +1,595 @@
+// C ABI of the extractor (declared in include/sift_gb300.h) and the
+// continuous-batching server.
+#include <chrono>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "engine.h"
+
+using sift::Engine;
+using sift::ImgIn;
+
+struct sift_handle {
+  Engine *eng = nullptr;
+  std::string err;
+  bool serving = false;
+};
+
+static sift_status fail(sift_handle *h, sift_status st, const std::string &m) {
+  if (h) h->err = m;
+  return st;
+}
+
+static sift_status pass(sift_handle *h, sift_status st) {
+  if (st != SIFT_OK && st != SIFT_W_TRUNCATED && h) h->err = h->eng->err;
+  return st;
+}
+
+static bool kpts_ok(const sift_kpts_dev &k) {
+  return k.x && k.y && k.sigma && k.angle && k.response && k.octave && k.layer;
+}
+
+extern "C" {
+
+sift_status sift_params_default(sift_params *p) {
+  if (!p) return SIFT_E_INVALID;
+  p->n_scales = 3;
+  p->sigma0 = 1.6f;
+  p->init_blur = 0.5f;
+  p->upsample = 0;
+  p->min_octave_side = 16;
+  p->contrast_thr = 0.04f / 3.0f;
+  p->edge_ratio = 10.0f;
+  p->border = 5;
+  p->max_refine_iter = 5;
+  p->prefilter_ratio = 0.5f;
+  p->ori_peak_ratio = 0.8f;
+  p->max_kpts = 8192;
+  p->upright = 0;
+  p->dsp = 0;
+  p->rootsift = 0;
+  return SIFT_OK;
+}
+
+sift_status sift_create(const sift_params *p, sift_handle **out) {
+  if (!p || !out) return SIFT_E_INVALID;
+  *out = nullptr;
+  std::string why;
+  if (sift::validate_params(*p, &why) != SIFT_OK) return SIFT_E_INVALID;
+  sift_handle *h = new sift_handle();
+  h->eng = new Engine(*p);
+  const sift_status st = h->eng->init();
+  if (st != SIFT_OK) {
+    delete h->eng;
+    delete h;
+    return st;
+  }
+  *out = h;
+  return SIFT_OK;
+}
+
+sift_status sift_destroy(sift_handle *h) {
+  if (!h) return SIFT_E_INVALID;
+  delete h->eng;
+  delete h;
+  return SIFT_OK;
+}
+
+const char *sift_last_error(sift_handle *h) {
+  if (!h) return "null handle";
+  return h->err.c_str();
+}
+
+const char *sift_version(void) { return "gb300-sift 0.1 (sm_103a)"; }
+
+sift_status sift_extract(sift_handle *h, const float *img_dev, int H, int W, int pitch_elems,
+                         void *stream, sift_kpts_dev out_kpts, float *out_desc_dev,
+                         int *out_count_dev) {
+  if (!h) return SIFT_E_INVALID;
+  if (h->serving) return fail(h, SIFT_E_INVALID, "handle is owned by a server");
+  if (!img_dev || !out_desc_dev || !out_count_dev || !kpts_ok(out_kpts))
+    return fail(h, SIFT_E_INVALID, "null pointer argument");
+  const int ms = h->eng->params().min_octave_side;
+  if (H < ms || W < ms || pitch_elems < W)
+    return fail(h, SIFT_E_INVALID, "image smaller than min_octave_side or pitch < W");
+  ImgIn in{img_dev, H, W, pitch_elems, out_kpts, out_desc_dev, out_count_dev};
+  return pass(h, h->eng->run(1, &in, (cudaStream_t)stream));
+}
+
+sift_status sift_extract_batch(sift_handle *h, int n, const float *const *imgs_dev, const int *H,
+                               const int *W, const int *pitch_elems, void *stream,
+                               const sift_kpts_dev *out_kpts, float *const *out_desc,
+                               int *out_counts_dev) {
+  if (!h) return SIFT_E_INVALID;
+  if (h->serving) return fail(h, SIFT_E_INVALID, "handle is owned by a server");
+  if (n < 1 || !imgs_dev || !H || !W || !out_kpts || !out_desc || !out_counts_dev)
+    return fail(h, SIFT_E_INVALID, "null pointer argument or n < 1");
+  const int ms = h->eng->params().min_octave_side;
+  std::vector<ImgIn> in(n);
+  for (int i = 0; i < n; i++) {
+    const int p = pitch_elems ? pitch_elems[i] : W[i];
+    if (!imgs_dev[i] || !out_desc[i] || !kpts_ok(out_kpts[i]))
+      return fail(h, SIFT_E_INVALID, "null pointer in image " + std::to_string(i));
+    if (H[i] < ms || W[i] < ms || p < W[i])
+      return fail(h, SIFT_E_INVALID, "image " + std::to_string(i) + " smaller than min_octave_side");
+    in[i] = ImgIn{imgs_dev[i], H[i], W[i], p, out_kpts[i], out_desc[i], out_counts_dev + i};
+  }
+  for (int b0 = 0; b0 < n; b0 += sift::kMaxImg) {
+    const int m = std::min(sift::kMaxImg, n - b0);
+    const sift_status st = h->eng->run(m, in.data() + b0, (cudaStream_t)stream);
+    if (st != SIFT_OK) return pass(h, st);
+  }
+  return SIFT_OK;
+}
+
+sift_status sift_last_stats(sift_handle *h, int *stats, int max_images) {
+  if (!h || !stats || max_images < 1) return SIFT_E_INVALID;
+  return pass(h, h->eng->last_stats(stats, max_images));
+}
+
+sift_status sift_pyramid_size(sift_handle *h, int H, int W, int *n_octaves, size_t *total_elems) {
+  if (!h || !n_octaves || !total_elems) return SIFT_E_INVALID;
+  int hs[sift::kMaxOct], ws[sift::kMaxOct];
+  const int no = h->eng->octave_sizes(H, W, hs, ws);
+  if (no == 0) return fail(h, SIFT_E_INVALID, "image smaller than min_octave_side");
+  size_t tot = 0;
+  const int L = h->eng->params().n_scales + 3;
+  for (int o = 0; o < no; o++) tot += (size_t)L * hs[o] * ws[o];
+  *n_octaves = no;
+  *total_elems = tot;
+  return SIFT_OK;
+}
+
+sift_status sift_build_pyramid(sift_handle *h, const float *img_dev, int H, int W,
+                               int pitch_elems, void *stream, float *out_dev, size_t out_elems) {
+  if (!h || !img_dev || !out_dev) return SIFT_E_INVALID;
+  int no = 0;
+  size_t need = 0;
+  sift_status st = sift_pyramid_size(h, H, W, &no, &need);
+  if (st != SIFT_OK) return st;
+  if (out_elems < need || pitch_elems < W) return fail(h, SIFT_E_INVALID, "output too small");
+  ImgIn in{img_dev, H, W, pitch_elems, {}, nullptr, nullptr};
+  cudaStream_t s = (cudaStream_t)stream;
+  st = h->eng->run_pyramid(in, s);
+  if (st != SIFT_OK) return pass(h, st);
+  const sift::Desc &hd = h->eng->host_desc();
+  const int L = h->eng->params().n_scales + 3;
+  const float *pyr = reinterpret_cast<const float *>(h->eng->workspace() + h->eng->layout().pyr);
+  size_t off = 0;
+  for (int o = 0; o < no; o++) {
+    const sift::OctDev &od = hd.oct[o];
+    for (int l = 0; l < L; l++) {
+      cudaError_t e = cudaMemcpy2DAsync(out_dev + off, od.W * sizeof(float),
+                                        pyr + od.lvl + (size_t)l * od.lstride,
+                                        od.pitch * sizeof(float), od.W * sizeof(float), od.H,
+                                        cudaMemcpyDeviceToDevice, s);
+      if (e != cudaSuccess) return fail(h, SIFT_E_CUDA, cudaGetErrorString(e));
+      off += (size_t)od.H * od.W;
+    }
+  }
+  return SIFT_OK;
+}
+
+sift_status sift_set_profiling(sift_handle *h, int enable) {
+  if (!h) return SIFT_E_INVALID;
+  h->eng->set_profiling(enable != 0);
+  return SIFT_OK;
+}
+
+sift_status sift_kernel_times(sift_handle *h, double *ms, int *launches, int n_classes) {
+  if (!h || n_classes < 1) return SIFT_E_INVALID;
+  return pass(h, h->eng->kernel_times(ms, launches, n_classes));
+}
+
+sift_status sift_autotune(sift_handle *h, int H, int W, void *stream) {
+  if (!h) return SIFT_E_INVALID;
+  const int ms = h->eng->params().min_octave_side;
+  if (H < ms || W < ms) return fail(h, SIFT_E_INVALID, "autotune size below min_octave_side");
+  return pass(h, h->eng->autotune(H, W, (cudaStream_t)stream));
+}
+
+sift_status sift_get_tuning(sift_handle *h, char *json, size_t len) {
+  if (!h || !json || len == 0) return SIFT_E_INVALID;
+  const sift::Tuning t = h->eng->tuning();
+  std::string s = "{\"blur_tile_rows\": [";
+  const int S = h->eng->params().n_scales;
+  for (int l = 1; l <= S + 2; l++) {
+    const int k = t.lvl_kind[l];
+    s += std::to_string(k == sift::TK_BLUR16 ? 16 : k == sift::TK_BLUR64 ? 64 : 32);
+    if (l < S + 2) s += ", ";
+  }
+  s += "]}";
+  if (s.size() + 1 > len) return fail(h, SIFT_E_INVALID, "buffer too small");
+  std::memcpy(json, s.c_str(), s.size() + 1);
+  return SIFT_OK;
+}
+
+sift_status sift_set_tuning(sift_handle *h, const char *json) {
+  if (!h || !json) return SIFT_E_INVALID;
+  const char *p = std::strchr(json, '[');
+  if (!p) return fail(h, SIFT_E_INVALID, "expected {\"blur_tile_rows\": [...]}");
+  sift::Tuning t = h->eng->tuning();
+  const int S = h->eng->params().n_scales;
+  p++;
+  for (int l = 1; l <= S + 2; l++) {
+    char *end = nullptr;
+    const long v = std::strtol(p, &end, 10);
+    if (end == p || (v != 16 && v != 32 && v != 64))
+      return fail(h, SIFT_E_INVALID, "tile rows must be 16, 32 or 64, one per level");
+    t.lvl_kind[l] = v == 16 ? sift::TK_BLUR16 : v == 64 ? sift::TK_BLUR64 : sift::TK_BLUR32;
+    p = end;
+    while (*p == ',' || *p == ' ') p++;
+  }
+  h->eng->set_tuning(t);
+  return SIFT_OK;
+}
+
+}  // extern "C"
+
+// ===================================================================== server
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+  uint64_t id = 0;
+  const float *img = nullptr;
+  int H = 0, W = 0, pitch = 0;
+  size_t out_bytes = 0, ws_bytes = 0;
+  Clock::time_point t_submit, t_done;
+  int state = 0;  // 0 queued, 1 running, 2 done
+  sift_status status = SIFT_PENDING;
+  int count = 0;
+  char *buf = nullptr;
+  sift_kpts_dev k{};
+  float *desc = nullptr;
+  int *dcount = nullptr;
+};
+
+struct Lane;
+
+struct Server;
+
+struct DoneMsg {
+  Server *srv;
+  int lane;
+};
+
+struct Lane {
+  Engine *eng = nullptr;
+  cudaStream_t stream = nullptr;
+  bool busy = false;
+  bool finished = false;
+  std::vector<uint64_t> reqs;
+  int *h_counts = nullptr;                 // pinned
+  sift::ImgCounters *h_flags = nullptr;    // pinned
+  Clock::time_point t_done;
+  DoneMsg msg{};
+};
+
+struct Server {
+  sift_handle *h = nullptr;
+  size_t budget = 0;
+  int max_slots = 0;
+  std::mutex mu;
+  std::condition_variable cv;      // scheduler wake-up
+  std::condition_variable cv_done; // request completion
+  std::thread th;
+  bool stop = false;
+  std::deque<uint64_t> queue;
+  std::unordered_map<uint64_t, Request> reqs;
+  std::vector<Lane> lanes;
+  size_t held = 0;                 // output bytes of admitted / finished requests
+  int in_flight = 0;
+  uint64_t next_id = 1;
+  std::string err;
+};
+
+size_t out_bytes_for(int K) {
+  return (size_t)K * (7 * sizeof(float) + sift::kDescLen * sizeof(float)) + 256;
+}
+
+void CUDART_CB on_lane_done(void *p) {
+  DoneMsg *m = static_cast<DoneMsg *>(p);
+  Server *s = m->srv;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->lanes[m->lane].finished = true;
+    s->lanes[m->lane].t_done = Clock::now();
+  }
+  s->cv.notify_all();
+}
+
+size_t lanes_ws(Server *s) {
+  size_t t = 0;
+  for (auto &l : s->lanes) t += l.eng->workspace() ? l.eng->layout().total : 0;
+  return t;
+}
+
+void retire(Server *s, Lane &l) {
+  for (size_t i = 0; i < l.reqs.size(); i++) {
+    auto it = s->reqs.find(l.reqs[i]);
+    if (it == s->reqs.end()) continue;
+    Request &r = it->second;
+    r.state = 2;
+    r.count = l.h_counts[i];
+    r.status = (l.h_flags[i].flags & (sift::TF_CAND | sift::TF_ORI)) ? SIFT_W_TRUNCATED : SIFT_OK;
+    r.t_done = l.t_done;
+    s->in_flight--;
+  }
+  l.reqs.clear();
+  l.busy = false;
+  l.finished = false;
+  s->cv_done.notify_all();
+}
+
+void launch_step(Server *s, int li, std::vector<uint64_t> &batch) {
+  Lane &l = s->lanes[li];
+  const int K = s->h->eng->params().max_kpts;
+  std::vector<ImgIn> in;
+  for (uint64_t id : batch) {
+    Request &r = s->reqs[id];
+    if (!r.buf) {
+      if (cudaMallocAsync(reinterpret_cast<void **>(&r.buf), r.out_bytes, l.stream) != cudaSuccess) {
+        cudaGetLastError();
+        r.state = 2;
+        r.status = SIFT_E_OOM;
+        r.t_done = Clock::now();
+        s->in_flight--;
+        continue;
+      }
+      float *f = reinterpret_cast<float *>(r.buf);
+      r.k.x = f;
+      r.k.y = f + K;
+      r.k.sigma = f + 2 * K;
+      r.k.angle = f + 3 * K;
+      r.k.response = f + 4 * K;
+      r.k.octave = reinterpret_cast<int *>(f + 5 * K);
+      r.k.layer = reinterpret_cast<int *>(f + 6 * K);
+      r.desc = f + 7 * K;
+      r.dcount = reinterpret_cast<int *>(f + 7 * K + (size_t)K * sift::kDescLen);
+    }
+    r.state = 1;
+    in.push_back(ImgIn{r.img, r.H, r.W, r.pitch, r.k, r.desc, r.dcount});
+    l.reqs.push_back(id);
+  }
+  if (in.empty()) return;
+  sift_status st = l.eng->run((int)in.size(), in.data(), l.stream);
+  cudaError_t e = cudaSuccess;
+  if (st == SIFT_OK) {
+    for (size_t i = 0; i < in.size() && e == cudaSuccess; i++)
+      e = cudaMemcpyAsync(l.h_counts + i, in[i].count, sizeof(int), cudaMemcpyDeviceToHost, l.stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(l.h_flags, l.eng->workspace() + l.eng->layout().cnt,
+                          in.size() * sizeof(sift::ImgCounters), cudaMemcpyDeviceToHost, l.stream);
+    if (e == cudaSuccess) e = cudaLaunchHostFunc(l.stream, on_lane_done, &l.msg);
+  }
+  if (st != SIFT_OK || e != cudaSuccess) {
+    for (uint64_t id : l.reqs) {
+      Request &r = s->reqs[id];
+      r.state = 2;
+      r.status = st != SIFT_OK ? st : SIFT_E_CUDA;
+      r.t_done = Clock::now();
+      s->in_flight--;
+    }
+    s->err = l.eng->err;
+    l.reqs.clear();
+    s->cv_done.notify_all();
+    return;
+  }
+  l.busy = true;
+  l.finished = false;
+}
+
+void scheduler(Server *s) {
+  std::unique_lock<std::mutex> lk(s->mu);
+  while (true) {
+    for (auto &l : s->lanes)
+      if (l.busy && l.finished) retire(s, l);
+    if (s->stop) {
+      bool any = false;
+      for (auto &l : s->lanes) any |= l.busy;
+      if (!any) break;
+    }
+    // Admit queued requests into a step for the first free lane.
+    int free_lane = -1;
+    for (size_t i = 0; i < s->lanes.size(); i++)
+      if (!s->lanes[i].busy) {
+        free_lane = (int)i;
+        break;
+      }
+    if (free_lane >= 0 && !s->queue.empty() && !s->stop) {
+      Engine *eng = s->lanes[free_lane].eng;
+      std::vector<uint64_t> batch;
+      std::vector<int> hs, ws;
+      size_t ws_now = lanes_ws(s) - (eng->workspace() ? eng->layout().total : 0);
+      while (!s->queue.empty() && (int)batch.size() < sift::kMaxImg &&
+             s->in_flight < s->max_slots) {
+        Request &r = s->reqs[s->queue.front()];
+        hs.push_back(r.H);
+        ws.push_back(r.W);
+        const size_t need_ws = eng->workspace_bytes((int)hs.size(), hs.data(), ws.data());
+        const size_t need = s->held + r.out_bytes + ws_now + need_ws + need_ws / 4;
+        if (need > s->budget) {
+          hs.pop_back();
+          ws.pop_back();
+          break;
+        }
+        s->held += r.out_bytes;
+        s->in_flight++;
+        batch.push_back(s->queue.front());
+        s->queue.pop_front();
+      }
+      if (!batch.empty()) {
+        launch_step(s, free_lane, batch);
+        continue;
+      }
+    }
+    s->cv.wait_for(lk, std::chrono::milliseconds(5));
+  }
+}
+
+}  // namespace
+
+struct sift_server {
+  Server s;
+};
+
+extern "C" {
+
+sift_status sift_serve_create(sift_handle *h, size_t mem_budget_bytes, int max_slots,
+                              sift_server **out) {
+  if (!h || !out || max_slots < 1 || mem_budget_bytes == 0) return SIFT_E_INVALID;
+  if (h->serving) return fail(h, SIFT_E_INVALID, "handle already owned by a server");
+  sift_server *sv = new sift_server();
+  Server &s = sv->s;
+  s.h = h;
+  s.budget = mem_budget_bytes;
+  s.max_slots = max_slots;
+  const int n_lanes = 3;
+  s.lanes.resize(n_lanes);
+  for (int i = 0; i < n_lanes; i++) {
+    Lane &l = s.lanes[i];
+    l.eng = new Engine(h->eng->params());
+    l.eng->set_tuning(h->eng->tuning());
+    sift_status st = l.eng->init();
+    cudaError_t e = cudaStreamCreateWithFlags(&l.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaHostAlloc(&l.h_counts, sift::kMaxImg * sizeof(int), 0);
+    if (e == cudaSuccess)
+      e = cudaHostAlloc(&l.h_flags, sift::kMaxImg * sizeof(sift::ImgCounters), 0);
+    l.msg = DoneMsg{&s, i};
+    if (st != SIFT_OK || e != cudaSuccess) {
+      for (auto &m : s.lanes) {
+        delete m.eng;
+        if (m.stream) cudaStreamDestroy(m.stream);
+        if (m.h_counts) cudaFreeHost(m.h_counts);
+        if (m.h_flags) cudaFreeHost(m.h_flags);
+      }
+      delete sv;
+      return fail(h, SIFT_E_CUDA, "server lane initialisation failed");
+    }
+  }
+  h->serving = true;
+  s.th = std::thread(scheduler, &s);
+  *out = sv;
+  return SIFT_OK;
+}
+
+sift_status sift_serve_submit(sift_server *sv, const float *img_dev, int H, int W, int pitch_elems,
+                              uint64_t *ticket) {
+  if (!sv || !img_dev || !ticket) return SIFT_E_INVALID;
+  Server &s = sv->s;
+  const sift_params &p = s.h->eng->params();
+  if (H < p.min_octave_side || W < p.min_octave_side || pitch_elems < W) return SIFT_E_INVALID;
+  Request r;
+  r.img = img_dev;
+  r.H = H;
+  r.W = W;
+  r.pitch = pitch_elems;
+  r.out_bytes = out_bytes_for(p.max_kpts);
+  r.ws_bytes = s.lanes[0].eng->workspace_bytes(1, &H, &W);
+  if (r.out_bytes + r.ws_bytes + r.ws_bytes / 4 > s.budget) return SIFT_E_BUDGET;
+  r.t_submit = Clock::now();
+  {
+    std::lock_guard<std::mutex> lk(s.mu);
+    if (s.stop) return SIFT_E_INVALID;
+    r.id = s.next_id++;
+    *ticket = r.id;
+    s.reqs.emplace(r.id, r);
+    s.queue.push_back(r.id);
+  }
+  s.cv.notify_all();
+  return SIFT_OK;
+}
+
+static void fill_result(const Request &r, sift_result *out) {
+  out->status = r.status;
+  out->count = r.count;
+  out->kpts = r.k;
+  out->desc = r.desc;
+  out->submit_to_done_ms =
+      std::chrono::duration<double, std::milli>(r.t_done - r.t_submit).count();
+}
+
+sift_status sift_serve_poll(sift_server *sv, uint64_t ticket, sift_result *out) {
+  if (!sv || !out) return SIFT_E_INVALID;
+  Server &s = sv->s;
+  std::lock_guard<std::mutex> lk(s.mu);
+  auto it = s.reqs.find(ticket);
+  if (it == s.reqs.end()) return SIFT_E_NOTFOUND;
+  if (it->second.state != 2) return SIFT_PENDING;
+  fill_result(it->second, out);
+  return it->second.status;
+}
+
+sift_status sift_serve_wait(sift_server *sv, uint64_t ticket, int timeout_ms, sift_result *out) {
+  if (!sv || !out) return SIFT_E_INVALID;
+  Server &s = sv->s;
+  std::unique_lock<std::mutex> lk(s.mu);
+  const auto deadline = Clock::now() + std::chrono::milliseconds(timeout_ms);
+  while (true) {
+    auto it = s.reqs.find(ticket);
+    if (it == s.reqs.end()) return SIFT_E_NOTFOUND;
+    if (it->second.state == 2) {
+      fill_result(it->second, out);
+      return it->second.status;
+    }
+    if (s.cv_done.wait_until(lk, deadline) == std::cv_status::timeout) {
+      it = s.reqs.find(ticket);
+      if (it != s.reqs.end() && it->second.state == 2) {
+        fill_result(it->second, out);
+        return it->second.status;
+      }
+      return SIFT_E_TIMEOUT;
+    }
+  }
+}
+
+sift_status sift_serve_release(sift_server *sv, uint64_t ticket) {
+  if (!sv) return SIFT_E_INVALID;
+  Server &s = sv->s;
+  {
+    std::lock_guard<std::mutex> lk(s.mu);
+    auto it = s.reqs.find(ticket);
+    if (it == s.reqs.end()) return SIFT_E_NOTFOUND;
+    if (it->second.state != 2) return SIFT_PENDING;
+    if (it->second.buf) cudaFreeAsync(it->second.buf, s.lanes[0].stream);
+    s.held -= it->second.out_bytes;
+    s.reqs.erase(it);
+  }
+  s.cv.notify_all();
+  return SIFT_OK;
+}
+
+sift_status sift_serve_destroy(sift_server *sv) {
+  if (!sv) return SIFT_E_INVALID;
+  Server &s = sv->s;
+  {
+    std::lock_guard<std::mutex> lk(s.mu);
+    s.stop = true;
+  }
+  s.cv.notify_all();
+  if (s.th.joinable()) s.th.join();
+  for (auto &l : s.lanes) cudaStreamSynchronize(l.stream);
+  for (auto &kv : s.reqs)
+    if (kv.second.buf) cudaFreeAsync(kv.second.buf, s.lanes[0].stream);
+  for (auto &l : s.lanes) {
+    cudaStreamSynchronize(l.stream);
+    delete l.eng;
+    cudaStreamDestroy(l.stream);
+    cudaFreeHost(l.h_counts);
+    cudaFreeHost(l.h_flags);
+  }
+  s.h->serving = false;
+  delete sv;
+  return SIFT_OK;
+}
+
+}  // extern "C"

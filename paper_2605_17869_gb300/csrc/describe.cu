@@ -1,0 +1,399 @@
+// Orientation and descriptor (§3.2), output cap, and the deterministic
+// reduction scheme of §5 ("Bitwise Deterministic GPU Execution").
+//
+// Each keypoint is handled by one warp. Lanes sweep the sample window in a
+// fixed interleaved order and accumulate into lane-private histogram columns
+// in shared memory (layout [bin][lane], so no two lanes ever touch the same
+// word and there are no bank conflicts). The 32 columns are then summed bin by
+// bin in ascending lane order. No atomics are used anywhere: the sum order is
+// fixed by the code, so outputs are bitwise reproducible.
+#include "scan.cuh"
+#include "sift_dev.cuh"
+
+namespace sift {
+
+namespace {
+
+constexpr float kTwoPi = 6.283185307179586f;
+constexpr int kOriWarps = 8;
+constexpr int kDescWarps = 4;
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ float sigma_of(const Desc *d, const RefRec &r) {
+  return d->sigma0 * exp2f(((float)r.s + r.ds) / (float)d->n_scales);
+}
+
+// ------------------------------------------------------------ orientation
+
+__global__ void __launch_bounds__(kOriWarps * 32) k_orientation(const Desc *__restrict__ d) {
+  __shared__ float hist[kOriWarps][kOriBins][32];
+  __shared__ float hsum[kOriWarps][kOriBins];
+  __shared__ float hsm[kOriWarps][kOriBins];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int n = d->n_img;
+  const int total = d->cand_flat[n];
+  for (int t = blockIdx.x * kOriWarps + warp; t < total; t += gridDim.x * kOriWarps) {
+    const int b = find_owner(d->cand_flat, n, t);
+    const ImgDev &im = d->img[b];
+    const long long slot = im.cand_off + (t - d->cand_flat[b]);
+    if (d->code[slot] != RC_KEEP) {
+      if (lane == 0) d->npk[slot] = 0;
+      continue;
+    }
+    if (d->upright) {
+      if (lane == 0) {
+        d->npk[slot] = 1;
+        d->angs[slot * kMaxPeaks] = 0.f;
+      }
+      continue;
+    }
+    const RefRec r = d->ref[slot];
+    const OctDev od = d->oct[im.oct0 + r.o];
+    const float *L = d->pyr + od.lvl + (long long)r.s * od.lstride;
+    const float sw = 1.5f * sigma_of(d, r);
+    const int R = (int)floorf(3.0f * sw + 0.5f);
+    const float ninv = -1.0f / (2.0f * sw * sw);
+    for (int k = 0; k < kOriBins; k++) hist[warp][k][lane] = 0.f;
+    const int side = 2 * R + 1, ns = side * side;
+    for (int idx = lane; idx < ns; idx += 32) {
+      const int jj = idx / side;
+      const int i = idx - jj * side - R, j = jj - R;
+      const int px = r.x + i, py = r.y + j;
+      if (px < 1 || px > od.W - 2 || py < 1 || py > od.H - 2) continue;
+      const float *p = L + (long long)py * od.pitch + px;
+      const float dx = __ldg(p + 1) - __ldg(p - 1);
+      const float dy = __ldg(p + od.pitch) - __ldg(p - od.pitch);
+      const float mag = sqrtf(dx * dx + dy * dy);
+      float th = atan2f(dy, dx);
+      if (th < 0.f) th += kTwoPi;
+      int bin = (int)floorf(th * ((float)kOriBins / kTwoPi) + 0.5f);
+      if (bin >= kOriBins) bin -= kOriBins;
+      hist[warp][bin][lane] += expf((float)(i * i + j * j) * ninv) * mag;
+    }
+    __syncwarp();
+    for (int k = lane; k < kOriBins; k += 32) {
+      float s = 0.f;
+      for (int q = 0; q < 32; q++) s += hist[warp][k][q];
+      hsum[warp][k] = s;
+    }
+    __syncwarp();
+    float hmax = 0.f;
+    for (int k = lane; k < kOriBins; k += 32) {
+      const float hm = hsum[warp][(k + kOriBins - 1) % kOriBins];
+      const float hp = hsum[warp][(k + 1) % kOriBins];
+      const float v = 0.25f * hm + 0.5f * hsum[warp][k] + 0.25f * hp;
+      hsm[warp][k] = v;
+      hmax = fmaxf(hmax, v);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) hmax = fmaxf(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
+    __syncwarp();
+    const float thr = d->ori_peak_ratio * hmax;
+    int base = 0;
+    for (int k0 = 0; k0 < kOriBins; k0 += 32) {
+      const int k = k0 + lane;
+      bool peak = false;
+      float ang = 0.f;
+      if (k < kOriBins) {
+        const float hk = hsm[warp][k];
+        const float hm = hsm[warp][(k + kOriBins - 1) % kOriBins];
+        const float hp = hsm[warp][(k + 1) % kOriBins];
+        if (hk > hm && hk > hp && hk >= thr) {
+          peak = true;
+          float kf = (float)k + 0.5f * (hm - hp) / (hm - 2.0f * hk + hp);
+          if (kf < 0.f) kf += (float)kOriBins;
+          if (kf >= (float)kOriBins) kf -= (float)kOriBins;
+          ang = kf * (360.0f / (float)kOriBins);
+          if (ang >= 360.0f) ang -= 360.0f;
+        }
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, peak);
+      if (peak) d->angs[slot * kMaxPeaks + base + __popc(m & ((1u << lane) - 1u))] = ang;
+      base += __popc(m);
+    }
+    if (lane == 0) d->npk[slot] = base;
+    __syncwarp();
+  }
+}
+
+// --------------------------------------------- oriented keypoint compaction
+
+__global__ void __launch_bounds__(kThreads) k_cc_count(const Desc *__restrict__ d) {
+  __shared__ int tmp[kThreads / 32 + 1];
+  constexpr int SPT = kChunk / kThreads;
+  const int n = d->n_img;
+  for (int c = blockIdx.x; c < d->n_cc_chunks; c += gridDim.x) {
+    const int b = find_owner(d->cc_pre, n, c);
+    const ImgDev &im = d->img[b];
+    const int nc = d->cnt[b].n_cand;
+    const int s0 = (c - d->cc_pre[b]) * kChunk + threadIdx.x * SPT;
+    int v = 0;
+#pragma unroll
+    for (int k = 0; k < SPT; k++)
+      if (s0 + k < nc) v += d->npk[im.cand_off + s0 + k];
+    const int tot = block_sum(v, tmp);
+    if (threadIdx.x == 0) d->cc_cnt[c] = tot;
+  }
+}
+
+// One block: per image scan of chunk counts, oriented totals, the final
+// (capped) counts, their prefix over images, and the caller's count output.
+__global__ void __launch_bounds__(1024) k_cc_scan(const Desc *__restrict__ d) {
+  __shared__ int tmp[1024 / 32 + 1];
+  const int n = d->n_img;
+  int flat = 0;
+  for (int b = 0; b < n; b++) {
+    const ImgDev &im = d->img[b];
+    int carry = 0;
+    for (int base = 0; base < im.cc_n; base += blockDim.x) {
+      const int i = base + threadIdx.x;
+      const int v = i < im.cc_n ? d->cc_cnt[im.cc0 + i] : 0;
+      int tot;
+      const int ex = block_excl_scan(v, tmp, &tot);
+      if (i < im.cc_n) d->cc_off[im.cc0 + i] = carry + ex;
+      carry += tot;
+    }
+    const int no = min(carry, im.ori_cap);
+    const int nf = min(no, im.kcap);
+    if (threadIdx.x == 0) {
+      ImgCounters &k = d->cnt[b];
+      k.n_ori_raw = carry;
+      k.n_ori = no;
+      k.n_fin = nf;
+      k.flags |= (carry > im.ori_cap ? TF_ORI : 0) | (no > im.kcap ? TF_TOPK : 0);
+      d->fin_flat[b] = flat;
+      if (im.ocount) *im.ocount = nf;
+    }
+    flat += nf;
+  }
+  if (threadIdx.x == 0) d->fin_flat[n] = flat;
+}
+
+__global__ void __launch_bounds__(kThreads) k_cc_emit(const Desc *__restrict__ d) {
+  __shared__ int tmp[kThreads / 32 + 1];
+  constexpr int SPT = kChunk / kThreads;
+  const int n = d->n_img;
+  for (int c = blockIdx.x; c < d->n_cc_chunks; c += gridDim.x) {
+    const int b = find_owner(d->cc_pre, n, c);
+    const ImgDev &im = d->img[b];
+    const int nc = d->cnt[b].n_cand;
+    const int s0 = (c - d->cc_pre[b]) * kChunk + threadIdx.x * SPT;
+    int np[SPT];
+    int v = 0;
+#pragma unroll
+    for (int k = 0; k < SPT; k++) {
+      np[k] = (s0 + k < nc) ? d->npk[im.cand_off + s0 + k] : 0;
+      v += np[k];
+    }
+    int tot;
+    int j = d->cc_off[c] + block_excl_scan(v, tmp, &tot);
+    if (tot == 0) continue;
+#pragma unroll
+    for (int k = 0; k < SPT; k++) {
+      if (!np[k]) continue;
+      const long long slot = im.cand_off + s0 + k;
+      const uint32_t key = __float_as_uint(d->ref[slot].resp);
+      for (int p = 0; p < np[k]; p++, j++) {
+        if (j < im.ori_cap) {
+          d->ori[im.ori_off + j] = make_int2(s0 + k, p);
+          d->okey[im.ori_off + j] = key;
+        }
+      }
+    }
+  }
+}
+
+// --------------------------------------------------------- top-K cap
+
+// Per image (one block): if more than kcap oriented keypoints, keep the kcap
+// largest responses, ties broken by canonical order, and list the kept indices
+// in canonical order. The threshold is found by a bitwise search on the
+// response bits (responses are non-negative, so bit order = value order).
+__global__ void __launch_bounds__(1024) k_select(const Desc *__restrict__ d) {
+  __shared__ int tmp[1024 / 32 + 1];
+  const int n_img = d->n_img;
+  for (int b = blockIdx.x; b < n_img; b += gridDim.x) {
+    const ImgDev &im = d->img[b];
+    const int n = d->cnt[b].n_ori;
+    const int K = im.kcap;
+    if (n <= K) continue;
+    const uint32_t *key = d->okey + im.ori_off;
+    uint32_t thr = 0;
+    for (int bit = 31; bit >= 0; bit--) {
+      const uint32_t cand = thr | (1u << bit);
+      int c = 0;
+      for (int j = threadIdx.x; j < n; j += blockDim.x) c += key[j] >= cand;
+      if (block_sum(c, tmp) >= K) thr = cand;
+    }
+    int cg = 0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) cg += key[j] > thr;
+    const int need_eq = K - block_sum(cg, tmp);
+    int out = 0, eq_seen = 0;
+    for (int base = 0; base < n; base += blockDim.x) {
+      const int j = base + threadIdx.x;
+      const uint32_t kv = j < n ? key[j] : 0u;
+      const int is_eq = (j < n && kv == thr) ? 1 : 0;
+      int eq_tot;
+      const int eq_rank = eq_seen + block_excl_scan(is_eq, tmp, &eq_tot);
+      const int keep = (j < n && (kv > thr || (is_eq && eq_rank < need_eq))) ? 1 : 0;
+      int k_tot;
+      const int pos = out + block_excl_scan(keep, tmp, &k_tot);
+      if (keep) d->fin[im.fin_off + pos] = j;
+      out += k_tot;
+      eq_seen += eq_tot;
+    }
+  }
+}
+
+// ------------------------------------------------------------- descriptor
+
+__global__ void __launch_bounds__(kDescWarps * 32) k_descriptor(const Desc *__restrict__ d) {
+  extern __shared__ float dsm[];
+  float *hist = dsm + (threadIdx.x >> 5) * (kDescLen * 32);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int n = d->n_img;
+  const int total = d->fin_flat[n];
+  for (int t = blockIdx.x * kDescWarps + warp; t < total; t += gridDim.x * kDescWarps) {
+    const int b = find_owner(d->fin_flat, n, t);
+    const ImgDev &im = d->img[b];
+    const int j = t - d->fin_flat[b];
+    const int oi = (d->cnt[b].n_ori > im.kcap) ? d->fin[im.fin_off + j] : j;
+    const int2 e = d->ori[im.ori_off + oi];
+    const long long slot = im.cand_off + e.x;
+    const RefRec r = d->ref[slot];
+    const float angle = d->angs[slot * kMaxPeaks + e.y];
+    const OctDev od = d->oct[im.oct0 + r.o];
+    const float sig = sigma_of(d, r);
+    if (lane == 0) {
+      const float sc = ldexpf(d->upsample ? 0.5f : 1.0f, r.o);
+      im.ox[j] = ((float)r.x + r.dx) * sc;
+      im.oy[j] = ((float)r.y + r.dy) * sc;
+      im.osig[j] = sig * sc;
+      im.oang[j] = angle;
+      im.oresp[j] = r.resp;
+      im.ooct[j] = r.o;
+      im.olay[j] = r.s;
+    }
+    const float *L = d->pyr + od.lvl + (long long)r.s * od.lstride;
+    const float wbin = 3.0f * sig;
+    const float inv_w = 1.0f / wbin;
+    const int R = (int)floorf(wbin * 1.41421356237f * 2.5f + 0.5f);
+    const float th = angle * (kTwoPi / 360.0f);
+    float st, ct;
+    sincosf(th, &st, &ct);
+    for (int k = 0; k < kDescLen; k++) hist[k * 32 + lane] = 0.f;
+    const int side = 2 * R + 1, ns = side * side;
+    for (int idx = lane; idx < ns; idx += 32) {
+      const int jj = idx / side;
+      const int i = idx - jj * side - R, jy = jj - R;
+      const int px = r.x + i, py = r.y + jy;
+      if (px < 1 || px > od.W - 2 || py < 1 || py > od.H - 2) continue;
+      const float ox = (float)i - r.dx, oy = (float)jy - r.dy;
+      const float rx = (ct * ox + st * oy) * inv_w;
+      const float ry = (-st * ox + ct * oy) * inv_w;
+      const float u = rx + 1.5f, v = ry + 1.5f;
+      if (!(u > -1.f && u < 4.f && v > -1.f && v < 4.f)) continue;
+      const float *p = L + (long long)py * od.pitch + px;
+      const float gx = __ldg(p + 1) - __ldg(p - 1);
+      const float gy = __ldg(p + od.pitch) - __ldg(p - od.pitch);
+      const float mag = sqrtf(gx * gx + gy * gy);
+      float phi = atan2f(gy, gx) - th;
+      if (phi < 0.f) phi += kTwoPi;
+      if (phi < 0.f) phi += kTwoPi;
+      if (phi >= kTwoPi) phi -= kTwoPi;
+      const float ob = phi * (8.0f / kTwoPi);
+      const float wt = mag * expf(-(rx * rx + ry * ry) * 0.125f);
+      const float u0f = floorf(u), v0f = floorf(v), o0f = floorf(ob);
+      const float fu = u - u0f, fv = v - v0f, fo = ob - o0f;
+      const int u0 = (int)u0f, v0 = (int)v0f, o0 = (int)o0f;
+#pragma unroll
+      for (int dv = 0; dv < 2; dv++) {
+        const int vv = v0 + dv;
+        if (vv < 0 || vv > 3) continue;
+        const float wv = dv ? fv : 1.f - fv;
+#pragma unroll
+        for (int du = 0; du < 2; du++) {
+          const int uu = u0 + du;
+          if (uu < 0 || uu > 3) continue;
+          const float wu = du ? fu : 1.f - fu;
+#pragma unroll
+          for (int dob = 0; dob < 2; dob++) {
+            const int oo = (o0 + dob) & 7;
+            const float wo = dob ? fo : 1.f - fo;
+            hist[((vv * 4 + uu) * 8 + oo) * 32 + lane] += wt * wv * wu * wo;
+          }
+        }
+      }
+    }
+    __syncwarp();
+    float val[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const float *h = hist + (lane + 32 * q) * 32;
+      float s = 0.f;
+      for (int l = 0; l < 32; l++) s += h[l];
+      val[q] = s;
+    }
+    float sq = val[0] * val[0] + val[1] * val[1] + val[2] * val[2] + val[3] * val[3];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    float *out = im.odesc + (long long)j * kDescLen;
+    if (sq > 0.f) {
+      float nrm = sqrtf(sq);
+#pragma unroll
+      for (int q = 0; q < 4; q++) val[q] = fminf(val[q] / nrm, 0.2f);
+      sq = val[0] * val[0] + val[1] * val[1] + val[2] * val[2] + val[3] * val[3];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+      nrm = sqrtf(sq);
+#pragma unroll
+      for (int q = 0; q < 4; q++) val[q] = val[q] / nrm;
+      if (d->rootsift) {
+        float l1 = val[0] + val[1] + val[2] + val[3];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) l1 += __shfl_xor_sync(0xffffffffu, l1, o);
+#pragma unroll
+        for (int q = 0; q < 4; q++) val[q] = sqrtf(val[q] / l1);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; q++) val[q] = 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) out[lane + 32 * q] = val[q];
+    __syncwarp();
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_orientation(const Desc *d, int grid, cudaStream_t s) {
+  k_orientation<<<grid, kOriWarps * 32, 0, s>>>(d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ori_compact(const Desc *d, int grid, cudaStream_t s) {
+  k_cc_count<<<grid, kThreads, 0, s>>>(d);
+  k_cc_scan<<<1, 1024, 0, s>>>(d);
+  k_cc_emit<<<grid, kThreads, 0, s>>>(d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_select(const Desc *d, int grid, cudaStream_t s) {
+  k_select<<<grid, 1024, 0, s>>>(d);
+  return cudaGetLastError();
+}
+
+int descriptor_smem_bytes() { return kDescWarps * kDescLen * 32 * (int)sizeof(float); }
+
+cudaError_t descriptor_set_attributes() {
+  return cudaFuncSetAttribute(k_descriptor, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              descriptor_smem_bytes());
+}
+
+cudaError_t launch_descriptor(const Desc *d, int grid, cudaStream_t s) {
+  k_descriptor<<<grid, kDescWarps * 32, descriptor_smem_bytes(), s>>>(d);
+  return cudaGetLastError();
+}
+
+}  // namespace sift

@@ -1,0 +1,676 @@
+// Host planner and launch sequencing for the extractor.
+//
+// Per call the host computes the octave geometry of every image, the
+// flattened tile queues (one per octave and tile kind), the compaction chunk
+// tables and the workspace slices, writes them into a pinned descriptor and
+// copies it to the device on the caller's stream. The launch sequence itself
+// (per octave: base blur or decimation, S+2 level blurs, extrema scan; then
+// compaction, refinement, orientation, compaction, cap, descriptor) is a CUDA
+// graph keyed only by the largest octave count of the batch, because every
+// kernel reads its geometry from the descriptor and uses a persistent grid.
+#include <algorithm>
+#include <cmath>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+
+#include "engine.h"
+
+namespace sift {
+
+namespace {
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
+constexpr size_t kAlign = 256;
+}  // namespace
+
+int gaussian_taps(double sigma, BlurTaps *t) {
+  std::memset(t, 0, sizeof(*t));
+  if (!(sigma > 0.0)) {
+    t->w[0] = 1.0f;
+    return 0;
+  }
+  const int r = (int)std::ceil(4.0 * sigma);
+  if (r > kMaxR) return -1;
+  double w[2 * kMaxR + 1];
+  double sum = 0.0;
+  for (int k = -r; k <= r; k++) {
+    w[k + r] = std::exp(-(double)k * k / (2.0 * sigma * sigma));
+    sum += w[k + r];
+  }
+  for (int k = 0; k <= 2 * r; k++) t->w[k] = (float)(w[k] / sum);
+  return r;
+}
+
+static double level_sigma(const sift_params &p, int i) {
+  return (double)p.sigma0 * std::pow(2.0, (double)i / p.n_scales);
+}
+
+static double base_sigma(const sift_params &p) {
+  const double eff = (double)p.init_blur * (p.upsample ? 2.0 : 1.0);
+  const double d = (double)p.sigma0 * p.sigma0 - eff * eff;
+  return d > 0 ? std::sqrt(d) : 0.0;
+}
+
+sift_status validate_params(const sift_params &p, std::string *why) {
+  auto bad = [&](const char *m) {
+    if (why) *why = m;
+    return SIFT_E_INVALID;
+  };
+  if (p.n_scales < 2 || p.n_scales > kMaxScales) return bad("n_scales must be in 2..6");
+  if (!(p.sigma0 > 0.f)) return bad("sigma0 must be > 0");
+  if (!(p.init_blur >= 0.f)) return bad("init_blur must be >= 0");
+  if (!(p.contrast_thr > 0.f)) return bad("contrast_thr must be > 0");
+  if (!(p.edge_ratio > 0.f)) return bad("edge_ratio must be > 0");
+  if (!(p.prefilter_ratio >= 0.f)) return bad("prefilter_ratio must be >= 0");
+  if (!(p.ori_peak_ratio > 0.f && p.ori_peak_ratio <= 1.f)) return bad("ori_peak_ratio in (0, 1]");
+  if (p.border < 1) return bad("border must be >= 1");
+  if (p.max_refine_iter < 1) return bad("max_refine_iter must be >= 1");
+  if (p.max_kpts < 1) return bad("max_kpts must be >= 1");
+  if (p.dsp != 0) return bad("dsp pooling is not available");
+  BlurTaps t;
+  int rmax = gaussian_taps(base_sigma(p), &t);
+  for (int i = 1; i <= p.n_scales + 2 && rmax >= 0; i++) {
+    const double k = std::sqrt(level_sigma(p, i) * level_sigma(p, i) -
+                               level_sigma(p, i - 1) * level_sigma(p, i - 1));
+    const int r = gaussian_taps(k, &t);
+    rmax = r < 0 ? -1 : std::max(rmax, r);
+  }
+  if (rmax < 0) return bad("sigma0 too large: blur radius above 16");
+  if (p.min_octave_side < 16 || p.min_octave_side <= rmax || p.min_octave_side <= 2 * p.border)
+    return bad("min_octave_side must be >= 16, above the blur radius and twice the border");
+  return SIFT_OK;
+}
+
+Engine::Engine(const sift_params &p) : P_(p) {}
+
+Engine::~Engine() {
+  drop_graphs();
+  if (ws_) cudaFree(ws_);
+  if (ddesc_) cudaFree(ddesc_);
+  for (int i = 0; i < kRing; i++) {
+    if (hdesc_[i]) cudaFreeHost(hdesc_[i]);
+    if (hevt_[i]) cudaEventDestroy(hevt_[i]);
+  }
+  if (done_) cudaEventDestroy(done_);
+  if (cap_) cudaStreamDestroy(cap_);
+}
+
+sift_status Engine::init() {
+  if (inited_) return SIFT_OK;
+  std::string why;
+  if (validate_params(P_, &why) != SIFT_OK) {
+    err = why;
+    return SIFT_E_INVALID;
+  }
+  cudaError_t e = cudaGetDevice(&dev_);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm_, cudaDevAttrMultiProcessorCount, dev_);
+  if (e == cudaSuccess) e = blur_set_attributes();
+  if (e == cudaSuccess) e = descriptor_set_attributes();
+  if (e == cudaSuccess) e = cudaMalloc(&ddesc_, sizeof(Desc));
+  for (int i = 0; i < kRing && e == cudaSuccess; i++) {
+    e = cudaHostAlloc(&hdesc_[i], sizeof(Desc), cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&hevt_[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) std::memset(hdesc_[i], 0, sizeof(Desc));
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done_, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap_, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    err = std::string("CUDA initialisation failed: ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? SIFT_E_OOM : SIFT_E_CUDA;
+  }
+  S_ = P_.n_scales;
+  base_R_ = gaussian_taps(base_sigma(P_), &base_t_);
+  for (int i = 1; i <= S_ + 2; i++) {
+    const double k = std::sqrt(level_sigma(P_, i) * level_sigma(P_, i) -
+                               level_sigma(P_, i - 1) * level_sigma(P_, i - 1));
+    lvl_R_[i] = gaussian_taps(k, &lvl_t_[i]);
+    tun_.lvl_kind[i] = TK_BLUR32;
+  }
+  tun_.grid_mult_blur = 4;
+  inited_ = true;
+  return SIFT_OK;
+}
+
+int Engine::octave_sizes(int H, int W, int *hs, int *ws) const {
+  int h = P_.upsample ? 2 * H : H, w = P_.upsample ? 2 * W : W;
+  int n = 0;
+  while (std::min(h, w) >= P_.min_octave_side && n < kMaxOct) {
+    if (hs) hs[n] = h;
+    if (ws) ws[n] = w;
+    n++;
+    h /= 2;
+    w /= 2;
+  }
+  return n;
+}
+
+namespace {
+// Candidate slots per image: one per 32 octave pixels, at least 8192.
+int cand_capacity(long long octave_px) {
+  long long c = octave_px / 32;
+  c = std::max<long long>(c, 8192);
+  c = std::min<long long>(c, 1 << 22);
+  return (int)((c + kChunk - 1) / kChunk * kChunk);
+}
+int tile_h_of(int kind) { return kind == TK_BLUR16 ? 16 : kind == TK_BLUR64 ? 64 : 32; }
+}  // namespace
+
+size_t Engine::workspace_bytes(int n, const int *H, const int *W) const {
+  size_t pyr = 0, bm = 0, cand = 0, ori = 0, fin = 0, chunks = 0;
+  for (int b = 0; b < n; b++) {
+    int hs[kMaxOct], ws[kMaxOct];
+    const int no = octave_sizes(H[b], W[b], hs, ws);
+    long long px = 0, words = 0;
+    for (int o = 0; o < no; o++) {
+      const long long pitch = align_up(ws[o], 32);
+      pyr += (size_t)(S_ + 3) * hs[o] * pitch;
+      words += (long long)S_ * hs[o] * ((ws[o] + 31) / 32);
+      px += (long long)hs[o] * ws[o];
+    }
+    bm += words;
+    const int cc = cand_capacity(px);
+    cand += cc;
+    ori += 2 * (size_t)cc;
+    fin += P_.max_kpts;
+    chunks += div_up(words, kChunk) + cc / kChunk;
+  }
+  return pyr * 4 + bm * 4 + cand * (16 + sizeof(RefRec) + 8 + 4 * kMaxPeaks) + ori * 12 +
+         fin * 4 + chunks * 8 + 16 * kAlign + kMaxImg * 48;
+}
+
+sift_status Engine::fill_plan(int n, const ImgIn *in, Desc &hd, WsLayout &L, int *max_oct) const {
+  hd.n_img = n;
+  hd.n_scales = S_;
+  hd.upsample = P_.upsample ? 1 : 0;
+  hd.sigma0 = P_.sigma0;
+  hd.contrast_thr = P_.contrast_thr;
+  hd.prefilter = (float)((double)P_.prefilter_ratio * (double)P_.contrast_thr);
+  hd.edge_ratio = P_.edge_ratio;
+  hd.border = P_.border;
+  hd.max_iter = P_.max_refine_iter;
+  hd.upright = P_.upright ? 1 : 0;
+  hd.rootsift = P_.rootsift ? 1 : 0;
+  hd.ori_peak_ratio = P_.ori_peak_ratio;
+  size_t pyr = 0, bm = 0, cand = 0, ori = 0, fin = 0;
+  int bmc = 0, cc = 0, oc = 0, M = 0;
+  for (int b = 0; b < n; b++) {
+    ImgDev &d = hd.img[b];
+    std::memset(&d, 0, sizeof(d));
+    d.src = in[b].src;
+    d.H = in[b].H;
+    d.W = in[b].W;
+    d.spitch = in[b].pitch;
+    d.src_vec_ok = ((reinterpret_cast<uintptr_t>(in[b].src) & 15) == 0 && (in[b].pitch & 3) == 0);
+    int hs[kMaxOct], ws[kMaxOct];
+    const int no = octave_sizes(in[b].H, in[b].W, hs, ws);
+    if (no == 0) return SIFT_E_INVALID;
+    d.n_oct = no;
+    d.oct0 = oc;
+    M = std::max(M, no);
+    d.bm_begin = (long long)bm;
+    long long px = 0;
+    for (int o = 0; o < no; o++) {
+      OctDev &od = hd.oct[oc + o];
+      od.H = hs[o];
+      od.W = ws[o];
+      od.pitch = (int)align_up(ws[o], 32);
+      od.wpr = (ws[o] + 31) / 32;
+      od.lvl = (long long)pyr;
+      od.lstride = (long long)od.H * od.pitch;
+      pyr += (size_t)(S_ + 3) * od.lstride;
+      od.bm = (long long)bm;
+      bm += (size_t)S_ * od.H * od.wpr;
+      px += (long long)od.H * od.W;
+    }
+    d.bm_words = (long long)bm - d.bm_begin;
+    d.bmc0 = bmc;
+    d.bmc_n = div_up(d.bm_words, kChunk);
+    bmc += d.bmc_n;
+    d.cand_cap = cand_capacity(px);
+    d.cand_off = (long long)cand;
+    cand += d.cand_cap;
+    d.cc0 = cc;
+    d.cc_n = d.cand_cap / kChunk;
+    cc += d.cc_n;
+    d.ori_cap = 2 * d.cand_cap;
+    d.ori_off = (long long)ori;
+    ori += d.ori_cap;
+    d.kcap = P_.max_kpts;
+    d.fin_off = (long long)fin;
+    fin += d.kcap;
+    d.ox = in[b].k.x;
+    d.oy = in[b].k.y;
+    d.osig = in[b].k.sigma;
+    d.oang = in[b].k.angle;
+    d.oresp = in[b].k.response;
+    d.ooct = in[b].k.octave;
+    d.olay = in[b].k.layer;
+    d.odesc = in[b].desc;
+    d.ocount = in[b].count;
+    oc += no;
+  }
+  hd.n_oct_max = M;
+  hd.n_bm_chunks = bmc;
+  hd.n_cc_chunks = cc;
+  for (int k = 0; k < TK_COUNT; k++) {
+    for (int o = 0; o < kMaxOct; o++) {
+      int *pre = hd.tile_pre[k][o];
+      pre[0] = 0;
+      for (int b = 0; b < n; b++) {
+        int t = 0;
+        if (o < hd.img[b].n_oct) {
+          const OctDev &od = hd.oct[hd.img[b].oct0 + o];
+          if (k == TK_EXT) t = od.wpr * div_up(od.H, kExtTH);
+          else t = div_up(od.W, kBlurTW) * div_up(od.H, tile_h_of(k));
+        }
+        pre[b + 1] = pre[b] + t;
+      }
+    }
+  }
+  hd.bmc_pre[0] = 0;
+  hd.cc_pre[0] = 0;
+  for (int b = 0; b < n; b++) {
+    hd.bmc_pre[b + 1] = hd.bmc_pre[b] + hd.img[b].bmc_n;
+    hd.cc_pre[b + 1] = hd.cc_pre[b] + hd.img[b].cc_n;
+  }
+  size_t off = 0;
+  auto put = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + bytes, kAlign);
+    return o;
+  };
+  L.pyr = put(pyr * sizeof(float));
+  L.bm = put(bm * sizeof(uint32_t));
+  L.cand = put(cand * sizeof(int4));
+  L.ref = put(cand * sizeof(RefRec));
+  L.code = put(cand * sizeof(int));
+  L.npk = put(cand * sizeof(int));
+  L.angs = put(cand * kMaxPeaks * sizeof(float));
+  L.ori = put(ori * sizeof(int2));
+  L.okey = put(ori * sizeof(uint32_t));
+  L.fin = put(fin * sizeof(int));
+  L.bm_cnt = put(bmc * sizeof(int));
+  L.bm_off = put(bmc * sizeof(int));
+  L.cc_cnt = put(cc * sizeof(int));
+  L.cc_off = put(cc * sizeof(int));
+  L.cnt = put(kMaxImg * sizeof(ImgCounters));
+  L.cand_flat = put((kMaxImg + 1) * sizeof(int));
+  L.fin_flat = put((kMaxImg + 1) * sizeof(int));
+  L.total = off;
+  *max_oct = M;
+  return SIFT_OK;
+}
+
+sift_status Engine::ensure_workspace(size_t bytes) {
+  if (bytes <= ws_cap_) return SIFT_OK;
+  if (ws_) {
+    cudaFree(ws_);  // synchronises the device: earlier launches finish first
+    ws_ = nullptr;
+    ws_cap_ = 0;
+  }
+  const size_t want = align_up(bytes + bytes / 4, 1 << 20);
+  cudaError_t e = cudaMalloc(&ws_, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ws_ = nullptr;
+    err = "workspace allocation of " + std::to_string(want) + " bytes failed";
+    return SIFT_E_OOM;
+  }
+  ws_cap_ = want;
+  return SIFT_OK;
+}
+
+sift_status Engine::upload(Desc *hd, size_t bytes, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyAsync(ddesc_, hd, bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaEventRecord(hevt_[ring_], s);
+  if (e != cudaSuccess) {
+    err = std::string("descriptor upload failed: ") + cudaGetErrorString(e);
+    return SIFT_E_CUDA;
+  }
+  return SIFT_OK;
+}
+
+int Engine::grid_blur(int R, int kind, int mode) const {
+  const int per_sm = blur_blocks_per_sm(R, kind, mode);
+  return std::max(1, n_sm_ * per_sm);
+}
+
+cudaError_t Engine::enqueue_pyramid(cudaStream_t s, int M, std::vector<ProfRec> *prof) {
+  cudaError_t e = cudaSuccess;
+  auto rec = [&](int cls, auto &&fn) {
+    if (e != cudaSuccess) return;
+    ProfRec r{nullptr, nullptr, cls};
+    if (prof) {
+      cudaEventCreate(&r.a);
+      cudaEventCreate(&r.b);
+      e = cudaEventRecordWithFlags(r.a, s, cudaEventRecordExternal);
+    }
+    if (e == cudaSuccess) e = fn();
+    if (prof && e == cudaSuccess) {
+      e = cudaEventRecordWithFlags(r.b, s, cudaEventRecordExternal);
+      prof->push_back(r);
+    }
+  };
+  const Desc *d = ddesc_;
+  const int g4 = n_sm_ * 4;
+  for (int o = 0; o < M; o++) {
+    if (o == 0) {
+      const int mode = P_.upsample ? 2 : 1;
+      rec(PC_BASE, [&] {
+        return launch_base_blur(d, base_R_, base_t_, TK_BLUR32, P_.upsample != 0,
+                                grid_blur(base_R_, TK_BLUR32, mode), s);
+      });
+    } else {
+      rec(PC_DECIMATE, [&] { return launch_decimate(d, o, g4, s); });
+    }
+    for (int l = 1; l <= S_ + 2; l++) {
+      const int kind = tun_.lvl_kind[l];
+      rec(PC_BLUR, [&] {
+        return launch_level_blur(d, o, l, lvl_R_[l], lvl_t_[l], kind, grid_blur(lvl_R_[l], kind, 0), s);
+      });
+    }
+  }
+  return e;
+}
+
+cudaError_t Engine::enqueue_all(cudaStream_t s, int M, std::vector<ProfRec> *prof) {
+  cudaError_t e = cudaSuccess;
+  auto rec = [&](int cls, auto &&fn) {
+    if (e != cudaSuccess) return;
+    ProfRec r{nullptr, nullptr, cls};
+    if (prof) {
+      cudaEventCreate(&r.a);
+      cudaEventCreate(&r.b);
+      e = cudaEventRecordWithFlags(r.a, s, cudaEventRecordExternal);
+    }
+    if (e == cudaSuccess) e = fn();
+    if (prof && e == cudaSuccess) {
+      e = cudaEventRecordWithFlags(r.b, s, cudaEventRecordExternal);
+      prof->push_back(r);
+    }
+  };
+  const Desc *d = ddesc_;
+  const int g4 = n_sm_ * 4;
+  for (int o = 0; o < M; o++) {
+    if (o == 0) {
+      const int mode = P_.upsample ? 2 : 1;
+      rec(PC_BASE, [&] {
+        return launch_base_blur(d, base_R_, base_t_, TK_BLUR32, P_.upsample != 0,
+                                grid_blur(base_R_, TK_BLUR32, mode), s);
+      });
+    } else {
+      rec(PC_DECIMATE, [&] { return launch_decimate(d, o, g4, s); });
+    }
+    for (int l = 1; l <= S_ + 2; l++) {
+      const int kind = tun_.lvl_kind[l];
+      rec(PC_BLUR, [&] {
+        return launch_level_blur(d, o, l, lvl_R_[l], lvl_t_[l], kind, grid_blur(lvl_R_[l], kind, 0), s);
+      });
+    }
+    rec(PC_EXTREMA, [&] { return launch_extrema(d, o, S_, n_sm_ * 8, s); });
+  }
+  rec(PC_KEYPOINT, [&] { return launch_bm_compact(d, g4, s); });
+  rec(PC_KEYPOINT, [&] { return launch_refine(d, g4, s); });
+  rec(PC_KEYPOINT, [&] { return launch_orientation(d, g4, s); });
+  rec(PC_KEYPOINT, [&] { return launch_ori_compact(d, g4, s); });
+  rec(PC_KEYPOINT, [&] { return launch_select(d, n_sm_, s); });
+  rec(PC_DESCRIPTOR, [&] { return launch_descriptor(d, n_sm_ * 3, s); });
+  return e;
+}
+
+void Engine::drop_graphs() {
+  for (auto &kv : graphs_) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.prof) {
+      for (auto &r : *kv.second.prof) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+      }
+      delete kv.second.prof;
+    }
+  }
+  graphs_.clear();
+  last_prof_ = nullptr;
+}
+
+sift_status Engine::get_graph(int M, cudaGraphExec_t *out) {
+  const int key = M * 2 + (profiling_ ? 1 : 0);
+  auto it = graphs_.find(key);
+  if (it != graphs_.end()) {
+    *out = it->second.exec;
+    last_prof_ = it->second.prof;
+    return SIFT_OK;
+  }
+  GraphEntry ge;
+  if (profiling_) ge.prof = new std::vector<ProfRec>();
+  cudaError_t e = cudaStreamBeginCapture(cap_, cudaStreamCaptureModeThreadLocal);
+  cudaError_t e1 = e == cudaSuccess ? enqueue_all(cap_, M, ge.prof) : e;
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(cap_, &g) : e;
+  cudaError_t e3 = (e1 == cudaSuccess && e2 == cudaSuccess) ? cudaGraphInstantiate(&ge.exec, g, 0)
+                                                             : (e1 != cudaSuccess ? e1 : e2);
+  if (g) cudaGraphDestroy(g);
+  if (e3 != cudaSuccess) {
+    cudaGetLastError();
+    err = std::string("graph capture failed: ") + cudaGetErrorString(e3);
+    if (ge.prof) delete ge.prof;
+    return SIFT_E_CUDA;
+  }
+  graphs_[key] = ge;
+  *out = ge.exec;
+  last_prof_ = ge.prof;
+  return SIFT_OK;
+}
+
+sift_status Engine::run(int n, const ImgIn *imgs, cudaStream_t s) {
+  sift_status st = init();
+  if (st != SIFT_OK) return st;
+  if (n < 1 || n > kMaxImg) {
+    err = "batch size out of range";
+    return SIFT_E_INVALID;
+  }
+  const int slot = (ring_ + 1) % kRing;
+  cudaEventSynchronize(hevt_[slot]);  // the descriptor copy that last used this buffer is done
+  ring_ = slot;
+  Desc *hd = hdesc_[slot];
+  WsLayout lay;
+  int M = 0;
+  st = fill_plan(n, imgs, *hd, lay, &M);
+  if (st != SIFT_OK) {
+    err = "image smaller than min_octave_side";
+    return st;
+  }
+  st = ensure_workspace(lay.total);
+  if (st != SIFT_OK) return st;
+  lay_ = lay;
+  hd->pyr = reinterpret_cast<float *>(ws_ + lay.pyr);
+  hd->bm = reinterpret_cast<uint32_t *>(ws_ + lay.bm);
+  hd->cand = reinterpret_cast<int4 *>(ws_ + lay.cand);
+  hd->ref = reinterpret_cast<RefRec *>(ws_ + lay.ref);
+  hd->code = reinterpret_cast<int *>(ws_ + lay.code);
+  hd->npk = reinterpret_cast<int *>(ws_ + lay.npk);
+  hd->angs = reinterpret_cast<float *>(ws_ + lay.angs);
+  hd->ori = reinterpret_cast<int2 *>(ws_ + lay.ori);
+  hd->okey = reinterpret_cast<uint32_t *>(ws_ + lay.okey);
+  hd->fin = reinterpret_cast<int *>(ws_ + lay.fin);
+  hd->bm_cnt = reinterpret_cast<int *>(ws_ + lay.bm_cnt);
+  hd->bm_off = reinterpret_cast<int *>(ws_ + lay.bm_off);
+  hd->cc_cnt = reinterpret_cast<int *>(ws_ + lay.cc_cnt);
+  hd->cc_off = reinterpret_cast<int *>(ws_ + lay.cc_off);
+  hd->cnt = reinterpret_cast<ImgCounters *>(ws_ + lay.cnt);
+  hd->cand_flat = reinterpret_cast<int *>(ws_ + lay.cand_flat);
+  hd->fin_flat = reinterpret_cast<int *>(ws_ + lay.fin_flat);
+  int n_oct_total = 0;
+  for (int b = 0; b < n; b++) n_oct_total += hd->img[b].n_oct;
+  const size_t bytes = offsetof(Desc, oct) + (size_t)n_oct_total * sizeof(OctDev);
+  cudaGraphExec_t exec = nullptr;
+  st = get_graph(M, &exec);
+  if (st != SIFT_OK) return st;
+  cudaError_t e = cudaStreamWaitEvent(s, done_, 0);
+  if (e == cudaSuccess) st = upload(hd, bytes, s);
+  if (e != cudaSuccess || st != SIFT_OK) {
+    err = "stream ordering failed";
+    return SIFT_E_CUDA;
+  }
+  e = cudaGraphLaunch(exec, s);
+  if (e == cudaSuccess) e = cudaEventRecord(done_, s);
+  if (e != cudaSuccess) {
+    err = std::string("graph launch failed: ") + cudaGetErrorString(e);
+    return SIFT_E_CUDA;
+  }
+  ring_last_ = slot;
+  last_stream = s;
+  last_n = n;
+  return SIFT_OK;
+}
+
+sift_status Engine::run_pyramid(const ImgIn &img, cudaStream_t s) {
+  sift_status st = init();
+  if (st != SIFT_OK) return st;
+  const int slot = (ring_ + 1) % kRing;
+  cudaEventSynchronize(hevt_[slot]);
+  ring_ = slot;
+  Desc *hd = hdesc_[slot];
+  WsLayout lay;
+  int M = 0;
+  st = fill_plan(1, &img, *hd, lay, &M);
+  if (st != SIFT_OK) return st;
+  st = ensure_workspace(lay.total);
+  if (st != SIFT_OK) return st;
+  lay_ = lay;
+  hd->pyr = reinterpret_cast<float *>(ws_ + lay.pyr);
+  hd->bm = reinterpret_cast<uint32_t *>(ws_ + lay.bm);
+  const size_t bytes = offsetof(Desc, oct) + (size_t)hd->img[0].n_oct * sizeof(OctDev);
+  cudaError_t e = cudaStreamWaitEvent(s, done_, 0);
+  if (e == cudaSuccess) st = upload(hd, bytes, s);
+  if (e == cudaSuccess && st == SIFT_OK) e = enqueue_pyramid(s, M, nullptr);
+  if (e == cudaSuccess) e = cudaEventRecord(done_, s);
+  if (e != cudaSuccess || st != SIFT_OK) {
+    err = std::string("pyramid launch failed: ") + cudaGetErrorString(e);
+    return SIFT_E_CUDA;
+  }
+  ring_last_ = slot;
+  last_stream = s;
+  last_n = 1;
+  return SIFT_OK;
+}
+
+void Engine::set_profiling(bool on) { profiling_ = on; }
+
+sift_status Engine::kernel_times(double *ms, int *launches, int n_classes) {
+  for (int c = 0; c < n_classes; c++) {
+    if (ms) ms[c] = 0.0;
+    if (launches) launches[c] = 0;
+  }
+  if (!last_prof_) {
+    err = "no profiled run: enable profiling before extracting";
+    return SIFT_E_INVALID;
+  }
+  cudaError_t e = cudaEventSynchronize(done_);
+  for (auto &r : *last_prof_) {
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
+    if (r.cls < n_classes) {
+      if (ms) ms[r.cls] += t;
+      if (launches) launches[r.cls] += 1;
+    }
+  }
+  if (e != cudaSuccess) {
+    err = std::string("event timing failed: ") + cudaGetErrorString(e);
+    return SIFT_E_CUDA;
+  }
+  return SIFT_OK;
+}
+
+sift_status Engine::last_stats(int *stats, int max_images) {
+  if (!ws_ || last_n == 0) {
+    err = "no extraction has run";
+    return SIFT_E_INVALID;
+  }
+  cudaError_t e = cudaEventSynchronize(done_);
+  std::vector<ImgCounters> c(last_n);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(c.data(), ws_ + lay_.cnt, last_n * sizeof(ImgCounters), cudaMemcpyDeviceToHost);
+  const Desc &hd = *hdesc_[ring_last_];
+  bool trunc = false;
+  for (int b = 0; b < last_n && b < max_images && e == cudaSuccess; b++) {
+    std::vector<int> codes(c[b].n_cand);
+    if (c[b].n_cand)
+      e = cudaMemcpy(codes.data(), ws_ + lay_.code + hd.img[b].cand_off * sizeof(int),
+                     c[b].n_cand * sizeof(int), cudaMemcpyDeviceToHost);
+    int keep = 0;
+    for (int v : codes) keep += v == RC_KEEP;
+    stats[4 * b + 0] = c[b].n_cand;
+    stats[4 * b + 1] = keep;
+    stats[4 * b + 2] = c[b].n_ori;
+    stats[4 * b + 3] = c[b].flags;
+    trunc |= (c[b].flags & (TF_CAND | TF_ORI)) != 0;
+  }
+  if (e != cudaSuccess) {
+    err = std::string("stats read failed: ") + cudaGetErrorString(e);
+    return SIFT_E_CUDA;
+  }
+  return trunc ? SIFT_W_TRUNCATED : SIFT_OK;
+}
+
+void Engine::set_tuning(const Tuning &t) {
+  tun_ = t;
+  drop_graphs();
+}
+
+sift_status Engine::autotune(int H, int W, cudaStream_t s) {
+  sift_status st = init();
+  if (st != SIFT_OK) return st;
+  float *img = nullptr;
+  if (cudaMalloc(&img, (size_t)H * W * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    err = "autotune image allocation failed";
+    return SIFT_E_OOM;
+  }
+  cudaMemsetAsync(img, 0, (size_t)H * W * sizeof(float), s);
+  ImgIn in{};
+  in.src = img;
+  in.H = H;
+  in.W = W;
+  in.pitch = W;
+  st = run_pyramid(in, s);
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  const Desc *d = ddesc_;
+  const int kinds[3] = {TK_BLUR16, TK_BLUR32, TK_BLUR64};
+  for (int l = 1; l <= S_ + 2 && st == SIFT_OK; l++) {
+    float best = 1e30f;
+    int best_kind = tun_.lvl_kind[l];
+    for (int kk = 0; kk < 3; kk++) {
+      const int kind = kinds[kk];
+      const int g = grid_blur(lvl_R_[l], kind, 0);
+      for (int w = 0; w < 2; w++) launch_level_blur(d, 0, l, lvl_R_[l], lvl_t_[l], kind, g, s);
+      cudaEventRecord(a, s);
+      for (int r = 0; r < 5; r++) launch_level_blur(d, 0, l, lvl_R_[l], lvl_t_[l], kind, g, s);
+      cudaEventRecord(b, s);
+      cudaEventSynchronize(b);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      if (ms < best) {
+        best = ms;
+        best_kind = kind;
+      }
+    }
+    tun_.lvl_kind[l] = best_kind;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaStreamSynchronize(s);
+  cudaFree(img);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    err = std::string("autotune failed: ") + cudaGetErrorString(e);
+    return SIFT_E_CUDA;
+  }
+  drop_graphs();
+  return st;
+}
+
+}  // namespace sift

@@ -1,0 +1,120 @@
+// Host-side extraction engine: geometry planning, workspace, descriptor
+// upload and per-octave-count CUDA graphs. One engine runs one batch at a time
+// on the stream it is given; the server owns several engines so that steps
+// overlap on the device.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/sift_gb300.h"
+#include "sift_dev.cuh"
+
+namespace sift {
+
+struct ImgIn {
+  const float *src;
+  int H, W, pitch;
+  sift_kpts_dev k;
+  float *desc;
+  int *count;
+};
+
+enum ProfClass { PC_BLUR = 0, PC_BASE = 1, PC_EXTREMA = 2, PC_DECIMATE = 3, PC_KEYPOINT = 4,
+                 PC_DESCRIPTOR = 5, PC_COUNT = 6 };
+
+struct Tuning {
+  int lvl_kind[kMaxLevels];   // tile-height class per level (TK_BLUR16/32/64)
+  int grid_mult_blur;         // persistent grid = n_sm * blocks/SM * mult / 4
+};
+
+struct WsLayout {
+  size_t pyr, bm, cand, ref, code, npk, angs, ori, okey, fin, bm_cnt, bm_off, cc_cnt, cc_off,
+      cnt, cand_flat, fin_flat, total;
+};
+
+class Engine {
+ public:
+  explicit Engine(const sift_params &p);
+  ~Engine();
+  sift_status init();
+  // Queue the extraction of n <= kMaxImg images on stream s.
+  sift_status run(int n, const ImgIn *imgs, cudaStream_t s);
+  // Queue the pyramid stage only (for export); one image.
+  sift_status run_pyramid(const ImgIn &img, cudaStream_t s);
+  // Octave sizes for an input; returns the octave count.
+  int octave_sizes(int H, int W, int *hs, int *ws) const;
+  // Workspace bytes a batch needs (serving admission).
+  size_t workspace_bytes(int n, const int *H, const int *W) const;
+  // Device-side per-image geometry of the last run (valid until the next run).
+  const Desc &host_desc() const { return *hdesc_[ring_last_]; }
+  const WsLayout &layout() const { return lay_; }
+  char *workspace() const { return ws_; }
+
+  void set_profiling(bool on);
+  sift_status kernel_times(double *ms, int *launches, int n_classes);
+  sift_status last_stats(int *stats, int max_images);
+
+  Tuning tuning() const { return tun_; }
+  void set_tuning(const Tuning &t);
+  sift_status autotune(int H, int W, cudaStream_t s);
+  int level_radius(int l) const { return lvl_R_[l]; }
+
+  const sift_params &params() const { return P_; }
+  std::string err;
+  cudaStream_t last_stream = nullptr;
+  int last_n = 0;
+
+ private:
+  sift_status fill_plan(int n, const ImgIn *imgs, Desc &hd, WsLayout &lay, int *max_oct) const;
+  sift_status ensure_workspace(size_t bytes);
+  sift_status upload(Desc *hd, size_t bytes, cudaStream_t s);
+  cudaError_t enqueue_pyramid(cudaStream_t s, int max_oct, std::vector<struct ProfRec> *prof);
+  cudaError_t enqueue_all(cudaStream_t s, int max_oct, std::vector<struct ProfRec> *prof);
+  sift_status get_graph(int max_oct, cudaGraphExec_t *out);
+  void drop_graphs();
+  int grid_blur(int R, int kind, int mode) const;
+
+  sift_params P_;
+  int dev_ = 0, n_sm_ = 0;
+  int S_ = 3;
+  int base_R_ = 0;
+  BlurTaps base_t_{};
+  int lvl_R_[kMaxLevels] = {};
+  BlurTaps lvl_t_[kMaxLevels] = {};
+  Tuning tun_{};
+
+  char *ws_ = nullptr;
+  size_t ws_cap_ = 0;
+  WsLayout lay_{};
+  Desc *ddesc_ = nullptr;
+  static constexpr int kRing = 3;
+  Desc *hdesc_[kRing] = {};
+  cudaEvent_t hevt_[kRing] = {};
+  int ring_ = 0, ring_last_ = 0;
+  cudaEvent_t done_ = nullptr;   // recorded after each run
+  cudaStream_t cap_ = nullptr;   // capture stream
+
+  struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<struct ProfRec> *prof = nullptr;
+  };
+  std::map<int, GraphEntry> graphs_;
+  bool profiling_ = false;
+  std::vector<struct ProfRec> *last_prof_ = nullptr;
+  bool inited_ = false;
+};
+
+struct ProfRec {
+  cudaEvent_t a, b;
+  int cls;
+};
+
+// Gaussian taps with 4-sigma truncation, computed in double and rounded to
+// float: radius ceil(4 sigma), w_k = exp(-k^2 / 2 sigma^2) / sum.
+int gaussian_taps(double sigma, BlurTaps *t);
+sift_status validate_params(const sift_params &p, std::string *why);
+
+}  // namespace sift

@@ -1,0 +1,155 @@
+// Internal definitions shared by the CUDA translation units of the extractor.
+//
+// Data layout in device memory (one "engine" = one workspace + descriptor):
+//  * Pyramid: per image, per octave o, levels 0..S+2 stored back to back, each
+//    H_o rows of `pitch` floats (pitch = W_o rounded up to 32 floats, 128 B).
+//  * Candidate bitmap: per image, per octave, per DoG layer 1..S, H_o rows of
+//    ceil(W_o / 32) 32-bit words; bit k of word w in row y marks pixel
+//    x = 32 w + k. Walking the bitmap in memory order is the canonical order
+//    (octave, layer, row, column).
+//  * Keypoint-stage arrays are per image slices of global arrays; every slice
+//    is addressed through the per-image fields of ImgDev.
+// All geometry lives in a device-side descriptor (Desc) written before each
+// launch, so the captured CUDA graphs depend only on the number of octaves.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sift {
+
+constexpr int kMaxImg = 128;       // images per device launch (larger batches are split)
+constexpr int kMaxOct = 14;        // octaves (2^14 px sides)
+constexpr int kMaxScales = 6;      // S <= 6
+constexpr int kMaxLevels = kMaxScales + 3;
+constexpr int kMaxR = 16;          // largest blur radius supported (halo 16)
+constexpr int kOriBins = 36;       // §3.2: 36-bin orientation histogram
+constexpr int kMaxPeaks = kOriBins / 2;  // strict circular maxima of 36 bins
+constexpr int kDescLen = 128;      // 4 x 4 x 8
+constexpr int kBlurTW = 128;       // blur tile width (32 lanes x float4)
+constexpr int kBlurHalo = 16;      // staged columns left/right of a blur tile
+constexpr int kExtTH = 32;         // extrema tile rows (tile = 32 columns)
+constexpr int kChunk = 2048;       // compaction chunk (words or slots)
+
+// Tile-queue kinds: blur with tile height 16/32/64, extrema tiles, decimation.
+enum TileKind { TK_BLUR16 = 0, TK_BLUR32 = 1, TK_BLUR64 = 2, TK_EXT = 3, TK_COUNT = 4 };
+
+// Rejection codes of the refinement (0 = kept).
+enum RefCode { RC_KEEP = 0, RC_SINGULAR = 1, RC_NOCONV = 2, RC_BOUNDS = 3, RC_CONTRAST = 4, RC_EDGE = 5 };
+
+// Truncation flags per image.
+enum { TF_CAND = 1, TF_ORI = 2, TF_TOPK = 4 };
+
+struct OctDev {
+  int H, W, pitch, wpr;        // size, row pitch (floats), bitmap words per row
+  long long lvl;               // float offset of level 0 in the pyramid array
+  long long lstride;           // floats between consecutive levels (H * pitch)
+  long long bm;                // word offset of layer 1's bitmap
+};
+
+struct ImgDev {
+  const float *src;            // input image (device)
+  int H, W, spitch;            // input size and pitch (elements)
+  int src_vec_ok;              // 1 if 16-byte aligned rows (vector loads allowed)
+  int n_oct, oct0;             // octaves and index of the first OctDev
+  long long bm_begin, bm_words;  // bitmap slice
+  int bmc0, bmc_n;             // bitmap chunks [bmc0, bmc0 + bmc_n)
+  int cand_cap;                // candidate slots
+  long long cand_off;          // slice start in cand / ref / code / npk arrays
+  int cc0, cc_n;               // candidate-slot chunks
+  int ori_cap;                 // oriented keypoint slots
+  long long ori_off;
+  int kcap;                    // output capacity (top-K)
+  long long fin_off;           // slice start in the final index list
+  float *ox, *oy, *osig, *oang, *oresp;
+  int *ooct, *olay;
+  float *odesc;
+  int *ocount;
+};
+
+// Dynamic per-image results written by kernels.
+struct ImgCounters {
+  int n_cand_raw, n_cand, n_ori_raw, n_ori, n_fin, n_ref, flags, pad;
+};
+
+struct RefRec {               // refined keypoint (octave-local coordinates)
+  int o, s, y, x;
+  float dx, dy, ds, resp;
+};
+
+struct Desc {
+  int n_img, n_oct_max, n_scales, upsample;
+  float sigma0, contrast_thr, prefilter, edge_ratio;
+  int border, max_iter, upright, rootsift;
+  float ori_peak_ratio, pad_f[3];
+  int n_bm_chunks, n_cc_chunks, pad_i[2];
+  // workspace arrays
+  float *pyr;
+  uint32_t *bm;
+  int4 *cand;
+  RefRec *ref;
+  int *code;
+  int *npk;
+  float *angs;                 // kMaxPeaks per candidate slot
+  int2 *ori;                   // (candidate slot, peak index)
+  uint32_t *okey;              // response bits of oriented keypoints
+  int *fin;                    // final indices into the oriented list
+  int *bm_cnt, *bm_off;        // per bitmap chunk: count, image-relative offset
+  int *cc_cnt, *cc_off;        // per candidate chunk
+  ImgCounters *cnt;            // per image
+  int *cand_flat;              // [kMaxImg + 1] prefix of n_cand over images
+  int *fin_flat;               // [kMaxImg + 1] prefix of n_fin over images
+  // geometry
+  int tile_pre[TK_COUNT][kMaxOct][kMaxImg + 1];
+  int bmc_pre[kMaxImg + 1];
+  int cc_pre[kMaxImg + 1];
+  ImgDev img[kMaxImg];
+  OctDev oct[kMaxImg * kMaxOct];
+};
+
+struct BlurTaps {
+  float w[2 * kMaxR + 1];
+};
+
+// Index of the image owning flattened item t, given an exclusive prefix pre[0..n].
+__device__ __forceinline__ int find_owner(const int *pre, int n, int t) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (pre[mid] <= t) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// reflect-101 for indices in (-n, 2n-1); anything further is clamped (such
+// samples only feed outputs outside the image, which are never read).
+__device__ __forceinline__ int refl101(int i, int n) {
+  i = i < 0 ? -i : i;
+  i = i >= n ? 2 * n - 2 - i : i;
+  return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+// ---------------------------------------------------------------- launchers
+// Pyramid (pyramid.cu)
+cudaError_t launch_base_blur(const Desc *d, int R, const BlurTaps &t, int th_kind, bool upsample,
+                             int grid, cudaStream_t s);
+cudaError_t launch_level_blur(const Desc *d, int oct, int lvl_out, int R, const BlurTaps &t,
+                              int th_kind, int grid, cudaStream_t s);
+cudaError_t launch_decimate(const Desc *d, int oct, int grid, cudaStream_t s);
+int blur_smem_bytes(int R, int th_kind);
+int blur_blocks_per_sm(int R, int th_kind, int mode);
+cudaError_t blur_set_attributes();
+
+// Detection (detect.cu)
+cudaError_t launch_extrema(const Desc *d, int oct, int n_scales, int grid, cudaStream_t s);
+cudaError_t launch_bm_compact(const Desc *d, int grid, cudaStream_t s);
+cudaError_t launch_refine(const Desc *d, int grid, cudaStream_t s);
+
+// Description (describe.cu)
+cudaError_t launch_orientation(const Desc *d, int grid, cudaStream_t s);
+cudaError_t launch_ori_compact(const Desc *d, int grid, cudaStream_t s);
+cudaError_t launch_select(const Desc *d, int grid, cudaStream_t s);
+cudaError_t launch_descriptor(const Desc *d, int grid, cudaStream_t s);
+cudaError_t descriptor_set_attributes();
+int descriptor_smem_bytes();
+
+}  // namespace sift

@@ -1,0 +1,172 @@
+"""GPU parity: the CUDA extractor (through the C ABI) against the FP64 oracle.
+
+Tolerances: pyramid max abs error <= 1e-4 on [0, 1] images; >= 99% of the
+oracle's keypoints that are not within 1e-4 (relative) of a decision
+threshold are found within 0.01 px, 1e-3 relative scale and 0.5 degrees;
+matched descriptors differ by at most 1e-3 in L2."""
+import hashlib
+
+import numpy as np
+import pytest
+
+from oracle import compare
+from oracle import sift_oracle as so
+from workloads import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2605_17869_gb300 as pkg  # noqa: E402
+
+
+def _oracle_params(**kw):
+    p = so.Params()
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def _gpu(img, **kw):
+    ex = pkg.Extractor(**kw)
+    f = ex.extract(torch.from_numpy(np.ascontiguousarray(img)).cuda())
+    torch.cuda.synchronize()
+    return ex, f
+
+
+def _assert_parity(ref, f, label=""):
+    m = compare.match(ref, f.as_numpy())
+    info = (f"{label}: oracle {m.n_oracle} (eligible {m.n_eligible}), gpu {m.n_gpu}, "
+            f"found {m.n_found}, gpu-unmatched {m.n_gpu_unmatched}, worst {m.worst}, "
+            f"desc max L2 {m.desc_max_l2:.2e} over {m.desc_pairs}")
+    print(info)
+    assert m.n_eligible > 0, info
+    assert m.found_frac >= 0.99, info
+    assert m.desc_max_l2 <= compare.DESC_TOL, info
+    assert m.n_gpu_unmatched <= max(2, 0.02 * m.n_gpu), info
+    return m
+
+
+# ------------------------------------------------------------------ pyramid
+
+@pytest.mark.parametrize("shape,up", [((480, 640), False), ((203, 301), False),
+                                      ((150, 190), True), ((16, 16), False), ((17, 130), False)])
+def test_pyramid_matches_oracle(shape, up):
+    img = synth.make_image(synth.rng_for(10, shape[0]), *shape)
+    ex = pkg.Extractor(upsample=int(up))
+    pyr = ex.pyramid(torch.from_numpy(img).cuda())
+    torch.cuda.synchronize()
+    ref = so.build_pyramid(img, _oracle_params(upsample=up))
+    assert len(pyr) == len(ref)
+    worst = 0.0
+    for o, (g, r) in enumerate(zip(pyr, ref)):
+        assert tuple(g.shape) == r.shape, (o, g.shape, r.shape)
+        worst = max(worst, float(np.abs(g.cpu().numpy().astype(np.float64) - r).max()))
+    print("pyramid max abs error", worst)
+    assert worst <= 1e-4
+
+
+# ------------------------------------------------------------------ keypoints
+
+def test_vga_keypoints_match_oracle():
+    img = synth.single_vga(0)
+    _, f = _gpu(img, max_kpts=8192)
+    ref = so.extract(img, _oracle_params())
+    _assert_parity(ref, f, "640x480")
+
+
+@pytest.mark.parametrize("shape", [(333, 517), (97, 211), (600, 130)])
+def test_ragged_sizes_match_oracle(shape):
+    img = synth.make_image(synth.rng_for(11, shape[1]), *shape, n_blobs=60)
+    _, f = _gpu(img, max_kpts=8192)
+    ref = so.extract(img, _oracle_params())
+    _assert_parity(ref, f, f"{shape}")
+
+
+def test_upsampled_keypoints_match_oracle():
+    img = synth.make_image(synth.rng_for(12, 0), 260, 350)
+    _, f = _gpu(img, upsample=1, max_kpts=8000)
+    ref = so.extract(img, _oracle_params(upsample=True, max_kpts=8000))
+    _assert_parity(ref, f, "260x350 upsampled")
+
+
+def test_upright_mode_matches_oracle():
+    img = synth.make_image(synth.rng_for(13, 0), 300, 400)
+    _, f = _gpu(img, upright=1)
+    ref = so.extract(img, _oracle_params(upright=True))
+    assert np.all(f.angle.cpu().numpy() == 0)
+    _assert_parity(ref, f, "upright")
+
+
+def test_topk_cap_matches_oracle():
+    img = synth.single_vga(1)
+    K = 40
+    _, f = _gpu(img, max_kpts=K)
+    ref = so.extract(img, _oracle_params(max_kpts=K))
+    assert f.count == min(K, len(so.extract(img, _oracle_params())))
+    resp = f.response.cpu().numpy()
+    # Kept responses are the K largest: compare the sorted response lists.
+    np.testing.assert_allclose(np.sort(resp), np.sort(ref.response), rtol=1e-4)
+    _assert_parity(ref, f, "top-K")
+
+
+# ------------------------------------------------------------------ edge cases
+
+def test_flat_image_has_no_keypoints():
+    ex = pkg.Extractor()
+    f = ex.extract(torch.full((64, 80), 0.5, device="cuda"))
+    assert f.count == 0
+
+
+def test_minimum_and_invalid_sizes():
+    ex = pkg.Extractor()
+    f = ex.extract(torch.rand(16, 16, device="cuda"))
+    assert f.count >= 0
+    with pytest.raises(pkg.SiftError) as e:
+        ex.extract(torch.rand(15, 40, device="cuda"))
+    assert e.value.status == pkg.SIFT_E_INVALID
+
+
+def test_pitched_input():
+    img = synth.make_image(synth.rng_for(14, 0), 200, 250)
+    big = torch.zeros((200, 300), device="cuda")
+    big[:, :250] = torch.from_numpy(img).cuda()
+    ex = pkg.Extractor()
+    a = ex.extract(big[:, :250])
+    b = ex.extract(torch.from_numpy(img).cuda())
+    assert a.count == b.count
+    assert torch.equal(a.desc, b.desc) and torch.equal(a.x, b.x)
+
+
+# ------------------------------------------------------------------ determinism
+
+def _digest(f):
+    h = hashlib.sha256()
+    h.update(np.int64(f.count).tobytes())
+    for t in (f.x, f.y, f.sigma, f.angle, f.response, f.octave, f.layer, f.desc):
+        h.update(t.cpu().numpy().tobytes())
+    return h.hexdigest()
+
+
+def test_bitwise_deterministic_100_runs():
+    img = torch.from_numpy(synth.single_vga(2)).cuda()
+    ex = pkg.Extractor()
+    d0 = _digest(ex.extract(img))
+    for _ in range(99):
+        assert _digest(ex.extract(img)) == d0
+
+
+def test_batch_composition_invariance():
+    shapes = [(480, 640), (300, 410), (97, 211), (640, 480), (256, 256)]
+    imgs = [torch.from_numpy(synth.make_image(synth.rng_for(15, i), *s)).cuda()
+            for i, s in enumerate(shapes)]
+    ex = pkg.Extractor()
+    single = [_digest(ex.extract(im)) for im in imgs]
+    batch = [_digest(f) for f in ex.extract_batch(imgs)]
+    assert batch == single
+    rev = [_digest(f) for f in ex.extract_batch(imgs[::-1])]
+    assert rev == single[::-1]
+    sub = [_digest(f) for f in ex.extract_batch([imgs[2], imgs[0]])]
+    assert sub == [single[2], single[0]]
