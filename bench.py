@@ -1,0 +1,455 @@
+"""Benchmark: batched SIFT extraction on GB300 (one JSON line on stdout).
+
+Workload (timed as `value`): a homography-sequence batch, 6 FP32 grayscale
+images of 1000x750 (one seeded base image plus 5 warps by random
+homographies with gain), 2x bilinear upsampled first octave, 8000 keypoints
+cap, extracted in one sift_extract_batch call per step. value = input
+megapixels per second over all ranks. Between timed steps L2 is flushed by
+writing a 256 MB buffer (outside the timed events).
+
+Also reported: keypoints/s; the same images through the per-image entry
+point and the batched/per-image ratio; the same for a 64-image mixed-size
+batch; serving images/s with p50/p99 latency under Poisson arrivals;
+end-to-end throughput through the public API from pinned host buffers;
+the blur kernel's achieved HBM bandwidth against the measured peak; and the
+FP64 oracle timed on the host cores on a bounded sample.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-serving]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import synth  # noqa: E402
+
+METRIC = "SIFT Mpix/s and keypoints/s, batched vs per-image; serving p50/p99 latency"
+WORKLOAD = ("homography-sequence batch: 6 x 1000x750 FP32 grayscale (seeded base + 5 "
+            "homography warps), 2x upsampled first octave, cap 8000 keypoints/image")
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------ oracle (CPU)
+
+def _oracle_one(args):
+    img, upsample, max_kpts = args
+    from oracle import sift_oracle as so
+    t = time.perf_counter()
+    r = so.extract(img, so.Params(upsample=bool(upsample), max_kpts=max_kpts))
+    return time.perf_counter() - t, len(r)
+
+
+def _oracle_pool(n):
+    return mp.get_context("spawn").Pool(n)
+
+
+def cpu_baseline(pool, n_workers, imgs, upsample=True, max_kpts=8000):
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_one, [(im, upsample, max_kpts) for im in imgs])
+    wall = time.perf_counter() - t0
+    mpix = sum(im.size for im in imgs) / 1e6
+    return {"value": round(mpix / wall, 4), "unit": "Mpix/s", "cores": n_workers,
+            "kind": "oracle", "keypoints_per_s": round(sum(k for _, k in res) / wall, 1),
+            "sample": f"{len(imgs)} images of the timed batch (1000x750, 2x upsampled), "
+                      f"one image per worker process, {wall:.1f} s wall"}
+
+
+# ------------------------------------------------------------ clocks
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_index):
+        self.proc = None
+        self.dev = dev_index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ GPU arm
+
+def _device_images(imgs, torch):
+    return [torch.from_numpy(np.ascontiguousarray(im)).cuda() for im in imgs]
+
+
+def _alg_blur_bytes(shapes, upsample, S=3, min_side=16):
+    """Algorithmic bytes of all level-blur launches of one step: each level
+    blur reads its source level once and writes the new level once (8 B per
+    octave pixel), S + 2 levels per octave."""
+    tot = 0
+    for (h, w) in shapes:
+        if upsample:
+            h, w = 2 * h, 2 * w
+        while min(h, w) >= min_side:
+            tot += 8 * h * w * (S + 2)
+            h, w = h // 2, w // 2
+    return tot
+
+
+def timed_steps(torch, fn, steps, warmup, flush, stream):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    times = []
+    t_wall = time.perf_counter()
+    for _ in range(steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    torch.cuda.synchronize()
+    return times, time.perf_counter() - t_wall
+
+
+def serving_bench(torch, pkg, rates, n_req, budget=8 << 30):
+    pool = {}
+    for (h, w) in ((480, 640), (1080, 1920), (2160, 3840)):
+        pool[(h, w)] = [torch.from_numpy(synth.serving_image(h, w, i)).cuda() for i in range(2)]
+    ex = pkg.Extractor(max_kpts=8192)
+    srv = pkg.Server(ex, budget_bytes=budget, max_slots=256)
+    # warm-up: one of each size
+    for k in pool:
+        t = srv.submit(pool[k][0])
+        srv.result(t)
+        srv.release(t)
+    out = []
+    for lam in rates:
+        trace = synth.serving_trace(lam, n_req, index=int(lam))
+        tickets = []
+        t0 = time.perf_counter()
+        for (ta, h, w, i) in trace:
+            now = time.perf_counter() - t0
+            if ta > now:
+                time.sleep(ta - now)
+            tickets.append(srv.submit(pool[(h, w)][i % 2]))
+        lat = []
+        px = 0
+        for tk, (_, h, w, _) in zip(tickets, trace):
+            f, ms, st = srv.result(tk)
+            lat.append(ms)
+            px += h * w
+            srv.release(tk)
+        span = time.perf_counter() - t0
+        lat.sort()
+        out.append({"rate_per_s": lam, "requests": n_req, "images_per_s": round(n_req / span, 1),
+                    "mpix_per_s": round(px / 1e6 / span, 1),
+                    "p50_ms": round(lat[len(lat) // 2], 3),
+                    "p99_ms": round(lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)], 3)})
+    srv.close()
+    ex.close()
+    return {"workload": "Poisson arrivals, 640x480 (50%) / 1920x1080 (35%) / 3840x2160 (15%), "
+                        "8 GB device-memory budget, no upsampling, cap 8192",
+            "points": out}
+
+
+def gpu_arm(args, rank, world, pool, n_workers):
+    import torch
+    import paper_2605_17869_gb300 as pkg
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    seq = synth.homography_sequence(index=rank)
+    imgs_np = seq.images
+    shapes = [im.shape for im in imgs_np]
+    imgs = _device_images(imgs_np, torch)
+    mpix = sum(h * w for h, w in shapes) / 1e6
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    ex = pkg.Extractor(upsample=1, max_kpts=8000)
+    tuning = ex.autotune(1500, 2000)
+
+    def step():
+        ex.extract_batch_async(imgs, stream)
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    clocks = Clocks(dev)
+    clocks.start()
+    times, wall = timed_steps(torch, step, args.steps, args.warmup, flush, stream)
+    clock_info = clocks.stop()
+    counts = ex._counts[:len(imgs)].tolist()
+    kpts = sum(counts)
+    launches_per_step = ex.launch_count()
+    total_ms = sum(times)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    value = world * mpix * args.steps / (total_ms / 1e3)
+
+    # Per-image path on the same images.
+    def step_single():
+        for im in imgs:
+            ex.extract_async(im, stream)
+    t_single, _ = timed_steps(torch, step_single, max(3, args.steps // 2), 2, flush, stream)
+    per_image = mpix * len(t_single) / (sum(t_single) / 1e3)
+
+    # Per-kernel device times (profiled graph: an event pair around every launch).
+    ex.set_profiling(True)
+    step()
+    torch.cuda.synchronize()
+    acc = {}
+    reps = max(3, args.steps // 2)
+    for _ in range(reps):
+        flush.zero_()
+        step()
+        for k, (ms, n) in ex.kernel_times().items():
+            a = acc.setdefault(k, [0.0, 0])
+            a[0] += ms
+            a[1] += n
+    ex.set_profiling(False)
+    blur_ms, blur_n = acc["blur"]
+    alg_total = _alg_blur_bytes(shapes, True) * reps
+    peak, peak_kind = _peaks()
+    achieved = alg_total / (blur_ms / 1e3) / 1e9 if blur_ms > 0 else 0.0
+    kernel_share = {k: round(v[0] / reps, 4) for k, v in acc.items()}
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "blur_level_traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            tj = json.load(f)
+        import hashlib
+        src = open(os.path.join(ROOT, "paper_2605_17869_gb300", "csrc", "pyramid.cu"), "rb").read()
+        if tj.get("pyramid_cu_sha256") == hashlib.sha256(src).hexdigest():
+            traffic = tj.get("bytes_per_launch")
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "kernel": "k_blur (pyramid level blur)",
+                "alg_bytes_per_launch": int(alg_total / max(1, blur_n)),
+                "launch_ms_avg": round(blur_ms / max(1, blur_n), 5),
+                "peak_source": "hbm_gbs, " + ("of measured (MEASURED_PEAKS.json)"
+                                              if peak_kind == "measured" else "of fallback")}
+
+    # End to end: pinned host images -> device -> extract -> counts + results back.
+    host = [torch.from_numpy(np.ascontiguousarray(im)).pin_memory() for im in imgs_np]
+    dev_in = [torch.empty_like(h, device="cuda") for h in host]
+    e2e_times = []
+    h2d = sum(h.numel() * 4 for h in host)
+    d2h_bytes = []
+    for it in range(args.warmup + max(3, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for d, h in zip(dev_in, host):
+            d.copy_(h, non_blocking=True)
+        bufs, cnt = ex.extract_batch_async(dev_in, stream)
+        counts_h = cnt.cpu().tolist()
+        nbytes = 4 * len(counts_h)
+        for b, n in zip(bufs, counts_h):
+            for t in (b.x, b.y, b.sigma, b.angle, b.response, b.octave, b.layer, b.desc):
+                t[:n].cpu()
+                nbytes += t[:n].numel() * 4
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            e2e_times.append(time.perf_counter() - t0)
+            d2h_bytes.append(nbytes)
+    e2e = {"value": round(world * mpix * len(e2e_times) / sum(e2e_times), 3), "unit": "Mpix/s",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(np.mean(d2h_bytes)),
+           "api": "Extractor.extract_batch_async (sift_extract_batch) from pinned host buffers"}
+
+    # Mixed-size 64-image batch (batching workload): batched vs per-image.
+    mixed = None
+    if rank == 0 and not args.no_mixed:
+        mimgs_np = pool.map(_mixed_one, list(range(64))) if pool else [
+            _mixed_one(i) for i in range(64)]
+        mimgs = _device_images(mimgs_np, torch)
+        mmpix = sum(im.size for im in mimgs_np) / 1e6
+        exm = pkg.Extractor(max_kpts=8192)
+        exm.set_tuning(tuning)
+        tb, _ = timed_steps(torch, lambda: exm.extract_batch_async(mimgs, stream), 5, 2, flush,
+                            stream)
+        mcounts = exm._counts[:64].tolist()
+
+        def single_all():
+            for im in mimgs:
+                exm.extract_async(im, stream)
+        ts, _ = timed_steps(torch, single_all, 3, 1, flush, stream)
+        mixed = {"workload": "64 mixed-size images, long side 480-1600, aspect 4:3/3:4/16:9, "
+                             "1/f texture, no upsampling, cap 8192",
+                 "batched_mpix_s": round(mmpix * len(tb) / (sum(tb) / 1e3), 1),
+                 "per_image_mpix_s": round(mmpix * len(ts) / (sum(ts) / 1e3), 1),
+                 "keypoints_per_s": round(sum(mcounts) * len(tb) / (sum(tb) / 1e3), 1),
+                 "ms_per_batch": round(statistics.mean(tb), 3)}
+        mixed["batched_vs_per_image"] = round(mixed["batched_mpix_s"] / mixed["per_image_mpix_s"], 2)
+        exm.close()
+
+    serving = None
+    if rank == 0 and not args.no_serving:
+        serving = serving_bench(torch, pkg, (50, 200, 1000, 2000), 200)
+
+    res = {
+        "metric": METRIC, "value": round(value, 2), "unit": "Mpix/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "images_per_step_per_gpu": len(imgs),
+                   "input_mpix_per_step_per_gpu": round(mpix, 3),
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"replicas x{world} (independent images per rank)",
+                   "tuning": tuning},
+        "keypoints_per_s": round(world * kpts * args.steps / (total_ms / 1e3), 1),
+        "keypoints_per_step_per_gpu": kpts,
+        "per_image_mpix_s": round(per_image, 2),
+        "batched_vs_per_image": round(value / world / per_image, 3),
+        "wall_s_timed_region": round(wall, 3),
+        "gpu_launches": launches_per_step * args.steps,
+        "gpu_launches_per_step": launches_per_step,
+        "kernel_ms_per_step": kernel_share,
+        "roofline": roofline,
+        "e2e": e2e,
+        "clocks": clock_info,
+        "mixed_batch": mixed,
+        "serving": serving,
+    }
+    return res, imgs_np
+
+
+def _mixed_one(i):
+    (h, w) = synth.mixed_batch_shapes(64)[i]
+    return synth.make_image(synth.rng_for(3, i), h, w, fractal_std=0.05)
+
+
+# ------------------------------------------------------------ reference arm
+
+def reference_arm(args, pool, n_workers):
+    seq = synth.homography_sequence(index=0)
+    imgs = seq.images
+    mpix = sum(im.size for im in imgs) / 1e6
+    for _ in range(args.warmup):
+        pool.map(_oracle_one, [(im, True, 8000) for im in imgs[:n_workers]])
+    times, kp = [], 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = pool.map(_oracle_one, [(im, True, 8000) for im in imgs])
+        times.append(time.perf_counter() - t0)
+        kp += sum(k for _, k in r)
+    total = sum(times)
+    value = mpix * args.steps / total
+    sample = (f"each step: the 6 images of the timed batch through the FP64 oracle, one image "
+              f"per worker process ({n_workers} workers)")
+    return {"metric": METRIC, "value": round(value, 4), "unit": "Mpix/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * total / args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference", "config": {"workload": WORKLOAD},
+            "keypoints_per_s": round(kp / total, 1),
+            "cpu_baseline": {"value": round(value, 4), "unit": "Mpix/s", "cores": n_workers,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": "Mpix/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+# ------------------------------------------------------------ main
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        n_workers = min(6, os.cpu_count() or 1)
+        with _oracle_pool(n_workers) as pool:
+            print(json.dumps(reference_arm(args, pool, n_workers)))
+        return
+
+    # The oracle's worker pool is started (spawn) before any GPU call.
+    n_workers = min(6, os.cpu_count() or 1)
+    pool = _oracle_pool(n_workers) if rank == 0 else None
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    try:
+        res, imgs_np = gpu_arm(args, rank, world, pool, n_workers)
+        if rank == 0:
+            if not args.no_cpu_baseline:
+                res["cpu_baseline"] = cpu_baseline(pool, n_workers, imgs_np)
+            print(json.dumps(res))
+    finally:
+        if pool is not None:
+            pool.close()
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

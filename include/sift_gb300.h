@@ -62,7 +62,7 @@ typedef enum {
  * ratio 10, border 5, 5 refinement iterations, pre-gate 0.5 x threshold,
  * secondary orientation peaks at >= 0.8 of the maximum, no keypoint cap. */
 typedef struct {
-  int n_scales;          /* S: scales per octave (1..8) */
+  int n_scales;          /* S: scales per octave (2..6) */
   float sigma0;          /* base scale of each octave */
   float init_blur;       /* blur already present in the input */
   int upsample;          /* 1: first octave from the 2x bilinear magnified input */
@@ -154,15 +154,19 @@ sift_status sift_build_pyramid(sift_handle *h, const float *img_dev, int H, int 
                                int pitch_elems, void *stream, float *out_dev, size_t out_elems);
 
 /* Per-kernel timing. When enabled, the graphs captured afterwards carry CUDA
- * event nodes around the pyramid blur launches and the descriptor launch, and
- * sift_kernel_times() returns, for the last extraction, the summed device time
- * in milliseconds and launch count of each kernel class:
+ * event nodes around every launch, and sift_kernel_times() returns, for the
+ * last extraction, the summed device time in milliseconds and the launch count
+ * of each kernel class:
  *   0 blur levels, 1 base level (blur of the input / magnified input),
- *   2 DoG extrema scan, 3 keypoint stages (refine, orientation, compaction),
- *   4 descriptor.
- * Reading synchronises the handle's last stream. */
+ *   2 DoG extrema scan, 3 decimation, 4 keypoint stages (compaction,
+ *   refinement, orientation, cap), 5 descriptor.
+ * Reading synchronises the handle's last run. */
 sift_status sift_set_profiling(sift_handle *h, int enable);
 sift_status sift_kernel_times(sift_handle *h, double *ms, int *launches, int n_classes);
+
+/* Number of CUDA kernels the last extraction on this handle launched (one
+ * graph replay). Host-only: no synchronisation. */
+sift_status sift_last_launch_count(sift_handle *h, int *kernels);
 
 /* Autotuner: time the blur and extrema kernels' tile shapes on a synthetic
  * H x W workload on `stream` and keep the fastest. Tile shapes change only how

@@ -532,6 +532,7 @@ class Result:
     layer: np.ndarray
     desc: np.ndarray
     margin: np.ndarray          # smallest decision margin behind each keypoint
+    internals: dict = field(default_factory=dict)  # octave-local refinement state per keypoint
     cand: dict = field(default_factory=dict)     # candidate table
     n_refined: int = 0
     pyramid: list = None
@@ -580,6 +581,7 @@ def extract(img: np.ndarray, p: Params = None, keep_pyramid: bool = False,
     octv = np.zeros(n, dtype=np.int64)
     layer = np.zeros(n, dtype=np.int64)
     desc = np.zeros((n, p.desc_width ** 2 * p.desc_bins))
+    internals = {k: np.zeros(n) for k in ("xi", "yi", "dx", "dy", "sigma_oct")}
     for t, idx in enumerate(keep):
         o, r, sigma_oct, a, m = rows[idx]
         f = (2.0 ** o) * scale_up
@@ -592,8 +594,10 @@ def extract(img: np.ndarray, p: Params = None, keep_pyramid: bool = False,
         out["margin"][t] = m
         octv[t] = o
         layer[t] = r.s
+        for k, v in (("xi", r.x), ("yi", r.y), ("dx", r.dx), ("dy", r.dy), ("sigma_oct", sigma_oct)):
+            internals[k][t] = v
         if with_descriptors:
             desc[t] = descriptor(pyr[o][r.s], xk, yk, r.x, r.y, sigma_oct, a, p)
     cand = {k: np.array(v) for k, v in cand_tab.items()}
     return Result(out["x"], out["y"], out["sigma"], out["angle"], out["response"], octv, layer,
-                  desc, out["margin"], cand, n_ref, pyr if keep_pyramid else None)
+                  desc, out["margin"], internals, cand, n_ref, pyr if keep_pyramid else None)

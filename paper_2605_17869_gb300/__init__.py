@@ -22,7 +22,7 @@ __all__ = [
     "SiftError", "SiftParams", "SiftKptsDev", "SiftResult", "Features", "Extractor", "Server",
     "sift_params_default", "sift_create", "sift_destroy", "sift_extract", "sift_extract_batch",
     "sift_last_stats", "sift_pyramid_size", "sift_build_pyramid", "sift_set_profiling",
-    "sift_kernel_times", "sift_autotune", "sift_get_tuning", "sift_set_tuning",
+    "sift_kernel_times", "sift_last_launch_count", "sift_autotune", "sift_get_tuning", "sift_set_tuning",
     "sift_serve_create", "sift_serve_submit", "sift_serve_poll", "sift_serve_wait",
     "sift_serve_release", "sift_serve_destroy", "sift_last_error", "sift_version",
     "SIFT_OK", "SIFT_W_TRUNCATED", "SIFT_PENDING", "SIFT_E_INVALID", "SIFT_E_OOM",
@@ -125,6 +125,12 @@ def sift_kernel_times(handle):
     cnt = (c_int * n)()
     _check(_lib().sift_kernel_times(handle, ms, cnt, n), handle, "sift_kernel_times")
     return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+def sift_last_launch_count(handle) -> int:
+    k = c_int()
+    _check(_lib().sift_last_launch_count(handle, byref(k)), handle, "sift_last_launch_count")
+    return k.value
 
 
 def sift_autotune(handle, H: int, W: int, stream: int) -> None:
@@ -356,6 +362,9 @@ class Extractor:
 
     def kernel_times(self):
         return sift_kernel_times(self.handle)
+
+    def launch_count(self) -> int:
+        return sift_last_launch_count(self.handle)
 
     def autotune(self, H: int, W: int):
         sift_autotune(self.handle, H, W, _torch().cuda.current_stream().cuda_stream)

@@ -57,6 +57,7 @@ SIGNATURES = {
                                    c_size_t]),
     "sift_set_profiling": (c_int, [c_void_p, c_int]),
     "sift_kernel_times": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int), c_int]),
+    "sift_last_launch_count": (c_int, [c_void_p, POINTER(c_int)]),
     "sift_autotune": (c_int, [c_void_p, c_int, c_int, c_void_p]),
     "sift_get_tuning": (c_int, [c_void_p, c_char_p, c_size_t]),
     "sift_set_tuning": (c_int, [c_void_p, c_char_p]),

@@ -187,6 +187,12 @@ sift_status sift_kernel_times(sift_handle *h, double *ms, int *launches, int n_c
   return pass(h, h->eng->kernel_times(ms, launches, n_classes));
 }
 
+sift_status sift_last_launch_count(sift_handle *h, int *kernels) {
+  if (!h || !kernels) return SIFT_E_INVALID;
+  *kernels = h->eng->last_launch_count();
+  return SIFT_OK;
+}
+
 sift_status sift_autotune(sift_handle *h, int H, int W, void *stream) {
   if (!h) return SIFT_E_INVALID;
   const int ms = h->eng->params().min_octave_side;
@@ -330,37 +336,46 @@ void retire(Server *s, Lane &l) {
   s->cv_done.notify_all();
 }
 
-void launch_step(Server *s, int li, std::vector<uint64_t> &batch) {
-  Lane &l = s->lanes[li];
-  const int K = s->h->eng->params().max_kpts;
+// One request of a step, copied out of the request table so that the CUDA
+// work below runs without the server lock.
+struct Job {
+  uint64_t id;
+  const float *img;
+  int H, W, pitch;
+  size_t out_bytes;
+  char *buf;
+  bool ok;
+};
+
+// Runs WITHOUT the server lock: the completion callback of a running step
+// takes that lock, and a CUDA call made here may wait for such a step.
+// Allocates missing output buffers (stream-ordered), queues the batch, the
+// count / flag read-back and the completion callback. Returns the status of
+// the launch; per-job allocation failures are marked in Job::ok.
+sift_status launch_step(Lane &l, int K, std::vector<Job> &jobs, std::string *err) {
   std::vector<ImgIn> in;
-  for (uint64_t id : batch) {
-    Request &r = s->reqs[id];
-    if (!r.buf) {
-      if (cudaMallocAsync(reinterpret_cast<void **>(&r.buf), r.out_bytes, l.stream) != cudaSuccess) {
-        cudaGetLastError();
-        r.state = 2;
-        r.status = SIFT_E_OOM;
-        r.t_done = Clock::now();
-        s->in_flight--;
-        continue;
-      }
-      float *f = reinterpret_cast<float *>(r.buf);
-      r.k.x = f;
-      r.k.y = f + K;
-      r.k.sigma = f + 2 * K;
-      r.k.angle = f + 3 * K;
-      r.k.response = f + 4 * K;
-      r.k.octave = reinterpret_cast<int *>(f + 5 * K);
-      r.k.layer = reinterpret_cast<int *>(f + 6 * K);
-      r.desc = f + 7 * K;
-      r.dcount = reinterpret_cast<int *>(f + 7 * K + (size_t)K * sift::kDescLen);
+  for (Job &j : jobs) {
+    j.ok = true;
+    if (!j.buf &&
+        cudaMallocAsync(reinterpret_cast<void **>(&j.buf), j.out_bytes, l.stream) != cudaSuccess) {
+      cudaGetLastError();
+      j.buf = nullptr;
+      j.ok = false;
+      continue;
     }
-    r.state = 1;
-    in.push_back(ImgIn{r.img, r.H, r.W, r.pitch, r.k, r.desc, r.dcount});
-    l.reqs.push_back(id);
+    float *f = reinterpret_cast<float *>(j.buf);
+    sift_kpts_dev k;
+    k.x = f;
+    k.y = f + K;
+    k.sigma = f + 2 * K;
+    k.angle = f + 3 * K;
+    k.response = f + 4 * K;
+    k.octave = reinterpret_cast<int *>(f + 5 * K);
+    k.layer = reinterpret_cast<int *>(f + 6 * K);
+    in.push_back(ImgIn{j.img, j.H, j.W, j.pitch, k, f + 7 * K,
+                       reinterpret_cast<int *>(f + 7 * K + (size_t)K * sift::kDescLen)});
   }
-  if (in.empty()) return;
+  if (in.empty()) return SIFT_E_OOM;
   sift_status st = l.eng->run((int)in.size(), in.data(), l.stream);
   cudaError_t e = cudaSuccess;
   if (st == SIFT_OK) {
@@ -370,25 +385,31 @@ void launch_step(Server *s, int li, std::vector<uint64_t> &batch) {
       e = cudaMemcpyAsync(l.h_flags, l.eng->workspace() + l.eng->layout().cnt,
                           in.size() * sizeof(sift::ImgCounters), cudaMemcpyDeviceToHost, l.stream);
     if (e == cudaSuccess) e = cudaLaunchHostFunc(l.stream, on_lane_done, &l.msg);
-  }
-  if (st != SIFT_OK || e != cudaSuccess) {
-    for (uint64_t id : l.reqs) {
-      Request &r = s->reqs[id];
-      r.state = 2;
-      r.status = st != SIFT_OK ? st : SIFT_E_CUDA;
-      r.t_done = Clock::now();
-      s->in_flight--;
+    if (e != cudaSuccess) {
+      st = SIFT_E_CUDA;
+      *err = cudaGetErrorString(e);
     }
-    s->err = l.eng->err;
-    l.reqs.clear();
-    s->cv_done.notify_all();
-    return;
+  } else {
+    *err = l.eng->err;
   }
-  l.busy = true;
-  l.finished = false;
+  return st;
+}
+
+void set_buffers(Request &r, int K) {
+  float *f = reinterpret_cast<float *>(r.buf);
+  r.k.x = f;
+  r.k.y = f + K;
+  r.k.sigma = f + 2 * K;
+  r.k.angle = f + 3 * K;
+  r.k.response = f + 4 * K;
+  r.k.octave = reinterpret_cast<int *>(f + 5 * K);
+  r.k.layer = reinterpret_cast<int *>(f + 6 * K);
+  r.desc = f + 7 * K;
+  r.dcount = reinterpret_cast<int *>(f + 7 * K + (size_t)K * sift::kDescLen);
 }
 
 void scheduler(Server *s) {
+  const int K = s->h->eng->params().max_kpts;
   std::unique_lock<std::mutex> lk(s->mu);
   while (true) {
     for (auto &l : s->lanes)
@@ -406,11 +427,12 @@ void scheduler(Server *s) {
         break;
       }
     if (free_lane >= 0 && !s->queue.empty() && !s->stop) {
-      Engine *eng = s->lanes[free_lane].eng;
-      std::vector<uint64_t> batch;
+      Lane &lane = s->lanes[free_lane];
+      Engine *eng = lane.eng;
+      std::vector<Job> jobs;
       std::vector<int> hs, ws;
       size_t ws_now = lanes_ws(s) - (eng->workspace() ? eng->layout().total : 0);
-      while (!s->queue.empty() && (int)batch.size() < sift::kMaxImg &&
+      while (!s->queue.empty() && (int)jobs.size() < sift::kMaxImg &&
              s->in_flight < s->max_slots) {
         Request &r = s->reqs[s->queue.front()];
         hs.push_back(r.H);
@@ -424,15 +446,43 @@ void scheduler(Server *s) {
         }
         s->held += r.out_bytes;
         s->in_flight++;
-        batch.push_back(s->queue.front());
+        r.state = 1;
+        jobs.push_back(Job{r.id, r.img, r.H, r.W, r.pitch, r.out_bytes, r.buf, false});
         s->queue.pop_front();
       }
-      if (!batch.empty()) {
-        launch_step(s, free_lane, batch);
+      if (!jobs.empty()) {
+        lane.busy = true;
+        lane.finished = false;
+        std::string err;
+        lk.unlock();
+        const sift_status st = launch_step(lane, K, jobs, &err);
+        lk.lock();
+        const auto now = Clock::now();
+        lane.reqs.clear();
+        for (Job &j : jobs) {
+          Request &r = s->reqs[j.id];
+          r.buf = j.buf;
+          if (r.buf) set_buffers(r, K);
+          if (j.ok && st == SIFT_OK) {
+            lane.reqs.push_back(j.id);
+          } else {
+            r.state = 2;
+            r.status = j.ok ? st : SIFT_E_OOM;
+            r.t_done = now;
+            s->in_flight--;
+          }
+        }
+        if (st != SIFT_OK) {
+          s->err = err;
+          lane.busy = false;
+          lane.finished = false;
+          lane.reqs.clear();
+        }
+        s->cv_done.notify_all();
         continue;
       }
     }
-    s->cv.wait_for(lk, std::chrono::milliseconds(5));
+    s->cv.wait_for(lk, std::chrono::milliseconds(2));
   }
 }
 

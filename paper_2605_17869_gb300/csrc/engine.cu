@@ -302,15 +302,18 @@ sift_status Engine::fill_plan(int n, const ImgIn *in, Desc &hd, WsLayout &L, int
   return SIFT_OK;
 }
 
-sift_status Engine::ensure_workspace(size_t bytes) {
+// Grows the workspace with stream-ordered allocation on the run's stream,
+// which already waits for the previous run (so the old block is no longer in
+// use when it is freed). Nothing here synchronises the device.
+sift_status Engine::ensure_workspace(size_t bytes, cudaStream_t s) {
   if (bytes <= ws_cap_) return SIFT_OK;
   if (ws_) {
-    cudaFree(ws_);  // synchronises the device: earlier launches finish first
+    cudaFreeAsync(ws_, s);
     ws_ = nullptr;
     ws_cap_ = 0;
   }
   const size_t want = align_up(bytes + bytes / 4, 1 << 20);
-  cudaError_t e = cudaMalloc(&ws_, want);
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&ws_), want, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
     ws_ = nullptr;
@@ -376,8 +379,10 @@ cudaError_t Engine::enqueue_pyramid(cudaStream_t s, int M, std::vector<ProfRec> 
 
 cudaError_t Engine::enqueue_all(cudaStream_t s, int M, std::vector<ProfRec> *prof) {
   cudaError_t e = cudaSuccess;
-  auto rec = [&](int cls, auto &&fn) {
+  kernels_ = 0;
+  auto rec = [&](int cls, auto &&fn, int nk = 1) {
     if (e != cudaSuccess) return;
+    kernels_ += nk;
     ProfRec r{nullptr, nullptr, cls};
     if (prof) {
       cudaEventCreate(&r.a);
@@ -410,10 +415,10 @@ cudaError_t Engine::enqueue_all(cudaStream_t s, int M, std::vector<ProfRec> *pro
     }
     rec(PC_EXTREMA, [&] { return launch_extrema(d, o, S_, n_sm_ * 8, s); });
   }
-  rec(PC_KEYPOINT, [&] { return launch_bm_compact(d, g4, s); });
+  rec(PC_KEYPOINT, [&] { return launch_bm_compact(d, g4, s); }, 3);
   rec(PC_KEYPOINT, [&] { return launch_refine(d, g4, s); });
   rec(PC_KEYPOINT, [&] { return launch_orientation(d, g4, s); });
-  rec(PC_KEYPOINT, [&] { return launch_ori_compact(d, g4, s); });
+  rec(PC_KEYPOINT, [&] { return launch_ori_compact(d, g4, s); }, 3);
   rec(PC_KEYPOINT, [&] { return launch_select(d, n_sm_, s); });
   rec(PC_DESCRIPTOR, [&] { return launch_descriptor(d, n_sm_ * 3, s); });
   return e;
@@ -440,6 +445,7 @@ sift_status Engine::get_graph(int M, cudaGraphExec_t *out) {
   if (it != graphs_.end()) {
     *out = it->second.exec;
     last_prof_ = it->second.prof;
+    last_kernels_ = it->second.kernels;
     return SIFT_OK;
   }
   GraphEntry ge;
@@ -457,9 +463,11 @@ sift_status Engine::get_graph(int M, cudaGraphExec_t *out) {
     if (ge.prof) delete ge.prof;
     return SIFT_E_CUDA;
   }
+  ge.kernels = kernels_;
   graphs_[key] = ge;
   *out = ge.exec;
   last_prof_ = ge.prof;
+  last_kernels_ = ge.kernels;
   return SIFT_OK;
 }
 
@@ -481,7 +489,11 @@ sift_status Engine::run(int n, const ImgIn *imgs, cudaStream_t s) {
     err = "image smaller than min_octave_side";
     return st;
   }
-  st = ensure_workspace(lay.total);
+  if (cudaStreamWaitEvent(s, done_, 0) != cudaSuccess) {
+    err = "stream ordering failed";
+    return SIFT_E_CUDA;
+  }
+  st = ensure_workspace(lay.total, s);
   if (st != SIFT_OK) return st;
   lay_ = lay;
   hd->pyr = reinterpret_cast<float *>(ws_ + lay.pyr);
@@ -507,13 +519,9 @@ sift_status Engine::run(int n, const ImgIn *imgs, cudaStream_t s) {
   cudaGraphExec_t exec = nullptr;
   st = get_graph(M, &exec);
   if (st != SIFT_OK) return st;
-  cudaError_t e = cudaStreamWaitEvent(s, done_, 0);
-  if (e == cudaSuccess) st = upload(hd, bytes, s);
-  if (e != cudaSuccess || st != SIFT_OK) {
-    err = "stream ordering failed";
-    return SIFT_E_CUDA;
-  }
-  e = cudaGraphLaunch(exec, s);
+  st = upload(hd, bytes, s);
+  if (st != SIFT_OK) return st;
+  cudaError_t e = cudaGraphLaunch(exec, s);
   if (e == cudaSuccess) e = cudaEventRecord(done_, s);
   if (e != cudaSuccess) {
     err = std::string("graph launch failed: ") + cudaGetErrorString(e);
@@ -536,14 +544,18 @@ sift_status Engine::run_pyramid(const ImgIn &img, cudaStream_t s) {
   int M = 0;
   st = fill_plan(1, &img, *hd, lay, &M);
   if (st != SIFT_OK) return st;
-  st = ensure_workspace(lay.total);
+  if (cudaStreamWaitEvent(s, done_, 0) != cudaSuccess) {
+    err = "stream ordering failed";
+    return SIFT_E_CUDA;
+  }
+  st = ensure_workspace(lay.total, s);
   if (st != SIFT_OK) return st;
   lay_ = lay;
   hd->pyr = reinterpret_cast<float *>(ws_ + lay.pyr);
   hd->bm = reinterpret_cast<uint32_t *>(ws_ + lay.bm);
   const size_t bytes = offsetof(Desc, oct) + (size_t)hd->img[0].n_oct * sizeof(OctDev);
-  cudaError_t e = cudaStreamWaitEvent(s, done_, 0);
-  if (e == cudaSuccess) st = upload(hd, bytes, s);
+  cudaError_t e = cudaSuccess;
+  st = upload(hd, bytes, s);
   if (e == cudaSuccess && st == SIFT_OK) e = enqueue_pyramid(s, M, nullptr);
   if (e == cudaSuccess) e = cudaEventRecord(done_, s);
   if (e != cudaSuccess || st != SIFT_OK) {

@@ -56,6 +56,7 @@ class Engine {
   void set_profiling(bool on);
   sift_status kernel_times(double *ms, int *launches, int n_classes);
   sift_status last_stats(int *stats, int max_images);
+  int last_launch_count() const { return last_kernels_; }
 
   Tuning tuning() const { return tun_; }
   void set_tuning(const Tuning &t);
@@ -69,7 +70,7 @@ class Engine {
 
  private:
   sift_status fill_plan(int n, const ImgIn *imgs, Desc &hd, WsLayout &lay, int *max_oct) const;
-  sift_status ensure_workspace(size_t bytes);
+  sift_status ensure_workspace(size_t bytes, cudaStream_t s);
   sift_status upload(Desc *hd, size_t bytes, cudaStream_t s);
   cudaError_t enqueue_pyramid(cudaStream_t s, int max_oct, std::vector<struct ProfRec> *prof);
   cudaError_t enqueue_all(cudaStream_t s, int max_oct, std::vector<struct ProfRec> *prof);
@@ -100,7 +101,10 @@ class Engine {
   struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
     std::vector<struct ProfRec> *prof = nullptr;
+    int kernels = 0;
   };
+  int kernels_ = 0;       // kernels enqueued by the current capture
+  int last_kernels_ = 0;  // kernels in the last replayed graph
   std::map<int, GraphEntry> graphs_;
   bool profiling_ = false;
   std::vector<struct ProfRec> *last_prof_ = nullptr;

@@ -36,15 +36,17 @@ def _gpu(img, **kw):
     return ex, f
 
 
-def _assert_parity(ref, f, label=""):
-    m = compare.match(ref, f.as_numpy())
+def _assert_parity(ref, f, params, label=""):
+    m = compare.match(ref, f.as_numpy(), params=params)
     info = (f"{label}: oracle {m.n_oracle} (eligible {m.n_eligible}), gpu {m.n_gpu}, "
             f"found {m.n_found}, gpu-unmatched {m.n_gpu_unmatched}, worst {m.worst}, "
-            f"desc max L2 {m.desc_max_l2:.2e} over {m.desc_pairs}")
+            f"desc max L2 {m.desc_max_l2:.2e} (direct {m.desc_max_l2_direct:.2e}, "
+            f"{m.n_angle_propagated} angle-propagated) over {m.desc_pairs}")
     print(info)
     assert m.n_eligible > 0, info
     assert m.found_frac >= 0.99, info
     assert m.desc_max_l2 <= compare.DESC_TOL, info
+    assert m.n_angle_propagated <= max(1, 0.01 * m.desc_pairs), info
     assert m.n_gpu_unmatched <= max(2, 0.02 * m.n_gpu), info
     return m
 
@@ -73,43 +75,48 @@ def test_pyramid_matches_oracle(shape, up):
 def test_vga_keypoints_match_oracle():
     img = synth.single_vga(0)
     _, f = _gpu(img, max_kpts=8192)
-    ref = so.extract(img, _oracle_params())
-    _assert_parity(ref, f, "640x480")
+    p = _oracle_params()
+    ref = so.extract(img, p, keep_pyramid=True)
+    _assert_parity(ref, f, p, "640x480")
 
 
 @pytest.mark.parametrize("shape", [(333, 517), (97, 211), (600, 130)])
 def test_ragged_sizes_match_oracle(shape):
     img = synth.make_image(synth.rng_for(11, shape[1]), *shape, n_blobs=60)
     _, f = _gpu(img, max_kpts=8192)
-    ref = so.extract(img, _oracle_params())
-    _assert_parity(ref, f, f"{shape}")
+    p = _oracle_params()
+    ref = so.extract(img, p, keep_pyramid=True)
+    _assert_parity(ref, f, p, f"{shape}")
 
 
 def test_upsampled_keypoints_match_oracle():
     img = synth.make_image(synth.rng_for(12, 0), 260, 350)
     _, f = _gpu(img, upsample=1, max_kpts=8000)
-    ref = so.extract(img, _oracle_params(upsample=True, max_kpts=8000))
-    _assert_parity(ref, f, "260x350 upsampled")
+    p = _oracle_params(upsample=True, max_kpts=8000)
+    ref = so.extract(img, p, keep_pyramid=True)
+    _assert_parity(ref, f, p, "260x350 upsampled")
 
 
 def test_upright_mode_matches_oracle():
     img = synth.make_image(synth.rng_for(13, 0), 300, 400)
     _, f = _gpu(img, upright=1)
-    ref = so.extract(img, _oracle_params(upright=True))
+    p = _oracle_params(upright=True)
+    ref = so.extract(img, p, keep_pyramid=True)
     assert np.all(f.angle.cpu().numpy() == 0)
-    _assert_parity(ref, f, "upright")
+    _assert_parity(ref, f, p, "upright")
 
 
 def test_topk_cap_matches_oracle():
     img = synth.single_vga(1)
     K = 40
     _, f = _gpu(img, max_kpts=K)
-    ref = so.extract(img, _oracle_params(max_kpts=K))
+    p = _oracle_params(max_kpts=K)
+    ref = so.extract(img, p, keep_pyramid=True)
     assert f.count == min(K, len(so.extract(img, _oracle_params())))
     resp = f.response.cpu().numpy()
     # Kept responses are the K largest: compare the sorted response lists.
     np.testing.assert_allclose(np.sort(resp), np.sort(ref.response), rtol=1e-4)
-    _assert_parity(ref, f, "top-K")
+    _assert_parity(ref, f, p, "top-K")
 
 
 # ------------------------------------------------------------------ edge cases

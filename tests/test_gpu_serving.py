@@ -1,0 +1,91 @@
+"""Serving (continuous batching) and autotuning on the GPU.
+
+Each served result must be bit-identical to the same image extracted alone:
+requests are batched with whatever else is in flight, and batching never
+changes an image's arithmetic. Autotuned tile shapes change only the work
+distribution, so tuned and default runs must also agree bit for bit."""
+import numpy as np
+import pytest
+
+from workloads import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2605_17869_gb300 as pkg  # noqa: E402
+
+
+def _same(a, b):
+    if a.count != b.count:
+        return False
+    return all(torch.equal(x, y) for x, y in ((a.x, b.x), (a.y, b.y), (a.sigma, b.sigma),
+                                             (a.angle, b.angle), (a.response, b.response),
+                                             (a.octave, b.octave), (a.layer, b.layer),
+                                             (a.desc, b.desc)))
+
+
+def test_served_results_equal_singleton_runs():
+    shapes = [(480, 640), (1080, 1920), (300, 411), (480, 640), (720, 1280), (97, 211)] * 3
+    imgs = [torch.from_numpy(synth.make_image(synth.rng_for(40, i), *s)).cuda()
+            for i, s in enumerate(shapes)]
+    ref_ex = pkg.Extractor(max_kpts=4096)
+    refs = [ref_ex.extract(im) for im in imgs]
+    ex = pkg.Extractor(max_kpts=4096)
+    srv = pkg.Server(ex, budget_bytes=2 << 30, max_slots=8)
+    tickets = [srv.submit(im) for im in imgs]       # arrive while others run
+    lat = []
+    for t, r in zip(tickets, refs):
+        f, ms, st = srv.result(t)
+        assert st in (pkg.SIFT_OK, pkg.SIFT_W_TRUNCATED)
+        assert _same(f, r)
+        lat.append(ms)
+        srv.release(t)
+    assert all(v > 0 for v in lat)
+    srv.close()
+
+
+def test_poll_and_release_protocol():
+    ex = pkg.Extractor(max_kpts=1024)
+    srv = pkg.Server(ex, budget_bytes=1 << 30, max_slots=4)
+    img = torch.from_numpy(synth.single_vga(3)).cuda()
+    t = srv.submit(img)
+    f = None
+    for _ in range(20000):
+        f = srv.poll(t)
+        if f is not None:
+            break
+    if f is None:
+        f, _, _ = srv.result(t)
+    assert f.count > 0
+    srv.release(t)
+    with pytest.raises(pkg.SiftError) as e:
+        srv.release(t)
+    assert e.value.status == pkg.SIFT_E_NOTFOUND
+    srv.close()
+
+
+def test_budget_rejects_oversized_request():
+    ex = pkg.Extractor(max_kpts=1024)
+    srv = pkg.Server(ex, budget_bytes=8 << 20, max_slots=4)
+    big = torch.zeros((2160, 3840), device="cuda")
+    with pytest.raises(pkg.SiftError) as e:
+        srv.submit(big)
+    assert e.value.status == pkg.SIFT_E_BUDGET
+    srv.close()
+
+
+def test_autotuned_tiles_bit_identical():
+    img = torch.from_numpy(synth.make_image(synth.rng_for(41, 0), 700, 900)).cuda()
+    a = pkg.Extractor()
+    fa = a.extract(img)
+    b = pkg.Extractor()
+    js = b.autotune(700, 900)
+    assert "blur_tile_rows" in js
+    fb = b.extract(img)
+    assert _same(fa, fb)
+    for rows in ("[16, 16, 16, 16, 16]", "[64, 64, 64, 64, 64]", "[16, 32, 64, 32, 16]"):
+        b.set_tuning('{"blur_tile_rows": %s}' % rows)
+        assert _same(fa, b.extract(img))
