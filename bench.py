@@ -211,7 +211,7 @@ def gpu_arm(args, rank, world, pool, n_workers):
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
-    seq = synth.homography_sequence(index=rank)
+    seq = synth.homography_sequence(index=rank, n_warped=args.images - 1)
     imgs_np = seq.images
     shapes = [im.shape for im in imgs_np]
     imgs = _device_images(imgs_np, torch)
@@ -219,7 +219,20 @@ def gpu_arm(args, rank, world, pool, n_workers):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     ex = pkg.Extractor(upsample=1, max_kpts=8000)
-    tuning = ex.autotune(1500, 2000)
+    if args.tuning:
+        ex.set_tuning(args.tuning)
+        tuning = ex.get_tuning()
+    else:
+        tuning = ex.autotune(1500, 2000)
+
+    if args.minimal:
+        def step_min():
+            ex.extract_batch_async(imgs, stream)
+        times, _ = timed_steps(torch, step_min, args.steps, args.warmup, flush, stream)
+        return {"metric": METRIC, "value": round(mpix * args.steps / (sum(times) / 1e3), 2),
+                "unit": "Mpix/s", "mode": "minimal (timed loop only)", "images": len(imgs),
+                "ms_per_step": round(sum(times) / args.steps, 4),
+                "gpu_launches_per_step": ex.launch_count(), "tuning": tuning}, imgs_np
 
     def step():
         ex.extract_batch_async(imgs, stream)
@@ -416,6 +429,10 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--minimal", action="store_true",
+                    help="only the timed batch loop (for profiler launch lists)")
+    ap.add_argument("--images", type=int, default=6, help="images per batch (default 6)")
+    ap.add_argument("--tuning", default="", help='fixed tiles, e.g. {"blur_tile_rows": [32,...]}')
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank = int(os.environ.get("RANK", 0))
@@ -431,7 +448,7 @@ def main():
 
     # The oracle's worker pool is started (spawn) before any GPU call.
     n_workers = min(6, os.cpu_count() or 1)
-    pool = _oracle_pool(n_workers) if rank == 0 else None
+    pool = _oracle_pool(n_workers) if rank == 0 and not args.minimal else None
     if world > 1:
         import torch
         import torch.distributed as dist
@@ -440,7 +457,7 @@ def main():
     try:
         res, imgs_np = gpu_arm(args, rank, world, pool, n_workers)
         if rank == 0:
-            if not args.no_cpu_baseline:
+            if not args.no_cpu_baseline and not args.minimal:
                 res["cpu_baseline"] = cpu_baseline(pool, n_workers, imgs_np)
             print(json.dumps(res))
     finally:
