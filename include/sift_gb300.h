@@ -133,6 +133,29 @@ sift_status sift_extract_batch(sift_handle *h, int n, const float *const *imgs_d
                                const sift_kpts_dev *out_kpts, float *const *out_desc,
                                int *out_counts_dev);
 
+/* Allocation-free extraction of one image, for callers that cannot call
+ * cudaMalloc: plug-ins whose host framework owns all device memory, and
+ * real-time loops that forbid any allocation after start-up. The paper has no
+ * counterpart; this is a deployment variant of sift_extract().
+ * No handle: it takes the parameters directly, because creating a handle
+ * allocates. Its scratch memory (descriptor and workspace) is a fixed 64 MiB
+ * __device__ array inside the library, which every GPU that loads the library
+ * holds until the process exits. It allocates nothing: no cudaMalloc,
+ * cudaFree, stream-ordered or pinned allocation, and no CUDA graph.
+ *   Arguments, outputs and results are those of sift_extract() (same kernels,
+ *   bit-identical output). Returns SIFT_E_BUDGET if the image needs more than
+ *   the fixed scratch (about 1.6 Mpx without upsampling, about 0.4 Mpx with
+ *   it), SIFT_E_INVALID for bad arguments, SIFT_E_CUDA on a launch failure.
+ *   The first call on a device (which must be the current device) resolves the
+ *   scratch array's device address and sets kernel attributes; make that
+ *   first call before any stream capture.
+ *   Every call shares the one scratch array, and it keeps the last call's
+ *   contents (nothing in it needs clearing). Calls whose GPU work overlaps,
+ *   e.g. on two unordered streams, race on it: order them on one stream. */
+sift_status sift_extract_noalloc(const sift_params *p, const float *img_dev, int H, int W,
+                                 int pitch_elems, void *stream, sift_kpts_dev out_kpts,
+                                 float *out_desc_dev, int *out_count_dev);
+
 /* Statistics of the last extraction on this handle, read after synchronising
  * its stream. stats receives, per image i of the last call (up to max_images):
  *   stats[4*i+0] candidates (extrema after the gate), stats[4*i+1] refined

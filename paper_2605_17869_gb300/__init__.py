@@ -21,6 +21,7 @@ from ._abi import (SIFT_E_BUDGET, SIFT_E_CUDA, SIFT_E_INVALID, SIFT_E_NOTFOUND, 
 __all__ = [
     "SiftError", "SiftParams", "SiftKptsDev", "SiftResult", "Features", "Extractor", "Server",
     "sift_params_default", "sift_create", "sift_destroy", "sift_extract", "sift_extract_batch",
+    "sift_extract_noalloc",
     "sift_last_stats", "sift_pyramid_size", "sift_build_pyramid", "sift_set_profiling",
     "sift_kernel_times", "sift_last_launch_count", "sift_autotune", "sift_get_tuning", "sift_set_tuning",
     "sift_serve_create", "sift_serve_submit", "sift_serve_poll", "sift_serve_wait",
@@ -91,6 +92,15 @@ def sift_extract_batch(handle, img_ptrs, Hs, Ws, pitches, stream: int, kpts_list
         handle, n, (c_void_p * n)(*img_ptrs), (c_int * n)(*Hs), (c_int * n)(*Ws),
         (c_int * n)(*pitches), c_void_p(stream), (SiftKptsDev * n)(*kpts_list),
         (c_void_p * n)(*desc_ptrs), c_void_p(counts_ptr)), handle, "sift_extract_batch")
+
+
+def sift_extract_noalloc(params: SiftParams, img_ptr: int, H: int, W: int, pitch: int,
+                         stream: int, kpts: SiftKptsDev, desc_ptr: int, count_ptr: int) -> int:
+    """Allocation-free variant of sift_extract for callers that cannot call
+    cudaMalloc (fixed 64 MiB in-library scratch; see the C header)."""
+    return _check(_lib().sift_extract_noalloc(byref(params), c_void_p(img_ptr), H, W, pitch,
+                                              c_void_p(stream), kpts, c_void_p(desc_ptr),
+                                              c_void_p(count_ptr)), what="sift_extract_noalloc")
 
 
 def sift_last_stats(handle, n_images: int):

@@ -132,6 +132,32 @@ sift_status Engine::init() {
   return SIFT_OK;
 }
 
+// Same set-up as init() minus every allocation: taps, SM count, tile tuning
+// and kernel attributes only.
+sift_status Engine::init_noalloc() {
+  std::string why;
+  if (validate_params(P_, &why) != SIFT_OK) {
+    err = why;
+    return SIFT_E_INVALID;
+  }
+  cudaError_t e = cudaGetDevice(&dev_);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm_, cudaDevAttrMultiProcessorCount, dev_);
+  if (e != cudaSuccess) {
+    err = std::string("CUDA device query failed: ") + cudaGetErrorString(e);
+    return SIFT_E_CUDA;
+  }
+  S_ = P_.n_scales;
+  base_R_ = gaussian_taps(base_sigma(P_), &base_t_);
+  for (int i = 1; i <= S_ + 2; i++) {
+    const double k = std::sqrt(level_sigma(P_, i) * level_sigma(P_, i) -
+                               level_sigma(P_, i - 1) * level_sigma(P_, i - 1));
+    lvl_R_[i] = gaussian_taps(k, &lvl_t_[i]);
+    tun_.lvl_kind[i] = TK_BLUR32;
+  }
+  tun_.grid_mult_blur = 4;
+  return SIFT_OK;
+}
+
 int Engine::octave_sizes(int H, int W, int *hs, int *ws) const {
   int h = P_.upsample ? 2 * H : H, w = P_.upsample ? 2 * W : W;
   int n = 0;

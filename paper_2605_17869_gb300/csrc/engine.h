@@ -64,6 +64,20 @@ class Engine {
   int level_radius(int l) const { return lvl_R_[l]; }
 
   const sift_params &params() const { return P_; }
+
+  // Fixed-scratch path: everything run() does except allocating. The caller
+  // supplies the device descriptor and workspace (see noalloc.cu).
+  sift_status init_noalloc();
+  sift_status plan_noalloc(const ImgIn &img, Desc *hd, WsLayout *lay, int *max_oct) const {
+    return fill_plan(1, &img, *hd, *lay, max_oct);
+  }
+  cudaError_t enqueue_noalloc(Desc *d_desc, cudaStream_t s, int max_oct) {
+    ddesc_ = d_desc;
+    const cudaError_t e = enqueue_all(s, max_oct, nullptr);
+    ddesc_ = nullptr;  // not owned: the destructor must not free it
+    return e;
+  }
+
   std::string err;
   cudaStream_t last_stream = nullptr;
   int last_n = 0;

@@ -1,0 +1,145 @@
+// sift_extract_noalloc: one-image extraction that allocates nothing.
+//
+// Some callers cannot call cudaMalloc: a plug-in hosted by a framework whose
+// memory manager owns all device memory (an allocation behind its back can
+// fail or fragment its pool), or a real-time loop that forbids allocation
+// after start-up so that no call can stall or run out of memory mid-stream.
+// This entry point serves them. Its scratch memory (the device descriptor and
+// every workspace slice) lives in one file-scope __device__ array of fixed
+// size, created when the library's device code is loaded, so a call makes no
+// allocation of any kind: no cudaMalloc / cudaFree / cudaMallocAsync, no
+// pinned host buffer, no CUDA graph. The geometry is written into the array
+// by a one-warp set-up kernel that receives it as a launch parameter.
+#include <cstddef>
+#include <cstring>
+#include <mutex>
+
+#include "engine.h"
+
+namespace sift {
+
+namespace {
+
+// 64 MiB: fits one image of up to about 1.6 Mpx without upsampling (e.g.
+// 1600x1000), or about 0.4 Mpx with the 2x magnified first octave.
+constexpr size_t kScratchBytes = 64ull << 20;
+constexpr int kMaxDevices = 64;
+constexpr size_t kDescBytes = (sizeof(Desc) + 255) / 256 * 256;
+
+// Shared by every call on a device; it keeps the last call's contents. No
+// part of it needs to start at zero: every kernel writes all the entries it
+// later reads. Calls whose work overlaps on the GPU (different streams, no
+// ordering between them) race on it.
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+// The part of a one-image Desc that is not a per-image table.
+struct SetupArgs {
+  unsigned char head[offsetof(Desc, tile_pre)];
+  int tiles[TK_COUNT][kMaxOct];
+  int bmc_n, cc_n;
+  ImgDev img;
+  OctDev oct[kMaxOct];
+};
+
+__global__ void k_noalloc_setup(Desc *d, SetupArgs a) {
+  const int lane = threadIdx.x;
+  unsigned char *dst = reinterpret_cast<unsigned char *>(d);
+  for (int i = lane; i < (int)sizeof(a.head); i += 32) dst[i] = a.head[i];
+  for (int i = lane; i < TK_COUNT * kMaxOct; i += 32) {
+    const int k = i / kMaxOct, o = i % kMaxOct;
+    d->tile_pre[k][o][0] = 0;
+    d->tile_pre[k][o][1] = a.tiles[k][o];
+  }
+  if (lane == 0) {
+    d->bmc_pre[0] = 0;
+    d->bmc_pre[1] = a.bmc_n;
+    d->cc_pre[0] = 0;
+    d->cc_pre[1] = a.cc_n;
+    d->img[0] = a.img;
+  }
+  for (int o = lane; o < a.img.n_oct; o += 32) d->oct[o] = a.oct[o];
+}
+
+struct DeviceScratch {
+  std::once_flag once;
+  void *ptr = nullptr;
+  cudaError_t err = cudaSuccess;
+};
+DeviceScratch g_dev[kMaxDevices];
+
+std::mutex g_plan_mu;
+Desc g_host_desc;  // host-side planning buffer (static storage, not allocated per call)
+
+}  // namespace
+
+}  // namespace sift
+
+using namespace sift;
+
+extern "C" sift_status sift_extract_noalloc(const sift_params *p, const float *img_dev, int H,
+                                            int W, int pitch_elems, void *stream,
+                                            sift_kpts_dev out_kpts, float *out_desc_dev,
+                                            int *out_count_dev) {
+  if (!p || !img_dev || !out_desc_dev || !out_count_dev || !out_kpts.x || !out_kpts.y ||
+      !out_kpts.sigma || !out_kpts.angle || !out_kpts.response || !out_kpts.octave ||
+      !out_kpts.layer)
+    return SIFT_E_INVALID;
+  if (validate_params(*p, nullptr) != SIFT_OK) return SIFT_E_INVALID;
+  if (H < p->min_octave_side || W < p->min_octave_side || pitch_elems < W) return SIFT_E_INVALID;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SIFT_E_CUDA;
+  // First call on this device (which must be current): resolve the device
+  // address of the scratch array and set the kernels' shared-memory limits.
+  DeviceScratch &ds = g_dev[dev];
+  std::call_once(ds.once, [&ds] {
+    ds.err = cudaGetSymbolAddress(&ds.ptr, g_scratch);
+    if (ds.err == cudaSuccess) ds.err = blur_set_attributes();
+    if (ds.err == cudaSuccess) ds.err = descriptor_set_attributes();
+  });
+  if (ds.err != cudaSuccess || !ds.ptr) return SIFT_E_CUDA;
+
+  Engine eng(*p);  // planning and launch sequencing only; it allocates nothing
+  if (eng.init_noalloc() != SIFT_OK) return SIFT_E_CUDA;
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  Desc &hd = g_host_desc;
+  WsLayout lay;
+  int M = 0;
+  ImgIn in{img_dev, H, W, pitch_elems, out_kpts, out_desc_dev, out_count_dev};
+  if (eng.plan_noalloc(in, &hd, &lay, &M) != SIFT_OK) return SIFT_E_INVALID;
+  if (kDescBytes + lay.total > kScratchBytes) return SIFT_E_BUDGET;  // image too large
+
+  char *base = static_cast<char *>(ds.ptr);
+  Desc *d_desc = reinterpret_cast<Desc *>(base);
+  char *ws = base + kDescBytes;
+  hd.pyr = reinterpret_cast<float *>(ws + lay.pyr);
+  hd.bm = reinterpret_cast<uint32_t *>(ws + lay.bm);
+  hd.cand = reinterpret_cast<int4 *>(ws + lay.cand);
+  hd.ref = reinterpret_cast<RefRec *>(ws + lay.ref);
+  hd.code = reinterpret_cast<int *>(ws + lay.code);
+  hd.npk = reinterpret_cast<int *>(ws + lay.npk);
+  hd.angs = reinterpret_cast<float *>(ws + lay.angs);
+  hd.ori = reinterpret_cast<int2 *>(ws + lay.ori);
+  hd.okey = reinterpret_cast<uint32_t *>(ws + lay.okey);
+  hd.fin = reinterpret_cast<int *>(ws + lay.fin);
+  hd.bm_cnt = reinterpret_cast<int *>(ws + lay.bm_cnt);
+  hd.bm_off = reinterpret_cast<int *>(ws + lay.bm_off);
+  hd.cc_cnt = reinterpret_cast<int *>(ws + lay.cc_cnt);
+  hd.cc_off = reinterpret_cast<int *>(ws + lay.cc_off);
+  hd.cnt = reinterpret_cast<ImgCounters *>(ws + lay.cnt);
+  hd.cand_flat = reinterpret_cast<int *>(ws + lay.cand_flat);
+  hd.fin_flat = reinterpret_cast<int *>(ws + lay.fin_flat);
+
+  SetupArgs a;
+  std::memcpy(a.head, &hd, sizeof(a.head));
+  for (int k = 0; k < TK_COUNT; k++)
+    for (int o = 0; o < kMaxOct; o++) a.tiles[k][o] = hd.tile_pre[k][o][1];
+  a.bmc_n = hd.bmc_pre[1];
+  a.cc_n = hd.cc_pre[1];
+  a.img = hd.img[0];
+  for (int o = 0; o < kMaxOct; o++) a.oct[o] = o < hd.img[0].n_oct ? hd.oct[o] : OctDev{};
+  k_noalloc_setup<<<1, 32, 0, s>>>(d_desc, a);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = eng.enqueue_noalloc(d_desc, s, M);
+  return e == cudaSuccess ? SIFT_OK : SIFT_E_CUDA;
+}
