@@ -207,7 +207,7 @@ sift_status sift_get_tuning(sift_handle *h, char *json, size_t len) {
   const int S = h->eng->params().n_scales;
   for (int l = 1; l <= S + 2; l++) {
     const int k = t.lvl_kind[l];
-    s += std::to_string(k == sift::TK_BLUR16 ? 16 : k == sift::TK_BLUR64 ? 64 : 32);
+    s += std::to_string(k == sift::TK_BLUR64 ? 64 : 32);
     if (l < S + 2) s += ", ";
   }
   s += "]}";
@@ -226,9 +226,9 @@ sift_status sift_set_tuning(sift_handle *h, const char *json) {
   for (int l = 1; l <= S + 2; l++) {
     char *end = nullptr;
     const long v = std::strtol(p, &end, 10);
-    if (end == p || (v != 16 && v != 32 && v != 64))
-      return fail(h, SIFT_E_INVALID, "tile rows must be 16, 32 or 64, one per level");
-    t.lvl_kind[l] = v == 16 ? sift::TK_BLUR16 : v == 64 ? sift::TK_BLUR64 : sift::TK_BLUR32;
+    if (end == p || (v != 32 && v != 64))
+      return fail(h, SIFT_E_INVALID, "tile rows must be 32 or 64, one per level");
+    t.lvl_kind[l] = v == 64 ? sift::TK_BLUR64 : sift::TK_BLUR32;
     p = end;
     while (*p == ',' || *p == ' ') p++;
   }

@@ -1,12 +1,13 @@
 // Orientation and descriptor (§3.2), output cap, and the deterministic
 // reduction scheme of §5 ("Bitwise Deterministic GPU Execution").
 //
-// Each keypoint is handled by one warp. Lanes sweep the sample window in a
-// fixed interleaved order and accumulate into lane-private histogram columns
-// in shared memory (layout [bin][lane], so no two lanes ever touch the same
-// word and there are no bank conflicts). The 32 columns are then summed bin by
-// bin in ascending lane order. No atomics are used anywhere: the sum order is
-// fixed by the code, so outputs are bitwise reproducible.
+// Each keypoint is handled by one block of four warps. Threads sweep the
+// sample window in a fixed interleaved order and accumulate into
+// thread-private histogram columns in shared memory (layout [warp][bin][lane],
+// so no two threads ever touch the same word and there are no bank
+// conflicts). The columns are then summed bin by bin, warp by warp and lane by
+// lane. No atomics are used anywhere: the sum order is fixed by the code, so
+// outputs are bitwise reproducible.
 #include "scan.cuh"
 #include "sift_dev.cuh"
 
@@ -15,9 +16,23 @@ namespace sift {
 namespace {
 
 constexpr float kTwoPi = 6.283185307179586f;
-constexpr int kOriWarps = 8;
-constexpr int kDescWarps = 4;
+constexpr int kKpWarps = 4;  // warps per keypoint (orientation and descriptor)
 constexpr int kThreads = 256;
+
+// Sum over the kKpWarps * 32 threads of the block in a fixed order: a butterfly
+// within each warp (every lane ends with the same value), then the warp sums
+// in warp order. Every thread returns the same total.
+__device__ __forceinline__ float block_sum_f(float v, float *red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float s = 0.f;
+#pragma unroll
+  for (int w = 0; w < kKpWarps; w++) s += red[w];
+  __syncthreads();
+  return s;
+}
 
 __device__ __forceinline__ float sigma_of(const Desc *d, const RefRec &r) {
   return d->sigma0 * exp2f(((float)r.s + r.ds) / (float)d->n_scales);
@@ -25,23 +40,26 @@ __device__ __forceinline__ float sigma_of(const Desc *d, const RefRec &r) {
 
 // ------------------------------------------------------------ orientation
 
-__global__ void __launch_bounds__(kOriWarps * 32) k_orientation(const Desc *__restrict__ d) {
-  __shared__ float hist[kOriWarps][kOriBins][32];
-  __shared__ float hsum[kOriWarps][kOriBins];
-  __shared__ float hsm[kOriWarps][kOriBins];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// One block of kKpWarps warps per candidate slot. Lane (w, l) sweeps samples
+// w*32 + l, w*32 + l + 128, ... and votes into its private column hist[w][.][l];
+// bin k is then the sum over w, then l, in that fixed order.
+__global__ void __launch_bounds__(kKpWarps * 32) k_orientation(const Desc *__restrict__ d) {
+  __shared__ float hist[kKpWarps][kOriBins][32];
+  __shared__ float hsum[kOriBins];
+  __shared__ float hsm[kOriBins];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = d->n_img;
   const int total = d->cand_flat[n];
-  for (int t = blockIdx.x * kOriWarps + warp; t < total; t += gridDim.x * kOriWarps) {
+  for (int t = blockIdx.x; t < total; t += gridDim.x) {
     const int b = find_owner(d->cand_flat, n, t);
     const ImgDev &im = d->img[b];
     const long long slot = im.cand_off + (t - d->cand_flat[b]);
     if (d->code[slot] != RC_KEEP) {
-      if (lane == 0) d->npk[slot] = 0;
+      if (tid == 0) d->npk[slot] = 0;
       continue;
     }
     if (d->upright) {
-      if (lane == 0) {
+      if (tid == 0) {
         d->npk[slot] = 1;
         d->angs[slot * kMaxPeaks] = 0.f;
       }
@@ -55,7 +73,7 @@ __global__ void __launch_bounds__(kOriWarps * 32) k_orientation(const Desc *__re
     const float ninv = -1.0f / (2.0f * sw * sw);
     for (int k = 0; k < kOriBins; k++) hist[warp][k][lane] = 0.f;
     const int side = 2 * R + 1, ns = side * side;
-    for (int idx = lane; idx < ns; idx += 32) {
+    for (int idx = tid; idx < ns; idx += kKpWarps * 32) {
       const int jj = idx / side;
       const int i = idx - jj * side - R, j = jj - R;
       const int px = r.x + i, py = r.y + j;
@@ -70,49 +88,51 @@ __global__ void __launch_bounds__(kOriWarps * 32) k_orientation(const Desc *__re
       if (bin >= kOriBins) bin -= kOriBins;
       hist[warp][bin][lane] += expf((float)(i * i + j * j) * ninv) * mag;
     }
-    __syncwarp();
-    for (int k = lane; k < kOriBins; k += 32) {
+    __syncthreads();
+    if (tid < kOriBins) {
       float s = 0.f;
-      for (int q = 0; q < 32; q++) s += hist[warp][k][q];
-      hsum[warp][k] = s;
+      for (int w = 0; w < kKpWarps; w++)
+        for (int q = 0; q < 32; q++) s += hist[w][tid][q];
+      hsum[tid] = s;
     }
-    __syncwarp();
-    float hmax = 0.f;
-    for (int k = lane; k < kOriBins; k += 32) {
-      const float hm = hsum[warp][(k + kOriBins - 1) % kOriBins];
-      const float hp = hsum[warp][(k + 1) % kOriBins];
-      const float v = 0.25f * hm + 0.5f * hsum[warp][k] + 0.25f * hp;
-      hsm[warp][k] = v;
-      hmax = fmaxf(hmax, v);
+    __syncthreads();
+    if (tid < kOriBins) {
+      const float hm = hsum[(tid + kOriBins - 1) % kOriBins];
+      const float hp = hsum[(tid + 1) % kOriBins];
+      hsm[tid] = 0.25f * hm + 0.5f * hsum[tid] + 0.25f * hp;
     }
+    __syncthreads();
+    if (warp == 0) {
+      float hmax = 0.f;
+      for (int k = lane; k < kOriBins; k += 32) hmax = fmaxf(hmax, hsm[k]);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) hmax = fmaxf(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
-    __syncwarp();
-    const float thr = d->ori_peak_ratio * hmax;
-    int base = 0;
-    for (int k0 = 0; k0 < kOriBins; k0 += 32) {
-      const int k = k0 + lane;
-      bool peak = false;
-      float ang = 0.f;
-      if (k < kOriBins) {
-        const float hk = hsm[warp][k];
-        const float hm = hsm[warp][(k + kOriBins - 1) % kOriBins];
-        const float hp = hsm[warp][(k + 1) % kOriBins];
-        if (hk > hm && hk > hp && hk >= thr) {
-          peak = true;
-          float kf = (float)k + 0.5f * (hm - hp) / (hm - 2.0f * hk + hp);
-          if (kf < 0.f) kf += (float)kOriBins;
-          if (kf >= (float)kOriBins) kf -= (float)kOriBins;
-          ang = kf * (360.0f / (float)kOriBins);
-          if (ang >= 360.0f) ang -= 360.0f;
+      for (int o = 16; o > 0; o >>= 1) hmax = fmaxf(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
+      const float thr = d->ori_peak_ratio * hmax;
+      int base = 0;
+      for (int k0 = 0; k0 < kOriBins; k0 += 32) {
+        const int k = k0 + lane;
+        bool peak = false;
+        float ang = 0.f;
+        if (k < kOriBins) {
+          const float hk = hsm[k];
+          const float hm = hsm[(k + kOriBins - 1) % kOriBins];
+          const float hp = hsm[(k + 1) % kOriBins];
+          if (hk > hm && hk > hp && hk >= thr) {
+            peak = true;
+            float kf = (float)k + 0.5f * (hm - hp) / (hm - 2.0f * hk + hp);
+            if (kf < 0.f) kf += (float)kOriBins;
+            if (kf >= (float)kOriBins) kf -= (float)kOriBins;
+            ang = kf * (360.0f / (float)kOriBins);
+            if (ang >= 360.0f) ang -= 360.0f;
+          }
         }
+        const unsigned m = __ballot_sync(0xffffffffu, peak);
+        if (peak) d->angs[slot * kMaxPeaks + base + __popc(m & ((1u << lane) - 1u))] = ang;
+        base += __popc(m);
       }
-      const unsigned m = __ballot_sync(0xffffffffu, peak);
-      if (peak) d->angs[slot * kMaxPeaks + base + __popc(m & ((1u << lane) - 1u))] = ang;
-      base += __popc(m);
+      if (lane == 0) d->npk[slot] = base;
     }
-    if (lane == 0) d->npk[slot] = base;
-    __syncwarp();
+    __syncthreads();
   }
 }
 
@@ -247,13 +267,16 @@ __global__ void __launch_bounds__(1024) k_select(const Desc *__restrict__ d) {
 
 // ------------------------------------------------------------- descriptor
 
-__global__ void __launch_bounds__(kDescWarps * 32) k_descriptor(const Desc *__restrict__ d) {
+// One block of kKpWarps warps per output keypoint; same lane-private
+// histogram scheme as the orientation (merge order: warp, then lane).
+__global__ void __launch_bounds__(kKpWarps * 32) k_descriptor(const Desc *__restrict__ d) {
   extern __shared__ float dsm[];
-  float *hist = dsm + (threadIdx.x >> 5) * (kDescLen * 32);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ float red[kKpWarps];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float *hist = dsm + warp * (kDescLen * 32);
   const int n = d->n_img;
   const int total = d->fin_flat[n];
-  for (int t = blockIdx.x * kDescWarps + warp; t < total; t += gridDim.x * kDescWarps) {
+  for (int t = blockIdx.x; t < total; t += gridDim.x) {
     const int b = find_owner(d->fin_flat, n, t);
     const ImgDev &im = d->img[b];
     const int j = t - d->fin_flat[b];
@@ -264,7 +287,7 @@ __global__ void __launch_bounds__(kDescWarps * 32) k_descriptor(const Desc *__re
     const float angle = d->angs[slot * kMaxPeaks + e.y];
     const OctDev od = d->oct[im.oct0 + r.o];
     const float sig = sigma_of(d, r);
-    if (lane == 0) {
+    if (tid == 0) {
       const float sc = ldexpf(d->upsample ? 0.5f : 1.0f, r.o);
       im.ox[j] = ((float)r.x + r.dx) * sc;
       im.oy[j] = ((float)r.y + r.dy) * sc;
@@ -283,7 +306,7 @@ __global__ void __launch_bounds__(kDescWarps * 32) k_descriptor(const Desc *__re
     sincosf(th, &st, &ct);
     for (int k = 0; k < kDescLen; k++) hist[k * 32 + lane] = 0.f;
     const int side = 2 * R + 1, ns = side * side;
-    for (int idx = lane; idx < ns; idx += 32) {
+    for (int idx = tid; idx < ns; idx += kKpWarps * 32) {
       const int jj = idx / side;
       const int i = idx - jj * side - R, jy = jj - R;
       const int px = r.x + i, py = r.y + jy;
@@ -325,50 +348,32 @@ __global__ void __launch_bounds__(kDescWarps * 32) k_descriptor(const Desc *__re
         }
       }
     }
-    __syncwarp();
-    float val[4];
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-      const float *h = hist + (lane + 32 * q) * 32;
-      float s = 0.f;
-      for (int l = 0; l < 32; l++) s += h[l];
-      val[q] = s;
+    __syncthreads();
+    // Bin tid: sum over warps, then lanes.
+    float val = 0.f;
+    for (int w = 0; w < kKpWarps; w++) {
+      const float *h = dsm + w * (kDescLen * 32) + tid * 32;
+      for (int l = 0; l < 32; l++) val += h[l];
     }
-    float sq = val[0] * val[0] + val[1] * val[1] + val[2] * val[2] + val[3] * val[3];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
     float *out = im.odesc + (long long)j * kDescLen;
+    const float sq = block_sum_f(val * val, red);
     if (sq > 0.f) {
-      float nrm = sqrtf(sq);
-#pragma unroll
-      for (int q = 0; q < 4; q++) val[q] = fminf(val[q] / nrm, 0.2f);
-      sq = val[0] * val[0] + val[1] * val[1] + val[2] * val[2] + val[3] * val[3];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-      nrm = sqrtf(sq);
-#pragma unroll
-      for (int q = 0; q < 4; q++) val[q] = val[q] / nrm;
-      if (d->rootsift) {
-        float l1 = val[0] + val[1] + val[2] + val[3];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) l1 += __shfl_xor_sync(0xffffffffu, l1, o);
-#pragma unroll
-        for (int q = 0; q < 4; q++) val[q] = sqrtf(val[q] / l1);
-      }
+      val = fminf(val / sqrtf(sq), 0.2f);
+      const float sq2 = block_sum_f(val * val, red);
+      val = val / sqrtf(sq2);
+      if (d->rootsift) val = sqrtf(val / block_sum_f(val, red));
     } else {
-#pragma unroll
-      for (int q = 0; q < 4; q++) val[q] = 0.f;
+      val = 0.f;
     }
-#pragma unroll
-    for (int q = 0; q < 4; q++) out[lane + 32 * q] = val[q];
-    __syncwarp();
+    out[tid] = val;
+    __syncthreads();
   }
 }
 
 }  // namespace
 
 cudaError_t launch_orientation(const Desc *d, int grid, cudaStream_t s) {
-  k_orientation<<<grid, kOriWarps * 32, 0, s>>>(d);
+  k_orientation<<<grid, kKpWarps * 32, 0, s>>>(d);
   return cudaGetLastError();
 }
 
@@ -384,7 +389,7 @@ cudaError_t launch_select(const Desc *d, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-int descriptor_smem_bytes() { return kDescWarps * kDescLen * 32 * (int)sizeof(float); }
+int descriptor_smem_bytes() { return kKpWarps * kDescLen * 32 * (int)sizeof(float); }
 
 cudaError_t descriptor_set_attributes() {
   return cudaFuncSetAttribute(k_descriptor, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -392,7 +397,7 @@ cudaError_t descriptor_set_attributes() {
 }
 
 cudaError_t launch_descriptor(const Desc *d, int grid, cudaStream_t s) {
-  k_descriptor<<<grid, kDescWarps * 32, descriptor_smem_bytes(), s>>>(d);
+  k_descriptor<<<grid, kKpWarps * 32, descriptor_smem_bytes(), s>>>(d);
   return cudaGetLastError();
 }
 

@@ -21,79 +21,101 @@ constexpr int kThreads = 256;
 
 // ------------------------------------------------------------ extrema scan
 
-template <int S>
-__device__ __forceinline__ bool is_extremum(const float *__restrict__ G, long long ls, int pitch,
-                                            int y, int x, int s, float c, const float *Dc) {
-  bool mx = true, mn = true;
-#pragma unroll
-  for (int ds = -1; ds <= 1; ds++) {
-    const float *g0 = G + (long long)(s + ds) * ls;
-    const float *g1 = g0 + ls;
-#pragma unroll
-    for (int dy = -1; dy <= 1; dy++) {
-#pragma unroll
-      for (int dx = -1; dx <= 1; dx++) {
-        if (ds == 0 && dy == 0 && dx == 0) continue;
-        float nb;
-        if (dy == 0 && dx == 0) {
-          nb = Dc[s + ds];
-        } else {
-          const long long o = (long long)(y + dy) * pitch + (x + dx);
-          nb = __ldg(g1 + o) - __ldg(g0 + o);
-        }
-        mx = mx && (c > nb);
-        mn = mn && (c < nb);
-        if (!mx && !mn) return false;
-      }
-    }
-  }
-  return true;
-}
-
-// One warp scans 32 adjacent columns of a row; a tile is 32 columns x kExtTH rows.
+// A warp owns a tile of 32 columns x kExtTH rows (lane = column). It issues
+// the loads of all S+3 levels for the tile's rows plus one halo row above and
+// below at once, forms the DoG values in registers (one FP32 subtraction each,
+// as everywhere else), and tests each pixel in three steps:
+//  1. the contrast gate |D| > 0.5 T;
+//  2. a branch-free check against the four direct neighbours in its layer
+//     (left / right by warp shuffle, up / down from the adjacent rows; lanes 0
+//     and 31 skip their outer neighbour here, the exact test below covers it);
+//  3. for the few pixels that pass, the exact 26-neighbour test, done by the
+//     whole warp per pixel (lane k < 26 compares one neighbour, then a vote).
+// Only step 3 decides; steps 1-2 merely skip pixels that cannot pass it.
 template <int S>
 __global__ void __launch_bounds__(kThreads) k_extrema(const Desc *__restrict__ d, int oct) {
+  constexpr int ND = S + 2;
+  constexpr int RR = kExtTH + 2;  // rows held: y0 - 1 .. y0 + kExtTH
+  constexpr int WPB = kThreads / 32;
   const int n = d->n_img;
   const int *pre = d->tile_pre[TK_EXT][oct];
   const int total = pre[n];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   const float thr = d->prefilter;
   const int bord = d->border;
-  for (int t = blockIdx.x; t < total; t += gridDim.x) {
+  // Neighbour k of the 26 (3x3x3 minus the centre), owned by lane k.
+  const int jn = lane < 13 ? lane : lane + 1;
+  const int nds = jn / 9 - 1, ndy = (jn / 3) % 3 - 1, ndx = jn % 3 - 1;
+  for (int t = blockIdx.x * WPB + (threadIdx.x >> 5); t < total; t += gridDim.x * WPB) {
     const int b = find_owner(pre, n, t);
     const ImgDev &im = d->img[b];
     const OctDev od = d->oct[im.oct0 + oct];
+    const int H = od.H, W = od.W, pitch = od.pitch;
     const int lt = t - pre[b];
     const int ty = lt / od.wpr, tx = lt - ty * od.wpr;
-    const int x = tx * 32 + lane;
+    const int x = tx * 32 + lane, y0 = ty * kExtTH;
     const float *G = d->pyr + od.lvl;
-    uint32_t *bm = d->bm + od.bm;
-    const long long layer_words = (long long)od.H * od.wpr;
-    for (int rr = warp; rr < kExtTH; rr += kThreads / 32) {
-      const int y = ty * kExtTH + rr;
-      if (y >= od.H) break;  // uniform over the warp
-      const bool inb = x >= bord && x < od.W - bord && y >= bord && y < od.H - bord;
-      bool cand[S];
+    const long long ls = od.lstride;
+    const int xc = min(x, W - 1);
+    float D[RR][ND];
+    {
+      float g[RR][S + 3];
 #pragma unroll
-      for (int s = 0; s < S; s++) cand[s] = false;
-      if (inb) {
-        float g[S + 3], Dc[S + 2];
-        const long long o = (long long)y * od.pitch + x;
+      for (int r = 0; r < RR; r++) {
+        const int yc = min(max(y0 - 1 + r, 0), H - 1);
+        const float *p = G + (long long)yc * pitch + xc;
 #pragma unroll
-        for (int i = 0; i < S + 3; i++) g[i] = __ldg(G + i * od.lstride + o);
+        for (int l = 0; l < S + 3; l++) g[r][l] = __ldg(p + l * ls);
+      }
 #pragma unroll
-        for (int i = 0; i < S + 2; i++) Dc[i] = g[i + 1] - g[i];
+      for (int r = 0; r < RR; r++)
+#pragma unroll
+        for (int l = 0; l < ND; l++) D[r][l] = g[r][l + 1] - g[r][l];
+    }
+    // Lane s < S writes layer s+1's word of each row.
+    uint32_t *bmw = d->bm + od.bm + (long long)lane * H * od.wpr + tx;
+    const bool xin = x >= bord && x < W - bord;
+#pragma unroll
+    for (int r = 1; r <= kExtTH; r++) {
+      const int y = y0 + r - 1;
+      if (y >= H) break;  // uniform over the warp
+      const bool inb = xin && y >= bord && y < H - bord;
+      bool gated = false;
+#pragma unroll
+      for (int s = 1; s <= S; s++) gated = gated || fabsf(D[r][s]) > thr;
+      unsigned bits[S];
+#pragma unroll
+      for (int s = 0; s < S; s++) bits[s] = 0u;
+      if (__any_sync(0xffffffffu, inb && gated)) {  // most rows skip everything below
 #pragma unroll
         for (int s = 1; s <= S; s++) {
-          const float c = Dc[s];
-          if (fabsf(c) > thr) cand[s - 1] = is_extremum<S>(G, od.lstride, od.pitch, y, x, s, c, Dc);
+          const float cv = D[r][s];
+          const float lf = __shfl_up_sync(0xffffffffu, cv, 1);
+          const float rt = __shfl_down_sync(0xffffffffu, cv, 1);
+          const float up = D[r - 1][s], dn = D[r + 1][s];
+          const bool pmax = cv > up && cv > dn && (lane == 0 || cv > lf) && (lane == 31 || cv > rt);
+          const bool pmin = cv < up && cv < dn && (lane == 0 || cv < lf) && (lane == 31 || cv < rt);
+          const bool ok = inb && fabsf(cv) > thr && (pmax || pmin);
+          unsigned surv = __ballot_sync(0xffffffffu, ok);
+          while (surv) {
+            const int sl = __ffs(surv) - 1;
+            surv &= surv - 1;
+            const float sv = __shfl_sync(0xffffffffu, cv, sl);
+            float nb = 0.f;
+            if (lane < 26) {
+              const long long q = (long long)(y + ndy) * pitch + (x - lane + sl + ndx);
+              nb = __ldg(G + (s + nds + 1) * ls + q) - __ldg(G + (s + nds) * ls + q);
+            }
+            const bool ext = __all_sync(0xffffffffu, lane >= 26 || sv > nb) ||
+                             __all_sync(0xffffffffu, lane >= 26 || sv < nb);
+            if (ext) bits[s - 1] |= 1u << sl;
+          }
         }
       }
+      unsigned mine = bits[0];
 #pragma unroll
-      for (int s = 0; s < S; s++) {
-        const unsigned bits = __ballot_sync(0xffffffffu, cand[s]);
-        if (lane == 0) bm[s * layer_words + (long long)y * od.wpr + tx] = bits;
-      }
+      for (int s = 1; s < S; s++) mine = lane == s ? bits[s] : mine;
+      if (lane < S) bmw[(long long)y * od.wpr] = mine;
     }
   }
 }
@@ -291,6 +313,8 @@ __global__ void __launch_bounds__(kThreads) k_refine(const Desc *__restrict__ d)
 }
 
 }  // namespace
+
+cudaError_t extrema_set_attributes() { return cudaSuccess; }
 
 cudaError_t launch_extrema(const Desc *d, int oct, int n_scales, int grid, cudaStream_t s) {
   switch (n_scales) {

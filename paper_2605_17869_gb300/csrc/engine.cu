@@ -107,6 +107,7 @@ sift_status Engine::init() {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm_, cudaDevAttrMultiProcessorCount, dev_);
   if (e == cudaSuccess) e = blur_set_attributes();
   if (e == cudaSuccess) e = descriptor_set_attributes();
+  if (e == cudaSuccess) e = extrema_set_attributes();
   if (e == cudaSuccess) e = cudaMalloc(&ddesc_, sizeof(Desc));
   for (int i = 0; i < kRing && e == cudaSuccess; i++) {
     e = cudaHostAlloc(&hdesc_[i], sizeof(Desc), cudaHostAllocDefault);
@@ -287,7 +288,7 @@ sift_status Engine::fill_plan(int n, const ImgIn *in, Desc &hd, WsLayout &L, int
         int t = 0;
         if (o < hd.img[b].n_oct) {
           const OctDev &od = hd.oct[hd.img[b].oct0 + o];
-          if (k == TK_EXT) t = od.wpr * div_up(od.H, kExtTH);
+          if (k == TK_EXT) t = div_up(od.W, kExtTW) * div_up(od.H, kExtTH);
           else t = div_up(od.W, kBlurTW) * div_up(od.H, tile_h_of(k));
         }
         pre[b + 1] = pre[b] + t;
@@ -439,11 +440,11 @@ cudaError_t Engine::enqueue_all(cudaStream_t s, int M, std::vector<ProfRec> *pro
         return launch_level_blur(d, o, l, lvl_R_[l], lvl_t_[l], kind, grid_blur(lvl_R_[l], kind, 0), s);
       });
     }
-    rec(PC_EXTREMA, [&] { return launch_extrema(d, o, S_, n_sm_ * 8, s); });
+    rec(PC_EXTREMA, [&] { return launch_extrema(d, o, S_, n_sm_ * 3, s); });
   }
   rec(PC_KEYPOINT, [&] { return launch_bm_compact(d, g4, s); }, 3);
   rec(PC_KEYPOINT, [&] { return launch_refine(d, g4, s); });
-  rec(PC_KEYPOINT, [&] { return launch_orientation(d, g4, s); });
+  rec(PC_KEYPOINT, [&] { return launch_orientation(d, n_sm_ * 8, s); });
   rec(PC_KEYPOINT, [&] { return launch_ori_compact(d, g4, s); }, 3);
   rec(PC_KEYPOINT, [&] { return launch_select(d, n_sm_, s); });
   rec(PC_DESCRIPTOR, [&] { return launch_descriptor(d, n_sm_ * 3, s); });
@@ -677,11 +678,11 @@ sift_status Engine::autotune(int H, int W, cudaStream_t s) {
   cudaEventCreate(&a);
   cudaEventCreate(&b);
   const Desc *d = ddesc_;
-  const int kinds[3] = {TK_BLUR16, TK_BLUR32, TK_BLUR64};
+  const int kinds[2] = {TK_BLUR32, TK_BLUR64};
   for (int l = 1; l <= S_ + 2 && st == SIFT_OK; l++) {
     float best = 1e30f;
     int best_kind = tun_.lvl_kind[l];
-    for (int kk = 0; kk < 3; kk++) {
+    for (int kk = 0; kk < 2; kk++) {
       const int kind = kinds[kk];
       const int g = grid_blur(lvl_R_[l], kind, 0);
       for (int w = 0; w < 2; w++) launch_level_blur(d, 0, l, lvl_R_[l], lvl_t_[l], kind, g, s);

@@ -26,7 +26,7 @@ enum ProfClass { PC_BLUR = 0, PC_BASE = 1, PC_EXTREMA = 2, PC_DECIMATE = 3, PC_K
                  PC_DESCRIPTOR = 5, PC_COUNT = 6 };
 
 struct Tuning {
-  int lvl_kind[kMaxLevels];   // tile-height class per level (TK_BLUR16/32/64)
+  int lvl_kind[kMaxLevels];   // tile-height class per level (TK_BLUR32/64)
   int grid_mult_blur;         // persistent grid = n_sm * blocks/SM * mult / 4
 };
 

@@ -95,6 +95,7 @@ extern "C" sift_status sift_extract_noalloc(const sift_params *p, const float *i
     ds.err = cudaGetSymbolAddress(&ds.ptr, g_scratch);
     if (ds.err == cudaSuccess) ds.err = blur_set_attributes();
     if (ds.err == cudaSuccess) ds.err = descriptor_set_attributes();
+    if (ds.err == cudaSuccess) ds.err = extrema_set_attributes();
   });
   if (ds.err != cudaSuccess || !ds.ptr) return SIFT_E_CUDA;
 

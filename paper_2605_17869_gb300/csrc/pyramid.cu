@@ -3,12 +3,16 @@
 //
 // One kernel launch computes one pyramid level for every image of the batch:
 // a persistent grid walks a flattened queue of 128 x TH output tiles. A tile
-// stages its (TH + 2R) x 160 input window in shared memory (float4 loads on
-// interior tiles, reflect-101 indexing on border tiles), runs the row pass
-// into a second shared buffer (each lane computes 4 adjacent outputs from
-// float4 reads), then the column pass (each lane computes a 4-wide column
-// strip of TH/8 rows, register-blocked). Every output pixel is the same
-// fixed-order FMA chain over its taps whatever the tile shape, so results do
+// stages its (TH + 2R) x 160 input window in shared memory with cp.async
+// (16-byte copies on interior tiles, reflect-101 element copies on border
+// tiles; every copy of the tile is in flight before the one wait), runs the
+// column pass (each thread: a 4-column x TH/8-row block, packed two-lane FP32
+// FMAs) into a second shared buffer, then the row pass (each lane: 4 adjacent
+// outputs from float4 reads) and stores float4 rows.
+//
+// Every output pixel is the same fixed-order FMA chain whatever the tile
+// height: out(y, x) = sum_i w_i * (sum_j w_j * in(y - R + j, x - R + i)), the
+// inner sum over j ascending, the outer over i ascending. Results therefore do
 // not depend on tiling or on which other images share the launch.
 #include "sift_dev.cuh"
 
@@ -16,35 +20,78 @@ namespace sift {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 320;                   // 10 warps
+constexpr int kWarps = kThreads / 32;
 constexpr int kSinW = kBlurTW + 2 * kBlurHalo;  // 160 staged columns
+constexpr int kNG = kSinW / 4;                  // 40 float4 column groups
 
 template <int TH> struct KindOf;
-template <> struct KindOf<16> { static constexpr int v = TK_BLUR16; };
 template <> struct KindOf<32> { static constexpr int v = TK_BLUR32; };
 template <> struct KindOf<64> { static constexpr int v = TK_BLUR64; };
 
-// Stage rows [y0 - R, y0 + TH + R) x columns [x0 - 16, x0 + 144) of a plain
-// image (pyramid level or input) into s_in, reflect-101 at the borders.
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src));
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst)), "l"(src));
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Issue (without waiting) the copies of rows [y0 - R, y0 + TH + R) x columns
+// [x0 - 16, x0 + 144) of a plain image (pyramid level or input) into s_in,
+// reflect-101 at the borders.
+// Thread mapping without divisions: on the 16-byte path thread t copies float4
+// column group t % 40 of rows t / 40, t / 40 + 8, ...; on the element path it
+// copies column t % 160 of rows t / 160, t / 160 + 2, .... Reflection is only
+// computed where the window crosses an image edge.
+__device__ __forceinline__ void stage_plain_issue(const float *__restrict__ src, int pitch, int H,
+                                                  int W, bool vec_ok, int x0, int y0, int R,
+                                                  int rows, float *s_in) {
+  const int xb = x0 - kBlurHalo;
+  const int yb = y0 - R;
+  const bool xin = vec_ok && xb >= 0 && xb + kSinW <= W;
+  const bool yin = yb >= 0 && yb + rows <= H;
+  const int tid = threadIdx.x;
+  if (xin) {
+    constexpr int RPP = kThreads / kNG;  // rows per pass (8)
+    const int g = tid % kNG, r0 = tid / kNG;
+    const float *col = src + xb + 4 * g;
+    float *dst = s_in + r0 * kSinW + 4 * g;
+    if (yin) {
+      const float *p = col + (long long)(yb + r0) * pitch;
+      for (int r = r0; r < rows; r += RPP, p += (long long)RPP * pitch, dst += RPP * kSinW)
+        cp_async16(dst, p);
+    } else {
+      for (int r = r0; r < rows; r += RPP, dst += RPP * kSinW)
+        cp_async16(dst, col + (long long)refl101(yb + r, H) * pitch);
+    }
+  } else {
+    constexpr int RPP = kThreads / kSinW;  // rows per pass (2)
+    const int c = tid % kSinW, r0 = tid / kSinW;
+    const float *col = src + refl101(xb + c, W);
+    float *dst = s_in + r0 * kSinW + c;
+    for (int r = r0; r < rows; r += RPP, dst += RPP * kSinW)
+      cp_async4(dst, col + (long long)(yin ? yb + r : refl101(yb + r, H)) * pitch);
+  }
+}
+
 __device__ __forceinline__ void stage_plain(const float *__restrict__ src, int pitch, int H, int W,
                                             bool vec_ok, int x0, int y0, int R, int rows,
                                             float *s_in) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int xb = x0 - kBlurHalo;
-  const bool xin = vec_ok && xb >= 0 && xb + kSinW <= W;
-  for (int r = warp; r < rows; r += kThreads / 32) {
-    const int gy = refl101(y0 - R + r, H);
-    const float *row = src + (long long)gy * pitch;
-    float *dst = s_in + r * kSinW;
-    if (xin) {
-      const float4 *r4 = reinterpret_cast<const float4 *>(row + xb);
-      float4 *d4 = reinterpret_cast<float4 *>(dst);
-      d4[lane] = __ldg(r4 + lane);
-      if (lane < kSinW / 4 - 32) d4[32 + lane] = __ldg(r4 + 32 + lane);
-    } else {
-      for (int c = lane; c < kSinW; c += 32) dst[c] = __ldg(row + refl101(xb + c, W));
-    }
-  }
+  stage_plain_issue(src, pitch, H, W, vec_ok, x0, y0, R, rows, s_in);
+  cp_async_wait_all();
 }
 
 // Same window, sampled from the 2x bilinear magnification of the input:
@@ -53,136 +100,187 @@ __device__ __forceinline__ void stage_plain(const float *__restrict__ src, int p
 __device__ __forceinline__ void stage_upsampled(const float *__restrict__ src, int spitch, int h,
                                                 int w, int x0, int y0, int R, int rows,
                                                 float *s_in) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int H = 2 * h, W = 2 * w;
   const int xb = x0 - kBlurHalo;
-  for (int r = warp; r < rows; r += kThreads / 32) {
+  for (int idx = threadIdx.x; idx < rows * kSinW; idx += kThreads) {
+    const int r = idx / kSinW, c = idx - r * kSinW;
     const int gy = refl101(y0 - R + r, H);
     const int iy = gy >> 1, fy = gy & 1;
     const int iy1 = min(iy + 1, h - 1);
     const float *ra = src + (long long)iy * spitch;
     const float *rb = src + (long long)iy1 * spitch;
-    float *dst = s_in + r * kSinW;
-    for (int c = lane; c < kSinW; c += 32) {
-      const int gx = refl101(xb + c, W);
-      const int ix = gx >> 1, fx = gx & 1;
-      const int ix1 = min(ix + 1, w - 1);
-      const float a = __ldg(ra + ix);
-      float v;
-      if (!fy) {
-        v = fx ? 0.5f * (a + __ldg(ra + ix1)) : a;
-      } else {
-        const float c0 = __ldg(rb + ix);
-        v = fx ? 0.5f * (0.5f * (a + __ldg(ra + ix1)) + 0.5f * (c0 + __ldg(rb + ix1)))
-               : 0.5f * (a + c0);
-      }
-      dst[c] = v;
+    const int gx = refl101(xb + c, W);
+    const int ix = gx >> 1, fx = gx & 1;
+    const int ix1 = min(ix + 1, w - 1);
+    const float a = __ldg(ra + ix);
+    float v;
+    if (!fy) {
+      v = fx ? 0.5f * (a + __ldg(ra + ix1)) : a;
+    } else {
+      const float c0 = __ldg(rb + ix);
+      v = fx ? 0.5f * (0.5f * (a + __ldg(ra + ix1)) + 0.5f * (c0 + __ldg(rb + ix1)))
+             : 0.5f * (a + c0);
     }
+    s_in[idx] = v;
   }
 }
 
-// Row pass: s_h[r][k] = sum_j w[j] * s_in[r][16 + k - R + j], j = 0..2R in order.
+// Column pass: s_v[v][c] = sum_j w[j] * s_in[v + j][c], j = 0..2R in order.
+// Thread item = one float4 column group x V = TH/8 rows; 8 x 40 items.
 template <int R, int TH>
-__device__ __forceinline__ void row_pass(const float *s_in, float *s_h, const BlurTaps &tp) {
-  constexpr int ROWS = TH + 2 * R;
+__device__ __forceinline__ void col_pass(const float *s_in, float *s_v, const BlurTaps &tp) {
+  constexpr int V = TH / 8;
+  constexpr int ITEMS = (TH / V) * kNG;
+  for (int it = threadIdx.x; it < ITEMS; it += kThreads) {
+    const int rb = it / kNG, g = it - rb * kNG;
+    const float *src = s_in + rb * V * kSinW + 4 * g;
+    float2 acc[V][2];
+#pragma unroll
+    for (int i = 0; i < V + 2 * R; i++) {
+      const float4 f = *reinterpret_cast<const float4 *>(src + i * kSinW);
+      const float2 lo = make_float2(f.x, f.y), hi = make_float2(f.z, f.w);
+#pragma unroll
+      for (int v = 0; v < V; v++) {
+        const int j = i - v;
+        if (j == 0) {
+          const float2 w2 = make_float2(tp.w[0], tp.w[0]);
+          acc[v][0] = __fmul2_rn(w2, lo);
+          acc[v][1] = __fmul2_rn(w2, hi);
+        } else if (j > 0 && j <= 2 * R) {
+          const float2 w2 = make_float2(tp.w[j], tp.w[j]);
+          acc[v][0] = __ffma2_rn(w2, lo, acc[v][0]);
+          acc[v][1] = __ffma2_rn(w2, hi, acc[v][1]);
+        }
+      }
+    }
+    float *dst = s_v + rb * V * kSinW + 4 * g;
+#pragma unroll
+    for (int v = 0; v < V; v++)
+      *reinterpret_cast<float4 *>(dst + v * kSinW) =
+          make_float4(acc[v][0].x, acc[v][0].y, acc[v][1].x, acc[v][1].y);
+  }
+}
+
+// Row pass + store: out[y0 + v][x0 + k] = sum_i w[i] * s_v[v][16 + k - R + i].
+template <int R, int TH>
+__device__ __forceinline__ void row_pass_store(const float *s_v, float *out, int pitch, int H,
+                                               int x0, int y0, const BlurTaps &tp) {
   constexpr int OFF = (kBlurHalo - R) & 3;
   constexpr int C0 = (kBlurHalo - R) - OFF;
   constexpr int NV = (OFF + 4 + 2 * R + 3) / 4;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int r = warp; r < ROWS; r += kThreads / 32) {
-    const float4 *s4 = reinterpret_cast<const float4 *>(s_in + r * kSinW + C0 + 4 * lane);
-    float v[NV * 4];
+  const int x = x0 + 4 * lane;
+  for (int v = warp; v < TH; v += kWarps) {
+    const float4 *s4 = reinterpret_cast<const float4 *>(s_v + v * kSinW + C0 + 4 * lane);
+    float in[NV * 4];
 #pragma unroll
     for (int q = 0; q < NV; q++) {
       const float4 f = s4[q];
-      v[4 * q + 0] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
+      in[4 * q + 0] = f.x; in[4 * q + 1] = f.y; in[4 * q + 2] = f.z; in[4 * q + 3] = f.w;
     }
     float o[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-      float acc = tp.w[0] * v[OFF + k];
+      float acc = tp.w[0] * in[OFF + k];
 #pragma unroll
-      for (int j = 1; j <= 2 * R; j++) acc = fmaf(tp.w[j], v[OFF + k + j], acc);
+      for (int i = 1; i <= 2 * R; i++) acc = fmaf(tp.w[i], in[OFF + k + i], acc);
       o[k] = acc;
     }
-    reinterpret_cast<float4 *>(s_h + r * kBlurTW)[lane] = make_float4(o[0], o[1], o[2], o[3]);
-  }
-}
-
-// Column pass + store: lane owns columns 4*lane..4*lane+3, warp owns TH/8 rows.
-template <int R, int TH>
-__device__ __forceinline__ void col_pass_store(const float *s_h, float *out, int pitch, int H,
-                                               int x0, int y0, const BlurTaps &tp) {
-  constexpr int V = TH / 8;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int v0 = warp * V;
-  float acc[V][4];
-#pragma unroll
-  for (int i = 0; i < V + 2 * R; i++) {
-    const float4 f = reinterpret_cast<const float4 *>(s_h + (v0 + i) * kBlurTW)[lane];
-#pragma unroll
-    for (int v = 0; v < V; v++) {
-      const int j = i - v;
-      if (j == 0) {
-        acc[v][0] = tp.w[0] * f.x; acc[v][1] = tp.w[0] * f.y;
-        acc[v][2] = tp.w[0] * f.z; acc[v][3] = tp.w[0] * f.w;
-      } else if (j > 0 && j <= 2 * R) {
-        acc[v][0] = fmaf(tp.w[j], f.x, acc[v][0]); acc[v][1] = fmaf(tp.w[j], f.y, acc[v][1]);
-        acc[v][2] = fmaf(tp.w[j], f.z, acc[v][2]); acc[v][3] = fmaf(tp.w[j], f.w, acc[v][3]);
-      }
-    }
-  }
-  const int x = x0 + 4 * lane;
-  if (x < pitch) {
-#pragma unroll
-    for (int v = 0; v < V; v++) {
-      const int y = y0 + v0 + v;
-      if (y < H)
-        *reinterpret_cast<float4 *>(out + (long long)y * pitch + x) =
-            make_float4(acc[v][0], acc[v][1], acc[v][2], acc[v][3]);
-    }
+    const int y = y0 + v;
+    if (y < H && x < pitch)
+      *reinterpret_cast<float4 *>(out + (long long)y * pitch + x) = make_float4(o[0], o[1], o[2], o[3]);
   }
 }
 
 // MODE 0: level lvl_out from level lvl_out - 1 of octave `oct`.
 // MODE 1: octave 0 level 0 from the input image.  MODE 2: same, magnified 2x.
+struct TileGeo {
+  const ImgDev *im;
+  OctDev od;
+  int x0, y0;
+};
+
+template <int TH>
+__device__ __forceinline__ TileGeo tile_geo(const Desc *__restrict__ d, const int *pre, int n,
+                                            int oct, int t) {
+  TileGeo g;
+  const int b = find_owner(pre, n, t);
+  g.im = &d->img[b];
+  g.od = d->oct[g.im->oct0 + oct];
+  const int tiles_x = (g.od.W + kBlurTW - 1) / kBlurTW;
+  const int lt = t - pre[b];
+  const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
+  g.x0 = tx * kBlurTW;
+  g.y0 = ty * TH;
+  return g;
+}
+
+// MODE 0 and 1 double-buffer the staging: the copies of the block's next tile
+// are in flight while the current tile is computed.
+template <int R, int TH, int MODE>
+__device__ __forceinline__ void issue_stage(const Desc *__restrict__ d, const TileGeo &g,
+                                            int lvl_out, float *dst) {
+  constexpr int ROWS = TH + 2 * R;
+  if (MODE == 0) {
+    const float *src = d->pyr + g.od.lvl + (long long)(lvl_out - 1) * g.od.lstride;
+    stage_plain_issue(src, g.od.pitch, g.od.H, g.od.W, true, g.x0, g.y0, R, ROWS, dst);
+  } else {
+    stage_plain_issue(g.im->src, g.im->spitch, g.od.H, g.od.W, g.im->src_vec_ok != 0, g.x0, g.y0,
+                      R, ROWS, dst);
+  }
+  cp_async_commit();
+}
+
+// The block's tiles are t0, t0 + grid, t0 + 2 grid, ...; thread 0 resolves the
+// geometry of tile i + 2 while tile i is computed and publishes it through the
+// barrier that ends the iteration (a ring of 4 slots), so no other thread does
+// the image search or reads the descriptor per tile.
 template <int R, int TH, int MODE>
 __global__ void __launch_bounds__(kThreads) k_blur(const Desc *__restrict__ d, int oct, int lvl_out,
                                                    BlurTaps tp) {
   constexpr int ROWS = TH + 2 * R;
+  constexpr bool kPipe = MODE != 2;
   extern __shared__ float4 smem4[];
-  float *s_in = reinterpret_cast<float *>(smem4);
-  float *s_h = s_in + ROWS * kSinW;
+  __shared__ TileGeo geo[4];
+  float *buf0 = reinterpret_cast<float *>(smem4);
+  float *buf1 = buf0 + ROWS * kSinW;
+  float *s_v = kPipe ? buf1 + ROWS * kSinW : buf1;
   const int n = d->n_img;
   const int *pre = d->tile_pre[KindOf<TH>::v][oct];
   const int total = pre[n];
-  for (int t = blockIdx.x; t < total; t += gridDim.x) {
-    const int b = find_owner(pre, n, t);
-    const ImgDev &im = d->img[b];
-    const OctDev od = d->oct[im.oct0 + oct];
-    const int tiles_x = (od.W + kBlurTW - 1) / kBlurTW;
-    const int lt = t - pre[b];
-    const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
-    const int x0 = tx * kBlurTW, y0 = ty * TH;
-    float *out = d->pyr + od.lvl + (long long)lvl_out * od.lstride;
-    if (MODE == 0) {
-      const float *src = d->pyr + od.lvl + (long long)(lvl_out - 1) * od.lstride;
-      stage_plain(src, od.pitch, od.H, od.W, true, x0, y0, R, ROWS, s_in);
-    } else if (MODE == 1) {
-      stage_plain(im.src, im.spitch, od.H, od.W, im.src_vec_ok != 0, x0, y0, R, ROWS, s_in);
+  const int t0 = blockIdx.x, G = gridDim.x;
+  if (t0 >= total) return;
+  if (threadIdx.x == 0) {
+    geo[0] = tile_geo<TH>(d, pre, n, oct, t0);
+    if (t0 + G < total) geo[1] = tile_geo<TH>(d, pre, n, oct, t0 + G);
+  }
+  __syncthreads();
+  if (kPipe) issue_stage<R, TH, MODE>(d, geo[0], lvl_out, buf0);
+  for (int k = 0, t = t0; t < total; t += G, k++) {
+    const TileGeo g = geo[k & 3];
+    float *cur = (kPipe && (k & 1)) ? buf1 : buf0;
+    if (kPipe) {
+      if (t + G < total) {
+        issue_stage<R, TH, MODE>(d, geo[(k + 1) & 3], lvl_out, (k & 1) ? buf0 : buf1);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
     } else {
-      stage_upsampled(im.src, im.spitch, im.H, im.W, x0, y0, R, ROWS, s_in);
+      stage_upsampled(g.im->src, g.im->spitch, g.im->H, g.im->W, g.x0, g.y0, R, ROWS, cur);
     }
     __syncthreads();
-    row_pass<R, TH>(s_in, s_h, tp);
+    col_pass<R, TH>(cur, s_v, tp);
     __syncthreads();
-    col_pass_store<R, TH>(s_h, out, od.pitch, od.H, x0, y0, tp);
+    float *out = d->pyr + g.od.lvl + (long long)lvl_out * g.od.lstride;
+    row_pass_store<R, TH>(s_v, out, g.od.pitch, g.od.H, g.x0, g.y0, tp);
+    if (threadIdx.x == 0 && t + 2 * G < total) geo[(k + 2) & 3] = tile_geo<TH>(d, pre, n, oct, t + 2 * G);
     __syncthreads();
   }
 }
 
 // Fallback for radii without a specialised kernel (non-default parameters):
-// same staging and the same per-output tap order, plain loops.
+// same staging and the same per-output order of operations, plain loops.
 template <int MODE>
 __global__ void __launch_bounds__(kThreads) k_blur_generic(const Desc *__restrict__ d, int oct,
                                                            int lvl_out, int R, BlurTaps tp) {
@@ -190,7 +288,7 @@ __global__ void __launch_bounds__(kThreads) k_blur_generic(const Desc *__restric
   const int ROWS = TH + 2 * R;
   extern __shared__ float4 smem4[];
   float *s_in = reinterpret_cast<float *>(smem4);
-  float *s_h = s_in + ROWS * kSinW;
+  float *s_v = s_in + ROWS * kSinW;
   const int n = d->n_img;
   const int *pre = d->tile_pre[TK_BLUR32][oct];
   const int total = pre[n];
@@ -212,19 +310,19 @@ __global__ void __launch_bounds__(kThreads) k_blur_generic(const Desc *__restric
       stage_upsampled(im.src, im.spitch, im.H, im.W, x0, y0, R, ROWS, s_in);
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < ROWS * kBlurTW; idx += kThreads) {
-      const int r = idx / kBlurTW, k = idx - r * kBlurTW;
-      const float *row = s_in + r * kSinW + kBlurHalo + k - R;
-      float acc = tp.w[0] * row[0];
-      for (int j = 1; j <= 2 * R; j++) acc = fmaf(tp.w[j], row[j], acc);
-      s_h[idx] = acc;
+    for (int idx = threadIdx.x; idx < TH * kSinW; idx += kThreads) {
+      const int v = idx / kSinW, c = idx - v * kSinW;
+      float acc = tp.w[0] * s_in[v * kSinW + c];
+      for (int j = 1; j <= 2 * R; j++) acc = fmaf(tp.w[j], s_in[(v + j) * kSinW + c], acc);
+      s_v[idx] = acc;
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < TH * kBlurTW; idx += kThreads) {
-      const int r = idx / kBlurTW, k = idx - r * kBlurTW;
-      const int y = y0 + r, x = x0 + k;
-      float acc = tp.w[0] * s_h[r * kBlurTW + k];
-      for (int j = 1; j <= 2 * R; j++) acc = fmaf(tp.w[j], s_h[(r + j) * kBlurTW + k], acc);
+      const int v = idx / kBlurTW, k = idx - v * kBlurTW;
+      const int y = y0 + v, x = x0 + k;
+      const float *row = s_v + v * kSinW + kBlurHalo + k - R;
+      float acc = tp.w[0] * row[0];
+      for (int i = 1; i <= 2 * R; i++) acc = fmaf(tp.w[i], row[i], acc);
       if (y < od.H && x < od.pitch) out[(long long)y * od.pitch + x] = acc;
     }
     __syncthreads();
@@ -232,7 +330,7 @@ __global__ void __launch_bounds__(kThreads) k_blur_generic(const Desc *__restric
 }
 
 // Octave o > 0, level 0: every second sample of level S of octave o - 1.
-__global__ void __launch_bounds__(kThreads) k_decimate(const Desc *__restrict__ d, int oct) {
+__global__ void __launch_bounds__(256) k_decimate(const Desc *__restrict__ d, int oct) {
   const int n = d->n_img;
   const int *pre = d->tile_pre[TK_BLUR32][oct];
   const int total = pre[n];
@@ -247,24 +345,31 @@ __global__ void __launch_bounds__(kThreads) k_decimate(const Desc *__restrict__ 
     const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
     const float *src = d->pyr + op.lvl + (long long)S * op.lstride;
     float *dst = d->pyr + od.lvl;
-    for (int idx = threadIdx.x; idx < kBlurTW * 32; idx += kThreads) {
+    for (int idx = threadIdx.x; idx < kBlurTW * 32; idx += 256) {
       const int y = ty * 32 + idx / kBlurTW, x = tx * kBlurTW + (idx % kBlurTW);
       if (y < od.H && x < od.W) dst[(long long)y * od.pitch + x] = src[(long long)(2 * y) * op.pitch + 2 * x];
     }
   }
 }
 
-template <int R, int TH> constexpr int smem_bytes() {
-  return (TH + 2 * R) * (kSinW + kBlurTW) * (int)sizeof(float);
+// Shared memory: two staging buffers (one for the upsampling mode) plus the
+// column-pass output.
+template <int R, int TH, int MODE> constexpr int smem_bytes() {
+  return ((MODE == 2 ? 1 : 2) * (TH + 2 * R) + TH) * kSinW * (int)sizeof(float);
 }
 
-int th_of_kind(int kind) { return kind == TK_BLUR16 ? 16 : kind == TK_BLUR64 ? 64 : 32; }
+int th_of_kind(int kind) { return kind == TK_BLUR64 ? 64 : 32; }
+
+int blur_smem_bytes_mode(int R, int th_kind, int mode) {
+  const int th = th_of_kind(th_kind);
+  return ((mode == 2 ? 1 : 2) * (th + 2 * R) + th) * kSinW * (int)sizeof(float);
+}
+
+int generic_smem_bytes(int R) { return (2 * 32 + 2 * R) * kSinW * (int)sizeof(float); }
 
 }  // namespace
 
-int blur_smem_bytes(int R, int th_kind) {
-  return (th_of_kind(th_kind) + 2 * R) * (kSinW + kBlurTW) * (int)sizeof(float);
-}
+int blur_smem_bytes(int R, int th_kind) { return blur_smem_bytes_mode(R, th_kind, 0); }
 
 #define SIFT_FOR_EACH_R(X) X(5) X(7) X(8) X(10) X(13)
 
@@ -274,15 +379,14 @@ cudaError_t blur_set_attributes() {
   if (e == cudaSuccess)                                                                \
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 #define SET_R(R)                                             \
-  SET((k_blur<R, 16, 0>), (smem_bytes<R, 16>()))             \
-  SET((k_blur<R, 32, 0>), (smem_bytes<R, 32>()))             \
-  SET((k_blur<R, 64, 0>), (smem_bytes<R, 64>()))             \
-  SET((k_blur<R, 32, 1>), (smem_bytes<R, 32>()))             \
-  SET((k_blur<R, 32, 2>), (smem_bytes<R, 32>()))
+  SET((k_blur<R, 32, 0>), (smem_bytes<R, 32, 0>()))          \
+  SET((k_blur<R, 64, 0>), (smem_bytes<R, 64, 0>()))          \
+  SET((k_blur<R, 32, 1>), (smem_bytes<R, 32, 1>()))          \
+  SET((k_blur<R, 32, 2>), (smem_bytes<R, 32, 2>()))
   SIFT_FOR_EACH_R(SET_R)
-  SET(k_blur_generic<0>, (smem_bytes<kMaxR, 32>()))
-  SET(k_blur_generic<1>, (smem_bytes<kMaxR, 32>()))
-  SET(k_blur_generic<2>, (smem_bytes<kMaxR, 32>()))
+  SET(k_blur_generic<0>, generic_smem_bytes(kMaxR))
+  SET(k_blur_generic<1>, generic_smem_bytes(kMaxR))
+  SET(k_blur_generic<2>, generic_smem_bytes(kMaxR))
 #undef SET_R
 #undef SET
   return e;
@@ -290,17 +394,17 @@ cudaError_t blur_set_attributes() {
 
 cudaError_t launch_level_blur(const Desc *d, int oct, int lvl_out, int R, const BlurTaps &t,
                               int th_kind, int grid, cudaStream_t s) {
-  const int bytes = blur_smem_bytes(R, th_kind);
-#define CASE_R(RR)                                                                       \
-  case RR:                                                                               \
-    if (th_kind == TK_BLUR16) k_blur<RR, 16, 0><<<grid, kThreads, bytes, s>>>(d, oct, lvl_out, t); \
-    else if (th_kind == TK_BLUR64) k_blur<RR, 64, 0><<<grid, kThreads, bytes, s>>>(d, oct, lvl_out, t); \
-    else k_blur<RR, 32, 0><<<grid, kThreads, bytes, s>>>(d, oct, lvl_out, t);            \
+#define CASE_R(RR)                                                                            \
+  case RR:                                                                                    \
+    if (th_kind == TK_BLUR64)                                                                 \
+      k_blur<RR, 64, 0><<<grid, kThreads, smem_bytes<RR, 64, 0>(), s>>>(d, oct, lvl_out, t);  \
+    else                                                                                      \
+      k_blur<RR, 32, 0><<<grid, kThreads, smem_bytes<RR, 32, 0>(), s>>>(d, oct, lvl_out, t);  \
     break;
   switch (R) {
     SIFT_FOR_EACH_R(CASE_R)
     default:
-      k_blur_generic<0><<<grid, kThreads, blur_smem_bytes(R, TK_BLUR32), s>>>(d, oct, lvl_out, R, t);
+      k_blur_generic<0><<<grid, kThreads, generic_smem_bytes(R), s>>>(d, oct, lvl_out, R, t);
   }
 #undef CASE_R
   return cudaGetLastError();
@@ -309,17 +413,16 @@ cudaError_t launch_level_blur(const Desc *d, int oct, int lvl_out, int R, const 
 cudaError_t launch_base_blur(const Desc *d, int R, const BlurTaps &t, int th_kind, bool upsample,
                              int grid, cudaStream_t s) {
   (void)th_kind;
-  const int bytes = blur_smem_bytes(R, TK_BLUR32);
-#define CASE_R(RR)                                                                      \
-  case RR:                                                                              \
-    if (upsample) k_blur<RR, 32, 2><<<grid, kThreads, bytes, s>>>(d, 0, 0, t);          \
-    else k_blur<RR, 32, 1><<<grid, kThreads, bytes, s>>>(d, 0, 0, t);                   \
+#define CASE_R(RR)                                                                            \
+  case RR:                                                                                    \
+    if (upsample) k_blur<RR, 32, 2><<<grid, kThreads, smem_bytes<RR, 32, 2>(), s>>>(d, 0, 0, t); \
+    else k_blur<RR, 32, 1><<<grid, kThreads, smem_bytes<RR, 32, 1>(), s>>>(d, 0, 0, t);          \
     break;
   switch (R) {
     SIFT_FOR_EACH_R(CASE_R)
     default:
-      if (upsample) k_blur_generic<2><<<grid, kThreads, bytes, s>>>(d, 0, 0, R, t);
-      else k_blur_generic<1><<<grid, kThreads, bytes, s>>>(d, 0, 0, R, t);
+      if (upsample) k_blur_generic<2><<<grid, kThreads, generic_smem_bytes(R), s>>>(d, 0, 0, R, t);
+      else k_blur_generic<1><<<grid, kThreads, generic_smem_bytes(R), s>>>(d, 0, 0, R, t);
   }
 #undef CASE_R
   return cudaGetLastError();
@@ -327,23 +430,21 @@ cudaError_t launch_base_blur(const Desc *d, int R, const BlurTaps &t, int th_kin
 
 int blur_blocks_per_sm(int R, int th_kind, int mode) {
   int nb = 0;
-  const int bytes = mode == 0 ? blur_smem_bytes(R, th_kind) : blur_smem_bytes(R, TK_BLUR32);
   cudaError_t e = cudaErrorInvalidValue;
-#define OCC(fn) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kThreads, bytes);
-#define CASE_R(RR)                                                   \
-  case RR:                                                           \
-    if (mode == 1) { OCC((k_blur<RR, 32, 1>)) }                      \
-    else if (mode == 2) { OCC((k_blur<RR, 32, 2>)) }                 \
-    else if (th_kind == TK_BLUR16) { OCC((k_blur<RR, 16, 0>)) }      \
-    else if (th_kind == TK_BLUR64) { OCC((k_blur<RR, 64, 0>)) }      \
-    else { OCC((k_blur<RR, 32, 0>)) }                                \
+#define OCC(fn, bytes) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kThreads, bytes);
+#define CASE_R(RR)                                                                       \
+  case RR:                                                                               \
+    if (mode == 1) { OCC((k_blur<RR, 32, 1>), (smem_bytes<RR, 32, 1>())) }                \
+    else if (mode == 2) { OCC((k_blur<RR, 32, 2>), (smem_bytes<RR, 32, 2>())) }           \
+    else if (th_kind == TK_BLUR64) { OCC((k_blur<RR, 64, 0>), (smem_bytes<RR, 64, 0>())) } \
+    else { OCC((k_blur<RR, 32, 0>), (smem_bytes<RR, 32, 0>())) }                          \
     break;
   switch (R) {
     SIFT_FOR_EACH_R(CASE_R)
     default:
-      if (mode == 0) { OCC(k_blur_generic<0>) }
-      else if (mode == 1) { OCC(k_blur_generic<1>) }
-      else { OCC(k_blur_generic<2>) }
+      if (mode == 0) { OCC(k_blur_generic<0>, generic_smem_bytes(R)) }
+      else if (mode == 1) { OCC(k_blur_generic<1>, generic_smem_bytes(R)) }
+      else { OCC(k_blur_generic<2>, generic_smem_bytes(R)) }
   }
 #undef CASE_R
 #undef OCC
@@ -351,7 +452,7 @@ int blur_blocks_per_sm(int R, int th_kind, int mode) {
 }
 
 cudaError_t launch_decimate(const Desc *d, int oct, int grid, cudaStream_t s) {
-  k_decimate<<<grid, kThreads, 0, s>>>(d, oct);
+  k_decimate<<<grid, 256, 0, s>>>(d, oct);
   return cudaGetLastError();
 }
 

@@ -27,7 +27,8 @@ constexpr int kMaxPeaks = kOriBins / 2;  // strict circular maxima of 36 bins
 constexpr int kDescLen = 128;      // 4 x 4 x 8
 constexpr int kBlurTW = 128;       // blur tile width (32 lanes x float4)
 constexpr int kBlurHalo = 16;      // staged columns left/right of a blur tile
-constexpr int kExtTH = 32;         // extrema tile rows (tile = 32 columns)
+constexpr int kExtTW = 32;         // extrema tile columns (one warp)
+constexpr int kExtTH = 8;          // extrema tile rows
 constexpr int kChunk = 2048;       // compaction chunk (words or slots)
 
 // Tile-queue kinds: blur with tile height 16/32/64, extrema tiles, decimation.
@@ -141,6 +142,7 @@ cudaError_t blur_set_attributes();
 
 // Detection (detect.cu)
 cudaError_t launch_extrema(const Desc *d, int oct, int n_scales, int grid, cudaStream_t s);
+cudaError_t extrema_set_attributes();
 cudaError_t launch_bm_compact(const Desc *d, int grid, cudaStream_t s);
 cudaError_t launch_refine(const Desc *d, int grid, cudaStream_t s);
 

@@ -86,6 +86,6 @@ def test_autotuned_tiles_bit_identical():
     assert "blur_tile_rows" in js
     fb = b.extract(img)
     assert _same(fa, fb)
-    for rows in ("[16, 16, 16, 16, 16]", "[64, 64, 64, 64, 64]", "[16, 32, 64, 32, 16]"):
+    for rows in ("[32, 32, 32, 32, 32]", "[64, 64, 64, 64, 64]", "[64, 32, 64, 32, 64]"):
         b.set_tuning('{"blur_tile_rows": %s}' % rows)
         assert _same(fa, b.extract(img))
