@@ -391,13 +391,14 @@ cudaError_t Engine::enqueue_pyramid(cudaStream_t s, int M, std::vector<ProfRec> 
         return launch_base_blur(d, base_R_, base_t_, TK_BLUR32, P_.upsample != 0,
                                 grid_blur(base_R_, TK_BLUR32, mode), s);
       });
-    } else {
-      rec(PC_DECIMATE, [&] { return launch_decimate(d, o, g4, s); });
     }
+    // Octaves above 0: the level-1 launch also produces level 0 by decimating
+    // level S of the previous octave (no separate decimation pass).
     for (int l = 1; l <= S_ + 2; l++) {
       const int kind = tun_.lvl_kind[l];
       rec(PC_BLUR, [&] {
-        return launch_level_blur(d, o, l, lvl_R_[l], lvl_t_[l], kind, grid_blur(lvl_R_[l], kind, 0), s);
+        return launch_level_blur(d, o, l, lvl_R_[l], lvl_t_[l], kind, grid_blur(lvl_R_[l], kind, 0), s,
+                                 o > 0 && l == 1);
       });
     }
   }
@@ -431,13 +432,14 @@ cudaError_t Engine::enqueue_all(cudaStream_t s, int M, std::vector<ProfRec> *pro
         return launch_base_blur(d, base_R_, base_t_, TK_BLUR32, P_.upsample != 0,
                                 grid_blur(base_R_, TK_BLUR32, mode), s);
       });
-    } else {
-      rec(PC_DECIMATE, [&] { return launch_decimate(d, o, g4, s); });
     }
+    // Octaves above 0: the level-1 launch also produces level 0 by decimating
+    // level S of the previous octave (no separate decimation pass).
     for (int l = 1; l <= S_ + 2; l++) {
       const int kind = tun_.lvl_kind[l];
       rec(PC_BLUR, [&] {
-        return launch_level_blur(d, o, l, lvl_R_[l], lvl_t_[l], kind, grid_blur(lvl_R_[l], kind, 0), s);
+        return launch_level_blur(d, o, l, lvl_R_[l], lvl_t_[l], kind, grid_blur(lvl_R_[l], kind, 0), s,
+                                 o > 0 && l == 1);
       });
     }
     rec(PC_EXTREMA, [&] { return launch_extrema(d, o, S_, n_sm_ * 3, s); });

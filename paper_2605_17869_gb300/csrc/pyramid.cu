@@ -125,6 +125,48 @@ __device__ __forceinline__ void stage_upsampled(const float *__restrict__ src, i
   }
 }
 
+// Fast path of the magnified window for tiles that need no reflection: the
+// input rows and columns the window covers are copied with cp.async into
+// s_tmp (rows past the last one are clamped, as the magnification defines),
+// then each magnified sample is formed from shared memory with the same
+// operands and formulas as stage_upsampled. Returns false (having done
+// nothing) when the tile needs the general path. Called by the whole block.
+template <int R, int TH>
+__device__ __forceinline__ bool stage_upsampled_fast(const float *__restrict__ src, int spitch,
+                                                     int h, int w, bool vec_ok, int x0, int y0,
+                                                     float *s_in, float *s_tmp) {
+  constexpr int ROWS = TH + 2 * R;
+  constexpr int NR = ROWS / 2 + 2;  // input rows covered (upper bound)
+  constexpr int NC = 88;            // input columns staged: 80 used + neighbour, float4-rounded
+  const int gyb = y0 - R, gxb = x0 - kBlurHalo;
+  const int ixb = gxb >> 1;
+  if (!(vec_ok && gyb >= 0 && gyb + ROWS <= 2 * h && gxb >= 0 && ixb + NC <= w)) return false;
+  const int iyb = gyb >> 1;
+  for (int q = threadIdx.x; q < NR * (NC / 4); q += kThreads) {
+    const int r = q / (NC / 4), g = q - r * (NC / 4);
+    cp_async16(s_tmp + r * NC + 4 * g, src + (long long)min(iyb + r, h - 1) * spitch + ixb + 4 * g);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  const int c = threadIdx.x % kSinW, r0 = threadIdx.x / kSinW;
+  const int gx = gxb + c;
+  const int ix = (gx >> 1) - ixb, fx = gx & 1;
+  for (int r = r0; r < ROWS; r += kThreads / kSinW) {
+    const int gy = gyb + r;
+    const float *ta = s_tmp + ((gy >> 1) - iyb) * NC + ix;
+    const float a = ta[0];
+    float v;
+    if (!(gy & 1)) {
+      v = fx ? 0.5f * (a + ta[1]) : a;
+    } else {
+      const float c0 = ta[NC];
+      v = fx ? 0.5f * (0.5f * (a + ta[1]) + 0.5f * (c0 + ta[NC + 1])) : 0.5f * (a + c0);
+    }
+    s_in[r * kSinW + c] = v;
+  }
+  return true;
+}
+
 // Column pass: s_v[v][c] = sum_j w[j] * s_in[v + j][c], j = 0..2R in order.
 // Thread item = one float4 column group x V = TH/8 rows; 8 x 40 items.
 template <int R, int TH>
@@ -194,9 +236,13 @@ __device__ __forceinline__ void row_pass_store(const float *s_v, float *out, int
 
 // MODE 0: level lvl_out from level lvl_out - 1 of octave `oct`.
 // MODE 1: octave 0 level 0 from the input image.  MODE 2: same, magnified 2x.
+// MODE 3: level 1 of octave `oct` > 0 from its level 0, decimated on the fly
+//         from level S of octave oct - 1; level 0 itself is stored on the way.
 struct TileGeo {
   const ImgDev *im;
   OctDev od;
+  const float *dsrc;  // octaves > 0: level S of the previous octave (decimation source)
+  int dpitch;
   int x0, y0;
 };
 
@@ -207,6 +253,13 @@ __device__ __forceinline__ TileGeo tile_geo(const Desc *__restrict__ d, const in
   const int b = find_owner(pre, n, t);
   g.im = &d->img[b];
   g.od = d->oct[g.im->oct0 + oct];
+  g.dsrc = nullptr;
+  g.dpitch = 0;
+  if (oct > 0) {
+    const OctDev op = d->oct[g.im->oct0 + oct - 1];
+    g.dsrc = d->pyr + op.lvl + (long long)d->n_scales * op.lstride;
+    g.dpitch = op.pitch;
+  }
   const int tiles_x = (g.od.W + kBlurTW - 1) / kBlurTW;
   const int lt = t - pre[b];
   const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
@@ -215,8 +268,38 @@ __device__ __forceinline__ TileGeo tile_geo(const Desc *__restrict__ d, const in
   return g;
 }
 
-// MODE 0 and 1 double-buffer the staging: the copies of the block's next tile
-// are in flight while the current tile is computed.
+// Issue the copies of the window of octave o > 0's level 0 without storing
+// that level first: sample (y, x) of level 0 is sample (2y, 2x) of level S of
+// octave o - 1, so the window is gathered from there (reflect-101 applied in
+// octave o's own domain), element by element.
+__device__ __forceinline__ void stage_decim_issue(const float *__restrict__ src, int spitch, int H,
+                                                  int W, int x0, int y0, int R, int rows,
+                                                  float *s_in) {
+  const int xb = x0 - kBlurHalo, yb = y0 - R;
+  const bool yin = yb >= 0 && yb + rows <= H;
+  constexpr int RPP = kThreads / kSinW;  // rows per pass (2)
+  const int c = threadIdx.x % kSinW, r0 = threadIdx.x / kSinW;
+  const float *col = src + 2 * refl101(xb + c, W);
+  float *dst = s_in + r0 * kSinW + c;
+  for (int r = r0; r < rows; r += RPP, dst += RPP * kSinW)
+    cp_async4(dst, col + (long long)(2 * (yin ? yb + r : refl101(yb + r, H))) * spitch);
+}
+
+// Store the tile's own rows / columns of the staged (decimated) level 0.
+template <int R, int TH>
+__device__ __forceinline__ void store_level0(const float *s_in, float *out0, int pitch, int H,
+                                             int x0, int y0) {
+  for (int q = threadIdx.x; q < TH * (kBlurTW / 4); q += kThreads) {
+    const int v = q / (kBlurTW / 4), g = q - v * (kBlurTW / 4);
+    const int y = y0 + v, x = x0 + 4 * g;
+    if (y < H && x < pitch)
+      *reinterpret_cast<float4 *>(out0 + (long long)y * pitch + x) =
+          *reinterpret_cast<const float4 *>(s_in + (R + v) * kSinW + kBlurHalo + 4 * g);
+  }
+}
+
+// MODE 0, 1 and 3 double-buffer the staging: the copies of the block's next
+// tile are in flight while the current tile is computed.
 template <int R, int TH, int MODE>
 __device__ __forceinline__ void issue_stage(const Desc *__restrict__ d, const TileGeo &g,
                                             int lvl_out, float *dst) {
@@ -224,6 +307,8 @@ __device__ __forceinline__ void issue_stage(const Desc *__restrict__ d, const Ti
   if (MODE == 0) {
     const float *src = d->pyr + g.od.lvl + (long long)(lvl_out - 1) * g.od.lstride;
     stage_plain_issue(src, g.od.pitch, g.od.H, g.od.W, true, g.x0, g.y0, R, ROWS, dst);
+  } else if (MODE == 3) {
+    stage_decim_issue(g.dsrc, g.dpitch, g.od.H, g.od.W, g.x0, g.y0, R, ROWS, dst);
   } else {
     stage_plain_issue(g.im->src, g.im->spitch, g.od.H, g.od.W, g.im->src_vec_ok != 0, g.x0, g.y0,
                       R, ROWS, dst);
@@ -266,10 +351,12 @@ __global__ void __launch_bounds__(kThreads) k_blur(const Desc *__restrict__ d, i
       } else {
         cp_async_wait<0>();
       }
-    } else {
+    } else if (!stage_upsampled_fast<R, TH>(g.im->src, g.im->spitch, g.im->H, g.im->W,
+                                             g.im->src_vec_ok != 0, g.x0, g.y0, cur, s_v)) {
       stage_upsampled(g.im->src, g.im->spitch, g.im->H, g.im->W, g.x0, g.y0, R, ROWS, cur);
     }
     __syncthreads();
+    if (MODE == 3) store_level0<R, TH>(cur, d->pyr + g.od.lvl, g.od.pitch, g.od.H, g.x0, g.y0);
     col_pass<R, TH>(cur, s_v, tp);
     __syncthreads();
     float *out = d->pyr + g.od.lvl + (long long)lvl_out * g.od.lstride;
@@ -306,10 +393,22 @@ __global__ void __launch_bounds__(kThreads) k_blur_generic(const Desc *__restric
       stage_plain(src, od.pitch, od.H, od.W, true, x0, y0, R, ROWS, s_in);
     } else if (MODE == 1) {
       stage_plain(im.src, im.spitch, od.H, od.W, im.src_vec_ok != 0, x0, y0, R, ROWS, s_in);
+    } else if (MODE == 3) {
+      const OctDev op = d->oct[im.oct0 + oct - 1];
+      stage_decim_issue(d->pyr + op.lvl + (long long)d->n_scales * op.lstride, op.pitch, od.H, od.W,
+                        x0, y0, R, ROWS, s_in);
+      cp_async_wait_all();
     } else {
       stage_upsampled(im.src, im.spitch, im.H, im.W, x0, y0, R, ROWS, s_in);
     }
     __syncthreads();
+    if (MODE == 3) {
+      for (int q = threadIdx.x; q < TH * kBlurTW; q += kThreads) {
+        const int v = q / kBlurTW, k = q - v * kBlurTW;
+        if (y0 + v < od.H && x0 + k < od.pitch)
+          d->pyr[od.lvl + (long long)(y0 + v) * od.pitch + x0 + k] = s_in[(R + v) * kSinW + kBlurHalo + k];
+      }
+    }
     for (int idx = threadIdx.x; idx < TH * kSinW; idx += kThreads) {
       const int v = idx / kSinW, c = idx - v * kSinW;
       float acc = tp.w[0] * s_in[v * kSinW + c];
@@ -381,10 +480,13 @@ cudaError_t blur_set_attributes() {
 #define SET_R(R)                                             \
   SET((k_blur<R, 32, 0>), (smem_bytes<R, 32, 0>()))          \
   SET((k_blur<R, 64, 0>), (smem_bytes<R, 64, 0>()))          \
+  SET((k_blur<R, 32, 3>), (smem_bytes<R, 32, 3>()))          \
+  SET((k_blur<R, 64, 3>), (smem_bytes<R, 64, 3>()))          \
   SET((k_blur<R, 32, 1>), (smem_bytes<R, 32, 1>()))          \
   SET((k_blur<R, 32, 2>), (smem_bytes<R, 32, 2>()))
   SIFT_FOR_EACH_R(SET_R)
   SET(k_blur_generic<0>, generic_smem_bytes(kMaxR))
+  SET(k_blur_generic<3>, generic_smem_bytes(kMaxR))
   SET(k_blur_generic<1>, generic_smem_bytes(kMaxR))
   SET(k_blur_generic<2>, generic_smem_bytes(kMaxR))
 #undef SET_R
@@ -393,18 +495,23 @@ cudaError_t blur_set_attributes() {
 }
 
 cudaError_t launch_level_blur(const Desc *d, int oct, int lvl_out, int R, const BlurTaps &t,
-                              int th_kind, int grid, cudaStream_t s) {
-#define CASE_R(RR)                                                                            \
-  case RR:                                                                                    \
-    if (th_kind == TK_BLUR64)                                                                 \
-      k_blur<RR, 64, 0><<<grid, kThreads, smem_bytes<RR, 64, 0>(), s>>>(d, oct, lvl_out, t);  \
-    else                                                                                      \
-      k_blur<RR, 32, 0><<<grid, kThreads, smem_bytes<RR, 32, 0>(), s>>>(d, oct, lvl_out, t);  \
+                              int th_kind, int grid, cudaStream_t s, bool from_prev_octave) {
+  const bool m3 = from_prev_octave;
+#define CASE_R(RR)                                                                               \
+  case RR:                                                                                       \
+    if (th_kind == TK_BLUR64) {                                                                  \
+      if (m3) k_blur<RR, 64, 3><<<grid, kThreads, smem_bytes<RR, 64, 3>(), s>>>(d, oct, lvl_out, t); \
+      else k_blur<RR, 64, 0><<<grid, kThreads, smem_bytes<RR, 64, 0>(), s>>>(d, oct, lvl_out, t);    \
+    } else {                                                                                     \
+      if (m3) k_blur<RR, 32, 3><<<grid, kThreads, smem_bytes<RR, 32, 3>(), s>>>(d, oct, lvl_out, t); \
+      else k_blur<RR, 32, 0><<<grid, kThreads, smem_bytes<RR, 32, 0>(), s>>>(d, oct, lvl_out, t);    \
+    }                                                                                            \
     break;
   switch (R) {
     SIFT_FOR_EACH_R(CASE_R)
     default:
-      k_blur_generic<0><<<grid, kThreads, generic_smem_bytes(R), s>>>(d, oct, lvl_out, R, t);
+      if (m3) k_blur_generic<3><<<grid, kThreads, generic_smem_bytes(R), s>>>(d, oct, lvl_out, R, t);
+      else k_blur_generic<0><<<grid, kThreads, generic_smem_bytes(R), s>>>(d, oct, lvl_out, R, t);
   }
 #undef CASE_R
   return cudaGetLastError();

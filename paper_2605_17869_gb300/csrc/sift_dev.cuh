@@ -134,7 +134,7 @@ __device__ __forceinline__ int refl101(int i, int n) {
 cudaError_t launch_base_blur(const Desc *d, int R, const BlurTaps &t, int th_kind, bool upsample,
                              int grid, cudaStream_t s);
 cudaError_t launch_level_blur(const Desc *d, int oct, int lvl_out, int R, const BlurTaps &t,
-                              int th_kind, int grid, cudaStream_t s);
+                              int th_kind, int grid, cudaStream_t s, bool from_prev_octave = false);
 cudaError_t launch_decimate(const Desc *d, int oct, int grid, cudaStream_t s);
 int blur_smem_bytes(int R, int th_kind);
 int blur_blocks_per_sm(int R, int th_kind, int mode);
