@@ -24,10 +24,19 @@ inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
 constexpr size_t kAlign = 256;
 }  // namespace
 
+static void fill_tap_pairs(BlurTaps *t) {
+  for (int i = 0; i <= kMaxR; i++) {
+    t->wp[i] = make_float2(t->w[2 * i], t->w[2 * i + 1]);
+    t->wq[i] = make_float2(t->w[2 * i + 1], 2 * i + 2 <= 2 * kMaxR ? t->w[2 * i + 2] : 0.0f);
+  }
+  for (int j = 0; j <= 2 * kMaxR; j++) t->wd[j] = make_float2(t->w[j], t->w[j]);
+}
+
 int gaussian_taps(double sigma, BlurTaps *t) {
   std::memset(t, 0, sizeof(*t));
   if (!(sigma > 0.0)) {
     t->w[0] = 1.0f;
+    fill_tap_pairs(t);
     return 0;
   }
   const int r = (int)std::ceil(4.0 * sigma);
@@ -39,6 +48,7 @@ int gaussian_taps(double sigma, BlurTaps *t) {
     sum += w[k + r];
   }
   for (int k = 0; k <= 2 * r; k++) t->w[k] = (float)(w[k] / sum);
+  fill_tap_pairs(t);
   return r;
 }
 

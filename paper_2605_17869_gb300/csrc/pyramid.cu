@@ -10,10 +10,12 @@
 // FMAs) into a second shared buffer, then the row pass (each lane: 4 adjacent
 // outputs from float4 reads) and stores float4 rows.
 //
-// Every output pixel is the same fixed-order FMA chain whatever the tile
-// height: out(y, x) = sum_i w_i * (sum_j w_j * in(y - R + j, x - R + i)), the
-// inner sum over j ascending, the outer over i ascending. Results therefore do
-// not depend on tiling or on which other images share the launch.
+// Every output pixel is the same fixed-order chain of FP32 operations whatever
+// the tile: out(y, x) = sum_i w_i * c_i with c_i = sum_j w_j * in(y - R + j,
+// x - R + i), each c_i summed over j ascending and the outer sum split into
+// two ascending chains of alternate taps whose grouping depends only on the
+// parity of x - R (row_pass_store). Results therefore do not depend on tiling
+// or on which other images share the launch.
 #include "sift_dev.cuh"
 
 namespace sift {
@@ -42,40 +44,47 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-template <int N> __device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
 // Issue (without waiting) the copies of rows [y0 - R, y0 + TH + R) x columns
 // [x0 - 16, x0 + 144) of a plain image (pyramid level or input) into s_in,
 // reflect-101 at the borders.
-// Thread mapping without divisions: on the 16-byte path thread t copies float4
-// column group t % 40 of rows t / 40, t / 40 + 8, ...; on the element path it
-// copies column t % 160 of rows t / 160, t / 160 + 2, .... Reflection is only
-// computed where the window crosses an image edge.
+// 16-byte path (16-byte aligned rows): thread t copies float4 column group
+// t % 40 of rows t / 40, t / 40 + 8, ...; a group that crosses or lies past an
+// image edge copies its four reflected columns one by one. Element path
+// (unaligned input rows): thread t copies column t % 160 of rows t / 160,
+// t / 160 + 2, .... Reflection is only computed where the window crosses an
+// image edge.
 __device__ __forceinline__ void stage_plain_issue(const float *__restrict__ src, int pitch, int H,
                                                   int W, bool vec_ok, int x0, int y0, int R,
                                                   int rows, float *s_in) {
   const int xb = x0 - kBlurHalo;
   const int yb = y0 - R;
-  const bool xin = vec_ok && xb >= 0 && xb + kSinW <= W;
   const bool yin = yb >= 0 && yb + rows <= H;
   const int tid = threadIdx.x;
-  if (xin) {
+  if (vec_ok) {
     constexpr int RPP = kThreads / kNG;  // rows per pass (8)
     const int g = tid % kNG, r0 = tid / kNG;
-    const float *col = src + xb + 4 * g;
+    const int c = xb + 4 * g;
     float *dst = s_in + r0 * kSinW + 4 * g;
-    if (yin) {
-      const float *p = col + (long long)(yb + r0) * pitch;
-      for (int r = r0; r < rows; r += RPP, p += (long long)RPP * pitch, dst += RPP * kSinW)
-        cp_async16(dst, p);
+    if (c >= 0 && c + 4 <= W) {
+      const float *col = src + c;
+      if (yin) {
+        const float *p = col + (long long)(yb + r0) * pitch;
+        for (int r = r0; r < rows; r += RPP, p += (long long)RPP * pitch, dst += RPP * kSinW)
+          cp_async16(dst, p);
+      } else {
+        for (int r = r0; r < rows; r += RPP, dst += RPP * kSinW)
+          cp_async16(dst, col + (long long)refl101(yb + r, H) * pitch);
+      }
     } else {
-      for (int r = r0; r < rows; r += RPP, dst += RPP * kSinW)
-        cp_async16(dst, col + (long long)refl101(yb + r, H) * pitch);
+      const int c0 = refl101(c, W), c1 = refl101(c + 1, W), c2 = refl101(c + 2, W),
+                c3 = refl101(c + 3, W);
+      for (int r = r0; r < rows; r += RPP, dst += RPP * kSinW) {
+        const float *row = src + (long long)(yin ? yb + r : refl101(yb + r, H)) * pitch;
+        cp_async4(dst, row + c0);
+        cp_async4(dst + 1, row + c1);
+        cp_async4(dst + 2, row + c2);
+        cp_async4(dst + 3, row + c3);
+      }
     }
   } else {
     constexpr int RPP = kThreads / kSinW;  // rows per pass (2)
@@ -167,14 +176,25 @@ __device__ __forceinline__ bool stage_upsampled_fast(const float *__restrict__ s
   return true;
 }
 
-// Column pass: s_v[v][c] = sum_j w[j] * s_in[v + j][c], j = 0..2R in order.
-// Thread item = one float4 column group x V = TH/8 rows; 8 x 40 items.
+// Staged columns the row pass reads: float4 groups [RowSpan<R>::G0, G1).
+template <int R> struct RowSpan {
+  static constexpr int OFF = (kBlurHalo - R) & 3;      // first tap's offset in the first group
+  static constexpr int C0 = (kBlurHalo - R) - OFF;     // first column read by lane 0
+  static constexpr int NV = (OFF + 4 + 2 * R + 3) / 4; // float4 groups read per lane
+  static constexpr int G0 = C0 / 4;
+  static constexpr int G1 = G0 + 31 + NV;
+};
+
+// Column pass: s_v[v][c] = sum_j w[j] * s_in[v + j][c], j = 0..2R in order,
+// for the column groups the row pass reads. Thread item = one float4 column
+// group x V = TH/8 rows.
 template <int R, int TH>
 __device__ __forceinline__ void col_pass(const float *s_in, float *s_v, const BlurTaps &tp) {
   constexpr int V = TH / 8;
-  constexpr int ITEMS = (TH / V) * kNG;
+  constexpr int NG = RowSpan<R>::G1 - RowSpan<R>::G0;
+  constexpr int ITEMS = (TH / V) * NG;
   for (int it = threadIdx.x; it < ITEMS; it += kThreads) {
-    const int rb = it / kNG, g = it - rb * kNG;
+    const int rb = it / NG, g = RowSpan<R>::G0 + it - rb * NG;
     const float *src = s_in + rb * V * kSinW + 4 * g;
     float2 acc[V][2];
 #pragma unroll
@@ -185,13 +205,11 @@ __device__ __forceinline__ void col_pass(const float *s_in, float *s_v, const Bl
       for (int v = 0; v < V; v++) {
         const int j = i - v;
         if (j == 0) {
-          const float2 w2 = make_float2(tp.w[0], tp.w[0]);
-          acc[v][0] = __fmul2_rn(w2, lo);
-          acc[v][1] = __fmul2_rn(w2, hi);
+          acc[v][0] = __fmul2_rn(tp.wd[0], lo);
+          acc[v][1] = __fmul2_rn(tp.wd[0], hi);
         } else if (j > 0 && j <= 2 * R) {
-          const float2 w2 = make_float2(tp.w[j], tp.w[j]);
-          acc[v][0] = __ffma2_rn(w2, lo, acc[v][0]);
-          acc[v][1] = __ffma2_rn(w2, hi, acc[v][1]);
+          acc[v][0] = __ffma2_rn(tp.wd[j], lo, acc[v][0]);
+          acc[v][1] = __ffma2_rn(tp.wd[j], hi, acc[v][1]);
         }
       }
     }
@@ -203,17 +221,29 @@ __device__ __forceinline__ void col_pass(const float *s_in, float *s_v, const Bl
   }
 }
 
-// Row pass + store: out[y0 + v][x0 + k] = sum_i w[i] * s_v[v][16 + k - R + i].
+// Row pass + store: out[y0 + v][x0 + k] from s_v[v][16 + k - R + i], i = 0..2R.
+// Lane l of a warp produces outputs x0 + 4l .. x0 + 4l + 3 of one row. The
+// taps are taken two at a time by packed FMAs whose operand pairs are aligned
+// (even, odd) column pairs of the row, so with s the output's first tap
+// column (each lane of a packed FMA is an ordinary FP32 fma):
+//   s even: a = (w0 v[s], w1 v[s+1]), a += (w2i, w2i+1)(v[s+2i], v[s+2i+1]) for
+//           i = 1..R-1, out = fma(w2R, v[s+2R], a.x) + a.y;
+//   s odd:  a = (w1 v[s+1], w2 v[s+2]), a += (w2i+1, w2i+2)(v[s+2i+1], v[s+2i+2])
+//           for i = 1..R-1, out = fma(w0, v[s], a.x) + a.y.
+// The parity of s is that of the output's column, so the order of operations
+// is a fixed function of the pixel, independent of tiling.
 template <int R, int TH>
 __device__ __forceinline__ void row_pass_store(const float *s_v, float *out, int pitch, int H,
                                                int x0, int y0, const BlurTaps &tp) {
-  constexpr int OFF = (kBlurHalo - R) & 3;
-  constexpr int C0 = (kBlurHalo - R) - OFF;
-  constexpr int NV = (OFF + 4 + 2 * R + 3) / 4;
+  constexpr int OFF = RowSpan<R>::OFF;
+  constexpr int NV = RowSpan<R>::NV;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int x = x0 + 4 * lane;
-  for (int v = warp; v < TH; v += kWarps) {
-    const float4 *s4 = reinterpret_cast<const float4 *>(s_v + v * kSinW + C0 + 4 * lane);
+  const bool xok = x < pitch;
+  const float *sp = s_v + warp * kSinW + RowSpan<R>::C0 + 4 * lane;
+  float *op = out + (long long)(y0 + warp) * pitch + x;
+  for (int v = warp; v < TH; v += kWarps, sp += kWarps * kSinW, op += (long long)kWarps * pitch) {
+    const float4 *s4 = reinterpret_cast<const float4 *>(sp);
     float in[NV * 4];
 #pragma unroll
     for (int q = 0; q < NV; q++) {
@@ -223,15 +253,45 @@ __device__ __forceinline__ void row_pass_store(const float *s_v, float *out, int
     float o[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-      float acc = tp.w[0] * in[OFF + k];
+      const int s = OFF + k;
+      if ((s & 1) == 0) {
+        float2 a = __fmul2_rn(tp.wp[0], make_float2(in[s], in[s + 1]));
 #pragma unroll
-      for (int i = 1; i <= 2 * R; i++) acc = fmaf(tp.w[i], in[OFF + k + i], acc);
-      o[k] = acc;
+        for (int i = 1; i < R; i++)
+          a = __ffma2_rn(tp.wp[i], make_float2(in[s + 2 * i], in[s + 2 * i + 1]), a);
+        o[k] = __fadd_rn(fmaf(tp.w[2 * R], in[s + 2 * R], a.x), a.y);
+      } else {
+        float2 a = __fmul2_rn(tp.wq[0], make_float2(in[s + 1], in[s + 2]));
+#pragma unroll
+        for (int i = 1; i < R; i++)
+          a = __ffma2_rn(tp.wq[i], make_float2(in[s + 2 * i + 1], in[s + 2 * i + 2]), a);
+        o[k] = __fadd_rn(fmaf(tp.w[0], in[s], a.x), a.y);
+      }
     }
-    const int y = y0 + v;
-    if (y < H && x < pitch)
-      *reinterpret_cast<float4 *>(out + (long long)y * pitch + x) = make_float4(o[0], o[1], o[2], o[3]);
+    if (y0 + v < H && xok) *reinterpret_cast<float4 *>(op) = make_float4(o[0], o[1], o[2], o[3]);
   }
+}
+
+// The same output from scalar operations, for the generic kernel: row points
+// at the output's first tap column s, odd tells the parity of s.
+__device__ __forceinline__ float row_tap_sum(const float *row, bool odd, int R, const float *w) {
+  float ax, ay;
+  if (!odd) {
+    ax = __fmul_rn(w[0], row[0]);
+    ay = __fmul_rn(w[1], row[1]);
+    for (int i = 1; i < R; i++) {
+      ax = fmaf(w[2 * i], row[2 * i], ax);
+      ay = fmaf(w[2 * i + 1], row[2 * i + 1], ay);
+    }
+    return __fadd_rn(fmaf(w[2 * R], row[2 * R], ax), ay);
+  }
+  ax = __fmul_rn(w[1], row[1]);
+  ay = __fmul_rn(w[2], row[2]);
+  for (int i = 1; i < R; i++) {
+    ax = fmaf(w[2 * i + 1], row[2 * i + 1], ax);
+    ay = fmaf(w[2 * i + 2], row[2 * i + 2], ay);
+  }
+  return __fadd_rn(fmaf(w[0], row[0], ax), ay);
 }
 
 // MODE 0: level lvl_out from level lvl_out - 1 of octave `oct`.
@@ -239,28 +299,47 @@ __device__ __forceinline__ void row_pass_store(const float *s_v, float *out, int
 // MODE 3: level 1 of octave `oct` > 0 from its level 0, decimated on the fly
 //         from level S of octave oct - 1; level 0 itself is stored on the way.
 struct TileGeo {
-  const ImgDev *im;
-  OctDev od;
-  const float *dsrc;  // octaves > 0: level S of the previous octave (decimation source)
-  int dpitch;
+  const float *src;  // staging source: level lvl_out - 1 (MODE 0), the input (1, 2),
+                     // level S of the previous octave (3)
+  float *out;        // level lvl_out of the tile's octave
+  float *out0;       // level 0 of the tile's octave (MODE 3 stores it)
+  int spitch;        // source pitch (elements)
+  int pitch, H, W;   // the octave's pitch and size
+  int sh, sw;        // input size (MODE 2)
+  int vec;           // 16-byte aligned source rows
   int x0, y0;
 };
 
-template <int TH>
+template <int TH, int MODE>
 __device__ __forceinline__ TileGeo tile_geo(const Desc *__restrict__ d, const int *pre, int n,
-                                            int oct, int t) {
+                                            int oct, int lvl_out, int t) {
   TileGeo g;
   const int b = find_owner(pre, n, t);
-  g.im = &d->img[b];
-  g.od = d->oct[g.im->oct0 + oct];
-  g.dsrc = nullptr;
-  g.dpitch = 0;
-  if (oct > 0) {
-    const OctDev op = d->oct[g.im->oct0 + oct - 1];
-    g.dsrc = d->pyr + op.lvl + (long long)d->n_scales * op.lstride;
-    g.dpitch = op.pitch;
+  const ImgDev &im = d->img[b];
+  const OctDev od = d->oct[im.oct0 + oct];
+  g.pitch = od.pitch;
+  g.H = od.H;
+  g.W = od.W;
+  float *lv = d->pyr + od.lvl;
+  g.out0 = lv;
+  g.out = lv + (long long)lvl_out * od.lstride;
+  g.sh = im.H;
+  g.sw = im.W;
+  if (MODE == 0) {
+    g.src = lv + (long long)(lvl_out - 1) * od.lstride;
+    g.spitch = od.pitch;
+    g.vec = 1;
+  } else if (MODE == 3) {
+    const OctDev op = d->oct[im.oct0 + oct - 1];
+    g.src = d->pyr + op.lvl + (long long)d->n_scales * op.lstride;
+    g.spitch = op.pitch;
+    g.vec = 0;
+  } else {
+    g.src = im.src;
+    g.spitch = im.spitch;
+    g.vec = im.src_vec_ok;
   }
-  const int tiles_x = (g.od.W + kBlurTW - 1) / kBlurTW;
+  const int tiles_x = (od.W + kBlurTW - 1) / kBlurTW;
   const int lt = t - pre[b];
   const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
   g.x0 = tx * kBlurTW;
@@ -298,70 +377,53 @@ __device__ __forceinline__ void store_level0(const float *s_in, float *out0, int
   }
 }
 
-// MODE 0, 1 and 3 double-buffer the staging: the copies of the block's next
-// tile are in flight while the current tile is computed.
 template <int R, int TH, int MODE>
-__device__ __forceinline__ void issue_stage(const Desc *__restrict__ d, const TileGeo &g,
-                                            int lvl_out, float *dst) {
+__device__ __forceinline__ void issue_stage(const TileGeo &g, float *dst) {
   constexpr int ROWS = TH + 2 * R;
-  if (MODE == 0) {
-    const float *src = d->pyr + g.od.lvl + (long long)(lvl_out - 1) * g.od.lstride;
-    stage_plain_issue(src, g.od.pitch, g.od.H, g.od.W, true, g.x0, g.y0, R, ROWS, dst);
-  } else if (MODE == 3) {
-    stage_decim_issue(g.dsrc, g.dpitch, g.od.H, g.od.W, g.x0, g.y0, R, ROWS, dst);
-  } else {
-    stage_plain_issue(g.im->src, g.im->spitch, g.od.H, g.od.W, g.im->src_vec_ok != 0, g.x0, g.y0,
-                      R, ROWS, dst);
-  }
-  cp_async_commit();
+  if (MODE == 3)
+    stage_decim_issue(g.src, g.spitch, g.H, g.W, g.x0, g.y0, R, ROWS, dst);
+  else
+    stage_plain_issue(g.src, g.spitch, g.H, g.W, g.vec != 0, g.x0, g.y0, R, ROWS, dst);
 }
 
 // The block's tiles are t0, t0 + grid, t0 + 2 grid, ...; thread 0 resolves the
-// geometry of tile i + 2 while tile i is computed and publishes it through the
-// barrier that ends the iteration (a ring of 4 slots), so no other thread does
-// the image search or reads the descriptor per tile.
+// geometry of the next tile while the current one is computed and publishes it
+// through the barrier that ends the iteration, so no other thread does the
+// image search or reads the descriptor per tile. The staging buffer is single:
+// copy/compute overlap comes from the other blocks resident on the SM (three
+// or four per SM for the default radii), which measured faster than double
+// buffering with fewer blocks.
 template <int R, int TH, int MODE>
 __global__ void __launch_bounds__(kThreads) k_blur(const Desc *__restrict__ d, int oct, int lvl_out,
                                                    BlurTaps tp) {
   constexpr int ROWS = TH + 2 * R;
-  constexpr bool kPipe = MODE != 2;
   extern __shared__ float4 smem4[];
-  __shared__ TileGeo geo[4];
-  float *buf0 = reinterpret_cast<float *>(smem4);
-  float *buf1 = buf0 + ROWS * kSinW;
-  float *s_v = kPipe ? buf1 + ROWS * kSinW : buf1;
+  __shared__ TileGeo geo[2];
+  float *s_in = reinterpret_cast<float *>(smem4);
+  float *s_v = s_in + ROWS * kSinW;
   const int n = d->n_img;
   const int *pre = d->tile_pre[KindOf<TH>::v][oct];
   const int total = pre[n];
   const int t0 = blockIdx.x, G = gridDim.x;
   if (t0 >= total) return;
-  if (threadIdx.x == 0) {
-    geo[0] = tile_geo<TH>(d, pre, n, oct, t0);
-    if (t0 + G < total) geo[1] = tile_geo<TH>(d, pre, n, oct, t0 + G);
-  }
+  if (threadIdx.x == 0) geo[0] = tile_geo<TH, MODE>(d, pre, n, oct, lvl_out, t0);
   __syncthreads();
-  if (kPipe) issue_stage<R, TH, MODE>(d, geo[0], lvl_out, buf0);
   for (int k = 0, t = t0; t < total; t += G, k++) {
-    const TileGeo g = geo[k & 3];
-    float *cur = (kPipe && (k & 1)) ? buf1 : buf0;
-    if (kPipe) {
-      if (t + G < total) {
-        issue_stage<R, TH, MODE>(d, geo[(k + 1) & 3], lvl_out, (k & 1) ? buf0 : buf1);
-        cp_async_wait<1>();
-      } else {
-        cp_async_wait<0>();
-      }
-    } else if (!stage_upsampled_fast<R, TH>(g.im->src, g.im->spitch, g.im->H, g.im->W,
-                                             g.im->src_vec_ok != 0, g.x0, g.y0, cur, s_v)) {
-      stage_upsampled(g.im->src, g.im->spitch, g.im->H, g.im->W, g.x0, g.y0, R, ROWS, cur);
+    const TileGeo &g = geo[k & 1];
+    if (MODE != 2) {
+      issue_stage<R, TH, MODE>(g, s_in);
+      cp_async_wait_all();
+    } else if (!stage_upsampled_fast<R, TH>(g.src, g.spitch, g.sh, g.sw, g.vec != 0, g.x0, g.y0,
+                                             s_in, s_v)) {
+      stage_upsampled(g.src, g.spitch, g.sh, g.sw, g.x0, g.y0, R, ROWS, s_in);
     }
     __syncthreads();
-    if (MODE == 3) store_level0<R, TH>(cur, d->pyr + g.od.lvl, g.od.pitch, g.od.H, g.x0, g.y0);
-    col_pass<R, TH>(cur, s_v, tp);
+    if (MODE == 3) store_level0<R, TH>(s_in, g.out0, g.pitch, g.H, g.x0, g.y0);
+    col_pass<R, TH>(s_in, s_v, tp);
     __syncthreads();
-    float *out = d->pyr + g.od.lvl + (long long)lvl_out * g.od.lstride;
-    row_pass_store<R, TH>(s_v, out, g.od.pitch, g.od.H, g.x0, g.y0, tp);
-    if (threadIdx.x == 0 && t + 2 * G < total) geo[(k + 2) & 3] = tile_geo<TH>(d, pre, n, oct, t + 2 * G);
+    row_pass_store<R, TH>(s_v, g.out, g.pitch, g.H, g.x0, g.y0, tp);
+    if (threadIdx.x == 0 && t + G < total)
+      geo[(k + 1) & 1] = tile_geo<TH, MODE>(d, pre, n, oct, lvl_out, t + G);
     __syncthreads();
   }
 }
@@ -419,49 +481,25 @@ __global__ void __launch_bounds__(kThreads) k_blur_generic(const Desc *__restric
     for (int idx = threadIdx.x; idx < TH * kBlurTW; idx += kThreads) {
       const int v = idx / kBlurTW, k = idx - v * kBlurTW;
       const int y = y0 + v, x = x0 + k;
-      const float *row = s_v + v * kSinW + kBlurHalo + k - R;
-      float acc = tp.w[0] * row[0];
-      for (int i = 1; i <= 2 * R; i++) acc = fmaf(tp.w[i], row[i], acc);
+      const int sc = kBlurHalo + k - R;  // first tap column; its parity is that of x - R
+      const float acc = row_tap_sum(s_v + v * kSinW + sc, (sc & 1) != 0, R, tp.w);
       if (y < od.H && x < od.pitch) out[(long long)y * od.pitch + x] = acc;
     }
     __syncthreads();
   }
 }
 
-// Octave o > 0, level 0: every second sample of level S of octave o - 1.
-__global__ void __launch_bounds__(256) k_decimate(const Desc *__restrict__ d, int oct) {
-  const int n = d->n_img;
-  const int *pre = d->tile_pre[TK_BLUR32][oct];
-  const int total = pre[n];
-  const int S = d->n_scales;
-  for (int t = blockIdx.x; t < total; t += gridDim.x) {
-    const int b = find_owner(pre, n, t);
-    const ImgDev &im = d->img[b];
-    const OctDev od = d->oct[im.oct0 + oct];
-    const OctDev op = d->oct[im.oct0 + oct - 1];
-    const int tiles_x = (od.W + kBlurTW - 1) / kBlurTW;
-    const int lt = t - pre[b];
-    const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
-    const float *src = d->pyr + op.lvl + (long long)S * op.lstride;
-    float *dst = d->pyr + od.lvl;
-    for (int idx = threadIdx.x; idx < kBlurTW * 32; idx += 256) {
-      const int y = ty * 32 + idx / kBlurTW, x = tx * kBlurTW + (idx % kBlurTW);
-      if (y < od.H && x < od.W) dst[(long long)y * od.pitch + x] = src[(long long)(2 * y) * op.pitch + 2 * x];
-    }
-  }
-}
-
-// Shared memory: two staging buffers (one for the upsampling mode) plus the
-// column-pass output.
+// Shared memory: the staging buffer plus the column-pass output.
 template <int R, int TH, int MODE> constexpr int smem_bytes() {
-  return ((MODE == 2 ? 1 : 2) * (TH + 2 * R) + TH) * kSinW * (int)sizeof(float);
+  return ((TH + 2 * R) + TH) * kSinW * (int)sizeof(float);
 }
 
 int th_of_kind(int kind) { return kind == TK_BLUR64 ? 64 : 32; }
 
 int blur_smem_bytes_mode(int R, int th_kind, int mode) {
   const int th = th_of_kind(th_kind);
-  return ((mode == 2 ? 1 : 2) * (th + 2 * R) + th) * kSinW * (int)sizeof(float);
+  (void)mode;
+  return ((th + 2 * R) + th) * kSinW * (int)sizeof(float);
 }
 
 int generic_smem_bytes(int R) { return (2 * 32 + 2 * R) * kSinW * (int)sizeof(float); }
@@ -556,11 +594,6 @@ int blur_blocks_per_sm(int R, int th_kind, int mode) {
 #undef CASE_R
 #undef OCC
   return (e == cudaSuccess && nb > 0) ? nb : 1;
-}
-
-cudaError_t launch_decimate(const Desc *d, int oct, int grid, cudaStream_t s) {
-  k_decimate<<<grid, 256, 0, s>>>(d, oct);
-  return cudaGetLastError();
 }
 
 }  // namespace sift

@@ -107,8 +107,13 @@ struct Desc {
   OctDev oct[kMaxImg * kMaxOct];
 };
 
+// Normalised taps w[0..2R] of one blur, plus the pairs the packed FMAs take
+// as operands (prepared on the host so each is one aligned 8-byte constant).
 struct BlurTaps {
-  float w[2 * kMaxR + 1];
+  float w[2 * kMaxR + 2];     // zero past 2R
+  float2 wp[kMaxR + 1];       // (w[2i], w[2i + 1])
+  float2 wq[kMaxR + 1];       // (w[2i + 1], w[2i + 2])
+  float2 wd[2 * kMaxR + 1];   // (w[j], w[j])
 };
 
 // Index of the image owning flattened item t, given an exclusive prefix pre[0..n].
@@ -135,7 +140,6 @@ cudaError_t launch_base_blur(const Desc *d, int R, const BlurTaps &t, int th_kin
                              int grid, cudaStream_t s);
 cudaError_t launch_level_blur(const Desc *d, int oct, int lvl_out, int R, const BlurTaps &t,
                               int th_kind, int grid, cudaStream_t s, bool from_prev_octave = false);
-cudaError_t launch_decimate(const Desc *d, int oct, int grid, cudaStream_t s);
 int blur_smem_bytes(int R, int th_kind);
 int blur_blocks_per_sm(int R, int th_kind, int mode);
 cudaError_t blur_set_attributes();
