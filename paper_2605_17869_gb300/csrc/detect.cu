@@ -48,8 +48,7 @@ __global__ void __launch_bounds__(kThreads) k_extrema(const Desc *__restrict__ d
   const int nds = jn / 9 - 1, ndy = (jn / 3) % 3 - 1, ndx = jn % 3 - 1;
   for (int t = blockIdx.x * WPB + (threadIdx.x >> 5); t < total; t += gridDim.x * WPB) {
     const int b = find_owner(pre, n, t);
-    const ImgDev &im = d->img[b];
-    const OctDev od = d->oct[im.oct0 + oct];
+    const OctDev od = d->oct[b * kMaxOct + oct];  // image b's octaves sit at fixed slots
     const int H = od.H, W = od.W, pitch = od.pitch;
     const int lt = t - pre[b];
     const int ty = lt / od.wpr, tx = lt - ty * od.wpr;

@@ -230,7 +230,7 @@ sift_status Engine::fill_plan(int n, const ImgIn *in, Desc &hd, WsLayout &L, int
   hd.rootsift = P_.rootsift ? 1 : 0;
   hd.ori_peak_ratio = P_.ori_peak_ratio;
   size_t pyr = 0, bm = 0, cand = 0, ori = 0, fin = 0;
-  int bmc = 0, cc = 0, oc = 0, M = 0;
+  int bmc = 0, cc = 0, M = 0;
   for (int b = 0; b < n; b++) {
     ImgDev &d = hd.img[b];
     std::memset(&d, 0, sizeof(d));
@@ -243,12 +243,12 @@ sift_status Engine::fill_plan(int n, const ImgIn *in, Desc &hd, WsLayout &L, int
     const int no = octave_sizes(in[b].H, in[b].W, hs, ws);
     if (no == 0) return SIFT_E_INVALID;
     d.n_oct = no;
-    d.oct0 = oc;
+    d.oct0 = b * kMaxOct;  // fixed slot: kernels locate an octave without reading ImgDev
     M = std::max(M, no);
     d.bm_begin = (long long)bm;
     long long px = 0;
     for (int o = 0; o < no; o++) {
-      OctDev &od = hd.oct[oc + o];
+      OctDev &od = hd.oct[d.oct0 + o];
       od.H = hs[o];
       od.W = ws[o];
       od.pitch = (int)align_up(ws[o], 32);
@@ -285,7 +285,6 @@ sift_status Engine::fill_plan(int n, const ImgIn *in, Desc &hd, WsLayout &L, int
     d.olay = in[b].k.layer;
     d.odesc = in[b].desc;
     d.ocount = in[b].count;
-    oc += no;
   }
   hd.n_oct_max = M;
   hd.n_bm_chunks = bmc;
@@ -552,9 +551,8 @@ sift_status Engine::run(int n, const ImgIn *imgs, cudaStream_t s) {
   hd->cnt = reinterpret_cast<ImgCounters *>(ws_ + lay.cnt);
   hd->cand_flat = reinterpret_cast<int *>(ws_ + lay.cand_flat);
   hd->fin_flat = reinterpret_cast<int *>(ws_ + lay.fin_flat);
-  int n_oct_total = 0;
-  for (int b = 0; b < n; b++) n_oct_total += hd->img[b].n_oct;
-  const size_t bytes = offsetof(Desc, oct) + (size_t)n_oct_total * sizeof(OctDev);
+  const size_t bytes =
+      offsetof(Desc, oct) + (size_t)(hd->img[n - 1].oct0 + hd->img[n - 1].n_oct) * sizeof(OctDev);
   cudaGraphExec_t exec = nullptr;
   st = get_graph(M, &exec);
   if (st != SIFT_OK) return st;

@@ -310,33 +310,37 @@ struct TileGeo {
   int x0, y0;
 };
 
+// Geometry of flattened tile t. Image b's octaves sit at fixed slots
+// oct[b * kMaxOct + o], so no ImgDev read is needed for pyramid levels.
 template <int TH, int MODE>
-__device__ __forceinline__ TileGeo tile_geo(const Desc *__restrict__ d, const int *pre, int n,
-                                            int oct, int lvl_out, int t) {
+__device__ __forceinline__ TileGeo tile_geo(const Desc *__restrict__ d, const int *pre, int oct,
+                                            int lvl_out, int t) {
   TileGeo g;
-  const int b = find_owner(pre, n, t);
-  const ImgDev &im = d->img[b];
-  const OctDev od = d->oct[im.oct0 + oct];
+  const int b = find_owner(pre, d->n_img, t);
+  const OctDev od = d->oct[b * kMaxOct + oct];
   g.pitch = od.pitch;
   g.H = od.H;
   g.W = od.W;
   float *lv = d->pyr + od.lvl;
   g.out0 = lv;
   g.out = lv + (long long)lvl_out * od.lstride;
-  g.sh = im.H;
-  g.sw = im.W;
+  g.sh = 0;
+  g.sw = 0;
   if (MODE == 0) {
     g.src = lv + (long long)(lvl_out - 1) * od.lstride;
     g.spitch = od.pitch;
     g.vec = 1;
   } else if (MODE == 3) {
-    const OctDev op = d->oct[im.oct0 + oct - 1];
+    const OctDev op = d->oct[b * kMaxOct + oct - 1];
     g.src = d->pyr + op.lvl + (long long)d->n_scales * op.lstride;
     g.spitch = op.pitch;
     g.vec = 0;
   } else {
+    const ImgDev &im = d->img[b];
     g.src = im.src;
     g.spitch = im.spitch;
+    g.sh = im.H;
+    g.sw = im.W;
     g.vec = im.src_vec_ok;
   }
   const int tiles_x = (od.W + kBlurTW - 1) / kBlurTW;
@@ -401,12 +405,11 @@ __global__ void __launch_bounds__(kThreads) k_blur(const Desc *__restrict__ d, i
   __shared__ TileGeo geo[2];
   float *s_in = reinterpret_cast<float *>(smem4);
   float *s_v = s_in + ROWS * kSinW;
-  const int n = d->n_img;
   const int *pre = d->tile_pre[KindOf<TH>::v][oct];
-  const int total = pre[n];
+  const int total = pre[d->n_img];
   const int t0 = blockIdx.x, G = gridDim.x;
   if (t0 >= total) return;
-  if (threadIdx.x == 0) geo[0] = tile_geo<TH, MODE>(d, pre, n, oct, lvl_out, t0);
+  if (threadIdx.x == 0) geo[0] = tile_geo<TH, MODE>(d, pre, oct, lvl_out, t0);
   __syncthreads();
   for (int k = 0, t = t0; t < total; t += G, k++) {
     const TileGeo &g = geo[k & 1];
@@ -423,7 +426,7 @@ __global__ void __launch_bounds__(kThreads) k_blur(const Desc *__restrict__ d, i
     __syncthreads();
     row_pass_store<R, TH>(s_v, g.out, g.pitch, g.H, g.x0, g.y0, tp);
     if (threadIdx.x == 0 && t + G < total)
-      geo[(k + 1) & 1] = tile_geo<TH, MODE>(d, pre, n, oct, lvl_out, t + G);
+      geo[(k + 1) & 1] = tile_geo<TH, MODE>(d, pre, oct, lvl_out, t + G);
     __syncthreads();
   }
 }
