@@ -33,7 +33,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from workloads import synth  # noqa: E402
+from workloads import matching, synth  # noqa: E402
 
 METRIC = "SIFT Mpix/s and keypoints/s, batched vs per-image; serving p50/p99 latency"
 WORKLOAD = ("homography-sequence batch: 6 x 1000x750 FP32 grayscale (seeded base + 5 "
@@ -160,6 +160,31 @@ def _alg_blur_bytes(shapes, upsample, S=3, min_side=16):
     return tot, px_tot
 
 
+# ------------------------------------------------------------ replicas
+# Multi-GPU runs are independent replicas: rank r extracts its own batch (the
+# homography sequence with seed index r); the only communication is a barrier
+# and the max of the timed-region durations.
+
+def replica_batch(rank, n_images):
+    """The images rank `rank` processes (distinct per rank)."""
+    return synth.homography_sequence(index=rank, n_warped=n_images - 1)
+
+
+def max_over_ranks(x, device):
+    """Max of a per-rank float over the process group (then a barrier)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def whole_job_value(world, mpix_per_rank, steps, max_ms):
+    """Whole-job throughput: the pixels all ranks processed / the slowest rank's time."""
+    return world * mpix_per_rank * steps / (max_ms / 1e3)
+
+
 def timed_steps(torch, fn, steps, warmup, flush, stream):
     for _ in range(warmup):
         fn()
@@ -227,7 +252,7 @@ def gpu_arm(args, rank, world, pool, n_workers):
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
-    seq = synth.homography_sequence(index=rank, n_warped=args.images - 1)
+    seq = replica_batch(rank, args.images)
     imgs_np = seq.images
     shapes = [im.shape for im in imgs_np]
     imgs = _device_images(imgs_np, torch)
@@ -262,15 +287,17 @@ def gpu_arm(args, rank, world, pool, n_workers):
     clock_info = clocks.stop()
     counts = ex._counts[:len(imgs)].tolist()
     kpts = sum(counts)
+    accuracy = None
+    if rank == 0:
+        feats = [ex._bufs[i].view(counts[i]) for i in range(len(imgs))]
+        accuracy = {"what": "image 0 matched to each warped image of the timed batch; MMA against "
+                            "the known homographies (harness: torch mutual NN + ratio 0.8)",
+                    **matching.sequence_mma(feats, seq.homographies)}
     launches_per_step = ex.launch_count()
     total_ms = sum(times)
     if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        dist.barrier()
-    value = world * mpix * args.steps / (total_ms / 1e3)
+        total_ms = max_over_ranks(total_ms, "cuda")
+    value = whole_job_value(world, mpix, args.steps, total_ms)
 
     # Per-image path on the same images.
     def step_single():
@@ -373,6 +400,12 @@ def gpu_arm(args, rank, world, pool, n_workers):
         mixed["batched_vs_per_image"] = round(mixed["batched_mpix_s"] / mixed["per_image_mpix_s"], 2)
         exm.close()
 
+    configs = None
+    if rank == 0 and not args.no_configs:
+        configs = other_configs(torch, pkg, flush, stream, tuning)
+        configs["dsp_rootsift"] = dsp_variant(torch, pkg, imgs, mpix, flush, stream, tuning,
+                                              seq, max(10, args.steps // 4))
+
     serving = None
     if rank == 0 and not args.no_serving:
         serving = serving_bench(torch, pkg, (50, 200, 1000, 2000), 200)
@@ -398,10 +431,68 @@ def gpu_arm(args, rank, world, pool, n_workers):
         "roofline": roofline,
         "e2e": e2e,
         "clocks": clock_info,
+        "accuracy": accuracy,
         "mixed_batch": mixed,
+        "single_and_pair": configs,
         "serving": serving,
     }
     return res, imgs_np
+
+
+def dsp_variant(torch, pkg, imgs, mpix, flush, stream, tuning, seq, steps):
+    """The timed batch again with DSP pooling and RootSIFT (§3.2): throughput,
+    per-class device time and matching accuracy."""
+    ex = pkg.Extractor(upsample=1, max_kpts=8000, dsp=1, rootsift=1)
+    ex.set_tuning(tuning)
+    t, _ = timed_steps(torch, lambda: ex.extract_batch_async(imgs, stream), steps, 3, flush, stream)
+    counts = ex._counts[:len(imgs)].tolist()
+    feats = [ex._bufs[i].view(counts[i]) for i in range(len(imgs))]
+    acc = matching.sequence_mma(feats, seq.homographies)
+    ex.set_profiling(True)
+    ex.extract_batch_async(imgs, stream)
+    torch.cuda.synchronize()
+    acc_t = {}
+    for _ in range(3):
+        flush.zero_()
+        ex.extract_batch_async(imgs, stream)
+        for k, (ms, n) in ex.kernel_times().items():
+            acc_t[k] = acc_t.get(k, 0.0) + ms / 3
+    ex.close()
+    return {"workload": "the timed batch with dsp=1, rootsift=1",
+            "ms_per_step": round(statistics.mean(t), 4),
+            "mpix_s": round(mpix * len(t) / (sum(t) / 1e3), 1),
+            "keypoints_per_s": round(sum(counts) * len(t) / (sum(t) / 1e3), 1),
+            "kernel_ms_per_step": {k: round(v, 4) for k, v in acc_t.items()},
+            "matches": acc["matches"], **{k: v for k, v in acc.items() if k.startswith("mma@")}}
+
+
+def other_configs(torch, pkg, flush, stream, tuning):
+    """Latency of the single-image and wide-baseline-pair workloads (device
+    time per call, warm, L2 flushed before each), with MMA for the pair."""
+    out = {}
+    vga = _device_images([synth.single_vga(0)], torch)
+    ex0 = pkg.Extractor(upsample=0)
+    t0, _ = timed_steps(torch, lambda: ex0.extract_async(vga[0], stream), 20, 3, flush, stream)
+    n0 = int(ex0._counts[0].item())
+    out["single_vga"] = {"workload": "one 640x480 image, plain SIFT, no upsampling",
+                         "ms_per_image": round(statistics.median(t0), 4), "keypoints": n0}
+    ex0.close()
+    seq = synth.wide_baseline_pair(0)
+    pair = _device_images(seq.images, torch)
+    ex2 = pkg.Extractor(upsample=1, max_kpts=8192)
+    ex2.set_tuning(tuning)
+    t2, _ = timed_steps(torch, lambda: ex2.extract_batch_async(pair, stream), 10, 3, flush, stream)
+    c2 = ex2._counts[:2].tolist()
+    feats = [ex2._bufs[i].view(c2[i]) for i in range(2)]
+    acc = matching.sequence_mma(feats, seq.homographies)
+    out["pair"] = {"workload": "two 1600x1200 images (textured base + homography warp with "
+                               "N(0, 0.02) noise), 2x upsampled, cap 8192, one batched call",
+                   "ms_per_pair": round(statistics.median(t2), 4),
+                   "pairs_per_s": round(1e3 / statistics.median(t2), 1), "keypoints": c2,
+                   "matches": acc["matches"],
+                   **{k: v for k, v in acc.items() if k.startswith("mma@")}}
+    ex2.close()
+    return out
 
 
 def _mixed_one(i):
@@ -472,6 +563,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the single-image and image-pair latency runs")
     ap.add_argument("--minimal", action="store_true",
                     help="only the timed batch loop (for profiler launch lists)")
     ap.add_argument("--images", type=int, default=6, help="images per batch (default 6)")

@@ -75,7 +75,9 @@ typedef struct {
   float ori_peak_ratio;  /* orientation peaks >= ratio * histogram maximum */
   int max_kpts;          /* output capacity and top-K cap (by response); > 0 */
   int upright;           /* 1: orientation fixed to 0, one keypoint per extremum */
-  int dsp;               /* reserved (DSP-SIFT pooling, §3.2); must be 0 */
+  int dsp;               /* 1: DSP-SIFT pooling (§3.2): histograms of 5 relative
+                            scales {1/2, 1/sqrt2, 1, sqrt2, 2}, each a 32 x 32
+                            sample patch, pooled before normalisation */
   int rootsift;          /* 1: RootSIFT epilogue (L1 normalise, square root, §3.2) */
 } sift_params;
 
@@ -191,11 +193,13 @@ sift_status sift_kernel_times(sift_handle *h, double *ms, int *launches, int n_c
  * graph replay). Host-only: no synchronisation. */
 sift_status sift_last_launch_count(sift_handle *h, int *kernels);
 
-/* Autotuner: time the blur and extrema kernels' tile shapes on a synthetic
- * H x W workload on `stream` and keep the fastest. Tile shapes change only how
- * work is distributed, never the arithmetic of any output, so tuned and
- * untuned runs give bit-identical results. The choice can be saved and
- * restored as a short JSON string. */
+/* Autotuner: for each level blur of octave 0, time the two tile heights (32
+ * and 64 rows) on a synthetic H x W workload on `stream` and keep the faster;
+ * octaves above 0 always use 32-row tiles, which give their few tiles more
+ * parallelism. Tile shapes change only how work is distributed, never the
+ * arithmetic of any output, so tuned and untuned runs give bit-identical
+ * results. The choice can be saved and restored as a short JSON string,
+ * {"blur_tile_rows": [r1, ..., rS+2]} with each r 32 or 64. */
 sift_status sift_autotune(sift_handle *h, int H, int W, void *stream);
 sift_status sift_get_tuning(sift_handle *h, char *json, size_t len);
 sift_status sift_set_tuning(sift_handle *h, const char *json);

@@ -10,9 +10,10 @@ Gaussian scale space built by separable blurs with 4-sigma truncation, DoG
 subtraction, 26-neighbour extrema with a contrast gate, sub-pixel refinement of
 the 3-D Taylor expansion solved by Cramer's rule with up to five iterations and
 Hessian edge rejection, 36-bin orientation histograms smoothed with
-[1/4, 1/2, 1/4] and refined by a parabola, and 4x4x8 gradient descriptors
-(§3.2 "DSP Multi-Scale Descriptor Pooling" describes the descriptor; its plain
-single-scale form is used here, with the 0.2 clip and renormalisation). Where the
+[1/4, 1/2, 1/4] and refined by a parabola, and 4x4x8 gradient descriptors with
+the 0.2 clip and renormalisation: by default the plain single-scale form, and
+optionally the DSP multi-scale pooling and RootSIFT normalisation of §3.2
+("DSP Multi-Scale Descriptor Pooling", "RootSIFT Normalization"). Where the
 paper is silent the textbook SIFT definition (Lowe, IJCV 2004, the method the
 paper builds on, §1) is used; every such reading is marked READING below.
 
@@ -21,9 +22,9 @@ definition reads: no blocking, fusion or reordering beyond it.
 
 Parity status per function:
   gaussian_taps, blur, upsample2x, decimate, build_pyramid, dog,
-  find_candidates, refine_candidate, orientation_peaks, descriptor,
-  cap_topk : pinned by tests/test_oracle_pins.py (closed forms, brute force,
-  invariants, rotation / transpose equivariance).
+  find_candidates, refine_candidate, orientation_peaks, descriptor (plain,
+  DSP and RootSIFT), bilinear, cap_topk : pinned by tests/test_oracle_pins.py
+  (closed forms, brute force, invariants, rotation / transpose equivariance).
   extract (end-to-end composition): parity unpinned as an absolute result,
   since the paper prints no worked example; its parts are pinned above.
 """
@@ -59,6 +60,10 @@ class Params:
     desc_clip: float = 0.2
     max_kpts: int = 0            # 0 = no cap
     upright: bool = False        # orientation fixed to 0 (no histogram)
+    dsp: bool = False            # §3.2 DSP multi-scale descriptor pooling
+    dsp_scales: tuple = (0.5, 2 ** -0.5, 1.0, 2 ** 0.5, 2.0)  # §3.2: 5 relative scales
+    dsp_grid: int = 32           # §3.2: a 32 x 32 sample patch per DSP scale
+    rootsift: bool = False       # §3.2 RootSIFT: L1 normalise, then element-wise sqrt
 
 
 # ------------------------------------------------------------------ A2/A3: blur
@@ -446,17 +451,41 @@ def orientation_peaks(hist_s: np.ndarray, p: Params):
 
 # ------------------------------------------------------------- A8: descriptor
 
-def descriptor(L: np.ndarray, xk: float, yk: float, xi: int, yi: int, sigma_oct: float,
-               angle_deg: float, p: Params) -> np.ndarray:
-    """4x4x8 gradient descriptor (§3.2), layout [v][u][o] row-major.
+def _trilinear_histogram(u, v, o, wt, p: Params) -> np.ndarray:
+    """Accumulate samples at continuous bin coordinates (v, u, o) with weights
+    wt into the d x d x nb histogram, each split over its 2 x 2 x 2 nearest
+    bins (o circular; spatial bins outside 0..d-1 are dropped)."""
+    d, nb = p.desc_width, p.desc_bins
+    u0 = np.floor(u).astype(np.int64)
+    v0 = np.floor(v).astype(np.int64)
+    o0 = np.floor(o).astype(np.int64)
+    fu, fv, fo = u - u0, v - v0, o - o0
+    hist = np.zeros((d, d, nb))
+    for dv in (0, 1):
+        wv = fv if dv else 1 - fv
+        vv = v0 + dv
+        for du in (0, 1):
+            wu = fu if du else 1 - fu
+            uu = u0 + du
+            inb = (vv >= 0) & (vv < d) & (uu >= 0) & (uu < d)
+            for do in (0, 1):
+                wo = fo if do else 1 - fo
+                oo = (o0 + do) % nb
+                np.add.at(hist, (vv[inb], uu[inb], oo[inb]), (wt * wv * wu * wo)[inb])
+    return hist
+
+
+def plain_histogram(L: np.ndarray, xk: float, yk: float, xi: int, yi: int, sigma_oct: float,
+                    angle_deg: float, p: Params) -> np.ndarray:
+    """Raw (unnormalised) 4x4x8 gradient histogram of the single-scale
+    descriptor (§3.2), on the pixel grid.
 
     READING (textbook SIFT): spatial bin width w = desc_scale * sigma; samples are
     the pixels within Chebyshev radius round(w * sqrt(2) * (d + 1) / 2) of the
     integer keypoint pixel; offsets from the sub-pixel keypoint are rotated by
     -theta and divided by w, giving bin coordinates (u, v) = (rx, ry) + d/2 - 1/2,
     kept when -1 < u, v < d; weight m * exp(-(rx^2 + ry^2) / (2 (d/2)^2));
-    trilinear split over (v, u, o) with o circular. Then L2 normalise, clip at
-    0.2, L2 renormalise (zero vector if the norm is 0).
+    trilinear split over (v, u, o) with o circular.
     """
     h, w = L.shape
     d, nb = p.desc_width, p.desc_bins
@@ -482,29 +511,85 @@ def descriptor(L: np.ndarray, xk: float, yk: float, xi: int, yi: int, sigma_oct:
     phi = np.mod(phi, 2 * math.pi)
     o = phi * nb / (2 * math.pi)
     wt = mag * np.exp(-(rx * rx + ry * ry) / (2.0 * (0.5 * d) ** 2))
-    u0 = np.floor(u).astype(np.int64)
-    v0 = np.floor(v).astype(np.int64)
-    o0 = np.floor(o).astype(np.int64)
-    fu, fv, fo = u - u0, v - v0, o - o0
-    hist = np.zeros((d, d, nb))
-    for dv in (0, 1):
-        wv = fv if dv else 1 - fv
-        vv = v0 + dv
-        for du in (0, 1):
-            wu = fu if du else 1 - fu
-            uu = u0 + du
-            inb = (vv >= 0) & (vv < d) & (uu >= 0) & (uu < d)
-            for do in (0, 1):
-                wo = fo if do else 1 - fo
-                oo = (o0 + do) % nb
-                np.add.at(hist, (vv[inb], uu[inb], oo[inb]), (wt * wv * wu * wo)[inb])
-    vec = hist.ravel()
+    return _trilinear_histogram(u, v, o, wt, p)
+
+
+def bilinear(L: np.ndarray, x: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """Bilinear interpolation of L at continuous positions (x, y), which must
+    satisfy 0 <= x < W - 1 and 0 <= y < H - 1."""
+    x0 = np.floor(x).astype(np.int64)
+    y0 = np.floor(y).astype(np.int64)
+    fx, fy = x - x0, y - y0
+    top = (1 - fx) * L[y0, x0] + fx * L[y0, x0 + 1]
+    bot = (1 - fx) * L[y0 + 1, x0] + fx * L[y0 + 1, x0 + 1]
+    return (1 - fy) * top + fy * bot
+
+
+def dsp_scale_histogram(L: np.ndarray, xk: float, yk: float, sigma_oct: float,
+                        angle_deg: float, scale: float, p: Params) -> np.ndarray:
+    """Raw 4x4x8 histogram of one DSP scale (§3.2 "DSP Multi-Scale Descriptor
+    Pooling": a 32 x 32 patch per scale).
+
+    READING: the patch is a G x G grid (G = dsp_grid) of samples covering the
+    descriptor's d x d spatial bins of width w = desc_scale * sigma * scale,
+    G / d samples per bin along each axis, at bin coordinates
+    (rx, ry) = ((a + 1/2) d / G - d/2, (b + 1/2) d / G - d/2) from the keypoint
+    in its rotated frame; image position (x, y) = (xk, yk) + w R(theta) (rx, ry).
+    The gradient there is the central difference of the bilinearly
+    interpolated level, dx = L(x+1, y) - L(x-1, y), dy = L(x, y+1) - L(x, y-1);
+    samples whose stencil leaves the image (unless 1 <= x < W-2 and
+    1 <= y < H-2) are skipped. Weight, orientation bin and the trilinear split
+    are those of the single-scale descriptor with (u, v) = (rx, ry) + d/2 - 1/2.
+    """
+    h, w = L.shape
+    d, nb, G = p.desc_width, p.desc_bins, p.dsp_grid
+    wbin = p.desc_scale * sigma_oct * scale
+    th = math.radians(angle_deg)
+    ct, st = math.cos(th), math.sin(th)
+    c = (np.arange(G) + 0.5) * d / G - 0.5 * d
+    ry, rx = np.meshgrid(c, c, indexing="ij")
+    rx, ry = rx.ravel(), ry.ravel()
+    x = xk + wbin * (ct * rx - st * ry)
+    y = yk + wbin * (st * rx + ct * ry)
+    ok = (x >= 1) & (x < w - 2) & (y >= 1) & (y < h - 2)
+    x, y, rx, ry = x[ok], y[ok], rx[ok], ry[ok]
+    dx = bilinear(L, x + 1, y) - bilinear(L, x - 1, y)
+    dy = bilinear(L, x, y + 1) - bilinear(L, x, y - 1)
+    mag = np.sqrt(dx * dx + dy * dy)
+    phi = np.mod(np.arctan2(dy, dx) - th, 2 * math.pi)
+    o = phi * nb / (2 * math.pi)
+    wt = mag * np.exp(-(rx * rx + ry * ry) / (2.0 * (0.5 * d) ** 2))
+    return _trilinear_histogram(rx + 0.5 * d - 0.5, ry + 0.5 * d - 0.5, o, wt, p)
+
+
+def normalise_descriptor(hist: np.ndarray, p: Params) -> np.ndarray:
+    """L2 normalise, clip at desc_clip, L2 renormalise (zero vector if the
+    norm is 0); with rootsift (§3.2 "RootSIFT Normalization"), then divide by
+    the L1 norm and take element-wise square roots."""
+    vec = hist.ravel().astype(np.float64)
     nrm = math.sqrt(float(vec @ vec))
     if nrm == 0:
-        return np.zeros(d * d * nb)
+        return np.zeros(vec.size)
     vec = np.minimum(vec / nrm, p.desc_clip)
     nrm = math.sqrt(float(vec @ vec))
-    return vec / nrm if nrm > 0 else vec
+    vec = vec / nrm if nrm > 0 else vec
+    if p.rootsift:
+        l1 = float(np.sum(np.abs(vec)))
+        vec = np.sqrt(vec / l1) if l1 > 0 else vec
+    return vec
+
+
+def descriptor(L: np.ndarray, xk: float, yk: float, xi: int, yi: int, sigma_oct: float,
+               angle_deg: float, p: Params) -> np.ndarray:
+    """4x4x8 descriptor (§3.2), layout [v][u][o] row-major: the single-scale
+    pixel-grid histogram, or with dsp the mean of the DSP scales' histograms
+    (pooled before normalisation, §3.2), then normalise_descriptor."""
+    if p.dsp:
+        hist = sum(dsp_scale_histogram(L, xk, yk, sigma_oct, angle_deg, f, p)
+                   for f in p.dsp_scales) / len(p.dsp_scales)
+    else:
+        hist = plain_histogram(L, xk, yk, xi, yi, sigma_oct, angle_deg, p)
+    return normalise_descriptor(hist, p)
 
 
 # ------------------------------------------------------------------ A9: cap

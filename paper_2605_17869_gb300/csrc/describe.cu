@@ -267,8 +267,54 @@ __global__ void __launch_bounds__(1024) k_select(const Desc *__restrict__ d) {
 
 // ------------------------------------------------------------- descriptor
 
+// Accumulate one gradient sample at bin coordinates (rx, ry) from the
+// keypoint, (u, v) = (rx, ry) + 3/2, into the thread's histogram column: weight
+// m * exp(-(rx^2 + ry^2) / 8), orientation relative to th, trilinear split.
+__device__ __forceinline__ void desc_vote(float *hist, int lane, float rx, float ry, float gx,
+                                          float gy, float th) {
+  const float u = rx + 1.5f, v = ry + 1.5f;
+  const float mag = sqrtf(gx * gx + gy * gy);
+  float phi = atan2f(gy, gx) - th;
+  if (phi < 0.f) phi += kTwoPi;
+  if (phi < 0.f) phi += kTwoPi;
+  if (phi >= kTwoPi) phi -= kTwoPi;
+  const float ob = phi * (8.0f / kTwoPi);
+  const float wt = mag * expf(-(rx * rx + ry * ry) * 0.125f);
+  const float u0f = floorf(u), v0f = floorf(v), o0f = floorf(ob);
+  const float fu = u - u0f, fv = v - v0f, fo = ob - o0f;
+  const int u0 = (int)u0f, v0 = (int)v0f, o0 = (int)o0f;
+#pragma unroll
+  for (int dv = 0; dv < 2; dv++) {
+    const int vv = v0 + dv;
+    if (vv < 0 || vv > 3) continue;
+    const float wv = dv ? fv : 1.f - fv;
+#pragma unroll
+    for (int du = 0; du < 2; du++) {
+      const int uu = u0 + du;
+      if (uu < 0 || uu > 3) continue;
+      const float wu = du ? fu : 1.f - fu;
+#pragma unroll
+      for (int dob = 0; dob < 2; dob++) {
+        const int oo = (o0 + dob) & 7;
+        const float wo = dob ? fo : 1.f - fo;
+        hist[((vv * 4 + uu) * 8 + oo) * 32 + lane] += wt * wv * wu * wo;
+      }
+    }
+  }
+}
+
+// DSP-SIFT pooling (§3.2): relative scales of the descriptor's bin width.
+__constant__ float kDspScale[5] = {0.5f, 0.70710678118654752f, 1.0f, 1.41421356237309505f, 2.0f};
+
 // One block of kKpWarps warps per output keypoint; same lane-private
 // histogram scheme as the orientation (merge order: warp, then lane).
+// Plain mode samples the pixel grid around the keypoint. DSP mode samples, for
+// each of the 5 scales, a 32 x 32 grid at bin coordinates (a + 1/2)/8 - 2 in
+// the keypoint's rotated frame (bin width 3 sigma x scale) and takes the
+// gradient as central differences of the bilinearly interpolated level; all
+// scales vote into the same histogram (pooling before normalisation).
+// Positions are kept relative to the integer keypoint pixel, so the
+// interpolation weights keep full FP32 precision in large octaves.
 __global__ void __launch_bounds__(kKpWarps * 32) k_descriptor(const Desc *__restrict__ d) {
   extern __shared__ float dsm[];
   __shared__ float red[kKpWarps];
@@ -305,46 +351,47 @@ __global__ void __launch_bounds__(kKpWarps * 32) k_descriptor(const Desc *__rest
     float st, ct;
     sincosf(th, &st, &ct);
     for (int k = 0; k < kDescLen; k++) hist[k * 32 + lane] = 0.f;
-    const int side = 2 * R + 1, ns = side * side;
-    for (int idx = tid; idx < ns; idx += kKpWarps * 32) {
-      const int jj = idx / side;
-      const int i = idx - jj * side - R, jy = jj - R;
-      const int px = r.x + i, py = r.y + jy;
-      if (px < 1 || px > od.W - 2 || py < 1 || py > od.H - 2) continue;
-      const float ox = (float)i - r.dx, oy = (float)jy - r.dy;
-      const float rx = (ct * ox + st * oy) * inv_w;
-      const float ry = (-st * ox + ct * oy) * inv_w;
-      const float u = rx + 1.5f, v = ry + 1.5f;
-      if (!(u > -1.f && u < 4.f && v > -1.f && v < 4.f)) continue;
-      const float *p = L + (long long)py * od.pitch + px;
-      const float gx = __ldg(p + 1) - __ldg(p - 1);
-      const float gy = __ldg(p + od.pitch) - __ldg(p - od.pitch);
-      const float mag = sqrtf(gx * gx + gy * gy);
-      float phi = atan2f(gy, gx) - th;
-      if (phi < 0.f) phi += kTwoPi;
-      if (phi < 0.f) phi += kTwoPi;
-      if (phi >= kTwoPi) phi -= kTwoPi;
-      const float ob = phi * (8.0f / kTwoPi);
-      const float wt = mag * expf(-(rx * rx + ry * ry) * 0.125f);
-      const float u0f = floorf(u), v0f = floorf(v), o0f = floorf(ob);
-      const float fu = u - u0f, fv = v - v0f, fo = ob - o0f;
-      const int u0 = (int)u0f, v0 = (int)v0f, o0 = (int)o0f;
-#pragma unroll
-      for (int dv = 0; dv < 2; dv++) {
-        const int vv = v0 + dv;
-        if (vv < 0 || vv > 3) continue;
-        const float wv = dv ? fv : 1.f - fv;
-#pragma unroll
-        for (int du = 0; du < 2; du++) {
-          const int uu = u0 + du;
-          if (uu < 0 || uu > 3) continue;
-          const float wu = du ? fu : 1.f - fu;
-#pragma unroll
-          for (int dob = 0; dob < 2; dob++) {
-            const int oo = (o0 + dob) & 7;
-            const float wo = dob ? fo : 1.f - fo;
-            hist[((vv * 4 + uu) * 8 + oo) * 32 + lane] += wt * wv * wu * wo;
-          }
+    if (!d->dsp) {
+      const int side = 2 * R + 1, ns = side * side;
+      for (int idx = tid; idx < ns; idx += kKpWarps * 32) {
+        const int jj = idx / side;
+        const int i = idx - jj * side - R, jy = jj - R;
+        const int px = r.x + i, py = r.y + jy;
+        if (px < 1 || px > od.W - 2 || py < 1 || py > od.H - 2) continue;
+        const float ox = (float)i - r.dx, oy = (float)jy - r.dy;
+        const float rx = (ct * ox + st * oy) * inv_w;
+        const float ry = (-st * ox + ct * oy) * inv_w;
+        const float u = rx + 1.5f, v = ry + 1.5f;
+        if (!(u > -1.f && u < 4.f && v > -1.f && v < 4.f)) continue;
+        const float *p = L + (long long)py * od.pitch + px;
+        const float gx = __ldg(p + 1) - __ldg(p - 1);
+        const float gy = __ldg(p + od.pitch) - __ldg(p - od.pitch);
+        desc_vote(hist, lane, rx, ry, gx, gy, th);
+      }
+    } else {
+      for (int f = 0; f < 5; f++) {
+        const float wb = wbin * kDspScale[f];
+        for (int idx = tid; idx < 32 * 32; idx += kKpWarps * 32) {
+          const float rx = ((float)(idx & 31) + 0.5f) * 0.125f - 2.0f;
+          const float ry = ((float)(idx >> 5) + 0.5f) * 0.125f - 2.0f;
+          const float xr = r.dx + wb * (ct * rx - st * ry);  // relative to pixel (r.x, r.y)
+          const float yr = r.dy + wb * (st * rx + ct * ry);
+          const float xf = floorf(xr), yf = floorf(yr);
+          const int x0 = r.x + (int)xf, y0 = r.y + (int)yf;
+          if (x0 < 1 || x0 > od.W - 3 || y0 < 1 || y0 > od.H - 3) continue;
+          const float fx = xr - xf, fy = yr - yf, gx1 = 1.f - fx, gy1 = 1.f - fy;
+          const float *p = L + (long long)y0 * od.pitch + x0;
+          const float *pm = p - od.pitch, *pp = p + od.pitch, *p2 = pp + od.pitch;
+          // L(x + 1, y) - L(x - 1, y) and L(x, y + 1) - L(x, y - 1), bilinear
+          const float xp = gy1 * (gx1 * __ldg(p + 1) + fx * __ldg(p + 2)) +
+                           fy * (gx1 * __ldg(pp + 1) + fx * __ldg(pp + 2));
+          const float xm = gy1 * (gx1 * __ldg(p - 1) + fx * __ldg(p)) +
+                           fy * (gx1 * __ldg(pp - 1) + fx * __ldg(pp));
+          const float yp = gy1 * (gx1 * __ldg(pp) + fx * __ldg(pp + 1)) +
+                           fy * (gx1 * __ldg(p2) + fx * __ldg(p2 + 1));
+          const float ym = gy1 * (gx1 * __ldg(pm) + fx * __ldg(pm + 1)) +
+                           fy * (gx1 * __ldg(p) + fx * __ldg(p + 1));
+          desc_vote(hist, lane, rx, ry, xp - xm, yp - ym, th);
         }
       }
     }

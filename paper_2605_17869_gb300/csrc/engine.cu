@@ -77,7 +77,7 @@ sift_status validate_params(const sift_params &p, std::string *why) {
   if (p.border < 1) return bad("border must be >= 1");
   if (p.max_refine_iter < 1) return bad("max_refine_iter must be >= 1");
   if (p.max_kpts < 1) return bad("max_kpts must be >= 1");
-  if (p.dsp != 0) return bad("dsp pooling is not available");
+  if (p.dsp != 0 && p.dsp != 1) return bad("dsp must be 0 or 1");
   BlurTaps t;
   int rmax = gaussian_taps(base_sigma(p), &t);
   for (int i = 1; i <= p.n_scales + 2 && rmax >= 0; i++) {
@@ -228,6 +228,7 @@ sift_status Engine::fill_plan(int n, const ImgIn *in, Desc &hd, WsLayout &L, int
   hd.max_iter = P_.max_refine_iter;
   hd.upright = P_.upright ? 1 : 0;
   hd.rootsift = P_.rootsift ? 1 : 0;
+  hd.dsp = P_.dsp ? 1 : 0;
   hd.ori_peak_ratio = P_.ori_peak_ratio;
   size_t pyr = 0, bm = 0, cand = 0, ori = 0, fin = 0;
   int bmc = 0, cc = 0, M = 0;
@@ -404,7 +405,7 @@ cudaError_t Engine::enqueue_pyramid(cudaStream_t s, int M, std::vector<ProfRec> 
     // Octaves above 0: the level-1 launch also produces level 0 by decimating
     // level S of the previous octave (no separate decimation pass).
     for (int l = 1; l <= S_ + 2; l++) {
-      const int kind = tun_.lvl_kind[l];
+      const int kind = o == 0 ? tun_.lvl_kind[l] : TK_BLUR32;  // tuned on octave 0 only
       rec(PC_BLUR, [&] {
         return launch_level_blur(d, o, l, lvl_R_[l], lvl_t_[l], kind, grid_blur(lvl_R_[l], kind, 0), s,
                                  o > 0 && l == 1);
@@ -445,7 +446,7 @@ cudaError_t Engine::enqueue_all(cudaStream_t s, int M, std::vector<ProfRec> *pro
     // Octaves above 0: the level-1 launch also produces level 0 by decimating
     // level S of the previous octave (no separate decimation pass).
     for (int l = 1; l <= S_ + 2; l++) {
-      const int kind = tun_.lvl_kind[l];
+      const int kind = o == 0 ? tun_.lvl_kind[l] : TK_BLUR32;  // tuned on octave 0 only
       rec(PC_BLUR, [&] {
         return launch_level_blur(d, o, l, lvl_R_[l], lvl_t_[l], kind, grid_blur(lvl_R_[l], kind, 0), s,
                                  o > 0 && l == 1);
@@ -684,30 +685,35 @@ sift_status Engine::autotune(int H, int W, cudaStream_t s) {
   in.W = W;
   in.pitch = W;
   st = run_pyramid(in, s);
+  int hs[kMaxOct], ws[kMaxOct];
+  const int M = octave_sizes(H, W, hs, ws);
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
-  const Desc *d = ddesc_;
-  const int kinds[2] = {TK_BLUR32, TK_BLUR64};
-  for (int l = 1; l <= S_ + 2 && st == SIFT_OK; l++) {
-    float best = 1e30f;
-    int best_kind = tun_.lvl_kind[l];
-    for (int kk = 0; kk < 2; kk++) {
-      const int kind = kinds[kk];
-      const int g = grid_blur(lvl_R_[l], kind, 0);
-      for (int w = 0; w < 2; w++) launch_level_blur(d, 0, l, lvl_R_[l], lvl_t_[l], kind, g, s);
-      cudaEventRecord(a, s);
-      for (int r = 0; r < 5; r++) launch_level_blur(d, 0, l, lvl_R_[l], lvl_t_[l], kind, g, s);
-      cudaEventRecord(b, s);
-      cudaEventSynchronize(b);
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, a, b);
-      if (ms < best) {
-        best = ms;
-        best_kind = kind;
-      }
+  // Time the whole pyramid stage (all octaves, as the pipeline runs it), not
+  // one level in isolation: a level's tile height also changes how the level
+  // overlaps its neighbours and how warm L2 is for them. Coordinate descent
+  // from 32-row tiles everywhere; a level switches to 64 rows only if the
+  // stage gets at least 1% faster.
+  auto time_stage = [&]() -> float {
+    for (int w = 0; w < 2; w++) enqueue_pyramid(s, M, nullptr);
+    cudaEventRecord(a, s);
+    for (int r = 0; r < 5; r++) enqueue_pyramid(s, M, nullptr);
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+  };
+  if (st == SIFT_OK) {
+    for (int l = 0; l < kMaxLevels; l++) tun_.lvl_kind[l] = TK_BLUR32;
+    float best = time_stage();
+    for (int l = 1; l <= S_ + 2; l++) {
+      tun_.lvl_kind[l] = TK_BLUR64;
+      const float t = time_stage();
+      if (t < 0.99f * best) best = t;
+      else tun_.lvl_kind[l] = TK_BLUR32;
     }
-    tun_.lvl_kind[l] = best_kind;
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);

@@ -82,7 +82,7 @@ struct Desc {
   float sigma0, contrast_thr, prefilter, edge_ratio;
   int border, max_iter, upright, rootsift;
   float ori_peak_ratio, pad_f[3];
-  int n_bm_chunks, n_cc_chunks, pad_i[2];
+  int n_bm_chunks, n_cc_chunks, dsp, pad_i;
   // workspace arrays
   float *pyr;
   uint32_t *bm;

@@ -119,6 +119,24 @@ def test_topk_cap_matches_oracle():
     _assert_parity(ref, f, p, "top-K")
 
 
+@pytest.mark.parametrize("up,dsp,root", [(False, 1, 0), (False, 1, 1), (True, 1, 1),
+                                         (False, 0, 1)])
+def test_dsp_and_rootsift_match_oracle(up, dsp, root):
+    """DSP multi-scale pooling and the RootSIFT epilogue (§3.2) against the
+    oracle's, with the same tolerances; repeated runs are bitwise identical."""
+    img = synth.make_image(synth.rng_for(14, int(up)), 300, 380)
+    ex, f = _gpu(img, upsample=int(up), dsp=dsp, rootsift=root, max_kpts=8192)
+    p = _oracle_params(upsample=up, dsp=bool(dsp), rootsift=bool(root))
+    ref = so.extract(img, p, keep_pyramid=True)
+    _assert_parity(ref, f, p, f"dsp={dsp} rootsift={root} upsample={up}")
+    if root:
+        d = f.desc.cpu().numpy()
+        np.testing.assert_allclose(np.linalg.norm(d, axis=1), 1.0, atol=1e-5)
+    g = ex.extract(torch.from_numpy(img).cuda())
+    assert f.count == g.count
+    assert np.array_equal(f.desc.cpu().numpy(), g.desc.cpu().numpy())
+
+
 # ------------------------------------------------------------------ edge cases
 
 def test_flat_image_has_no_keypoints():

@@ -51,6 +51,20 @@ MUTANTS = {
         "    bins = np.floor(n * th / (2 * math.pi) + 0.5).astype(np.int64) % n",
         "    bins = np.floor(n * th / (2 * math.pi)).astype(np.int64) % n"),
     "taps_not_normalised": ("    return r, w / w.sum()", "    return r, w / (math.sqrt(2 * math.pi) * sigma)"),
+    "dsp_grid_no_half": ("    c = (np.arange(G) + 0.5) * d / G - 0.5 * d",
+                         "    c = np.arange(G) * d / G - 0.5 * d"),
+    "dsp_rotation_sign": ("    x = xk + wbin * (ct * rx - st * ry)\n    y = yk + wbin * (st * rx + ct * ry)",
+                          "    x = xk + wbin * (ct * rx + st * ry)\n    y = yk + wbin * (-st * rx + ct * ry)"),
+    "dsp_scale_ignored": ("    wbin = p.desc_scale * sigma_oct * scale",
+                          "    wbin = p.desc_scale * sigma_oct"),
+    "dsp_weight_in_pixels": (
+        "    wt = mag * np.exp(-(rx * rx + ry * ry) / (2.0 * (0.5 * d) ** 2))\n    return _trilinear_histogram(rx",
+        "    wt = mag * np.exp(-wbin * wbin * (rx * rx + ry * ry) / (2.0 * (0.5 * d) ** 2))\n"
+        "    return _trilinear_histogram(rx"),
+    "dsp_dy_from_x": ("    dy = bilinear(L, x, y + 1) - bilinear(L, x, y - 1)",
+                      "    dy = bilinear(L, x + 1, y + 1) - bilinear(L, x - 1, y - 1)"),
+    "rootsift_no_l1": ("        vec = np.sqrt(vec / l1) if l1 > 0 else vec",
+                       "        vec = np.sqrt(vec) if l1 > 0 else vec"),
 }
 
 

@@ -332,11 +332,14 @@ def _angle_diff(a, b):
     return np.abs((a - b + 180.0) % 360.0 - 180.0)
 
 
-def test_rot90_equivariance_octave0():
+@pytest.mark.parametrize("dsp", [False, True])
+def test_rot90_equivariance_octave0(dsp):
     """Under a 90-degree counter-clockwise rotation (x, y) -> (y, W-1-x), octave-0
     keypoints map one to one, the orientation shifts by -90 degrees and the
-    descriptor is unchanged (octave 0 involves no decimation, so it commutes)."""
-    p = so.Params()
+    descriptor is unchanged (octave 0 involves no decimation, so it commutes).
+    The DSP sample grids are symmetric about the keypoint, so they rotate onto
+    themselves and the pooled descriptor is unchanged too."""
+    p = so.Params(dsp=dsp)
     img = synth.make_image(synth.rng_for(90, 0), 96, 112)
     r0 = so.extract(img, p)
     r1 = so.extract(np.rot90(img).copy(), p)
@@ -357,10 +360,11 @@ def test_rot90_equivariance_octave0():
         np.testing.assert_allclose(d0[i], d1[j], atol=1e-9)
 
 
-def test_rot90_upright_descriptor_permutation():
+@pytest.mark.parametrize("dsp", [False, True])
+def test_rot90_upright_descriptor_permutation(dsp):
     """Upright mode: rotating the image permutes the descriptor as
     (v, u, o) -> (3 - u, v, o - 2 mod 8)."""
-    p = so.Params(upright=True)
+    p = so.Params(upright=True, dsp=dsp)
     img = synth.make_image(synth.rng_for(90, 1), 96, 96)
     r0 = so.extract(img, p)
     r1 = so.extract(np.rot90(img).copy(), p)
@@ -381,11 +385,12 @@ def test_rot90_upright_descriptor_permutation():
         np.testing.assert_allclose(d1[j], want, atol=1e-9)
 
 
-def test_transpose_equivariance_all_octaves():
+@pytest.mark.parametrize("dsp", [False, True])
+def test_transpose_equivariance_all_octaves(dsp):
     """Transposing the image commutes with blur, decimation and upsampling, so every
     keypoint maps (x, y) -> (y, x) with angle 90 - a, and the descriptor mirrors:
     (v, u, o) -> (3 - v, u, -o mod 8)."""
-    p = so.Params(upsample=True)
+    p = so.Params(upsample=True, dsp=dsp)
     img = synth.make_image(synth.rng_for(91, 0), 70, 90)
     r0 = so.extract(img, p)
     r1 = so.extract(img.T.copy(), p)
@@ -405,6 +410,101 @@ def test_transpose_equivariance_all_octaves():
                 for o in range(8):
                     want[3 - v, u, (-o) % 8] = d0[i, v, u, o]
         np.testing.assert_allclose(d1[j], want, atol=1e-9)
+
+
+# ------------------------------------------------------------- DSP / RootSIFT
+
+def test_bilinear_reproduces_bilinear_functions():
+    """Bilinear interpolation is exact on f = a + bx + cy + exy and returns the
+    sample itself at integer nodes."""
+    Y, X = np.mgrid[0:20, 0:30].astype(float)
+    a, b, c, e = 0.3, -0.02, 0.05, 0.001
+    L = a + b * X + c * Y + e * X * Y
+    x = RNG.uniform(0, 28.999, 200)
+    y = RNG.uniform(0, 18.999, 200)
+    np.testing.assert_allclose(so.bilinear(L, x, y), a + b * x + c * y + e * x * y, atol=1e-12)
+    xi = RNG.integers(0, 29, 50).astype(float)
+    yi = RNG.integers(0, 19, 50).astype(float)
+    np.testing.assert_array_equal(so.bilinear(L, xi, yi), L[yi.astype(int), xi.astype(int)])
+
+
+@pytest.mark.parametrize("deg", [0.0, 45.0, 120.0])
+def test_dsp_ramp_is_scale_invariant_and_separable(deg):
+    """On a linear ramp every sample's gradient is the same vector (bilinear
+    interpolation is exact on it), and each DSP scale samples the same pattern
+    in bin units, so every scale gives the same normalised histogram and the
+    pooled descriptor equals any single scale's. Its spatial mass is the outer
+    product of one symmetric profile with itself, all in the two orientation
+    bins bracketing the gradient angle (one bin at a bin centre)."""
+    p = so.Params(dsp=True)
+    Y, X = np.mgrid[0:200, 0:200].astype(float)
+    th = math.radians(deg)
+    L = 0.004 * (math.cos(th) * X + math.sin(th) * Y)
+    xk, yk, sig = 100.25, 99.6, 1.9
+    pooled = so.descriptor(L, xk, yk, 100, 100, sig, 0.0, p)
+    for f in p.dsp_scales:
+        one = so.normalise_descriptor(so.dsp_scale_histogram(L, xk, yk, sig, 0.0, f, p), p)
+        np.testing.assert_allclose(one, pooled, atol=1e-12)
+    h = so.dsp_scale_histogram(L, xk, yk, sig, 0.0, 1.0, p)
+    ob = set(np.nonzero(h.sum(axis=(0, 1)) > 1e-12)[0].tolist())
+    k = deg * 8 / 360.0
+    assert ob == ({int(k)} if k == int(k) else {int(k), int(k) + 1})
+    sp = h.sum(axis=2)
+    assert np.linalg.matrix_rank(sp, tol=1e-9 * sp.max()) == 1
+    np.testing.assert_allclose(sp, sp.T, rtol=1e-12)
+    np.testing.assert_allclose(sp, sp[::-1, ::-1], rtol=1e-12)
+
+
+def test_dsp_patch_mass_closed_form():
+    """On L = x/2 (gradient (1, 0): magnitude 1, all mass in orientation bin 0)
+    each DSP scale's histogram mass is a closed form of the G x G patch: the
+    Gaussian weight and the trilinear split are separable, so the total is
+    (sum_a g(c_a) k(u_a))^2 over the G sample coordinates c_a = (a + 1/2) d/G
+    - d/2, with g(c) = exp(-c^2 / 8), u = c + 3/2 and k(u) the share of a
+    sample's split that stays inside bins 0..3 (1 + u below 0, 4 - u above 3).
+    A wrong grid offset, spacing, patch size or weight width changes it."""
+    p = so.Params(dsp=True)
+    Y, X = np.mgrid[0:300, 0:300].astype(float)
+    L = 0.5 * X
+    c = (np.arange(p.dsp_grid) + 0.5) * 4 / p.dsp_grid - 2.0
+    u = c + 1.5
+    k = np.where(u < 0, 1 + u, np.where(u > 3, 4 - u, 1.0))
+    want = (np.exp(-c * c / 8.0) * k).sum() ** 2
+    for f in p.dsp_scales:
+        h = so.dsp_scale_histogram(L, 150.0, 150.0, 2.0, 0.0, f, p)
+        assert h[:, :, 1:].sum() == 0.0
+        assert h.sum() == pytest.approx(want, rel=1e-12)
+
+
+def test_dsp_patch_extent_per_scale():
+    """Scale f's patch spans d * w_f = 4 * 3 * sigma * f pixels; with sigma = 2 and
+    upright sampling its samples lie within (2 - 1/16) * 6 f = 11.625 f px of the
+    keypoint. A step edge between columns 70 and 71 changes the interpolated
+    level only for x > 70, i.e. for samples more than 9 px right of a keypoint at
+    x = 60 (the stencil reaches x + 1): scales 0.5 and 1/sqrt(2) (reach 5.8 and
+    8.2 px) see nothing, scales 1, sqrt(2) and 2 (11.6 to 23.3 px) see it."""
+    p = so.Params(dsp=True)
+    L = np.zeros((120, 120))
+    L[:, 71:] = 1.0
+    for f in p.dsp_scales:
+        h = so.dsp_scale_histogram(L, 60.0, 60.0, 2.0, 0.0, f, p)
+        if f < 0.8:
+            assert h.sum() == 0.0, f
+        else:
+            assert h.sum() > 0.0, f
+
+
+def test_rootsift_is_sqrt_of_l1_normalised_plain():
+    """RootSIFT output squared equals the plain (clipped, L2-renormalised)
+    descriptor divided by its L1 norm; it has unit L2 norm and no negative entry."""
+    img = synth.make_image(synth.rng_for(92, 0), 90, 110)
+    r0 = so.extract(img, so.Params())
+    r1 = so.extract(img, so.Params(rootsift=True))
+    assert len(r0) == len(r1) > 5
+    l1 = r0.desc.sum(axis=1, keepdims=True)
+    np.testing.assert_allclose(r1.desc ** 2, r0.desc / l1, atol=1e-14)
+    np.testing.assert_allclose(np.linalg.norm(r1.desc, axis=1), 1.0, atol=1e-12)
+    assert np.all(r1.desc >= 0)
 
 
 # ------------------------------------------------------------------ cap
