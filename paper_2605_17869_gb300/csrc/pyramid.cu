@@ -37,6 +37,9 @@ __device__ __forceinline__ unsigned smem_u32(const void *p) {
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src));
 }
+__device__ __forceinline__ void cp_async16_u(unsigned dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
+}
 __device__ __forceinline__ void cp_async4(void *dst, const void *src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst)), "l"(src));
 }
@@ -381,40 +384,74 @@ __device__ __forceinline__ void store_level0(const float *s_in, float *out0, int
   }
 }
 
+// Interior tile of a 16-byte aligned plane (no staged row or column outside
+// the image): a fixed, fully unrolled copy schedule, thread t copying float4
+// group t % 40 of rows t / 40 + 8 i, so the copies cost almost nothing but
+// the copy instructions themselves.
+template <int ROWS>
+__device__ __forceinline__ void stage_interior(const float *__restrict__ src, int pitch, int xb,
+                                               int yb, float *s_in) {
+  constexpr int RPP = kThreads / kNG;  // 8
+  constexpr int NIT = (ROWS + RPP - 1) / RPP;
+  const int tid = threadIdx.x;
+  const int g = tid % kNG, r0 = tid / kNG;
+  const unsigned d0 = smem_u32(s_in + r0 * kSinW + 4 * g);
+  const float *p = src + (long long)(yb + r0) * pitch + (xb + 4 * g);
+  const long long step = (long long)RPP * pitch;
+#pragma unroll
+  for (int i = 0; i < NIT; i++)
+    if (i + 1 < NIT || r0 + i * RPP < ROWS) cp_async16_u(d0 + i * RPP * kSinW * 4, p + i * step);
+}
+
 template <int R, int TH, int MODE>
 __device__ __forceinline__ void issue_stage(const TileGeo &g, float *dst) {
   constexpr int ROWS = TH + 2 * R;
-  if (MODE == 3)
+  if (MODE == 3) {
     stage_decim_issue(g.src, g.spitch, g.H, g.W, g.x0, g.y0, R, ROWS, dst);
-  else
-    stage_plain_issue(g.src, g.spitch, g.H, g.W, g.vec != 0, g.x0, g.y0, R, ROWS, dst);
+  } else {
+    const int xb = g.x0 - kBlurHalo, yb = g.y0 - R;
+    if (g.vec && xb >= 0 && xb + kSinW <= g.W && yb >= 0 && yb + ROWS <= g.H)
+      stage_interior<ROWS>(g.src, g.spitch, xb, yb, dst);
+    else
+      stage_plain_issue(g.src, g.spitch, g.H, g.W, g.vec != 0, g.x0, g.y0, R, ROWS, dst);
+  }
 }
 
-// The block's tiles are t0, t0 + grid, t0 + 2 grid, ...; thread 0 resolves the
-// geometry of the next tile while the current one is computed and publishes it
-// through the barrier that ends the iteration, so no other thread does the
-// image search or reads the descriptor per tile. The staging buffer is single:
-// copy/compute overlap comes from the other blocks resident on the SM (three
-// or four per SM for the default radii), which measured faster than double
-// buffering with fewer blocks.
+// The block's tiles are t0, t0 + grid, t0 + 2 grid, .... Their geometry is
+// resolved 32 tiles at a time, one tile per lane of warp 0, into a ring of two
+// 32-entry chunks in shared memory: the lanes' owner searches and descriptor
+// loads overlap, and chunk m + 1 is filled half-way through chunk m, so no
+// tile waits on a dependent chain of global loads.
+// One staging buffer per block, but its copies run ahead: once the column pass
+// of tile i has read the staged window, the block issues tile i + 1's copies
+// into it and they land while the row pass of tile i runs (MODE 2 stages
+// synchronously). With three or four blocks per SM this measured faster than
+// a second buffer with fewer blocks.
+constexpr int kGeoChunk = 32;
 template <int R, int TH, int MODE>
-__global__ void __launch_bounds__(kThreads) k_blur(const Desc *__restrict__ d, int oct, int lvl_out,
-                                                   BlurTaps tp) {
+__global__ void __launch_bounds__(kThreads, TH == 32 ? (MODE == 0 ? 4 : 3) : 1)
+    k_blur(const Desc *__restrict__ d, int oct, int lvl_out, BlurTaps tp) {
   constexpr int ROWS = TH + 2 * R;
+  constexpr bool kAhead = MODE != 2;
   extern __shared__ float4 smem4[];
-  __shared__ TileGeo geo[2];
+  __shared__ TileGeo geo[2 * kGeoChunk];
   float *s_in = reinterpret_cast<float *>(smem4);
   float *s_v = s_in + ROWS * kSinW;
   const int *pre = d->tile_pre[KindOf<TH>::v][oct];
   const int total = pre[d->n_img];
   const int t0 = blockIdx.x, G = gridDim.x;
   if (t0 >= total) return;
-  if (threadIdx.x == 0) geo[0] = tile_geo<TH, MODE>(d, pre, oct, lvl_out, t0);
+  const int n_mine = (total - t0 + G - 1) / G;  // tiles of this block
+  auto fill_chunk = [&](int m) {                // tiles 32 m .. 32 m + 31, by warp 0
+    const int k = m * kGeoChunk + (int)threadIdx.x;
+    if (k < n_mine) geo[k & (2 * kGeoChunk - 1)] = tile_geo<TH, MODE>(d, pre, oct, lvl_out, t0 + k * G);
+  };
+  if (threadIdx.x < 32) fill_chunk(0);
   __syncthreads();
-  for (int k = 0, t = t0; t < total; t += G, k++) {
-    const TileGeo &g = geo[k & 1];
-    if (MODE != 2) {
-      issue_stage<R, TH, MODE>(g, s_in);
+  if (kAhead) issue_stage<R, TH, MODE>(geo[0], s_in);
+  for (int k = 0; k < n_mine; k++) {
+    const TileGeo &g = geo[k & (2 * kGeoChunk - 1)];
+    if (kAhead) {
       cp_async_wait_all();
     } else if (!stage_upsampled_fast<R, TH>(g.src, g.spitch, g.sh, g.sw, g.vec != 0, g.x0, g.y0,
                                              s_in, s_v)) {
@@ -424,9 +461,10 @@ __global__ void __launch_bounds__(kThreads) k_blur(const Desc *__restrict__ d, i
     if (MODE == 3) store_level0<R, TH>(s_in, g.out0, g.pitch, g.H, g.x0, g.y0);
     col_pass<R, TH>(s_in, s_v, tp);
     __syncthreads();
+    if (kAhead && k + 1 < n_mine) issue_stage<R, TH, MODE>(geo[(k + 1) & (2 * kGeoChunk - 1)], s_in);
     row_pass_store<R, TH>(s_v, g.out, g.pitch, g.H, g.x0, g.y0, tp);
-    if (threadIdx.x == 0 && t + G < total)
-      geo[(k + 1) & 1] = tile_geo<TH, MODE>(d, pre, oct, lvl_out, t + G);
+    if (threadIdx.x < 32 && (k & (kGeoChunk - 1)) == kGeoChunk / 2)
+      fill_chunk(k / kGeoChunk + 1);
     __syncthreads();
   }
 }
