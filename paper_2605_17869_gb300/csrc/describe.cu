@@ -44,6 +44,8 @@ __device__ __forceinline__ float sigma_of(const Desc *d, const RefRec &r) {
 // w*32 + l, w*32 + l + 128, ... and votes into its private column hist[w][.][l];
 // bin k is then the sum over w, then l, in that fixed order.
 __global__ void __launch_bounds__(kKpWarps * 32) k_orientation(const Desc *__restrict__ d) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ float hist[kKpWarps][kOriBins][32];
   __shared__ float hsum[kOriBins];
   __shared__ float hsm[kOriBins];
@@ -139,6 +141,8 @@ __global__ void __launch_bounds__(kKpWarps * 32) k_orientation(const Desc *__res
 // --------------------------------------------- oriented keypoint compaction
 
 __global__ void __launch_bounds__(kThreads) k_cc_count(const Desc *__restrict__ d) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ int tmp[kThreads / 32 + 1];
   constexpr int SPT = kChunk / kThreads;
   const int n = d->n_img;
@@ -159,6 +163,8 @@ __global__ void __launch_bounds__(kThreads) k_cc_count(const Desc *__restrict__ 
 // One block: per image scan of chunk counts, oriented totals, the final
 // (capped) counts, their prefix over images, and the caller's count output.
 __global__ void __launch_bounds__(1024) k_cc_scan(const Desc *__restrict__ d) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ int tmp[1024 / 32 + 1];
   const int n = d->n_img;
   int flat = 0;
@@ -190,6 +196,8 @@ __global__ void __launch_bounds__(1024) k_cc_scan(const Desc *__restrict__ d) {
 }
 
 __global__ void __launch_bounds__(kThreads) k_cc_emit(const Desc *__restrict__ d) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ int tmp[kThreads / 32 + 1];
   constexpr int SPT = kChunk / kThreads;
   const int n = d->n_img;
@@ -230,6 +238,8 @@ __global__ void __launch_bounds__(kThreads) k_cc_emit(const Desc *__restrict__ d
 // in canonical order. The threshold is found by a bitwise search on the
 // response bits (responses are non-negative, so bit order = value order).
 __global__ void __launch_bounds__(1024) k_select(const Desc *__restrict__ d) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ int tmp[1024 / 32 + 1];
   const int n_img = d->n_img;
   for (int b = blockIdx.x; b < n_img; b += gridDim.x) {
@@ -316,6 +326,8 @@ __constant__ float kDspScale[5] = {0.5f, 0.70710678118654752f, 1.0f, 1.414213562
 // Positions are kept relative to the integer keypoint pixel, so the
 // interpolation weights keep full FP32 precision in large octaves.
 __global__ void __launch_bounds__(kKpWarps * 32) k_descriptor(const Desc *__restrict__ d) {
+  pdl_trigger();
+  pdl_wait();
   extern __shared__ float dsm[];
   __shared__ float red[kKpWarps];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -420,19 +432,22 @@ __global__ void __launch_bounds__(kKpWarps * 32) k_descriptor(const Desc *__rest
 }  // namespace
 
 cudaError_t launch_orientation(const Desc *d, int grid, cudaStream_t s) {
-  k_orientation<<<grid, kKpWarps * 32, 0, s>>>(d);
+  cudaError_t e = launch_pdl(k_orientation, grid, kKpWarps * 32, 0, s, d);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
 cudaError_t launch_ori_compact(const Desc *d, int grid, cudaStream_t s) {
-  k_cc_count<<<grid, kThreads, 0, s>>>(d);
-  k_cc_scan<<<1, 1024, 0, s>>>(d);
-  k_cc_emit<<<grid, kThreads, 0, s>>>(d);
+  cudaError_t e = launch_pdl(k_cc_count, grid, kThreads, 0, s, d);
+  if (e == cudaSuccess) e = launch_pdl(k_cc_scan, 1, 1024, 0, s, d);
+  if (e == cudaSuccess) e = launch_pdl(k_cc_emit, grid, kThreads, 0, s, d);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
 cudaError_t launch_select(const Desc *d, int grid, cudaStream_t s) {
-  k_select<<<grid, 1024, 0, s>>>(d);
+  cudaError_t e = launch_pdl(k_select, grid, 1024, 0, s, d);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -444,7 +459,8 @@ cudaError_t descriptor_set_attributes() {
 }
 
 cudaError_t launch_descriptor(const Desc *d, int grid, cudaStream_t s) {
-  k_descriptor<<<grid, kKpWarps * 32, descriptor_smem_bytes(), s>>>(d);
+  cudaError_t e = launch_pdl(k_descriptor, grid, kKpWarps * 32, descriptor_smem_bytes(), s, d);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

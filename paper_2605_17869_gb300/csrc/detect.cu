@@ -46,7 +46,9 @@ __global__ void __launch_bounds__(kThreads) k_extrema(const Desc *__restrict__ d
   // Neighbour k of the 26 (3x3x3 minus the centre), owned by lane k.
   const int jn = lane < 13 ? lane : lane + 1;
   const int nds = jn / 9 - 1, ndy = (jn / 3) % 3 - 1, ndx = jn % 3 - 1;
+  pdl_wait();
   for (int t = blockIdx.x * WPB + (threadIdx.x >> 5); t < total; t += gridDim.x * WPB) {
+    if (t + gridDim.x * WPB >= total) pdl_trigger();  // this warp's last tile
     const int b = find_owner(pre, n, t);
     const OctDev od = d->oct[b * kMaxOct + oct];  // image b's octaves sit at fixed slots
     const int H = od.H, W = od.W, pitch = od.pitch;
@@ -122,6 +124,8 @@ __global__ void __launch_bounds__(kThreads) k_extrema(const Desc *__restrict__ d
 // ----------------------------------------------------- bitmap compaction
 
 __global__ void __launch_bounds__(kThreads) k_bm_count(const Desc *__restrict__ d) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ int tmp[kThreads / 32 + 1];
   const int n = d->n_img;
   for (int c = blockIdx.x; c < d->n_bm_chunks; c += gridDim.x) {
@@ -141,6 +145,8 @@ __global__ void __launch_bounds__(kThreads) k_bm_count(const Desc *__restrict__ 
 // One block: per image, exclusive scan of chunk counts; candidate totals and
 // the prefix of candidate counts over images.
 __global__ void __launch_bounds__(1024) k_bm_scan(const Desc *__restrict__ d) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ int tmp[1024 / 32 + 1];
   const int n = d->n_img;
   int flat = 0;
@@ -169,6 +175,8 @@ __global__ void __launch_bounds__(1024) k_bm_scan(const Desc *__restrict__ d) {
 }
 
 __global__ void __launch_bounds__(kThreads) k_bm_emit(const Desc *__restrict__ d) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ int tmp[kThreads / 32 + 1];
   constexpr int WPT = kChunk / kThreads;  // words per thread
   const int n = d->n_img;
@@ -230,6 +238,8 @@ __device__ __forceinline__ int round_half_away(float v) {
 }
 
 __global__ void __launch_bounds__(kThreads) k_refine(const Desc *__restrict__ d) {
+  pdl_trigger();
+  pdl_wait();
   const int n = d->n_img;
   const int total = d->cand_flat[n];
   const int S = d->n_scales, bord = d->border, iters = d->max_iter;
@@ -317,25 +327,27 @@ cudaError_t extrema_set_attributes() { return cudaSuccess; }
 
 cudaError_t launch_extrema(const Desc *d, int oct, int n_scales, int grid, cudaStream_t s) {
   switch (n_scales) {
-    case 2: k_extrema<2><<<grid, kThreads, 0, s>>>(d, oct); break;
-    case 3: k_extrema<3><<<grid, kThreads, 0, s>>>(d, oct); break;
-    case 4: k_extrema<4><<<grid, kThreads, 0, s>>>(d, oct); break;
-    case 5: k_extrema<5><<<grid, kThreads, 0, s>>>(d, oct); break;
-    case 6: k_extrema<6><<<grid, kThreads, 0, s>>>(d, oct); break;
+    case 2: return launch_pdl(k_extrema<2>, grid, kThreads, 0, s, d, oct);
+    case 3: return launch_pdl(k_extrema<3>, grid, kThreads, 0, s, d, oct);
+    case 4: return launch_pdl(k_extrema<4>, grid, kThreads, 0, s, d, oct);
+    case 5: return launch_pdl(k_extrema<5>, grid, kThreads, 0, s, d, oct);
+    case 6: return launch_pdl(k_extrema<6>, grid, kThreads, 0, s, d, oct);
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_bm_compact(const Desc *d, int grid, cudaStream_t s) {
-  k_bm_count<<<grid, kThreads, 0, s>>>(d);
-  k_bm_scan<<<1, 1024, 0, s>>>(d);
-  k_bm_emit<<<grid, kThreads, 0, s>>>(d);
+  cudaError_t e = launch_pdl(k_bm_count, grid, kThreads, 0, s, d);
+  if (e == cudaSuccess) e = launch_pdl(k_bm_scan, 1, 1024, 0, s, d);
+  if (e == cudaSuccess) e = launch_pdl(k_bm_emit, grid, kThreads, 0, s, d);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
 cudaError_t launch_refine(const Desc *d, int grid, cudaStream_t s) {
-  k_refine<<<grid, kThreads, 0, s>>>(d);
+  cudaError_t e = launch_pdl(k_refine, grid, kThreads, 0, s, d);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

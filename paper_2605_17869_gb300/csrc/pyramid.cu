@@ -475,8 +475,10 @@ __global__ void __launch_bounds__(kThreads, TH == 32 ? (MODE == 0 ? 4 : 3) : 1)
   };
   if (threadIdx.x < 32) fill_chunk(0);
   __syncthreads();
+  pdl_wait();  // the source level is the previous kernel's output
   if (kAhead) issue_stage<R, TH, MODE>(geo[0], s_in);
   for (int k = 0; k < n_mine; k++) {
+    if (k + 1 == n_mine) pdl_trigger();  // successors launch during this block's last tile
     const TileGeo &g = geo[k & (2 * kGeoChunk - 1)];
     if (kAhead) {
       cp_async_wait_all();
@@ -504,6 +506,8 @@ __global__ void __launch_bounds__(kThreads, TH == 32 ? (MODE == 0 ? 4 : 3) : 1)
 template <int MODE>
 __global__ void __launch_bounds__(kThreads) k_blur_generic(const Desc *__restrict__ d, int oct,
                                                            int lvl_out, int R, BlurTaps tp) {
+  pdl_trigger();
+  pdl_wait();
   constexpr int TH = 32;
   const int ROWS = TH + 2 * R;
   extern __shared__ float4 smem4[];
@@ -609,18 +613,18 @@ cudaError_t launch_level_blur(const Desc *d, int oct, int lvl_out, int R, const 
 #define CASE_R(RR)                                                                               \
   case RR:                                                                                       \
     if (th_kind == TK_BLUR64) {                                                                  \
-      if (m3) k_blur<RR, 64, 3><<<grid, kThreads, smem_bytes<RR, 64, 3>(), s>>>(d, oct, lvl_out, t); \
-      else k_blur<RR, 64, 0><<<grid, kThreads, smem_bytes<RR, 64, 0>(), s>>>(d, oct, lvl_out, t);    \
+      return m3 ? launch_pdl(k_blur<RR, 64, 3>, grid, kThreads, smem_bytes<RR, 64, 3>(), s, d, oct, lvl_out, t) \
+                : launch_pdl(k_blur<RR, 64, 0>, grid, kThreads, smem_bytes<RR, 64, 0>(), s, d, oct, lvl_out, t); \
     } else {                                                                                     \
-      if (m3) k_blur<RR, 32, 3><<<grid, kThreads, smem_bytes<RR, 32, 3>(), s>>>(d, oct, lvl_out, t); \
-      else k_blur<RR, 32, 0><<<grid, kThreads, smem_bytes<RR, 32, 0>(), s>>>(d, oct, lvl_out, t);    \
+      return m3 ? launch_pdl(k_blur<RR, 32, 3>, grid, kThreads, smem_bytes<RR, 32, 3>(), s, d, oct, lvl_out, t) \
+                : launch_pdl(k_blur<RR, 32, 0>, grid, kThreads, smem_bytes<RR, 32, 0>(), s, d, oct, lvl_out, t); \
     }                                                                                            \
     break;
   switch (R) {
     SIFT_FOR_EACH_R(CASE_R)
     default:
-      if (m3) k_blur_generic<3><<<grid, kThreads, generic_smem_bytes(R), s>>>(d, oct, lvl_out, R, t);
-      else k_blur_generic<0><<<grid, kThreads, generic_smem_bytes(R), s>>>(d, oct, lvl_out, R, t);
+      return m3 ? launch_pdl(k_blur_generic<3>, grid, kThreads, generic_smem_bytes(R), s, d, oct, lvl_out, R, t)
+                : launch_pdl(k_blur_generic<0>, grid, kThreads, generic_smem_bytes(R), s, d, oct, lvl_out, R, t);
   }
 #undef CASE_R
   return cudaGetLastError();

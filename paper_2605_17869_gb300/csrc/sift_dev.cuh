@@ -116,6 +116,33 @@ struct BlurTaps {
   float2 wd[2 * kMaxR + 1];   // (w[j], w[j])
 };
 
+// Programmatic dependent launch. Every kernel after the first of a run is
+// launched so that its blocks may start while the previous kernel of the
+// stream is still finishing: a kernel first lets its own successor launch
+// (pdl_trigger), runs the prologue that needs only the descriptor (which the
+// host wrote before the run), and calls pdl_wait before it reads anything a
+// previous kernel produced and before it writes any global memory. pdl_wait
+// returns once the previous kernel has completed and its writes are visible;
+// in a kernel launched without the attribute both calls do nothing.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+
 // Index of the image owning flattened item t, given an exclusive prefix pre[0..n].
 __device__ __forceinline__ int find_owner(const int *pre, int n, int t) {
   int lo = 0, hi = n;
