@@ -44,7 +44,6 @@ __device__ __forceinline__ float sigma_of(const Desc *d, const RefRec &r) {
 // w*32 + l, w*32 + l + 128, ... and votes into its private column hist[w][.][l];
 // bin k is then the sum over w, then l, in that fixed order.
 __global__ void __launch_bounds__(kKpWarps * 32) k_orientation(const Desc *__restrict__ d) {
-  pdl_trigger();
   pdl_wait();
   __shared__ float hist[kKpWarps][kOriBins][32];
   __shared__ float hsum[kOriBins];
@@ -141,7 +140,6 @@ __global__ void __launch_bounds__(kKpWarps * 32) k_orientation(const Desc *__res
 // --------------------------------------------- oriented keypoint compaction
 
 __global__ void __launch_bounds__(kThreads) k_cc_count(const Desc *__restrict__ d) {
-  pdl_trigger();
   pdl_wait();
   __shared__ int tmp[kThreads / 32 + 1];
   constexpr int SPT = kChunk / kThreads;
@@ -163,7 +161,6 @@ __global__ void __launch_bounds__(kThreads) k_cc_count(const Desc *__restrict__ 
 // One block: per image scan of chunk counts, oriented totals, the final
 // (capped) counts, their prefix over images, and the caller's count output.
 __global__ void __launch_bounds__(1024) k_cc_scan(const Desc *__restrict__ d) {
-  pdl_trigger();
   pdl_wait();
   __shared__ int tmp[1024 / 32 + 1];
   const int n = d->n_img;
@@ -196,7 +193,6 @@ __global__ void __launch_bounds__(1024) k_cc_scan(const Desc *__restrict__ d) {
 }
 
 __global__ void __launch_bounds__(kThreads) k_cc_emit(const Desc *__restrict__ d) {
-  pdl_trigger();
   pdl_wait();
   __shared__ int tmp[kThreads / 32 + 1];
   constexpr int SPT = kChunk / kThreads;
@@ -238,7 +234,6 @@ __global__ void __launch_bounds__(kThreads) k_cc_emit(const Desc *__restrict__ d
 // in canonical order. The threshold is found by a bitwise search on the
 // response bits (responses are non-negative, so bit order = value order).
 __global__ void __launch_bounds__(1024) k_select(const Desc *__restrict__ d) {
-  pdl_trigger();
   pdl_wait();
   __shared__ int tmp[1024 / 32 + 1];
   const int n_img = d->n_img;
@@ -326,7 +321,6 @@ __constant__ float kDspScale[5] = {0.5f, 0.70710678118654752f, 1.0f, 1.414213562
 // Positions are kept relative to the integer keypoint pixel, so the
 // interpolation weights keep full FP32 precision in large octaves.
 __global__ void __launch_bounds__(kKpWarps * 32) k_descriptor(const Desc *__restrict__ d) {
-  pdl_trigger();
   pdl_wait();
   extern __shared__ float dsm[];
   __shared__ float red[kKpWarps];

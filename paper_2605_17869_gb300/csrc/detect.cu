@@ -124,7 +124,6 @@ __global__ void __launch_bounds__(kThreads) k_extrema(const Desc *__restrict__ d
 // ----------------------------------------------------- bitmap compaction
 
 __global__ void __launch_bounds__(kThreads) k_bm_count(const Desc *__restrict__ d) {
-  pdl_trigger();
   pdl_wait();
   __shared__ int tmp[kThreads / 32 + 1];
   const int n = d->n_img;
@@ -145,7 +144,6 @@ __global__ void __launch_bounds__(kThreads) k_bm_count(const Desc *__restrict__ 
 // One block: per image, exclusive scan of chunk counts; candidate totals and
 // the prefix of candidate counts over images.
 __global__ void __launch_bounds__(1024) k_bm_scan(const Desc *__restrict__ d) {
-  pdl_trigger();
   pdl_wait();
   __shared__ int tmp[1024 / 32 + 1];
   const int n = d->n_img;
@@ -175,7 +173,6 @@ __global__ void __launch_bounds__(1024) k_bm_scan(const Desc *__restrict__ d) {
 }
 
 __global__ void __launch_bounds__(kThreads) k_bm_emit(const Desc *__restrict__ d) {
-  pdl_trigger();
   pdl_wait();
   __shared__ int tmp[kThreads / 32 + 1];
   constexpr int WPT = kChunk / kThreads;  // words per thread
@@ -238,7 +235,6 @@ __device__ __forceinline__ int round_half_away(float v) {
 }
 
 __global__ void __launch_bounds__(kThreads) k_refine(const Desc *__restrict__ d) {
-  pdl_trigger();
   pdl_wait();
   const int n = d->n_img;
   const int total = d->cand_flat[n];

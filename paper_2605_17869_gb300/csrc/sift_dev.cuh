@@ -118,12 +118,14 @@ struct BlurTaps {
 
 // Programmatic dependent launch. Every kernel after the first of a run is
 // launched so that its blocks may start while the previous kernel of the
-// stream is still finishing: a kernel first lets its own successor launch
-// (pdl_trigger), runs the prologue that needs only the descriptor (which the
-// host wrote before the run), and calls pdl_wait before it reads anything a
-// previous kernel produced and before it writes any global memory. pdl_wait
-// returns once the previous kernel has completed and its writes are visible;
-// in a kernel launched without the attribute both calls do nothing.
+// stream is still finishing. A kernel runs the prologue that needs only the
+// descriptor (which the host wrote before the run) and calls pdl_wait before
+// it reads anything a previous kernel produced and before it writes any
+// global memory; pdl_wait returns once the previous kernel has completed and
+// its writes are visible. The level blurs and the extrema scan call
+// pdl_trigger when a block starts its last tile, letting their successor's
+// blocks take the SMs that the tail frees; other kernels let it launch when
+// they exit. In a kernel launched without the attribute both calls do nothing.
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
