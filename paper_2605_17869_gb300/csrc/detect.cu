@@ -28,12 +28,13 @@ constexpr int kThreads = 256;
 //  1. the contrast gate |D| > 0.5 T;
 //  2. a branch-free check against the four direct neighbours in its layer
 //     (left / right by warp shuffle, up / down from the adjacent rows; lanes 0
-//     and 31 skip their outer neighbour here, the exact test below covers it);
+//     and 31 skip their outer neighbour here, the exact test below covers it)
+//     and the same pixel in the two adjacent layers (registers);
 //  3. for the few pixels that pass, the exact 26-neighbour test, done by the
 //     whole warp per pixel (lane k < 26 compares one neighbour, then a vote).
 // Only step 3 decides; steps 1-2 merely skip pixels that cannot pass it.
 template <int S>
-__global__ void __launch_bounds__(kThreads) k_extrema(const Desc *__restrict__ d, int oct) {
+__global__ void __launch_bounds__(kThreads, 3) k_extrema(const Desc *__restrict__ d, int oct) {
   constexpr int ND = S + 2;
   constexpr int RR = kExtTH + 2;  // rows held: y0 - 1 .. y0 + kExtTH
   constexpr int WPB = kThreads / 32;
@@ -94,8 +95,11 @@ __global__ void __launch_bounds__(kThreads) k_extrema(const Desc *__restrict__ d
           const float lf = __shfl_up_sync(0xffffffffu, cv, 1);
           const float rt = __shfl_down_sync(0xffffffffu, cv, 1);
           const float up = D[r - 1][s], dn = D[r + 1][s];
-          const bool pmax = cv > up && cv > dn && (lane == 0 || cv > lf) && (lane == 31 || cv > rt);
-          const bool pmin = cv < up && cv < dn && (lane == 0 || cv < lf) && (lane == 31 || cv < rt);
+          const float sb = D[r][s - 1], sa = D[r][s + 1];  // same pixel, adjacent scales
+          const bool pmax = cv > up && cv > dn && cv > sb && cv > sa && (lane == 0 || cv > lf) &&
+                            (lane == 31 || cv > rt);
+          const bool pmin = cv < up && cv < dn && cv < sb && cv < sa && (lane == 0 || cv < lf) &&
+                            (lane == 31 || cv < rt);
           const bool ok = inb && fabsf(cv) > thr && (pmax || pmin);
           unsigned surv = __ballot_sync(0xffffffffu, ok);
           while (surv) {
