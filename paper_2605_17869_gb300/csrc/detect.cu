@@ -29,7 +29,8 @@ constexpr int kThreads = 256;
 //  2. a branch-free check against the four direct neighbours in its layer
 //     (left / right by warp shuffle, up / down from the adjacent rows; lanes 0
 //     and 31 skip their outer neighbour here, the exact test below covers it)
-//     and the same pixel in the two adjacent layers (registers);
+//     and the same column of rows r - 1 .. r + 1 in the two adjacent layers
+//     (registers); 10 of the 26 neighbours in all;
 //  3. for the few pixels that pass, the exact 26-neighbour test, done by the
 //     whole warp per pixel (lane k < 26 compares one neighbour, then a vote).
 // Only step 3 decides; steps 1-2 merely skip pixels that cannot pass it.
@@ -95,11 +96,16 @@ __global__ void __launch_bounds__(kThreads, 3) k_extrema(const Desc *__restrict_
           const float lf = __shfl_up_sync(0xffffffffu, cv, 1);
           const float rt = __shfl_down_sync(0xffffffffu, cv, 1);
           const float up = D[r - 1][s], dn = D[r + 1][s];
-          const float sb = D[r][s - 1], sa = D[r][s + 1];  // same pixel, adjacent scales
-          const bool pmax = cv > up && cv > dn && cv > sb && cv > sa && (lane == 0 || cv > lf) &&
-                            (lane == 31 || cv > rt);
-          const bool pmin = cv < up && cv < dn && cv < sb && cv < sa && (lane == 0 || cv < lf) &&
-                            (lane == 31 || cv < rt);
+          // Same column in the adjacent layers, rows r - 1 .. r + 1 (registers).
+          const float s0 = D[r][s - 1], s1 = D[r][s + 1];
+          const float s2 = D[r - 1][s - 1], s3 = D[r + 1][s - 1];
+          const float s4 = D[r - 1][s + 1], s5 = D[r + 1][s + 1];
+          const float hi = fmaxf(fmaxf(fmaxf(up, dn), fmaxf(s0, s1)),
+                                 fmaxf(fmaxf(s2, s3), fmaxf(s4, s5)));
+          const float lo = fminf(fminf(fminf(up, dn), fminf(s0, s1)),
+                                 fminf(fminf(s2, s3), fminf(s4, s5)));
+          const bool pmax = cv > hi && (lane == 0 || cv > lf) && (lane == 31 || cv > rt);
+          const bool pmin = cv < lo && (lane == 0 || cv < lf) && (lane == 31 || cv < rt);
           const bool ok = inb && fabsf(cv) > thr && (pmax || pmin);
           unsigned surv = __ballot_sync(0xffffffffu, ok);
           while (surv) {
