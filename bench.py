@@ -185,6 +185,22 @@ def whole_job_value(world, mpix_per_rank, steps, max_ms):
     return world * mpix_per_rank * steps / (max_ms / 1e3)
 
 
+def _alg_class_bytes(shapes, upsample, S=3, min_side=16):
+    """Algorithmic bytes of one step for the base blur and the extrema scan.
+    Base: the input read once (4 B per input pixel) and level 0 of octave 0
+    written once (4 B per octave pixel). Extrema: the S + 3 levels of every
+    octave read once (the DoG is formed on the fly) plus the candidate bitmap
+    (S bits per octave pixel)."""
+    base = ext = 0
+    for (h, w) in shapes:
+        H, W = (2 * h, 2 * w) if upsample else (h, w)
+        base += 4 * h * w + 4 * H * W
+        while min(H, W) >= min_side:
+            ext += 4 * (S + 3) * H * W + S * H * W // 8
+            H, W = H // 2, W // 2
+    return {"base": base, "extrema": ext}
+
+
 def timed_steps(torch, fn, steps, warmup, flush, stream):
     for _ in range(warmup):
         fn()
@@ -347,6 +363,24 @@ def gpu_arm(args, rank, world, pool, n_workers):
                 "peak_source": "hbm_gbs, " + ("of measured (MEASURED_PEAKS.json)"
                                               if peak_kind == "measured" else "of fallback")}
 
+    # Per-class rooflines (CUDA-event time of each class inside the graph).
+    cls_bytes = _alg_class_bytes(shapes, True)
+    cls_bytes["blur"] = alg_step
+    nominal = 8000.0
+    per_class = {}
+    for k in ("blur", "base", "extrema"):
+        ms = acc.get(k, (0.0, 0))[0] / reps
+        if ms > 0:
+            gbs = cls_bytes[k] / (ms / 1e3) / 1e9
+            per_class[k] = {"alg_bytes_per_step": int(cls_bytes[k]), "ms_per_step": round(ms, 4),
+                            "achieved_gbs": round(gbs, 1), "frac_of_measured": round(gbs / peak, 4),
+                            "frac_of_nominal_8tbs": round(gbs / nominal, 4)}
+    for k in ("keypoint", "descriptor"):
+        ms = acc.get(k, (0.0, 0))[0] / reps
+        if ms > 0:
+            per_class[k] = {"ms_per_step": round(ms, 4),
+                            "keypoints_per_s": round(kpts / (ms / 1e3), 1)}
+
     # End to end: pinned host images -> device -> extract -> counts + results back.
     host = [torch.from_numpy(np.ascontiguousarray(im)).pin_memory() for im in imgs_np]
     dev_in = [torch.empty_like(h, device="cuda") for h in host]
@@ -429,6 +463,7 @@ def gpu_arm(args, rank, world, pool, n_workers):
         "gpu_launches_per_step": launches_per_step,
         "kernel_ms_per_step": kernel_share,
         "roofline": roofline,
+        "per_class_roofline": per_class,
         "e2e": e2e,
         "clocks": clock_info,
         "accuracy": accuracy,
