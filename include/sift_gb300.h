@@ -158,6 +158,24 @@ sift_status sift_extract_noalloc(const sift_params *p, const float *img_dev, int
                                  int pitch_elems, void *stream, sift_kpts_dev out_kpts,
                                  float *out_desc_dev, int *out_count_dev);
 
+/* Symmetric ratio-test matcher (§3.3 "Descriptor Matching", first backend).
+ * The similarity matrix of two descriptor sets is formed from fp16
+ * tensor-core products (tcgen05, FP32 accumulation): for every descriptor
+ * its nearest neighbour in the other set (largest dot product, ties to the
+ * smaller index) and the second nearest. A pair (i, j) is kept when each is
+ * the other's nearest neighbour and both pass Lowe's ratio test
+ * d1 < ratio * d2 on the unit-vector distance d = sqrt(2 - 2 s).
+ *   desc_a: n_a x 128 FP32 (device, row-major, 16-byte aligned, unit
+ *   vectors, e.g. an extraction's output); desc_b: n_b x 128 likewise.
+ *   out_match_a: device, n_a ints: j for a kept pair (i, j), else -1; -2 in
+ *   every entry if a bounded device wait gave up (the run is not valid).
+ * Asynchronous on `stream`; the handle keeps a small workspace that grows with
+ * n_a + n_b. Errors: SIFT_E_INVALID for a null pointer, n_a or n_b outside
+ * [0, 65536] or ratio outside (0, 1]; SIFT_E_OOM / SIFT_E_CUDA. With fewer
+ * than two descriptors on either side no pair is kept. */
+sift_status sift_match(sift_handle *h, const float *desc_a, int n_a, const float *desc_b, int n_b,
+                       float ratio, void *stream, int *out_match_a);
+
 /* Statistics of the last extraction on this handle, read after synchronising
  * its stream. stats receives, per image i of the last call (up to max_images):
  *   stats[4*i+0] candidates (extrema after the gate), stats[4*i+1] refined

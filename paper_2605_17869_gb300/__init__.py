@@ -10,7 +10,7 @@ using this package raises.
 from __future__ import annotations
 
 import ctypes
-from ctypes import byref, c_double, c_int, c_size_t, c_uint64, c_void_p
+from ctypes import byref, c_double, c_float, c_int, c_size_t, c_uint64, c_void_p
 from dataclasses import dataclass
 
 from . import _abi
@@ -101,6 +101,14 @@ def sift_extract_noalloc(params: SiftParams, img_ptr: int, H: int, W: int, pitch
     return _check(_lib().sift_extract_noalloc(byref(params), c_void_p(img_ptr), H, W, pitch,
                                               c_void_p(stream), kpts, c_void_p(desc_ptr),
                                               c_void_p(count_ptr)), what="sift_extract_noalloc")
+
+
+def sift_match(handle, a_ptr: int, n_a: int, b_ptr: int, n_b: int, ratio: float, stream: int,
+               out_ptr: int) -> int:
+    """Symmetric ratio-test matcher on fp16 tensor cores (see the C header)."""
+    return _check(_lib().sift_match(handle, c_void_p(a_ptr), n_a, c_void_p(b_ptr), n_b,
+                                    c_float(ratio), c_void_p(stream), c_void_p(out_ptr)),
+                  handle, "sift_match")
 
 
 def sift_last_stats(handle, n_images: int):
@@ -343,6 +351,21 @@ class Extractor:
                 f = Features(*(t.clone() for t in (f.x, f.y, f.sigma, f.angle, f.response,
                                                    f.octave, f.layer, f.desc)), n)
             out.append(f)
+        return out
+
+    def match(self, desc_a, desc_b, ratio: float = 0.8, stream=None):
+        """Mutual nearest neighbours of two descriptor sets (N x 128 float32 CUDA
+        tensors) passing the ratio test both ways: an int32 tensor m with
+        m[i] = j for each kept pair (i, j), else -1 (queued on the stream)."""
+        torch = _torch()
+        for t in (desc_a, desc_b):
+            if not (t.is_cuda and t.dtype == torch.float32 and t.dim() == 2 and t.shape[1] == 128
+                    and t.is_contiguous()):
+                raise SiftError(SIFT_E_INVALID, "descriptors must be contiguous N x 128 float32 CUDA tensors")
+        s = stream if stream is not None else torch.cuda.current_stream()
+        out = torch.empty(desc_a.shape[0], dtype=torch.int32, device=desc_a.device)
+        sift_match(self.handle, desc_a.data_ptr(), desc_a.shape[0], desc_b.data_ptr(),
+                   desc_b.shape[0], ratio, s.cuda_stream, out.data_ptr())
         return out
 
     def stats(self, n_images: int = 1):

@@ -53,6 +53,8 @@ SIGNATURES = {
                                    POINTER(SiftKptsDev), POINTER(c_void_p), c_void_p]),
     "sift_extract_noalloc": (c_int, [POINTER(SiftParams), c_void_p, c_int, c_int, c_int, c_void_p,
                                      SiftKptsDev, c_void_p, c_void_p]),
+    "sift_match": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_int, c_float, c_void_p,
+                           c_void_p]),
     "sift_last_stats": (c_int, [c_void_p, POINTER(c_int), c_int]),
     "sift_pyramid_size": (c_int, [c_void_p, c_int, c_int, POINTER(c_int), POINTER(c_size_t)]),
     "sift_build_pyramid": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, c_void_p,

@@ -19,6 +19,10 @@ struct sift_handle {
   Engine *eng = nullptr;
   std::string err;
   bool serving = false;
+  void *match_ws = nullptr;  // matcher workspace (stream-ordered allocation)
+  size_t match_cap = 0;
+  cudaStream_t match_stream = nullptr;
+  bool match_attr = false;
 };
 
 static sift_status fail(sift_handle *h, sift_status st, const std::string &m) {
@@ -76,8 +80,43 @@ sift_status sift_create(const sift_params *p, sift_handle **out) {
 
 sift_status sift_destroy(sift_handle *h) {
   if (!h) return SIFT_E_INVALID;
+  if (h->match_ws) {
+    cudaStreamSynchronize(h->match_stream);
+    cudaFree(h->match_ws);
+  }
   delete h->eng;
   delete h;
+  return SIFT_OK;
+}
+
+sift_status sift_match(sift_handle *h, const float *desc_a, int n_a, const float *desc_b, int n_b,
+                       float ratio, void *stream, int *out_match_a) {
+  if (!h) return SIFT_E_INVALID;
+  if (n_a < 0 || n_b < 0 || n_a > 65536 || n_b > 65536)
+    return fail(h, SIFT_E_INVALID, "set sizes must be in [0, 65536]");
+  if (!(ratio > 0.f && ratio <= 1.f)) return fail(h, SIFT_E_INVALID, "ratio must be in (0, 1]");
+  if ((n_a > 0 && (!desc_a || !out_match_a)) || (n_b > 0 && !desc_b))
+    return fail(h, SIFT_E_INVALID, "null pointer argument");
+  if (n_a == 0) return SIFT_OK;
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!h->match_attr) {
+    if (sift::match_set_attributes() != cudaSuccess) return fail(h, SIFT_E_CUDA, "matcher attributes");
+    h->match_attr = true;
+  }
+  const size_t need = sift::match_workspace_bytes(n_a, n_b);
+  if (need > h->match_cap) {
+    if (h->match_ws) cudaFreeAsync(h->match_ws, h->match_stream ? h->match_stream : s);
+    h->match_ws = nullptr;
+    h->match_cap = 0;
+    if (cudaMallocAsync(&h->match_ws, need, s) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, SIFT_E_OOM, "matcher workspace allocation failed");
+    }
+    h->match_cap = need;
+  }
+  h->match_stream = s;
+  const cudaError_t e = sift::launch_match(desc_a, n_a, desc_b, n_b, ratio, h->match_ws, out_match_a, s);
+  if (e != cudaSuccess) return fail(h, SIFT_E_CUDA, std::string("matcher: ") + cudaGetErrorString(e));
   return SIFT_OK;
 }
 

@@ -185,6 +185,11 @@ cudaError_t launch_ori_compact(const Desc *d, int grid, cudaStream_t s);
 cudaError_t launch_select(const Desc *d, int grid, cudaStream_t s);
 cudaError_t launch_descriptor(const Desc *d, int grid, cudaStream_t s);
 cudaError_t descriptor_set_attributes();
+// Matcher (match.cu)
+size_t match_workspace_bytes(int n_a, int n_b);
+cudaError_t match_set_attributes();
+cudaError_t launch_match(const float *A, int n_a, const float *B, int n_b, float ratio, void *ws,
+                         int *out, cudaStream_t s);
 int descriptor_smem_bytes();
 
 }  // namespace sift
