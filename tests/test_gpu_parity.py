@@ -195,3 +195,32 @@ def test_batch_composition_invariance():
     assert rev == single[::-1]
     sub = [_digest(f) for f in ex.extract_batch([imgs[2], imgs[0]])]
     assert sub == [single[2], single[0]]
+
+
+# ------------------------------------------------------------------ full size
+
+def _oracle_full(args):
+    idx, = args
+    from oracle import sift_oracle as so_  # noqa: PLC0415 (worker process)
+    from workloads import synth as sy  # noqa: PLC0415
+    img = sy.homography_sequence(0).images[idx]
+    return so_.extract(img, so_.Params(upsample=True, max_kpts=8000), keep_pyramid=True)
+
+
+def test_full_size_batch_matches_oracle():
+    """The timed workload itself: 6 x 1000x750, 2x upsampled, cap 8000, one
+    batched call (the launch configuration the benchmark times), every image
+    against the FP64 oracle; and the same batch is bitwise identical to the
+    per-image calls."""
+    import multiprocessing as mp
+    seq = synth.homography_sequence(0)
+    imgs = [torch.from_numpy(im).cuda() for im in seq.images]
+    ex = pkg.Extractor(upsample=1, max_kpts=8000)
+    feats = ex.extract_batch(imgs)
+    single = [_digest(ex.extract(im)) for im in imgs]
+    assert [_digest(f) for f in feats] == single
+    with mp.get_context("spawn").Pool(min(6, mp.cpu_count())) as pool:
+        refs = pool.map(_oracle_full, [(i,) for i in range(len(imgs))])
+    p = _oracle_params(upsample=True, max_kpts=8000)
+    for i, (ref, f) in enumerate(zip(refs, feats)):
+        _assert_parity(ref, f, p, f"full-size image {i}")
