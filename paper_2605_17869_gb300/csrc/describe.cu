@@ -48,6 +48,7 @@ __global__ void __launch_bounds__(kKpWarps * 32) k_orientation(const Desc *__res
   __shared__ float hist[kKpWarps][kOriBins][32];
   __shared__ float hsum[kOriBins];
   __shared__ float hsm[kOriBins];
+  __shared__ float win[kOriWin];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = d->n_img;
   const int total = d->cand_flat[n];
@@ -73,27 +74,61 @@ __global__ void __launch_bounds__(kKpWarps * 32) k_orientation(const Desc *__res
     const int R = (int)floorf(3.0f * sw + 0.5f);
     const float ninv = -1.0f / (2.0f * sw * sw);
     for (int k = 0; k < kOriBins; k++) hist[warp][k][lane] = 0.f;
-    const int side = 2 * R + 1, ns = side * side;
-    for (int idx = tid; idx < ns; idx += kKpWarps * 32) {
-      const int jj = idx / side;
-      const int i = idx - jj * side - R, j = jj - R;
-      const int px = r.x + i, py = r.y + j;
-      if (px < 1 || px > od.W - 2 || py < 1 || py > od.H - 2) continue;
-      const float *p = L + (long long)py * od.pitch + px;
-      const float dx = __ldg(p + 1) - __ldg(p - 1);
-      const float dy = __ldg(p + od.pitch) - __ldg(p - od.pitch);
-      const float mag = sqrtf(dx * dx + dy * dy);
-      float th = atan2f(dy, dx);
-      if (th < 0.f) th += kTwoPi;
-      int bin = (int)floorf(th * ((float)kOriBins / kTwoPi) + 0.5f);
-      if (bin >= kOriBins) bin -= kOriBins;
-      hist[warp][bin][lane] += expf((float)(i * i + j * j) * ninv) * mag;
+    // The window's pixels are staged in shared memory in bands of B sample
+    // rows (B + 2 pixel rows of width 2R + 3, coalesced loads); thread tid
+    // takes samples tid, tid + 128, ... of each band in row-major order.
+    const int side = 2 * R + 1, wd = side + 2;
+    const int B = kOriWin / wd - 2;  // >= 1: the parameter check bounds R
+    for (int jb = -R; jb <= R; jb += B) {
+      const int nb = min(B, R - jb + 1);
+      for (int rr = warp; rr < nb + 2; rr += kKpWarps) {
+        const int gy = r.y + jb - 1 + rr;
+        float *dst = win + rr * wd;
+        if (gy >= 0 && gy < od.H) {
+          const float *src = L + (long long)gy * od.pitch;
+          for (int c = lane; c < wd; c += 32) {
+            const int gx = r.x - R - 1 + c;
+            dst[c] = (gx >= 0 && gx < od.W) ? __ldg(src + gx) : 0.f;
+          }
+        } else {
+          for (int c = lane; c < wd; c += 32) dst[c] = 0.f;
+        }
+      }
+      __syncthreads();
+      const int ns = nb * side;
+      for (int idx = tid; idx < ns; idx += kKpWarps * 32) {
+        const int jj = idx / side;
+        const int i = idx - jj * side - R, j = jb + jj;
+        const int px = r.x + i, py = r.y + j;
+        if (px < 1 || px > od.W - 2 || py < 1 || py > od.H - 2) continue;
+        const float *w = win + (jj + 1) * wd + (i + R + 1);
+        const float dx = w[1] - w[-1];
+        const float dy = w[wd] - w[-wd];
+        const float mag = sqrtf(dx * dx + dy * dy);
+        float th = atan2f(dy, dx);
+        if (th < 0.f) th += kTwoPi;
+        int bin = (int)floorf(th * ((float)kOriBins / kTwoPi) + 0.5f);
+        if (bin >= kOriBins) bin -= kOriBins;
+        hist[warp][bin][lane] += expf((float)(i * i + j * j) * ninv) * mag;
+      }
+      __syncthreads();
     }
     __syncthreads();
     if (tid < kOriBins) {
-      float s = 0.f;
-      for (int w = 0; w < kKpWarps; w++)
-        for (int q = 0; q < 32; q++) s += hist[w][tid][q];
+      // Bin tid: per warp, the 32 lane columns starting at lane tid % 32 (so
+      // the 32 threads read 32 distinct banks), then the warp partials in
+      // warp order.
+      float pw[kKpWarps];
+#pragma unroll
+      for (int w = 0; w < kKpWarps; w++) {
+        float s = 0.f;
+#pragma unroll 8
+        for (int q = 0; q < 32; q++) s += hist[w][tid][(q + tid) & 31];
+        pw[w] = s;
+      }
+      float s = pw[0];
+#pragma unroll
+      for (int w = 1; w < kKpWarps; w++) s += pw[w];
       hsum[tid] = s;
     }
     __syncthreads();
@@ -158,38 +193,30 @@ __global__ void __launch_bounds__(kThreads) k_cc_count(const Desc *__restrict__ 
   }
 }
 
-// One block: per image scan of chunk counts, oriented totals, the final
-// (capped) counts, their prefix over images, and the caller's count output.
-__global__ void __launch_bounds__(1024) k_cc_scan(const Desc *__restrict__ d) {
+// One block: per image (one warp each), scan of chunk counts, oriented totals,
+// the final (capped) counts and the caller's count output; then the prefix of
+// final counts over images.
+__global__ void __launch_bounds__(512) k_cc_scan(const Desc *__restrict__ d) {
   pdl_wait();
-  __shared__ int tmp[1024 / 32 + 1];
-  const int n = d->n_img;
-  int flat = 0;
-  for (int b = 0; b < n; b++) {
+  __shared__ int s_nf[kMaxImg];
+  const int n = d->n_img, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int b = warp; b < n; b += 16) {
     const ImgDev &im = d->img[b];
-    int carry = 0;
-    for (int base = 0; base < im.cc_n; base += blockDim.x) {
-      const int i = base + threadIdx.x;
-      const int v = i < im.cc_n ? d->cc_cnt[im.cc0 + i] : 0;
-      int tot;
-      const int ex = block_excl_scan(v, tmp, &tot);
-      if (i < im.cc_n) d->cc_off[im.cc0 + i] = carry + ex;
-      carry += tot;
-    }
+    const int carry = warp_excl_scan_array(d->cc_cnt + im.cc0, d->cc_off + im.cc0, im.cc_n);
     const int no = min(carry, im.ori_cap);
     const int nf = min(no, im.kcap);
-    if (threadIdx.x == 0) {
+    if (lane == 0) {
       ImgCounters &k = d->cnt[b];
       k.n_ori_raw = carry;
       k.n_ori = no;
       k.n_fin = nf;
       k.flags |= (carry > im.ori_cap ? TF_ORI : 0) | (no > im.kcap ? TF_TOPK : 0);
-      d->fin_flat[b] = flat;
       if (im.ocount) *im.ocount = nf;
+      s_nf[b] = nf;
     }
-    flat += nf;
   }
-  if (threadIdx.x == 0) d->fin_flat[n] = flat;
+  __syncthreads();
+  if (warp == 0) warp_excl_scan_small(s_nf, d->fin_flat, n);
 }
 
 __global__ void __launch_bounds__(kThreads) k_cc_emit(const Desc *__restrict__ d) {
@@ -322,8 +349,10 @@ __constant__ float kDspScale[5] = {0.5f, 0.70710678118654752f, 1.0f, 1.414213562
 // interpolation weights keep full FP32 precision in large octaves.
 __global__ void __launch_bounds__(kKpWarps * 32) k_descriptor(const Desc *__restrict__ d) {
   pdl_wait();
-  extern __shared__ float dsm[];
+  extern __shared__ __align__(16) float dsm[];
   __shared__ float red[kKpWarps];
+  __shared__ int s_row_lo[kKpWarps * 32], s_row_pre[kKpWarps * 32 + 1];
+  __shared__ int s_scan[kKpWarps + 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float *hist = dsm + warp * (kDescLen * 32);
   const int n = d->n_img;
@@ -356,23 +385,72 @@ __global__ void __launch_bounds__(kKpWarps * 32) k_descriptor(const Desc *__rest
     const float th = angle * (kTwoPi / 360.0f);
     float st, ct;
     sincosf(th, &st, &ct);
-    for (int k = 0; k < kDescLen; k++) hist[k * 32 + lane] = 0.f;
+    {
+      float4 *h4 = reinterpret_cast<float4 *>(hist);
+#pragma unroll 8
+      for (int k = lane; k < kDescLen * 8; k += 32) h4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncwarp();
     if (!d->dsp) {
-      const int side = 2 * R + 1, ns = side * side;
-      for (int idx = tid; idx < ns; idx += kKpWarps * 32) {
-        const int jj = idx / side;
-        const int i = idx - jj * side - R, jy = jj - R;
-        const int px = r.x + i, py = r.y + jy;
-        if (px < 1 || px > od.W - 2 || py < 1 || py > od.H - 2) continue;
-        const float ox = (float)i - r.dx, oy = (float)jy - r.dy;
-        const float rx = (ct * ox + st * oy) * inv_w;
-        const float ry = (-st * ox + ct * oy) * inv_w;
-        const float u = rx + 1.5f, v = ry + 1.5f;
-        if (!(u > -1.f && u < 4.f && v > -1.f && v < 4.f)) continue;
-        const float *p = L + (long long)py * od.pitch + px;
-        const float gx = __ldg(p + 1) - __ldg(p - 1);
-        const float gy = __ldg(p + od.pitch) - __ldg(p - od.pitch);
-        desc_vote(hist, lane, rx, ry, gx, gy, th);
+      // Samples: integer offsets (i, jy) in [-R, R]^2 inside the image whose
+      // rotated bin coordinates fall in (-1, 4)^2, i.e. inside a square of half
+      // side h = 2.5 bins around the keypoint. Each row's candidates are cut to
+      // an interval (a superset of the square's chord, widened by 2 pixels so
+      // that rounding can only add candidates), and the exact test below
+      // decides, so the sample set is the same as a sweep of the whole window.
+      // Thread q takes samples q, q + 128, ... of the concatenated intervals.
+      const float h = 2.5f * wbin;
+      const int ilo = max(-R, 1 - r.x), ihi = min(R, od.W - 2 - r.x);
+      const int jlo = max(-R, 1 - r.y), jhi = min(R, od.H - 2 - r.y);
+      for (int j0 = jlo; j0 <= jhi; j0 += kKpWarps * 32) {
+        const int nr = min(kKpWarps * 32, jhi - j0 + 1);
+        int len = 0;
+        if (tid < nr) {
+          const float oy = (float)(j0 + tid) - r.dy;
+          float lo = -1e30f, hi = 1e30f;
+          // slab a * ox + b in (-h, h) for (a, b) = (ct, st * oy), (-st, ct * oy)
+#pragma unroll
+          for (int k = 0; k < 2; k++) {
+            const float a = k ? -st : ct, b = k ? ct * oy : st * oy;
+            if (fabsf(a) * (float)(R + 1) < 1.0f) {
+              if (fabsf(b) >= h + 2.0f) hi = -1e30f;  // |a * ox| < 1: the row misses the slab
+            } else {
+              const float e0 = (-h - b) / a, e1 = (h - b) / a;
+              lo = fmaxf(lo, fminf(e0, e1));
+              hi = fminf(hi, fmaxf(e0, e1));
+            }
+          }
+          int a0 = ilo, a1 = ihi;
+          if (hi < lo) {
+            a1 = a0 - 1;
+          } else {
+            if (lo + r.dx > (float)ilo) a0 = max(ilo, (int)floorf(lo + r.dx) - 2);
+            if (hi + r.dx < (float)ihi) a1 = min(ihi, (int)ceilf(hi + r.dx) + 2);
+          }
+          len = max(0, a1 - a0 + 1);
+          s_row_lo[tid] = a0;
+        }
+        int tot;
+        const int ex = block_excl_scan(len, s_scan, &tot);
+        if (tid < nr) s_row_pre[tid] = ex;
+        if (tid == 0) s_row_pre[nr] = tot;
+        __syncthreads();
+        int row = 0;
+        for (int q = tid; q < tot; q += kKpWarps * 32) {
+          while (s_row_pre[row + 1] <= q) row++;
+          const int jy = j0 + row;
+          const int i = s_row_lo[row] + (q - s_row_pre[row]);
+          const float ox = (float)i - r.dx, oy = (float)jy - r.dy;
+          const float rx = (ct * ox + st * oy) * inv_w;
+          const float ry = (-st * ox + ct * oy) * inv_w;
+          const float u = rx + 1.5f, v = ry + 1.5f;
+          if (!(u > -1.f && u < 4.f && v > -1.f && v < 4.f)) continue;
+          const float *p = L + (long long)(r.y + jy) * od.pitch + (r.x + i);
+          const float gx = __ldg(p + 1) - __ldg(p - 1);
+          const float gy = __ldg(p + od.pitch) - __ldg(p - od.pitch);
+          desc_vote(hist, lane, rx, ry, gx, gy, th);
+        }
+        __syncthreads();
       }
     } else {
       for (int f = 0; f < 5; f++) {
@@ -402,12 +480,20 @@ __global__ void __launch_bounds__(kKpWarps * 32) k_descriptor(const Desc *__rest
       }
     }
     __syncthreads();
-    // Bin tid: sum over warps, then lanes.
-    float val = 0.f;
+    // Bin tid: per warp, the 32 lane columns starting at lane tid % 32 (32
+    // distinct banks across a warp), then the warp partials in warp order.
+    float pw[kKpWarps];
+#pragma unroll
     for (int w = 0; w < kKpWarps; w++) {
       const float *h = dsm + w * (kDescLen * 32) + tid * 32;
-      for (int l = 0; l < 32; l++) val += h[l];
+      float s = 0.f;
+#pragma unroll 8
+      for (int l = 0; l < 32; l++) s += h[(l + tid) & 31];
+      pw[w] = s;
     }
+    float val = pw[0];
+#pragma unroll
+    for (int w = 1; w < kKpWarps; w++) val += pw[w];
     float *out = im.odesc + (long long)j * kDescLen;
     const float sq = block_sum_f(val * val, red);
     if (sq > 0.f) {
@@ -433,7 +519,7 @@ cudaError_t launch_orientation(const Desc *d, int grid, cudaStream_t s) {
 
 cudaError_t launch_ori_compact(const Desc *d, int grid, cudaStream_t s) {
   cudaError_t e = launch_pdl(k_cc_count, grid, kThreads, 0, s, d);
-  if (e == cudaSuccess) e = launch_pdl(k_cc_scan, 1, 1024, 0, s, d);
+  if (e == cudaSuccess) e = launch_pdl(k_cc_scan, 1, 512, 0, s, d);
   if (e == cudaSuccess) e = launch_pdl(k_cc_emit, grid, kThreads, 0, s, d);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();

@@ -151,35 +151,26 @@ __global__ void __launch_bounds__(kThreads) k_bm_count(const Desc *__restrict__ 
   }
 }
 
-// One block: per image, exclusive scan of chunk counts; candidate totals and
-// the prefix of candidate counts over images.
-__global__ void __launch_bounds__(1024) k_bm_scan(const Desc *__restrict__ d) {
+// One block: per image (one warp each), exclusive scan of chunk counts and the
+// candidate totals; then the prefix of candidate counts over images.
+__global__ void __launch_bounds__(512) k_bm_scan(const Desc *__restrict__ d) {
   pdl_wait();
-  __shared__ int tmp[1024 / 32 + 1];
-  const int n = d->n_img;
-  int flat = 0;
-  for (int b = 0; b < n; b++) {
+  __shared__ int s_nc[kMaxImg];
+  const int n = d->n_img, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int b = warp; b < n; b += 16) {
     const ImgDev &im = d->img[b];
-    int carry = 0;
-    for (int base = 0; base < im.bmc_n; base += blockDim.x) {
-      const int i = base + threadIdx.x;
-      const int v = i < im.bmc_n ? d->bm_cnt[im.bmc0 + i] : 0;
-      int tot;
-      const int ex = block_excl_scan(v, tmp, &tot);
-      if (i < im.bmc_n) d->bm_off[im.bmc0 + i] = carry + ex;
-      carry += tot;
-    }
+    const int carry = warp_excl_scan_array(d->bm_cnt + im.bmc0, d->bm_off + im.bmc0, im.bmc_n);
     const int nc = min(carry, im.cand_cap);
-    if (threadIdx.x == 0) {
+    if (lane == 0) {
       ImgCounters &k = d->cnt[b];
       k.n_cand_raw = carry;
       k.n_cand = nc;
       k.flags = carry > im.cand_cap ? TF_CAND : 0;
-      d->cand_flat[b] = flat;
+      s_nc[b] = nc;
     }
-    flat += nc;
   }
-  if (threadIdx.x == 0) d->cand_flat[n] = flat;
+  __syncthreads();
+  if (warp == 0) warp_excl_scan_small(s_nc, d->cand_flat, n);
 }
 
 __global__ void __launch_bounds__(kThreads) k_bm_emit(const Desc *__restrict__ d) {
@@ -345,7 +336,7 @@ cudaError_t launch_extrema(const Desc *d, int oct, int n_scales, int grid, cudaS
 
 cudaError_t launch_bm_compact(const Desc *d, int grid, cudaStream_t s) {
   cudaError_t e = launch_pdl(k_bm_count, grid, kThreads, 0, s, d);
-  if (e == cudaSuccess) e = launch_pdl(k_bm_scan, 1, 1024, 0, s, d);
+  if (e == cudaSuccess) e = launch_pdl(k_bm_scan, 1, 512, 0, s, d);
   if (e == cudaSuccess) e = launch_pdl(k_bm_emit, grid, kThreads, 0, s, d);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();

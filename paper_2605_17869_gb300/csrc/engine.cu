@@ -87,6 +87,13 @@ sift_status validate_params(const sift_params &p, std::string *why) {
     rmax = r < 0 ? -1 : std::max(rmax, r);
   }
   if (rmax < 0) return bad("sigma0 too large: blur radius above 16");
+  {
+    // The orientation window (radius 4.5 sigma at the largest keypoint scale,
+    // s + ds < S + 1/2) is staged in bands of kOriWin / (2R + 3) - 2 rows.
+    const double smax = (double)p.sigma0 * std::pow(2.0, (p.n_scales + 1.0) / p.n_scales);
+    const int rori = (int)std::floor(4.5 * smax + 0.5);
+    if (kOriWin / (2 * rori + 3) - 2 < 1) return bad("sigma0 too large for the orientation window");
+  }
   if (p.min_octave_side < 16 || p.min_octave_side <= rmax || p.min_octave_side <= 2 * p.border)
     return bad("min_octave_side must be >= 16, above the blur radius and twice the border");
   return SIFT_OK;

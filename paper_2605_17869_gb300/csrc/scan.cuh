@@ -36,6 +36,44 @@ __device__ __forceinline__ int block_excl_scan(int v, int *tmp, int *total) {
   return r;
 }
 
+// Exclusive scan of cnt[0, n) into off[0, n) by one warp; every lane returns
+// the total. Each lane issues 8 loads ahead of the 8 warp scans they feed.
+__device__ __forceinline__ int warp_excl_scan_array(const int *cnt, int *off, int n) {
+  const int lane = threadIdx.x & 31;
+  int carry = 0;
+  for (int base = 0; base < n; base += 256) {
+    int v[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      const int i = base + k * 32 + lane;
+      v[k] = i < n ? cnt[i] : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      const int incl = warp_incl_scan(v[k]);
+      const int i = base + k * 32 + lane;
+      if (i < n) off[i] = carry + incl - v[k];
+      carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+  }
+  return carry;
+}
+
+// Exclusive scan of v[0, n) (shared or global) into out[0, n) by one warp;
+// out[n] receives the total.
+__device__ __forceinline__ void warp_excl_scan_small(const int *v, int *out, int n) {
+  const int lane = threadIdx.x & 31;
+  int flat = 0;
+  for (int b0 = 0; b0 < n; b0 += 32) {
+    const int b = b0 + lane;
+    const int x = b < n ? v[b] : 0;
+    const int incl = warp_incl_scan(x);
+    if (b < n) out[b] = flat + incl - x;
+    flat += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  if (lane == 0) out[n] = flat;
+}
+
 __device__ __forceinline__ int block_sum(int v, int *tmp) {
   int total;
   block_excl_scan(v, tmp, &total);

@@ -25,6 +25,7 @@ constexpr int kMaxR = 16;          // largest blur radius supported (halo 16)
 constexpr int kOriBins = 36;       // §3.2: 36-bin orientation histogram
 constexpr int kMaxPeaks = kOriBins / 2;  // strict circular maxima of 36 bins
 constexpr int kDescLen = 128;      // 4 x 4 x 8
+constexpr int kOriWin = 1600;      // staged orientation window (floats, one band)
 constexpr int kBlurTW = 128;       // blur tile width (32 lanes x float4)
 constexpr int kBlurHalo = 16;      // staged columns left/right of a blur tile
 constexpr int kExtTW = 32;         // extrema tile columns (one warp)
