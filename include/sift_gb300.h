@@ -58,7 +58,8 @@ typedef enum {
 
 /* Extraction parameters. sift_params_default() gives plain SIFT as evaluated
  * here: 3 scales per octave, sigma0 1.6, assumed input blur 0.5, no
- * upsampling, octaves while min side >= 16, contrast threshold 0.04/3, edge
+ * upsampling (and, when it is switched on, none above 4,000,000 input
+ * pixels), octaves while min side >= 16, contrast threshold 0.04/3, edge
  * ratio 10, border 5, 5 refinement iterations, pre-gate 0.5 x threshold,
  * secondary orientation peaks at >= 0.8 of the maximum, no keypoint cap. */
 typedef struct {
@@ -79,6 +80,11 @@ typedef struct {
                             scales {1/2, 1/sqrt2, 1, sqrt2, 2}, each a 32 x 32
                             sample patch, pooled before normalisation */
   int rootsift;          /* 1: RootSIFT epilogue (L1 normalise, square root, §3.2) */
+  int upsample_max_px;   /* with upsample = 1, an image of more than this many
+                            input pixels keeps its own resolution as the first
+                            octave (the paper's VRAM-adaptive suppression of the
+                            double image above 4 MP, §1 and §5); decided per
+                            image, also within a batch; 0: no limit; >= 0 */
 } sift_params;
 
 /* Keypoint outputs: structure of arrays in device memory, capacity max_kpts.

@@ -23,7 +23,8 @@ definition reads: no blocking, fusion or reordering beyond it.
 Parity status per function:
   gaussian_taps, blur, upsample2x, decimate, build_pyramid, dog,
   find_candidates, refine_candidate, orientation_peaks, descriptor (plain,
-  DSP and RootSIFT), bilinear, cap_topk : pinned by tests/test_oracle_pins.py
+  DSP and RootSIFT), bilinear, cap_topk, magnify : pinned by
+  tests/test_oracle_pins.py
   (closed forms, brute force, invariants, rotation / transpose equivariance).
   extract (end-to-end composition): parity unpinned as an absolute result,
   since the paper prints no worked example; its parts are pinned above.
@@ -31,7 +32,7 @@ Parity status per function:
 from __future__ import annotations
 
 import math
-from dataclasses import dataclass, field
+from dataclasses import dataclass, field, replace
 
 import numpy as np
 
@@ -64,6 +65,7 @@ class Params:
     dsp_scales: tuple = (0.5, 2 ** -0.5, 1.0, 2 ** 0.5, 2.0)  # §3.2: 5 relative scales
     dsp_grid: int = 32           # §3.2: a 32 x 32 sample patch per DSP scale
     rootsift: bool = False       # §3.2 RootSIFT: L1 normalise, then element-wise sqrt
+    upsample_max_px: int = 4_000_000  # §5: no magnification above 4 MP (0 = no limit)
 
 
 # ------------------------------------------------------------------ A2/A3: blur
@@ -126,9 +128,25 @@ def decimate(img: np.ndarray) -> np.ndarray:
 
 # ------------------------------------------------------------------ pyramid
 
+def magnify(h: int, w: int, p: Params) -> bool:
+    """Whether an h x w input gets the 2x magnified first octave. The paper's
+    VRAM-adaptive execution (§1 contributions, §5 "Resolution Scaling")
+    suppresses the double image above 4 MP. READING: the limit counts input
+    pixels, an image of exactly upsample_max_px pixels is still magnified, and
+    0 turns the limit off."""
+    return bool(p.upsample) and (p.upsample_max_px <= 0 or h * w <= p.upsample_max_px)
+
+
+def for_image(h: int, w: int, p: Params) -> Params:
+    """The parameters one h x w image is processed with: upsample resolved by
+    magnify(); every later step reads only this resolved flag."""
+    up = magnify(h, w, p)
+    return p if up == bool(p.upsample) else replace(p, upsample=up)
+
+
 def octave_sizes(h: int, w: int, p: Params):
     """Octave geometry: (H_o, W_o) while min side >= min_octave_side."""
-    if p.upsample:
+    if magnify(h, w, p):
         h, w = 2 * h, 2 * w
     sizes = []
     while min(h, w) >= p.min_octave_side:
@@ -159,6 +177,7 @@ def build_pyramid(img: np.ndarray, p: Params):
     """Gaussian scale space (§3.2): per octave S+3 levels, each level blurred from
     the previous one (READING of the paper's in-place construction, §4.2)."""
     img = np.asarray(img, dtype=np.float64)
+    p = for_image(img.shape[0], img.shape[1], p)
     base = upsample2x(img) if p.upsample else img
     sb = base_sigma(p)
     kap = increment_sigmas(p)
@@ -631,6 +650,7 @@ def extract(img: np.ndarray, p: Params = None, keep_pyramid: bool = False,
     """Whole extraction path for one image, stage by stage (§3.2, Eq. 1's
     Pyr -> DoG -> Ext -> Ori -> Desc)."""
     p = p or Params()
+    p = for_image(np.shape(img)[0], np.shape(img)[1], p)
     pyr = build_pyramid(img, p)
     scale_up = 0.5 if p.upsample else 1.0
     S = p.n_scales

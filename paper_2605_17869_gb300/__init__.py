@@ -381,8 +381,10 @@ class Extractor:
         sift_build_pyramid(self.handle, img.data_ptr(), H, W, pitch, s.cuda_stream,
                            out.data_ptr(), tot)
         L = self.params.n_scales + 3
-        h = 2 * H if self.params.upsample else H
-        w = 2 * W if self.params.upsample else W
+        lim = self.params.upsample_max_px
+        up = bool(self.params.upsample) and (lim <= 0 or H * W <= lim)
+        h = 2 * H if up else H
+        w = 2 * W if up else W
         res, off = [], 0
         for _ in range(no):
             res.append(out[off:off + L * h * w].view(L, h, w))

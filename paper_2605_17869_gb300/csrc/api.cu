@@ -58,6 +58,7 @@ sift_status sift_params_default(sift_params *p) {
   p->upright = 0;
   p->dsp = 0;
   p->rootsift = 0;
+  p->upsample_max_px = 4000000;
   return SIFT_OK;
 }
 

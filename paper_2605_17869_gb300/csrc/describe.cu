@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(kKpWarps * 32) k_descriptor(const Desc *__rest
     const OctDev od = d->oct[im.oct0 + r.o];
     const float sig = sigma_of(d, r);
     if (tid == 0) {
-      const float sc = ldexpf(d->upsample ? 0.5f : 1.0f, r.o);
+      const float sc = ldexpf(im.up ? 0.5f : 1.0f, r.o);
       im.ox[j] = ((float)r.x + r.dx) * sc;
       im.oy[j] = ((float)r.y + r.dy) * sc;
       im.osig[j] = sig * sc;

@@ -56,8 +56,9 @@ static double level_sigma(const sift_params &p, int i) {
   return (double)p.sigma0 * std::pow(2.0, (double)i / p.n_scales);
 }
 
-static double base_sigma(const sift_params &p) {
-  const double eff = (double)p.init_blur * (p.upsample ? 2.0 : 1.0);
+// Blur that brings the input (2x magnified when up) to sigma0.
+static double base_sigma(const sift_params &p, bool up) {
+  const double eff = (double)p.init_blur * (up ? 2.0 : 1.0);
   const double d = (double)p.sigma0 * p.sigma0 - eff * eff;
   return d > 0 ? std::sqrt(d) : 0.0;
 }
@@ -78,8 +79,15 @@ sift_status validate_params(const sift_params &p, std::string *why) {
   if (p.max_refine_iter < 1) return bad("max_refine_iter must be >= 1");
   if (p.max_kpts < 1) return bad("max_kpts must be >= 1");
   if (p.dsp != 0 && p.dsp != 1) return bad("dsp must be 0 or 1");
+  if (p.upsample_max_px < 0) return bad("upsample_max_px must be >= 0");
   BlurTaps t;
-  int rmax = gaussian_taps(base_sigma(p), &t);
+  // Base blur of each mode in use: magnified first octaves when upsampling,
+  // the input as is without upsampling or for images above upsample_max_px.
+  int rmax = p.upsample ? gaussian_taps(base_sigma(p, true), &t) : 0;
+  if (rmax >= 0 && (!p.upsample || p.upsample_max_px > 0)) {
+    const int r0 = gaussian_taps(base_sigma(p, false), &t);
+    rmax = r0 < 0 ? -1 : std::max(rmax, r0);
+  }
   for (int i = 1; i <= p.n_scales + 2 && rmax >= 0; i++) {
     const double k = std::sqrt(level_sigma(p, i) * level_sigma(p, i) -
                                level_sigma(p, i - 1) * level_sigma(p, i - 1));
@@ -138,7 +146,7 @@ sift_status Engine::init() {
     return e == cudaErrorMemoryAllocation ? SIFT_E_OOM : SIFT_E_CUDA;
   }
   S_ = P_.n_scales;
-  base_R_ = gaussian_taps(base_sigma(P_), &base_t_);
+  for (int m = 0; m < 2; m++) base_R_[m] = gaussian_taps(base_sigma(P_, m == 1), &base_t_[m]);
   for (int i = 1; i <= S_ + 2; i++) {
     const double k = std::sqrt(level_sigma(P_, i) * level_sigma(P_, i) -
                                level_sigma(P_, i - 1) * level_sigma(P_, i - 1));
@@ -165,7 +173,7 @@ sift_status Engine::init_noalloc() {
     return SIFT_E_CUDA;
   }
   S_ = P_.n_scales;
-  base_R_ = gaussian_taps(base_sigma(P_), &base_t_);
+  for (int m = 0; m < 2; m++) base_R_[m] = gaussian_taps(base_sigma(P_, m == 1), &base_t_[m]);
   for (int i = 1; i <= S_ + 2; i++) {
     const double k = std::sqrt(level_sigma(P_, i) * level_sigma(P_, i) -
                                level_sigma(P_, i - 1) * level_sigma(P_, i - 1));
@@ -176,8 +184,13 @@ sift_status Engine::init_noalloc() {
   return SIFT_OK;
 }
 
+bool Engine::magnify(int H, int W) const {
+  return P_.upsample && (P_.upsample_max_px <= 0 || (long long)H * W <= P_.upsample_max_px);
+}
+
 int Engine::octave_sizes(int H, int W, int *hs, int *ws) const {
-  int h = P_.upsample ? 2 * H : H, w = P_.upsample ? 2 * W : W;
+  const bool up = magnify(H, W);
+  int h = up ? 2 * H : H, w = up ? 2 * W : W;
   int n = 0;
   while (std::min(h, w) >= P_.min_octave_side && n < kMaxOct) {
     if (hs) hs[n] = h;
@@ -247,6 +260,7 @@ sift_status Engine::fill_plan(int n, const ImgIn *in, Desc &hd, WsLayout &L, int
     d.W = in[b].W;
     d.spitch = in[b].pitch;
     d.src_vec_ok = ((reinterpret_cast<uintptr_t>(in[b].src) & 15) == 0 && (in[b].pitch & 3) == 0);
+    d.up = magnify(in[b].H, in[b].W) ? 1 : 0;
     int hs[kMaxOct], ws[kMaxOct];
     const int no = octave_sizes(in[b].H, in[b].W, hs, ws);
     if (no == 0) return SIFT_E_INVALID;
@@ -311,6 +325,16 @@ sift_status Engine::fill_plan(int n, const ImgIn *in, Desc &hd, WsLayout &L, int
         pre[b + 1] = pre[b] + t;
       }
     }
+  }
+  // Base-blur tile queues: octave-0 tiles of the images of each mode (the
+  // other mode's images contribute none).
+  for (int m = 0; m < 2; m++) {
+    int *pre = hd.base_pre[m];
+    pre[0] = 0;
+    for (int b = 0; b < n; b++)
+      pre[b + 1] = pre[b] + (hd.img[b].up == m ? hd.tile_pre[TK_BLUR32][0][b + 1] -
+                                                     hd.tile_pre[TK_BLUR32][0][b]
+                                               : 0);
   }
   hd.bmc_pre[0] = 0;
   hd.cc_pre[0] = 0;
@@ -383,7 +407,7 @@ int Engine::grid_blur(int R, int kind, int mode) const {
   return std::max(1, n_sm_ * per_sm);
 }
 
-cudaError_t Engine::enqueue_pyramid(cudaStream_t s, int M, std::vector<ProfRec> *prof) {
+cudaError_t Engine::enqueue_pyramid(cudaStream_t s, int M, int modes, std::vector<ProfRec> *prof) {
   cudaError_t e = cudaSuccess;
   auto rec = [&](int cls, auto &&fn) {
     if (e != cudaSuccess) return;
@@ -403,11 +427,14 @@ cudaError_t Engine::enqueue_pyramid(cudaStream_t s, int M, std::vector<ProfRec> 
   const int g4 = n_sm_ * 4;
   for (int o = 0; o < M; o++) {
     if (o == 0) {
-      const int mode = P_.upsample ? 2 : 1;
-      rec(PC_BASE, [&] {
-        return launch_base_blur(d, base_R_, base_t_, TK_BLUR32, P_.upsample != 0,
-                                grid_blur(base_R_, TK_BLUR32, mode), s);
-      });
+      // One base launch per mode present (bit m of modes: images with up = m).
+      for (int m = 1; m >= 0; m--) {
+        if (!(modes >> m & 1)) continue;
+        rec(PC_BASE, [&] {
+          return launch_base_blur(d, base_R_[m], base_t_[m], TK_BLUR32, m == 1,
+                                  grid_blur(base_R_[m], TK_BLUR32, m == 1 ? 2 : 1), s);
+        });
+      }
     }
     // Octaves above 0: the level-1 launch also produces level 0 by decimating
     // level S of the previous octave (no separate decimation pass).
@@ -422,7 +449,7 @@ cudaError_t Engine::enqueue_pyramid(cudaStream_t s, int M, std::vector<ProfRec> 
   return e;
 }
 
-cudaError_t Engine::enqueue_all(cudaStream_t s, int M, std::vector<ProfRec> *prof) {
+cudaError_t Engine::enqueue_all(cudaStream_t s, int M, int modes, std::vector<ProfRec> *prof) {
   cudaError_t e = cudaSuccess;
   kernels_ = 0;
   auto rec = [&](int cls, auto &&fn, int nk = 1) {
@@ -444,11 +471,14 @@ cudaError_t Engine::enqueue_all(cudaStream_t s, int M, std::vector<ProfRec> *pro
   const int g4 = n_sm_ * 4;
   for (int o = 0; o < M; o++) {
     if (o == 0) {
-      const int mode = P_.upsample ? 2 : 1;
-      rec(PC_BASE, [&] {
-        return launch_base_blur(d, base_R_, base_t_, TK_BLUR32, P_.upsample != 0,
-                                grid_blur(base_R_, TK_BLUR32, mode), s);
-      });
+      // One base launch per mode present (bit m of modes: images with up = m).
+      for (int m = 1; m >= 0; m--) {
+        if (!(modes >> m & 1)) continue;
+        rec(PC_BASE, [&] {
+          return launch_base_blur(d, base_R_[m], base_t_[m], TK_BLUR32, m == 1,
+                                  grid_blur(base_R_[m], TK_BLUR32, m == 1 ? 2 : 1), s);
+        });
+      }
     }
     // Octaves above 0: the level-1 launch also produces level 0 by decimating
     // level S of the previous octave (no separate decimation pass).
@@ -485,8 +515,8 @@ void Engine::drop_graphs() {
   last_prof_ = nullptr;
 }
 
-sift_status Engine::get_graph(int M, cudaGraphExec_t *out) {
-  const int key = M * 2 + (profiling_ ? 1 : 0);
+sift_status Engine::get_graph(int M, int modes, cudaGraphExec_t *out) {
+  const int key = (M * 4 + modes) * 2 + (profiling_ ? 1 : 0);
   auto it = graphs_.find(key);
   if (it != graphs_.end()) {
     *out = it->second.exec;
@@ -497,7 +527,7 @@ sift_status Engine::get_graph(int M, cudaGraphExec_t *out) {
   GraphEntry ge;
   if (profiling_) ge.prof = new std::vector<ProfRec>();
   cudaError_t e = cudaStreamBeginCapture(cap_, cudaStreamCaptureModeThreadLocal);
-  cudaError_t e1 = e == cudaSuccess ? enqueue_all(cap_, M, ge.prof) : e;
+  cudaError_t e1 = e == cudaSuccess ? enqueue_all(cap_, M, modes, ge.prof) : e;
   cudaGraph_t g = nullptr;
   cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(cap_, &g) : e;
   cudaError_t e3 = (e1 == cudaSuccess && e2 == cudaSuccess) ? cudaGraphInstantiate(&ge.exec, g, 0)
@@ -562,7 +592,7 @@ sift_status Engine::run(int n, const ImgIn *imgs, cudaStream_t s) {
   const size_t bytes =
       offsetof(Desc, oct) + (size_t)(hd->img[n - 1].oct0 + hd->img[n - 1].n_oct) * sizeof(OctDev);
   cudaGraphExec_t exec = nullptr;
-  st = get_graph(M, &exec);
+  st = get_graph(M, base_modes(*hd), &exec);
   if (st != SIFT_OK) return st;
   st = upload(hd, bytes, s);
   if (st != SIFT_OK) return st;
@@ -601,7 +631,7 @@ sift_status Engine::run_pyramid(const ImgIn &img, cudaStream_t s) {
   const size_t bytes = offsetof(Desc, oct) + (size_t)hd->img[0].n_oct * sizeof(OctDev);
   cudaError_t e = cudaSuccess;
   st = upload(hd, bytes, s);
-  if (e == cudaSuccess && st == SIFT_OK) e = enqueue_pyramid(s, M, nullptr);
+  if (e == cudaSuccess && st == SIFT_OK) e = enqueue_pyramid(s, M, base_modes(*hd), nullptr);
   if (e == cudaSuccess) e = cudaEventRecord(done_, s);
   if (e != cudaSuccess || st != SIFT_OK) {
     err = std::string("pyramid launch failed: ") + cudaGetErrorString(e);
@@ -694,6 +724,7 @@ sift_status Engine::autotune(int H, int W, cudaStream_t s) {
   st = run_pyramid(in, s);
   int hs[kMaxOct], ws[kMaxOct];
   const int M = octave_sizes(H, W, hs, ws);
+  const int modes = magnify(H, W) ? 2 : 1;
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
@@ -703,9 +734,9 @@ sift_status Engine::autotune(int H, int W, cudaStream_t s) {
   // from 32-row tiles everywhere; a level switches to 64 rows only if the
   // stage gets at least 1% faster.
   auto time_stage = [&]() -> float {
-    for (int w = 0; w < 2; w++) enqueue_pyramid(s, M, nullptr);
+    for (int w = 0; w < 2; w++) enqueue_pyramid(s, M, modes, nullptr);
     cudaEventRecord(a, s);
-    for (int r = 0; r < 5; r++) enqueue_pyramid(s, M, nullptr);
+    for (int r = 0; r < 5; r++) enqueue_pyramid(s, M, modes, nullptr);
     cudaEventRecord(b, s);
     cudaEventSynchronize(b);
     float ms = 0.f;

@@ -44,6 +44,9 @@ class Engine {
   sift_status run(int n, const ImgIn *imgs, cudaStream_t s);
   // Queue the pyramid stage only (for export); one image.
   sift_status run_pyramid(const ImgIn &img, cudaStream_t s);
+  // Whether an H x W input gets the 2x magnified first octave: upsample on
+  // and at most upsample_max_px input pixels (0: no limit).
+  bool magnify(int H, int W) const;
   // Octave sizes for an input; returns the octave count.
   int octave_sizes(int H, int W, int *hs, int *ws) const;
   // Workspace bytes a batch needs (serving admission).
@@ -71,9 +74,9 @@ class Engine {
   sift_status plan_noalloc(const ImgIn &img, Desc *hd, WsLayout *lay, int *max_oct) const {
     return fill_plan(1, &img, *hd, *lay, max_oct);
   }
-  cudaError_t enqueue_noalloc(Desc *d_desc, cudaStream_t s, int max_oct) {
+  cudaError_t enqueue_noalloc(Desc *d_desc, cudaStream_t s, int max_oct, int modes) {
     ddesc_ = d_desc;
-    const cudaError_t e = enqueue_all(s, max_oct, nullptr);
+    const cudaError_t e = enqueue_all(s, max_oct, modes, nullptr);
     ddesc_ = nullptr;  // not owned: the destructor must not free it
     return e;
   }
@@ -86,17 +89,18 @@ class Engine {
   sift_status fill_plan(int n, const ImgIn *imgs, Desc &hd, WsLayout &lay, int *max_oct) const;
   sift_status ensure_workspace(size_t bytes, cudaStream_t s);
   sift_status upload(Desc *hd, size_t bytes, cudaStream_t s);
-  cudaError_t enqueue_pyramid(cudaStream_t s, int max_oct, std::vector<struct ProfRec> *prof);
-  cudaError_t enqueue_all(cudaStream_t s, int max_oct, std::vector<struct ProfRec> *prof);
-  sift_status get_graph(int max_oct, cudaGraphExec_t *out);
+  // modes: bit 0 set if an image is processed as is, bit 1 if one is magnified.
+  cudaError_t enqueue_pyramid(cudaStream_t s, int max_oct, int modes, std::vector<struct ProfRec> *prof);
+  cudaError_t enqueue_all(cudaStream_t s, int max_oct, int modes, std::vector<struct ProfRec> *prof);
+  sift_status get_graph(int max_oct, int modes, cudaGraphExec_t *out);
   void drop_graphs();
   int grid_blur(int R, int kind, int mode) const;
 
   sift_params P_;
   int dev_ = 0, n_sm_ = 0;
   int S_ = 3;
-  int base_R_ = 0;
-  BlurTaps base_t_{};
+  int base_R_[2] = {0, 0};  // base blur: [0] input as is, [1] 2x magnified input
+  BlurTaps base_t_[2] = {};
   int lvl_R_[kMaxLevels] = {};
   BlurTaps lvl_t_[kMaxLevels] = {};
   Tuning tun_{};
@@ -124,6 +128,11 @@ class Engine {
   std::vector<struct ProfRec> *last_prof_ = nullptr;
   bool inited_ = false;
 };
+
+// Base-blur modes a plan needs: bit m set when some image has up == m.
+inline int base_modes(const Desc &hd) {
+  return (hd.base_pre[0][hd.n_img] > 0 ? 1 : 0) | (hd.base_pre[1][hd.n_img] > 0 ? 2 : 0);
+}
 
 struct ProfRec {
   cudaEvent_t a, b;

@@ -36,6 +36,7 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 struct SetupArgs {
   unsigned char head[offsetof(Desc, tile_pre)];
   int tiles[TK_COUNT][kMaxOct];
+  int base_tiles[2];
   int bmc_n, cc_n;
   ImgDev img;
   OctDev oct[kMaxOct];
@@ -49,6 +50,10 @@ __global__ void k_noalloc_setup(Desc *d, SetupArgs a) {
     const int k = i / kMaxOct, o = i % kMaxOct;
     d->tile_pre[k][o][0] = 0;
     d->tile_pre[k][o][1] = a.tiles[k][o];
+  }
+  if (lane < 2) {
+    d->base_pre[lane][0] = 0;
+    d->base_pre[lane][1] = a.base_tiles[lane];
   }
   if (lane == 0) {
     d->bmc_pre[0] = 0;
@@ -135,12 +140,13 @@ extern "C" sift_status sift_extract_noalloc(const sift_params *p, const float *i
   std::memcpy(a.head, &hd, sizeof(a.head));
   for (int k = 0; k < TK_COUNT; k++)
     for (int o = 0; o < kMaxOct; o++) a.tiles[k][o] = hd.tile_pre[k][o][1];
+  for (int m = 0; m < 2; m++) a.base_tiles[m] = hd.base_pre[m][1];
   a.bmc_n = hd.bmc_pre[1];
   a.cc_n = hd.cc_pre[1];
   a.img = hd.img[0];
   for (int o = 0; o < kMaxOct; o++) a.oct[o] = o < hd.img[0].n_oct ? hd.oct[o] : OctDev{};
   k_noalloc_setup<<<1, 32, 0, s>>>(d_desc, a);
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = eng.enqueue_noalloc(d_desc, s, M);
+  if (e == cudaSuccess) e = eng.enqueue_noalloc(d_desc, s, M, base_modes(hd));
   return e == cudaSuccess ? SIFT_OK : SIFT_E_CUDA;
 }

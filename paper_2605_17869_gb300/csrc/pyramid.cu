@@ -475,7 +475,9 @@ __global__ void __launch_bounds__(kThreads, TH == 32 ? (MODE == 0 ? 4 : 3) : 1)
   float *s_in = reinterpret_cast<float *>(smem4);
   float *s_v = s_in + ROWS * kSinW;
   float *s_tmp = s_v + TH * kSinW;  // MODE 2: input rows of the next magnified window
-  const int *pre = d->tile_pre[KindOf<TH>::v][oct];
+  // Base blurs (MODE 1: input as is, MODE 2: magnified) take the queue of
+  // their own mode's images.
+  const int *pre = (MODE == 1 || MODE == 2) ? d->base_pre[MODE - 1] : d->tile_pre[KindOf<TH>::v][oct];
   const int total = pre[d->n_img];
   const int t0 = blockIdx.x, G = gridDim.x;
   if (t0 >= total) return;
@@ -532,7 +534,7 @@ __global__ void __launch_bounds__(kThreads) k_blur_generic(const Desc *__restric
   float *s_in = reinterpret_cast<float *>(smem4);
   float *s_v = s_in + ROWS * kSinW;
   const int n = d->n_img;
-  const int *pre = d->tile_pre[TK_BLUR32][oct];
+  const int *pre = (MODE == 1 || MODE == 2) ? d->base_pre[MODE - 1] : d->tile_pre[TK_BLUR32][oct];
   const int total = pre[n];
   for (int t = blockIdx.x; t < total; t += gridDim.x) {
     const int b = find_owner(pre, n, t);

@@ -52,6 +52,7 @@ struct ImgDev {
   const float *src;            // input image (device)
   int H, W, spitch;            // input size and pitch (elements)
   int src_vec_ok;              // 1 if 16-byte aligned rows (vector loads allowed)
+  int up;                      // 1 if the first octave is the 2x magnified input
   int n_oct, oct0;             // octaves and index of the first OctDev
   long long bm_begin, bm_words;  // bitmap slice
   int bmc0, bmc_n;             // bitmap chunks [bmc0, bmc0 + bmc_n)
@@ -102,6 +103,7 @@ struct Desc {
   int *fin_flat;               // [kMaxImg + 1] prefix of n_fin over images
   // geometry
   int tile_pre[TK_COUNT][kMaxOct][kMaxImg + 1];
+  int base_pre[2][kMaxImg + 1];  // base-blur tiles (32 rows) of the images with up = 0 / 1
   int bmc_pre[kMaxImg + 1];
   int cc_pre[kMaxImg + 1];
   ImgDev img[kMaxImg];

@@ -51,6 +51,7 @@ def test_host_only_calls(lib):
     assert L.sift_params_default(ctypes.byref(p)) == 0
     assert (p.n_scales, p.max_refine_iter, p.border) == (3, 5, 5)
     assert abs(p.contrast_thr - 0.04 / 3) < 1e-7 and abs(p.sigma0 - 1.6) < 1e-7
+    assert (p.upsample, p.upsample_max_px) == (0, 4_000_000)
     assert L.sift_version().startswith(b"gb300-sift")
     assert L.sift_params_default(None) == _abi.SIFT_E_INVALID
     h = ctypes.c_void_p()
@@ -59,6 +60,8 @@ def test_host_only_calls(lib):
     bad.n_scales = 0
     assert L.sift_create(ctypes.byref(bad), ctypes.byref(h)) == _abi.SIFT_E_INVALID
     bad.n_scales, bad.sigma0 = 3, 4.0   # blur radius above 16
+    assert L.sift_create(ctypes.byref(bad), ctypes.byref(h)) == _abi.SIFT_E_INVALID
+    bad.sigma0, bad.upsample_max_px = 1.6, -1
     assert L.sift_create(ctypes.byref(bad), ctypes.byref(h)) == _abi.SIFT_E_INVALID
     assert L.sift_destroy(None) == _abi.SIFT_E_INVALID
     assert L.sift_serve_poll(None, 1, None) == _abi.SIFT_E_INVALID

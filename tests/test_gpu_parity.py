@@ -197,6 +197,36 @@ def test_batch_composition_invariance():
     assert sub == [single[2], single[0]]
 
 
+# ------------------------------------------------------------------ upsample suppression
+
+def test_upsample_suppression_per_image():
+    """§5's suppression of the double image above a pixel limit, decided per
+    image within one batch: the image under the limit is magnified, the one
+    above keeps its size. Each matches the oracle under the same rule, the
+    batch equals single-image runs bit for bit, and the suppressed image equals
+    a run without upsampling bit for bit."""
+    lim = 20_000
+    small = synth.make_image(synth.rng_for(16, 0), 96, 128)    # 12,288 px: magnified
+    large = synth.make_image(synth.rng_for(16, 1), 150, 200)   # 30,000 px: suppressed
+    ts = [torch.from_numpy(im).cuda() for im in (small, large)]
+    ex = pkg.Extractor(upsample=1, upsample_max_px=lim, max_kpts=8192)
+    fb = ex.extract_batch(ts)
+    p = _oracle_params(upsample=True, upsample_max_px=lim, max_kpts=8192)
+    for im, f, label in zip((small, large), fb, ("magnified", "suppressed")):
+        _assert_parity(so.extract(im, p), f, p, f"{label} {im.shape}")
+    single = [_digest(ex.extract(t)) for t in ts]
+    assert [_digest(f) for f in fb] == single
+    assert [_digest(f) for f in ex.extract_batch(ts[::-1])] == single[::-1]
+    plain = pkg.Extractor(max_kpts=8192)
+    assert _digest(plain.extract(ts[1])) == single[1]
+    assert tuple(ex.pyramid(ts[0])[0].shape[1:]) == (192, 256)
+    assert tuple(ex.pyramid(ts[1])[0].shape[1:]) == (150, 200)
+    nolim = pkg.Extractor(upsample=1, upsample_max_px=0, max_kpts=8192)
+    assert tuple(nolim.pyramid(ts[1])[0].shape[1:]) == (300, 400)
+    for e in (ex, plain, nolim):
+        e.close()
+
+
 # ------------------------------------------------------------------ full size
 
 def _oracle_full(args):

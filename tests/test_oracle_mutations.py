@@ -63,6 +63,8 @@ MUTANTS = {
         "    return _trilinear_histogram(rx"),
     "dsp_dy_from_x": ("    dy = bilinear(L, x, y + 1) - bilinear(L, x, y - 1)",
                       "    dy = bilinear(L, x + 1, y + 1) - bilinear(L, x - 1, y - 1)"),
+    "magnify_limit_exclusive": ("(p.upsample_max_px <= 0 or h * w <= p.upsample_max_px)",
+                                "(p.upsample_max_px <= 0 or h * w < p.upsample_max_px)"),
     "rootsift_no_l1": ("        vec = np.sqrt(vec / l1) if l1 > 0 else vec",
                        "        vec = np.sqrt(vec) if l1 > 0 else vec"),
 }

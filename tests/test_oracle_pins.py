@@ -107,6 +107,34 @@ def test_upsample_identities():
     np.testing.assert_array_equal(so.decimate(u), img)
 
 
+def test_magnify_limit():
+    """§5's suppression of the double image above 4 MP: the limit counts input
+    pixels, an image of exactly the limit is still magnified, 0 disables it."""
+    p = so.Params(upsample=True, upsample_max_px=1000)
+    assert so.magnify(25, 40, p) and so.magnify(40, 25, p)
+    assert not so.magnify(25, 41, p) and not so.magnify(41, 25, p)
+    d = so.Params(upsample=True)
+    assert d.upsample_max_px == 4_000_000
+    assert so.magnify(2000, 2000, d) and not so.magnify(2000, 2001, d)
+    assert so.octave_sizes(2000, 2000, d)[0] == (4000, 4000)
+    assert so.octave_sizes(2000, 2001, d)[0] == (2000, 2001)
+    assert so.magnify(5000, 5000, so.Params(upsample=True, upsample_max_px=0))
+    assert not so.magnify(10, 10, so.Params(upsample=False, upsample_max_px=0))
+
+
+def test_suppressed_image_takes_the_plain_path():
+    """Above the limit the image is processed exactly as without upsampling
+    (octave 0 at the input size, base blur from the unmagnified input, output
+    coordinates not halved); at the limit it is magnified."""
+    img = RNG.random((40, 52))
+    plain = so.extract(img, so.Params())
+    supp = so.extract(img, so.Params(upsample=True, upsample_max_px=40 * 52 - 1))
+    for k in ("x", "y", "sigma", "angle", "response", "octave", "layer", "desc"):
+        np.testing.assert_array_equal(getattr(supp, k), getattr(plain, k))
+    assert so.build_pyramid(img, so.Params(upsample=True, upsample_max_px=40 * 52 - 1))[0].shape[1:] == (40, 52)
+    assert so.build_pyramid(img, so.Params(upsample=True, upsample_max_px=40 * 52))[0].shape[1:] == (80, 104)
+
+
 def test_decimate_floor_size_and_octaves():
     img = RNG.random((31, 18))
     d = so.decimate(img)
