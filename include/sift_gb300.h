@@ -164,7 +164,7 @@ sift_status sift_extract_noalloc(const sift_params *p, const float *img_dev, int
                                  int pitch_elems, void *stream, sift_kpts_dev out_kpts,
                                  float *out_desc_dev, int *out_count_dev);
 
-/* Symmetric ratio-test matcher (§3.3 "Descriptor Matching", first backend).
+/* Symmetric ratio-test matcher (§3.4 "Descriptor Matching", first backend).
  * The similarity matrix of two descriptor sets is formed from fp16
  * tensor-core products (tcgen05, FP32 accumulation): for every descriptor
  * its nearest neighbour in the other set (largest dot product, ties to the

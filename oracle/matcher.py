@@ -3,7 +3,7 @@
 Only the test-suite and the benchmark's CPU arms may import this module; the
 product path never does, and it shares no code with the CUDA sources.
 
-The paper's first matching backend (§3.3 "Descriptor Matching") forms the
+The paper's first matching backend (§3.4 "Descriptor Matching") forms the
 similarity matrix of two descriptor sets with fp16 tensor-core products and
 keeps mutually consistent pairs that pass a ratio test. Readings where the
 paper is silent (marked READING):

@@ -1,4 +1,4 @@
-// Symmetric ratio-test matcher (§3.3 "Descriptor Matching", first backend):
+// Symmetric ratio-test matcher (§3.4 "Descriptor Matching", first backend):
 // the similarity matrix of two descriptor sets from fp16 tensor-core products,
 // nearest neighbours in both directions, mutual consistency and Lowe's ratio
 // test on both sides.
