@@ -182,6 +182,36 @@ sift_status sift_extract_noalloc(const sift_params *p, const float *img_dev, int
 sift_status sift_match(sift_handle *h, const float *desc_a, int n_a, const float *desc_b, int n_b,
                        float ratio, void *stream, int *out_match_a);
 
+/* GPU MAGSAC++ homography verification (§3.6 "GPU MAGSAC++"): the best of
+ * n_hyp minimal-sample homographies under the MAGSAC++ score.
+ *   xa, xb: device, n x 2 FP32 (x, y) points of the two images, 8-byte aligned;
+ *   correspondence i is xa[i] -> xb[i] (e.g. matched keypoints), n >= 4.
+ *   samples: device, n_hyp x 4 int32 indices into [0, n): the random draw is
+ *   the caller's (the Python binding draws 4 distinct indices per hypothesis
+ *   from a seeded generator). An index outside [0, n) makes that hypothesis
+ *   invalid; it is never read.
+ *   sigma_max: upper bound of the inlier noise in pixels (> 0).
+ * Per hypothesis: the normalised DLT in FP64 (Hartley normalisation, the 8 x 8
+ * system with h33 = 1 by pivoted elimination, de-normalised, H[2][2] = 1); a
+ * sample is invalid (score +inf) if three of its points are collinear in
+ * either image or the system is (near-)singular. Score: the sum over all
+ * correspondences of the MAGSAC++ loss of the forward transfer error
+ * r = |pi(H xa) - xb|: the chi (4 degrees of freedom) likelihood marginalised
+ * over the noise sigma in [0, sigma_max], truncated at k sigma_max with k the
+ * 0.99 chi quantile (3.644), as an M-estimator loss; lower is better.
+ * Outputs (device): H_out 9 doubles, row-major, of the best hypothesis
+ * (smallest score, ties to the smaller index; zeros if none is valid);
+ * best_out its index or -1; score_out its score (+inf if none);
+ * inliers_out n bytes, 1 where r <= k sigma_max under H_out; scores_out
+ * (optional, may be NULL) the n_hyp scores. Scores are bitwise reproducible.
+ * Asynchronous on `stream`; the handle keeps a workspace of about 80 bytes
+ * per hypothesis. Errors: SIFT_E_INVALID for a null pointer, misaligned
+ * points, n outside [4, 2^24], n_hyp outside [1, 2^20] or sigma_max outside
+ * (0, 1e6); SIFT_E_OOM / SIFT_E_CUDA. */
+sift_status sift_magsac(sift_handle *h, const float *xa, const float *xb, int n, const int *samples,
+                        int n_hyp, float sigma_max, void *stream, double *H_out, int *best_out,
+                        float *score_out, unsigned char *inliers_out, float *scores_out);
+
 /* Statistics of the last extraction on this handle, read after synchronising
  * its stream. stats receives, per image i of the last call (up to max_images):
  *   stats[4*i+0] candidates (extrema after the gate), stats[4*i+1] refined

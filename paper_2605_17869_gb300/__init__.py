@@ -111,6 +111,37 @@ def sift_match(handle, a_ptr: int, n_a: int, b_ptr: int, n_b: int, ratio: float,
                   handle, "sift_match")
 
 
+def sift_magsac(handle, xa_ptr: int, xb_ptr: int, n: int, samples_ptr: int, n_hyp: int,
+                sigma_max: float, stream: int, H_ptr: int, best_ptr: int, score_ptr: int,
+                inliers_ptr: int, scores_ptr: int = 0) -> int:
+    """GPU MAGSAC++ homography verification (see the C header)."""
+    return _check(_lib().sift_magsac(handle, c_void_p(xa_ptr), c_void_p(xb_ptr), n,
+                                     c_void_p(samples_ptr), n_hyp, c_float(sigma_max),
+                                     c_void_p(stream), c_void_p(H_ptr), c_void_p(best_ptr),
+                                     c_void_p(score_ptr), c_void_p(inliers_ptr),
+                                     c_void_p(scores_ptr or None)),
+                  handle, "sift_magsac")
+
+
+def draw_samples(n: int, n_hyp: int = 1500, seed: int = 0):
+    """Minimal samples for sift_magsac: an n_hyp x 4 int32 NumPy array of
+    distinct indices in [0, n), each row uniform over the 4-subsets in draw
+    order. Draw k picks uniformly among the n - k indices not yet taken (a
+    value v is stepped past the taken indices in ascending order)."""
+    import numpy as np
+    if n < 4:
+        raise SiftError(SIFT_E_INVALID, "MAGSAC++ needs at least 4 correspondences")
+    rng = np.random.default_rng(seed)
+    out = np.empty((n_hyp, 4), dtype=np.int64)
+    for k in range(4):
+        v = rng.integers(0, n - k, size=n_hyp)
+        taken = np.sort(out[:, :k], axis=1)
+        for j in range(k):
+            v = v + (v >= taken[:, j])
+        out[:, k] = v
+    return out.astype(np.int32)
+
+
 def sift_last_stats(handle, n_images: int):
     buf = (c_int * (4 * n_images))()
     st = _check(_lib().sift_last_stats(handle, buf, n_images), handle, "sift_last_stats")
@@ -366,6 +397,40 @@ class Extractor:
         out = torch.empty(desc_a.shape[0], dtype=torch.int32, device=desc_a.device)
         sift_match(self.handle, desc_a.data_ptr(), desc_a.shape[0], desc_b.data_ptr(),
                    desc_b.shape[0], ratio, s.cuda_stream, out.data_ptr())
+        return out
+
+    def magsac(self, xa, xb, samples=None, n_hyp: int = 1500, sigma_max: float = 1.0,
+               seed: int = 0, stream=None):
+        """GPU MAGSAC++ (§3.6): the best homography xa -> xb among n_hyp minimal
+        samples (n x 2 float32 CUDA tensors of corresponding points). samples:
+        an n_hyp x 4 int32 CUDA tensor, or None to draw them with draw_samples
+        (seeded). Returns a dict of CUDA tensors, queued on the stream: H (3 x 3
+        float64, H[2, 2] = 1), best (index, -1 if every sample is degenerate),
+        score, inliers (n uint8), scores (n_hyp float32)."""
+        torch = _torch()
+        for t in (xa, xb):
+            if not (t.is_cuda and t.dtype == torch.float32 and t.dim() == 2 and t.shape[1] == 2
+                    and t.is_contiguous()):
+                raise SiftError(SIFT_E_INVALID, "points must be contiguous N x 2 float32 CUDA tensors")
+        n = xa.shape[0]
+        if xb.shape[0] != n:
+            raise SiftError(SIFT_E_INVALID, "xa and xb must have the same length")
+        if samples is None:
+            samples = torch.from_numpy(draw_samples(n, n_hyp, seed)).to(xa.device)
+        if not (samples.is_cuda and samples.dtype == torch.int32 and samples.dim() == 2
+                and samples.shape[1] == 4 and samples.is_contiguous()):
+            raise SiftError(SIFT_E_INVALID, "samples must be a contiguous n_hyp x 4 int32 CUDA tensor")
+        n_hyp = samples.shape[0]
+        dev = xa.device
+        out = {"H": torch.empty((3, 3), dtype=torch.float64, device=dev),
+               "best": torch.empty(1, dtype=torch.int32, device=dev),
+               "score": torch.empty(1, dtype=torch.float32, device=dev),
+               "inliers": torch.empty(n, dtype=torch.uint8, device=dev),
+               "scores": torch.empty(n_hyp, dtype=torch.float32, device=dev)}
+        s = stream if stream is not None else torch.cuda.current_stream()
+        sift_magsac(self.handle, xa.data_ptr(), xb.data_ptr(), n, samples.data_ptr(), n_hyp,
+                    sigma_max, s.cuda_stream, out["H"].data_ptr(), out["best"].data_ptr(),
+                    out["score"].data_ptr(), out["inliers"].data_ptr(), out["scores"].data_ptr())
         return out
 
     def stats(self, n_images: int = 1):

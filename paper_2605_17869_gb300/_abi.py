@@ -56,6 +56,8 @@ SIGNATURES = {
                                      SiftKptsDev, c_void_p, c_void_p]),
     "sift_match": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_int, c_float, c_void_p,
                            c_void_p]),
+    "sift_magsac": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int, c_float, c_void_p,
+                            c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "sift_last_stats": (c_int, [c_void_p, POINTER(c_int), c_int]),
     "sift_pyramid_size": (c_int, [c_void_p, c_int, c_int, POINTER(c_int), POINTER(c_size_t)]),
     "sift_build_pyramid": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, c_void_p,

@@ -2,6 +2,7 @@
 // continuous-batching server.
 #include <chrono>
 #include <condition_variable>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <deque>
@@ -23,6 +24,9 @@ struct sift_handle {
   size_t match_cap = 0;
   cudaStream_t match_stream = nullptr;
   bool match_attr = false;
+  void *magsac_ws = nullptr;  // MAGSAC++ workspace (stream-ordered allocation)
+  size_t magsac_cap = 0;
+  cudaStream_t magsac_stream = nullptr;
 };
 
 static sift_status fail(sift_handle *h, sift_status st, const std::string &m) {
@@ -85,6 +89,10 @@ sift_status sift_destroy(sift_handle *h) {
     cudaStreamSynchronize(h->match_stream);
     cudaFree(h->match_ws);
   }
+  if (h->magsac_ws) {
+    cudaStreamSynchronize(h->magsac_stream);
+    cudaFree(h->magsac_ws);
+  }
   delete h->eng;
   delete h;
   return SIFT_OK;
@@ -118,6 +126,37 @@ sift_status sift_match(sift_handle *h, const float *desc_a, int n_a, const float
   h->match_stream = s;
   const cudaError_t e = sift::launch_match(desc_a, n_a, desc_b, n_b, ratio, h->match_ws, out_match_a, s);
   if (e != cudaSuccess) return fail(h, SIFT_E_CUDA, std::string("matcher: ") + cudaGetErrorString(e));
+  return SIFT_OK;
+}
+
+sift_status sift_magsac(sift_handle *h, const float *xa, const float *xb, int n, const int *samples,
+                        int n_hyp, float sigma_max, void *stream, double *H_out, int *best_out,
+                        float *score_out, unsigned char *inliers_out, float *scores_out) {
+  if (!h) return SIFT_E_INVALID;
+  if (n < 4 || n > (1 << 24)) return fail(h, SIFT_E_INVALID, "n must be in [4, 2^24]");
+  if (n_hyp < 1 || n_hyp > (1 << 20)) return fail(h, SIFT_E_INVALID, "n_hyp must be in [1, 2^20]");
+  if (!(sigma_max > 0.f && sigma_max < 1e6f))
+    return fail(h, SIFT_E_INVALID, "sigma_max must be in (0, 1e6)");
+  if (!xa || !xb || !samples || !H_out || !best_out || !score_out || !inliers_out)
+    return fail(h, SIFT_E_INVALID, "null pointer argument");
+  if ((reinterpret_cast<uintptr_t>(xa) | reinterpret_cast<uintptr_t>(xb)) & 7)
+    return fail(h, SIFT_E_INVALID, "point arrays must be 8-byte aligned");
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t need = sift::magsac_workspace_bytes(n_hyp);
+  if (need > h->magsac_cap) {
+    if (h->magsac_ws) cudaFreeAsync(h->magsac_ws, h->magsac_stream ? h->magsac_stream : s);
+    h->magsac_ws = nullptr;
+    h->magsac_cap = 0;
+    if (cudaMallocAsync(&h->magsac_ws, need, s) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, SIFT_E_OOM, "MAGSAC++ workspace allocation failed");
+    }
+    h->magsac_cap = need;
+  }
+  h->magsac_stream = s;
+  const cudaError_t e = sift::launch_magsac(xa, xb, n, samples, n_hyp, sigma_max, h->magsac_ws, s,
+                                            H_out, best_out, score_out, inliers_out, scores_out);
+  if (e != cudaSuccess) return fail(h, SIFT_E_CUDA, std::string("MAGSAC++: ") + cudaGetErrorString(e));
   return SIFT_OK;
 }
 

@@ -187,6 +187,12 @@ cudaError_t launch_orientation(const Desc *d, int grid, cudaStream_t s);
 cudaError_t launch_ori_compact(const Desc *d, int grid, cudaStream_t s);
 cudaError_t launch_select(const Desc *d, int grid, cudaStream_t s);
 cudaError_t launch_descriptor(const Desc *d, int grid, cudaStream_t s);
+
+// MAGSAC++ homography verification (magsac.cu).
+size_t magsac_workspace_bytes(int n_hyp);
+cudaError_t launch_magsac(const float *xa, const float *xb, int n, const int *samples, int n_hyp,
+                          float sigma_max, void *ws, cudaStream_t s, double *H_out, int *best_out,
+                          float *score_out, unsigned char *inliers, float *scores_out);
 cudaError_t descriptor_set_attributes();
 // Matcher (match.cu)
 size_t match_workspace_bytes(int n_a, int n_b);

@@ -70,18 +70,39 @@ MUTANTS = {
 }
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_pins_catch_mutant(name, tmp_path):
-    before, after = MUTANTS[name]
-    src = open(os.path.join(ROOT, "oracle", "sift_oracle.py")).read()
+# Mistakes planted in the MAGSAC++ oracle, caught by its own pin file.
+MAGSAC_MUTANTS = {
+    "magsac_loss_no_truncation_shift": (
+        "        + 0.5 * rc * rc * (_upper_gamma(a, x) - _upper_gamma(a, k * k / 2.0)))",
+        "        + 0.5 * rc * rc * _upper_gamma(a, x))"),
+    "magsac_loss_lower_gamma_order": ("sigma_max * sigma_max * _lower_gamma(a + 1.0, x)",
+                                      "sigma_max * sigma_max * _lower_gamma(a, x)"),
+    "magsac_no_denormalise": ("    H = np.linalg.inv(Tb) @ Hn @ Ta", "    H = Hn"),
+    "magsac_dlt_row": ("[-x, -y, -1.0, 0.0, 0.0, 0.0, u * x, u * y, u]",
+                       "[-x, -y, -1.0, 0.0, 0.0, 0.0, u * x, v * y, u]"),
+    "magsac_residual_wrong_image": ("np.sqrt((px - xb[:, 0]) ** 2 + (py - xb[:, 1]) ** 2)",
+                                    "np.sqrt((px - xa[:, 0]) ** 2 + (py - xa[:, 1]) ** 2)"),
+    "magsac_weight_sigma_scale": (
+        "    x = t * t / (2.0 * sigma_max * sigma_max)",
+        "    x = t * t / (sigma_max * sigma_max)"),
+}
+
+CASES = ([(n, "sift_oracle.py", "test_oracle_pins.py") for n in sorted(MUTANTS)]
+         + [(n, "magsac.py", "test_magsac_oracle.py") for n in sorted(MAGSAC_MUTANTS)])
+
+
+@pytest.mark.parametrize("name,target,pins", CASES, ids=[c[0] for c in CASES])
+def test_pins_catch_mutant(name, target, pins, tmp_path):
+    before, after = (MUTANTS if target == "sift_oracle.py" else MAGSAC_MUTANTS)[name]
+    src = open(os.path.join(ROOT, "oracle", target)).read()
     assert before in src, "mutation anchor missing: " + name
     for d in ("oracle", "workloads"):
         shutil.copytree(os.path.join(ROOT, d), tmp_path / d,
                         ignore=shutil.ignore_patterns("__pycache__"))
     (tmp_path / "tests").mkdir()
-    for f in ("conftest.py", "test_oracle_pins.py"):
+    for f in ("conftest.py", pins):
         shutil.copy(os.path.join(ROOT, "tests", f), tmp_path / "tests" / f)
-    (tmp_path / "oracle" / "sift_oracle.py").write_text(src.replace(before, after))
-    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-q", "-x",
+    (tmp_path / "oracle" / target).write_text(src.replace(before, after))
+    r = subprocess.run([sys.executable, "-m", "pytest", "tests/" + pins, "-q", "-x",
                         "-p", "no:cacheprovider"], cwd=tmp_path, capture_output=True, text=True)
     assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
