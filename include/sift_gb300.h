@@ -182,6 +182,18 @@ sift_status sift_extract_noalloc(const sift_params *p, const float *img_dev, int
 sift_status sift_match(sift_handle *h, const float *desc_a, int n_a, const float *desc_b, int n_b,
                        float ratio, void *stream, int *out_match_a);
 
+/* Pack the outputs of the last extraction call on this handle (at most 128
+ * images: a larger batch is run in pieces and only its last piece is packed)
+ * into one device block, for a single device-to-host copy. Queue it on the
+ * extraction's stream, after the extraction and before the next one.
+ * Layout, N = the total kept keypoints of the batch, images in batch order:
+ * N x 128 float descriptors, then N floats each of x, y, sigma, angle,
+ * response, then N int32 each of octave, layer (540 bytes per keypoint; the
+ * per-image counts split it). dst_dev: device, 16-byte aligned, at least
+ * 540 x images x max_kpts bytes. Asynchronous. Errors: SIFT_E_INVALID for a
+ * null or misaligned dst, a short dst or no extraction yet; SIFT_E_CUDA. */
+sift_status sift_pack_outputs(sift_handle *h, void *stream, void *dst_dev, size_t dst_bytes);
+
 /* GPU MAGSAC++ homography verification (§3.6 "GPU MAGSAC++"): the best of
  * n_hyp minimal-sample homographies under the MAGSAC++ score.
  *   xa, xb: device, n x 2 FP32 (x, y) points of the two images, 8-byte aligned;

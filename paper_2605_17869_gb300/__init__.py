@@ -312,6 +312,8 @@ class Extractor:
         self.device = torch.device("cuda", torch.cuda.current_device())
         self._bufs = []
         self._counts = None
+        self._last_batch = 0
+        self._pack_dev = self._pack_host = self._counts_host = None
 
     def close(self):
         if getattr(self, "handle", None) is not None:
@@ -350,6 +352,7 @@ class Extractor:
         buf = self._buffers(1)[0]
         sift_extract(self.handle, img.data_ptr(), H, W, pitch, s.cuda_stream, buf.kpts(),
                      buf.desc.data_ptr(), self._counts.data_ptr())
+        self._last_batch = 1
         return buf, self._counts[:1]
 
     def extract(self, img, stream=None, copy: bool = True) -> Features:
@@ -370,7 +373,51 @@ class Extractor:
                            [d[1] for d in dims], [d[2] for d in dims], s.cuda_stream,
                            [b.kpts() for b in bufs], [b.desc.data_ptr() for b in bufs],
                            self._counts.data_ptr())
+        self._last_batch = len(imgs)
         return bufs, self._counts[:len(imgs)]
+
+    def download(self, stream=None):
+        """Bring the outputs of the last extract / extract_batch call to the host
+        in one transfer. The library packs them on the device
+        (sift_pack_outputs); the counts come back first, then exactly the packed
+        bytes. Returns (counts, per-image list of dicts of NumPy arrays x, y,
+        sigma, angle, response, octave, layer, desc); the arrays are views of a
+        reused pinned buffer, valid until the next download."""
+        import numpy as np
+        torch = _torch()
+        n_img = self._last_batch
+        if n_img < 1:
+            raise SiftError(SIFT_E_INVALID, "no extraction to download")
+        s = stream if stream is not None else torch.cuda.current_stream()
+        rec = 128 * 4 + 7 * 4
+        cap = n_img * self.params.max_kpts * rec
+        if self._pack_dev is None or self._pack_dev.numel() < cap:
+            self._pack_dev = torch.empty(cap, dtype=torch.uint8, device=self.device)
+            self._pack_host = torch.empty(cap, dtype=torch.uint8).pin_memory()
+        if self._counts_host is None or self._counts_host.numel() < n_img:
+            self._counts_host = torch.empty(max(n_img, 128), dtype=torch.int32).pin_memory()
+        _check(_lib().sift_pack_outputs(self.handle, c_void_p(s.cuda_stream),
+                                        c_void_p(self._pack_dev.data_ptr()), c_size_t(cap)),
+               self.handle, "sift_pack_outputs")
+        with torch.cuda.stream(s):
+            self._counts_host[:n_img].copy_(self._counts[:n_img], non_blocking=True)
+            s.synchronize()
+            counts = self._counts_host[:n_img].tolist()
+            N = sum(counts)
+            self._pack_host[:N * rec].copy_(self._pack_dev[:N * rec], non_blocking=True)
+            s.synchronize()
+        raw = self._pack_host.numpy()
+        desc = raw[:N * 512].view(np.float32).reshape(N, 128)
+        f = raw[N * 512:N * 532].view(np.float32).reshape(5, N)
+        i = raw[N * 532:N * 540].view(np.int32).reshape(2, N)
+        out, o = [], 0
+        for n in counts:
+            sl = slice(o, o + n)
+            out.append({"x": f[0, sl], "y": f[1, sl], "sigma": f[2, sl], "angle": f[3, sl],
+                        "response": f[4, sl], "octave": i[0, sl], "layer": i[1, sl],
+                        "desc": desc[sl]})
+            o += n
+        return counts, out
 
     def extract_batch(self, imgs, stream=None, copy: bool = True):
         bufs, cnt = self.extract_batch_async(imgs, stream)

@@ -56,6 +56,7 @@ SIGNATURES = {
                                      SiftKptsDev, c_void_p, c_void_p]),
     "sift_match": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_int, c_float, c_void_p,
                            c_void_p]),
+    "sift_pack_outputs": (c_int, [c_void_p, c_void_p, c_void_p, c_size_t]),
     "sift_magsac": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int, c_float, c_void_p,
                             c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "sift_last_stats": (c_int, [c_void_p, POINTER(c_int), c_int]),

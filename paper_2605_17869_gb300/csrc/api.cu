@@ -129,6 +129,21 @@ sift_status sift_match(sift_handle *h, const float *desc_a, int n_a, const float
   return SIFT_OK;
 }
 
+sift_status sift_pack_outputs(sift_handle *h, void *stream, void *dst_dev, size_t dst_bytes) {
+  if (!h || !dst_dev) return SIFT_E_INVALID;
+  if (h->serving) return fail(h, SIFT_E_INVALID, "handle is serving");
+  if (!h->eng->last_extract || h->eng->last_n < 1 || !h->eng->device_desc())
+    return fail(h, SIFT_E_INVALID, "the last call on this handle was not an extraction");
+  if (reinterpret_cast<uintptr_t>(dst_dev) & 15) return fail(h, SIFT_E_INVALID, "dst must be 16-byte aligned");
+  const size_t need = (size_t)h->eng->last_n * h->eng->params().max_kpts *
+                      (sift::kDescLen * sizeof(float) + 7 * 4);
+  if (dst_bytes < need) return fail(h, SIFT_E_INVALID, "dst smaller than last_n * max_kpts * 540 bytes");
+  const cudaError_t e = sift::launch_pack(h->eng->device_desc(), dst_dev, h->eng->sm_count(),
+                                          static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return fail(h, SIFT_E_CUDA, std::string("pack: ") + cudaGetErrorString(e));
+  return SIFT_OK;
+}
+
 sift_status sift_magsac(sift_handle *h, const float *xa, const float *xb, int n, const int *samples,
                         int n_hyp, float sigma_max, void *stream, double *H_out, int *best_out,
                         float *score_out, unsigned char *inliers_out, float *scores_out) {

@@ -509,7 +509,43 @@ __global__ void __launch_bounds__(kKpWarps * 32) k_descriptor(const Desc *__rest
   }
 }
 
+// Outputs of a batch packed into one block: the N x 128 descriptors, then x,
+// y, sigma, angle, response, octave, layer (N entries each), N = fin_flat[n],
+// images in batch order. One thread per float4 of descriptor, then one per
+// keypoint for the scalar fields.
+__global__ void __launch_bounds__(kThreads) k_pack(const Desc *__restrict__ d, float4 *__restrict__ dst) {
+  const int n = d->n_img;
+  const int N = d->fin_flat[n];
+  const int stride = gridDim.x * blockDim.x;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int q = g; q < N * (kDescLen / 4); q += stride) {
+    const int t = q / (kDescLen / 4), c = q - t * (kDescLen / 4);
+    const int b = find_owner(d->fin_flat, n, t);
+    const int j = t - d->fin_flat[b];
+    dst[q] = reinterpret_cast<const float4 *>(d->img[b].odesc + (long long)j * kDescLen)[c];
+  }
+  float *f = reinterpret_cast<float *>(dst + (long long)N * (kDescLen / 4));
+  int *oi = reinterpret_cast<int *>(f + 5LL * N);
+  for (int t = g; t < N; t += stride) {
+    const int b = find_owner(d->fin_flat, n, t);
+    const ImgDev &im = d->img[b];
+    const int j = t - d->fin_flat[b];
+    f[t] = im.ox[j];
+    f[N + t] = im.oy[j];
+    f[2LL * N + t] = im.osig[j];
+    f[3LL * N + t] = im.oang[j];
+    f[4LL * N + t] = im.oresp[j];
+    oi[t] = im.ooct[j];
+    oi[N + t] = im.olay[j];
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_pack(const Desc *d, void *dst, int n_sm, cudaStream_t s) {
+  k_pack<<<n_sm * 4, kThreads, 0, s>>>(d, static_cast<float4 *>(dst));
+  return cudaGetLastError();
+}
 
 cudaError_t launch_orientation(const Desc *d, int grid, cudaStream_t s) {
   cudaError_t e = launch_pdl(k_orientation, grid, kKpWarps * 32, 0, s, d);

@@ -605,6 +605,7 @@ sift_status Engine::run(int n, const ImgIn *imgs, cudaStream_t s) {
   ring_last_ = slot;
   last_stream = s;
   last_n = n;
+  last_extract = true;
   return SIFT_OK;
 }
 
@@ -640,6 +641,7 @@ sift_status Engine::run_pyramid(const ImgIn &img, cudaStream_t s) {
   ring_last_ = slot;
   last_stream = s;
   last_n = 1;
+  last_extract = false;  // a pyramid export: the descriptor holds no outputs
   return SIFT_OK;
 }
 

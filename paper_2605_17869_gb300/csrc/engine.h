@@ -54,6 +54,9 @@ class Engine {
   // Device-side per-image geometry of the last run (valid until the next run).
   const Desc &host_desc() const { return *hdesc_[ring_last_]; }
   const WsLayout &layout() const { return lay_; }
+  // Device descriptor of the last run (valid on its stream until the next run).
+  const Desc *device_desc() const { return ddesc_; }
+  int sm_count() const { return n_sm_; }
   char *workspace() const { return ws_; }
 
   void set_profiling(bool on);
@@ -84,6 +87,7 @@ class Engine {
   std::string err;
   cudaStream_t last_stream = nullptr;
   int last_n = 0;
+  bool last_extract = false;  // the last run was an extraction (outputs described)
 
  private:
   sift_status fill_plan(int n, const ImgIn *imgs, Desc &hd, WsLayout &lay, int *max_oct) const;

@@ -197,6 +197,30 @@ def test_batch_composition_invariance():
     assert sub == [single[2], single[0]]
 
 
+def test_download_packs_the_batch_outputs():
+    """download(): one packed device-to-host transfer (sift_pack_outputs) gives
+    exactly the per-image device outputs, bit for bit."""
+    shapes = [(300, 410), (97, 211), (256, 256)]
+    imgs = [torch.from_numpy(synth.make_image(synth.rng_for(17, i), *s)).cuda()
+            for i, s in enumerate(shapes)]
+    ex = pkg.Extractor(max_kpts=4096)
+    bufs, cnt = ex.extract_batch_async(imgs)
+    counts, host = ex.download()
+    assert counts == cnt.tolist() and sum(counts) > 0
+    for b, n, h in zip(bufs, counts, host):
+        f = b.view(n)
+        for k in ("x", "y", "sigma", "angle", "response", "octave", "layer", "desc"):
+            assert np.array_equal(getattr(f, k).cpu().numpy(), h[k]), k
+    want = bufs[1].view(counts[1]).desc.cpu().numpy().copy()
+    ex.extract(imgs[1])
+    counts1, host1 = ex.download()
+    assert counts1 == [counts[1]] and np.array_equal(host1[0]["desc"], want)
+    ex.pyramid(imgs[0])                 # a pyramid export leaves no outputs to pack
+    with pytest.raises(pkg.SiftError):
+        ex.download()
+    ex.close()
+
+
 # ------------------------------------------------------------------ upsample suppression
 
 def test_upsample_suppression_per_image():
