@@ -322,16 +322,21 @@ __global__ void __launch_bounds__(kThreads) k_refine(const Desc *__restrict__ d)
 
 cudaError_t extrema_set_attributes() { return cudaSuccess; }
 
-cudaError_t launch_extrema(const Desc *d, int oct, int n_scales, int grid, cudaStream_t s) {
+cudaError_t launch_extrema(const Desc *d, int oct, int n_scales, int grid, cudaStream_t s, bool pdl) {
+#define EXT_CASE(SS)                                                               \
+  case SS:                                                                         \
+    if (pdl) return launch_pdl(k_extrema<SS>, grid, kThreads, 0, s, d, oct);        \
+    k_extrema<SS><<<grid, kThreads, 0, s>>>(d, oct);                               \
+    return cudaGetLastError();
   switch (n_scales) {
-    case 2: return launch_pdl(k_extrema<2>, grid, kThreads, 0, s, d, oct);
-    case 3: return launch_pdl(k_extrema<3>, grid, kThreads, 0, s, d, oct);
-    case 4: return launch_pdl(k_extrema<4>, grid, kThreads, 0, s, d, oct);
-    case 5: return launch_pdl(k_extrema<5>, grid, kThreads, 0, s, d, oct);
-    case 6: return launch_pdl(k_extrema<6>, grid, kThreads, 0, s, d, oct);
+    EXT_CASE(2)
+    EXT_CASE(3)
+    EXT_CASE(4)
+    EXT_CASE(5)
+    EXT_CASE(6)
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
+#undef EXT_CASE
 }
 
 cudaError_t launch_bm_compact(const Desc *d, int grid, cudaStream_t s) {

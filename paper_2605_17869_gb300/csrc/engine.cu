@@ -119,6 +119,10 @@ Engine::~Engine() {
   }
   if (done_) cudaEventDestroy(done_);
   if (cap_) cudaStreamDestroy(cap_);
+  if (side_) cudaStreamDestroy(side_);
+  for (int o = 0; o < kMaxOct; o++)
+    if (fork_ev_[o]) cudaEventDestroy(fork_ev_[o]);
+  if (join_ev_) cudaEventDestroy(join_ev_);
 }
 
 sift_status Engine::init() {
@@ -141,6 +145,10 @@ sift_status Engine::init() {
   }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done_, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap_, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&side_, cudaStreamNonBlocking);
+  for (int o = 0; o < kMaxOct && e == cudaSuccess; o++)
+    e = cudaEventCreateWithFlags(&fork_ev_[o], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join_ev_, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     err = std::string("CUDA initialisation failed: ") + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? SIFT_E_OOM : SIFT_E_CUDA;
@@ -449,24 +457,31 @@ cudaError_t Engine::enqueue_pyramid(cudaStream_t s, int M, int modes, std::vecto
   return e;
 }
 
-cudaError_t Engine::enqueue_all(cudaStream_t s, int M, int modes, std::vector<ProfRec> *prof) {
+cudaError_t Engine::enqueue_all(cudaStream_t s, int M, int modes, std::vector<ProfRec> *prof,
+                                bool fork) {
   cudaError_t e = cudaSuccess;
   kernels_ = 0;
-  auto rec = [&](int cls, auto &&fn, int nk = 1) {
+  auto rec_on = [&](cudaStream_t st, int cls, auto &&fn, int nk = 1) {
     if (e != cudaSuccess) return;
     kernels_ += nk;
     ProfRec r{nullptr, nullptr, cls};
     if (prof) {
       cudaEventCreate(&r.a);
       cudaEventCreate(&r.b);
-      e = cudaEventRecordWithFlags(r.a, s, cudaEventRecordExternal);
+      e = cudaEventRecordWithFlags(r.a, st, cudaEventRecordExternal);
     }
     if (e == cudaSuccess) e = fn();
     if (prof && e == cudaSuccess) {
-      e = cudaEventRecordWithFlags(r.b, s, cudaEventRecordExternal);
+      e = cudaEventRecordWithFlags(r.b, st, cudaEventRecordExternal);
       prof->push_back(r);
     }
   };
+  auto rec = [&](int cls, auto &&fn, int nk = 1) { rec_on(s, cls, fn, nk); };
+  // With fork, the extrema scan of octave o < M - 1 runs on a side branch (side_)
+  // concurrently with the blurs of octave o + 1: it reads only octave o's levels,
+  // and they read only its level S. The branch joins the main stream before the
+  // last octave's scan, which the keypoint stages follow.
+  fork = fork && side_ != nullptr && M > 1;
   const Desc *d = ddesc_;
   const int g4 = n_sm_ * 4;
   for (int o = 0; o < M; o++) {
@@ -489,7 +504,17 @@ cudaError_t Engine::enqueue_all(cudaStream_t s, int M, int modes, std::vector<Pr
                                  o > 0 && l == 1);
       });
     }
-    rec(PC_EXTREMA, [&] { return launch_extrema(d, o, S_, n_sm_ * 3, s); });
+    if (fork && o + 1 < M) {
+      if (e == cudaSuccess) e = cudaEventRecord(fork_ev_[o], s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(side_, fork_ev_[o], 0);
+      rec_on(side_, PC_EXTREMA, [&] { return launch_extrema(d, o, S_, n_sm_ * 3, side_, false); });
+    } else if (fork) {
+      if (e == cudaSuccess) e = cudaEventRecord(join_ev_, side_);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, join_ev_, 0);
+      rec(PC_EXTREMA, [&] { return launch_extrema(d, o, S_, n_sm_ * 3, s, false); });
+    } else {
+      rec(PC_EXTREMA, [&] { return launch_extrema(d, o, S_, n_sm_ * 3, s); });
+    }
   }
   rec(PC_KEYPOINT, [&] { return launch_bm_compact(d, g4, s); }, 3);
   rec(PC_KEYPOINT, [&] { return launch_refine(d, g4, s); });
@@ -527,7 +552,7 @@ sift_status Engine::get_graph(int M, int modes, cudaGraphExec_t *out) {
   GraphEntry ge;
   if (profiling_) ge.prof = new std::vector<ProfRec>();
   cudaError_t e = cudaStreamBeginCapture(cap_, cudaStreamCaptureModeThreadLocal);
-  cudaError_t e1 = e == cudaSuccess ? enqueue_all(cap_, M, modes, ge.prof) : e;
+  cudaError_t e1 = e == cudaSuccess ? enqueue_all(cap_, M, modes, ge.prof, true) : e;
   cudaGraph_t g = nullptr;
   cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(cap_, &g) : e;
   cudaError_t e3 = (e1 == cudaSuccess && e2 == cudaSuccess) ? cudaGraphInstantiate(&ge.exec, g, 0)

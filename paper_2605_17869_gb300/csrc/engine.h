@@ -95,7 +95,10 @@ class Engine {
   sift_status upload(Desc *hd, size_t bytes, cudaStream_t s);
   // modes: bit 0 set if an image is processed as is, bit 1 if one is magnified.
   cudaError_t enqueue_pyramid(cudaStream_t s, int max_oct, int modes, std::vector<struct ProfRec> *prof);
-  cudaError_t enqueue_all(cudaStream_t s, int max_oct, int modes, std::vector<struct ProfRec> *prof);
+  // fork: run the extrema scans of all but the last octave on a side branch
+  // (graph capture only; the allocation-free path runs everything in order).
+  cudaError_t enqueue_all(cudaStream_t s, int max_oct, int modes, std::vector<struct ProfRec> *prof,
+                          bool fork = false);
   sift_status get_graph(int max_oct, int modes, cudaGraphExec_t *out);
   void drop_graphs();
   int grid_blur(int R, int kind, int mode) const;
@@ -119,6 +122,9 @@ class Engine {
   int ring_ = 0, ring_last_ = 0;
   cudaEvent_t done_ = nullptr;   // recorded after each run
   cudaStream_t cap_ = nullptr;   // capture stream
+  cudaStream_t side_ = nullptr;  // side branch of the captured graph (extrema scans)
+  cudaEvent_t fork_ev_[kMaxOct] = {};
+  cudaEvent_t join_ev_ = nullptr;
 
   struct GraphEntry {
     cudaGraphExec_t exec = nullptr;

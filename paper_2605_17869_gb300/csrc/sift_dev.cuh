@@ -177,7 +177,9 @@ int blur_blocks_per_sm(int R, int th_kind, int mode);
 cudaError_t blur_set_attributes();
 
 // Detection (detect.cu)
-cudaError_t launch_extrema(const Desc *d, int oct, int n_scales, int grid, cudaStream_t s);
+// pdl: launch as a programmatic dependent of the previous kernel on s.
+cudaError_t launch_extrema(const Desc *d, int oct, int n_scales, int grid, cudaStream_t s,
+                           bool pdl = true);
 cudaError_t extrema_set_attributes();
 cudaError_t launch_bm_compact(const Desc *d, int grid, cudaStream_t s);
 cudaError_t launch_refine(const Desc *d, int grid, cudaStream_t s);
