@@ -477,10 +477,10 @@ cudaError_t Engine::enqueue_all(cudaStream_t s, int M, int modes, std::vector<Pr
     }
   };
   auto rec = [&](int cls, auto &&fn, int nk = 1) { rec_on(s, cls, fn, nk); };
-  // With fork, the extrema scan of octave o < M - 1 runs on a side branch (side_)
-  // concurrently with the blurs of octave o + 1: it reads only octave o's levels,
-  // and they read only its level S. The branch joins the main stream before the
-  // last octave's scan, which the keypoint stages follow.
+  // With fork, the last two levels and the extrema scan of octave o < M - 1 run
+  // on a side branch (side_) concurrently with octave o + 1, which reads only
+  // level S of octave o. The branch joins the main stream before the last
+  // octave's scan, which the keypoint stages follow.
   fork = fork && side_ != nullptr && M > 1;
   const Desc *d = ddesc_;
   const int g4 = n_sm_ * 4;
@@ -497,17 +497,23 @@ cudaError_t Engine::enqueue_all(cudaStream_t s, int M, int modes, std::vector<Pr
     }
     // Octaves above 0: the level-1 launch also produces level 0 by decimating
     // level S of the previous octave (no separate decimation pass).
+    // With fork, levels S + 1 and S + 2 of octave o < M - 1 and its extrema scan
+    // go to the side branch once level S (all the next octave reads) is done.
+    const bool branch = fork && o + 1 < M;
     for (int l = 1; l <= S_ + 2; l++) {
       const int kind = o == 0 ? tun_.lvl_kind[l] : TK_BLUR32;  // tuned on octave 0 only
-      rec(PC_BLUR, [&] {
-        return launch_level_blur(d, o, l, lvl_R_[l], lvl_t_[l], kind, grid_blur(lvl_R_[l], kind, 0), s,
-                                 o > 0 && l == 1);
+      const bool on_side = branch && l > S_;
+      if (on_side && l == S_ + 1) {
+        if (e == cudaSuccess) e = cudaEventRecord(fork_ev_[o], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(side_, fork_ev_[o], 0);
+      }
+      rec_on(on_side ? side_ : s, PC_BLUR, [&] {
+        return launch_level_blur(d, o, l, lvl_R_[l], lvl_t_[l], kind, grid_blur(lvl_R_[l], kind, 0),
+                                 on_side ? side_ : s, o > 0 && l == 1, !(on_side && l == S_ + 1));
       });
     }
-    if (fork && o + 1 < M) {
-      if (e == cudaSuccess) e = cudaEventRecord(fork_ev_[o], s);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(side_, fork_ev_[o], 0);
-      rec_on(side_, PC_EXTREMA, [&] { return launch_extrema(d, o, S_, n_sm_ * 3, side_, false); });
+    if (branch) {
+      rec_on(side_, PC_EXTREMA, [&] { return launch_extrema(d, o, S_, n_sm_ * 3, side_); });
     } else if (fork) {
       if (e == cudaSuccess) e = cudaEventRecord(join_ev_, side_);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(s, join_ev_, 0);

@@ -629,26 +629,30 @@ cudaError_t blur_set_attributes() {
 }
 
 cudaError_t launch_level_blur(const Desc *d, int oct, int lvl_out, int R, const BlurTaps &t,
-                              int th_kind, int grid, cudaStream_t s, bool from_prev_octave) {
+                              int th_kind, int grid, cudaStream_t s, bool from_prev_octave,
+                              bool pdl) {
   const bool m3 = from_prev_octave;
-#define CASE_R(RR)                                                                               \
-  case RR:                                                                                       \
-    if (th_kind == TK_BLUR64) {                                                                  \
-      return m3 ? launch_pdl(k_blur<RR, 64, 3>, grid, kThreads, smem_bytes<RR, 64, 3>(), s, d, oct, lvl_out, t) \
-                : launch_pdl(k_blur<RR, 64, 0>, grid, kThreads, smem_bytes<RR, 64, 0>(), s, d, oct, lvl_out, t); \
-    } else {                                                                                     \
-      return m3 ? launch_pdl(k_blur<RR, 32, 3>, grid, kThreads, smem_bytes<RR, 32, 3>(), s, d, oct, lvl_out, t) \
-                : launch_pdl(k_blur<RR, 32, 0>, grid, kThreads, smem_bytes<RR, 32, 0>(), s, d, oct, lvl_out, t); \
-    }                                                                                            \
-    break;
+  // A programmatic dependent of the previous kernel on s, or (pdl false) a plain
+  // launch that waits for everything before it (a branch after an event wait).
+  auto go = [&](auto kern, size_t smem, auto... args) -> cudaError_t {
+    if (pdl) return launch_pdl(kern, grid, kThreads, smem, s, d, oct, lvl_out, args...);
+    kern<<<grid, kThreads, smem, s>>>(d, oct, lvl_out, args...);
+    return cudaGetLastError();
+  };
+#define CASE_R(RR)                                                                        \
+  case RR:                                                                                \
+    if (th_kind == TK_BLUR64)                                                             \
+      return m3 ? go(k_blur<RR, 64, 3>, smem_bytes<RR, 64, 3>(), t)                         \
+                : go(k_blur<RR, 64, 0>, smem_bytes<RR, 64, 0>(), t);                        \
+    return m3 ? go(k_blur<RR, 32, 3>, smem_bytes<RR, 32, 3>(), t)                           \
+              : go(k_blur<RR, 32, 0>, smem_bytes<RR, 32, 0>(), t);
   switch (R) {
     SIFT_FOR_EACH_R(CASE_R)
     default:
-      return m3 ? launch_pdl(k_blur_generic<3>, grid, kThreads, generic_smem_bytes(R), s, d, oct, lvl_out, R, t)
-                : launch_pdl(k_blur_generic<0>, grid, kThreads, generic_smem_bytes(R), s, d, oct, lvl_out, R, t);
+      return m3 ? go(k_blur_generic<3>, generic_smem_bytes(R), R, t)
+                : go(k_blur_generic<0>, generic_smem_bytes(R), R, t);
   }
 #undef CASE_R
-  return cudaGetLastError();
 }
 
 cudaError_t launch_base_blur(const Desc *d, int R, const BlurTaps &t, int th_kind, bool upsample,

@@ -170,8 +170,10 @@ __device__ __forceinline__ int refl101(int i, int n) {
 // Pyramid (pyramid.cu)
 cudaError_t launch_base_blur(const Desc *d, int R, const BlurTaps &t, int th_kind, bool upsample,
                              int grid, cudaStream_t s);
+// pdl: launch as a programmatic dependent of the previous kernel on s.
 cudaError_t launch_level_blur(const Desc *d, int oct, int lvl_out, int R, const BlurTaps &t,
-                              int th_kind, int grid, cudaStream_t s, bool from_prev_octave = false);
+                              int th_kind, int grid, cudaStream_t s, bool from_prev_octave = false,
+                              bool pdl = true);
 int blur_smem_bytes(int R, int th_kind);
 int blur_blocks_per_sm(int R, int th_kind, int mode);
 cudaError_t blur_set_attributes();
