@@ -299,12 +299,23 @@ __global__ void __launch_bounds__(1024) k_select(const Desc *__restrict__ d) {
 
 // ------------------------------------------------------------- descriptor
 
-// Accumulate one gradient sample at bin coordinates (rx, ry) from the
-// keypoint, (u, v) = (rx, ry) + 3/2, into the thread's histogram column: weight
-// m * exp(-(rx^2 + ry^2) / 8), orientation relative to th, trilinear split.
-__device__ __forceinline__ void desc_vote(float *hist, int lane, float rx, float ry, float gx,
-                                          float gy, float th) {
-  const float u = rx + 1.5f, v = ry + 1.5f;
+// Histogram columns of the descriptor: kDescCols per warp, column lane % 16,
+// so lanes l and l + 16 share a column and commit their votes in two passes
+// (half-warp 0, then half-warp 1): within a pass no two lanes touch the same
+// word, and across passes the order is fixed. Layout [bin][column].
+constexpr int kDescCols = 16;
+
+// The 8 trilinear targets of one gradient sample at bin coordinates (rx, ry)
+// from the keypoint, (u, v) = (rx, ry) + 3/2: weight m * exp(-(rx^2 + ry^2) /
+// 8), orientation relative to th. Targets outside the 4 x 4 cells get bin -1.
+struct Vote {
+  int bin[8];
+  float w[8];
+};
+
+__device__ __forceinline__ void desc_targets(Vote &v, float rx, float ry, float gx, float gy,
+                                             float th) {
+  const float u = rx + 1.5f, vv0 = ry + 1.5f;
   const float mag = sqrtf(gx * gx + gy * gy);
   float phi = atan2f(gy, gx) - th;
   if (phi < 0.f) phi += kTwoPi;
@@ -312,26 +323,42 @@ __device__ __forceinline__ void desc_vote(float *hist, int lane, float rx, float
   if (phi >= kTwoPi) phi -= kTwoPi;
   const float ob = phi * (8.0f / kTwoPi);
   const float wt = mag * expf(-(rx * rx + ry * ry) * 0.125f);
-  const float u0f = floorf(u), v0f = floorf(v), o0f = floorf(ob);
-  const float fu = u - u0f, fv = v - v0f, fo = ob - o0f;
+  const float u0f = floorf(u), v0f = floorf(vv0), o0f = floorf(ob);
+  const float fu = u - u0f, fv = vv0 - v0f, fo = ob - o0f;
   const int u0 = (int)u0f, v0 = (int)v0f, o0 = (int)o0f;
 #pragma unroll
   for (int dv = 0; dv < 2; dv++) {
     const int vv = v0 + dv;
-    if (vv < 0 || vv > 3) continue;
     const float wv = dv ? fv : 1.f - fv;
 #pragma unroll
     for (int du = 0; du < 2; du++) {
       const int uu = u0 + du;
-      if (uu < 0 || uu > 3) continue;
       const float wu = du ? fu : 1.f - fu;
+      const bool in = vv >= 0 && vv <= 3 && uu >= 0 && uu <= 3;
 #pragma unroll
       for (int dob = 0; dob < 2; dob++) {
+        const int k = (dv * 2 + du) * 2 + dob;
         const int oo = (o0 + dob) & 7;
         const float wo = dob ? fo : 1.f - fo;
-        hist[((vv * 4 + uu) * 8 + oo) * 32 + lane] += wt * wv * wu * wo;
+        v.bin[k] = in ? (vv * 4 + uu) * 8 + oo : -1;
+        v.w[k] = wt * wv * wu * wo;
       }
     }
+  }
+}
+
+// Add the votes of the warp's lanes (ok: the lane has a sample) to the warp's
+// columns: half-warp 0, then half-warp 1. Every lane of the warp must call it.
+__device__ __forceinline__ void desc_commit(float *hist, int lane, bool ok, const Vote &v) {
+  const int col = lane & (kDescCols - 1);
+#pragma unroll
+  for (int half = 0; half < 2; half++) {
+    if (ok && (lane >> 4) == half) {
+#pragma unroll
+      for (int k = 0; k < 8; k++)
+        if (v.bin[k] >= 0) hist[v.bin[k] * kDescCols + col] += v.w[k];
+    }
+    __syncwarp();
   }
 }
 
@@ -347,14 +374,14 @@ __constant__ float kDspScale[5] = {0.5f, 0.70710678118654752f, 1.0f, 1.414213562
 // scales vote into the same histogram (pooling before normalisation).
 // Positions are kept relative to the integer keypoint pixel, so the
 // interpolation weights keep full FP32 precision in large octaves.
-__global__ void __launch_bounds__(kKpWarps * 32) k_descriptor(const Desc *__restrict__ d) {
+__global__ void __launch_bounds__(kKpWarps * 32, 6) k_descriptor(const Desc *__restrict__ d) {
   pdl_wait();
   extern __shared__ __align__(16) float dsm[];
   __shared__ float red[kKpWarps];
   __shared__ int s_row_lo[kKpWarps * 32], s_row_pre[kKpWarps * 32 + 1];
   __shared__ int s_scan[kKpWarps + 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  float *hist = dsm + warp * (kDescLen * 32);
+  float *hist = dsm + warp * (kDescLen * kDescCols);
   const int n = d->n_img;
   const int total = d->fin_flat[n];
   for (int t = blockIdx.x; t < total; t += gridDim.x) {
@@ -388,7 +415,7 @@ __global__ void __launch_bounds__(kKpWarps * 32) k_descriptor(const Desc *__rest
     {
       float4 *h4 = reinterpret_cast<float4 *>(hist);
 #pragma unroll 8
-      for (int k = lane; k < kDescLen * 8; k += 32) h4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int k = lane; k < kDescLen * kDescCols / 4; k += 32) h4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncwarp();
     if (!d->dsp) {
@@ -436,19 +463,28 @@ __global__ void __launch_bounds__(kKpWarps * 32) k_descriptor(const Desc *__rest
         if (tid == 0) s_row_pre[nr] = tot;
         __syncthreads();
         int row = 0;
-        for (int q = tid; q < tot; q += kKpWarps * 32) {
-          while (s_row_pre[row + 1] <= q) row++;
-          const int jy = j0 + row;
-          const int i = s_row_lo[row] + (q - s_row_pre[row]);
-          const float ox = (float)i - r.dx, oy = (float)jy - r.dy;
-          const float rx = (ct * ox + st * oy) * inv_w;
-          const float ry = (-st * ox + ct * oy) * inv_w;
-          const float u = rx + 1.5f, v = ry + 1.5f;
-          if (!(u > -1.f && u < 4.f && v > -1.f && v < 4.f)) continue;
-          const float *p = L + (long long)(r.y + jy) * od.pitch + (r.x + i);
-          const float gx = __ldg(p + 1) - __ldg(p - 1);
-          const float gy = __ldg(p + od.pitch) - __ldg(p - od.pitch);
-          desc_vote(hist, lane, rx, ry, gx, gy, th);
+        // Warp-uniform trip count: every lane reaches the commit's __syncwarp.
+        for (int q0 = 0; q0 < tot; q0 += kKpWarps * 32) {
+          const int q = q0 + tid;
+          bool ok = q < tot;
+          Vote vt;
+          if (ok) {
+            while (s_row_pre[row + 1] <= q) row++;
+            const int jy = j0 + row;
+            const int i = s_row_lo[row] + (q - s_row_pre[row]);
+            const float ox = (float)i - r.dx, oy = (float)jy - r.dy;
+            const float rx = (ct * ox + st * oy) * inv_w;
+            const float ry = (-st * ox + ct * oy) * inv_w;
+            const float u = rx + 1.5f, v = ry + 1.5f;
+            ok = u > -1.f && u < 4.f && v > -1.f && v < 4.f;
+            if (ok) {
+              const float *p = L + (long long)(r.y + jy) * od.pitch + (r.x + i);
+              const float gx = __ldg(p + 1) - __ldg(p - 1);
+              const float gy = __ldg(p + od.pitch) - __ldg(p - od.pitch);
+              desc_targets(vt, rx, ry, gx, gy, th);
+            }
+          }
+          desc_commit(hist, lane, ok, vt);
         }
         __syncthreads();
       }
@@ -462,7 +498,12 @@ __global__ void __launch_bounds__(kKpWarps * 32) k_descriptor(const Desc *__rest
           const float yr = r.dy + wb * (st * rx + ct * ry);
           const float xf = floorf(xr), yf = floorf(yr);
           const int x0 = r.x + (int)xf, y0 = r.y + (int)yf;
-          if (x0 < 1 || x0 > od.W - 3 || y0 < 1 || y0 > od.H - 3) continue;
+          const bool ok = !(x0 < 1 || x0 > od.W - 3 || y0 < 1 || y0 > od.H - 3);
+          Vote vt;
+          if (!ok) {  // (1024 samples per scale: the trip count is warp-uniform)
+            desc_commit(hist, lane, false, vt);
+            continue;
+          }
           const float fx = xr - xf, fy = yr - yf, gx1 = 1.f - fx, gy1 = 1.f - fy;
           const float *p = L + (long long)y0 * od.pitch + x0;
           const float *pm = p - od.pitch, *pp = p + od.pitch, *p2 = pp + od.pitch;
@@ -475,20 +516,22 @@ __global__ void __launch_bounds__(kKpWarps * 32) k_descriptor(const Desc *__rest
                            fy * (gx1 * __ldg(p2) + fx * __ldg(p2 + 1));
           const float ym = gy1 * (gx1 * __ldg(pm) + fx * __ldg(pm + 1)) +
                            fy * (gx1 * __ldg(p) + fx * __ldg(p + 1));
-          desc_vote(hist, lane, rx, ry, xp - xm, yp - ym, th);
+          desc_targets(vt, rx, ry, xp - xm, yp - ym, th);
+          desc_commit(hist, lane, true, vt);
         }
       }
     }
     __syncthreads();
-    // Bin tid: per warp, the 32 lane columns starting at lane tid % 32 (32
-    // distinct banks across a warp), then the warp partials in warp order.
+    // Bin tid: per warp, the 16 columns starting at column (tid / 2) % 16 (with
+    // the layout [bin][16], the 32 threads of a warp then read 32 distinct
+    // banks), then the warp partials in warp order.
     float pw[kKpWarps];
 #pragma unroll
     for (int w = 0; w < kKpWarps; w++) {
-      const float *h = dsm + w * (kDescLen * 32) + tid * 32;
+      const float *h = dsm + w * (kDescLen * kDescCols) + tid * kDescCols;
       float s = 0.f;
-#pragma unroll 8
-      for (int l = 0; l < 32; l++) s += h[(l + tid) & 31];
+#pragma unroll
+      for (int l = 0; l < kDescCols; l++) s += h[(l + (tid >> 1)) & (kDescCols - 1)];
       pw[w] = s;
     }
     float val = pw[0];
@@ -567,7 +610,7 @@ cudaError_t launch_select(const Desc *d, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-int descriptor_smem_bytes() { return kKpWarps * kDescLen * 32 * (int)sizeof(float); }
+int descriptor_smem_bytes() { return kKpWarps * kDescLen * kDescCols * (int)sizeof(float); }
 
 cudaError_t descriptor_set_attributes() {
   return cudaFuncSetAttribute(k_descriptor, cudaFuncAttributeMaxDynamicSharedMemorySize,

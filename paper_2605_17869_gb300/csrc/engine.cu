@@ -527,7 +527,7 @@ cudaError_t Engine::enqueue_all(cudaStream_t s, int M, int modes, std::vector<Pr
   rec(PC_KEYPOINT, [&] { return launch_orientation(d, n_sm_ * 8, s); });
   rec(PC_KEYPOINT, [&] { return launch_ori_compact(d, g4, s); }, 3);
   rec(PC_KEYPOINT, [&] { return launch_select(d, n_sm_, s); });
-  rec(PC_DESCRIPTOR, [&] { return launch_descriptor(d, n_sm_ * 3, s); });
+  rec(PC_DESCRIPTOR, [&] { return launch_descriptor(d, n_sm_ * 6, s); });
   return e;
 }
 
@@ -558,7 +558,10 @@ sift_status Engine::get_graph(int M, int modes, cudaGraphExec_t *out) {
   GraphEntry ge;
   if (profiling_) ge.prof = new std::vector<ProfRec>();
   cudaError_t e = cudaStreamBeginCapture(cap_, cudaStreamCaptureModeThreadLocal);
-  cudaError_t e1 = e == cudaSuccess ? enqueue_all(cap_, M, modes, ge.prof, true) : e;
+  // The profiled graph (an event pair around every launch) keeps every launch
+  // on one stream, so that each kernel's time is its own and not shared with a
+  // concurrent branch.
+  cudaError_t e1 = e == cudaSuccess ? enqueue_all(cap_, M, modes, ge.prof, !profiling_) : e;
   cudaGraph_t g = nullptr;
   cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(cap_, &g) : e;
   cudaError_t e3 = (e1 == cudaSuccess && e2 == cudaSuccess) ? cudaGraphInstantiate(&ge.exec, g, 0)
