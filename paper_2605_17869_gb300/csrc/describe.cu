@@ -34,6 +34,15 @@ __device__ __forceinline__ float block_sum_f(float v, float *red) {
   return s;
 }
 
+// 4-byte global -> shared asynchronous copy; with valid false the destination
+// is zero-filled and no source byte is read.
+__device__ __forceinline__ void cp_async4_zfill(float *dst, const float *src, bool valid) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src),
+               "r"(valid ? 4 : 0)
+               : "memory");
+}
+
 __device__ __forceinline__ float sigma_of(const Desc *d, const RefRec &r) {
   return d->sigma0 * exp2f(((float)r.s + r.ds) / (float)d->n_scales);
 }
@@ -81,19 +90,20 @@ __global__ void __launch_bounds__(kKpWarps * 32) k_orientation(const Desc *__res
     const int B = kOriWin / wd - 2;  // >= 1: the parameter check bounds R
     for (int jb = -R; jb <= R; jb += B) {
       const int nb = min(B, R - jb + 1);
+      // Every copy is issued before any is waited for (cp.async, 4 bytes,
+      // zero-filled outside the image, where no byte is read).
       for (int rr = warp; rr < nb + 2; rr += kKpWarps) {
         const int gy = r.y + jb - 1 + rr;
+        const bool row_ok = gy >= 0 && gy < od.H;
+        const float *src = L + (long long)(row_ok ? gy : 0) * od.pitch;
         float *dst = win + rr * wd;
-        if (gy >= 0 && gy < od.H) {
-          const float *src = L + (long long)gy * od.pitch;
-          for (int c = lane; c < wd; c += 32) {
-            const int gx = r.x - R - 1 + c;
-            dst[c] = (gx >= 0 && gx < od.W) ? __ldg(src + gx) : 0.f;
-          }
-        } else {
-          for (int c = lane; c < wd; c += 32) dst[c] = 0.f;
+        for (int c = lane; c < wd; c += 32) {
+          const int gx = r.x - R - 1 + c;
+          const bool ok = row_ok && gx >= 0 && gx < od.W;
+          cp_async4_zfill(dst + c, src + (ok ? gx : 0), ok);
         }
       }
+      asm volatile("cp.async.wait_all;\n" ::: "memory");
       __syncthreads();
       const int ns = nb * side;
       for (int idx = tid; idx < ns; idx += kKpWarps * 32) {
