@@ -119,10 +119,12 @@ Engine::~Engine() {
   }
   if (done_) cudaEventDestroy(done_);
   if (cap_) cudaStreamDestroy(cap_);
-  if (side_) cudaStreamDestroy(side_);
+  for (int k = 0; k < kSides; k++) {
+    if (side_[k]) cudaStreamDestroy(side_[k]);
+    if (join_ev_[k]) cudaEventDestroy(join_ev_[k]);
+  }
   for (int o = 0; o < kMaxOct; o++)
     if (fork_ev_[o]) cudaEventDestroy(fork_ev_[o]);
-  if (join_ev_) cudaEventDestroy(join_ev_);
 }
 
 sift_status Engine::init() {
@@ -145,10 +147,12 @@ sift_status Engine::init() {
   }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done_, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap_, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&side_, cudaStreamNonBlocking);
+  for (int k = 0; k < kSides && e == cudaSuccess; k++) {
+    e = cudaStreamCreateWithFlags(&side_[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join_ev_[k], cudaEventDisableTiming);
+  }
   for (int o = 0; o < kMaxOct && e == cudaSuccess; o++)
     e = cudaEventCreateWithFlags(&fork_ev_[o], cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join_ev_, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     err = std::string("CUDA initialisation failed: ") + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? SIFT_E_OOM : SIFT_E_CUDA;
@@ -478,10 +482,11 @@ cudaError_t Engine::enqueue_all(cudaStream_t s, int M, int modes, std::vector<Pr
   };
   auto rec = [&](int cls, auto &&fn, int nk = 1) { rec_on(s, cls, fn, nk); };
   // With fork, the last two levels and the extrema scan of octave o < M - 1 run
-  // on a side branch (side_) concurrently with octave o + 1, which reads only
-  // level S of octave o. The branch joins the main stream before the last
-  // octave's scan, which the keypoint stages follow.
-  fork = fork && side_ != nullptr && M > 1;
+  // on a side branch (side_[o % kSides]) concurrently with octave o + 1, which
+  // reads only level S of octave o, and with the other octaves' branches. The
+  // branches join the main stream before the last octave's scan, which the
+  // keypoint stages follow.
+  fork = fork && side_[0] != nullptr && M > 1;
   const Desc *d = ddesc_;
   const int g4 = n_sm_ * 4;
   for (int o = 0; o < M; o++) {
@@ -500,23 +505,26 @@ cudaError_t Engine::enqueue_all(cudaStream_t s, int M, int modes, std::vector<Pr
     // With fork, levels S + 1 and S + 2 of octave o < M - 1 and its extrema scan
     // go to the side branch once level S (all the next octave reads) is done.
     const bool branch = fork && o + 1 < M;
+    cudaStream_t side = side_[o % kSides];
     for (int l = 1; l <= S_ + 2; l++) {
       const int kind = o == 0 ? tun_.lvl_kind[l] : TK_BLUR32;  // tuned on octave 0 only
       const bool on_side = branch && l > S_;
       if (on_side && l == S_ + 1) {
         if (e == cudaSuccess) e = cudaEventRecord(fork_ev_[o], s);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(side_, fork_ev_[o], 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(side, fork_ev_[o], 0);
       }
-      rec_on(on_side ? side_ : s, PC_BLUR, [&] {
+      rec_on(on_side ? side : s, PC_BLUR, [&] {
         return launch_level_blur(d, o, l, lvl_R_[l], lvl_t_[l], kind, grid_blur(lvl_R_[l], kind, 0),
-                                 on_side ? side_ : s, o > 0 && l == 1, !(on_side && l == S_ + 1));
+                                 on_side ? side : s, o > 0 && l == 1, !(on_side && l == S_ + 1));
       });
     }
     if (branch) {
-      rec_on(side_, PC_EXTREMA, [&] { return launch_extrema(d, o, S_, n_sm_ * 3, side_); });
+      rec_on(side, PC_EXTREMA, [&] { return launch_extrema(d, o, S_, n_sm_ * 3, side); });
     } else if (fork) {
-      if (e == cudaSuccess) e = cudaEventRecord(join_ev_, side_);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, join_ev_, 0);
+      for (int k = 0; k < kSides && k < M - 1; k++) {
+        if (e == cudaSuccess) e = cudaEventRecord(join_ev_[k], side_[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, join_ev_[k], 0);
+      }
       rec(PC_EXTREMA, [&] { return launch_extrema(d, o, S_, n_sm_ * 3, s, false); });
     } else {
       rec(PC_EXTREMA, [&] { return launch_extrema(d, o, S_, n_sm_ * 3, s); });

@@ -122,9 +122,12 @@ class Engine {
   int ring_ = 0, ring_last_ = 0;
   cudaEvent_t done_ = nullptr;   // recorded after each run
   cudaStream_t cap_ = nullptr;   // capture stream
-  cudaStream_t side_ = nullptr;  // side branch of the captured graph (extrema scans)
+  // Side branches of the captured graph: octave o's last two levels and extrema
+  // scan run on side_[o % kSides].
+  static constexpr int kSides = 3;
+  cudaStream_t side_[kSides] = {};
   cudaEvent_t fork_ev_[kMaxOct] = {};
-  cudaEvent_t join_ev_ = nullptr;
+  cudaEvent_t join_ev_[kSides] = {};
 
   struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
