@@ -600,6 +600,128 @@ int blur_smem_bytes_mode(int R, int th_kind, int mode) {
 
 int generic_smem_bytes(int R) { return (2 * 32 + 2 * R) * kSinW * (int)sizeof(float); }
 
+// ------------------------------------------------- magnified base, polyphase
+//
+// The base level of a magnified first octave is G = g * U(I): U the 2x bilinear
+// magnification (u[2k] = I[k], u[2k+1] = (I[k] + I[k+1]) / 2, last sample
+// clamped), g the base Gaussian with reflect-101 on the magnified grid. Both
+// are linear, so output sample 2k + p (p = 0, 1) of a row is a 2Q + 1 tap
+// filter c_p of the input around k, with c_p[q] = sum_t g[t] * (weight of
+// I[k + q] in u[2k + p + t]), Q = (R + 2) / 2. The reflection and the clamp
+// are exact on an extended input I_e[i] = I[refl101(2i, 2n) / 2]
+// (reflect-101 on the left, half-sample symmetric on the right, which is what
+// the magnified grid's reflection maps back to). A tile of 128 x 32 outputs
+// stages (64 + 2Q) x (16 + 2Q) input samples, filters its rows into 128
+// columns at input-row resolution, then its columns into 32 rows: about 12
+// FMAs per output against 22 for the two passes on the magnified grid, and no
+// magnified window. Each output is the same fixed chain (sum over q
+// ascending, rows then columns) whatever the tile.
+constexpr int kPolyThreads = 256;
+constexpr int kPolyMaxQ = kMaxR / 2 + 1;
+
+struct PolyTaps {
+  float c[2][2 * kPolyMaxQ + 1];
+};
+
+template <int Q>
+__global__ void __launch_bounds__(kPolyThreads) k_base_poly(const Desc *__restrict__ d, PolyTaps pt) {
+  constexpr int NR = 16 + 2 * Q, NC = 64 + 2 * Q, NT = 2 * Q + 1;
+  __shared__ float sI[NR * NC];
+  __shared__ __align__(16) float sH[NR * kBlurTW];
+  const int *pre = d->base_pre[1];
+  const int total = pre[d->n_img];
+  const int G = gridDim.x;
+  for (int t = blockIdx.x; t < total; t += G) {
+    if (t + G >= total) pdl_trigger();  // successors launch during this block's last tile
+    const TileGeo g = tile_geo<32, 2>(d, pre, 0, 0, t);
+    const int kx0 = g.x0 >> 1, ky0 = g.y0 >> 1;
+    const int iyb = ky0 - Q, ixb = kx0 - Q;
+    if (iyb >= 0 && iyb + NR <= g.sh && ixb >= 0 && ixb + NC <= g.sw) {
+      // Interior: the window needs no reflection; warp w copies rows w, w + 8, ...
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+      for (int r = warp; r < NR; r += kPolyThreads / 32) {
+        const float *srow = g.src + (long long)(iyb + r) * g.spitch + ixb;
+        for (int c = lane; c < NC; c += 32) cp_async4(sI + r * NC + c, srow + c);
+      }
+    } else {
+      for (int idx = threadIdx.x; idx < NR * NC; idx += kPolyThreads) {
+        const int r = idx / NC, c = idx - r * NC;
+        const int iy = refl101(2 * (iyb + r), g.H) >> 1;
+        const int ix = refl101(2 * (ixb + c), g.W) >> 1;
+        cp_async4(sI + idx, g.src + (long long)iy * g.spitch + ix);
+      }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    // Rows: outputs 2j and 2j + 1 of input row r share the taps sI[r][j .. j + 2Q].
+    for (int idx = threadIdx.x; idx < NR * (kBlurTW / 2); idx += kPolyThreads) {
+      const int r = idx / (kBlurTW / 2), j = idx - r * (kBlurTW / 2);
+      const float *row = sI + r * NC + j;
+      float a = 0.f, b = 0.f;
+#pragma unroll
+      for (int q = 0; q < NT; q++) {
+        const float v = row[q];
+        a = fmaf(pt.c[0][q], v, a);
+        b = fmaf(pt.c[1][q], v, b);
+      }
+      *reinterpret_cast<float2 *>(sH + r * kBlurTW + 2 * j) = make_float2(a, b);
+    }
+    __syncthreads();
+    // Columns: output rows 2j and 2j + 1 of a 4-column group share the taps
+    // sH[j .. j + 2Q][4 g4 .. 4 g4 + 3].
+    for (int idx = threadIdx.x; idx < 16 * (kBlurTW / 4); idx += kPolyThreads) {
+      const int j = idx / (kBlurTW / 4), g4 = idx - j * (kBlurTW / 4);
+      float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+#pragma unroll
+      for (int q = 0; q < NT; q++) {
+        const float4 v = *reinterpret_cast<const float4 *>(sH + (j + q) * kBlurTW + 4 * g4);
+        const float c0 = pt.c[0][q], c1 = pt.c[1][q];
+        a.x = fmaf(c0, v.x, a.x);
+        a.y = fmaf(c0, v.y, a.y);
+        a.z = fmaf(c0, v.z, a.z);
+        a.w = fmaf(c0, v.w, a.w);
+        b.x = fmaf(c1, v.x, b.x);
+        b.y = fmaf(c1, v.y, b.y);
+        b.z = fmaf(c1, v.z, b.z);
+        b.w = fmaf(c1, v.w, b.w);
+      }
+      const int X = g.x0 + 4 * g4, Y = g.y0 + 2 * j;
+#pragma unroll
+      for (int p = 0; p < 2; p++) {
+        if (Y + p >= g.H) break;
+        const float4 v = p ? b : a;
+        float *o = g.out + (long long)(Y + p) * g.pitch + X;
+        if (X + 3 < g.W) {
+          *reinterpret_cast<float4 *>(o) = v;
+        } else {
+          if (X < g.W) o[0] = v.x;
+          if (X + 1 < g.W) o[1] = v.y;
+          if (X + 2 < g.W) o[2] = v.z;
+        }
+      }
+    }
+    __syncthreads();  // the next tile reuses sI and sH
+  }
+}
+
+PolyTaps make_poly_taps(const BlurTaps &t, int R) {
+  const int Q = (R + 2) / 2;
+  PolyTaps p{};
+  for (int ph = 0; ph < 2; ph++)
+    for (int q = -Q; q <= Q; q++) {
+      double c = 0.0;
+      for (int tt = -R; tt <= R; tt++) {
+        const int n = ph + tt;  // magnified offset from 2k
+        double w = 0.0;
+        if ((n & 1) == 0) w = (n / 2 == q) ? 1.0 : 0.0;
+        else w = ((n - 1) / 2 == q || (n + 1) / 2 == q) ? 0.5 : 0.0;
+        c += (double)t.w[tt + R] * w;
+      }
+      p.c[ph][q + Q] = (float)c;
+    }
+  return p;
+}
+
 }  // namespace
 
 int blur_smem_bytes(int R, int th_kind) { return blur_smem_bytes_mode(R, th_kind, 0); }
@@ -660,7 +782,7 @@ cudaError_t launch_base_blur(const Desc *d, int R, const BlurTaps &t, int th_kin
   (void)th_kind;
 #define CASE_R(RR)                                                                            \
   case RR:                                                                                    \
-    if (upsample) k_blur<RR, 32, 2><<<grid, kThreads, smem_bytes<RR, 32, 2>(), s>>>(d, 0, 0, t); \
+    if (upsample) k_base_poly<(RR + 2) / 2><<<grid, kPolyThreads, 0, s>>>(d, make_poly_taps(t, RR)); \
     else k_blur<RR, 32, 1><<<grid, kThreads, smem_bytes<RR, 32, 1>(), s>>>(d, 0, 0, t);          \
     break;
   switch (R) {
@@ -680,7 +802,7 @@ int blur_blocks_per_sm(int R, int th_kind, int mode) {
 #define CASE_R(RR)                                                                       \
   case RR:                                                                               \
     if (mode == 1) { OCC((k_blur<RR, 32, 1>), (smem_bytes<RR, 32, 1>())) }                \
-    else if (mode == 2) { OCC((k_blur<RR, 32, 2>), (smem_bytes<RR, 32, 2>())) }           \
+    else if (mode == 2) { e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_base_poly<(RR + 2) / 2>, kPolyThreads, 0); } \
     else if (th_kind == TK_BLUR64) { OCC((k_blur<RR, 64, 0>), (smem_bytes<RR, 64, 0>())) } \
     else { OCC((k_blur<RR, 32, 0>), (smem_bytes<RR, 32, 0>())) }                          \
     break;
