@@ -178,7 +178,6 @@ __global__ void __launch_bounds__(kThreads) k_bm_emit(const Desc *__restrict__ d
   __shared__ int tmp[kThreads / 32 + 1];
   constexpr int WPT = kChunk / kThreads;  // words per thread
   const int n = d->n_img;
-  const int S = d->n_scales;
   for (int c = blockIdx.x; c < d->n_bm_chunks; c += gridDim.x) {
     const int b = find_owner(d->bmc_pre, n, c);
     const ImgDev &im = d->img[b];
@@ -194,23 +193,26 @@ __global__ void __launch_bounds__(kThreads) k_bm_emit(const Desc *__restrict__ d
     int tot;
     int slot = d->bm_off[c] + block_excl_scan(cnt, tmp, &tot);
     if (tot == 0) continue;
+    // Octave of the thread's words: found once and advanced (the words are
+    // contiguous). Offsets within an octave's bitmap fit 32 bits.
+    int o = 0;
+    OctDev od = d->oct[im.oct0];
     for (int k = 0; k < WPT; k++) {
       uint32_t wv = words[k];
       if (!wv) continue;
       // Locate octave / layer / row / word of this bitmap word.
       const long long wa = im.bm_begin + w0 + k;
-      int o = 0;
-      OctDev od = d->oct[im.oct0];
       while (o + 1 < im.n_oct && wa >= d->oct[im.oct0 + o + 1].bm) {
         o++;
         od = d->oct[im.oct0 + o];
       }
-      const long long rel = wa - od.bm;
-      const long long lw = (long long)od.H * od.wpr;
-      const int layer = (int)(rel / lw) + 1;
-      const long long r2 = rel - (long long)(layer - 1) * lw;
-      const int y = (int)(r2 / od.wpr);
-      const int wx = (int)(r2 - (long long)y * od.wpr);
+      const unsigned rel = (unsigned)(wa - od.bm);
+      const unsigned lw = (unsigned)od.H * (unsigned)od.wpr;
+      const unsigned li = rel / lw;
+      const unsigned r2 = rel - li * lw;
+      const int layer = (int)li + 1;
+      const int y = (int)(r2 / (unsigned)od.wpr);
+      const int wx = (int)(r2 - (unsigned)y * (unsigned)od.wpr);
       while (wv) {
         const int bit = __ffs(wv) - 1;
         wv &= wv - 1;
@@ -218,7 +220,6 @@ __global__ void __launch_bounds__(kThreads) k_bm_emit(const Desc *__restrict__ d
         slot++;
       }
     }
-    (void)S;
   }
 }
 
@@ -241,7 +242,9 @@ __global__ void __launch_bounds__(kThreads) k_refine(const Desc *__restrict__ d)
   const int total = d->cand_flat[n];
   const int S = d->n_scales, bord = d->border, iters = d->max_iter;
   const float T = d->contrast_thr, er = d->edge_ratio;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+  // Candidate t goes to block t % G, thread (t / G) % blockDim.x: a few
+  // thousand candidates spread over every SM instead of filling the first blocks.
+  for (int t = blockIdx.x + gridDim.x * threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
     const int b = find_owner(d->cand_flat, n, t);
     const ImgDev &im = d->img[b];
     const long long slot = im.cand_off + (t - d->cand_flat[b]);
