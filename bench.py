@@ -654,6 +654,9 @@ def main():
                     help="skip the single-image and image-pair latency runs")
     ap.add_argument("--minimal", action="store_true",
                     help="only the timed batch loop (for profiler launch lists)")
+    ap.add_argument("--pair-only", action="store_true",
+                    help="only the single-image and wide-baseline pair runs (extraction, "
+                         "matcher, MAGSAC++), e.g. for profiling those kernels")
     ap.add_argument("--images", type=int, default=6, help="images per batch (default 6)")
     ap.add_argument("--tuning", default="", help='fixed tiles, e.g. {"blur_tile_rows": [32,...]}')
     args = ap.parse_args()
@@ -667,6 +670,15 @@ def main():
         n_workers = min(6, os.cpu_count() or 1)
         with _oracle_pool(n_workers) as pool:
             print(json.dumps(reference_arm(args, pool, n_workers)))
+        return
+
+    if args.pair_only:
+        import torch
+        import paper_2605_17869_gb300 as pkg
+        stream = torch.cuda.current_stream()
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        tuning = args.tuning or '{"blur_tile_rows": [32, 32, 32, 32, 32]}'
+        print(json.dumps({"single_and_pair": other_configs(torch, pkg, flush, stream, tuning)}))
         return
 
     # The oracle's worker pool is started (spawn) before any GPU call.

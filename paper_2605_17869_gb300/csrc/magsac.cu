@@ -28,6 +28,7 @@
 //
 // Selection: one block takes the smallest score (ties to the smaller index)
 // and marks the inliers of its model (r <= k sigma_max).
+#include <algorithm>
 #include <cmath>
 
 #include "sift_dev.cuh"
@@ -36,7 +37,7 @@ namespace sift {
 
 namespace {
 
-constexpr int kFitThreads = 32;  // FP64 solver threads per block (spread over SMs)
+constexpr int kFitThreads = 32;  // most FP64 solver threads per block
 constexpr int kScoreThreads = 256;
 constexpr int kSelectThreads = 1024;
 
@@ -105,6 +106,43 @@ __device__ bool collinear4(const double p[4][2]) {
   return false;
 }
 
+// Column C of Gaussian elimination with partial pivoting on the 8 x 9
+// augmented system: the row r >= C with the largest |M[r][C]| (the first on
+// ties) becomes the pivot row, the rows below are reduced. False if the
+// column is all zero (singular system).
+template <int C>
+__device__ __forceinline__ bool elim_step(double (&M)[8][9], double (&rinv)[8]) {
+  int piv = C;
+  double best = fabs(M[C][C]);
+#pragma unroll
+  for (int r = C + 1; r < 8; r++) {
+    const double a = fabs(M[r][C]);
+    if (a > best) {
+      best = a;
+      piv = r;
+    }
+  }
+  if (best == 0.0) return false;
+#pragma unroll
+  for (int r = C + 1; r < 8; r++) {
+    const bool sw = piv == r;
+#pragma unroll
+    for (int k = C; k < 9; k++) {
+      const double t = M[C][k];
+      M[C][k] = sw ? M[r][k] : t;
+      M[r][k] = sw ? t : M[r][k];
+    }
+  }
+  rinv[C] = 1.0 / M[C][C];
+#pragma unroll
+  for (int r = C + 1; r < 8; r++) {
+    const double f = M[r][C] * rinv[C];
+#pragma unroll
+    for (int k = C; k < 9; k++) M[r][k] -= f * M[C][k];
+  }
+  return true;
+}
+
 __global__ void __launch_bounds__(kFitThreads) k_magsac_fit(const float2 *__restrict__ xa,
                                                             const float2 *__restrict__ xb, int n,
                                                             const int *__restrict__ samples,
@@ -153,35 +191,25 @@ __global__ void __launch_bounds__(kFitThreads) k_magsac_fit(const float2 *__rest
       M[2 * j + 1][c] = r1[c];
     }
   }
-  for (int c = 0; c < 8; c++) {
-    int piv = c;
-    double best = fabs(M[c][c]);
-    for (int r = c + 1; r < 8; r++)
-      if (fabs(M[r][c]) > best) {
-        best = fabs(M[r][c]);
-        piv = r;
-      }
-    if (best == 0.0) {
-      valid[h] = 0;
-      return;
-    }
-    if (piv != c)
-      for (int k = c; k < 9; k++) {
-        const double t = M[c][k];
-        M[c][k] = M[piv][k];
-        M[piv][k] = t;
-      }
-    for (int r = c + 1; r < 8; r++) {
-      const double f = M[r][c] / M[c][c];
-      for (int k = c; k < 9; k++) M[r][k] -= f * M[c][k];
-    }
+  // One instantiation per pivot column (elim_step<C>), so every index is a
+  // compile-time constant and M stays in registers: the pivot row is swapped
+  // in by selects, and each pivot's reciprocal is taken once.
+  double rinv[8];
+  bool ok8 = elim_step<0>(M, rinv) && elim_step<1>(M, rinv) && elim_step<2>(M, rinv) &&
+             elim_step<3>(M, rinv) && elim_step<4>(M, rinv) && elim_step<5>(M, rinv) &&
+             elim_step<6>(M, rinv) && elim_step<7>(M, rinv);
+  if (!ok8) {
+    valid[h] = 0;
+    return;
   }
   double hn[9];
   hn[8] = 1.0;
+#pragma unroll
   for (int c = 7; c >= 0; c--) {
     double acc = M[c][8];
+#pragma unroll
     for (int k = c + 1; k < 8; k++) acc -= M[c][k] * hn[k];
-    hn[c] = acc / M[c][c];
+    hn[c] = acc * rinv[c];
   }
   double nn = 1.0;
   for (int k = 0; k < 8; k++) nn += hn[k] * hn[k];
@@ -353,13 +381,16 @@ cudaError_t launch_magsac(const float *xa, const float *xb, int n, const int *sa
   const MagsacConst c = make_const(sigma_max);
   const float2 *a = reinterpret_cast<const float2 *>(xa);
   const float2 *b = reinterpret_cast<const float2 *>(xb);
-  k_magsac_fit<<<(n_hyp + kFitThreads - 1) / kFitThreads, kFitThreads, 0, s>>>(a, b, n, samples, n_hyp,
-                                                                             models, valid);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
   int dev = 0, n_sm = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  // The FP64 solver is bound by each SM's FP64 rate: spread the hypotheses over
+  // every SM (ceil(n_hyp / SMs) threads per block, at most 32).
+  const int fit_threads = std::max(1, std::min(kFitThreads, (n_hyp + n_sm - 1) / n_sm));
+  k_magsac_fit<<<(n_hyp + fit_threads - 1) / fit_threads, fit_threads, 0, s>>>(a, b, n, samples,
+                                                                               n_hyp, models, valid);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   const int grid = n_hyp < 8 * n_sm ? n_hyp : 8 * n_sm;
   k_magsac_score<<<grid, kScoreThreads, 0, s>>>(a, b, n, models, valid, n_hyp, c, scores);
   e = cudaGetLastError();
