@@ -197,6 +197,42 @@ def test_batch_composition_invariance():
     assert sub == [single[2], single[0]]
 
 
+def test_large_batch_composition_invariance():
+    """40 images in one launch (more than 16, so each warp of the count scans
+    takes several images, and the owner search spans many prefixes): every
+    image's output equals its single-image extraction bit for bit, in either
+    order."""
+    rng = np.random.default_rng(18)
+    shapes = [(int(rng.integers(16, 120)), int(rng.integers(16, 160))) for _ in range(40)]
+    imgs = [torch.from_numpy(synth.make_image(synth.rng_for(18, i), *s)).cuda()
+            for i, s in enumerate(shapes)]
+    ex = pkg.Extractor(max_kpts=512)
+    single = [_digest(ex.extract(im)) for im in imgs]
+    assert [_digest(f) for f in ex.extract_batch(imgs)] == single
+    assert [_digest(f) for f in ex.extract_batch(imgs[::-1])] == single[::-1]
+    ex.close()
+
+
+def test_pack_outputs_argument_errors():
+    ex = pkg.Extractor(max_kpts=256)
+    img = torch.from_numpy(synth.make_image(synth.rng_for(19, 0), 64, 80)).cuda()
+    ex.extract(img)
+    L = pkg._lib()
+    s = torch.cuda.current_stream().cuda_stream
+    buf = torch.empty(540 * 256 + 16, dtype=torch.uint8, device="cuda")
+    import ctypes
+    P = lambda t, off=0: ctypes.c_void_p(t.data_ptr() + off)
+    assert L.sift_pack_outputs(ex.handle, ctypes.c_void_p(s), None, ctypes.c_size_t(0)) == pkg.SIFT_E_INVALID
+    assert L.sift_pack_outputs(ex.handle, ctypes.c_void_p(s), P(buf, 4),
+                               ctypes.c_size_t(540 * 256)) == pkg.SIFT_E_INVALID      # misaligned
+    assert L.sift_pack_outputs(ex.handle, ctypes.c_void_p(s), P(buf),
+                               ctypes.c_size_t(540 * 255)) == pkg.SIFT_E_INVALID      # too short
+    assert L.sift_pack_outputs(ex.handle, ctypes.c_void_p(s), P(buf),
+                               ctypes.c_size_t(540 * 256)) == 0
+    torch.cuda.synchronize()
+    ex.close()
+
+
 def test_download_packs_the_batch_outputs():
     """download(): one packed device-to-host transfer (sift_pack_outputs) gives
     exactly the per-image device outputs, bit for bit."""
