@@ -1,5 +1,6 @@
 // Gaussian scale space (§3.2, "GPU Pipeline Stages"): separable blurs with
-// 4-sigma truncation, the 2x magnified first octave, and octave decimation.
+// 4-sigma truncation, the 2x magnified first octave (k_base_poly, a polyphase
+// filter of the input, below), and octave decimation.
 //
 // One kernel launch computes one pyramid level for every image of the batch:
 // a persistent grid walks a flattened queue of 128 x TH output tiles. A tile
@@ -134,58 +135,6 @@ __device__ __forceinline__ void stage_upsampled(const float *__restrict__ src, i
              : 0.5f * (a + c0);
     }
     s_in[idx] = v;
-  }
-}
-
-// Fast path of the magnified window for tiles that need no reflection: the
-// input rows and columns the window covers are copied with cp.async into
-// s_tmp (rows past the last one are clamped, as the magnification defines),
-// then each magnified sample is formed from shared memory with the same
-// operands and formulas as stage_upsampled. Split in three so the copies of
-// the next tile can run ahead: upsample_fast_ok (the tile qualifies),
-// upsample_issue (the copies), upsample_expand (after the copies landed).
-constexpr int kUpNC = 88;  // input columns staged: 80 used + neighbour, float4-rounded
-template <int R, int TH> constexpr int up_rows() { return (TH + 2 * R) / 2 + 2; }
-
-template <int R, int TH>
-__device__ __forceinline__ bool upsample_fast_ok(int h, int w, bool vec_ok, int x0, int y0) {
-  constexpr int ROWS = TH + 2 * R;
-  const int gyb = y0 - R, gxb = x0 - kBlurHalo;
-  return vec_ok && gyb >= 0 && gyb + ROWS <= 2 * h && gxb >= 0 && (gxb >> 1) + kUpNC <= w;
-}
-
-template <int R, int TH>
-__device__ __forceinline__ void upsample_issue(const float *__restrict__ src, int spitch, int h,
-                                               int x0, int y0, float *s_tmp) {
-  constexpr int NR = up_rows<R, TH>();
-  const int ixb = (x0 - kBlurHalo) >> 1, iyb = (y0 - R) >> 1;
-  for (int q = threadIdx.x; q < NR * (kUpNC / 4); q += kThreads) {
-    const int r = q / (kUpNC / 4), g = q - r * (kUpNC / 4);
-    cp_async16(s_tmp + r * kUpNC + 4 * g, src + (long long)min(iyb + r, h - 1) * spitch + ixb + 4 * g);
-  }
-}
-
-// Thread t forms the magnified column pair (2p, 2p + 1) of the window, p =
-// t % 80, in rows t / 80, t / 80 + 4, ...: both samples read input column p
-// (and p + 1), u[2p] = I[p] and u[2p+1] = (I[p] + I[p+1]) / 2.
-template <int R, int TH>
-__device__ __forceinline__ void upsample_expand(int x0, int y0, const float *s_tmp, float *s_in) {
-  constexpr int ROWS = TH + 2 * R;
-  constexpr int NP = kSinW / 2;  // 80 column pairs
-  const int gyb = y0 - R, iyb = gyb >> 1;
-  const int p = threadIdx.x % NP, r0 = threadIdx.x / NP;
-  for (int r = r0; r < ROWS; r += kThreads / NP) {
-    const int gy = gyb + r;
-    const float *ta = s_tmp + ((gy >> 1) - iyb) * kUpNC + p;
-    const float a = ta[0], b = ta[1];
-    float2 v;
-    if (!(gy & 1)) {
-      v = make_float2(a, 0.5f * (a + b));
-    } else {
-      const float c0 = ta[kUpNC], d0 = ta[kUpNC + 1];
-      v = make_float2(0.5f * (a + c0), 0.5f * (0.5f * (a + b) + 0.5f * (c0 + d0)));
-    }
-    *reinterpret_cast<float2 *>(s_in + r * kSinW + 2 * p) = v;
   }
 }
 
@@ -469,15 +418,14 @@ template <int R, int TH, int MODE>
 __global__ void __launch_bounds__(kThreads, TH == 32 ? (MODE == 0 ? 4 : 3) : 1)
     k_blur(const Desc *__restrict__ d, int oct, int lvl_out, BlurTaps tp) {
   constexpr int ROWS = TH + 2 * R;
-  constexpr bool kAhead = MODE != 2;
+  static_assert(MODE != 2, "the magnified base is k_base_poly");
   extern __shared__ float4 smem4[];
   __shared__ TileGeo geo[2 * kGeoChunk];
   float *s_in = reinterpret_cast<float *>(smem4);
   float *s_v = s_in + ROWS * kSinW;
-  float *s_tmp = s_v + TH * kSinW;  // MODE 2: input rows of the next magnified window
-  // Base blurs (MODE 1: input as is, MODE 2: magnified) take the queue of
-  // their own mode's images.
-  const int *pre = (MODE == 1 || MODE == 2) ? d->base_pre[MODE - 1] : d->tile_pre[KindOf<TH>::v][oct];
+  // The base blur of images kept at their size (MODE 1) takes the queue of
+  // those images only.
+  const int *pre = MODE == 1 ? d->base_pre[0] : d->tile_pre[KindOf<TH>::v][oct];
   const int total = pre[d->n_img];
   const int t0 = blockIdx.x, G = gridDim.x;
   if (t0 >= total) return;
@@ -489,29 +437,17 @@ __global__ void __launch_bounds__(kThreads, TH == 32 ? (MODE == 0 ? 4 : 3) : 1)
   if (threadIdx.x < 32) fill_chunk(0);
   __syncthreads();
   pdl_wait();  // the source level is the previous kernel's output
-  auto up_ok = [&](const TileGeo &q) {
-    return upsample_fast_ok<R, TH>(q.sh, q.sw, q.vec != 0, q.x0, q.y0);
-  };
-  if (kAhead) issue_stage<R, TH, MODE>(geo[0], s_in);
-  else if (up_ok(geo[0])) upsample_issue<R, TH>(geo[0].src, geo[0].spitch, geo[0].sh, geo[0].x0, geo[0].y0, s_tmp);
+  issue_stage<R, TH, MODE>(geo[0], s_in);
   for (int k = 0; k < n_mine; k++) {
     if (k + 1 == n_mine) pdl_trigger();  // successors launch during this block's last tile
     const TileGeo &g = geo[k & (2 * kGeoChunk - 1)];
     const TileGeo &gn = geo[(k + 1) & (2 * kGeoChunk - 1)];
     cp_async_wait_all();
     __syncthreads();
-    if (!kAhead) {
-      // MODE 2: expand the landed input rows (or gather a border window),
-      // then let the next window's input rows run ahead into s_tmp.
-      if (up_ok(g)) upsample_expand<R, TH>(g.x0, g.y0, s_tmp, s_in);
-      else stage_upsampled(g.src, g.spitch, g.sh, g.sw, g.x0, g.y0, R, ROWS, s_in);
-      __syncthreads();
-      if (k + 1 < n_mine && up_ok(gn)) upsample_issue<R, TH>(gn.src, gn.spitch, gn.sh, gn.x0, gn.y0, s_tmp);
-    }
     if (MODE == 3) store_level0<R, TH>(s_in, g.out0, g.pitch, g.H, g.x0, g.y0);
     col_pass<R, TH>(s_in, s_v, tp);
     __syncthreads();
-    if (kAhead && k + 1 < n_mine) issue_stage<R, TH, MODE>(gn, s_in);
+    if (k + 1 < n_mine) issue_stage<R, TH, MODE>(gn, s_in);
     row_pass_store<R, TH>(s_v, g.out, g.pitch, g.H, g.x0, g.y0, tp);
     if (threadIdx.x < 32 && (k & (kGeoChunk - 1)) == kGeoChunk / 2)
       fill_chunk(k / kGeoChunk + 1);
@@ -586,17 +522,12 @@ __global__ void __launch_bounds__(kThreads) k_blur_generic(const Desc *__restric
 
 // Shared memory: the staging buffer plus the column-pass output.
 template <int R, int TH, int MODE> constexpr int smem_bytes() {
-  return (((TH + 2 * R) + TH) * kSinW + (MODE == 2 ? up_rows<R, TH>() * kUpNC : 0)) *
-         (int)sizeof(float);
+  return ((TH + 2 * R) + TH) * kSinW * (int)sizeof(float);
 }
 
 int th_of_kind(int kind) { return kind == TK_BLUR64 ? 64 : 32; }
 
-int blur_smem_bytes_mode(int R, int th_kind, int mode) {
-  const int th = th_of_kind(th_kind);
-  const int tmp = mode == 2 ? ((th + 2 * R) / 2 + 2) * kUpNC : 0;
-  return (((th + 2 * R) + th) * kSinW + tmp) * (int)sizeof(float);
-}
+
 
 int generic_smem_bytes(int R) { return (2 * 32 + 2 * R) * kSinW * (int)sizeof(float); }
 
@@ -724,7 +655,10 @@ PolyTaps make_poly_taps(const BlurTaps &t, int R) {
 
 }  // namespace
 
-int blur_smem_bytes(int R, int th_kind) { return blur_smem_bytes_mode(R, th_kind, 0); }
+int blur_smem_bytes(int R, int th_kind) {
+  const int th = th_of_kind(th_kind);
+  return ((th + 2 * R) + th) * kSinW * (int)sizeof(float);
+}
 
 #define SIFT_FOR_EACH_R(X) X(5) X(7) X(8) X(10) X(13)
 
@@ -738,8 +672,7 @@ cudaError_t blur_set_attributes() {
   SET((k_blur<R, 64, 0>), (smem_bytes<R, 64, 0>()))          \
   SET((k_blur<R, 32, 3>), (smem_bytes<R, 32, 3>()))          \
   SET((k_blur<R, 64, 3>), (smem_bytes<R, 64, 3>()))          \
-  SET((k_blur<R, 32, 1>), (smem_bytes<R, 32, 1>()))          \
-  SET((k_blur<R, 32, 2>), (smem_bytes<R, 32, 2>()))
+  SET((k_blur<R, 32, 1>), (smem_bytes<R, 32, 1>()))
   SIFT_FOR_EACH_R(SET_R)
   SET(k_blur_generic<0>, generic_smem_bytes(kMaxR))
   SET(k_blur_generic<3>, generic_smem_bytes(kMaxR))
