@@ -82,6 +82,10 @@ MAGSAC_MUTANTS = {
                        "[-x, -y, -1.0, 0.0, 0.0, 0.0, u * x, v * y, u]"),
     "magsac_residual_wrong_image": ("np.sqrt((px - xb[:, 0]) ** 2 + (py - xb[:, 1]) ** 2)",
                                     "np.sqrt((px - xa[:, 0]) ** 2 + (py - xa[:, 1]) ** 2)"),
+    "magsac_inlier_threshold_sigma": ("inl = residuals(H, xa, xb) <= chi_quantile() * sigma_max",
+                                      "inl = residuals(H, xa, xb) <= sigma_max"),
+    "magsac_best_is_worst": ("    best = int(np.argmin(scores))",
+                             "    best = int(np.argmax(np.where(np.isfinite(scores), scores, -np.inf)))"),
     "magsac_weight_sigma_scale": (
         "    x = t * t / (2.0 * sigma_max * sigma_max)",
         "    x = t * t / (sigma_max * sigma_max)"),
