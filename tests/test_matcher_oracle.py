@@ -91,3 +91,18 @@ def test_degenerate_cases():
 def test_fp16_rounding_reading():
     v = np.array([[0.1, 0.2, 0.3]], dtype=np.float64)
     np.testing.assert_array_equal(om.round_fp16(v), v.astype(np.float16).astype(np.float64))
+
+
+def test_ties_go_to_the_smaller_index():
+    """READING: the nearest neighbour is the largest dot product, ties to the
+    smaller index (the match itself never depends on it: a tie fails the ratio
+    test, but the reported best indices do)."""
+    S = np.array([[1.0, 3.0, 3.0], [2.0, 2.0, 1.0], [0.5, 0.25, 0.5]])
+    j1, s1, s2 = om._best_two(S)
+    assert list(j1) == [1, 0, 0]
+    assert list(s1) == [3.0, 2.0, 0.5] and list(s2) == [3.0, 2.0, 0.5]
+    b = _unit(np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]]))
+    a = _unit(np.array([[0.1, 1.0, 0.0], [1.0, 0.1, 0.0]]))
+    m, info = om.match(a, b)
+    assert info["best_a"][0] == 1            # b[1] and b[2] tie: the first wins
+    assert m[0] == -1                        # and the tie fails the ratio test

@@ -91,13 +91,25 @@ MAGSAC_MUTANTS = {
         "    x = t * t / (sigma_max * sigma_max)"),
 }
 
+# Mistakes planted in the matcher oracle, caught by its own pin file.
+MATCHER_MUTANTS = {
+    "matcher_no_mutual_check": ("keep = ib[j] == i and da1[i] < ratio * da2[i]",
+                                "keep = da1[i] < ratio * da2[i]"),
+    "matcher_ratio_one_side": ("and da1[i] < ratio * da2[i] and db1[j] < ratio * db2[j]",
+                               "and da1[i] < ratio * da2[i]"),
+    "matcher_ties_to_last": ("    j1 = np.argmax(S, axis=1)                      # first occurrence = smallest index",
+                             "    j1 = S.shape[1] - 1 - np.argmax(S[:, ::-1], axis=1)"),
+}
+
 CASES = ([(n, "sift_oracle.py", "test_oracle_pins.py") for n in sorted(MUTANTS)]
-         + [(n, "magsac.py", "test_magsac_oracle.py") for n in sorted(MAGSAC_MUTANTS)])
+         + [(n, "magsac.py", "test_magsac_oracle.py") for n in sorted(MAGSAC_MUTANTS)]
+         + [(n, "matcher.py", "test_matcher_oracle.py") for n in sorted(MATCHER_MUTANTS)])
+_TABLE = {"sift_oracle.py": MUTANTS, "magsac.py": MAGSAC_MUTANTS, "matcher.py": MATCHER_MUTANTS}
 
 
 @pytest.mark.parametrize("name,target,pins", CASES, ids=[c[0] for c in CASES])
 def test_pins_catch_mutant(name, target, pins, tmp_path):
-    before, after = (MUTANTS if target == "sift_oracle.py" else MAGSAC_MUTANTS)[name]
+    before, after = _TABLE[target][name]
     src = open(os.path.join(ROOT, "oracle", target)).read()
     assert before in src, "mutation anchor missing: " + name
     for d in ("oracle", "workloads"):
