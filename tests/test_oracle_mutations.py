@@ -65,6 +65,13 @@ MUTANTS = {
                       "    dy = bilinear(L, x + 1, y + 1) - bilinear(L, x - 1, y - 1)"),
     "magnify_limit_exclusive": ("(p.upsample_max_px <= 0 or h * w <= p.upsample_max_px)",
                                 "(p.upsample_max_px <= 0 or h * w < p.upsample_max_px)"),
+    "decimate_wrong_level": ("g0 = decimate(octaves[o - 1][p.n_scales])",
+                             "g0 = decimate(octaves[o - 1][p.n_scales + 1])"),
+    "smoothing_flat": ("    return 0.25 * np.roll(hist, 1) + 0.5 * hist + 0.25 * np.roll(hist, -1)",
+                       "    return (np.roll(hist, 1) + hist + np.roll(hist, -1)) / 3.0"),
+    "descriptor_bin_width": ("    wbin = p.desc_scale * sigma_oct\n", "    wbin = 2.0 * sigma_oct\n"),
+    "contrast_test_signed": ("    if abs(contrast) < p.contrast_thr:", "    if contrast < p.contrast_thr:"),
+    "peak_ratio_ignored": ("    thr = p.ori_peak_ratio * hmax", "    thr = hmax"),
     "rootsift_no_l1": ("        vec = np.sqrt(vec / l1) if l1 > 0 else vec",
                        "        vec = np.sqrt(vec) if l1 > 0 else vec"),
 }

@@ -597,3 +597,24 @@ def test_descriptor_clip_is_active_on_concentrated_mass():
     np.testing.assert_allclose(clp[big], clp.max(), rtol=1e-12)
     assert np.all(clp[~big] < clp.max())
     assert clp.max() < raw.max()
+
+
+def test_descriptor_support_is_two_and_a_half_bins_of_three_sigma():
+    """READING: spatial bin width w = 3 sigma, samples kept while their rotated
+    bin coordinates satisfy |rx|, |ry| < 2.5 (u, v in (-1, 4)). A vertical step
+    edge e pixels to the right of the keypoint (angle 0) has gradient only in
+    the two pixel columns beside it (central differences, at offsets e - 1 and
+    e): with sigma = 2 (w = 6 px) an edge at 12 px lands in spatial column
+    floor(rx + 1.5) = 3 with orientation bin 0 only, and one at 17 px lies
+    outside the support (rx > 2.5), so the descriptor is zero."""
+    p = so.Params()
+    n, c, sig = 101, 50, 2.0
+    for e, seen in ((12, True), (17, False)):
+        L = np.zeros((n, n))
+        L[:, c + e:] = 1.0
+        d = so.descriptor(L, float(c), float(c), c, c, sig, 0.0, p).reshape(4, 4, 8)
+        assert (np.abs(d).sum() > 0) == seen, e
+        if seen:
+            cols = np.nonzero(d.sum(axis=(0, 2)) > 1e-12)[0].tolist()
+            bins = np.nonzero(d.sum(axis=(0, 1)) > 1e-12)[0].tolist()
+            assert cols == [3] and bins == [0], (cols, bins)
