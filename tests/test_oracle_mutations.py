@@ -72,6 +72,13 @@ MUTANTS = {
     "descriptor_bin_width": ("    wbin = p.desc_scale * sigma_oct\n", "    wbin = 2.0 * sigma_oct\n"),
     "contrast_test_signed": ("    if abs(contrast) < p.contrast_thr:", "    if contrast < p.contrast_thr:"),
     "peak_ratio_ignored": ("    thr = p.ori_peak_ratio * hmax", "    thr = hmax"),
+    "orientation_mag_squared": ("    mag = np.sqrt(dx * dx + dy * dy)\n    th = np.arctan2(dy, dx)",
+                                "    mag = dx * dx + dy * dy\n    th = np.arctan2(dy, dx)"),
+    "refine_threshold_loose": ("        if m < 0.5:", "        if m < 0.6:"),
+    "blur_border_symmetric": ('    return np.pad(a, pad, mode="reflect")  # numpy',
+                              '    return np.pad(a, pad, mode="symmetric")  # numpy'),
+    "descriptor_first_norm_l1": ("    nrm = math.sqrt(float(vec @ vec))\n    if nrm == 0:",
+                                 "    nrm = float(np.sum(np.abs(vec)))\n    if nrm == 0:"),
     "rootsift_no_l1": ("        vec = np.sqrt(vec / l1) if l1 > 0 else vec",
                        "        vec = np.sqrt(vec) if l1 > 0 else vec"),
 }

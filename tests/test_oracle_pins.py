@@ -208,10 +208,12 @@ def test_cramer_matches_linalg_solve():
 
 
 @pytest.mark.parametrize("off", [(0.3, -0.2, 0.1), (-0.45, 0.4, -0.35), (1.3, -0.2, 0.2),
-                                 (-2.2, 1.6, 0.3)])
+                                 (-2.2, 1.6, 0.3), (0.55, -0.3, 0.1), (-0.58, 0.52, 0.05)])
 def test_refinement_recovers_quadratic_vertex(off):
     """Central differences are exact on a quadratic, so the vertex is recovered
-    exactly, after one move per whole-pixel offset; the contrast is the vertex value."""
+    exactly, after one move per whole-pixel offset; the contrast is the vertex value.
+    An offset component of 0.5 or more always moves the pixel (offsets 0.55 and
+    -0.58 end at the neighbouring pixel with |offset| < 0.5)."""
     p = so.Params(contrast_thr=0.001)
     H = -np.array([[0.010, 0.002, 0.001], [0.002, 0.012, -0.001], [0.001, -0.001, 0.02]])
     v = (12 + off[0], 12 + off[1], 2 + off[2])
