@@ -79,6 +79,10 @@ MUTANTS = {
                               '    return np.pad(a, pad, mode="symmetric")  # numpy'),
     "descriptor_first_norm_l1": ("    nrm = math.sqrt(float(vec @ vec))\n    if nrm == 0:",
                                  "    nrm = float(np.sum(np.abs(vec)))\n    if nrm == 0:"),
+    "octave_min_side_strict": ("    while min(h, w) >= p.min_octave_side:",
+                               "    while min(h, w) > p.min_octave_side:"),
+    "descriptor_orientation_no_wrap": ("                oo = (o0 + do) % nb",
+                                       "                oo = np.minimum(o0 + do, nb - 1)"),
     "rootsift_no_l1": ("        vec = np.sqrt(vec / l1) if l1 > 0 else vec",
                        "        vec = np.sqrt(vec) if l1 > 0 else vec"),
 }

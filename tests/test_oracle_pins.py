@@ -142,6 +142,11 @@ def test_decimate_floor_size_and_octaves():
     np.testing.assert_array_equal(d, img[0:30:2, 0:18:2])
     assert so.octave_sizes(480, 640, so.Params()) == [(480, 640), (240, 320), (120, 160),
                                                         (60, 80), (30, 40)]
+    # an octave is kept while its smaller side is at least min_octave_side (16)
+    assert so.octave_sizes(16, 16, so.Params()) == [(16, 16)]
+    assert so.octave_sizes(32, 40, so.Params()) == [(32, 40), (16, 20)]
+    assert so.octave_sizes(15, 100, so.Params()) == []
+    assert so.octave_sizes(8, 9, so.Params(upsample=True)) == [(16, 18)]
     assert len(so.octave_sizes(750, 1000, so.Params(upsample=True))) == 7
     assert len(so.octave_sizes(1200, 1600, so.Params(upsample=True))) == 8
 
