@@ -83,6 +83,10 @@ MUTANTS = {
                                "    while min(h, w) > p.min_octave_side:"),
     "descriptor_orientation_no_wrap": ("                oo = (o0 + do) % nb",
                                        "                oo = np.minimum(o0 + do, nb - 1)"),
+    "orientation_radius_ceil": ("    R = _round_pos(p.ori_radius_factor * sw)",
+                                "    R = int(math.ceil(p.ori_radius_factor * sw))"),
+    "orientation_peak_not_strict": ("        is_lmax = hk > hm and hk > hp",
+                                    "        is_lmax = hk >= hm and hk >= hp"),
     "rootsift_no_l1": ("        vec = np.sqrt(vec / l1) if l1 > 0 else vec",
                        "        vec = np.sqrt(vec) if l1 > 0 else vec"),
 }

@@ -625,3 +625,18 @@ def test_descriptor_support_is_two_and_a_half_bins_of_three_sigma():
             cols = np.nonzero(d.sum(axis=(0, 2)) > 1e-12)[0].tolist()
             bins = np.nonzero(d.sum(axis=(0, 1)) > 1e-12)[0].tolist()
             assert cols == [3] and bins == [0], (cols, bins)
+
+
+def test_orientation_peaks_are_strict_maxima():
+    """READING: a peak is a strict circular local maximum of the smoothed
+    histogram at >= 0.8 of its maximum. A two-bin plateau at the maximum gives
+    no peak (neither bin exceeds its neighbour), while a separate strict peak at
+    0.9 of the maximum gives one orientation at its bin centre."""
+    h = np.zeros(36)
+    h[10] = h[11] = 1.0
+    h[20] = 0.9
+    angles, _ = so.orientation_peaks(h, so.Params())
+    assert angles == [200.0]
+    h[11] = 0.999                       # break the tie: bin 10 becomes a strict peak
+    angles, _ = so.orientation_peaks(h, so.Params())
+    assert len(angles) == 2 and abs(angles[1] - 200.0) < 1e-12
