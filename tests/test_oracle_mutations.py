@@ -87,6 +87,10 @@ MUTANTS = {
                                 "    R = int(math.ceil(p.ori_radius_factor * sw))"),
     "orientation_peak_not_strict": ("        is_lmax = hk > hm and hk > hp",
                                     "        is_lmax = hk >= hm and hk >= hp"),
+    "descriptor_offsets_from_pixel": ("    ox = xs - xk\n    oy = ys - yk\n    rx = (ct * ox + st * oy) / wbin",
+                                      "    ox = xs - xi\n    oy = ys - yi\n    rx = (ct * ox + st * oy) / wbin"),
+    "descriptor_radius_no_sqrt2": ("    R = _round_pos(wbin * math.sqrt(2.0) * (d + 1) * 0.5)",
+                                   "    R = _round_pos(wbin * (d + 1) * 0.5)"),
     "rootsift_no_l1": ("        vec = np.sqrt(vec / l1) if l1 > 0 else vec",
                        "        vec = np.sqrt(vec) if l1 > 0 else vec"),
 }

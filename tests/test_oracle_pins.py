@@ -640,3 +640,26 @@ def test_orientation_peaks_are_strict_maxima():
     h[11] = 0.999                       # break the tie: bin 10 becomes a strict peak
     angles, _ = so.orientation_peaks(h, so.Params())
     assert len(angles) == 2 and abs(angles[1] - 200.0) < 1e-12
+
+
+def test_descriptor_offsets_from_the_subpixel_keypoint_and_window_reach():
+    """READING: sample offsets are taken from the sub-pixel keypoint, and the
+    sample window has radius round(w sqrt(2) (d + 1) / 2), which covers the
+    rotated 2.5-bin support (w = 3 sigma = 6 px for sigma = 2).
+    (a) Angle 0, keypoint 0.4 px right of pixel c, a step whose gradient sits in
+        columns c + 15 and c + 16: the first lies 14.6 px = 2.43 bins away,
+        inside the support, so the descriptor is not zero.
+    (b) Angle 45 degrees, keypoint at pixel c, a step whose gradient sits in
+        columns c + 20 and c + 21: the rotated support reaches them (rx, |ry|
+        < 2.5 for rows c - 1 .. c + 1), but only a window of radius
+        21 = round(6 sqrt(2) 2.5) includes them."""
+    p = so.Params()
+    n, c, sig = 101, 50, 2.0
+    L = np.zeros((n, n))
+    L[:, c + 16:] = 1.0
+    d = so.descriptor(L, c + 0.4, float(c), c, c, sig, 0.0, p)
+    assert np.abs(d).sum() > 0
+    L = np.zeros((n, n))
+    L[:, c + 21:] = 1.0
+    d = so.descriptor(L, float(c), float(c), c, c, sig, 45.0, p)
+    assert np.abs(d).sum() > 0
