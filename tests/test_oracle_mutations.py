@@ -91,6 +91,14 @@ MUTANTS = {
                                       "    ox = xs - xi\n    oy = ys - yi\n    rx = (ct * ox + st * oy) / wbin"),
     "descriptor_radius_no_sqrt2": ("    R = _round_pos(wbin * math.sqrt(2.0) * (d + 1) * 0.5)",
                                    "    R = _round_pos(wbin * (d + 1) * 0.5)"),
+    "upsample_wraps": ("        nxt = np.concatenate([a[1:], a[-1:]], axis=0)",
+                       "        nxt = np.concatenate([a[1:], a[:1]], axis=0)"),
+    "taps_radius_round": ("    r = int(math.ceil(4.0 * sigma))", "    r = int(round(4.0 * sigma))"),
+    "extrema_same_layer_only": ("        for ds in (-1, 0, 1):\n            for dy in (-1, 0, 1):",
+                                "        for ds in (0,):\n            for dy in (-1, 0, 1):"),
+    "extrema_layers_off_by_one": ("    for s in range(1, S + 1):\n        c = D[s, b:h - b, b:w - b]",
+                                  "    for s in range(1, S):\n        c = D[s, b:h - b, b:w - b]"),
+    "pregate_ignored": ("        gate = np.abs(c) > thr", "        gate = np.abs(c) >= 0"),
     "rootsift_no_l1": ("        vec = np.sqrt(vec / l1) if l1 > 0 else vec",
                        "        vec = np.sqrt(vec) if l1 > 0 else vec"),
 }

@@ -663,3 +663,19 @@ def test_descriptor_offsets_from_the_subpixel_keypoint_and_window_reach():
     L[:, c + 21:] = 1.0
     d = so.descriptor(L, float(c), float(c), c, c, sig, 45.0, p)
     assert np.abs(d).sum() > 0
+
+
+def test_pregate_threshold():
+    """READING: candidates need |D| > 0.5 * contrast_thr besides being strict
+    3x3x3 extrema: an isolated extremum at 0.4 T is dropped, at 0.6 T kept (both
+    signs)."""
+    p = so.Params()
+    T = p.contrast_thr
+    for sign in (1.0, -1.0):
+        for frac, n_want in ((0.4, 0), (0.6, 1)):
+            D = np.zeros((5, 21, 21))
+            D[2, 10, 10] = sign * frac * T
+            cs, cy, cx, _, _ = so.find_candidates(D, p)
+            assert len(cs) == n_want, (sign, frac)
+            if n_want:
+                assert (cs[0], cy[0], cx[0]) == (2, 10, 10)
