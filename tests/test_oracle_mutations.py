@@ -99,6 +99,9 @@ MUTANTS = {
     "extrema_layers_off_by_one": ("    for s in range(1, S + 1):\n        c = D[s, b:h - b, b:w - b]",
                                   "    for s in range(1, S):\n        c = D[s, b:h - b, b:w - b]"),
     "pregate_ignored": ("        gate = np.abs(c) > thr", "        gate = np.abs(c) >= 0"),
+    "output_no_half_when_upsampled": ("    scale_up = 0.5 if p.upsample else 1.0",
+                                      "    scale_up = 1.0"),
+    "output_octave_scale_missing": ("        f = (2.0 ** o) * scale_up", "        f = scale_up"),
     "rootsift_no_l1": ("        vec = np.sqrt(vec / l1) if l1 > 0 else vec",
                        "        vec = np.sqrt(vec) if l1 > 0 else vec"),
 }

@@ -679,3 +679,22 @@ def test_pregate_threshold():
             assert len(cs) == n_want, (sign, frac)
             if n_want:
                 assert (cs[0], cy[0], cx[0]) == (2, 10, 10)
+
+
+def test_upsampled_outputs_are_in_input_pixels():
+    """With the 2x magnified first octave, positions and scales are reported in
+    input pixels: a blob centred on input pixel c (magnified pixel 2c, a centre
+    of symmetry of the whole pyramid) is found at exactly (c, c), at the scale
+    the non-magnified prediction gives in input pixels (the bilinear
+    magnification adds a little blur: 3%)."""
+    p = so.Params(contrast_thr=0.001, upsample=True)
+    s, n = 5.0, 129
+    c = n // 2
+    Y, X = np.mgrid[0:n, 0:n]
+    img = 0.5 + 0.3 * np.exp(-((X - c) ** 2 + (Y - c) ** 2) / (2 * s * s))
+    r = so.extract(img, p, with_descriptors=False)
+    sel = (np.abs(r.x - c) < 1) & (np.abs(r.y - c) < 1)
+    assert sel.any()
+    assert np.all(np.abs(r.x[sel] - c) < 1e-9) and np.all(np.abs(r.y[sel] - c) < 1e-9)
+    pred = math.sqrt(s * s - p.init_blur ** 2) / math.sqrt(2 ** (1 / 3))
+    assert np.all(np.abs(r.sigma[sel] - pred) / pred < 3e-2), (r.sigma[sel], pred)
