@@ -26,6 +26,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -85,7 +86,7 @@ class Clocks:
     def __init__(self, dev_index):
         self.proc = None
         self.dev = dev_index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"sift_bench_clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
