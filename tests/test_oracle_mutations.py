@@ -102,6 +102,12 @@ MUTANTS = {
     "output_no_half_when_upsampled": ("    scale_up = 0.5 if p.upsample else 1.0",
                                       "    scale_up = 1.0"),
     "output_octave_scale_missing": ("        f = (2.0 ** o) * scale_up", "        f = scale_up"),
+    "dsp_stencil_bound_inclusive": ("    ok = (x >= 1) & (x < w - 2) & (y >= 1) & (y < h - 2)\n    x, y, rx, ry = x[ok], y[ok], rx[ok], ry[ok]",
+                                    "    ok = (x >= 1) & (x <= w - 2) & (y >= 1) & (y <= h - 2)\n    x, y, rx, ry = x[ok], y[ok], rx[ok], ry[ok]"),
+    "dsp_stencil_lower_strict": ("    ok = (x >= 1) & (x < w - 2) & (y >= 1) & (y < h - 2)\n    x, y, rx, ry = x[ok], y[ok], rx[ok], ry[ok]",
+                                 "    ok = (x > 1) & (x < w - 2) & (y > 1) & (y < h - 2)\n    x, y, rx, ry = x[ok], y[ok], rx[ok], ry[ok]"),
+    "dsp_scales_four": ("    dsp_scales: tuple = (0.5, 2 ** -0.5, 1.0, 2 ** 0.5, 2.0)",
+                        "    dsp_scales: tuple = (2 ** -0.5, 1.0, 2 ** 0.5, 2.0)"),
     "rootsift_no_l1": ("        vec = np.sqrt(vec / l1) if l1 > 0 else vec",
                        "        vec = np.sqrt(vec) if l1 > 0 else vec"),
 }

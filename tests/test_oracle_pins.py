@@ -529,6 +529,58 @@ def test_dsp_patch_extent_per_scale():
             assert h.sum() > 0.0, f
 
 
+def test_dsp_pooled_scale_mean_on_quadratic():
+    """On L = x^2 the central difference of the bilinear level is exactly 4x
+    (the interpolation error f(1 - f) is the same at x + 1 and x - 1) and
+    dy = 0, so every sample votes 4 (xk + w_f rx) into orientation bin 0.
+    Scale f's histogram column u is then 4 (xk A_u + w_f B_u) with A, B fixed
+    sums over the bin-unit grid; A is mirror-symmetric and B antisymmetric,
+    so the outer columns' ratio r gives (r - 1)/(r + 1) = w B_3 / (xk A_3), with
+    w the mean bin width over the pooled scales. Against a single scale f = 1 it
+    must be the mean of the five relative scales of §3.2 (1/2 to 2 in steps
+    of sqrt 2)."""
+    Y, X = np.mgrid[0:128, 0:128].astype(float)
+    L = X * X
+    xk, yk, sig = 64.3, 63.7, 2.0
+
+    def t(p):
+        D = so.descriptor(L, xk, yk, 64, 64, sig, 0.0, p).reshape(4, 4, 8)
+        assert D[:, :, 1:].sum() < 1e-12 * D.sum()   # dy rounds to about 1e-13
+        col = D.sum(axis=(0, 2))
+        r = col[3] / col[0]
+        return (r - 1) / (r + 1)
+
+    five = (0.5, 2 ** -0.5, 1.0, 2 ** 0.5, 2.0)
+    pooled = t(so.Params(dsp=True, desc_clip=1.0))
+    single = t(so.Params(dsp=True, desc_clip=1.0, dsp_scales=(1.0,)))
+    assert pooled / single == pytest.approx(sum(five) / 5, rel=1e-9)
+
+
+@pytest.mark.parametrize("side", ["left", "right", "top", "bottom"])
+def test_dsp_stencil_bound_at_image_edge(side):
+    """A DSP sample is kept only if its stencil stays inside: 1 <= x < W - 2
+    and 1 <= y < H - 2 (the bilinear read at x + 1 needs x + 1 < W - 1). With
+    sigma = 2 and scale 2 the bin width is 12 px and the outermost sample
+    coordinate is 1.9375 bins, 23.25 px from the keypoint; a keypoint 23.25 px
+    inside the edge puts one row (or column) of 32 samples exactly on the
+    bound: kept at x = 1 (y = 1), dropped at x = W - 2 (y = H - 2). On a unit
+    gradient the mass is the separable closed form of the patch with that
+    row or column's share removed when it is dropped."""
+    p = so.Params(dsp=True)
+    H, W = 160, 150
+    Y, X = np.mgrid[0:H, 0:W].astype(float)
+    L = 0.5 * (Y if side in ("top", "bottom") else X)
+    xk, yk = {"left": (1 + 23.25, 80.0), "right": (W - 2 - 23.25, 80.0),
+              "top": (75.0, 1 + 23.25), "bottom": (75.0, H - 2 - 23.25)}[side]
+    c = (np.arange(p.dsp_grid) + 0.5) * 4 / p.dsp_grid - 2.0
+    u = c + 1.5
+    k = np.where(u < 0, 1 + u, np.where(u > 3, 4 - u, 1.0)) * np.exp(-c * c / 8.0)
+    full = k.sum()
+    edge = full - k[-1] if side in ("right", "bottom") else full
+    h = so.dsp_scale_histogram(L, xk, yk, 2.0, 0.0, 2.0, p)
+    assert h.sum() == pytest.approx(edge * full, rel=1e-12)
+
+
 def test_rootsift_is_sqrt_of_l1_normalised_plain():
     """RootSIFT output squared equals the plain (clipped, L2-renormalised)
     descriptor divided by its L1 norm; it has unit L2 norm and no negative entry."""
