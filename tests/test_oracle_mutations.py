@@ -1,6 +1,7 @@
 """Mutation check of the oracle pins: each plausible mistake below is planted in
 a temporary copy of the oracle (on the CPU only) and the pin suite must fail on
 it. A mutant that survives means a part of the oracle is not pinned."""
+import concurrent.futures
 import os
 import shutil
 import subprocess
@@ -108,6 +109,14 @@ MUTANTS = {
                                  "    ok = (x > 1) & (x < w - 2) & (y > 1) & (y < h - 2)\n    x, y, rx, ry = x[ok], y[ok], rx[ok], ry[ok]"),
     "dsp_scales_four": ("    dsp_scales: tuple = (0.5, 2 ** -0.5, 1.0, 2 ** 0.5, 2.0)",
                         "    dsp_scales: tuple = (2 ** -0.5, 1.0, 2 ** 0.5, 2.0)"),
+    "dog_reversed": ("    return octave[1:] - octave[:-1]", "    return octave[:-1] - octave[1:]"),
+    "refine_round_half_even": ("    return int(math.floor(abs(v) + 0.5)) * (1 if v >= 0 else -1)",
+                               "    return int(round(v))"),
+    "refine_four_iterations": ("    for _ in range(p.max_refine_iter):",
+                               "    for _ in range(p.max_refine_iter - 1):"),
+    "edge_ratio_equality_kept": ("    if det <= 0 or lhs >= rhs:", "    if det <= 0 or lhs > rhs:"),
+    "peak_ratio_strict": ("        above = hk >= thr", "        above = hk > thr"),
+    "margin_skips_convergence": ("        margin = min(margin, abs(0.5 - m) / 0.5)\n", "\n"),
     "rootsift_no_l1": ("        vec = np.sqrt(vec / l1) if l1 > 0 else vec",
                        "        vec = np.sqrt(vec) if l1 > 0 else vec"),
 }
@@ -150,18 +159,40 @@ CASES = ([(n, "sift_oracle.py", "test_oracle_pins.py") for n in sorted(MUTANTS)]
 _TABLE = {"sift_oracle.py": MUTANTS, "magsac.py": MAGSAC_MUTANTS, "matcher.py": MATCHER_MUTANTS}
 
 
-@pytest.mark.parametrize("name,target,pins", CASES, ids=[c[0] for c in CASES])
-def test_pins_catch_mutant(name, target, pins, tmp_path):
+def _run_mutant(name, target, pins, work):
+    """Plant one mutant in a copy of the oracle under `work` and run its pin file;
+    returns (exit code, tail of the output)."""
     before, after = _TABLE[target][name]
     src = open(os.path.join(ROOT, "oracle", target)).read()
-    assert before in src, "mutation anchor missing: " + name
+    if before not in src:
+        return None, "mutation anchor missing: " + name
     for d in ("oracle", "workloads"):
-        shutil.copytree(os.path.join(ROOT, d), tmp_path / d,
+        shutil.copytree(os.path.join(ROOT, d), os.path.join(work, d),
                         ignore=shutil.ignore_patterns("__pycache__"))
-    (tmp_path / "tests").mkdir()
+    os.mkdir(os.path.join(work, "tests"))
     for f in ("conftest.py", pins):
-        shutil.copy(os.path.join(ROOT, "tests", f), tmp_path / "tests" / f)
-    (tmp_path / "oracle" / target).write_text(src.replace(before, after))
+        shutil.copy(os.path.join(ROOT, "tests", f), os.path.join(work, "tests", f))
+    with open(os.path.join(work, "oracle", target), "w") as fh:
+        fh.write(src.replace(before, after))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-m", "pytest", "tests/" + pins, "-q", "-x",
-                        "-p", "no:cacheprovider"], cwd=tmp_path, capture_output=True, text=True)
-    assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
+                        "-p", "no:cacheprovider"], cwd=work, capture_output=True, text=True,
+                       env=env)
+    return r.returncode, r.stdout[-2000:]
+
+
+@pytest.fixture(scope="module")
+def mutant_results(tmp_path_factory):
+    """All mutants run at once, one pin-suite process per core."""
+    base = tmp_path_factory.mktemp("mutants")
+    workers = max(1, min(8, os.cpu_count() or 1))
+    with concurrent.futures.ThreadPoolExecutor(workers) as ex:
+        futs = {c[0]: ex.submit(_run_mutant, *c, str(base / c[0])) for c in CASES}
+        return {k: f.result() for k, f in futs.items()}
+
+
+@pytest.mark.parametrize("name,target,pins", CASES, ids=[c[0] for c in CASES])
+def test_pins_catch_mutant(name, target, pins, mutant_results):
+    code, out = mutant_results[name]
+    assert code is not None, out
+    assert code != 0, f"mutant {name} survived the pins:\n{out}"

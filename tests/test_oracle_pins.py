@@ -255,6 +255,97 @@ def test_edge_test_threshold(a, b):
         assert r.code == so.KEEP
 
 
+def _separable_stack(fx, fy, fs, x0, y0, s0, shape=(5, 25, 25), c0=0.0):
+    """D = c0 + fx + fy + fs with each profile given on consecutive indices from
+    (x0, y0, s0) and zero elsewhere; mixed differences of a separable sum are 0."""
+    D = np.full(shape, c0)
+    gx, gy, gs = np.zeros(shape[2]), np.zeros(shape[1]), np.zeros(shape[0])
+    gx[x0:x0 + len(fx)] = fx
+    gy[y0:y0 + len(fy)] = fy
+    gs[s0:s0 + len(fs)] = fs
+    return D + gs[:, None, None] + gy[None, :, None] + gx[None, None, :]
+
+
+def test_refinement_half_offset_rounds_away_from_zero():
+    """An offset of exactly +-1/2 is not converged (|delta| < 0.5 is required) and
+    moves the pixel, rounded half away from zero. A profile 0, 1, 1 along x has
+    dx = 1/2 and dxx = -1, so delta_x = 1/2 exactly (powers of two, exact in
+    Cramer's rule); at x = W - b - 1 the move lands on the border and is
+    rejected, as is the mirrored profile at x = b and the same profile along s
+    at the top layer s = S."""
+    p = so.Params(contrast_thr=0.001)
+    b, S = p.border, p.n_scales
+    peak = [0.0, 1.0, 0.0]
+    x = 25 - b - 1
+    D = _separable_stack([0.0, 1.0, 1.0], peak, peak, x - 1, 11, 1)
+    assert so.refine_candidate(D, 2, 12, x, p).code == so.REJ_BOUNDS
+    D = _separable_stack([1.0, 1.0, 0.0], peak, peak, b - 1, 11, 1)
+    assert so.refine_candidate(D, 2, 12, b, p).code == so.REJ_BOUNDS
+    D = _separable_stack(peak, peak, [0.0, 1.0, 1.0], 11, 11, S - 1)
+    assert so.refine_candidate(D, S, 12, 12, p).code == so.REJ_BOUNDS
+
+
+def test_refinement_is_capped_at_five_steps():
+    """§3.2 fixes five refinement iterations. Along x the profile f(k+1) =
+    (4 f(k) - f(k-1)) / 3 from f = 0, 1 makes every Newton step exactly one
+    pixel; ending it with a mirror (f(k+1) = f(k-1)) puts the vertex on a pixel.
+    Four moves then converge on the fifth evaluation and are kept; five moves
+    exhaust the iterations and are rejected."""
+    p = so.Params(contrast_thr=0.001)
+    for moves, code in ((4, so.KEEP), (5, so.REJ_NOCONV)):
+        f = [0.0, 1.0]
+        for _ in range(moves):
+            f.append((4 * f[-1] - f[-2]) / 3)
+        f.append(f[-2])
+        peak = [-1 / 81, 0.0, -1 / 81]
+        D = _separable_stack(f, peak, [-2 / 81, 0.0, -2 / 81], 7, 11, 1)
+        r = so.refine_candidate(D, 2, 12, 8, p)
+        assert r.code == code, moves
+        if code == so.KEEP:
+            assert r.x == 8 + moves and abs(r.dx) < 1e-9
+
+
+def test_edge_ratio_at_exact_threshold_is_rejected():
+    """Principal curvatures in ratio exactly r = 10 (dxx = -10, dyy = -1, all
+    integers) give tr^2 r = (r + 1)^2 det = 1210; only tr^2 r < (r + 1)^2 det
+    passes, so the candidate is rejected as an edge."""
+    p = so.Params(contrast_thr=0.001, edge_ratio=10.0)
+    D = _separable_stack([-5.0, 0.0, -5.0], [-0.5, 0.0, -0.5], [-0.5, 0.0, -0.5], 11, 11, 1,
+                         c0=20.0)
+    assert so.refine_candidate(D, 2, 12, 12, p).code == so.REJ_EDGE
+    D = _separable_stack([-5.0, 0.0, -5.0], [-0.5625, 0.0, -0.5625], [-0.5, 0.0, -0.5],
+                         11, 11, 1, c0=20.0)   # ratio 10 / 1.125: kept
+    assert so.refine_candidate(D, 2, 12, 12, p).code == so.KEEP
+
+
+def test_refinement_margin_reports_the_convergence_decision():
+    """The margin is the smallest relative distance of any decision from its
+    threshold: a vertex 0.45 px off converges with |0.5 - 0.45| / 0.5 = 0.1,
+    nearer than the contrast and edge decisions here."""
+    p = so.Params(contrast_thr=0.001)
+    H = -np.diag([0.01, 0.012, 0.02])
+    D = _quadratic_stack((12.45, 12.1, 2.1), H)
+    r = so.refine_candidate(D, 2, 12, 12, p)
+    assert r.code == so.KEEP
+    assert abs(r.margin - 0.1) < 1e-9
+
+
+def test_dog_is_next_level_minus_this_one():
+    """§3.2: D_i = G_{i+1} - G_i. Each further blur lowers the centre of a bright
+    blob and raises the centre of a dark one, so D is negative at the first and
+    positive at the second, on every layer of every octave."""
+    n = 64
+    Y, X = np.mgrid[0:n, 0:n].astype(float)
+    blob = np.exp(-((X - 31.5) ** 2 + (Y - 31.5) ** 2) / (2 * 3.0 ** 2))
+    p = so.Params(min_octave_side=16)
+    for sign in (1.0, -1.0):
+        for G in so.build_pyramid(0.5 + 0.4 * sign * blob, p):
+            D = so.dog(G)
+            c = D.shape[1] // 2
+            centre = D[:, c - 1:c + 1, c - 1:c + 1].mean(axis=(1, 2))
+            assert np.all(-sign * centre > 0), (sign, centre)
+
+
 # ------------------------------------------------------------------ blob scale
 
 @pytest.mark.parametrize("s", [3.0, 4.0, 6.0, 8.0, 11.0, 16.0])
@@ -692,6 +783,16 @@ def test_orientation_peaks_are_strict_maxima():
     h[11] = 0.999                       # break the tie: bin 10 becomes a strict peak
     angles, _ = so.orientation_peaks(h, so.Params())
     assert len(angles) == 2 and abs(angles[1] - 200.0) < 1e-12
+
+
+def test_orientation_peak_at_exactly_the_ratio_is_kept():
+    """READING: a secondary peak is kept at >= 0.8 of the maximum, so one at
+    exactly 0.8 (the same double as 0.8 * 1.0) gives a second orientation."""
+    h = np.zeros(36)
+    h[5] = 1.0
+    h[20] = 0.8
+    angles, _ = so.orientation_peaks(h, so.Params())
+    assert angles == [50.0, 200.0]
 
 
 def test_descriptor_offsets_from_the_subpixel_keypoint_and_window_reach():
