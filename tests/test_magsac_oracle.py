@@ -101,6 +101,47 @@ def test_dlt_degenerate_and_residual_cases():
     assert np.isinf(r[0]) and np.isfinite(r[1])
 
 
+def test_default_model_has_four_degrees_of_freedom():
+    """READING: a correspondence's residual carries the noise of its four
+    coordinates, so the defaults are the chi distribution with 4 degrees of
+    freedom (0.99 quantile: chi^2 = 13.2767 in the tables) and the weight is
+    that of n = 4."""
+    assert abs(om.chi_quantile() ** 2 - 13.2767) < 1e-3
+    k = om.chi_quantile()
+    shift = _weight_numeric(k, 1.0, n=4)
+    for t in (0.3, 1.0, 2.5):
+        assert abs(float(om.weight(t, 1.0)) - (_weight_numeric(t, 1.0, n=4) - shift)) < 1e-10
+
+
+def test_hartley_normaliser():
+    """Hartley normalisation: the centroid goes to the origin and the mean
+    distance from it becomes sqrt(2)."""
+    p = RNG.uniform(0, 1000, size=(4, 2))
+    q = om._apply(om._normaliser(p), p)
+    np.testing.assert_allclose(q.mean(axis=0), 0.0, atol=1e-12)
+    assert abs(np.linalg.norm(q, axis=1).mean() - math.sqrt(2.0)) < 1e-12
+
+
+def test_dlt_degenerate_forms_of_the_minimal_solver():
+    """READING of the minimal solver (h33 = 1 in normalised coordinates, then
+    H[2, 2] = 1): three collinear points in the second image only, a model that
+    sends the first sample's centroid to the line at infinity (normalised
+    h33 = 0), and one that sends the image origin there (H[2, 2] = 0) have no
+    such solution and are degenerate."""
+    xa = np.array([[400.0, 420.0], [610.0, 380.0], [580.0, 600.0], [390.0, 590.0]])
+    xb = np.array([[0.0, 0.0], [100.0, 100.0], [200.0, 200.0], [0.0, 300.0]])
+    assert om.dlt(xa, xb) is None
+    c = xa.mean(axis=0)
+    H = np.array([[1.0, 0.1, 5.0], [0.05, 1.0, 3.0], [1e-3, 2e-3, -1e-3 * c[0] - 2e-3 * c[1]]])
+    assert om.dlt(xa, _project(H, xa)) is None
+    H[2, 2] = 0.0
+    assert om.dlt(xa, _project(H, xa)) is None
+    H[2, 2] = 1.0                                   # the same model with H[2, 2] = 1 is fine
+    G = om.dlt(xa, _project(H, xa))
+    assert G is not None
+    np.testing.assert_allclose(G, H, rtol=1e-8, atol=1e-10)
+
+
 def _planted(rng, n_in=150, n_out=100, noise=0.5):
     H = _random_h(rng)
     xa_in = rng.uniform(0, 1000, size=(n_in, 2))

@@ -138,6 +138,16 @@ MAGSAC_MUTANTS = {
                                       "inl = residuals(H, xa, xb) <= sigma_max"),
     "magsac_best_is_worst": ("    best = int(np.argmin(scores))",
                              "    best = int(np.argmax(np.where(np.isfinite(scores), scores, -np.inf)))"),
+    "magsac_two_dof": ("DOF = 4 ", "DOF = 2 "),
+    "magsac_normaliser_unit_distance": ("    s = math.sqrt(2.0) / d if d > 0 else 1.0",
+                                        "    s = 1.0 / d if d > 0 else 1.0"),
+    "magsac_normaliser_no_centroid": (
+        "    return np.array([[s, 0.0, -s * c[0]], [0.0, s, -s * c[1]], [0.0, 0.0, 1.0]])",
+        "    return np.array([[s, 0.0, 0.0], [0.0, s, 0.0], [0.0, 0.0, 1.0]])"),
+    "magsac_collinear_first_image_only": ("    if _collinear(pa) or _collinear(pb):",
+                                          "    if _collinear(pa):"),
+    "magsac_normalised_h33_unchecked": ("    if abs(v[8]) < 1e-9:", "    if False:"),
+    "magsac_h22_unchecked": ("    if abs(H[2, 2]) < 1e-12 * np.abs(H).max():", "    if False:"),
     "magsac_weight_sigma_scale": (
         "    x = t * t / (2.0 * sigma_max * sigma_max)",
         "    x = t * t / (sigma_max * sigma_max)"),
