@@ -117,6 +117,17 @@ MUTANTS = {
     "edge_ratio_equality_kept": ("    if det <= 0 or lhs >= rhs:", "    if det <= 0 or lhs > rhs:"),
     "peak_ratio_strict": ("        above = hk >= thr", "        above = hk > thr"),
     "margin_skips_convergence": ("        margin = min(margin, abs(0.5 - m) / 0.5)\n", "\n"),
+    "orientation_edge_columns_dropped": (
+        "    ys, xs, i, j = ys[ok], xs[ok], i[ok], j[ok]",
+        "    ok = ok & (xs >= 2) & (xs <= w - 3) & (ys >= 2) & (ys <= h - 3)\n"
+        "    ys, xs, i, j = ys[ok], xs[ok], i[ok], j[ok]"),
+    "descriptor_edge_pixels_dropped": (
+        "    ys, xs = ys[ok], xs[ok]\n    ox = xs - xk",
+        "    ok = ok & (xs >= 2) & (xs <= w - 3) & (ys >= 2) & (ys <= h - 3)\n"
+        "    ys, xs = ys[ok], xs[ok]\n    ox = xs - xk"),
+    "descriptor_on_next_level": ("            desc[t] = descriptor(pyr[o][r.s], xk, yk",
+                                 "            desc[t] = descriptor(pyr[o][r.s + 1], xk, yk"),
+    "orientation_on_next_level": ("            L = G[r.s]\n", "            L = G[r.s + 1]\n"),
     "rootsift_no_l1": ("        vec = np.sqrt(vec / l1) if l1 > 0 else vec",
                        "        vec = np.sqrt(vec) if l1 > 0 else vec"),
 }

@@ -733,6 +733,88 @@ def test_orientation_window_mass_closed_form(sigma_oct):
     assert abs(hist.sum() - want) / want < 1e-12
 
 
+@pytest.mark.parametrize("xi", [3, 116])
+def test_orientation_window_clipped_at_the_image_edge(xi):
+    """Orientation samples need both stencil neighbours, so columns 1..W-2 are
+    used: on a ramp the mass is m * (sum of g over the kept columns) * (sum of g
+    over all rows), with g(k) = exp(-k^2 / (2 (1.5 sigma)^2)). With sigma = 1.8
+    (R = 8) the window at x = 3 loses columns -5..0 and keeps column 1; at
+    x = W - 4 it keeps column W - 2."""
+    p = so.Params()
+    W = 120
+    Y, X = np.mgrid[0:121, 0:W].astype(float)
+    L = 0.003 * X + 0.004 * Y
+    m = 2.0 * math.hypot(0.003, 0.004)
+    sig = 1.8
+    hist = so.orientation_histogram(L, xi, 60, sig, p)
+    sw = 1.5 * sig
+    R = int(math.floor(4.5 * sig + 0.5))
+    k = np.arange(-R, R + 1)
+    g = np.exp(-(k * k) / (2 * sw * sw))
+    cols = (xi + k >= 1) & (xi + k <= W - 2)
+    assert not cols.all() and (xi + k[cols]).min() in (1, xi - R)
+    want = m * g[cols].sum() * g.sum()
+    assert abs(hist.sum() - want) / want < 1e-12
+
+
+@pytest.mark.parametrize("xk", [10.3, 109.6])
+def test_descriptor_pixels_clipped_at_the_image_edge(xk):
+    """The single-scale descriptor uses pixels 1..W-2 (both stencil neighbours
+    inside). On L = x/2 (gradient (1, 0): magnitude 1, all in orientation bin 0)
+    at angle 0 the raw mass is separable: (sum over kept columns of g k)(sum over
+    rows of g k), offsets from the sub-pixel keypoint in bins of w = 3 sigma,
+    g(r) = exp(-r^2 / 8), u = r + 3/2 and k(u) the share of the trilinear split
+    inside bins 0..3. With sigma = 2 the support reaches 15 px, past column 1
+    (or W - 2)."""
+    p = so.Params()
+    W, Hh = 120, 121
+    Y, X = np.mgrid[0:Hh, 0:W].astype(float)
+    L = 0.5 * X
+    sig, yk = 2.0, 60.25
+    xi, yi = int(round(xk)), 60
+    h = so.plain_histogram(L, xk, yk, xi, yi, sig, 0.0, p)
+    wbin = 3.0 * sig
+
+    def side(pix, centre, lo, hi):
+        r = (pix - centre) / wbin
+        u = r + 1.5
+        ok = (pix >= lo) & (pix <= hi) & (u > -1) & (u < 4)
+        kk = np.where(u < 0, 1 + u, np.where(u > 3, 4 - u, 1.0))
+        return (np.exp(-r * r / 8.0) * kk)[ok].sum()
+
+    R = int(math.floor(wbin * math.sqrt(2.0) * 2.5 + 0.5))
+    px = np.arange(xi - R, xi + R + 1).astype(float)
+    py = np.arange(yi - R, yi + R + 1).astype(float)
+    want = side(px, xk, 1, W - 2) * side(py, yk, 1, Hh - 2)
+    assert side(px, xk, 1, W - 2) < side(px, xk, -10 ** 6, 10 ** 6)   # the edge cuts the support
+    assert h[:, :, 1:].sum() < 1e-12 * h.sum()
+    assert h.sum() == pytest.approx(want, rel=1e-12)
+
+
+def test_orientation_and_descriptor_use_the_nearest_gaussian_level():
+    """Orientation and descriptor are taken on the Gaussian level whose scale
+    sigma0 2^(i/S) is nearest the keypoint's octave-relative sigma (the
+    refined scale offset is below 1/2 level). The level is found here from the
+    reported sigma alone, and both results are recomputed on it."""
+    img = synth.make_image(synth.rng_for(93, 0), 96, 120)
+    p = so.Params()
+    res = so.extract(img, p, keep_pyramid=True)
+    assert len(res) >= 5
+    S = p.n_scales
+    for t in range(len(res)):
+        o = int(res.octave[t])
+        so_t = res.sigma[t] / 2.0 ** o
+        i = int(np.argmin([abs(math.log2(so_t / (p.sigma0 * 2.0 ** (k / S)))) for k in range(S + 3)]))
+        L = res.pyramid[o][i]
+        xi, yi = int(res.internals["xi"][t]), int(res.internals["yi"][t])
+        xk, yk = res.x[t] / 2.0 ** o, res.y[t] / 2.0 ** o
+        d = so.descriptor(L, xk, yk, xi, yi, so_t, res.angle[t], p)
+        np.testing.assert_allclose(res.desc[t], d, atol=1e-12)
+        hist = so.orientation_histogram(L, xi, yi, so_t, p)
+        angles, _ = so.orientation_peaks(so.smooth_histogram(hist), p)
+        assert min(abs((a - res.angle[t] + 180) % 360 - 180) for a in angles) < 1e-9
+
+
 def test_descriptor_clip_is_active_on_concentrated_mass():
     """Upright on a ramp along a bin centre: all mass sits in one orientation bin and
     the central cells exceed 0.2 of the norm. After clipping, exactly those entries
