@@ -246,38 +246,6 @@ def find_candidates(D: np.ndarray, p: Params):
             np.concatenate(m_gate), np.concatenate(m_ext))
 
 
-def near_miss_candidates(D: np.ndarray, p: Params, eps: float):
-    """Positions that fail the extremum / gate test by a relative margin below
-    eps (these may legitimately become candidates under FP32 rounding)."""
-    S = p.n_scales
-    b = p.border
-    _, h, w = D.shape
-    res = []
-    if h - 2 * b <= 0 or w - 2 * b <= 0:
-        return res
-    thr = p.prefilter_ratio * p.contrast_thr
-    for s in range(1, S + 1):
-        c = D[s, b:h - b, b:w - b]
-        nmax = np.full(c.shape, -np.inf)
-        nmin = np.full(c.shape, np.inf)
-        for ds in (-1, 0, 1):
-            for dy in (-1, 0, 1):
-                for dx in (-1, 0, 1):
-                    if ds == 0 and dy == 0 and dx == 0:
-                        continue
-                    n = D[s + ds, b + dy:h - b + dy, b + dx:w - b + dx]
-                    nmax = np.maximum(nmax, n)
-                    nmin = np.minimum(nmin, n)
-        tol = eps * np.abs(c)
-        near = ((c > nmax - tol) | (c < nmin + tol)) & (np.abs(c) > thr * (1 - eps))
-        strict = (c > nmax) | (c < nmin)
-        strict &= np.abs(c) > thr
-        ys, xs = np.nonzero(near & ~strict)
-        for y, x in zip(ys, xs):
-            res.append((s, y + b, x + b))
-    return res
-
-
 # --------------------------------------------------------------- A6: refinement
 
 def _round_half_away(v: float) -> int:

@@ -128,6 +128,21 @@ MUTANTS = {
     "descriptor_on_next_level": ("            desc[t] = descriptor(pyr[o][r.s], xk, yk",
                                  "            desc[t] = descriptor(pyr[o][r.s + 1], xk, yk"),
     "orientation_on_next_level": ("            L = G[r.s]\n", "            L = G[r.s + 1]\n"),
+    "extremum_margin_absolute": ("        m_ext.append(gap / np.abs(cv))", "        m_ext.append(gap)"),
+    "gate_margin_absolute": ("        m_gate.append((np.abs(cv) - thr) / np.maximum(np.abs(cv), thr))",
+                             "        m_gate.append(np.abs(cv) - thr)"),
+    "margin_skips_contrast": (
+        "    margin = min(margin, abs(abs(contrast) - p.contrast_thr) / max(abs(contrast), p.contrast_thr))\n",
+        "\n"),
+    "margin_skips_edge": ("        margin = min(margin, abs(rhs - lhs) / denom)\n", "        pass\n"),
+    "margin_skips_peak_ratio": ("            margin = min(margin, abs(hk - thr) / hmax)\n", "            pass\n"),
+    "margin_skips_rounding": ("            margin = min(margin, abs(a - edge) / edge)\n", "            pass\n"),
+    "response_signed": ("                   abs(contrast), margin)", "                   contrast, margin)"),
+    "keypoint_margin_skips_candidate": (
+        "            m0 = min(float(mg[ci]), float(me[ci]), r.margin)", "            m0 = r.margin"),
+    "keypoint_margin_skips_orientation": (
+        "                rows.append((o, r, sigma_oct, a, min(m0, m1)))",
+        "                rows.append((o, r, sigma_oct, a, m0))"),
     "rootsift_no_l1": ("        vec = np.sqrt(vec / l1) if l1 > 0 else vec",
                        "        vec = np.sqrt(vec) if l1 > 0 else vec"),
 }

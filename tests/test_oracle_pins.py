@@ -330,6 +330,93 @@ def test_refinement_margin_reports_the_convergence_decision():
     assert abs(r.margin - 0.1) < 1e-9
 
 
+def test_candidate_margins_are_relative_distances():
+    """Each candidate carries two margins: the pre-gate's (|D| - T') / max(|D|, T')
+    with T' = contrast_thr / 2, and the extremum's gap to the nearest of its 26
+    neighbours relative to |D|. A maximum 0.1 beside 0.08 has gap 0.2; a minimum
+    -0.1 beside -0.05 has gap 0.5."""
+    p = so.Params()
+    D = np.zeros((5, 21, 21))
+    D[2, 7, 7], D[2, 7, 8] = 0.1, 0.08
+    D[3, 12, 12], D[3, 12, 13] = -0.1, -0.05
+    cs, cy, cx, mg, me = so.find_candidates(D, p)
+    assert list(zip(cs, cy, cx)) == [(2, 7, 7), (3, 12, 12)]
+    gate = 0.5 * p.contrast_thr
+    np.testing.assert_allclose(mg, [(0.1 - gate) / 0.1] * 2, rtol=1e-12)
+    np.testing.assert_allclose(me, [0.2, 0.5], rtol=1e-12)
+
+
+@pytest.mark.parametrize("vertex,c0,diag,want", [
+    ((13.3, 12.1, 2.1), 0.04, (10.0, 12.0, 20.0), 0.2 / 1.5),   # move of 1.3: 0.2 from the 1.5 rounding edge
+    ((12.1, 12.1, 2.1), 0.0011, (10.0, 12.0, 20.0), 0.0001 / 0.0011),   # contrast 0.0011 vs 0.001
+    ((12.1, 12.1, 2.1), 0.04, (1.0, 9.0, 5.0), 89.0 / 2089.0),   # edge: |121*9 - 10*10^2| / (1089 + 1000)
+])
+def test_refinement_margin_takes_the_nearest_decision(vertex, c0, diag, want):
+    """The refinement margin is the smallest of: |0.5 - max|delta|| / 0.5 per
+    step, |a - (floor(a) + 1/2)| / (floor(a) + 1/2) per moved offset component a,
+    the contrast's | |c| - T| / max(|c|, T), and the edge test's
+    |(r+1)^2 det - r tr^2| / (|r tr^2| + |(r+1)^2 det|). Each case makes one of the
+    last three the smallest."""
+    p = so.Params(contrast_thr=0.001)
+    H = -1e-3 * np.diag(diag)
+    D = _quadratic_stack(vertex, H, c0=c0)
+    r = so.refine_candidate(D, 2, 12, 12, p)
+    assert r.code == so.KEEP
+    assert abs(r.margin - want) < 1e-9
+
+
+def test_refinement_of_a_minimum_reports_positive_response():
+    """The response is |D| at the refined position: a minimum with value -0.04
+    reports 0.04."""
+    p = so.Params(contrast_thr=0.001)
+    H = np.diag([0.010, 0.012, 0.02])
+    D = _quadratic_stack((12.2, 11.9, 2.1), H, c0=-0.04)
+    r = so.refine_candidate(D, 2, 12, 12, p)
+    assert r.code == so.KEEP and abs(r.response - 0.04) < 1e-12
+
+
+def test_orientation_peak_margins():
+    """The peak margin is the distance of every local maximum from the 0.8 ratio
+    and, for bins at or near it, of the gap to each neighbour, both relative to
+    the maximum: a secondary maximum at 0.75 gives 0.05; a shoulder at 0.99 beside
+    the maximum gives 0.01."""
+    h = np.zeros(36)
+    h[5], h[20] = 1.0, 0.75
+    angles, m = so.orientation_peaks(h, so.Params())
+    assert angles == [50.0] and abs(m - 0.05) < 1e-12
+    h[20], h[6] = 0.0, 0.99
+    _, m = so.orientation_peaks(h, so.Params())
+    assert abs(m - 0.01) < 1e-12
+
+
+def test_keypoint_margin_is_the_minimum_over_its_decisions(monkeypatch):
+    """A keypoint's margin is the smallest margin of every decision behind it:
+    pre-gate, extremum, refinement and orientation peaks. Making each stage's
+    margin tiny in turn (by wrapping the stage) must bring every keypoint's
+    margin down to it."""
+    img = synth.make_image(synth.rng_for(93, 0), 96, 120)
+    p = so.Params()
+    base = so.extract(img, p, with_descriptors=False)
+    assert len(base) >= 5 and base.margin.min() > 1e-6
+    fc, op = so.find_candidates, so.orientation_peaks
+
+    def cand_stage(k, v):
+        def f(D, pp):
+            out = list(fc(D, pp))
+            out[k] = np.full(len(out[k]), v)
+            return tuple(out)
+        return f
+
+    for k, v in ((3, 1e-9), (4, 2e-9)):
+        monkeypatch.setattr(so, "find_candidates", cand_stage(k, v))
+        res = so.extract(img, p, with_descriptors=False)
+        assert len(res) == len(base) and np.all(res.margin == v), k
+    monkeypatch.setattr(so, "find_candidates", fc)
+    monkeypatch.setattr(so, "orientation_peaks", lambda hs, pp: (op(hs, pp)[0], 3e-9))
+    res = so.extract(img, p, with_descriptors=False)
+    assert len(res) == len(base) and np.all(res.margin == 3e-9)
+
+
 def test_dog_is_next_level_minus_this_one():
     """§3.2: D_i = G_{i+1} - G_i. Each further blur lowers the centre of a bright
     blob and raises the centre of a dark one, so D is negative at the first and
