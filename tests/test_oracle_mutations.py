@@ -189,10 +189,32 @@ MATCHER_MUTANTS = {
                              "    j1 = S.shape[1] - 1 - np.argmax(S[:, ::-1], axis=1)"),
 }
 
+# Mistakes planted in the parity comparator, caught by its own test file.
+COMPARE_MUTANTS = {
+    "compare_position_tolerance": ("POS_TOL = 0.01", "POS_TOL = 0.05"),
+    "compare_angle_without_wrap": (
+        "    return np.abs((np.asarray(a) - np.asarray(b) + 180.0) % 360.0 - 180.0)",
+        "    return np.abs(np.asarray(a) - np.asarray(b))"),
+    "compare_no_margin_excuse": ("    eligible = oracle_res.margin >= margin_eps",
+                                 "    eligible = oracle_res.margin >= 0"),
+    "compare_position_x_only": (
+        "        dpos = np.maximum(np.abs(gx[cand] - ox[i]), np.abs(gy[cand] - oy[i]))",
+        "        dpos = np.abs(gx[cand] - ox[i])"),
+    "compare_scale_absolute": ("        ds = np.abs(gsig[near] - osig[i]) / osig[i]",
+                               "        ds = np.abs(gsig[near] - osig[i]) / 10.0"),
+    "compare_ignores_layer": ("        cand = buckets.get((int(ooct[i]), int(olay[i])))",
+                              "        cand = np.concatenate(list(buckets.values()))"),
+    "compare_propagation_uncounted": ("                    if dd2 <= DESC_TOL:\n                        n_prop += 1",
+                                      "                    if True:\n                        n_prop += 0"),
+    "compare_no_recompute": ("                    dd = min(dd, dd2)", "                    dd = dd"),
+}
+
 CASES = ([(n, "sift_oracle.py", "test_oracle_pins.py") for n in sorted(MUTANTS)]
          + [(n, "magsac.py", "test_magsac_oracle.py") for n in sorted(MAGSAC_MUTANTS)]
-         + [(n, "matcher.py", "test_matcher_oracle.py") for n in sorted(MATCHER_MUTANTS)])
-_TABLE = {"sift_oracle.py": MUTANTS, "magsac.py": MAGSAC_MUTANTS, "matcher.py": MATCHER_MUTANTS}
+         + [(n, "matcher.py", "test_matcher_oracle.py") for n in sorted(MATCHER_MUTANTS)]
+         + [(n, "compare.py", "test_compare.py") for n in sorted(COMPARE_MUTANTS)])
+_TABLE = {"sift_oracle.py": MUTANTS, "magsac.py": MAGSAC_MUTANTS, "matcher.py": MATCHER_MUTANTS,
+          "compare.py": COMPARE_MUTANTS}
 
 
 def _run_mutant(name, target, pins, work):
