@@ -76,6 +76,12 @@ def test_degenerate_cases():
     b = _unit(np.eye(8))
     m, _ = om.match(a, b)
     assert np.all(m == -1)                             # one descriptor: no ratio test possible
+    # Even an exact pair is not kept when one side has a single member: that
+    # member has no second neighbour, so its ratio test is undefined.
+    m, _ = om.match(b[:1], b)
+    assert np.all(m == -1)
+    m, _ = om.match(b, b[:1])
+    assert np.all(m == -1)
     m, _ = om.match(b, b)
     assert list(m) == list(range(8))                   # each unit vector matches itself (d1 = 0)
     dup = np.vstack([b[:1], b[:1], b[1:3]])
@@ -106,3 +112,39 @@ def test_ties_go_to_the_smaller_index():
     m, info = om.match(a, b)
     assert info["best_a"][0] == 1            # b[1] and b[2] tie: the first wins
     assert m[0] == -1                        # and the tie fails the ratio test
+
+
+def test_default_ratio_is_lowes():
+    """READING: the ratio defaults to Lowe's 0.8. With fp16-exact vectors the
+    first row's a-side ratio sqrt(2 - 2 s1) / sqrt(2 - 2 s2), s2 = -1/2, is 0.75
+    (s1 = 5/32: kept) or 0.850 (s1 = -43/512: rejected); the other side's test
+    and the mutual check pass clearly in both."""
+    for s1, kept in ((5 / 32, True), (-43 / 512, False)):
+        a = np.array([[1.0, 0.0, 0.0], [0.0, 0.0, 1.0]])
+        b = np.array([[s1, 0.0, -1.0], [-0.5, 0.0, 0.0]])
+        assert np.array_equal(om.round_fp16(b), b)
+        m, info = om.match(a, b)
+        assert info["best_a"][0] == 0 and info["best_b"][0] == 0
+        assert (m[0] == 0) == kept, s1
+        assert info["robust"][0]
+
+
+def test_robust_flags():
+    """A row is robust only when every decision behind it keeps its outcome under
+    a change of eps in each similarity: a tie between its two best similarities
+    is not robust; nor is a ratio test exactly at 0.8 on the other side, with
+    d1^2 = 0.64 d2^2 exactly (s1 = 23/64, s2 = -1/1024, all fp16-exact)."""
+    a = np.array([[1.0, 0.0, 0.0, 0.0], [0.0, 0.0, 1.0, 0.0]])
+    b = np.array([[0.5, 0.5, 0.0, 0.0], [0.5, -0.5, 0.0, 0.0]])
+    _, info = om.match(a, b)
+    assert info["s1_a"][0] == info["s2_a"][0] and not info["robust"][0]
+    a = np.array([[23 / 64, 0.0, 0.0, 0.0], [-1 / 1024, 0.0, 1.0, 0.0]])
+    b = np.array([[1.0, 0.0, 0.0, 0.0], [-1.0, 0.0, 0.0, 0.0]])
+    _, info = om.match(a, b)
+    assert info["best_a"][0] == 0 and info["best_b"][0] == 0
+    assert info["s1_b"][0] == 23 / 64 and info["s2_b"][0] == -1 / 1024
+    assert not info["robust"][0]
+    b[1, 0] = -0.5                                    # a clear case: robust
+    a[1, 0] = -0.5
+    _, info = om.match(a, b)
+    assert info["robust"][0]

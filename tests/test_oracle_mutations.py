@@ -185,6 +185,14 @@ MATCHER_MUTANTS = {
                                 "keep = da1[i] < ratio * da2[i]"),
     "matcher_ratio_one_side": ("and da1[i] < ratio * da2[i] and db1[j] < ratio * db2[j]",
                                "and da1[i] < ratio * da2[i]"),
+    "matcher_ratio_default_07": ("def match(desc_a: np.ndarray, desc_b: np.ndarray, ratio: float = 0.8,",
+                                 "def match(desc_a: np.ndarray, desc_b: np.ndarray, ratio: float = 0.7,"),
+    "matcher_robust_without_gap": (
+        "                             and sa1[i] - sa2[i] > 2 * eps and sb1[j] - sb2[j] > 2 * eps)",
+        "                             )"),
+    "matcher_robust_one_side": ("                             and _ratio_robust(sb1[j], sb2[j], ratio, eps)\n",
+                                "\n"),
+    "matcher_single_member_sets": ("    if na < 2 or nb < 2:", "    if na < 1 or nb < 1:"),
     "matcher_ties_to_last": ("    j1 = np.argmax(S, axis=1)                      # first occurrence = smallest index",
                              "    j1 = S.shape[1] - 1 - np.argmax(S[:, ::-1], axis=1)"),
 }
