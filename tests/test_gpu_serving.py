@@ -4,7 +4,6 @@ Each served result must be bit-identical to the same image extracted alone:
 requests are batched with whatever else is in flight, and batching never
 changes an image's arithmetic. Autotuned tile shapes change only the work
 distribution, so tuned and default runs must also agree bit for bit."""
-import numpy as np
 import pytest
 
 from workloads import synth

@@ -13,7 +13,6 @@ failure has already run every other test.
 """
 import ctypes
 
-import numpy as np
 import pytest
 
 from workloads import synth
