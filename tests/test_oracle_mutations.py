@@ -143,6 +143,14 @@ MUTANTS = {
     "keypoint_margin_skips_orientation": (
         "                rows.append((o, r, sigma_oct, a, min(m0, m1)))",
         "                rows.append((o, r, sigma_oct, a, m0))"),
+    "reported_layer_off_by_one": ("        layer[t] = r.s\n", "        layer[t] = r.s - 1\n"),
+    "cap_not_applied": (
+        "    keep = cap_topk(resp, p.max_kpts) if p.max_kpts > 0 else np.arange(len(rows))",
+        "    keep = np.arange(len(rows))"),
+    "cap_keeps_smallest": ("    resp = np.array([row[1].response for row in rows])",
+                           "    resp = -np.array([row[1].response for row in rows])"),
+    "upright_angle_nonzero": ("                angles, m1 = [0.0], math.inf",
+                              "                angles, m1 = [90.0], math.inf"),
     "rootsift_no_l1": ("        vec = np.sqrt(vec / l1) if l1 > 0 else vec",
                        "        vec = np.sqrt(vec) if l1 > 0 else vec"),
 }

@@ -389,6 +389,29 @@ def test_orientation_peak_margins():
     assert abs(m - 0.01) < 1e-12
 
 
+def test_extract_cap_keeps_the_largest_responses_in_canonical_order():
+    """With max_kpts = k the output is the k keypoints of largest response out
+    of the uncapped output (equal responses, e.g. the orientations of one point,
+    in canonical order), in the same canonical order."""
+    img = synth.make_image(synth.rng_for(93, 0), 96, 120)
+    full = so.extract(img, so.Params(), with_descriptors=False)
+    assert len(full) >= 6
+    for k in (1, 2, 3, len(full) - 1):
+        cap = so.extract(img, so.Params(max_kpts=k), with_descriptors=False)
+        top = np.sort(np.argsort(-full.response, kind="stable")[:k])
+        np.testing.assert_array_equal(cap.x, full.x[top])
+        np.testing.assert_array_equal(cap.response, full.response[top])
+
+
+def test_upright_gives_one_keypoint_at_angle_zero_per_refined_point():
+    """Upright mode skips the orientation histogram: every refined point gives
+    exactly one keypoint, at angle 0."""
+    img = synth.make_image(synth.rng_for(93, 0), 96, 120)
+    res = so.extract(img, so.Params(upright=True), with_descriptors=False)
+    assert len(res) == res.n_refined and len(res) > 0
+    assert np.all(res.angle == 0.0)
+
+
 def test_keypoint_margin_is_the_minimum_over_its_decisions(monkeypatch):
     """A keypoint's margin is the smallest margin of every decision behind it:
     pre-gate, extremum, refinement and orientation peaks. Making each stage's
@@ -892,6 +915,7 @@ def test_orientation_and_descriptor_use_the_nearest_gaussian_level():
         o = int(res.octave[t])
         so_t = res.sigma[t] / 2.0 ** o
         i = int(np.argmin([abs(math.log2(so_t / (p.sigma0 * 2.0 ** (k / S)))) for k in range(S + 3)]))
+        assert res.layer[t] == i and 1 <= i <= S      # the reported layer is that level
         L = res.pyramid[o][i]
         xi, yi = int(res.internals["xi"][t]), int(res.internals["yi"][t])
         xk, yk = res.x[t] / 2.0 ** o, res.y[t] / 2.0 ** o
