@@ -103,9 +103,11 @@ typedef struct sift_server sift_server;
 /* Fill *p with the defaults above (max_kpts = 8192). */
 sift_status sift_params_default(sift_params *p);
 
-/* Create a handle. The handle copies *p; device workspace is allocated lazily
- * on the first extraction and grown when a larger input arrives.
- * Errors: SIFT_E_INVALID on a null or out-of-range parameter. */
+/* Create a handle. The handle copies *p and creates its streams, events and
+ * pinned host descriptors on the current device; device workspace is allocated
+ * lazily on the first extraction and grown when a larger input arrives.
+ * Errors: SIFT_E_INVALID on a null or out-of-range parameter; SIFT_E_CUDA if
+ * no CUDA device is usable (nothing is created then). */
 sift_status sift_create(const sift_params *p, sift_handle **out);
 
 /* Release a handle and all device memory, graphs and streams it owns. The
@@ -239,8 +241,10 @@ sift_status sift_last_stats(sift_handle *h, int *stats, int max_images);
 sift_status sift_pyramid_size(sift_handle *h, int H, int W, int *n_octaves, size_t *total_elems);
 
 /* Build the Gaussian pyramid of one image (the first stage of sift_extract,
- * same kernels) and copy it, packed as above, into out_dev (capacity
- * out_elems floats). For inspection and tests. */
+ * same kernels: §3.2's scale space of separable 4-sigma blurs, incremental
+ * levels and decimated octaves) and copy it, packed as above, into out_dev
+ * (capacity out_elems floats). For inspection and tests. SIFT_E_INVALID if
+ * out_elems is below sift_pyramid_size()'s total or pitch_elems < W. */
 sift_status sift_build_pyramid(sift_handle *h, const float *img_dev, int H, int W,
                                int pitch_elems, void *stream, float *out_dev, size_t out_elems);
 
@@ -276,7 +280,8 @@ sift_status sift_set_tuning(sift_handle *h, const char *json);
  * step batch of everything admitted, and runs it on one of several worker
  * streams, so steps overlap on the device. Requests that arrive while other
  * steps are running join the next step. Pyramids and outputs stay on the
- * device; results are library-owned until released. */
+ * device (§3.3: results are handed to other frameworks by DLPack, without a
+ * copy); results are library-owned until released. */
 typedef struct {
   sift_status status;   /* SIFT_OK, SIFT_W_TRUNCATED or an error */
   int count;            /* keypoints in the buffers below */
