@@ -240,6 +240,19 @@ sift_status sift_last_stats(sift_handle *h, int *stats, int max_images);
  * layout [octave][level 0..S+2][H_o][W_o] (no padding). */
 sift_status sift_pyramid_size(sift_handle *h, int H, int W, int *n_octaves, size_t *total_elems);
 
+/* Octave geometry of an H x W input under *p, computed on the host alone (no
+ * handle and no device): the image is magnified when upsample is set and H*W
+ * is at most upsample_max_px (0: no limit; §1 and §5), octave 0 is then
+ * 2H x 2W, each further octave halves both sides rounding down (§3.2), and
+ * octaves are kept while the smaller side is at least min_octave_side.
+ *   *n_octaves, *magnified   outputs (magnified: 1 or 0)
+ *   heights, widths          host arrays: octave o's size for o < min(*n_octaves,
+ *                            cap); either may be NULL when cap is 0
+ * Errors: SIFT_E_INVALID for a null p, n_octaves or magnified, invalid
+ * parameters, H or W below 1, or cap < 0 (or cap > 0 with a NULL array). */
+sift_status sift_octave_geometry(const sift_params *p, int H, int W, int *n_octaves,
+                                 int *magnified, int *heights, int *widths, int cap);
+
 /* Build the Gaussian pyramid of one image (the first stage of sift_extract,
  * same kernels: §3.2's scale space of separable 4-sigma blurs, incremental
  * levels and decimated octaves) and copy it, packed as above, into out_dev

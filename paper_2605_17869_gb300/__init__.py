@@ -22,7 +22,7 @@ __all__ = [
     "SiftError", "SiftParams", "SiftKptsDev", "SiftResult", "Features", "Extractor", "Server",
     "sift_params_default", "sift_create", "sift_destroy", "sift_extract", "sift_extract_batch",
     "sift_extract_noalloc",
-    "sift_last_stats", "sift_pyramid_size", "sift_build_pyramid", "sift_set_profiling",
+    "sift_last_stats", "sift_pyramid_size", "sift_octave_geometry", "sift_build_pyramid", "sift_set_profiling",
     "sift_kernel_times", "sift_last_launch_count", "sift_autotune", "sift_get_tuning", "sift_set_tuning",
     "sift_serve_create", "sift_serve_submit", "sift_serve_poll", "sift_serve_wait",
     "sift_serve_release", "sift_serve_destroy", "sift_last_error", "sift_version",
@@ -155,6 +155,17 @@ def sift_pyramid_size(handle, H: int, W: int):
     _check(_lib().sift_pyramid_size(handle, H, W, byref(no), byref(tot)), handle,
            "sift_pyramid_size")
     return no.value, tot.value
+
+
+def sift_octave_geometry(params, H: int, W: int):
+    """Host-only octave geometry: (n_octaves, magnified, [(H_o, W_o), ...])."""
+    cap = 32
+    no, mag = c_int(), c_int()
+    hs, ws = (c_int * cap)(), (c_int * cap)()
+    _check(_lib().sift_octave_geometry(byref(params), H, W, byref(no), byref(mag), hs, ws, cap),
+           None, "sift_octave_geometry")
+    n = min(no.value, cap)
+    return no.value, bool(mag.value), [(hs[o], ws[o]) for o in range(n)]
 
 
 def sift_build_pyramid(handle, img_ptr: int, H: int, W: int, pitch: int, stream: int,

@@ -61,6 +61,8 @@ SIGNATURES = {
                             c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "sift_last_stats": (c_int, [c_void_p, POINTER(c_int), c_int]),
     "sift_pyramid_size": (c_int, [c_void_p, c_int, c_int, POINTER(c_int), POINTER(c_size_t)]),
+    "sift_octave_geometry": (c_int, [POINTER(SiftParams), c_int, c_int, POINTER(c_int), POINTER(c_int),
+                                     POINTER(c_int), POINTER(c_int), c_int]),
     "sift_build_pyramid": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, c_void_p,
                                    c_size_t]),
     "sift_set_profiling": (c_int, [c_void_p, c_int]),

@@ -240,6 +240,24 @@ sift_status sift_pyramid_size(sift_handle *h, int H, int W, int *n_octaves, size
   return SIFT_OK;
 }
 
+sift_status sift_octave_geometry(const sift_params *p, int H, int W, int *n_octaves,
+                                 int *magnified, int *heights, int *widths, int cap) {
+  if (!p || !n_octaves || !magnified || H < 1 || W < 1 || cap < 0) return SIFT_E_INVALID;
+  if (cap > 0 && (!heights || !widths)) return SIFT_E_INVALID;
+  std::string why;
+  if (sift::validate_params(*p, &why) != SIFT_OK) return SIFT_E_INVALID;
+  const Engine eng(*p);  // geometry only: construction touches no device state
+  int hs[sift::kMaxOct], ws[sift::kMaxOct];
+  const int no = eng.octave_sizes(H, W, hs, ws);
+  for (int o = 0; o < no && o < cap; o++) {
+    heights[o] = hs[o];
+    widths[o] = ws[o];
+  }
+  *n_octaves = no;
+  *magnified = eng.magnify(H, W) ? 1 : 0;
+  return SIFT_OK;
+}
+
 sift_status sift_build_pyramid(sift_handle *h, const float *img_dev, int H, int W,
                                int pitch_elems, void *stream, float *out_dev, size_t out_elems) {
   if (!h || !img_dev || !out_dev) return SIFT_E_INVALID;

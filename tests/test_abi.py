@@ -65,3 +65,54 @@ def test_host_only_calls(lib):
     assert L.sift_create(ctypes.byref(bad), ctypes.byref(h)) == _abi.SIFT_E_INVALID
     assert L.sift_destroy(None) == _abi.SIFT_E_INVALID
     assert L.sift_serve_poll(None, 1, None) == _abi.SIFT_E_INVALID
+
+
+def _params(**kw):
+    from paper_2605_17869_gb300 import _abi
+    p = _abi.SiftParams()
+    _abi.load().sift_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def test_host_octave_geometry_equals_the_oracle():
+    """The library's host-side geometry (magnification decision and octave
+    sizes, which size every launch and buffer) equals the oracle's, exactly,
+    over random and boundary sizes and parameters; no device is needed."""
+    import numpy as np
+    import paper_2605_17869_gb300 as pkg
+    from oracle import sift_oracle as so
+    rng = np.random.default_rng(3)
+    sizes = [(16, 16), (15, 400), (16, 17), (31, 32), (32, 31), (2000, 2000), (2000, 2001),
+             (1, 1), (4000, 1000), (1000, 4000)]
+    sizes += [tuple(int(v) for v in rng.integers(1, 5000, 2)) for _ in range(200)]
+    for up, lim, ms in ((0, 4_000_000, 16), (1, 4_000_000, 16), (1, 0, 16), (1, 150 * 200, 16),
+                        (1, 4_000_000, 40), (0, 4_000_000, 33)):
+        p = _params(upsample=up, upsample_max_px=lim, min_octave_side=ms)
+        op = so.Params(upsample=bool(up), upsample_max_px=lim, min_octave_side=ms)
+        for H, W in sizes + [(150, 200), (150, 201), (4_000_000 // 2000, 2000)]:
+            no, mag, geo = pkg.sift_octave_geometry(p, H, W)
+            want = so.octave_sizes(H, W, op)
+            assert mag == so.magnify(H, W, op), (up, lim, ms, H, W)
+            assert no == len(want) and geo == [tuple(s) for s in want], (up, lim, ms, H, W)
+
+
+def test_host_octave_geometry_argument_errors():
+    from paper_2605_17869_gb300 import _abi
+    L = _abi.load()
+    p = _params()
+    no, mag = ctypes.c_int(), ctypes.c_int()
+    hs = (ctypes.c_int * 4)()
+    ok = L.sift_octave_geometry(ctypes.byref(p), 64, 64, ctypes.byref(no), ctypes.byref(mag), hs, hs, 4)
+    assert ok == 0 and no.value == 3 and mag.value == 0 and hs[2] == 16
+    assert L.sift_octave_geometry(None, 64, 64, ctypes.byref(no), ctypes.byref(mag), hs, hs, 4) \
+        == _abi.SIFT_E_INVALID
+    assert L.sift_octave_geometry(ctypes.byref(p), 0, 64, ctypes.byref(no), ctypes.byref(mag), hs, hs, 4) \
+        == _abi.SIFT_E_INVALID
+    assert L.sift_octave_geometry(ctypes.byref(p), 64, 64, ctypes.byref(no), ctypes.byref(mag), None, None, 4) \
+        == _abi.SIFT_E_INVALID
+    assert L.sift_octave_geometry(ctypes.byref(p), 64, 64, ctypes.byref(no), ctypes.byref(mag), None, None, 0) == 0
+    bad = _params(n_scales=0)
+    assert L.sift_octave_geometry(ctypes.byref(bad), 64, 64, ctypes.byref(no), ctypes.byref(mag), hs, hs, 4) \
+        == _abi.SIFT_E_INVALID
