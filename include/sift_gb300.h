@@ -61,24 +61,28 @@ typedef enum {
  * upsampling (and, when it is switched on, none above 4,000,000 input
  * pixels), octaves while min side >= 16, contrast threshold 0.04/3, edge
  * ratio 10, border 5, 5 refinement iterations, pre-gate 0.5 x threshold,
- * secondary orientation peaks at >= 0.8 of the maximum, no keypoint cap. */
+ * secondary orientation peaks at >= 0.8 of the maximum, capacity and top-K
+ * cap of 8192 keypoints per image. sift_create() and sift_octave_geometry()
+ * reject (SIFT_E_INVALID) values outside the ranges given per field, and a
+ * sigma0 whose largest blur radius (ceil(4 sigma)) exceeds 16 pixels. */
 typedef struct {
   int n_scales;          /* S: scales per octave (2..6) */
-  float sigma0;          /* base scale of each octave */
-  float init_blur;       /* blur already present in the input */
+  float sigma0;          /* base scale of each octave; > 0 */
+  float init_blur;       /* blur already present in the input; >= 0 */
   int upsample;          /* 1: first octave from the 2x bilinear magnified input */
-  int min_octave_side;   /* keep octaves while min(H_o, W_o) >= this (>= 16) */
-  float contrast_thr;    /* |interpolated DoG| must be >= this */
-  float edge_ratio;      /* principal curvature ratio limit r */
-  int border;            /* candidates need b <= x < W-b, b <= y < H-b */
-  int max_refine_iter;   /* refinement iterations (paper: 5) */
-  float prefilter_ratio; /* candidates need |D| > prefilter_ratio * contrast_thr */
-  float ori_peak_ratio;  /* orientation peaks >= ratio * histogram maximum */
+  int min_octave_side;   /* keep octaves while min(H_o, W_o) >= this; >= 16,
+                            above the largest blur radius and 2 x border */
+  float contrast_thr;    /* |interpolated DoG| must be >= this; > 0 */
+  float edge_ratio;      /* principal curvature ratio limit r; > 0 */
+  int border;            /* candidates need b <= x < W-b, b <= y < H-b; >= 1 */
+  int max_refine_iter;   /* refinement iterations (paper: 5); >= 1 */
+  float prefilter_ratio; /* candidates need |D| > prefilter_ratio * contrast_thr; >= 0 */
+  float ori_peak_ratio;  /* orientation peaks >= ratio * histogram maximum; (0, 1] */
   int max_kpts;          /* output capacity and top-K cap (by response); > 0 */
   int upright;           /* 1: orientation fixed to 0, one keypoint per extremum */
   int dsp;               /* 1: DSP-SIFT pooling (§3.2): histograms of 5 relative
                             scales {1/2, 1/sqrt2, 1, sqrt2, 2}, each a 32 x 32
-                            sample patch, pooled before normalisation */
+                            sample patch, pooled before normalisation; 0 or 1 */
   int rootsift;          /* 1: RootSIFT epilogue (L1 normalise, square root, §3.2) */
   int upsample_max_px;   /* with upsample = 1, an image of more than this many
                             input pixels keeps its own resolution as the first

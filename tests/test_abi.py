@@ -116,3 +116,40 @@ def test_host_octave_geometry_argument_errors():
     bad = _params(n_scales=0)
     assert L.sift_octave_geometry(ctypes.byref(bad), 64, 64, ctypes.byref(no), ctypes.byref(mag), hs, hs, 4) \
         == _abi.SIFT_E_INVALID
+
+
+def test_parameter_ranges_are_enforced_as_documented():
+    """Each documented parameter bound, on both sides, through the host-only
+    geometry call (which validates like sift_create, without a device)."""
+    from paper_2605_17869_gb300 import _abi
+    L = _abi.load()
+    no, mag = ctypes.c_int(), ctypes.c_int()
+
+    def status(**kw):
+        p = _params(**kw)
+        return L.sift_octave_geometry(ctypes.byref(p), 64, 64, ctypes.byref(no), ctypes.byref(mag),
+                                      None, None, 0)
+
+    assert status() == 0
+    nan = float("nan")
+    for field, bad, good in (("n_scales", (1, 7), (3, 6)), ("sigma0", (0.0, -1.0, nan, 4.0), (1.0, 1.9)),
+                             ("init_blur", (-0.1, nan), (0.0,)), ("contrast_thr", (0.0, nan), (1e-6,)),
+                             ("edge_ratio", (0.0,), (1.0,)), ("prefilter_ratio", (-1.0, nan), (0.0,)),
+                             ("ori_peak_ratio", (0.0, 1.01, nan), (1.0, 0.5)), ("border", (0,), (1,)),
+                             ("max_refine_iter", (0,), (1,)), ("max_kpts", (0, -5), (1,)),
+                             ("dsp", (2, -1), (0, 1)), ("upsample_max_px", (-1,), (0, 1)),
+                             ("min_octave_side", (15, 0), (16, 64))):
+        for v in bad:
+            assert status(**{field: v}) == _abi.SIFT_E_INVALID, (field, v)
+        for v in good:
+            assert status(**{field: v}) == 0, (field, v)
+    # S = 2 at sigma0 = 1.6: the last level blur, 1.6 sqrt(2^4 - 2^3) = 4.5, needs
+    # radius 19 > 16; at sigma0 = 1 it needs 12.
+    assert status(n_scales=2) == _abi.SIFT_E_INVALID
+    assert status(n_scales=2, sigma0=1.0) == 0
+    # sigma0 = 2: the last level blur 2 sqrt(2^(10/3) - 2^(8/3)) = 3.86 needs radius
+    # 16, so the octave side must exceed 16.
+    assert status(sigma0=2.0) == _abi.SIFT_E_INVALID
+    assert status(sigma0=2.0, min_octave_side=17) == 0
+    assert status(border=8) == _abi.SIFT_E_INVALID               # 16 <= 2 x border
+    assert status(border=8, min_octave_side=17) == 0
