@@ -141,6 +141,8 @@ sift_status sift_extract(sift_handle *h, const float *img_dev, int H, int W, int
  *   imgs_dev[i], H[i], W[i], pitch_elems[i]  host arrays describing image i
  *   out_kpts[i], out_desc[i]                 host arrays of device buffers
  *   out_counts_dev                           device int[n]
+ * A batch of more than 128 images runs as consecutive launches of at most 128
+ * (outputs unchanged); sift_pack_outputs and sift_last_stats then refuse.
  * Errors as sift_extract. */
 sift_status sift_extract_batch(sift_handle *h, int n, const float *const *imgs_dev,
                                const int *H, const int *W, const int *pitch_elems, void *stream,
@@ -189,15 +191,16 @@ sift_status sift_match(sift_handle *h, const float *desc_a, int n_a, const float
                        float ratio, void *stream, int *out_match_a);
 
 /* Pack the outputs of the last extraction call on this handle (at most 128
- * images: a larger batch is run in pieces and only its last piece is packed)
- * into one device block, for a single device-to-host copy. Queue it on the
+ * images; after a larger batch, which runs as several launches, the call is
+ * refused) into one device block, for a single device-to-host copy. Queue it on the
  * extraction's stream, after the extraction and before the next one.
  * Layout, N = the total kept keypoints of the batch, images in batch order:
  * N x 128 float descriptors, then N floats each of x, y, sigma, angle,
  * response, then N int32 each of octave, layer (540 bytes per keypoint; the
  * per-image counts split it). dst_dev: device, 16-byte aligned, at least
  * 540 x images x max_kpts bytes. Asynchronous. Errors: SIFT_E_INVALID for a
- * null or misaligned dst, a short dst or no extraction yet; SIFT_E_CUDA. */
+ * null or misaligned dst, a short dst, no extraction yet, or a last batch of
+ * more than 128 images; SIFT_E_CUDA. */
 sift_status sift_pack_outputs(sift_handle *h, void *stream, void *dst_dev, size_t dst_bytes);
 
 /* GPU MAGSAC++ homography verification (§3.6 "GPU MAGSAC++"): the best of
@@ -236,7 +239,9 @@ sift_status sift_magsac(sift_handle *h, const float *xa, const float *xb, int n,
  *   keypoints, stats[4*i+2] oriented keypoints before the cap,
  *   stats[4*i+3] truncation flags (bit 0 candidate capacity, bit 1 oriented
  *   capacity, bit 2 top-K cap applied).
- * Returns SIFT_W_TRUNCATED if any capacity was exceeded, else SIFT_OK. */
+ * Returns SIFT_W_TRUNCATED if any capacity was exceeded, else SIFT_OK;
+ * SIFT_E_INVALID if the last batch had more than 128 images (it ran as several
+ * launches, and the statistics cover one launch). */
 sift_status sift_last_stats(sift_handle *h, int *stats, int max_images);
 
 /* Pyramid geometry for an H x W input under the handle's parameters:

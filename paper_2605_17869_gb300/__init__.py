@@ -393,7 +393,9 @@ class Extractor:
         (sift_pack_outputs); the counts come back first, then exactly the packed
         bytes. Returns (counts, per-image list of dicts of NumPy arrays x, y,
         sigma, angle, response, octave, layer, desc); the arrays are views of a
-        reused pinned buffer, valid until the next download."""
+        reused pinned buffer, valid until the next download. A batch of more than
+        128 images runs as several launches and cannot be packed (SiftError);
+        read its Features instead."""
         import numpy as np
         torch = _torch()
         n_img = self._last_batch

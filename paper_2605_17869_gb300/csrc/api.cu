@@ -20,6 +20,7 @@ struct sift_handle {
   Engine *eng = nullptr;
   std::string err;
   bool serving = false;
+  bool split_batch = false;  // the last extraction ran as several launches
   void *match_ws = nullptr;  // matcher workspace (stream-ordered allocation)
   size_t match_cap = 0;
   cudaStream_t match_stream = nullptr;
@@ -134,6 +135,8 @@ sift_status sift_pack_outputs(sift_handle *h, void *stream, void *dst_dev, size_
   if (h->serving) return fail(h, SIFT_E_INVALID, "handle is serving");
   if (!h->eng->last_extract || h->eng->last_n < 1 || !h->eng->device_desc())
     return fail(h, SIFT_E_INVALID, "the last call on this handle was not an extraction");
+  if (h->split_batch)
+    return fail(h, SIFT_E_INVALID, "the last batch had more than 128 images and ran as several launches");
   if (reinterpret_cast<uintptr_t>(dst_dev) & 15) return fail(h, SIFT_E_INVALID, "dst must be 16-byte aligned");
   const size_t need = (size_t)h->eng->last_n * h->eng->params().max_kpts *
                       (sift::kDescLen * sizeof(float) + 7 * 4);
@@ -193,6 +196,7 @@ sift_status sift_extract(sift_handle *h, const float *img_dev, int H, int W, int
   if (H < ms || W < ms || pitch_elems < W)
     return fail(h, SIFT_E_INVALID, "image smaller than min_octave_side or pitch < W");
   ImgIn in{img_dev, H, W, pitch_elems, out_kpts, out_desc_dev, out_count_dev};
+  h->split_batch = false;
   return pass(h, h->eng->run(1, &in, (cudaStream_t)stream));
 }
 
@@ -214,6 +218,7 @@ sift_status sift_extract_batch(sift_handle *h, int n, const float *const *imgs_d
       return fail(h, SIFT_E_INVALID, "image " + std::to_string(i) + " smaller than min_octave_side");
     in[i] = ImgIn{imgs_dev[i], H[i], W[i], p, out_kpts[i], out_desc[i], out_counts_dev + i};
   }
+  h->split_batch = n > sift::kMaxImg;
   for (int b0 = 0; b0 < n; b0 += sift::kMaxImg) {
     const int m = std::min(sift::kMaxImg, n - b0);
     const sift_status st = h->eng->run(m, in.data() + b0, (cudaStream_t)stream);
@@ -224,6 +229,8 @@ sift_status sift_extract_batch(sift_handle *h, int n, const float *const *imgs_d
 
 sift_status sift_last_stats(sift_handle *h, int *stats, int max_images) {
   if (!h || !stats || max_images < 1) return SIFT_E_INVALID;
+  if (h->split_batch)
+    return fail(h, SIFT_E_INVALID, "the last batch had more than 128 images and ran as several launches");
   return pass(h, h->eng->last_stats(stats, max_images));
 }
 
@@ -268,6 +275,7 @@ sift_status sift_build_pyramid(sift_handle *h, const float *img_dev, int H, int 
   if (out_elems < need || pitch_elems < W) return fail(h, SIFT_E_INVALID, "output too small");
   ImgIn in{img_dev, H, W, pitch_elems, {}, nullptr, nullptr};
   cudaStream_t s = (cudaStream_t)stream;
+  h->split_batch = false;
   st = h->eng->run_pyramid(in, s);
   if (st != SIFT_OK) return pass(h, st);
   const sift::Desc &hd = h->eng->host_desc();

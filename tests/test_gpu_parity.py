@@ -213,6 +213,30 @@ def test_large_batch_composition_invariance():
     ex.close()
 
 
+def test_batch_of_more_than_one_launch():
+    """130 images: one launch holds at most 128, so the batch runs as two
+    launches. Every image's output still equals its single-image extraction bit
+    for bit, and the calls that describe one launch (the packed download and
+    the per-image statistics) refuse rather than return part of the batch."""
+    shapes = [(16 + (i % 7) * 3, 20 + (i % 5) * 4) for i in range(130)]
+    imgs = [torch.from_numpy(synth.make_image(synth.rng_for(20, i), *s)).cuda()
+            for i, s in enumerate(shapes)]
+    ex = pkg.Extractor(max_kpts=64)
+    single = [_digest(ex.extract(im)) for im in imgs]
+    assert [_digest(f) for f in ex.extract_batch(imgs)] == single
+    with pytest.raises(pkg.SiftError):
+        ex.download()
+    with pytest.raises(pkg.SiftError):
+        pkg.sift_last_stats(ex.handle, 130)
+    feats = ex.extract_batch(imgs[:128])           # one launch again: both work
+    counts, out = ex.download()
+    assert counts == [f.count for f in feats]
+    for f, o in zip(feats, out):
+        np.testing.assert_array_equal(o["desc"], f.desc.cpu().numpy())
+    pkg.sift_last_stats(ex.handle, 128)
+    ex.close()
+
+
 def test_pack_outputs_argument_errors():
     ex = pkg.Extractor(max_kpts=256)
     img = torch.from_numpy(synth.make_image(synth.rng_for(19, 0), 64, 80)).cuda()
