@@ -49,7 +49,9 @@ def test_scale_tolerance(ref, rel, found):
     r, p = ref
     g = _as_gpu(r)
     g["sigma"] = g["sigma"] * (1 + rel)
-    assert compare.match(r, g, params=p).n_found == (len(r) if found else 0)
+    m = compare.match(r, g, params=p)
+    assert m.n_found == (len(r) if found else 0)
+    assert m.n_gpu_unmatched == 0          # every GPU keypoint still sits on an oracle keypoint
 
 
 def test_angle_tolerance_wraps(ref):
@@ -81,13 +83,16 @@ def test_keypoints_near_a_threshold_are_excused(ref):
     g = {k: v[keep] for k, v in g.items()}
     m = compare.match(r, g, params=p)
     assert m.n_found == m.n_eligible - 1
-    saved = r.margin[0]
+    saved = r.margin[:2].copy()
     r.margin[0] = 0.5 * compare.MARGIN_EPS
     try:
         m = compare.match(r, g, params=p)
         assert m.n_eligible == len(r) - 1 and m.n_found == m.n_eligible
+        r.margin[1] = 0.5 * compare.MARGIN_EPS   # excused although present: not counted as found
+        m = compare.match(r, g, params=p)
+        assert m.n_eligible == len(r) - 2 and m.n_found == m.n_eligible
     finally:
-        r.margin[0] = saved
+        r.margin[:2] = saved
 
 
 def test_descriptor_difference_and_angle_propagation(ref):
@@ -112,3 +117,19 @@ def test_descriptor_difference_and_angle_propagation(ref):
     assert m.desc_max_l2_direct > compare.DESC_TOL
     assert m.desc_max_l2 < 1e-12
     assert m.n_angle_propagated >= 1
+
+
+def test_closest_angle_and_worst_case_over_pairs(ref):
+    """Among GPU keypoints at the same place within tolerance, the pair uses the
+    closest angle; the worst-case figures are maxima over all pairs."""
+    r, p = ref
+    g = _as_gpu(r)
+    twin = {k: v.copy() for k, v in g.items()}
+    twin["angle"] = (twin["angle"] + 0.3) % 360.0       # a second orientation, 0.3 degrees off
+    both = {k: np.concatenate([g[k], twin[k]]) for k in g}
+    m = compare.match(r, both, params=p)
+    assert m.n_found == len(r) and m.worst["angle"] == 0.0 and m.desc_max_l2 == 0.0
+    g["x"] = g["x"].copy()
+    g["x"][0] += 0.005                                    # only the first keypoint moves
+    m = compare.match(r, g, params=p)
+    assert m.worst["pos"] == pytest.approx(0.005, rel=1e-6)

@@ -223,6 +223,16 @@ COMPARE_MUTANTS = {
     "compare_propagation_uncounted": ("                    if dd2 <= DESC_TOL:\n                        n_prop += 1",
                                       "                    if True:\n                        n_prop += 0"),
     "compare_no_recompute": ("                    dd = min(dd, dd2)", "                    dd = dd"),
+    "compare_hit_needs_scale": (
+        "        gpu_hit[near] = True\n",
+        "        gpu_hit[near[(np.abs(gsig[near] - osig[i]) / osig[i] < SIGMA_RTOL)]] = True\n"),
+    "compare_counts_excused": ("        if not eligible[i]:\n            continue\n", "\n"),
+    "compare_pair_not_closest_angle": ("            j = ok[np.argmin(angle_diff(gang[ok], oang[i]))]",
+                                       "            j = ok[-1]"),
+    "compare_worst_is_last": (
+        '            worst["pos"] = max(worst["pos"], float(max(abs(gx[j] - ox[i]), abs(gy[j] - oy[i]))))',
+        '            worst["pos"] = float(max(abs(gx[j] - ox[i]), abs(gy[j] - oy[i])))'),
+    "compare_pairs_uncounted": ("                pairs += 1", "                pairs += 0"),
 }
 
 CASES = ([(n, "sift_oracle.py", "test_oracle_pins.py") for n in sorted(MUTANTS)]
