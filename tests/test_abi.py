@@ -76,7 +76,7 @@ def _params(**kw):
     return p
 
 
-def test_host_octave_geometry_equals_the_oracle():
+def test_host_octave_geometry_equals_the_oracle(lib):
     """The library's host-side geometry (magnification decision and octave
     sizes, which size every launch and buffer) equals the oracle's, exactly,
     over random and boundary sizes and parameters; no device is needed."""
@@ -98,7 +98,7 @@ def test_host_octave_geometry_equals_the_oracle():
             assert no == len(want) and geo == [tuple(s) for s in want], (up, lim, ms, H, W)
 
 
-def test_host_octave_geometry_argument_errors():
+def test_host_octave_geometry_argument_errors(lib):
     from paper_2605_17869_gb300 import _abi
     L = _abi.load()
     p = _params()
@@ -118,7 +118,7 @@ def test_host_octave_geometry_argument_errors():
         == _abi.SIFT_E_INVALID
 
 
-def test_parameter_ranges_are_enforced_as_documented():
+def test_parameter_ranges_are_enforced_as_documented(lib):
     """Each documented parameter bound, on both sides, through the host-only
     geometry call (which validates like sift_create, without a device)."""
     from paper_2605_17869_gb300 import _abi
