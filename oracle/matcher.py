@@ -19,7 +19,8 @@ paper is silent (marked READING):
     keeps nothing.
 
 Parity status: match is pinned by tests/test_matcher_oracle.py (brute-force
-loops, planted pairs, symmetry and permutation invariance).
+loops, planted pairs, symmetry and permutation invariance, the default ratio
+and the robustness flags on fp16-exact vectors, single-member sets).
 """
 from __future__ import annotations
 

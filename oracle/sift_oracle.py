@@ -22,12 +22,15 @@ definition reads: no blocking, fusion or reordering beyond it.
 
 Parity status per function:
   gaussian_taps, blur, upsample2x, decimate, build_pyramid, dog,
-  find_candidates, refine_candidate, orientation_peaks, descriptor (plain,
-  DSP and RootSIFT), bilinear, cap_topk, magnify : pinned by
-  tests/test_oracle_pins.py
-  (closed forms, brute force, invariants, rotation / transpose equivariance).
-  extract (end-to-end composition): parity unpinned as an absolute result,
-  since the paper prints no worked example; its parts are pinned above.
+  find_candidates, refine_candidate, orientation_histogram, smooth_histogram,
+  orientation_peaks, descriptor (plain, DSP and RootSIFT), normalise_descriptor,
+  bilinear, cap_topk, magnify, for_image, octave_sizes : pinned by
+  tests/test_oracle_pins.py (closed forms, brute force, invariants, rotation /
+  transpose equivariance, hand-built DoG stacks and histograms), and the pins
+  are themselves checked by planting mistakes (tests/test_oracle_mutations.py).
+  extract (end-to-end composition): its level choice, decision margins, cap,
+  upright mode, output scaling and blob scales are pinned; as an absolute
+  result it is parity unpinned, since the paper prints no worked example.
 """
 from __future__ import annotations
 
