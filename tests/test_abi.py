@@ -153,3 +153,53 @@ def test_parameter_ranges_are_enforced_as_documented(lib):
     assert status(sigma0=2.0, min_octave_side=17) == 0
     assert status(border=8) == _abi.SIFT_E_INVALID               # 16 <= 2 x border
     assert status(border=8, min_octave_side=17) == 0
+
+
+def _prototypes():
+    """name -> parameter count, from the declarations in include/*.h."""
+    out = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"(sift_\w+)\s*\(([^;{]*?)\)\s*;", src, re.S):
+            args = m.group(2).strip()
+            out[m.group(1)] = 0 if args in ("", "void") else args.count(",") + 1
+    return out
+
+
+def test_binding_arity_matches_the_header():
+    from paper_2605_17869_gb300 import _abi
+    protos = _prototypes()
+    assert set(protos) == set(_abi.SIGNATURES)
+    for name, (_, argtypes) in _abi.SIGNATURES.items():
+        assert len(argtypes) == protos[name], name
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """sizeof and every field offset of the ABI structs, as a C compiler lays
+    them out from the header, equal the ctypes mirrors."""
+    import shutil
+    import subprocess
+    from paper_2605_17869_gb300 import _abi
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"sift_params": _abi.SiftParams, "sift_kpts_dev": _abi.SiftKptsDev,
+               "sift_result": _abi.SiftResult}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "sift_gb300.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        a, b, v = line.split()
+        got[(a, b)] = int(v)
+    for cname, cls in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
