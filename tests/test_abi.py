@@ -203,3 +203,37 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(cls), cname
         for f, _ in cls._fields_:
             assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
+
+
+def test_binding_argument_types_match_the_header():
+    """Each parameter's kind: pointers as pointers, and int, size_t, float,
+    double, uint64_t and structs passed by value as exactly those ctypes."""
+    from ctypes import c_char_p, c_double, c_float, c_int, c_size_t, c_uint64, c_void_p
+    from paper_2605_17869_gb300 import _abi
+    scalar = {"int": c_int, "size_t": c_size_t, "float": c_float, "double": c_double,
+              "uint64_t": c_uint64, "sift_kpts_dev": _abi.SiftKptsDev, "sift_status": c_int}
+
+    def is_ptr(t):
+        return t in (c_void_p, c_char_p) or isinstance(t, type) and issubclass(t, ctypes._Pointer)
+
+    seen = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"([\w\s\*]+?)\b(sift_\w+)\s*\(([^;{]*?)\)\s*;", src, re.S):
+            ret, name, args = m.group(1).strip(), m.group(2), m.group(3).strip()
+            seen.add(name)
+            restype, argtypes = _abi.SIGNATURES[name]
+            ret_t = ret.split()[-1] if "*" not in ret else "*"
+            assert (is_ptr(restype) if ret_t == "*" else restype is scalar[ret_t]), name
+            if args in ("", "void"):
+                continue
+            for k, a in enumerate(args.split(",")):
+                a = " ".join(a.split())
+                want_ptr = "*" in a
+                base = re.sub(r"\bconst\b", "", a.replace("*", " ")).split()[0]
+                got = argtypes[k]
+                if want_ptr:
+                    assert is_ptr(got), (name, k, a)
+                else:
+                    assert got is scalar[base], (name, k, a, got)
+    assert seen == set(_abi.SIGNATURES)
