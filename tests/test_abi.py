@@ -237,3 +237,13 @@ def test_binding_argument_types_match_the_header():
                 else:
                     assert got is scalar[base], (name, k, a, got)
     assert seen == set(_abi.SIGNATURES)
+
+
+def test_status_codes_match_the_header():
+    from paper_2605_17869_gb300 import _abi
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "sift_gb300.h")).read(), flags=re.S)
+    codes = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(SIFT_[A-Z_]+)\s*=\s*(-?\d+)", src)}
+    assert len(codes) == 9
+    for name, v in codes.items():
+        assert getattr(_abi, name) == v, name
+        assert _abi.STATUS_NAMES[v] == name
