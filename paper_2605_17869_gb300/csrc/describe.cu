@@ -596,28 +596,22 @@ __global__ void __launch_bounds__(kThreads) k_pack(const Desc *__restrict__ d, f
 }  // namespace
 
 cudaError_t launch_pack(const Desc *d, void *dst, int n_sm, cudaStream_t s) {
-  k_pack<<<n_sm * 4, kThreads, 0, s>>>(d, static_cast<float4 *>(dst));
-  return cudaGetLastError();
+  return launch_plain(k_pack, n_sm * 4, kThreads, 0, s, d, static_cast<float4 *>(dst));
 }
 
 cudaError_t launch_orientation(const Desc *d, int grid, cudaStream_t s) {
-  cudaError_t e = launch_pdl(k_orientation, grid, kKpWarps * 32, 0, s, d);
-  if (e != cudaSuccess) return e;
-  return cudaGetLastError();
+  return launch_pdl(k_orientation, grid, kKpWarps * 32, 0, s, d);
 }
 
 cudaError_t launch_ori_compact(const Desc *d, int grid, cudaStream_t s) {
   cudaError_t e = launch_pdl(k_cc_count, grid, kThreads, 0, s, d);
   if (e == cudaSuccess) e = launch_pdl(k_cc_scan, 1, 512, 0, s, d);
   if (e == cudaSuccess) e = launch_pdl(k_cc_emit, grid, kThreads, 0, s, d);
-  if (e != cudaSuccess) return e;
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_select(const Desc *d, int grid, cudaStream_t s) {
-  cudaError_t e = launch_pdl(k_select, grid, 1024, 0, s, d);
-  if (e != cudaSuccess) return e;
-  return cudaGetLastError();
+  return launch_pdl(k_select, grid, 1024, 0, s, d);
 }
 
 int descriptor_smem_bytes() { return kKpWarps * kDescLen * kDescCols * (int)sizeof(float); }
@@ -628,9 +622,7 @@ cudaError_t descriptor_set_attributes() {
 }
 
 cudaError_t launch_descriptor(const Desc *d, int grid, cudaStream_t s) {
-  cudaError_t e = launch_pdl(k_descriptor, grid, kKpWarps * 32, descriptor_smem_bytes(), s, d);
-  if (e != cudaSuccess) return e;
-  return cudaGetLastError();
+  return launch_pdl(k_descriptor, grid, kKpWarps * 32, descriptor_smem_bytes(), s, d);
 }
 
 }  // namespace sift

@@ -329,8 +329,7 @@ cudaError_t launch_extrema(const Desc *d, int oct, int n_scales, int grid, cudaS
 #define EXT_CASE(SS)                                                               \
   case SS:                                                                         \
     if (pdl) return launch_pdl(k_extrema<SS>, grid, kThreads, 0, s, d, oct);        \
-    k_extrema<SS><<<grid, kThreads, 0, s>>>(d, oct);                               \
-    return cudaGetLastError();
+    return launch_plain(k_extrema<SS>, grid, kThreads, 0, s, d, oct);
   switch (n_scales) {
     EXT_CASE(2)
     EXT_CASE(3)
@@ -346,14 +345,11 @@ cudaError_t launch_bm_compact(const Desc *d, int grid, cudaStream_t s) {
   cudaError_t e = launch_pdl(k_bm_count, grid, kThreads, 0, s, d);
   if (e == cudaSuccess) e = launch_pdl(k_bm_scan, 1, 512, 0, s, d);
   if (e == cudaSuccess) e = launch_pdl(k_bm_emit, grid, kThreads, 0, s, d);
-  if (e != cudaSuccess) return e;
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_refine(const Desc *d, int grid, cudaStream_t s) {
-  cudaError_t e = launch_pdl(k_refine, grid, kThreads, 0, s, d);
-  if (e != cudaSuccess) return e;
-  return cudaGetLastError();
+  return launch_pdl(k_refine, grid, kThreads, 0, s, d);
 }
 
 }  // namespace sift

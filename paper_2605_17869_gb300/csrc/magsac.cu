@@ -387,17 +387,15 @@ cudaError_t launch_magsac(const float *xa, const float *xb, int n, const int *sa
   // The FP64 solver is bound by each SM's FP64 rate: spread the hypotheses over
   // every SM (ceil(n_hyp / SMs) threads per block, at most 32).
   const int fit_threads = std::max(1, std::min(kFitThreads, (n_hyp + n_sm - 1) / n_sm));
-  k_magsac_fit<<<(n_hyp + fit_threads - 1) / fit_threads, fit_threads, 0, s>>>(a, b, n, samples,
-                                                                               n_hyp, models, valid);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_plain(k_magsac_fit, (n_hyp + fit_threads - 1) / fit_threads, fit_threads,
+                               0, s, a, b, n, samples, n_hyp, models, valid);
   if (e != cudaSuccess) return e;
   const int grid = n_hyp < 8 * n_sm ? n_hyp : 8 * n_sm;
-  k_magsac_score<<<grid, kScoreThreads, 0, s>>>(a, b, n, models, valid, n_hyp, c, scores);
-  e = cudaGetLastError();
+  e = launch_plain(k_magsac_score, grid, kScoreThreads, 0, s, a, b, n, models, valid, n_hyp, c,
+                   scores);
   if (e != cudaSuccess) return e;
-  k_magsac_select<<<1, kSelectThreads, 0, s>>>(a, b, n, models, scores, n_hyp, c, H_out, best_out,
-                                               score_out, inliers, scores_out);
-  return cudaGetLastError();
+  return launch_plain(k_magsac_select, 1, kSelectThreads, 0, s, a, b, n, models, scores, n_hyp, c,
+                      H_out, best_out, score_out, inliers, scores_out);
 }
 
 }  // namespace sift

@@ -324,20 +324,27 @@ cudaError_t launch_match(const float *A, int n_a, const float *B, int n_b, float
   cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), s);
   if (e != cudaSuccess || n_a == 0) return e;
   if (n_b > 0) {
-    k_to_core_matrices<<<(int)((pa * 16 + 255) / 256), 256, 0, s>>>(A, n_a, (int)pa, Acm);
-    k_to_core_matrices<<<(int)((pb * 16 + 255) / 256), 256, 0, s>>>(B, n_b, (int)pb, Bcm);
-    k_match_tile<<<dim3((n_a + kMM - 1) / kMM, tb), kMThreads, kSmemA + kSmemB, s>>>(
-        Acm, n_a, Bcm, n_b, (int)pa, pab_best, pab_s1, pab_s2, err);
-    k_match_tile<<<dim3((n_b + kMM - 1) / kMM, ta), kMThreads, kSmemA + kSmemB, s>>>(
-        Bcm, n_b, Acm, n_a, (int)pb, pba_best, pba_s1, pba_s2, err);
-    k_match_merge<<<(n_a + 255) / 256, 256, 0, s>>>(n_a, (int)pa, tb, pab_best, pab_s1, pab_s2,
-                                                    best_a, s1_a, s2_a);
-    k_match_merge<<<(n_b + 255) / 256, 256, 0, s>>>(n_b, (int)pb, ta, pba_best, pba_s1, pba_s2,
-                                                    best_b, s1_b, s2_b);
+    e = launch_plain(k_to_core_matrices, (int)((pa * 16 + 255) / 256), 256, 0, s, A, n_a, (int)pa,
+                     Acm);
+    if (e == cudaSuccess)
+      e = launch_plain(k_to_core_matrices, (int)((pb * 16 + 255) / 256), 256, 0, s, B, n_b,
+                       (int)pb, Bcm);
+    if (e == cudaSuccess)
+      e = launch_plain(k_match_tile, dim3((n_a + kMM - 1) / kMM, tb), kMThreads, kSmemA + kSmemB,
+                       s, Acm, n_a, Bcm, n_b, (int)pa, pab_best, pab_s1, pab_s2, err);
+    if (e == cudaSuccess)
+      e = launch_plain(k_match_tile, dim3((n_b + kMM - 1) / kMM, ta), kMThreads, kSmemA + kSmemB,
+                       s, Bcm, n_b, Acm, n_a, (int)pb, pba_best, pba_s1, pba_s2, err);
+    if (e == cudaSuccess)
+      e = launch_plain(k_match_merge, (n_a + 255) / 256, 256, 0, s, n_a, (int)pa, tb, pab_best,
+                       pab_s1, pab_s2, best_a, s1_a, s2_a);
+    if (e == cudaSuccess)
+      e = launch_plain(k_match_merge, (n_b + 255) / 256, 256, 0, s, n_b, (int)pb, ta, pba_best,
+                       pba_s1, pba_s2, best_b, s1_b, s2_b);
+    if (e != cudaSuccess) return e;
   }
-  k_match_final<<<(n_a + 255) / 256, 256, 0, s>>>(n_a, n_b, ratio, best_a, s1_a, s2_a, best_b,
-                                                  s1_b, s2_b, err, out);
-  return cudaGetLastError();
+  return launch_plain(k_match_final, (n_a + 255) / 256, 256, 0, s, n_a, n_b, ratio, best_a, s1_a,
+                      s2_a, best_b, s1_b, s2_b, err, out);
 }
 
 }  // namespace sift

@@ -65,12 +65,29 @@ __global__ void k_noalloc_setup(Desc *d, SetupArgs a) {
   for (int o = lane; o < a.img.n_oct; o += 32) d->oct[o] = a.oct[o];
 }
 
+// Per-device set-up state. Only a successful set-up is kept: after a failure
+// (for example a call made before the device's context is usable) the next
+// call on that device tries again.
 struct DeviceScratch {
-  std::once_flag once;
-  void *ptr = nullptr;
-  cudaError_t err = cudaSuccess;
+  std::mutex mu;
+  void *ptr = nullptr;  // device address of g_scratch on this device, once set up
 };
 DeviceScratch g_dev[kMaxDevices];
+
+// Resolve the scratch array's device address and set the kernels'
+// shared-memory limits on the current device. Returns the failing call's
+// status, or cudaSuccess.
+cudaError_t setup_device(DeviceScratch &ds) {
+  std::lock_guard<std::mutex> lk(ds.mu);
+  if (ds.ptr) return cudaSuccess;
+  void *ptr = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&ptr, g_scratch);
+  if (e == cudaSuccess) e = blur_set_attributes();
+  if (e == cudaSuccess) e = descriptor_set_attributes();
+  if (e == cudaSuccess) e = extrema_set_attributes();
+  if (e == cudaSuccess && ptr) ds.ptr = ptr;
+  return e == cudaSuccess && !ptr ? cudaErrorInvalidSymbol : e;
+}
 
 std::mutex g_plan_mu;
 Desc g_host_desc;  // host-side planning buffer (static storage, not allocated per call)
@@ -95,17 +112,13 @@ extern "C" sift_status sift_extract_noalloc(const sift_params *p, const float *i
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SIFT_E_CUDA;
   // First call on this device (which must be current): resolve the device
   // address of the scratch array and set the kernels' shared-memory limits.
+  // A failed set-up is not remembered; the next call retries it.
   DeviceScratch &ds = g_dev[dev];
-  std::call_once(ds.once, [&ds] {
-    ds.err = cudaGetSymbolAddress(&ds.ptr, g_scratch);
-    if (ds.err == cudaSuccess) ds.err = blur_set_attributes();
-    if (ds.err == cudaSuccess) ds.err = descriptor_set_attributes();
-    if (ds.err == cudaSuccess) ds.err = extrema_set_attributes();
-  });
-  if (ds.err != cudaSuccess || !ds.ptr) return SIFT_E_CUDA;
+  if (setup_device(ds) != cudaSuccess) return SIFT_E_CUDA;
 
   Engine eng(*p);  // planning and launch sequencing only; it allocates nothing
-  if (eng.init_noalloc() != SIFT_OK) return SIFT_E_CUDA;
+  const sift_status ist = eng.init_noalloc();  // parameters were validated above
+  if (ist != SIFT_OK) return ist;
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
   std::lock_guard<std::mutex> lk(g_plan_mu);
   Desc &hd = g_host_desc;
@@ -145,8 +158,9 @@ extern "C" sift_status sift_extract_noalloc(const sift_params *p, const float *i
   a.cc_n = hd.cc_pre[1];
   a.img = hd.img[0];
   for (int o = 0; o < kMaxOct; o++) a.oct[o] = o < hd.img[0].n_oct ? hd.oct[o] : OctDev{};
-  k_noalloc_setup<<<1, 32, 0, s>>>(d_desc, a);
-  cudaError_t e = cudaGetLastError();
+  // launch_plain reports this launch's own status; an error that an earlier,
+  // unrelated call left in the runtime is not taken for ours.
+  cudaError_t e = launch_plain(k_noalloc_setup, 1, 32, 0, s, d_desc, a);
   if (e == cudaSuccess) e = eng.enqueue_noalloc(d_desc, s, M, base_modes(hd));
   return e == cudaSuccess ? SIFT_OK : SIFT_E_CUDA;
 }

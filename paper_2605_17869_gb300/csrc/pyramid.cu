@@ -691,8 +691,7 @@ cudaError_t launch_level_blur(const Desc *d, int oct, int lvl_out, int R, const 
   // launch that waits for everything before it (a branch after an event wait).
   auto go = [&](auto kern, size_t smem, auto... args) -> cudaError_t {
     if (pdl) return launch_pdl(kern, grid, kThreads, smem, s, d, oct, lvl_out, args...);
-    kern<<<grid, kThreads, smem, s>>>(d, oct, lvl_out, args...);
-    return cudaGetLastError();
+    return launch_plain(kern, grid, kThreads, smem, s, d, oct, lvl_out, args...);
   };
 #define CASE_R(RR)                                                                        \
   case RR:                                                                                \
@@ -713,19 +712,20 @@ cudaError_t launch_level_blur(const Desc *d, int oct, int lvl_out, int R, const 
 cudaError_t launch_base_blur(const Desc *d, int R, const BlurTaps &t, int th_kind, bool upsample,
                              int grid, cudaStream_t s) {
   (void)th_kind;
-#define CASE_R(RR)                                                                            \
-  case RR:                                                                                    \
-    if (upsample) k_base_poly<(RR + 2) / 2><<<grid, kPolyThreads, 0, s>>>(d, make_poly_taps(t, RR)); \
-    else k_blur<RR, 32, 1><<<grid, kThreads, smem_bytes<RR, 32, 1>(), s>>>(d, 0, 0, t);          \
-    break;
+#define CASE_R(RR)                                                                             \
+  case RR:                                                                                     \
+    if (upsample)                                                                              \
+      return launch_plain(k_base_poly<(RR + 2) / 2>, grid, kPolyThreads, 0, s, d,              \
+                          make_poly_taps(t, RR));                                              \
+    return launch_plain(k_blur<RR, 32, 1>, grid, kThreads, smem_bytes<RR, 32, 1>(), s, d, 0, 0, t);
   switch (R) {
     SIFT_FOR_EACH_R(CASE_R)
     default:
-      if (upsample) k_blur_generic<2><<<grid, kThreads, generic_smem_bytes(R), s>>>(d, 0, 0, R, t);
-      else k_blur_generic<1><<<grid, kThreads, generic_smem_bytes(R), s>>>(d, 0, 0, R, t);
+      if (upsample)
+        return launch_plain(k_blur_generic<2>, grid, kThreads, generic_smem_bytes(R), s, d, 0, 0, R, t);
+      return launch_plain(k_blur_generic<1>, grid, kThreads, generic_smem_bytes(R), s, d, 0, 0, R, t);
   }
 #undef CASE_R
-  return cudaGetLastError();
 }
 
 int blur_blocks_per_sm(int R, int th_kind, int mode) {

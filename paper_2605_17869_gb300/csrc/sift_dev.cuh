@@ -148,6 +148,20 @@ inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t
   return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
 }
 
+// A launch without attributes. Like launch_pdl it returns the status of this
+// launch alone: an error an earlier call left in the runtime's last-error
+// state is neither reported as this launch's nor cleared.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_plain(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+
 // Index of the image owning flattened item t, given an exclusive prefix pre[0..n].
 __device__ __forceinline__ int find_owner(const int *pre, int n, int t) {
   int lo = 0, hi = n;

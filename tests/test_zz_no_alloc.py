@@ -4,9 +4,11 @@ The allocation-free variant exists for callers that cannot call cudaMalloc
 (plug-ins whose host framework owns all device memory, real-time loops that
 forbid allocation after start-up). It runs the same kernels on a fixed
 in-library scratch array, so its output must equal sift_extract's bit for bit
-(the tolerance used for GPU-vs-GPU comparisons throughout these tests). Two
-calls in a row on different images also check that nothing left in the shared
-scratch by one call leaks into the next.
+(the tolerance used for GPU-vs-GPU comparisons throughout these tests). Calls
+in a row on different images also check that nothing left in the shared
+scratch by one call leaks into the next: a small image, then a larger one whose
+layout covers everything the first wrote, then the small image again, whose
+layout leaves part of the larger call's contents in place.
 
 This file is collected last on purpose, so that a run stopping at the first
 failure has already run every other test.
@@ -59,6 +61,8 @@ def test_noalloc_matches_extract_two_calls_in_a_row():
     second = _noalloc(imgs[1], params)
     _assert_same(first, refs[0])
     _assert_same(second, refs[1])
+    third = _noalloc(imgs[0], params)   # after the larger image: stale scratch beyond its layout
+    _assert_same(third, refs[0])
     ex.close()
 
 
