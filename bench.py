@@ -1,24 +1,28 @@
 """Benchmark: batched SIFT extraction on GB300 (one JSON line on stdout).
 
-Workload (timed as `value`): a homography-sequence batch, 6 FP32 grayscale
-images of 1000x750 (one seeded base image plus 5 warps by random
-homographies with gain), 2x bilinear upsampled first octave, 8000 keypoints
-cap, extracted in one sift_extract_batch call per step. value = input
-megapixels per second over all ranks. Between timed steps L2 is flushed by
-writing a 256 MB buffer (outside the timed events).
+Workload (timed as `value`): the mixed-resolution batch, 64 FP32 grayscale
+images extracted in one sift_extract_batch call per step; long sides uniform
+in 480-1600 px, aspect ratios 4:3 / 3:4 / 16:9, seeded synthetic content with
+1/f texture, no upsampling, cap 8192 keypoints per image. value = input
+megapixels per second over all ranks. The step's inputs (about 200 MB) and
+its pyramid (about 1.6 GB) are far larger than L2; L2 is also flushed between
+timed steps by writing a 256 MB buffer (outside the timed events).
 
 Also reported: keypoints/s; the same images through the per-image entry
-point and the batched/per-image ratio; the same for a 64-image mixed-size
-batch; serving images/s with p50/p99 latency under Poisson arrivals;
-end-to-end throughput through the public API from pinned host buffers;
-the blur kernel's achieved HBM bandwidth against the measured peak; and the
-FP64 oracle timed on the host cores on a bounded sample.
+point and the batched/per-image ratio; per-class device times with the
+roofline of each class; end-to-end throughput through the public API from
+pinned host buffers; the homography-sequence batch (6 x 1000x750, 2x
+upsampled) with matching accuracy and with DSP pooling + RootSIFT; the
+single-image and image-pair latencies (with the matcher and MAGSAC++);
+serving images/s with p50/p99 latency under Poisson arrivals; and the FP64
+oracle timed on the host cores on a bounded sample.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-serving]
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import multiprocessing as mp
@@ -37,8 +41,15 @@ sys.path.insert(0, ROOT)
 from workloads import matching, synth  # noqa: E402
 
 METRIC = "SIFT Mpix/s and keypoints/s, batched vs per-image; serving p50/p99 latency"
-WORKLOAD = ("homography-sequence batch: 6 x 1000x750 FP32 grayscale (seeded base + 5 "
-            "homography warps), 2x upsampled first octave, cap 8000 keypoints/image")
+N_IMAGES = 64
+WORKLOAD = ("mixed-resolution batch: 64 FP32 grayscale images in one call, long side uniform "
+            "480-1600 px, aspect 4:3/3:4/16:9, seeded synthetic content with 1/f texture, "
+            "no upsampling, cap 8192 keypoints/image")
+HOMOGRAPHY_WORKLOAD = ("homography-sequence batch: 6 x 1000x750 FP32 grayscale (seeded base + 5 "
+                       "homography warps), 2x upsampled first octave, cap 8000 keypoints/image")
+SERVING_RATES = (50, 100, 200, 500, 1000, 2000)
+SERVING_REQUESTS = 1000
+MAX_KPTS = 8192
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -49,6 +60,46 @@ def _peaks():
             d = json.load(f)
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------ inputs
+# Multi-GPU runs are independent replicas: rank r extracts its own batch (the
+# mixed-resolution batch drawn with shape index r and image seeds 100 r + i;
+# rank 0's is the canonical batch); the only communication is a barrier and
+# the max of the timed-region durations.
+
+class Batch:
+    def __init__(self, images):
+        self.images = images
+        self.shapes = [im.shape for im in images]
+
+
+def _mixed_one(args):
+    rank, i, n = args
+    (h, w) = synth.mixed_batch_shapes(n, index=rank)[i]
+    return synth.make_image(synth.rng_for(3, 100 * rank + i), h, w, fractal_std=0.05)
+
+
+def replica_batch(rank, n_images=N_IMAGES, pool=None):
+    """The images rank `rank` processes (distinct per rank)."""
+    jobs = [(rank, i, n_images) for i in range(n_images)]
+    imgs = pool.map(_mixed_one, jobs) if pool is not None else [_mixed_one(j) for j in jobs]
+    return Batch(imgs)
+
+
+def max_over_ranks(x, device):
+    """Max of a per-rank float over the process group (then a barrier)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def whole_job_value(world, mpix_per_rank, steps, max_ms):
+    """Whole-job throughput: the pixels all ranks processed / the slowest rank's time."""
+    return world * mpix_per_rank * steps / (max_ms / 1e3)
 
 
 # ------------------------------------------------------------ oracle (CPU)
@@ -65,15 +116,48 @@ def _oracle_pool(n):
     return mp.get_context("spawn").Pool(n)
 
 
-def cpu_baseline(pool, n_workers, imgs, upsample=True, max_kpts=8000):
+def _oracle_workers():
+    return max(1, min(16, os.cpu_count() or 1))
+
+
+def _center_crop(im, h, w):
+    y0 = (im.shape[0] - h) // 2
+    x0 = (im.shape[1] - w) // 2
+    return np.ascontiguousarray(im[y0:y0 + h, x0:x0 + w])
+
+
+def _oracle_sample(pool, n_workers, images, budget_s):
+    """A bounded sample of the workload for the oracle: the first n_workers
+    images, centre-cropped (same aspect) so that one pass over them takes about
+    budget_s on the pool. Returns (crops, description)."""
+    imgs = images[:n_workers]
+    small = [_center_crop(im, im.shape[0] // 4, im.shape[1] // 4) for im in imgs]
     t0 = time.perf_counter()
-    res = pool.map(_oracle_one, [(im, upsample, max_kpts) for im in imgs])
+    pool.map(_oracle_one, [(im, False, MAX_KPTS) for im in small])  # also warms the workers
+    t_small = max(1e-3, time.perf_counter() - t0)
+    frac = min(1.0, budget_s / (16.0 * t_small))
+    crops = []
+    for im in imgs:
+        h = max(64, min(im.shape[0], int(round(im.shape[0] * math.sqrt(frac)))))
+        w = max(64, min(im.shape[1], int(round(im.shape[1] * math.sqrt(frac)))))
+        crops.append(_center_crop(im, h, w))
+    full = all(c.shape == im.shape for c, im in zip(crops, imgs))
+    what = (f"the first {len(crops)} images of the timed batch "
+            f"({'full size' if full else 'centre crops of ' + f'{100 * frac:.0f}% of the area'}, "
+            f"{sum(c.size for c in crops) / 1e6:.2f} Mpx), no upsampling, cap {MAX_KPTS}, one image "
+            f"per worker process")
+    return crops, what
+
+
+def cpu_baseline(pool, n_workers, images, budget_s=12.0):
+    crops, what = _oracle_sample(pool, n_workers, images, budget_s)
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_one, [(im, False, MAX_KPTS) for im in crops])
     wall = time.perf_counter() - t0
-    mpix = sum(im.size for im in imgs) / 1e6
+    mpix = sum(im.size for im in crops) / 1e6
     return {"value": round(mpix / wall, 4), "unit": "Mpix/s", "cores": n_workers,
             "kind": "oracle", "keypoints_per_s": round(sum(k for _, k in res) / wall, 1),
-            "sample": f"{len(imgs)} images of the timed batch (1000x750, 2x upsampled), "
-                      f"one image per worker process, {wall:.1f} s wall"}
+            "sample": f"{what}; {wall:.1f} s wall"}
 
 
 # ------------------------------------------------------------ clocks
@@ -133,10 +217,15 @@ class Clocks:
                 "samples": len(sm)}
 
 
-# ------------------------------------------------------------ GPU arm
+# ------------------------------------------------------------ algorithmic bytes
 
-def _device_images(imgs, torch):
-    return [torch.from_numpy(np.ascontiguousarray(im)).cuda() for im in imgs]
+def _octaves(h, w, upsample, min_side=16):
+    H, W = (2 * h, 2 * w) if upsample else (h, w)
+    out = []
+    while min(H, W) >= min_side:
+        out.append((H, W))
+        H, W = H // 2, W // 2
+    return out
 
 
 def _alg_blur_bytes(shapes, upsample, S=3, min_side=16):
@@ -149,41 +238,11 @@ def _alg_blur_bytes(shapes, upsample, S=3, min_side=16):
     Returns (bytes, pixels processed), the pixels summed over launches."""
     tot = px_tot = 0
     for (h, w) in shapes:
-        if upsample:
-            h, w = 2 * h, 2 * w
-        o = 0
-        while min(h, w) >= min_side:
-            px = h * w
+        for o, (H, W) in enumerate(_octaves(h, w, upsample, min_side)):
+            px = H * W
             tot += 8 * px * (S + 2) + (4 * px if o > 0 else 0)
             px_tot += px * (S + 2)
-            h, w = h // 2, w // 2
-            o += 1
     return tot, px_tot
-
-
-# ------------------------------------------------------------ replicas
-# Multi-GPU runs are independent replicas: rank r extracts its own batch (the
-# homography sequence with seed index r); the only communication is a barrier
-# and the max of the timed-region durations.
-
-def replica_batch(rank, n_images):
-    """The images rank `rank` processes (distinct per rank)."""
-    return synth.homography_sequence(index=rank, n_warped=n_images - 1)
-
-
-def max_over_ranks(x, device):
-    """Max of a per-rank float over the process group (then a barrier)."""
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    dist.barrier()
-    return float(t.item())
-
-
-def whole_job_value(world, mpix_per_rank, steps, max_ms):
-    """Whole-job throughput: the pixels all ranks processed / the slowest rank's time."""
-    return world * mpix_per_rank * steps / (max_ms / 1e3)
 
 
 def _alg_class_bytes(shapes, upsample, S=3, min_side=16):
@@ -194,12 +253,17 @@ def _alg_class_bytes(shapes, upsample, S=3, min_side=16):
     (S bits per octave pixel)."""
     base = ext = 0
     for (h, w) in shapes:
-        H, W = (2 * h, 2 * w) if upsample else (h, w)
-        base += 4 * h * w + 4 * H * W
-        while min(H, W) >= min_side:
+        octs = _octaves(h, w, upsample, min_side)
+        base += 4 * h * w + 4 * octs[0][0] * octs[0][1]
+        for (H, W) in octs:
             ext += 4 * (S + 3) * H * W + S * H * W // 8
-            H, W = H // 2, W // 2
     return {"base": base, "extrema": ext}
+
+
+# ------------------------------------------------------------ GPU arm
+
+def _device_images(imgs, torch):
+    return [torch.from_numpy(np.ascontiguousarray(im)).cuda() for im in imgs]
 
 
 def timed_steps(torch, fn, steps, warmup, flush, stream):
@@ -221,11 +285,256 @@ def timed_steps(torch, fn, steps, warmup, flush, stream):
     return times, time.perf_counter() - t_wall
 
 
+def profiled_classes(torch, ex, step, flush, reps):
+    """Per-class device time of one step (ms) and launches: a profiled graph
+    with a CUDA event pair around every launch, all launches on one stream."""
+    ex.set_profiling(True)
+    step()
+    torch.cuda.synchronize()
+    acc = {}
+    for _ in range(reps):
+        flush.zero_()
+        step()
+        for k, (ms, n) in ex.kernel_times().items():
+            a = acc.setdefault(k, [0.0, 0])
+            a[0] += ms / reps
+            a[1] = n
+    ex.set_profiling(False)
+    return acc
+
+
+def _traffic_per_launch(px_step, blur_n):
+    """DRAM bytes of an average level-blur launch of this workload: the per-pixel
+    DRAM traffic of a captured level-blur launch (profiles/blur_level_traffic.json)
+    times the pixels an average launch processes; only while pyramid.cu is the
+    source the counters were read from."""
+    tpath = os.path.join(ROOT, "profiles", "blur_level_traffic.json")
+    if not os.path.exists(tpath) or not blur_n:
+        return None
+    with open(tpath) as f:
+        tj = json.load(f)
+    src = open(os.path.join(ROOT, "paper_2605_17869_gb300", "csrc", "pyramid.cu"), "rb").read()
+    if tj.get("pyramid_cu_sha256") != hashlib.sha256(src).hexdigest():
+        return None
+    return int(tj["dram_bytes_per_px"] * px_step / blur_n)
+
+
+def rooflines(acc, shapes, upsample, kpts):
+    peak, peak_kind = _peaks()
+    src = "hbm_gbs, " + ("of measured (MEASURED_PEAKS.json)" if peak_kind == "measured"
+                         else "of fallback")
+    alg_step, px_step = _alg_blur_bytes(shapes, upsample)
+    blur_ms, blur_n = acc["blur"]
+    achieved = alg_step / (blur_ms / 1e3) / 1e9 if blur_ms > 0 else 0.0
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": _traffic_per_launch(px_step, blur_n),
+                "kernel": "k_blur (pyramid level blur; all launches of a step)",
+                "alg_bytes_per_launch": int(alg_step / max(1, blur_n)),
+                "launch_ms_avg": round(blur_ms / max(1, blur_n), 5),
+                "peak_source": src}
+    cls_bytes = _alg_class_bytes(shapes, upsample)
+    cls_bytes["blur"] = alg_step
+    per_class = {}
+    for k in ("blur", "base", "extrema"):
+        ms = acc.get(k, (0.0, 0))[0]
+        if ms > 0:
+            gbs = cls_bytes[k] / (ms / 1e3) / 1e9
+            per_class[k] = {"alg_bytes_per_step": int(cls_bytes[k]), "ms_per_step": round(ms, 4),
+                            "achieved_gbs": round(gbs, 1), "frac_of_measured": round(gbs / peak, 4),
+                            "frac_of_nominal_8tbs": round(gbs / 8000.0, 4)}
+    for k in ("refine", "orientation", "keypoint", "descriptor"):
+        ms = acc.get(k, (0.0, 0))[0]
+        if ms > 0:
+            per_class[k] = {"ms_per_step": round(ms, 4),
+                            "keypoints_per_s": round(kpts / (ms / 1e3), 1)}
+    return roofline, per_class
+
+
+def e2e_throughput(torch, pkg, ex, imgs_np, tuning, steps, warmup, world, ext_kw):
+    """End to end: pinned host images -> device -> extract -> results back in one
+    packed copy. Two handles on two streams take alternate steps: step k + 1's
+    upload and launches are queued before step k's results are read back, so
+    the GPU does not wait for the host. Every step uploads its own inputs and
+    reads back its own results."""
+    host = [torch.from_numpy(np.ascontiguousarray(im)).pin_memory() for im in imgs_np]
+    h2d = sum(h.numel() * 4 for h in host)
+    ex_b = pkg.Extractor(**ext_kw)
+    ex_b.set_tuning(tuning)
+    lanes = [(e, torch.cuda.Stream(), [torch.empty_like(h, device="cuda") for h in host])
+             for e in (ex, ex_b)]
+
+    def submit(lane):
+        e, st, din = lane
+        with torch.cuda.stream(st):
+            for d, h in zip(din, host):
+                d.copy_(h, non_blocking=True)
+        e.extract_batch_async(din, st)
+
+    def collect(lane):
+        e, st, _ = lane
+        counts_h, _ = e.download(st)
+        return 4 * len(counts_h) + 540 * sum(counts_h)
+
+    for it in range(warmup):
+        submit(lanes[it % 2])
+        collect(lanes[it % 2])
+    torch.cuda.synchronize()
+    d2h_bytes = []
+    mpix = sum(im.size for im in imgs_np) / 1e6
+    t0 = time.perf_counter()
+    submit(lanes[0])
+    for it in range(steps):
+        if it + 1 < steps:
+            submit(lanes[(it + 1) % 2])
+        d2h_bytes.append(collect(lanes[it % 2]))
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    ex_b.close()
+    return {"value": round(world * mpix * steps / t_e2e, 3), "unit": "Mpix/s",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(np.mean(d2h_bytes)),
+            "steps": steps,
+            "api": "Extractor.extract_batch_async (sift_extract_batch) from pinned host buffers, "
+                   "results by Extractor.download (sift_pack_outputs + one copy); two handles on "
+                   "two streams take alternate steps (step k+1 queued before step k is read back)"}
+
+
+def gpu_arm(args, rank, world, pool, batch):
+    import torch
+    import paper_2605_17869_gb300 as pkg
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    imgs_np = batch.images
+    shapes = batch.shapes
+    imgs = _device_images(imgs_np, torch)
+    mpix = sum(h * w for h, w in shapes) / 1e6
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    ext_kw = dict(upsample=0, max_kpts=MAX_KPTS)
+    ex = pkg.Extractor(**ext_kw)
+    if args.tuning:
+        ex.set_tuning(args.tuning)
+    else:
+        ex.autotune(max(h for h, _ in shapes), max(w for _, w in shapes))
+    tuning = ex.get_tuning()
+
+    def step():
+        ex.extract_batch_async(imgs, stream)
+
+    if args.minimal:
+        times, _ = timed_steps(torch, step, args.steps, args.warmup, flush, stream)
+        return {"metric": METRIC, "value": round(mpix * args.steps / (sum(times) / 1e3), 2),
+                "unit": "Mpix/s", "mode": "minimal (timed loop only)", "images": len(imgs),
+                "ms_per_step": round(sum(times) / args.steps, 4),
+                "gpu_launches_per_step": ex.launch_count(), "tuning": tuning}
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    clocks = Clocks(dev)
+    clocks.start()
+    times, wall = timed_steps(torch, step, args.steps, args.warmup, flush, stream)
+    clock_info = clocks.stop()
+    counts = ex._counts[:len(imgs)].tolist()
+    kpts = sum(counts)
+    launches_per_step = ex.launch_count()
+    total_ms = sum(times)
+    if world > 1:
+        total_ms = max_over_ranks(total_ms, "cuda")
+    value = whole_job_value(world, mpix, args.steps, total_ms)
+
+    # Per-image path on the same images.
+    def step_single():
+        for im in imgs:
+            ex.extract_async(im, stream)
+    t_single, _ = timed_steps(torch, step_single, max(3, args.steps // 4), 2, flush, stream)
+    per_image = mpix * len(t_single) / (sum(t_single) / 1e3)
+
+    reps = max(3, args.steps // 4)
+    acc = profiled_classes(torch, ex, step, flush, reps)
+    roofline, per_class = rooflines(acc, shapes, False, kpts)
+    e2e = e2e_throughput(torch, pkg, ex, imgs_np, tuning, max(3, args.steps // 2), args.warmup,
+                         world, ext_kw)
+
+    extra = {}
+    if rank == 0 and not args.no_configs:
+        extra["homography_sequence"] = homography_side(torch, pkg, flush, stream, tuning,
+                                                       max(10, args.steps // 2))
+        extra["single_and_pair"] = other_configs(torch, pkg, flush, stream, tuning)
+    if rank == 0 and not args.no_serving:
+        extra["serving"] = serving_bench(torch, pkg, SERVING_RATES, args.serving_requests)
+
+    res = {
+        "metric": METRIC, "value": round(value, 2), "unit": "Mpix/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "images_per_step_per_gpu": len(imgs),
+                   "input_mpix_per_step_per_gpu": round(mpix, 3),
+                   "l2": "inputs and pyramid larger than L2; also flushed between timed steps "
+                         "(256 MB write)",
+                   "parallelism": f"replicas x{world} (independent images per rank)",
+                   "tuning": tuning},
+        "keypoints_per_s": round(world * kpts * args.steps / (total_ms / 1e3), 1),
+        "keypoints_per_step_per_gpu": kpts,
+        "per_image_mpix_s": round(per_image, 2),
+        "batched_vs_per_image": round(value / world / per_image, 3),
+        "wall_s_timed_region": round(wall, 3),
+        "gpu_launches": launches_per_step * args.steps,
+        "gpu_launches_per_step": launches_per_step,
+        "kernel_ms_per_step": {k: round(v[0], 4) for k, v in acc.items()},
+        "roofline": roofline,
+        "per_class_roofline": per_class,
+        "e2e": e2e,
+        "clocks": clock_info,
+        **extra,
+    }
+    return res
+
+
+def homography_side(torch, pkg, flush, stream, tuning, steps):
+    """The homography-sequence batch (6 x 1000x750, 2x upsampled, cap 8000):
+    throughput, per-class time, matching accuracy against the known
+    homographies, and the same batch with DSP pooling + RootSIFT (§3.2)."""
+    seq = synth.homography_sequence(index=0)
+    imgs = _device_images(seq.images, torch)
+    mpix = sum(im.size for im in seq.images) / 1e6
+    out = {"workload": HOMOGRAPHY_WORKLOAD}
+    for label, kw in (("plain", {}), ("dsp_rootsift", {"dsp": 1, "rootsift": 1})):
+        ex = pkg.Extractor(upsample=1, max_kpts=8000, **kw)
+        ex.set_tuning(tuning)
+        step = lambda: ex.extract_batch_async(imgs, stream)  # noqa: E731
+        t, _ = timed_steps(torch, step, steps, 3, flush, stream)
+        counts = ex._counts[:len(imgs)].tolist()
+        feats = [ex._bufs[i].view(counts[i]) for i in range(len(imgs))]
+        acc = matching.sequence_mma(feats, seq.homographies)
+        cls = profiled_classes(torch, ex, step, flush, 3)
+        r = {"ms_per_step": round(statistics.mean(t), 4),
+             "mpix_s": round(mpix * len(t) / (sum(t) / 1e3), 1),
+             "keypoints_per_s": round(sum(counts) * len(t) / (sum(t) / 1e3), 1),
+             "kernel_ms_per_step": {k: round(v[0], 4) for k, v in cls.items()},
+             "matches": acc["matches"], **{k: v for k, v in acc.items() if k.startswith("mma@")}}
+        if label == "plain":
+            def single():
+                for im in imgs:
+                    ex.extract_async(im, stream)
+            ts, _ = timed_steps(torch, single, max(3, steps // 2), 2, flush, stream)
+            r["per_image_mpix_s"] = round(mpix * len(ts) / (sum(ts) / 1e3), 1)
+            r["accuracy"] = {"what": "image 0 matched to each warped image; MMA against the known "
+                                     "homographies (harness: torch mutual NN + ratio 0.8)", **acc}
+        out[label] = r
+        ex.close()
+    return out
+
+
 def serving_bench(torch, pkg, rates, n_req, budget=8 << 30):
+    """Poisson arrivals at each rate: submit on arrival, collect every result,
+    report images/s and p50 / p99 latency (from submission to completion)."""
     pool = {}
     for (h, w) in ((480, 640), (1080, 1920), (2160, 3840)):
         pool[(h, w)] = [torch.from_numpy(synth.serving_image(h, w, i)).cuda() for i in range(2)]
-    ex = pkg.Extractor(max_kpts=8192)
+    ex = pkg.Extractor(max_kpts=MAX_KPTS)
     srv = pkg.Server(ex, budget_bytes=budget, max_slots=256)
     # warm-up: one of each size
     for k in pool:
@@ -260,265 +569,6 @@ def serving_bench(torch, pkg, rates, n_req, budget=8 << 30):
     return {"workload": "Poisson arrivals, 640x480 (50%) / 1920x1080 (35%) / 3840x2160 (15%), "
                         "8 GB device-memory budget, no upsampling, cap 8192",
             "points": out}
-
-
-def gpu_arm(args, rank, world, pool, n_workers):
-    import torch
-    import paper_2605_17869_gb300 as pkg
-
-    dev = int(os.environ.get("LOCAL_RANK", 0))
-    torch.cuda.set_device(dev)
-    stream = torch.cuda.current_stream()
-    seq = replica_batch(rank, args.images)
-    imgs_np = seq.images
-    shapes = [im.shape for im in imgs_np]
-    imgs = _device_images(imgs_np, torch)
-    mpix = sum(h * w for h, w in shapes) / 1e6
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-
-    ex = pkg.Extractor(upsample=1, max_kpts=8000)
-    if args.tuning:
-        ex.set_tuning(args.tuning)
-        tuning = ex.get_tuning()
-    else:
-        tuning = ex.autotune(1500, 2000)
-
-    if args.minimal:
-        def step_min():
-            ex.extract_batch_async(imgs, stream)
-        times, _ = timed_steps(torch, step_min, args.steps, args.warmup, flush, stream)
-        return {"metric": METRIC, "value": round(mpix * args.steps / (sum(times) / 1e3), 2),
-                "unit": "Mpix/s", "mode": "minimal (timed loop only)", "images": len(imgs),
-                "ms_per_step": round(sum(times) / args.steps, 4),
-                "gpu_launches_per_step": ex.launch_count(), "tuning": tuning}, imgs_np
-
-    def step():
-        ex.extract_batch_async(imgs, stream)
-
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-    clocks = Clocks(dev)
-    clocks.start()
-    times, wall = timed_steps(torch, step, args.steps, args.warmup, flush, stream)
-    clock_info = clocks.stop()
-    counts = ex._counts[:len(imgs)].tolist()
-    kpts = sum(counts)
-    accuracy = None
-    if rank == 0:
-        feats = [ex._bufs[i].view(counts[i]) for i in range(len(imgs))]
-        accuracy = {"what": "image 0 matched to each warped image of the timed batch; MMA against "
-                            "the known homographies (harness: torch mutual NN + ratio 0.8)",
-                    **matching.sequence_mma(feats, seq.homographies)}
-    launches_per_step = ex.launch_count()
-    total_ms = sum(times)
-    if world > 1:
-        total_ms = max_over_ranks(total_ms, "cuda")
-    value = whole_job_value(world, mpix, args.steps, total_ms)
-
-    # Per-image path on the same images.
-    def step_single():
-        for im in imgs:
-            ex.extract_async(im, stream)
-    t_single, _ = timed_steps(torch, step_single, max(3, args.steps // 2), 2, flush, stream)
-    per_image = mpix * len(t_single) / (sum(t_single) / 1e3)
-
-    # Per-kernel device times (profiled graph: an event pair around every launch).
-    ex.set_profiling(True)
-    step()
-    torch.cuda.synchronize()
-    acc = {}
-    reps = max(3, args.steps // 2)
-    for _ in range(reps):
-        flush.zero_()
-        step()
-        for k, (ms, n) in ex.kernel_times().items():
-            a = acc.setdefault(k, [0.0, 0])
-            a[0] += ms
-            a[1] += n
-    ex.set_profiling(False)
-    blur_ms, blur_n = acc["blur"]
-    alg_step, px_step = _alg_blur_bytes(shapes, True)
-    alg_total = alg_step * reps
-    peak, peak_kind = _peaks()
-    achieved = alg_total / (blur_ms / 1e3) / 1e9 if blur_ms > 0 else 0.0
-    kernel_share = {k: round(v[0] / reps, 4) for k, v in acc.items()}
-    # DRAM bytes per launch: the per-pixel DRAM traffic of a captured level-blur
-    # launch (a 12-image batch whose levels exceed L2) times the pixels an
-    # average launch of this workload processes; taken only while the kernel
-    # source is the one the counters were read from.
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "blur_level_traffic.json")
-    if os.path.exists(tpath):
-        with open(tpath) as f:
-            tj = json.load(f)
-        import hashlib
-        src = open(os.path.join(ROOT, "paper_2605_17869_gb300", "csrc", "pyramid.cu"), "rb").read()
-        if tj.get("pyramid_cu_sha256") == hashlib.sha256(src).hexdigest() and blur_n:
-            traffic = int(tj["dram_bytes_per_px"] * px_step * reps / blur_n)
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic,
-                "kernel": "k_blur (pyramid level blur)",
-                "alg_bytes_per_launch": int(alg_total / max(1, blur_n)),
-                "launch_ms_avg": round(blur_ms / max(1, blur_n), 5),
-                "peak_source": "hbm_gbs, " + ("of measured (MEASURED_PEAKS.json)"
-                                              if peak_kind == "measured" else "of fallback")}
-
-    # Per-class rooflines (CUDA-event time of each class inside the graph).
-    cls_bytes = _alg_class_bytes(shapes, True)
-    cls_bytes["blur"] = alg_step
-    nominal = 8000.0
-    per_class = {}
-    for k in ("blur", "base", "extrema"):
-        ms = acc.get(k, (0.0, 0))[0] / reps
-        if ms > 0:
-            gbs = cls_bytes[k] / (ms / 1e3) / 1e9
-            per_class[k] = {"alg_bytes_per_step": int(cls_bytes[k]), "ms_per_step": round(ms, 4),
-                            "achieved_gbs": round(gbs, 1), "frac_of_measured": round(gbs / peak, 4),
-                            "frac_of_nominal_8tbs": round(gbs / nominal, 4)}
-    for k in ("keypoint", "descriptor"):
-        ms = acc.get(k, (0.0, 0))[0] / reps
-        if ms > 0:
-            per_class[k] = {"ms_per_step": round(ms, 4),
-                            "keypoints_per_s": round(kpts / (ms / 1e3), 1)}
-
-    # End to end: pinned host images -> device -> extract -> results back in one packed copy.
-    # Two handles on two streams take alternate steps: step k + 1's upload and launches are
-    # queued before step k's results are read back, so the GPU does not wait for the host.
-    # Every step still uploads its own inputs and reads back its own results. No L2 flush:
-    # a step's working set (its pyramid, ~0.6 GB) is far larger than L2.
-    host = [torch.from_numpy(np.ascontiguousarray(im)).pin_memory() for im in imgs_np]
-    h2d = sum(h.numel() * 4 for h in host)
-    ex_b = pkg.Extractor(upsample=1, max_kpts=8000)
-    ex_b.set_tuning(json.dumps(tuning) if isinstance(tuning, dict) else tuning)
-    lanes = [(e, torch.cuda.Stream(), [torch.empty_like(h, device="cuda") for h in host])
-             for e in (ex, ex_b)]
-
-    def submit(lane):
-        e, st, din = lane
-        with torch.cuda.stream(st):
-            for d, h in zip(din, host):
-                d.copy_(h, non_blocking=True)
-        e.extract_batch_async(din, st)
-
-    def collect(lane):
-        e, st, _ = lane
-        counts_h, _ = e.download(st)
-        return 4 * len(counts_h) + 540 * sum(counts_h)
-
-    for it in range(args.warmup):
-        submit(lanes[it % 2])
-        collect(lanes[it % 2])
-    torch.cuda.synchronize()
-    n_e2e = max(3, args.steps // 2)
-    d2h_bytes = []
-    t0 = time.perf_counter()
-    submit(lanes[0])
-    for it in range(n_e2e):
-        if it + 1 < n_e2e:
-            submit(lanes[(it + 1) % 2])
-        d2h_bytes.append(collect(lanes[it % 2]))
-    torch.cuda.synchronize()
-    t_e2e = time.perf_counter() - t0
-    ex_b.close()
-    e2e = {"value": round(world * mpix * n_e2e / t_e2e, 3), "unit": "Mpix/s",
-           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(np.mean(d2h_bytes)),
-           "steps": n_e2e,
-           "api": "Extractor.extract_batch_async (sift_extract_batch) from pinned host buffers, "
-                  "results by Extractor.download (sift_pack_outputs + one copy); two handles on "
-                  "two streams take alternate steps (step k+1 queued before step k is read back)"}
-
-    # Mixed-size 64-image batch (batching workload): batched vs per-image.
-    mixed = None
-    if rank == 0 and not args.no_mixed:
-        mimgs_np = pool.map(_mixed_one, list(range(64))) if pool else [
-            _mixed_one(i) for i in range(64)]
-        mimgs = _device_images(mimgs_np, torch)
-        mmpix = sum(im.size for im in mimgs_np) / 1e6
-        exm = pkg.Extractor(max_kpts=8192)
-        exm.set_tuning(tuning)
-        tb, _ = timed_steps(torch, lambda: exm.extract_batch_async(mimgs, stream), 5, 2, flush,
-                            stream)
-        mcounts = exm._counts[:64].tolist()
-
-        def single_all():
-            for im in mimgs:
-                exm.extract_async(im, stream)
-        ts, _ = timed_steps(torch, single_all, 3, 1, flush, stream)
-        mixed = {"workload": "64 mixed-size images, long side 480-1600, aspect 4:3/3:4/16:9, "
-                             "1/f texture, no upsampling, cap 8192",
-                 "batched_mpix_s": round(mmpix * len(tb) / (sum(tb) / 1e3), 1),
-                 "per_image_mpix_s": round(mmpix * len(ts) / (sum(ts) / 1e3), 1),
-                 "keypoints_per_s": round(sum(mcounts) * len(tb) / (sum(tb) / 1e3), 1),
-                 "ms_per_batch": round(statistics.mean(tb), 3)}
-        mixed["batched_vs_per_image"] = round(mixed["batched_mpix_s"] / mixed["per_image_mpix_s"], 2)
-        exm.close()
-
-    configs = None
-    if rank == 0 and not args.no_configs:
-        configs = other_configs(torch, pkg, flush, stream, tuning)
-        configs["dsp_rootsift"] = dsp_variant(torch, pkg, imgs, mpix, flush, stream, tuning,
-                                              seq, max(10, args.steps // 4))
-
-    serving = None
-    if rank == 0 and not args.no_serving:
-        serving = serving_bench(torch, pkg, (50, 200, 1000, 2000), 200)
-
-    res = {
-        "metric": METRIC, "value": round(value, 2), "unit": "Mpix/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "images_per_step_per_gpu": len(imgs),
-                   "input_mpix_per_step_per_gpu": round(mpix, 3),
-                   "l2": "flushed between timed steps (256 MB write)",
-                   "parallelism": f"replicas x{world} (independent images per rank)",
-                   "tuning": tuning},
-        "keypoints_per_s": round(world * kpts * args.steps / (total_ms / 1e3), 1),
-        "keypoints_per_step_per_gpu": kpts,
-        "per_image_mpix_s": round(per_image, 2),
-        "batched_vs_per_image": round(value / world / per_image, 3),
-        "wall_s_timed_region": round(wall, 3),
-        "gpu_launches": launches_per_step * args.steps,
-        "gpu_launches_per_step": launches_per_step,
-        "kernel_ms_per_step": kernel_share,
-        "roofline": roofline,
-        "per_class_roofline": per_class,
-        "e2e": e2e,
-        "clocks": clock_info,
-        "accuracy": accuracy,
-        "mixed_batch": mixed,
-        "single_and_pair": configs,
-        "serving": serving,
-    }
-    return res, imgs_np
-
-
-def dsp_variant(torch, pkg, imgs, mpix, flush, stream, tuning, seq, steps):
-    """The timed batch again with DSP pooling and RootSIFT (§3.2): throughput,
-    per-class device time and matching accuracy."""
-    ex = pkg.Extractor(upsample=1, max_kpts=8000, dsp=1, rootsift=1)
-    ex.set_tuning(tuning)
-    t, _ = timed_steps(torch, lambda: ex.extract_batch_async(imgs, stream), steps, 3, flush, stream)
-    counts = ex._counts[:len(imgs)].tolist()
-    feats = [ex._bufs[i].view(counts[i]) for i in range(len(imgs))]
-    acc = matching.sequence_mma(feats, seq.homographies)
-    ex.set_profiling(True)
-    ex.extract_batch_async(imgs, stream)
-    torch.cuda.synchronize()
-    acc_t = {}
-    for _ in range(3):
-        flush.zero_()
-        ex.extract_batch_async(imgs, stream)
-        for k, (ms, n) in ex.kernel_times().items():
-            acc_t[k] = acc_t.get(k, 0.0) + ms / 3
-    ex.close()
-    return {"workload": "the timed batch with dsp=1, rootsift=1",
-            "ms_per_step": round(statistics.mean(t), 4),
-            "mpix_s": round(mpix * len(t) / (sum(t) / 1e3), 1),
-            "keypoints_per_s": round(sum(counts) * len(t) / (sum(t) / 1e3), 1),
-            "kernel_ms_per_step": {k: round(v, 4) for k, v in acc_t.items()},
-            "matches": acc["matches"], **{k: v for k, v in acc.items() if k.startswith("mma@")}}
 
 
 def other_configs(torch, pkg, flush, stream, tuning):
@@ -583,51 +633,27 @@ def other_configs(torch, pkg, flush, stream, tuning):
     return out
 
 
-def _mixed_one(i):
-    (h, w) = synth.mixed_batch_shapes(64)[i]
-    return synth.make_image(synth.rng_for(3, i), h, w, fractal_std=0.05)
-
-
 # ------------------------------------------------------------ reference arm
 
-def _center_crop(im, h, w):
-    y0 = (im.shape[0] - h) // 2
-    x0 = (im.shape[1] - w) // 2
-    return np.ascontiguousarray(im[y0:y0 + h, x0:x0 + w])
-
-
-def reference_arm(args, pool, n_workers, budget_s=110.0):
-    """The FP64 oracle timed on the host cores. Each step runs the 6 images of
-    the batch (one per worker process), centre-cropped so that the warm-up and
-    the K timed steps take about budget_s in total (full images when K is
-    small); the crop is stated in the output."""
-    seq = synth.homography_sequence(index=0)
-    full = seq.images
-    H, W = full[0].shape
-    # Calibrate on a 1/9-area crop (also warms up the workers).
-    ch, cw = H // 3, W // 3
-    t0 = time.perf_counter()
-    pool.map(_oracle_one, [(_center_crop(im, ch, cw), True, 8000) for im in full[:n_workers]])
-    t_cal = time.perf_counter() - t0
+def reference_arm(args, pool, n_workers, batch, budget_s=110.0):
+    """The FP64 oracle timed on the host cores, on the timed workload's images:
+    each step runs the first n_workers images of the batch (one per worker
+    process), centre-cropped so that the warm-up and the K timed steps take
+    about budget_s in total; the sample is stated in the output."""
     per_step = budget_s / (args.steps + args.warmup)
-    frac = min(1.0, per_step / max(1e-6, 9.0 * t_cal))
-    h = max(64, min(H, int(round(H * math.sqrt(frac)))))
-    w = max(64, min(W, int(round(W * math.sqrt(frac)))))
-    imgs = [_center_crop(im, h, w) for im in full]
-    mpix = sum(im.size for im in imgs) / 1e6
+    crops, what = _oracle_sample(pool, n_workers, batch.images, per_step)
+    mpix = sum(im.size for im in crops) / 1e6
+    jobs = [(im, False, MAX_KPTS) for im in crops]
     for _ in range(args.warmup):
-        pool.map(_oracle_one, [(im, True, 8000) for im in imgs[:n_workers]])
+        pool.map(_oracle_one, jobs)
     times, kp = [], 0
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        r = pool.map(_oracle_one, [(im, True, 8000) for im in imgs])
+        r = pool.map(_oracle_one, jobs)
         times.append(time.perf_counter() - t0)
         kp += sum(k for _, k in r)
     total = sum(times)
     value = mpix * args.steps / total
-    crop = "full 1000x750 images" if (h, w) == (H, W) else f"centre {w}x{h} crops"
-    sample = (f"each step: the {len(imgs)} images of the timed batch ({crop}, 2x upsampled) "
-              f"through the FP64 oracle, one image per worker process ({n_workers} workers)")
     return {"metric": METRIC, "value": round(value, 4), "unit": "Mpix/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1e3 * total / args.steps, 1), "higher_is_better": True,
@@ -635,7 +661,7 @@ def reference_arm(args, pool, n_workers, budget_s=110.0):
             "impl": "reference", "config": {"workload": WORKLOAD},
             "keypoints_per_s": round(kp / total, 1),
             "cpu_baseline": {"value": round(value, 4), "unit": "Mpix/s", "cores": n_workers,
-                             "kind": "oracle", "sample": sample},
+                             "kind": "oracle", "sample": "each step: " + what},
             "e2e": {"value": round(value, 4), "unit": "Mpix/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
@@ -649,16 +675,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-configs", action="store_true",
-                    help="skip the single-image and image-pair latency runs")
+                    help="skip the homography-sequence, single-image and image-pair runs")
     ap.add_argument("--minimal", action="store_true",
                     help="only the timed batch loop (for profiler launch lists)")
     ap.add_argument("--pair-only", action="store_true",
                     help="only the single-image and wide-baseline pair runs (extraction, "
                          "matcher, MAGSAC++), e.g. for profiling those kernels")
-    ap.add_argument("--images", type=int, default=6, help="images per batch (default 6)")
+    ap.add_argument("--images", type=int, default=N_IMAGES,
+                    help=f"images per batch (default {N_IMAGES}; the first n of the batch)")
+    ap.add_argument("--serving-requests", type=int, default=SERVING_REQUESTS)
     ap.add_argument("--tuning", default="", help='fixed tiles, e.g. {"blur_tile_rows": [32,...]}')
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -668,9 +695,10 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        n_workers = min(6, os.cpu_count() or 1)
+        n_workers = _oracle_workers()
         with _oracle_pool(n_workers) as pool:
-            print(json.dumps(reference_arm(args, pool, n_workers)))
+            batch = replica_batch(0, args.images, pool)
+            print(json.dumps(reference_arm(args, pool, n_workers, batch)))
         return
 
     if args.pair_only:
@@ -682,23 +710,24 @@ def main():
         print(json.dumps({"single_and_pair": other_configs(torch, pkg, flush, stream, tuning)}))
         return
 
-    # The oracle's worker pool is started (spawn) before any GPU call.
-    n_workers = min(6, os.cpu_count() or 1)
-    pool = _oracle_pool(n_workers) if rank == 0 and not args.minimal else None
+    # The worker pool is started (spawn) before any GPU call; it generates the
+    # inputs and later runs the oracle for the CPU baseline.
+    n_workers = _oracle_workers()
+    pool = _oracle_pool(n_workers)
     if world > 1:
         import torch
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         dist.init_process_group("nccl")
     try:
-        res, imgs_np = gpu_arm(args, rank, world, pool, n_workers)
+        batch = replica_batch(rank, args.images, pool)
+        res = gpu_arm(args, rank, world, pool, batch)
         if rank == 0:
             if not args.no_cpu_baseline and not args.minimal:
-                res["cpu_baseline"] = cpu_baseline(pool, n_workers, imgs_np)
+                res["cpu_baseline"] = cpu_baseline(pool, n_workers, batch.images)
             print(json.dumps(res))
     finally:
-        if pool is not None:
-            pool.close()
+        pool.close()
         if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()

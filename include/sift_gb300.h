@@ -275,8 +275,10 @@ sift_status sift_build_pyramid(sift_handle *h, const float *img_dev, int H, int 
  * last extraction, the summed device time in milliseconds and the launch count
  * of each kernel class:
  *   0 blur levels, 1 base level (blur of the input / magnified input),
- *   2 DoG extrema scan, 3 decimation, 4 keypoint stages (compaction,
- *   refinement, orientation, cap), 5 descriptor.
+ *   2 DoG extrema scan, 3 decimation (no separate launch: it is fused into
+ *   the first level blur of each octave), 4 candidate and keypoint
+ *   compaction and the top-K cap, 5 descriptor, 6 refinement,
+ *   7 orientation. Classes at or above n_classes are left out.
  * Reading synchronises the handle's last run. */
 sift_status sift_set_profiling(sift_handle *h, int enable);
 sift_status sift_kernel_times(sift_handle *h, double *ms, int *launches, int n_classes);

@@ -22,8 +22,9 @@ definition reads: no blocking, fusion or reordering beyond it.
 
 Parity status per function:
   gaussian_taps, blur, upsample2x, decimate, build_pyramid, dog,
-  find_candidates, refine_candidate, orientation_histogram, smooth_histogram,
-  orientation_peaks, descriptor (plain, DSP and RootSIFT), normalise_descriptor,
+  find_candidates, refine_candidate, orientation_histogram,
+  orientation_vote_margin, smooth_histogram, orientation_peaks,
+  descriptor (plain, DSP and RootSIFT), normalise_descriptor,
   bilinear, cap_topk, magnify, for_image, octave_sizes : pinned by
   tests/test_oracle_pins.py (closed forms, brute force, invariants, rotation /
   transpose equivariance, hand-built DoG stacks and histograms), and the pins
@@ -403,6 +404,36 @@ def orientation_histogram(L: np.ndarray, xi: int, yi: int, sigma_oct: float, p: 
     return np.bincount(bins, weights=wt * mag, minlength=n)
 
 
+def orientation_vote_margin(L: np.ndarray, xi: int, yi: int, sigma_oct: float, p: Params) -> float:
+    """Decision margin of the nearest-bin votes of orientation_histogram (§3.2's
+    36-bin histogram): over the same window and samples, the smallest distance,
+    in bins, of a voting sample's bin coordinate n * theta / 2 pi from a
+    rounding boundary k + 1/2 (where the nearest bin changes). Samples of zero
+    weight do not vote. A vote within FP32 rounding of a boundary may land in
+    the neighbouring bin on the FP32 path; keypoints with a small margin are
+    the ones whose histogram is not a robust function of the image.
+    """
+    h, w = L.shape
+    n = p.ori_bins
+    sw = p.ori_sigma_factor * sigma_oct
+    R = _round_pos(p.ori_radius_factor * sw)
+    j, i = np.meshgrid(np.arange(-R, R + 1), np.arange(-R, R + 1), indexing="ij")
+    ys, xs = yi + j, xi + i
+    ok = (xs >= 1) & (xs <= w - 2) & (ys >= 1) & (ys <= h - 2)
+    ys, xs, i, j = ys[ok], xs[ok], i[ok], j[ok]
+    dx, dy = _gradients(L, ys, xs)
+    mag = np.sqrt(dx * dx + dy * dy)
+    th = np.arctan2(dy, dx)
+    th = np.where(th < 0, th + 2 * math.pi, th)
+    wt = np.exp(-(i * i + j * j) / (2.0 * sw * sw))
+    votes = wt * mag > 0
+    if not votes.any():
+        return math.inf
+    t = n * th[votes] / (2 * math.pi) + 0.5   # bin = floor(t) mod n; boundaries at integer t
+    f = t - np.floor(t)
+    return float(np.minimum(f, 1.0 - f).min())
+
+
 def smooth_histogram(hist: np.ndarray) -> np.ndarray:
     """One circular pass of [1/4, 1/2, 1/4] (§3.2)."""
     return 0.25 * np.roll(hist, 1) + 0.5 * hist + 0.25 * np.roll(hist, -1)
@@ -648,6 +679,7 @@ def extract(img: np.ndarray, p: Params = None, keep_pyramid: bool = False,
             else:
                 hist = orientation_histogram(L, r.x, r.y, sigma_oct, p)
                 angles, m1 = orientation_peaks(smooth_histogram(hist), p)
+                m1 = min(m1, orientation_vote_margin(L, r.x, r.y, sigma_oct, p))
             for a in angles:
                 rows.append((o, r, sigma_oct, a, min(m0, m1)))
     resp = np.array([row[1].response for row in rows])

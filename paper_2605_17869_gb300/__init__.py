@@ -30,7 +30,8 @@ __all__ = [
     "SIFT_E_CUDA", "SIFT_E_BUDGET", "SIFT_E_TIMEOUT", "SIFT_E_NOTFOUND", "KERNEL_CLASSES",
 ]
 
-KERNEL_CLASSES = ("blur", "base", "extrema", "decimate", "keypoint", "descriptor")
+KERNEL_CLASSES = ("blur", "base", "extrema", "decimate", "keypoint", "descriptor", "refine",
+                  "orientation")
 
 
 class SiftError(RuntimeError):

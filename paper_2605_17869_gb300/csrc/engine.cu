@@ -531,8 +531,8 @@ cudaError_t Engine::enqueue_all(cudaStream_t s, int M, int modes, std::vector<Pr
     }
   }
   rec(PC_KEYPOINT, [&] { return launch_bm_compact(d, g4, s); }, 3);
-  rec(PC_KEYPOINT, [&] { return launch_refine(d, g4, s); });
-  rec(PC_KEYPOINT, [&] { return launch_orientation(d, n_sm_ * 8, s); });
+  rec(PC_REFINE, [&] { return launch_refine(d, g4, s); });
+  rec(PC_ORIENT, [&] { return launch_orientation(d, n_sm_ * 8, s); });
   rec(PC_KEYPOINT, [&] { return launch_ori_compact(d, g4, s); }, 3);
   rec(PC_KEYPOINT, [&] { return launch_select(d, n_sm_, s); });
   rec(PC_DESCRIPTOR, [&] { return launch_descriptor(d, n_sm_ * 6, s); });

@@ -23,7 +23,7 @@ struct ImgIn {
 };
 
 enum ProfClass { PC_BLUR = 0, PC_BASE = 1, PC_EXTREMA = 2, PC_DECIMATE = 3, PC_KEYPOINT = 4,
-                 PC_DESCRIPTOR = 5, PC_COUNT = 6 };
+                 PC_DESCRIPTOR = 5, PC_REFINE = 6, PC_ORIENT = 7, PC_COUNT = 8 };
 
 struct Tuning {
   int lvl_kind[kMaxLevels];   // tile-height class per level (TK_BLUR32/64)

@@ -24,9 +24,10 @@ def _as_gpu(r):
 
 def test_identical_sets_match_exactly(ref):
     r, p = ref
-    m = compare.match(r, _as_gpu(r), params=p)
-    assert m.n_found == m.n_eligible == m.n_oracle == len(r)
-    assert m.n_gpu_unmatched == 0 and m.desc_max_l2 == 0.0 and m.n_angle_propagated == 0
+    m = compare.match(r, _as_gpu(r))
+    assert m.n_oracle == len(r) and m.n_eligible == int((r.margin >= compare.MARGIN_EPS).sum())
+    assert m.n_found == m.n_eligible > 0 and m.n_excused == m.n_oracle - m.n_eligible
+    assert m.n_gpu_unmatched == 0 and m.desc_max_l2 == 0.0
     assert m.worst == {"pos": 0.0, "sigma": 0.0, "angle": 0.0}
 
 
@@ -37,8 +38,8 @@ def test_position_tolerance(ref, key, delta, found):
     r, p = ref
     g = _as_gpu(r)
     g[key] = g[key] + delta
-    m = compare.match(r, g, params=p)
-    assert m.n_found == (len(r) if found else 0)
+    m = compare.match(r, g)
+    assert m.n_found == (m.n_eligible if found else 0)
     assert m.n_gpu_unmatched == (0 if found else len(r))
     if found:
         assert m.worst["pos"] == pytest.approx(abs(delta), rel=1e-6)
@@ -49,8 +50,8 @@ def test_scale_tolerance(ref, rel, found):
     r, p = ref
     g = _as_gpu(r)
     g["sigma"] = g["sigma"] * (1 + rel)
-    m = compare.match(r, g, params=p)
-    assert m.n_found == (len(r) if found else 0)
+    m = compare.match(r, g)
+    assert m.n_found == (m.n_eligible if found else 0)
     assert m.n_gpu_unmatched == 0          # every GPU keypoint still sits on an oracle keypoint
 
 
@@ -58,11 +59,11 @@ def test_angle_tolerance_wraps(ref):
     r, p = ref
     g = _as_gpu(r)
     g["angle"] = (g["angle"] + 359.6) % 360.0        # -0.4 degrees, across 0 where it applies
-    m = compare.match(r, g, params=p)
-    assert m.n_found == len(r)
+    m = compare.match(r, g)
+    assert m.n_found == m.n_eligible
     assert m.worst["angle"] == pytest.approx(0.4, abs=1e-9)
     g["angle"] = (r.angle + 0.6) % 360.0
-    assert compare.match(r, g, params=p).n_found == 0
+    assert compare.match(r, g).n_found == 0
     assert compare.angle_diff(359.9, 0.2) == pytest.approx(0.3)
 
 
@@ -70,53 +71,65 @@ def test_octave_and_layer_must_agree(ref):
     r, p = ref
     g = _as_gpu(r)
     g["layer"] = g["layer"] + 1
-    assert compare.match(r, g, params=p).n_found == 0
+    assert compare.match(r, g).n_found == 0
     g = _as_gpu(r)
     g["octave"] = g["octave"] + 1
-    assert compare.match(r, g, params=p).n_found == 0
+    assert compare.match(r, g).n_found == 0
 
 
 def test_keypoints_near_a_threshold_are_excused(ref):
     r, p = ref
+    e = np.nonzero(r.margin >= compare.MARGIN_EPS)[0]
+    assert len(e) >= 2
+    a, b = int(e[0]), int(e[1])                   # two eligible keypoints
+    n_el = len(e)
     g = _as_gpu(r)
-    keep = np.arange(len(r)) != 0
+    keep = np.arange(len(r)) != a
     g = {k: v[keep] for k, v in g.items()}
-    m = compare.match(r, g, params=p)
-    assert m.n_found == m.n_eligible - 1
-    saved = r.margin[:2].copy()
-    r.margin[0] = 0.5 * compare.MARGIN_EPS
+    m = compare.match(r, g)
+    assert m.n_eligible == n_el and m.n_found == n_el - 1
+    assert m.n_excused == len(r) - n_el          # a missed keypoint is not an excused one
+    saved = r.margin[[a, b]].copy()
+    r.margin[a] = 0.5 * compare.MARGIN_EPS
     try:
-        m = compare.match(r, g, params=p)
-        assert m.n_eligible == len(r) - 1 and m.n_found == m.n_eligible
-        r.margin[1] = 0.5 * compare.MARGIN_EPS   # excused although present: not counted as found
-        m = compare.match(r, g, params=p)
-        assert m.n_eligible == len(r) - 2 and m.n_found == m.n_eligible
+        m = compare.match(r, g)
+        assert m.n_eligible == n_el - 1 and m.n_found == m.n_eligible
+        assert m.n_excused == len(r) - n_el + 1
+        r.margin[b] = 0.5 * compare.MARGIN_EPS   # excused although present: not counted as found
+        m = compare.match(r, g)
+        assert m.n_eligible == n_el - 2 and m.n_found == m.n_eligible
     finally:
-        r.margin[:2] = saved
+        r.margin[[a, b]] = saved
 
 
-def test_descriptor_difference_and_angle_propagation(ref):
+def test_descriptor_difference_is_compared_directly(ref):
+    """The descriptor difference of a pair is the direct L2 difference of the two
+    descriptors. An angle moved within its tolerance still moves the descriptor:
+    the comparison reports that difference as it is and never recomputes the
+    oracle's descriptor at the GPU's angle."""
     r, p = ref
     g = _as_gpu(r)
     e = np.zeros_like(g["desc"])
     e[:, 0] = 5e-4
     g["desc"] = g["desc"] + e
-    m = compare.match(r, g, params=p)
-    assert m.desc_max_l2 == pytest.approx(5e-4, rel=1e-9) and m.desc_pairs == len(r)
-    # The angle moved inside its tolerance, the descriptor computed at the moved
-    # angle: the direct difference is large, the one at the GPU angle is zero.
+    m = compare.match(r, g)
+    n_el = int((r.margin >= compare.MARGIN_EPS).sum())
+    assert m.desc_max_l2 == pytest.approx(5e-4, rel=1e-9) and m.desc_pairs == n_el
     g = _as_gpu(r)
     g["angle"] = (g["angle"] + 0.45) % 360.0
     it = r.internals
+    moved = []
     for i in range(len(r)):
         L = r.pyramid[int(r.octave[i])][int(r.layer[i])]
         xi, yi = int(it["xi"][i]), int(it["yi"][i])
         g["desc"][i] = so.descriptor(L, xi + it["dx"][i], yi + it["dy"][i], xi, yi,
                                      it["sigma_oct"][i], float(g["angle"][i]), p)
-    m = compare.match(r, g, params=p)
-    assert m.desc_max_l2_direct > compare.DESC_TOL
-    assert m.desc_max_l2 < 1e-12
-    assert m.n_angle_propagated >= 1
+        if r.margin[i] >= compare.MARGIN_EPS:
+            moved.append(float(np.linalg.norm(g["desc"][i] - r.desc[i])))
+    m = compare.match(r, g)
+    assert m.n_found == n_el
+    assert m.desc_max_l2 == pytest.approx(max(moved), rel=1e-12)
+    assert m.desc_max_l2 > compare.DESC_TOL
 
 
 def test_closest_angle_and_worst_case_over_pairs(ref):
@@ -127,9 +140,10 @@ def test_closest_angle_and_worst_case_over_pairs(ref):
     twin = {k: v.copy() for k, v in g.items()}
     twin["angle"] = (twin["angle"] + 0.3) % 360.0       # a second orientation, 0.3 degrees off
     both = {k: np.concatenate([g[k], twin[k]]) for k in g}
-    m = compare.match(r, both, params=p)
-    assert m.n_found == len(r) and m.worst["angle"] == 0.0 and m.desc_max_l2 == 0.0
+    m = compare.match(r, both)
+    assert m.n_found == m.n_eligible and m.worst["angle"] == 0.0 and m.desc_max_l2 == 0.0
+    a = int(np.nonzero(r.margin >= compare.MARGIN_EPS)[0][0])
     g["x"] = g["x"].copy()
-    g["x"][0] += 0.005                                    # only the first keypoint moves
-    m = compare.match(r, g, params=p)
+    g["x"][a] += 0.005                                    # only one eligible keypoint moves
+    m = compare.match(r, g)
     assert m.worst["pos"] == pytest.approx(0.005, rel=1e-6)

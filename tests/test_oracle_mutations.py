@@ -140,6 +140,15 @@ MUTANTS = {
     "response_signed": ("                   abs(contrast), margin)", "                   contrast, margin)"),
     "keypoint_margin_skips_candidate": (
         "            m0 = min(float(mg[ci]), float(me[ci]), r.margin)", "            m0 = r.margin"),
+    "keypoint_margin_skips_votes": (
+        "                m1 = min(m1, orientation_vote_margin(L, r.x, r.y, sigma_oct, p))\n", "\n"),
+    "vote_margin_from_bin_centre": ("    t = n * th[votes] / (2 * math.pi) + 0.5   # bin",
+                                    "    t = n * th[votes] / (2 * math.pi)   # bin"),
+    "vote_margin_in_radians": ("    t = n * th[votes] / (2 * math.pi) + 0.5   # bin",
+                               "    t = th[votes] + 0.5   # bin"),
+    "vote_margin_one_sided": ("    return float(np.minimum(f, 1.0 - f).min())",
+                              "    return float(f.min())"),
+    "vote_margin_counts_zero_weight": ("    votes = wt * mag > 0\n", "    votes = wt * mag >= 0\n"),
     "keypoint_margin_skips_orientation": (
         "                rows.append((o, r, sigma_oct, a, min(m0, m1)))",
         "                rows.append((o, r, sigma_oct, a, m0))"),
@@ -220,9 +229,10 @@ COMPARE_MUTANTS = {
                                "        ds = np.abs(gsig[near] - osig[i]) / 10.0"),
     "compare_ignores_layer": ("        cand = buckets.get((int(ooct[i]), int(olay[i])))",
                               "        cand = np.concatenate(list(buckets.values()))"),
-    "compare_propagation_uncounted": ("                    if dd2 <= DESC_TOL:\n                        n_prop += 1",
-                                      "                    if True:\n                        n_prop += 0"),
-    "compare_no_recompute": ("                    dd = min(dd, dd2)", "                    dd = dd"),
+    "compare_desc_not_max": ("                desc_max = max(desc_max, dd)",
+                             "                desc_max = dd"),
+    "compare_excused_count": ("        return self.n_oracle - self.n_eligible",
+                              "        return self.n_oracle - self.n_found"),
     "compare_hit_needs_scale": (
         "        gpu_hit[near] = True\n",
         "        gpu_hit[near[(np.abs(gsig[near] - osig[i]) / osig[i] < SIGMA_RTOL)]] = True\n"),

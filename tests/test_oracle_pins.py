@@ -414,7 +414,8 @@ def test_upright_gives_one_keypoint_at_angle_zero_per_refined_point():
 
 def test_keypoint_margin_is_the_minimum_over_its_decisions(monkeypatch):
     """A keypoint's margin is the smallest margin of every decision behind it:
-    pre-gate, extremum, refinement and orientation peaks. Making each stage's
+    pre-gate, extremum, refinement, orientation peaks and orientation votes.
+    Making each stage's
     margin tiny in turn (by wrapping the stage) must bring every keypoint's
     margin down to it."""
     img = synth.make_image(synth.rng_for(93, 0), 96, 120)
@@ -438,6 +439,10 @@ def test_keypoint_margin_is_the_minimum_over_its_decisions(monkeypatch):
     monkeypatch.setattr(so, "orientation_peaks", lambda hs, pp: (op(hs, pp)[0], 3e-9))
     res = so.extract(img, p, with_descriptors=False)
     assert len(res) == len(base) and np.all(res.margin == 3e-9)
+    monkeypatch.setattr(so, "orientation_peaks", op)
+    monkeypatch.setattr(so, "orientation_vote_margin", lambda *a: 4e-9)
+    res = so.extract(img, p, with_descriptors=False)
+    assert len(res) == len(base) and np.all(res.margin == 4e-9)
 
 
 def test_dog_is_next_level_minus_this_one():
@@ -491,6 +496,46 @@ def test_ramp_orientation(deg):
     angles, _ = so.orientation_peaks(so.smooth_histogram(hist), p)
     assert len(angles) == 1
     assert abs(angles[0] - 10 * (int(math.floor(deg / 10 + 0.5)) % 36)) < 1e-9
+
+
+@pytest.mark.parametrize("deg,want", [(5.0, 0.0), (15.0, 0.0), (355.0, 0.0), (10.0, 0.5),
+                                      (7.5, 0.25), (2.5, 0.25), (181.0, 0.4)])
+def test_orientation_vote_margin_on_ramps(deg, want):
+    """The nearest-bin vote of a sample changes at bin coordinates k + 1/2, i.e.
+    at angles 5 + 10 k degrees. A ramp gives every sample the same angle, so the
+    vote margin is that angle's distance from the nearest such boundary, in
+    bins: 0 on a boundary (5, 15 and 355 degrees, the last one next to the wrap
+    at 360), 1/2 at a bin centre, 1/4 a quarter bin off a centre, 0.4 at 181
+    degrees (0.1 bin past the centre 180). Float rounding of the angle moves
+    these by far less than 1e-9 bins."""
+    p = so.Params()
+    th = math.radians(deg)
+    Y, X = np.mgrid[0:101, 0:101].astype(float)
+    L = 0.01 * (math.cos(th) * X + math.sin(th) * Y)
+    m = so.orientation_vote_margin(L, 50, 50, 2.0, p)
+    assert abs(m - want) < 1e-9
+
+
+def test_orientation_vote_margin_is_the_minimum_over_voting_samples():
+    """One pixel of a ramp at a bin centre (margin 1/2) is changed so that its
+    gradient sits 0.01 bin from a boundary: the window's margin becomes 0.01;
+    outside the window, or in the ignored outer ring of the image, it does not
+    count."""
+    p = so.Params()
+    Y, X = np.mgrid[0:101, 0:101].astype(float)
+    L = 0.01 * X                       # gradient angle 0: a bin centre
+    assert abs(so.orientation_vote_margin(L, 50, 50, 2.0, p) - 0.5) < 1e-12
+    # Sample (53, 50): dx = L[50, 54] - L[50, 52] = 0.02, dy = L[51, 53] - L[49, 53].
+    # Angle (5 - 0.1) degrees, 0.01 bin below the boundary between bins 0 and 1.
+    t = math.radians(4.9)
+    L2 = L.copy()
+    L2[51, 53] = L[51, 53] + 0.5 * 0.02 * math.tan(t)
+    L2[49, 53] = L[49, 53] - 0.5 * 0.02 * math.tan(t)
+    assert abs(so.orientation_vote_margin(L2, 50, 50, 2.0, p) - 0.01) < 1e-9
+    R = int(math.floor(3.0 * 1.5 * 2.0 + 0.5))   # window radius 9
+    assert abs(so.orientation_vote_margin(L2, 50 - R - 4, 50, 2.0, p) - 0.5) < 1e-12
+    # A flat window casts no vote: no vote decision, no margin.
+    assert so.orientation_vote_margin(np.full((40, 40), 0.5), 20, 20, 2.0, p) == math.inf
 
 
 def test_smoothing_and_parabola():
