@@ -128,8 +128,11 @@ sift_status sift_destroy(sift_handle *h);
  * Keypoints beyond max_kpts are dropped keeping the largest responses (ties:
  * canonical order); the kept ones are written in canonical order.
  * Returns SIFT_OK once the work is queued; SIFT_E_INVALID for bad arguments
- * (including min(H, W) below min_octave_side), SIFT_E_OOM / SIFT_E_CUDA on
- * allocation or launch failure. */
+ * (including min(H, W) below min_octave_side, and an image whose first octave
+ * is too large to address: its n_scales + 3 levels of H_0 rows by W_0 rounded
+ * up to 32 floats must hold fewer than 2^32 floats, i.e. up to about 21,800 x
+ * 21,800 pixels at n_scales = 3, where H_0 x W_0 is 2H x 2W when the image is
+ * magnified), SIFT_E_OOM / SIFT_E_CUDA on allocation or launch failure. */
 sift_status sift_extract(sift_handle *h, const float *img_dev, int H, int W, int pitch_elems,
                          void *stream, sift_kpts_dev out_kpts, float *out_desc_dev,
                          int *out_count_dev);

@@ -195,6 +195,7 @@ sift_status sift_extract(sift_handle *h, const float *img_dev, int H, int W, int
   const int ms = h->eng->params().min_octave_side;
   if (H < ms || W < ms || pitch_elems < W)
     return fail(h, SIFT_E_INVALID, "image smaller than min_octave_side or pitch < W");
+  if (!h->eng->addressable(H, W)) return fail(h, SIFT_E_INVALID, "image too large");
   ImgIn in{img_dev, H, W, pitch_elems, out_kpts, out_desc_dev, out_count_dev};
   h->split_batch = false;
   return pass(h, h->eng->run(1, &in, (cudaStream_t)stream));
@@ -216,6 +217,8 @@ sift_status sift_extract_batch(sift_handle *h, int n, const float *const *imgs_d
       return fail(h, SIFT_E_INVALID, "null pointer in image " + std::to_string(i));
     if (H[i] < ms || W[i] < ms || p < W[i])
       return fail(h, SIFT_E_INVALID, "image " + std::to_string(i) + " smaller than min_octave_side");
+    if (!h->eng->addressable(H[i], W[i]))
+      return fail(h, SIFT_E_INVALID, "image " + std::to_string(i) + " too large");
     in[i] = ImgIn{imgs_dev[i], H[i], W[i], p, out_kpts[i], out_desc[i], out_counts_dev + i};
   }
   h->split_batch = n > sift::kMaxImg;
@@ -273,6 +276,7 @@ sift_status sift_build_pyramid(sift_handle *h, const float *img_dev, int H, int 
   sift_status st = sift_pyramid_size(h, H, W, &no, &need);
   if (st != SIFT_OK) return st;
   if (out_elems < need || pitch_elems < W) return fail(h, SIFT_E_INVALID, "output too small");
+  if (!h->eng->addressable(H, W)) return fail(h, SIFT_E_INVALID, "image too large");
   ImgIn in{img_dev, H, W, pitch_elems, {}, nullptr, nullptr};
   cudaStream_t s = (cudaStream_t)stream;
   h->split_batch = false;
@@ -658,6 +662,7 @@ sift_status sift_serve_submit(sift_server *sv, const float *img_dev, int H, int 
   Server &s = sv->s;
   const sift_params &p = s.h->eng->params();
   if (H < p.min_octave_side || W < p.min_octave_side || pitch_elems < W) return SIFT_E_INVALID;
+  if (!s.h->eng->addressable(H, W)) return SIFT_E_INVALID;
   Request r;
   r.img = img_dev;
   r.H = H;

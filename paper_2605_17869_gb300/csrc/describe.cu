@@ -49,136 +49,155 @@ __device__ __forceinline__ float sigma_of(const Desc *d, const RefRec &r) {
 
 // ------------------------------------------------------------ orientation
 
-// One block of kKpWarps warps per candidate slot. Lane (w, l) sweeps samples
-// w*32 + l, w*32 + l + 128, ... and votes into its private column hist[w][.][l];
-// bin k is then the sum over w, then l, in that fixed order.
+// One block of kKpWarps warps per candidate slot. Lane l of warp w votes into
+// its private column hist[w][.][l]; bin k is the sum over each warp's lanes,
+// then over the warps, in that fixed order.
 __global__ void __launch_bounds__(kKpWarps * 32) k_orientation(const Desc *__restrict__ d) {
   pdl_wait();
   __shared__ float hist[kKpWarps][kOriBins][32];
+  __shared__ float hpart[kKpWarps][kOriBins];
   __shared__ float hsum[kOriBins];
   __shared__ float hsm[kOriBins];
   __shared__ float win[kOriWin];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = d->n_img;
   const int total = d->cand_flat[n];
-  for (int t = blockIdx.x; t < total; t += gridDim.x) {
-    const int b = find_owner(d->cand_flat, n, t);
-    const ImgDev &im = d->img[b];
-    const long long slot = im.cand_off + (t - d->cand_flat[b]);
-    if (d->code[slot] != RC_KEEP) {
-      if (tid == 0) d->npk[slot] = 0;
-      continue;
-    }
-    if (d->upright) {
-      if (tid == 0) {
-        d->npk[slot] = 1;
-        d->angs[slot * kMaxPeaks] = 0.f;
+  const bool upright = d->upright != 0;
+  // Block k takes the candidate slots k, k + G, k + 2G, ... (G blocks), 32 at
+  // a time: lane l of every warp looks at the l-th of them; warp 0 settles
+  // the rejected slots (no peak) and, in upright mode, the kept ones (one peak
+  // at angle 0); the kept slots are then taken one at a time by the whole
+  // block. Every warp computes the same ballot, so the loop over it is
+  // uniform across the block, and the interleave spreads the kept candidates
+  // evenly over the blocks.
+  const int G = gridDim.x;
+  for (int g0 = blockIdx.x; g0 < total; g0 += 32 * G) {
+    const int tl = g0 + lane * G;
+    int bl = 0;
+    long long sl = 0;
+    bool keep = false;
+    if (tl < total) {
+      bl = find_owner(d->cand_flat, n, tl);
+      sl = d->img[bl].cand_off + (tl - d->cand_flat[bl]);
+      keep = d->code[sl] == RC_KEEP;
+      if (warp == 0 && (!keep || upright)) {
+        d->npk[sl] = keep ? 1 : 0;
+        if (keep) d->angs[sl * kMaxPeaks] = 0.f;
       }
-      continue;
     }
-    const RefRec r = d->ref[slot];
-    const OctDev od = d->oct[im.oct0 + r.o];
-    const float *L = d->pyr + od.lvl + (long long)r.s * od.lstride;
-    const float sw = 1.5f * sigma_of(d, r);
-    const int R = (int)floorf(3.0f * sw + 0.5f);
-    const float ninv = -1.0f / (2.0f * sw * sw);
-    for (int k = 0; k < kOriBins; k++) hist[warp][k][lane] = 0.f;
-    // The window's pixels are staged in shared memory in bands of B sample
-    // rows (B + 2 pixel rows of width 2R + 3, coalesced loads); thread tid
-    // takes samples tid, tid + 128, ... of each band in row-major order.
-    const int side = 2 * R + 1, wd = side + 2;
-    const int B = kOriWin / wd - 2;  // >= 1: the parameter check bounds R
-    for (int jb = -R; jb <= R; jb += B) {
-      const int nb = min(B, R - jb + 1);
-      // Every copy is issued before any is waited for (cp.async, 4 bytes,
-      // zero-filled outside the image, where no byte is read).
-      for (int rr = warp; rr < nb + 2; rr += kKpWarps) {
-        const int gy = r.y + jb - 1 + rr;
-        const bool row_ok = gy >= 0 && gy < od.H;
-        const float *src = L + (long long)(row_ok ? gy : 0) * od.pitch;
-        float *dst = win + rr * wd;
-        for (int c = lane; c < wd; c += 32) {
-          const int gx = r.x - R - 1 + c;
-          const bool ok = row_ok && gx >= 0 && gx < od.W;
-          cp_async4_zfill(dst + c, src + (ok ? gx : 0), ok);
-        }
-      }
-      asm volatile("cp.async.wait_all;\n" ::: "memory");
-      __syncthreads();
-      const int ns = nb * side;
-      for (int idx = tid; idx < ns; idx += kKpWarps * 32) {
-        const int jj = idx / side;
-        const int i = idx - jj * side - R, j = jb + jj;
-        const int px = r.x + i, py = r.y + j;
-        if (px < 1 || px > od.W - 2 || py < 1 || py > od.H - 2) continue;
-        const float *w = win + (jj + 1) * wd + (i + R + 1);
-        const float dx = w[1] - w[-1];
-        const float dy = w[wd] - w[-wd];
-        const float mag = sqrtf(dx * dx + dy * dy);
-        float th = atan2f(dy, dx);
-        if (th < 0.f) th += kTwoPi;
-        int bin = (int)floorf(th * ((float)kOriBins / kTwoPi) + 0.5f);
-        if (bin >= kOriBins) bin -= kOriBins;
-        hist[warp][bin][lane] += expf((float)(i * i + j * j) * ninv) * mag;
-      }
-      __syncthreads();
-    }
-    __syncthreads();
-    if (tid < kOriBins) {
-      // Bin tid: per warp, the 32 lane columns starting at lane tid % 32 (so
-      // the 32 threads read 32 distinct banks), then the warp partials in
-      // warp order.
-      float pw[kKpWarps];
-#pragma unroll
-      for (int w = 0; w < kKpWarps; w++) {
-        float s = 0.f;
-#pragma unroll 8
-        for (int q = 0; q < 32; q++) s += hist[w][tid][(q + tid) & 31];
-        pw[w] = s;
-      }
-      float s = pw[0];
-#pragma unroll
-      for (int w = 1; w < kKpWarps; w++) s += pw[w];
-      hsum[tid] = s;
-    }
-    __syncthreads();
-    if (tid < kOriBins) {
-      const float hm = hsum[(tid + kOriBins - 1) % kOriBins];
-      const float hp = hsum[(tid + 1) % kOriBins];
-      hsm[tid] = 0.25f * hm + 0.5f * hsum[tid] + 0.25f * hp;
-    }
-    __syncthreads();
-    if (warp == 0) {
-      float hmax = 0.f;
-      for (int k = lane; k < kOriBins; k += 32) hmax = fmaxf(hmax, hsm[k]);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) hmax = fmaxf(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
-      const float thr = d->ori_peak_ratio * hmax;
-      int base = 0;
-      for (int k0 = 0; k0 < kOriBins; k0 += 32) {
-        const int k = k0 + lane;
-        bool peak = false;
-        float ang = 0.f;
-        if (k < kOriBins) {
-          const float hk = hsm[k];
-          const float hm = hsm[(k + kOriBins - 1) % kOriBins];
-          const float hp = hsm[(k + 1) % kOriBins];
-          if (hk > hm && hk > hp && hk >= thr) {
-            peak = true;
-            float kf = (float)k + 0.5f * (hm - hp) / (hm - 2.0f * hk + hp);
-            if (kf < 0.f) kf += (float)kOriBins;
-            if (kf >= (float)kOriBins) kf -= (float)kOriBins;
-            ang = kf * (360.0f / (float)kOriBins);
-            if (ang >= 360.0f) ang -= 360.0f;
+    unsigned todo = upright ? 0u : __ballot_sync(0xffffffffu, keep);
+    while (todo) {
+      const int kl = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const int b = __shfl_sync(0xffffffffu, bl, kl);
+      const long long slot = __shfl_sync(0xffffffffu, sl, kl);
+      const ImgDev &im = d->img[b];
+      const RefRec r = d->ref[slot];
+      const OctDev od = d->oct[im.oct0 + r.o];
+      const float *L = d->pyr + od.lvl + (long long)r.s * od.lstride;
+      const float sw = 1.5f * sigma_of(d, r);
+      const int R = (int)floorf(3.0f * sw + 0.5f);
+      const float ninv = -1.0f / (2.0f * sw * sw);
+      for (int k = 0; k < kOriBins; k++) hist[warp][k][lane] = 0.f;
+      // The window's pixels are staged in shared memory in bands of B sample
+      // rows (B + 2 pixel rows of width 2R + 3, coalesced loads).
+      const int side = 2 * R + 1, wd = side + 2;
+      const int B = kOriWin / wd - 2;  // >= 1: the parameter check bounds R
+      for (int jb = -R; jb <= R; jb += B) {
+        const int nb = min(B, R - jb + 1);
+        // Every copy is issued before any is waited for (cp.async, 4 bytes,
+        // zero-filled outside the image, where no byte is read).
+        for (int rr = warp; rr < nb + 2; rr += kKpWarps) {
+          const int gy = r.y + jb - 1 + rr;
+          const bool row_ok = gy >= 0 && gy < od.H;
+          const float *src = L + (long long)(row_ok ? gy : 0) * od.pitch;
+          float *dst = win + rr * wd;
+          for (int c = lane; c < wd; c += 32) {
+            const int gx = r.x - R - 1 + c;
+            const bool ok = row_ok && gx >= 0 && gx < od.W;
+            cp_async4_zfill(dst + c, src + (ok ? gx : 0), ok);
           }
         }
-        const unsigned m = __ballot_sync(0xffffffffu, peak);
-        if (peak) d->angs[slot * kMaxPeaks + base + __popc(m & ((1u << lane) - 1u))] = ang;
-        base += __popc(m);
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+        __syncthreads();
+        // Warp w takes the band's sample rows w, w + 4, ...; its lanes take the
+        // row's columns 32 at a time.
+        for (int jj = warp; jj < nb; jj += kKpWarps) {
+          const int j = jb + jj, py = r.y + j;
+          if (py < 1 || py > od.H - 2) continue;  // uniform over the warp
+          const float *wrow = win + (jj + 1) * wd + 1;
+          for (int c = lane; c < side; c += 32) {
+            const int i = c - R, px = r.x + i;
+            if (px < 1 || px > od.W - 2) continue;
+            const float *w = wrow + c;
+            const float dx = w[1] - w[-1];
+            const float dy = w[wd] - w[-wd];
+            const float mag = sqrtf(dx * dx + dy * dy);
+            float th = atan2f(dy, dx);
+            if (th < 0.f) th += kTwoPi;
+            int bin = (int)floorf(th * ((float)kOriBins / kTwoPi) + 0.5f);
+            if (bin >= kOriBins) bin -= kOriBins;
+            hist[warp][bin][lane] += expf((float)(i * i + j * j) * ninv) * mag;
+          }
+        }
+        __syncthreads();
       }
-      if (lane == 0) d->npk[slot] = base;
+      // Bin sums in a fixed order: each warp adds up its own 32 columns of every
+      // bin (lane l: bins l and l + 32, reading the columns from a rotated start
+      // so that the lanes hit distinct banks), then the warp partials in warp
+      // order.
+      for (int k = lane; k < kOriBins; k += 32) {
+        float sacc = 0.f;
+#pragma unroll 8
+        for (int q = 0; q < 32; q++) sacc += hist[warp][k][(q + k) & 31];
+        hpart[warp][k] = sacc;
+      }
+      __syncthreads();
+      if (tid < kOriBins) {
+        float sacc = hpart[0][tid];
+#pragma unroll
+        for (int w = 1; w < kKpWarps; w++) sacc += hpart[w][tid];
+        hsum[tid] = sacc;
+      }
+      __syncthreads();
+      if (tid < kOriBins) {
+        const float hm = hsum[(tid + kOriBins - 1) % kOriBins];
+        const float hp = hsum[(tid + 1) % kOriBins];
+        hsm[tid] = 0.25f * hm + 0.5f * hsum[tid] + 0.25f * hp;
+      }
+      __syncthreads();
+      if (warp == 0) {
+        float hmax = 0.f;
+        for (int k = lane; k < kOriBins; k += 32) hmax = fmaxf(hmax, hsm[k]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) hmax = fmaxf(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
+        const float thr = d->ori_peak_ratio * hmax;
+        int base = 0;
+        for (int k0 = 0; k0 < kOriBins; k0 += 32) {
+          const int k = k0 + lane;
+          bool peak = false;
+          float ang = 0.f;
+          if (k < kOriBins) {
+            const float hk = hsm[k];
+            const float hm = hsm[(k + kOriBins - 1) % kOriBins];
+            const float hp = hsm[(k + 1) % kOriBins];
+            if (hk > hm && hk > hp && hk >= thr) {
+              peak = true;
+              float kf = (float)k + 0.5f * (hm - hp) / (hm - 2.0f * hk + hp);
+              if (kf < 0.f) kf += (float)kOriBins;
+              if (kf >= (float)kOriBins) kf -= (float)kOriBins;
+              ang = kf * (360.0f / (float)kOriBins);
+              if (ang >= 360.0f) ang -= 360.0f;
+            }
+          }
+          const unsigned m = __ballot_sync(0xffffffffu, peak);
+          if (peak) d->angs[slot * kMaxPeaks + base + __popc(m & ((1u << lane) - 1u))] = ang;
+          base += __popc(m);
+        }
+        if (lane == 0) d->npk[slot] = base;
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
@@ -310,17 +329,26 @@ __global__ void __launch_bounds__(1024) k_select(const Desc *__restrict__ d) {
 // ------------------------------------------------------------- descriptor
 
 // Histogram columns of the descriptor: kDescCols per warp, column lane % 16,
-// so lanes l and l + 16 share a column and commit their votes in two passes
-// (half-warp 0, then half-warp 1): within a pass no two lanes touch the same
-// word, and across passes the order is fixed. Layout [bin][column].
+// layout [bin][column] with bin = cell * 8 + orientation. Each sample votes
+// into at most 4 cells and into the two orientation bins around its angle, of
+// which one is even and one odd. Lanes l and l + 16 share a column and commit
+// in two passes: in pass 0 the lower half-warp adds its even-orientation votes
+// while the upper half adds its odd ones, in pass 1 the other way round. Two
+// lanes of one pass then never touch the same word (different column, or
+// different orientation parity), every lane is busy in both passes, and the
+// order in which a word receives its votes is fixed by the code.
 constexpr int kDescCols = 16;
+// Floats of one warp's histogram block: 128 bins x 16 columns + 32 scratch words.
+constexpr int kDescWarpFloats = kDescLen * kDescCols + 32;
 
-// The 8 trilinear targets of one gradient sample at bin coordinates (rx, ry)
+// The trilinear targets of one gradient sample at bin coordinates (rx, ry)
 // from the keypoint, (u, v) = (rx, ry) + 3/2: weight m * exp(-(rx^2 + ry^2) /
-// 8), orientation relative to th. Targets outside the 4 x 4 cells get bin -1.
+// 8), orientation relative to th. Cells outside the 4 x 4 grid get -1.
 struct Vote {
-  int bin[8];
-  float w[8];
+  int cell[4];    // (v * 4 + u) * 8, or -1
+  float w[4];     // spatial weights times the magnitude-Gaussian weight
+  int oe, oo;     // the even and the odd orientation bin
+  float fe, fo;   // their orientation weights
 };
 
 __device__ __forceinline__ void desc_targets(Vote &v, float rx, float ry, float gx, float gy,
@@ -334,8 +362,13 @@ __device__ __forceinline__ void desc_targets(Vote &v, float rx, float ry, float 
   const float ob = phi * (8.0f / kTwoPi);
   const float wt = mag * expf(-(rx * rx + ry * ry) * 0.125f);
   const float u0f = floorf(u), v0f = floorf(vv0), o0f = floorf(ob);
-  const float fu = u - u0f, fv = vv0 - v0f, fo = ob - o0f;
-  const int u0 = (int)u0f, v0 = (int)v0f, o0 = (int)o0f;
+  const float fu = u - u0f, fv = vv0 - v0f, f1 = ob - o0f;
+  const int u0 = (int)u0f, v0 = (int)v0f, o0 = (int)o0f & 7, o1 = (o0 + 1) & 7;
+  const bool even0 = (o0 & 1) == 0;
+  v.oe = even0 ? o0 : o1;
+  v.oo = even0 ? o1 : o0;
+  v.fe = even0 ? 1.f - f1 : f1;
+  v.fo = even0 ? f1 : 1.f - f1;
 #pragma unroll
   for (int dv = 0; dv < 2; dv++) {
     const int vv = v0 + dv;
@@ -345,28 +378,32 @@ __device__ __forceinline__ void desc_targets(Vote &v, float rx, float ry, float 
       const int uu = u0 + du;
       const float wu = du ? fu : 1.f - fu;
       const bool in = vv >= 0 && vv <= 3 && uu >= 0 && uu <= 3;
-#pragma unroll
-      for (int dob = 0; dob < 2; dob++) {
-        const int k = (dv * 2 + du) * 2 + dob;
-        const int oo = (o0 + dob) & 7;
-        const float wo = dob ? fo : 1.f - fo;
-        v.bin[k] = in ? (vv * 4 + uu) * 8 + oo : -1;
-        v.w[k] = wt * wv * wu * wo;
-      }
+      v.cell[dv * 2 + du] = in ? (vv * 4 + uu) * 8 : -1;
+      v.w[dv * 2 + du] = wt * wv * wu;
     }
   }
 }
 
 // Add the votes of the warp's lanes (ok: the lane has a sample) to the warp's
-// columns: half-warp 0, then half-warp 1. Every lane of the warp must call it.
+// columns in the two passes described above. A vote that has no target (a cell
+// outside the grid, or no sample) goes with weight 0 to the lane's own scratch
+// word after the 128 bins, so every lane does the same 8 read-modify-writes
+// without branches; the scratch words are never read. Every lane of the warp
+// must call it.
 __device__ __forceinline__ void desc_commit(float *hist, int lane, bool ok, const Vote &v) {
   const int col = lane & (kDescCols - 1);
+  const bool upper = lane >= 16;
+  float *scratch = hist + kDescLen * kDescCols + lane;
 #pragma unroll
-  for (int half = 0; half < 2; half++) {
-    if (ok && (lane >> 4) == half) {
+  for (int pass = 0; pass < 2; pass++) {
+    const bool even = (pass == 0) != upper;
+    const int o = even ? v.oe : v.oo;
+    const float f = even ? v.fe : v.fo;
 #pragma unroll
-      for (int k = 0; k < 8; k++)
-        if (v.bin[k] >= 0) hist[v.bin[k] * kDescCols + col] += v.w[k];
+    for (int k = 0; k < 4; k++) {
+      const bool hit = ok && v.cell[k] >= 0;
+      float *p = hit ? hist + (v.cell[k] + o) * kDescCols + col : scratch;
+      *p += hit ? v.w[k] * f : 0.f;
     }
     __syncwarp();
   }
@@ -388,10 +425,9 @@ __global__ void __launch_bounds__(kKpWarps * 32, 6) k_descriptor(const Desc *__r
   pdl_wait();
   extern __shared__ __align__(16) float dsm[];
   __shared__ float red[kKpWarps];
-  __shared__ int s_row_lo[kKpWarps * 32], s_row_pre[kKpWarps * 32 + 1];
-  __shared__ int s_scan[kKpWarps + 1];
+  __shared__ int s_lo[kKpWarps][32], s_pre[kKpWarps][33];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  float *hist = dsm + warp * (kDescLen * kDescCols);
+  float *hist = dsm + warp * kDescWarpFloats;
   const int n = d->n_img;
   const int total = d->fin_flat[n];
   for (int t = blockIdx.x; t < total; t += gridDim.x) {
@@ -431,57 +467,75 @@ __global__ void __launch_bounds__(kKpWarps * 32, 6) k_descriptor(const Desc *__r
     if (!d->dsp) {
       // Samples: integer offsets (i, jy) in [-R, R]^2 inside the image whose
       // rotated bin coordinates fall in (-1, 4)^2, i.e. inside a square of half
-      // side h = 2.5 bins around the keypoint. Each row's candidates are cut to
-      // an interval (a superset of the square's chord, widened by 2 pixels so
-      // that rounding can only add candidates), and the exact test below
-      // decides, so the sample set is the same as a sweep of the whole window.
-      // Thread q takes samples q, q + 128, ... of the concatenated intervals.
+      // side h = 2.5 bins around the keypoint. Warp w takes rows jlo + w,
+      // jlo + w + 4, ... (at most 32 of them, one per lane): each lane cuts its
+      // row to an interval, a superset of the square's chord widened by 2
+      // pixels so that rounding can only add candidates, and a warp scan lays
+      // the intervals end to end. The warp then sweeps that list 32 samples at
+      // a time, and the exact test below decides, so the sample set is the
+      // same as a sweep of the whole window.
       const float h = 2.5f * wbin;
       const int ilo = max(-R, 1 - r.x), ihi = min(R, od.W - 2 - r.x);
       const int jlo = max(-R, 1 - r.y), jhi = min(R, od.H - 2 - r.y);
-      for (int j0 = jlo; j0 <= jhi; j0 += kKpWarps * 32) {
-        const int nr = min(kKpWarps * 32, jhi - j0 + 1);
-        int len = 0;
-        if (tid < nr) {
-          const float oy = (float)(j0 + tid) - r.dy;
-          float lo = -1e30f, hi = 1e30f;
-          // slab a * ox + b in (-h, h) for (a, b) = (ct, st * oy), (-st, ct * oy)
+      const float ica = fabsf(ct) * (float)(R + 1) < 1.0f ? 0.f : 1.0f / ct;
+      const float isa = fabsf(st) * (float)(R + 1) < 1.0f ? 0.f : -1.0f / st;
+      // Rows per warp are at most (2R + 1) / 4 + 1, i.e. 20 for the largest
+      // octave-relative scale of the default parameters; larger windows take
+      // several rounds of 32 rows.
+      for (int rb = 0; jlo + warp + kKpWarps * rb <= jhi; rb += 32) {
+        int len = 0, a0 = 0;
+        {
+          const int jy = jlo + warp + kKpWarps * (rb + lane);
+          if (jy <= jhi) {
+            const float oy = (float)jy - r.dy;
+            float lo = -1e30f, hi = 1e30f;
+            // slab a * ox + b in (-h, h) for (a, b) = (ct, st * oy), (-st, ct * oy)
 #pragma unroll
-          for (int k = 0; k < 2; k++) {
-            const float a = k ? -st : ct, b = k ? ct * oy : st * oy;
-            if (fabsf(a) * (float)(R + 1) < 1.0f) {
-              if (fabsf(b) >= h + 2.0f) hi = -1e30f;  // |a * ox| < 1: the row misses the slab
-            } else {
-              const float e0 = (-h - b) / a, e1 = (h - b) / a;
-              lo = fmaxf(lo, fminf(e0, e1));
-              hi = fminf(hi, fmaxf(e0, e1));
+            for (int k = 0; k < 2; k++) {
+              const float ia = k ? isa : ica, b = k ? ct * oy : st * oy;
+              if (ia == 0.f) {
+                if (fabsf(b) >= h + 2.0f) hi = -1e30f;  // |a * ox| < 1: the row misses the slab
+              } else {
+                const float e0 = (-h - b) * ia, e1 = (h - b) * ia;
+                lo = fmaxf(lo, fminf(e0, e1));
+                hi = fminf(hi, fmaxf(e0, e1));
+              }
             }
+            int a1 = ihi;
+            a0 = ilo;
+            if (hi < lo) {
+              a1 = a0 - 1;
+            } else {
+              if (lo + r.dx > (float)ilo) a0 = max(ilo, (int)floorf(lo + r.dx) - 2);
+              if (hi + r.dx < (float)ihi) a1 = min(ihi, (int)ceilf(hi + r.dx) + 2);
+            }
+            len = max(0, a1 - a0 + 1);
           }
-          int a0 = ilo, a1 = ihi;
-          if (hi < lo) {
-            a1 = a0 - 1;
-          } else {
-            if (lo + r.dx > (float)ilo) a0 = max(ilo, (int)floorf(lo + r.dx) - 2);
-            if (hi + r.dx < (float)ihi) a1 = min(ihi, (int)ceilf(hi + r.dx) + 2);
-          }
-          len = max(0, a1 - a0 + 1);
-          s_row_lo[tid] = a0;
         }
-        int tot;
-        const int ex = block_excl_scan(len, s_scan, &tot);
-        if (tid < nr) s_row_pre[tid] = ex;
-        if (tid == 0) s_row_pre[nr] = tot;
-        __syncthreads();
+        // Exclusive scan of the interval lengths over the warp's rows.
+        int pre = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_up_sync(0xffffffffu, pre, o);
+          if (lane >= o) pre += v;
+        }
+        const int tot = __shfl_sync(0xffffffffu, pre, 31);
+        pre -= len;
+        int *wlo = s_lo[warp], *wpre = s_pre[warp];
+        wlo[lane] = a0;
+        wpre[lane] = pre;
+        if (lane == 31) wpre[32] = tot;
+        __syncwarp();
         int row = 0;
         // Warp-uniform trip count: every lane reaches the commit's __syncwarp.
-        for (int q0 = 0; q0 < tot; q0 += kKpWarps * 32) {
-          const int q = q0 + tid;
+        for (int q0 = 0; q0 < tot; q0 += 32) {
+          const int q = q0 + lane;
           bool ok = q < tot;
           Vote vt;
           if (ok) {
-            while (s_row_pre[row + 1] <= q) row++;
-            const int jy = j0 + row;
-            const int i = s_row_lo[row] + (q - s_row_pre[row]);
+            while (wpre[row + 1] <= q) row++;
+            const int jy = jlo + warp + kKpWarps * (rb + row);
+            const int i = wlo[row] + (q - wpre[row]);
             const float ox = (float)i - r.dx, oy = (float)jy - r.dy;
             const float rx = (ct * ox + st * oy) * inv_w;
             const float ry = (-st * ox + ct * oy) * inv_w;
@@ -496,7 +550,7 @@ __global__ void __launch_bounds__(kKpWarps * 32, 6) k_descriptor(const Desc *__r
           }
           desc_commit(hist, lane, ok, vt);
         }
-        __syncthreads();
+        __syncwarp();  // the next round rewrites this warp's interval table
       }
     } else {
       for (int f = 0; f < 5; f++) {
@@ -538,7 +592,7 @@ __global__ void __launch_bounds__(kKpWarps * 32, 6) k_descriptor(const Desc *__r
     float pw[kKpWarps];
 #pragma unroll
     for (int w = 0; w < kKpWarps; w++) {
-      const float *h = dsm + w * (kDescLen * kDescCols) + tid * kDescCols;
+      const float *h = dsm + w * kDescWarpFloats + tid * kDescCols;
       float s = 0.f;
 #pragma unroll
       for (int l = 0; l < kDescCols; l++) s += h[(l + (tid >> 1)) & (kDescCols - 1)];
@@ -614,7 +668,7 @@ cudaError_t launch_select(const Desc *d, int grid, cudaStream_t s) {
   return launch_pdl(k_select, grid, 1024, 0, s, d);
 }
 
-int descriptor_smem_bytes() { return kKpWarps * kDescLen * kDescCols * (int)sizeof(float); }
+int descriptor_smem_bytes() { return kKpWarps * kDescWarpFloats * (int)sizeof(float); }
 
 cudaError_t descriptor_set_attributes() {
   return cudaFuncSetAttribute(k_descriptor, cudaFuncAttributeMaxDynamicSharedMemorySize,

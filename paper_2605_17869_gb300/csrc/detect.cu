@@ -18,116 +18,186 @@ namespace sift {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kExtThreads = 128;  // extrema scan: four warps per block, five blocks per SM
 
 // ------------------------------------------------------------ extrema scan
 
-// A warp owns a tile of 32 columns x kExtTH rows (lane = column). It issues
-// the loads of all S+3 levels for the tile's rows plus one halo row above and
-// below at once, forms the DoG values in registers (one FP32 subtraction each,
-// as everywhere else), and tests each pixel in three steps:
-//  1. the contrast gate |D| > 0.5 T;
-//  2. a branch-free check against the four direct neighbours in its layer
-//     (left / right by warp shuffle, up / down from the adjacent rows; lanes 0
-//     and 31 skip their outer neighbour here, the exact test below covers it)
-//     and the same column of rows r - 1 .. r + 1 in the two adjacent layers
-//     (registers); 10 of the 26 neighbours in all;
-//  3. for the few pixels that pass, the exact 26-neighbour test, done by the
-//     whole warp per pixel (lane k < 26 compares one neighbour, then a vote).
-// Only step 3 decides; steps 1-2 merely skip pixels that cannot pass it.
+// 3-input maximum / minimum (one instruction on sm_100 and later).
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
+// One row of DoG values as the scan holds it, for the lane's column x: the
+// maximum and minimum over columns x - 1 .. x + 1 of each of the S + 2 DoG
+// layers, and for the tested layers 1 .. S the value itself and the larger and
+// smaller of its left and right neighbours.
+template <int S> struct ExtRow {
+  float hx[S + 2], hn[S + 2];
+  float c[S], lrx[S], lrn[S];
+};
+
+// DoG (one FP32 subtraction per value, as in every other stage) of one row
+// from its S + 3 Gaussian levels, and the row's three-column maxima / minima
+// (neighbours by warp shuffle; lanes 0 and 31 get meaningless values there,
+// they only supply neighbours).
 template <int S>
-__global__ void __launch_bounds__(kThreads, 3) k_extrema(const Desc *__restrict__ d, int oct) {
-  constexpr int ND = S + 2;
-  constexpr int RR = kExtTH + 2;  // rows held: y0 - 1 .. y0 + kExtTH
-  constexpr int WPB = kThreads / 32;
+__device__ __forceinline__ void ext_row(ExtRow<S> &R, const float (&g)[S + 3]) {
+#pragma unroll
+  for (int l = 0; l < S + 2; l++) {
+    const float v = g[l + 1] - g[l];
+    const float lf = __shfl_up_sync(0xffffffffu, v, 1);
+    const float rt = __shfl_down_sync(0xffffffffu, v, 1);
+    R.hx[l] = max3f(lf, v, rt);
+    R.hn[l] = min3f(lf, v, rt);
+    if (l >= 1 && l <= S) {
+      R.c[l - 1] = v;
+      R.lrx[l - 1] = fmaxf(lf, rt);
+      R.lrn[l - 1] = fminf(lf, rt);
+    }
+  }
+}
+
+// The rows a warp has in flight: a ring of kExtRing rows x (S + 3) levels x
+// 32 lanes in shared memory, filled by 4-byte asynchronous copies (each lane
+// copies its own column) so that kExtRing - 1 rows are on their way while
+// one is consumed.
+constexpr int kExtRing = 4;  // a power of two
+
+__device__ __forceinline__ void cp_async4_ca(float *dst, const float *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(
+                   static_cast<unsigned>(__cvta_generic_to_shared(dst))),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Copy the S + 3 levels of one image row at the lane's column into a ring
+// slot (lp[l]: level l at row 0 and the lane's column; row_off: the row's
+// offset, the same for the whole warp).
+template <int S>
+__device__ __forceinline__ void ext_issue(float *slot, const float *const (&lp)[S + 3],
+                                          long long row_off) {
+#pragma unroll
+  for (int l = 0; l < S + 3; l++) cp_async4_ca(slot + l * 32, lp[l] + row_off);
+}
+
+// Test row y (P, C, N: rows y - 1, y, y + 1) and write its bitmap words:
+// pixel x of layer s is a candidate when it lies inside the border, |D|
+// exceeds the pre-gate, and D is strictly above the maximum, or strictly
+// below the minimum, of its 26 neighbours. Those extrema are separable: the
+// 9 values of layer s +- 1 reduce to max(hx(y - 1), hx(y), hx(y + 1)), the 8
+// of layer s to max(hx(y - 1), hx(y + 1), left, right).
+template <int S>
+__device__ __forceinline__ void ext_test(const ExtRow<S> &P, const ExtRow<S> &C,
+                                         const ExtRow<S> &N, bool inb, float thr, int lane,
+                                         uint32_t *word) {
+  float vx[S + 2], vn[S + 2];
+#pragma unroll
+  for (int l = 0; l < S + 2; l++) {
+    vx[l] = max3f(P.hx[l], C.hx[l], N.hx[l]);
+    vn[l] = min3f(P.hn[l], C.hn[l], N.hn[l]);
+  }
+  unsigned mine = 0u;
+#pragma unroll
+  for (int s = 1; s <= S; s++) {
+    const float c = C.c[s - 1];
+    const float mx = max3f(vx[s - 1], vx[s + 1], max3f(P.hx[s], N.hx[s], C.lrx[s - 1]));
+    const float mn = min3f(vn[s - 1], vn[s + 1], min3f(P.hn[s], N.hn[s], C.lrn[s - 1]));
+    const bool ok = inb && fabsf(c) > thr && (c > mx || c < mn);
+    const unsigned bits = __ballot_sync(0xffffffffu, ok) >> 1;  // lanes 1 .. 30 -> bits 0 .. 29
+    mine = lane == s - 1 ? bits : mine;
+  }
+  if (lane < S) *word = mine;
+}
+
+// A warp owns a strip of kBmCols = 30 columns x kExtTH rows: lane l holds
+// column 30 tx - 1 + l, so lanes 1 .. 30 are the strip and lanes 0 and 31 its
+// neighbours, and one bitmap word covers the strip's row. The warp streams
+// down the strip: each image row's S + 3 levels are loaded once (the next
+// row's loads are in flight while the current row is tested) and every test
+// is done from registers. The candidate decisions are exact comparisons of
+// the same FP32 values, so they do not depend on the tiling. Bitmap words are
+// written by ballots; no atomics.
+template <int S>
+__global__ void __launch_bounds__(kExtThreads, 5) k_extrema(const Desc *__restrict__ d, int oct) {
+  constexpr int WPB = kExtThreads / 32;
+  constexpr int SLOT = (S + 3) * 32;
+  __shared__ float ring[WPB][kExtRing * SLOT];
   const int n = d->n_img;
   const int *pre = d->tile_pre[TK_EXT][oct];
   const int total = pre[n];
   const int lane = threadIdx.x & 31;
+  float *my = ring[threadIdx.x >> 5];
   const float thr = d->prefilter;
   const int bord = d->border;
-  // Neighbour k of the 26 (3x3x3 minus the centre), owned by lane k.
-  const int jn = lane < 13 ? lane : lane + 1;
-  const int nds = jn / 9 - 1, ndy = (jn / 3) % 3 - 1, ndx = jn % 3 - 1;
   pdl_wait();
   for (int t = blockIdx.x * WPB + (threadIdx.x >> 5); t < total; t += gridDim.x * WPB) {
     if (t + gridDim.x * WPB >= total) pdl_trigger();  // this warp's last tile
     const int b = find_owner(pre, n, t);
     const OctDev od = d->oct[b * kMaxOct + oct];  // image b's octaves sit at fixed slots
-    const int H = od.H, W = od.W, pitch = od.pitch;
+    const int H = od.H, W = od.W;
+    const long long pitch = od.pitch, ls = od.lstride;
     const int lt = t - pre[b];
     const int ty = lt / od.wpr, tx = lt - ty * od.wpr;
-    const int x = tx * 32 + lane, y0 = ty * kExtTH;
-    const float *G = d->pyr + od.lvl;
-    const long long ls = od.lstride;
-    const int xc = min(x, W - 1);
-    float D[RR][ND];
+    const int x = tx * kBmCols - 1 + lane;
+    const int y0 = ty * kExtTH, y1 = min(y0 + kExtTH, H);
+    const float *lp[S + 3];
     {
-      float g[RR][S + 3];
+      const float *G = d->pyr + od.lvl + min(max(x, 0), W - 1);
 #pragma unroll
-      for (int r = 0; r < RR; r++) {
-        const int yc = min(max(y0 - 1 + r, 0), H - 1);
-        const float *p = G + (long long)yc * pitch + xc;
-#pragma unroll
-        for (int l = 0; l < S + 3; l++) g[r][l] = __ldg(p + l * ls);
-      }
-#pragma unroll
-      for (int r = 0; r < RR; r++)
-#pragma unroll
-        for (int l = 0; l < ND; l++) D[r][l] = g[r][l + 1] - g[r][l];
+      for (int l = 0; l < S + 3; l++) lp[l] = G + l * ls;
     }
-    // Lane s < S writes layer s+1's word of each row.
+    float *mine_ring = my + lane;
+    const bool xin = lane >= 1 && lane <= kBmCols && x >= bord && x < W - bord;
     uint32_t *bmw = d->bm + od.bm + (long long)lane * H * od.wpr + tx;
-    const bool xin = x >= bord && x < W - bord;
-#pragma unroll
-    for (int r = 1; r <= kExtTH; r++) {
-      const int y = y0 + r - 1;
-      if (y >= H) break;  // uniform over the warp
-      const bool inb = xin && y >= bord && y < H - bord;
-      bool gated = false;
-#pragma unroll
-      for (int s = 1; s <= S; s++) gated = gated || fabsf(D[r][s]) > thr;
-      unsigned bits[S];
-#pragma unroll
-      for (int s = 0; s < S; s++) bits[s] = 0u;
-      if (__any_sync(0xffffffffu, inb && gated)) {  // most rows skip everything below
-#pragma unroll
-        for (int s = 1; s <= S; s++) {
-          const float cv = D[r][s];
-          const float lf = __shfl_up_sync(0xffffffffu, cv, 1);
-          const float rt = __shfl_down_sync(0xffffffffu, cv, 1);
-          const float up = D[r - 1][s], dn = D[r + 1][s];
-          // Same column in the adjacent layers, rows r - 1 .. r + 1 (registers).
-          const float s0 = D[r][s - 1], s1 = D[r][s + 1];
-          const float s2 = D[r - 1][s - 1], s3 = D[r + 1][s - 1];
-          const float s4 = D[r - 1][s + 1], s5 = D[r + 1][s + 1];
-          const float hi = fmaxf(fmaxf(fmaxf(up, dn), fmaxf(s0, s1)),
-                                 fmaxf(fmaxf(s2, s3), fmaxf(s4, s5)));
-          const float lo = fminf(fminf(fminf(up, dn), fminf(s0, s1)),
-                                 fminf(fminf(s2, s3), fminf(s4, s5)));
-          const bool pmax = cv > hi && (lane == 0 || cv > lf) && (lane == 31 || cv > rt);
-          const bool pmin = cv < lo && (lane == 0 || cv < lf) && (lane == 31 || cv < rt);
-          const bool ok = inb && fabsf(cv) > thr && (pmax || pmin);
-          unsigned surv = __ballot_sync(0xffffffffu, ok);
-          while (surv) {
-            const int sl = __ffs(surv) - 1;
-            surv &= surv - 1;
-            const float sv = __shfl_sync(0xffffffffu, cv, sl);
-            float nb = 0.f;
-            if (lane < 26) {
-              const long long q = (long long)(y + ndy) * pitch + (x - lane + sl + ndx);
-              nb = __ldg(G + (s + nds + 1) * ls + q) - __ldg(G + (s + nds) * ls + q);
-            }
-            const bool ext = __all_sync(0xffffffffu, lane >= 26 || sv > nb) ||
-                             __all_sync(0xffffffffu, lane >= 26 || sv < nb);
-            if (ext) bits[s - 1] |= 1u << sl;
-          }
-        }
+    // Row k of the strip's sequence is image row y0 - 1 + k (clamped), k = 0 ..
+    // n_rows - 1; it lives in ring slot k % kExtRing. One commit group per
+    // row, empty past the end, so that the number of pending groups is fixed.
+    const int n_rows = y1 - y0 + 2;
+    auto issue = [&](int k) {
+      if (k < n_rows) {
+        const int row = min(max(y0 - 1 + k, 0), H - 1);
+        ext_issue<S>(mine_ring + (k & (kExtRing - 1)) * SLOT, lp, row * pitch);
       }
-      unsigned mine = bits[0];
+      cp_async_commit();
+    };
+    auto consume = [&](ExtRow<S> &R, int k) {
+      cp_async_wait<kExtRing - 1>();  // row k's group is complete
+      const float *slot = mine_ring + (k & (kExtRing - 1)) * SLOT;
+      float g[S + 3];
 #pragma unroll
-      for (int s = 1; s < S; s++) mine = lane == s ? bits[s] : mine;
-      if (lane < S) bmw[(long long)y * od.wpr] = mine;
+      for (int l = 0; l < S + 3; l++) g[l] = slot[l * 32];
+      ext_row<S>(R, g);
+      issue(k + kExtRing);  // into the slot just read (each lane rewrites only its own words)
+    };
+#pragma unroll
+    for (int k = 0; k < kExtRing; k++) issue(k);
+    ExtRow<S> A, B, C;
+    consume(A, 0);
+    consume(B, 1);
+    // Rows rotate through A, B, C (previous, current, next) without copies.
+    auto step = [&](ExtRow<S> &Pr, ExtRow<S> &Cu, ExtRow<S> &Nx, int y) {
+      consume(Nx, y - y0 + 2);                                    // image row y + 1 (clamped)
+      const bool inb = xin && y >= bord && y < H - bord;
+      ext_test<S>(Pr, Cu, Nx, inb, thr, lane, bmw + (long long)y * od.wpr);
+    };
+    for (int y = y0; y < y1; y += 3) {
+      step(A, B, C, y);
+      if (y + 1 >= y1) break;
+      step(B, C, A, y + 1);
+      if (y + 2 >= y1) break;
+      step(C, A, B, y + 2);
     }
+    cp_async_wait<0>();  // no copy of this strip outlives it
   }
 }
 
@@ -216,7 +286,7 @@ __global__ void __launch_bounds__(kThreads) k_bm_emit(const Desc *__restrict__ d
       while (wv) {
         const int bit = __ffs(wv) - 1;
         wv &= wv - 1;
-        if (slot < im.cand_cap) d->cand[im.cand_off + slot] = make_int4(o, layer, y, wx * 32 + bit);
+        if (slot < im.cand_cap) d->cand[im.cand_off + slot] = make_int4(o, layer, y, wx * kBmCols + bit);
         slot++;
       }
     }
@@ -325,11 +395,25 @@ __global__ void __launch_bounds__(kThreads) k_refine(const Desc *__restrict__ d)
 
 cudaError_t extrema_set_attributes() { return cudaSuccess; }
 
+int extrema_grid(int n_sm, int n_scales) {
+  int nb = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (n_scales) {
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extrema<2>, kExtThreads, 0); break;
+    case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extrema<3>, kExtThreads, 0); break;
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extrema<4>, kExtThreads, 0); break;
+    case 5: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extrema<5>, kExtThreads, 0); break;
+    case 6: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extrema<6>, kExtThreads, 0); break;
+    default: break;
+  }
+  return n_sm * ((e == cudaSuccess && nb > 0) ? nb : 1);
+}
+
 cudaError_t launch_extrema(const Desc *d, int oct, int n_scales, int grid, cudaStream_t s, bool pdl) {
 #define EXT_CASE(SS)                                                               \
   case SS:                                                                         \
-    if (pdl) return launch_pdl(k_extrema<SS>, grid, kThreads, 0, s, d, oct);        \
-    return launch_plain(k_extrema<SS>, grid, kThreads, 0, s, d, oct);
+    if (pdl) return launch_pdl(k_extrema<SS>, grid, kExtThreads, 0, s, d, oct);     \
+    return launch_plain(k_extrema<SS>, grid, kExtThreads, 0, s, d, oct);
   switch (n_scales) {
     EXT_CASE(2)
     EXT_CASE(3)

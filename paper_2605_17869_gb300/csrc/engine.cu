@@ -166,6 +166,7 @@ sift_status Engine::init() {
     tun_.lvl_kind[i] = TK_BLUR32;
   }
   tun_.grid_mult_blur = 4;
+  ext_grid_ = extrema_grid(n_sm_, S_);
   inited_ = true;
   return SIFT_OK;
 }
@@ -193,6 +194,7 @@ sift_status Engine::init_noalloc() {
     tun_.lvl_kind[i] = TK_BLUR32;
   }
   tun_.grid_mult_blur = 4;
+  ext_grid_ = extrema_grid(n_sm_, S_);
   return SIFT_OK;
 }
 
@@ -212,6 +214,14 @@ int Engine::octave_sizes(int H, int W, int *hs, int *ws) const {
     w /= 2;
   }
   return n;
+}
+
+bool Engine::addressable(int H, int W) const {
+  const bool up = magnify(H, W);
+  const unsigned long long h = up ? 2ull * H : (unsigned long long)H;
+  const unsigned long long w = up ? 2ull * W : (unsigned long long)W;
+  const unsigned long long pitch = (w + 31) / 32 * 32;
+  return (unsigned long long)(P_.n_scales + 3) * h * pitch <= 0xffffffffull;
 }
 
 namespace {
@@ -234,7 +244,7 @@ size_t Engine::workspace_bytes(int n, const int *H, const int *W) const {
     for (int o = 0; o < no; o++) {
       const long long pitch = align_up(ws[o], 32);
       pyr += (size_t)(S_ + 3) * hs[o] * pitch;
-      words += (long long)S_ * hs[o] * ((ws[o] + 31) / 32);
+      words += (long long)S_ * hs[o] * div_up(ws[o], kBmCols);
       px += (long long)hs[o] * ws[o];
     }
     bm += words;
@@ -275,7 +285,7 @@ sift_status Engine::fill_plan(int n, const ImgIn *in, Desc &hd, WsLayout &L, int
     d.up = magnify(in[b].H, in[b].W) ? 1 : 0;
     int hs[kMaxOct], ws[kMaxOct];
     const int no = octave_sizes(in[b].H, in[b].W, hs, ws);
-    if (no == 0) return SIFT_E_INVALID;
+    if (no == 0 || !addressable(in[b].H, in[b].W)) return SIFT_E_INVALID;
     d.n_oct = no;
     d.oct0 = b * kMaxOct;  // fixed slot: kernels locate an octave without reading ImgDev
     M = std::max(M, no);
@@ -286,7 +296,7 @@ sift_status Engine::fill_plan(int n, const ImgIn *in, Desc &hd, WsLayout &L, int
       od.H = hs[o];
       od.W = ws[o];
       od.pitch = (int)align_up(ws[o], 32);
-      od.wpr = (ws[o] + 31) / 32;
+      od.wpr = div_up(ws[o], kBmCols);
       od.lvl = (long long)pyr;
       od.lstride = (long long)od.H * od.pitch;
       pyr += (size_t)(S_ + 3) * od.lstride;
@@ -331,7 +341,7 @@ sift_status Engine::fill_plan(int n, const ImgIn *in, Desc &hd, WsLayout &L, int
         int t = 0;
         if (o < hd.img[b].n_oct) {
           const OctDev &od = hd.oct[hd.img[b].oct0 + o];
-          if (k == TK_EXT) t = div_up(od.W, kExtTW) * div_up(od.H, kExtTH);
+          if (k == TK_EXT) t = od.wpr * div_up(od.H, kExtTH);
           else t = div_up(od.W, kBlurTW) * div_up(od.H, tile_h_of(k));
         }
         pre[b + 1] = pre[b] + t;
@@ -519,15 +529,15 @@ cudaError_t Engine::enqueue_all(cudaStream_t s, int M, int modes, std::vector<Pr
       });
     }
     if (branch) {
-      rec_on(side, PC_EXTREMA, [&] { return launch_extrema(d, o, S_, n_sm_ * 3, side); });
+      rec_on(side, PC_EXTREMA, [&] { return launch_extrema(d, o, S_, ext_grid_, side); });
     } else if (fork) {
       for (int k = 0; k < kSides && k < M - 1; k++) {
         if (e == cudaSuccess) e = cudaEventRecord(join_ev_[k], side_[k]);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, join_ev_[k], 0);
       }
-      rec(PC_EXTREMA, [&] { return launch_extrema(d, o, S_, n_sm_ * 3, s, false); });
+      rec(PC_EXTREMA, [&] { return launch_extrema(d, o, S_, ext_grid_, s, false); });
     } else {
-      rec(PC_EXTREMA, [&] { return launch_extrema(d, o, S_, n_sm_ * 3, s); });
+      rec(PC_EXTREMA, [&] { return launch_extrema(d, o, S_, ext_grid_, s); });
     }
   }
   rec(PC_KEYPOINT, [&] { return launch_bm_compact(d, g4, s); }, 3);

@@ -49,6 +49,9 @@ class Engine {
   bool magnify(int H, int W) const;
   // Octave sizes for an input; returns the octave count.
   int octave_sizes(int H, int W, int *hs, int *ws) const;
+  // Whether an H x W input's first octave is small enough to address with
+  // 32-bit offsets within its level stack (n_scales + 3 levels < 2^32 floats).
+  bool addressable(int H, int W) const;
   // Workspace bytes a batch needs (serving admission).
   size_t workspace_bytes(int n, const int *H, const int *W) const;
   // Device-side per-image geometry of the last run (valid until the next run).
@@ -105,6 +108,7 @@ class Engine {
 
   sift_params P_;
   int dev_ = 0, n_sm_ = 0;
+  int ext_grid_ = 0;  // extrema scan grid (SMs x resident blocks)
   int S_ = 3;
   int base_R_[2] = {0, 0};  // base blur: [0] input as is, [1] 2x magnified input
   BlurTaps base_t_[2] = {};

@@ -119,6 +119,7 @@ extern "C" sift_status sift_extract_noalloc(const sift_params *p, const float *i
   Engine eng(*p);  // planning and launch sequencing only; it allocates nothing
   const sift_status ist = eng.init_noalloc();  // parameters were validated above
   if (ist != SIFT_OK) return ist;
+  if (!eng.addressable(H, W)) return SIFT_E_BUDGET;  // far beyond the scratch array
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
   std::lock_guard<std::mutex> lk(g_plan_mu);
   Desc &hd = g_host_desc;

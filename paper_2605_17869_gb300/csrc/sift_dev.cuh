@@ -4,9 +4,10 @@
 //  * Pyramid: per image, per octave o, levels 0..S+2 stored back to back, each
 //    H_o rows of `pitch` floats (pitch = W_o rounded up to 32 floats, 128 B).
 //  * Candidate bitmap: per image, per octave, per DoG layer 1..S, H_o rows of
-//    ceil(W_o / 32) 32-bit words; bit k of word w in row y marks pixel
-//    x = 32 w + k. Walking the bitmap in memory order is the canonical order
-//    (octave, layer, row, column).
+//    ceil(W_o / 30) 32-bit words; bit k (< 30) of word w in row y marks pixel
+//    x = 30 w + k (one word is the row of one extrema strip). Walking the
+//    bitmap in memory order is the canonical order (octave, layer, row,
+//    column).
 //  * Keypoint-stage arrays are per image slices of global arrays; every slice
 //    is addressed through the per-image fields of ImgDev.
 // All geometry lives in a device-side descriptor (Desc) written before each
@@ -28,8 +29,8 @@ constexpr int kDescLen = 128;      // 4 x 4 x 8
 constexpr int kOriWin = 1600;      // staged orientation window (floats, one band)
 constexpr int kBlurTW = 128;       // blur tile width (32 lanes x float4)
 constexpr int kBlurHalo = 16;      // staged columns left/right of a blur tile
-constexpr int kExtTW = 32;         // extrema tile columns (one warp)
-constexpr int kExtTH = 8;          // extrema tile rows
+constexpr int kBmCols = 30;        // columns per bitmap word = extrema strip width (one warp)
+constexpr int kExtTH = 32;         // extrema tile rows (one warp streams down them)
 constexpr int kChunk = 2048;       // compaction chunk (words or slots)
 
 // Tile-queue kinds: blur with tile height 16/32/64, extrema tiles, decimation.
@@ -197,6 +198,8 @@ cudaError_t blur_set_attributes();
 cudaError_t launch_extrema(const Desc *d, int oct, int n_scales, int grid, cudaStream_t s,
                            bool pdl = true);
 cudaError_t extrema_set_attributes();
+// Persistent grid of the extrema scan: SMs x resident blocks per SM.
+int extrema_grid(int n_sm, int n_scales);
 cudaError_t launch_bm_compact(const Desc *d, int grid, cudaStream_t s);
 cudaError_t launch_refine(const Desc *d, int grid, cudaStream_t s);
 
