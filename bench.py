@@ -245,6 +245,17 @@ def _alg_blur_bytes(shapes, upsample, S=3, min_side=16):
     return tot, px_tot
 
 
+def _pyramid_bytes(shapes, upsample, fp16, S=3, min_side=16):
+    """Device bytes of one step's Gaussian pyramids: S + 3 levels per octave,
+    rows padded to 32 elements; 4-byte elements, or 2-byte ones above octave 0
+    in the fp16 storage mode."""
+    tot = 0
+    for (h, w) in shapes:
+        for o, (H, W) in enumerate(_octaves(h, w, upsample, min_side)):
+            tot += (S + 3) * H * ((W + 31) // 32 * 32) * (2 if fp16 and o > 0 else 4)
+    return tot
+
+
 def _alg_class_bytes(shapes, upsample, S=3, min_side=16):
     """Algorithmic bytes of one step for the base blur and the extrema scan.
     Base: the input read once (4 B per input pixel) and level 0 of octave 0
@@ -459,6 +470,8 @@ def gpu_arm(args, rank, world, pool, batch):
 
     extra = {}
     if rank == 0 and not args.no_configs:
+        extra["fp16_pyramid"] = fp16_side(torch, pkg, imgs, shapes, mpix, flush, stream, tuning,
+                                          max(10, args.steps // 2))
         extra["homography_sequence"] = homography_side(torch, pkg, flush, stream, tuning,
                                                        max(10, args.steps // 2))
         extra["single_and_pair"] = other_configs(torch, pkg, flush, stream, tuning)
@@ -491,6 +504,26 @@ def gpu_arm(args, rank, world, pool, batch):
         **extra,
     }
     return res
+
+
+def fp16_side(torch, pkg, imgs, shapes, mpix, flush, stream, tuning, steps):
+    """The timed batch in the fp16 storage mode (§3.2: octaves above 0 stored
+    as binary16, octave 0 FP32): throughput, per-class time and the pyramid's
+    device bytes against the FP32 mode."""
+    ex = pkg.Extractor(upsample=0, max_kpts=MAX_KPTS, fp16_pyramid=1)
+    ex.set_tuning(tuning)
+    step = lambda: ex.extract_batch_async(imgs, stream)  # noqa: E731
+    t, _ = timed_steps(torch, step, steps, 3, flush, stream)
+    counts = ex._counts[:len(imgs)].tolist()
+    cls = profiled_classes(torch, ex, step, flush, 3)
+    ex.close()
+    return {"workload": "the timed batch with fp16_pyramid=1",
+            "ms_per_step": round(statistics.mean(t), 4),
+            "mpix_s": round(mpix * len(t) / (sum(t) / 1e3), 1),
+            "keypoints_per_step": sum(counts),
+            "kernel_ms_per_step": {k: round(v[0], 4) for k, v in cls.items()},
+            "pyramid_bytes_per_step": _pyramid_bytes(shapes, False, True),
+            "pyramid_bytes_per_step_fp32": _pyramid_bytes(shapes, False, False)}
 
 
 def homography_side(torch, pkg, flush, stream, tuning, steps):

@@ -89,6 +89,12 @@ typedef struct {
                             octave (the paper's VRAM-adaptive suppression of the
                             double image above 4 MP, §1 and §5); decided per
                             image, also within a batch; 0: no limit; >= 0 */
+  int fp16_pyramid;      /* 1: the levels of every octave above 0 are stored as
+                            IEEE binary16 (rounded to nearest, ties to even) and
+                            read back into FP32 for all arithmetic; octave 0 stays
+                            FP32 (§3.2, "fp16 storage with fp32 compute (octave 0
+                            in fp32)"), halving those octaves' pyramid memory and
+                            traffic; 0 or 1 (default 0) */
 } sift_params;
 
 /* Keypoint outputs: structure of arrays in device memory, capacity max_kpts.

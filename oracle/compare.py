@@ -27,6 +27,14 @@ SIGMA_RTOL = 1e-3
 ANGLE_TOL = 0.5
 DESC_TOL = 1e-3
 MARGIN_EPS = 1e-4
+# fp16 storage mode (levels above octave 0 stored as binary16): a stored level
+# value can differ from the oracle's by one binary16 ulp of [0, 1) values,
+# 2^-11 (the GPU rounds its FP32 result, the oracle its FP64 one), where the
+# FP32 mode's pyramid differs by at most 1e-4. Everything downstream is a
+# Lipschitz function of the level values, so the FP32 mode's position, scale,
+# angle and descriptor tolerances are scaled by the ratio of the two pyramid
+# bounds, 2^-11 / 1e-4 = 4.9, rounded up to 5.
+FP16_TOL_SCALE = 5.0
 
 
 def angle_diff(a, b):
@@ -54,9 +62,11 @@ class Match:
         return self.n_oracle - self.n_eligible
 
 
-def match(oracle_res, gpu: dict, margin_eps: float = MARGIN_EPS) -> Match:
+def match(oracle_res, gpu: dict, margin_eps: float = MARGIN_EPS, tol_scale: float = 1.0) -> Match:
     """oracle_res: oracle Result; gpu: dict of numpy arrays (x, y, sigma, angle,
-    octave, layer, desc)."""
+    octave, layer, desc); tol_scale multiplies the position, scale and angle
+    tolerances (FP16_TOL_SCALE for the fp16 storage mode)."""
+    pos_tol, sig_tol, ang_tol = POS_TOL * tol_scale, SIGMA_RTOL * tol_scale, ANGLE_TOL * tol_scale
     ox, oy, osig, oang = oracle_res.x, oracle_res.y, oracle_res.sigma, oracle_res.angle
     ooct, olay = oracle_res.octave, oracle_res.layer
     gx, gy, gsig, gang = (np.asarray(gpu[k], dtype=np.float64) for k in ("x", "y", "sigma", "angle"))
@@ -78,13 +88,13 @@ def match(oracle_res, gpu: dict, margin_eps: float = MARGIN_EPS) -> Match:
         if cand is None:
             continue
         dpos = np.maximum(np.abs(gx[cand] - ox[i]), np.abs(gy[cand] - oy[i]))
-        near = cand[dpos < POS_TOL]
+        near = cand[dpos < pos_tol]
         if len(near) == 0:
             continue
         gpu_hit[near] = True
         ds = np.abs(gsig[near] - osig[i]) / osig[i]
         da = angle_diff(gang[near], oang[i])
-        ok = near[(ds < SIGMA_RTOL) & (da < ANGLE_TOL)]
+        ok = near[(ds < sig_tol) & (da < ang_tol)]
         if not eligible[i]:
             continue
         if len(ok):

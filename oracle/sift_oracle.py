@@ -21,7 +21,7 @@ Arithmetic is float64 throughout. Each step is computed exactly as its
 definition reads: no blocking, fusion or reordering beyond it.
 
 Parity status per function:
-  gaussian_taps, blur, upsample2x, decimate, build_pyramid, dog,
+  gaussian_taps, blur, upsample2x, decimate, store_level, build_pyramid, dog,
   find_candidates, refine_candidate, orientation_histogram,
   orientation_vote_margin, smooth_histogram, orientation_peaks,
   descriptor (plain, DSP and RootSIFT), normalise_descriptor,
@@ -70,6 +70,7 @@ class Params:
     dsp_grid: int = 32           # §3.2: a 32 x 32 sample patch per DSP scale
     rootsift: bool = False       # §3.2 RootSIFT: L1 normalise, then element-wise sqrt
     upsample_max_px: int = 4_000_000  # §5: no magnification above 4 MP (0 = no limit)
+    fp16_pyramid: bool = False   # §3.2: levels of octaves above 0 stored in fp16, octave 0 in full precision
 
 
 # ------------------------------------------------------------------ A2/A3: blur
@@ -177,9 +178,23 @@ def base_sigma(p: Params) -> float:
     return math.sqrt(d) if d > 0 else 0.0
 
 
+def store_level(level: np.ndarray, o: int, p: Params) -> np.ndarray:
+    """The value a pyramid level keeps once stored (§3.2, "fp16 storage with fp32
+    compute (octave 0 in fp32)"). READING: with fp16_pyramid, every level of an
+    octave above 0 is rounded to the nearest IEEE binary16 value (ties to even)
+    as soon as it is formed, and the next level (and the next octave's
+    decimated base) is computed from the rounded values; octave 0 and the
+    default mode keep full precision."""
+    if p.fp16_pyramid and o > 0:
+        return level.astype(np.float16).astype(np.float64)
+    return level
+
+
 def build_pyramid(img: np.ndarray, p: Params):
     """Gaussian scale space (§3.2): per octave S+3 levels, each level blurred from
-    the previous one (READING of the paper's in-place construction, §4.2)."""
+    the previous one (READING of the paper's in-place construction, §4.2).
+    With fp16_pyramid every level of octaves above 0 is stored in fp16
+    (store_level)."""
     img = np.asarray(img, dtype=np.float64)
     p = for_image(img.shape[0], img.shape[1], p)
     base = upsample2x(img) if p.upsample else img
@@ -193,9 +208,9 @@ def build_pyramid(img: np.ndarray, p: Params):
         else:
             g0 = decimate(octaves[o - 1][p.n_scales])
         assert g0.shape == (h, w)
-        levels = [g0]
+        levels = [store_level(g0, o, p)]
         for k in kap:
-            levels.append(blur(levels[-1], k))
+            levels.append(store_level(blur(levels[-1], k), o, p))
         octaves.append(np.stack(levels))
     return octaves
 
@@ -385,7 +400,11 @@ def orientation_histogram(L: np.ndarray, xi: int, yi: int, sigma_oct: float, p: 
 
     READING: Gaussian window sigma_w = 1.5 sigma, square radius round(3 sigma_w),
     samples with 1 <= x <= W-2 and 1 <= y <= H-2, weight m * exp(-(i^2+j^2) /
-    (2 sigma_w^2)) with (i, j) the integer offset, nearest-bin voting.
+    (2 sigma_w^2)) with (i, j) the integer offset, nearest-bin voting
+    floor(n theta / 2 pi + 1/2). A gradient with |dx| = |dy| (theta an odd
+    multiple of 45 degrees, the only bin boundaries a gradient can hit exactly)
+    is decided exactly by that formula in integers: (n (2q + 1) + 4) // 8 for
+    quadrant q, so a half-bin value goes up.
     """
     h, w = L.shape
     n = p.ori_bins
@@ -401,7 +420,18 @@ def orientation_histogram(L: np.ndarray, xi: int, yi: int, sigma_oct: float, p: 
     th = np.where(th < 0, th + 2 * math.pi, th)
     wt = np.exp(-(i * i + j * j) / (2.0 * sw * sw))
     bins = np.floor(n * th / (2 * math.pi) + 0.5).astype(np.int64) % n
+    diag, q = _diagonal_quadrant(dx, dy)
+    bins = np.where(diag, (n * (2 * q + 1) + 4) // 8 % n, bins)
     return np.bincount(bins, weights=wt * mag, minlength=n)
+
+
+def _diagonal_quadrant(dx, dy):
+    """Gradients with |dx| = |dy| != 0 and their quadrant q (theta = 45 (2q + 1)
+    degrees: q = 0 for dx, dy > 0, 1 for dx < 0 < dy, 2 for both negative, 3
+    for dy < 0 < dx)."""
+    diag = (np.abs(dx) == np.abs(dy)) & (dx != 0)
+    q = np.where(dy > 0, np.where(dx > 0, 0, 1), np.where(dx < 0, 2, 3))
+    return diag, q
 
 
 def orientation_vote_margin(L: np.ndarray, xi: int, yi: int, sigma_oct: float, p: Params) -> float:
@@ -409,9 +439,11 @@ def orientation_vote_margin(L: np.ndarray, xi: int, yi: int, sigma_oct: float, p
     36-bin histogram): over the same window and samples, the smallest distance,
     in bins, of a voting sample's bin coordinate n * theta / 2 pi from a
     rounding boundary k + 1/2 (where the nearest bin changes). Samples of zero
-    weight do not vote. A vote within FP32 rounding of a boundary may land in
-    the neighbouring bin on the FP32 path; keypoints with a small margin are
-    the ones whose histogram is not a robust function of the image.
+    weight do not vote, and samples exactly on a boundary (|dx| = |dy|) are
+    decided exactly (orientation_histogram), so they are not near one. A vote
+    within FP32 rounding of a boundary may land in the neighbouring bin on the
+    FP32 path; keypoints with a small margin are the ones whose histogram is
+    not a robust function of the image.
     """
     h, w = L.shape
     n = p.ori_bins
@@ -426,7 +458,8 @@ def orientation_vote_margin(L: np.ndarray, xi: int, yi: int, sigma_oct: float, p
     th = np.arctan2(dy, dx)
     th = np.where(th < 0, th + 2 * math.pi, th)
     wt = np.exp(-(i * i + j * j) / (2.0 * sw * sw))
-    votes = wt * mag > 0
+    diag, _ = _diagonal_quadrant(dx, dy)
+    votes = (wt * mag > 0) & ~diag
     if not votes.any():
         return math.inf
     t = n * th[votes] / (2 * math.pi) + 0.5   # bin = floor(t) mod n; boundaries at integer t

@@ -29,7 +29,7 @@ class SiftParams(ctypes.Structure):
                 ("edge_ratio", c_float), ("border", c_int), ("max_refine_iter", c_int),
                 ("prefilter_ratio", c_float), ("ori_peak_ratio", c_float), ("max_kpts", c_int),
                 ("upright", c_int), ("dsp", c_int), ("rootsift", c_int),
-                ("upsample_max_px", c_int)]
+                ("upsample_max_px", c_int), ("fp16_pyramid", c_int)]
 
 
 class SiftKptsDev(ctypes.Structure):

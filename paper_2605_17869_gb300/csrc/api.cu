@@ -64,6 +64,7 @@ sift_status sift_params_default(sift_params *p) {
   p->dsp = 0;
   p->rootsift = 0;
   p->upsample_max_px = 4000000;
+  p->fp16_pyramid = 0;
   return SIFT_OK;
 }
 
@@ -289,10 +290,11 @@ sift_status sift_build_pyramid(sift_handle *h, const float *img_dev, int H, int 
   for (int o = 0; o < no; o++) {
     const sift::OctDev &od = hd.oct[o];
     for (int l = 0; l < L; l++) {
-      cudaError_t e = cudaMemcpy2DAsync(out_dev + off, od.W * sizeof(float),
-                                        pyr + od.lvl + (size_t)l * od.lstride,
-                                        od.pitch * sizeof(float), od.W * sizeof(float), od.H,
-                                        cudaMemcpyDeviceToDevice, s);
+      const float *lv = od.half ? reinterpret_cast<const float *>(
+                                      reinterpret_cast<const __half *>(pyr + od.lvl) + (size_t)l * od.lstride)
+                                : pyr + od.lvl + (size_t)l * od.lstride;
+      cudaError_t e = sift::launch_export_level(lv, od.half != 0, od.pitch, od.H, od.W,
+                                                out_dev + off, s);
       if (e != cudaSuccess) return fail(h, SIFT_E_CUDA, cudaGetErrorString(e));
       off += (size_t)od.H * od.W;
     }

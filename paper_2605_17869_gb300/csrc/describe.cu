@@ -8,6 +8,8 @@
 // conflicts). The columns are then summed bin by bin, warp by warp and lane by
 // lane. No atomics are used anywhere: the sum order is fixed by the code, so
 // outputs are bitwise reproducible.
+#include <type_traits>
+
 #include "scan.cuh"
 #include "sift_dev.cuh"
 
@@ -94,7 +96,10 @@ __global__ void __launch_bounds__(kKpWarps * 32) k_orientation(const Desc *__res
       const ImgDev &im = d->img[b];
       const RefRec r = d->ref[slot];
       const OctDev od = d->oct[im.oct0 + r.o];
-      const float *L = d->pyr + od.lvl + (long long)r.s * od.lstride;
+      // Level r.s of the candidate's octave: FP32, or binary16 (od.half).
+      const bool hf = od.half != 0;
+      const float *L = d->pyr + od.lvl;
+      const long long lofs = (long long)r.s * od.lstride;
       const float sw = 1.5f * sigma_of(d, r);
       const int R = (int)floorf(3.0f * sw + 0.5f);
       const float ninv = -1.0f / (2.0f * sw * sw);
@@ -106,16 +111,18 @@ __global__ void __launch_bounds__(kKpWarps * 32) k_orientation(const Desc *__res
       for (int jb = -R; jb <= R; jb += B) {
         const int nb = min(B, R - jb + 1);
         // Every copy is issued before any is waited for (cp.async, 4 bytes,
-        // zero-filled outside the image, where no byte is read).
+        // zero-filled outside the image, where no byte is read); binary16
+        // levels, which cp.async cannot copy, are loaded and widened.
         for (int rr = warp; rr < nb + 2; rr += kKpWarps) {
           const int gy = r.y + jb - 1 + rr;
           const bool row_ok = gy >= 0 && gy < od.H;
-          const float *src = L + (long long)(row_ok ? gy : 0) * od.pitch;
+          const long long rofs = lofs + (long long)(row_ok ? gy : 0) * od.pitch;
           float *dst = win + rr * wd;
           for (int c = lane; c < wd; c += 32) {
             const int gx = r.x - R - 1 + c;
             const bool ok = row_ok && gx >= 0 && gx < od.W;
-            cp_async4_zfill(dst + c, src + (ok ? gx : 0), ok);
+            if (hf) dst[c] = ok ? lvl_ld(L, true, rofs + gx) : 0.f;
+            else cp_async4_zfill(dst + c, L + rofs + (ok ? gx : 0), ok);
           }
         }
         asm volatile("cp.async.wait_all;\n" ::: "memory");
@@ -137,6 +144,13 @@ __global__ void __launch_bounds__(kKpWarps * 32) k_orientation(const Desc *__res
             if (th < 0.f) th += kTwoPi;
             int bin = (int)floorf(th * ((float)kOriBins / kTwoPi) + 0.5f);
             if (bin >= kOriBins) bin -= kOriBins;
+            // |dx| = |dy|: theta is exactly 45 (2q + 1) degrees, a bin boundary
+            // the nearest-bin rule floor(36 theta / 2 pi + 1/2) resolves upward;
+            // decided in integers rather than left to the rounding of atan2f.
+            if (fabsf(dx) == fabsf(dy) && dx != 0.f) {
+              const int q = dy > 0.f ? (dx > 0.f ? 0 : 1) : (dx < 0.f ? 2 : 3);
+              bin = (kOriBins * (2 * q + 1) + 4) / 8 % kOriBins;
+            }
             hist[warp][bin][lane] += expf((float)(i * i + j * j) * ninv) * mag;
           }
         }
@@ -451,7 +465,10 @@ __global__ void __launch_bounds__(kKpWarps * 32, 6) k_descriptor(const Desc *__r
       im.ooct[j] = r.o;
       im.olay[j] = r.s;
     }
-    const float *L = d->pyr + od.lvl + (long long)r.s * od.lstride;
+    // Level r.s of the keypoint's octave: FP32, or binary16 (od.half).
+    const bool hf = od.half != 0;
+    const float *L = d->pyr + od.lvl;
+    const long long lofs = (long long)r.s * od.lstride;
     const float wbin = 3.0f * sig;
     const float inv_w = 1.0f / wbin;
     const int R = (int)floorf(wbin * 1.41421356237f * 2.5f + 0.5f);
@@ -464,127 +481,135 @@ __global__ void __launch_bounds__(kKpWarps * 32, 6) k_descriptor(const Desc *__r
       for (int k = lane; k < kDescLen * kDescCols / 4; k += 32) h4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncwarp();
-    if (!d->dsp) {
-      // Samples: integer offsets (i, jy) in [-R, R]^2 inside the image whose
-      // rotated bin coordinates fall in (-1, 4)^2, i.e. inside a square of half
-      // side h = 2.5 bins around the keypoint. Warp w takes rows jlo + w,
-      // jlo + w + 4, ... (at most 32 of them, one per lane): each lane cuts its
-      // row to an interval, a superset of the square's chord widened by 2
-      // pixels so that rounding can only add candidates, and a warp scan lays
-      // the intervals end to end. The warp then sweeps that list 32 samples at
-      // a time, and the exact test below decides, so the sample set is the
-      // same as a sweep of the whole window.
-      const float h = 2.5f * wbin;
-      const int ilo = max(-R, 1 - r.x), ihi = min(R, od.W - 2 - r.x);
-      const int jlo = max(-R, 1 - r.y), jhi = min(R, od.H - 2 - r.y);
-      const float ica = fabsf(ct) * (float)(R + 1) < 1.0f ? 0.f : 1.0f / ct;
-      const float isa = fabsf(st) * (float)(R + 1) < 1.0f ? 0.f : -1.0f / st;
-      // Rows per warp are at most (2R + 1) / 4 + 1, i.e. 20 for the largest
-      // octave-relative scale of the default parameters; larger windows take
-      // several rounds of 32 rows.
-      for (int rb = 0; jlo + warp + kKpWarps * rb <= jhi; rb += 32) {
-        int len = 0, a0 = 0;
-        {
-          const int jy = jlo + warp + kKpWarps * (rb + lane);
-          if (jy <= jhi) {
-            const float oy = (float)jy - r.dy;
-            float lo = -1e30f, hi = 1e30f;
-            // slab a * ox + b in (-h, h) for (a, b) = (ct, st * oy), (-st, ct * oy)
-#pragma unroll
-            for (int k = 0; k < 2; k++) {
-              const float ia = k ? isa : ica, b = k ? ct * oy : st * oy;
-              if (ia == 0.f) {
-                if (fabsf(b) >= h + 2.0f) hi = -1e30f;  // |a * ox| < 1: the row misses the slab
+    // The sample sweeps, instantiated once per storage type of the level so
+    // that no load tests it.
+    auto sweep = [&](auto half_tag) {
+      constexpr bool HF = decltype(half_tag)::value;
+      if (!d->dsp) {
+        // Samples: integer offsets (i, jy) in [-R, R]^2 inside the image whose
+        // rotated bin coordinates fall in (-1, 4)^2, i.e. inside a square of half
+        // side h = 2.5 bins around the keypoint. Warp w takes rows jlo + w,
+        // jlo + w + 4, ... (at most 32 of them, one per lane): each lane cuts its
+        // row to an interval, a superset of the square's chord widened by 2
+        // pixels so that rounding can only add candidates, and a warp scan lays
+        // the intervals end to end. The warp then sweeps that list 32 samples at
+        // a time, and the exact test below decides, so the sample set is the
+        // same as a sweep of the whole window.
+        const float h = 2.5f * wbin;
+        const int ilo = max(-R, 1 - r.x), ihi = min(R, od.W - 2 - r.x);
+        const int jlo = max(-R, 1 - r.y), jhi = min(R, od.H - 2 - r.y);
+        const float ica = fabsf(ct) * (float)(R + 1) < 1.0f ? 0.f : 1.0f / ct;
+        const float isa = fabsf(st) * (float)(R + 1) < 1.0f ? 0.f : -1.0f / st;
+        // Rows per warp are at most (2R + 1) / 4 + 1, i.e. 20 for the largest
+        // octave-relative scale of the default parameters; larger windows take
+        // several rounds of 32 rows.
+        for (int rb = 0; jlo + warp + kKpWarps * rb <= jhi; rb += 32) {
+          int len = 0, a0 = 0;
+          {
+            const int jy = jlo + warp + kKpWarps * (rb + lane);
+            if (jy <= jhi) {
+              const float oy = (float)jy - r.dy;
+              float lo = -1e30f, hi = 1e30f;
+              // slab a * ox + b in (-h, h) for (a, b) = (ct, st * oy), (-st, ct * oy)
+  #pragma unroll
+              for (int k = 0; k < 2; k++) {
+                const float ia = k ? isa : ica, b = k ? ct * oy : st * oy;
+                if (ia == 0.f) {
+                  if (fabsf(b) >= h + 2.0f) hi = -1e30f;  // |a * ox| < 1: the row misses the slab
+                } else {
+                  const float e0 = (-h - b) * ia, e1 = (h - b) * ia;
+                  lo = fmaxf(lo, fminf(e0, e1));
+                  hi = fminf(hi, fmaxf(e0, e1));
+                }
+              }
+              int a1 = ihi;
+              a0 = ilo;
+              if (hi < lo) {
+                a1 = a0 - 1;
               } else {
-                const float e0 = (-h - b) * ia, e1 = (h - b) * ia;
-                lo = fmaxf(lo, fminf(e0, e1));
-                hi = fminf(hi, fmaxf(e0, e1));
+                if (lo + r.dx > (float)ilo) a0 = max(ilo, (int)floorf(lo + r.dx) - 2);
+                if (hi + r.dx < (float)ihi) a1 = min(ihi, (int)ceilf(hi + r.dx) + 2);
+              }
+              len = max(0, a1 - a0 + 1);
+            }
+          }
+          // Exclusive scan of the interval lengths over the warp's rows.
+          int pre = len;
+  #pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, pre, o);
+            if (lane >= o) pre += v;
+          }
+          const int tot = __shfl_sync(0xffffffffu, pre, 31);
+          pre -= len;
+          int *wlo = s_lo[warp], *wpre = s_pre[warp];
+          wlo[lane] = a0;
+          wpre[lane] = pre;
+          if (lane == 31) wpre[32] = tot;
+          __syncwarp();
+          int row = 0;
+          // Warp-uniform trip count: every lane reaches the commit's __syncwarp.
+          for (int q0 = 0; q0 < tot; q0 += 32) {
+            const int q = q0 + lane;
+            bool ok = q < tot;
+            Vote vt;
+            if (ok) {
+              while (wpre[row + 1] <= q) row++;
+              const int jy = jlo + warp + kKpWarps * (rb + row);
+              const int i = wlo[row] + (q - wpre[row]);
+              const float ox = (float)i - r.dx, oy = (float)jy - r.dy;
+              const float rx = (ct * ox + st * oy) * inv_w;
+              const float ry = (-st * ox + ct * oy) * inv_w;
+              const float u = rx + 1.5f, v = ry + 1.5f;
+              ok = u > -1.f && u < 4.f && v > -1.f && v < 4.f;
+              if (ok) {
+                const long long q = lofs + (long long)(r.y + jy) * od.pitch + (r.x + i);
+                const float gx = lvl_ld(L, HF, q + 1) - lvl_ld(L, HF, q - 1);
+                const float gy = lvl_ld(L, HF, q + od.pitch) - lvl_ld(L, HF, q - od.pitch);
+                desc_targets(vt, rx, ry, gx, gy, th);
               }
             }
-            int a1 = ihi;
-            a0 = ilo;
-            if (hi < lo) {
-              a1 = a0 - 1;
-            } else {
-              if (lo + r.dx > (float)ilo) a0 = max(ilo, (int)floorf(lo + r.dx) - 2);
-              if (hi + r.dx < (float)ihi) a1 = min(ihi, (int)ceilf(hi + r.dx) + 2);
+            desc_commit(hist, lane, ok, vt);
+          }
+          __syncwarp();  // the next round rewrites this warp's interval table
+        }
+      } else {
+        for (int f = 0; f < 5; f++) {
+          const float wb = wbin * kDspScale[f];
+          for (int idx = tid; idx < 32 * 32; idx += kKpWarps * 32) {
+            const float rx = ((float)(idx & 31) + 0.5f) * 0.125f - 2.0f;
+            const float ry = ((float)(idx >> 5) + 0.5f) * 0.125f - 2.0f;
+            const float xr = r.dx + wb * (ct * rx - st * ry);  // relative to pixel (r.x, r.y)
+            const float yr = r.dy + wb * (st * rx + ct * ry);
+            const float xf = floorf(xr), yf = floorf(yr);
+            const int x0 = r.x + (int)xf, y0 = r.y + (int)yf;
+            const bool ok = !(x0 < 1 || x0 > od.W - 3 || y0 < 1 || y0 > od.H - 3);
+            Vote vt;
+            if (!ok) {  // (1024 samples per scale: the trip count is warp-uniform)
+              desc_commit(hist, lane, false, vt);
+              continue;
             }
-            len = max(0, a1 - a0 + 1);
+            const float fx = xr - xf, fy = yr - yf, gx1 = 1.f - fx, gy1 = 1.f - fy;
+            const long long p = lofs + (long long)y0 * od.pitch + x0;
+            const long long pm = p - od.pitch, pp = p + od.pitch, p2 = pp + od.pitch;
+            auto at = [&](long long i) { return lvl_ld(L, HF, i); };
+            // L(x + 1, y) - L(x - 1, y) and L(x, y + 1) - L(x, y - 1), bilinear
+            const float xp = gy1 * (gx1 * at(p + 1) + fx * at(p + 2)) +
+                             fy * (gx1 * at(pp + 1) + fx * at(pp + 2));
+            const float xm = gy1 * (gx1 * at(p - 1) + fx * at(p)) +
+                             fy * (gx1 * at(pp - 1) + fx * at(pp));
+            const float yp = gy1 * (gx1 * at(pp) + fx * at(pp + 1)) +
+                             fy * (gx1 * at(p2) + fx * at(p2 + 1));
+            const float ym = gy1 * (gx1 * at(pm) + fx * at(pm + 1)) +
+                             fy * (gx1 * at(p) + fx * at(p + 1));
+            desc_targets(vt, rx, ry, xp - xm, yp - ym, th);
+            desc_commit(hist, lane, true, vt);
           }
-        }
-        // Exclusive scan of the interval lengths over the warp's rows.
-        int pre = len;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int v = __shfl_up_sync(0xffffffffu, pre, o);
-          if (lane >= o) pre += v;
-        }
-        const int tot = __shfl_sync(0xffffffffu, pre, 31);
-        pre -= len;
-        int *wlo = s_lo[warp], *wpre = s_pre[warp];
-        wlo[lane] = a0;
-        wpre[lane] = pre;
-        if (lane == 31) wpre[32] = tot;
-        __syncwarp();
-        int row = 0;
-        // Warp-uniform trip count: every lane reaches the commit's __syncwarp.
-        for (int q0 = 0; q0 < tot; q0 += 32) {
-          const int q = q0 + lane;
-          bool ok = q < tot;
-          Vote vt;
-          if (ok) {
-            while (wpre[row + 1] <= q) row++;
-            const int jy = jlo + warp + kKpWarps * (rb + row);
-            const int i = wlo[row] + (q - wpre[row]);
-            const float ox = (float)i - r.dx, oy = (float)jy - r.dy;
-            const float rx = (ct * ox + st * oy) * inv_w;
-            const float ry = (-st * ox + ct * oy) * inv_w;
-            const float u = rx + 1.5f, v = ry + 1.5f;
-            ok = u > -1.f && u < 4.f && v > -1.f && v < 4.f;
-            if (ok) {
-              const float *p = L + (long long)(r.y + jy) * od.pitch + (r.x + i);
-              const float gx = __ldg(p + 1) - __ldg(p - 1);
-              const float gy = __ldg(p + od.pitch) - __ldg(p - od.pitch);
-              desc_targets(vt, rx, ry, gx, gy, th);
-            }
-          }
-          desc_commit(hist, lane, ok, vt);
-        }
-        __syncwarp();  // the next round rewrites this warp's interval table
-      }
-    } else {
-      for (int f = 0; f < 5; f++) {
-        const float wb = wbin * kDspScale[f];
-        for (int idx = tid; idx < 32 * 32; idx += kKpWarps * 32) {
-          const float rx = ((float)(idx & 31) + 0.5f) * 0.125f - 2.0f;
-          const float ry = ((float)(idx >> 5) + 0.5f) * 0.125f - 2.0f;
-          const float xr = r.dx + wb * (ct * rx - st * ry);  // relative to pixel (r.x, r.y)
-          const float yr = r.dy + wb * (st * rx + ct * ry);
-          const float xf = floorf(xr), yf = floorf(yr);
-          const int x0 = r.x + (int)xf, y0 = r.y + (int)yf;
-          const bool ok = !(x0 < 1 || x0 > od.W - 3 || y0 < 1 || y0 > od.H - 3);
-          Vote vt;
-          if (!ok) {  // (1024 samples per scale: the trip count is warp-uniform)
-            desc_commit(hist, lane, false, vt);
-            continue;
-          }
-          const float fx = xr - xf, fy = yr - yf, gx1 = 1.f - fx, gy1 = 1.f - fy;
-          const float *p = L + (long long)y0 * od.pitch + x0;
-          const float *pm = p - od.pitch, *pp = p + od.pitch, *p2 = pp + od.pitch;
-          // L(x + 1, y) - L(x - 1, y) and L(x, y + 1) - L(x, y - 1), bilinear
-          const float xp = gy1 * (gx1 * __ldg(p + 1) + fx * __ldg(p + 2)) +
-                           fy * (gx1 * __ldg(pp + 1) + fx * __ldg(pp + 2));
-          const float xm = gy1 * (gx1 * __ldg(p - 1) + fx * __ldg(p)) +
-                           fy * (gx1 * __ldg(pp - 1) + fx * __ldg(pp));
-          const float yp = gy1 * (gx1 * __ldg(pp) + fx * __ldg(pp + 1)) +
-                           fy * (gx1 * __ldg(p2) + fx * __ldg(p2 + 1));
-          const float ym = gy1 * (gx1 * __ldg(pm) + fx * __ldg(pm + 1)) +
-                           fy * (gx1 * __ldg(p) + fx * __ldg(p + 1));
-          desc_targets(vt, rx, ry, xp - xm, yp - ym, th);
-          desc_commit(hist, lane, true, vt);
         }
       }
-    }
+    };
+    if (hf) sweep(std::true_type{});
+    else sweep(std::false_type{});
     __syncthreads();
     // Bin tid: per warp, the 16 columns starting at column (tid / 2) % 16 (with
     // the layout [bin][16], the 32 threads of a warp then read 32 distinct

@@ -127,7 +127,10 @@ __device__ __forceinline__ void ext_test(const ExtRow<S> &P, const ExtRow<S> &C,
 // is done from registers. The candidate decisions are exact comparisons of
 // the same FP32 values, so they do not depend on the tiling. Bitmap words are
 // written by ballots; no atomics.
-template <int S>
+// HALF: the octave's levels are binary16 (fp16 storage mode). cp.async has no
+// 2-byte copy, so a row is then loaded into registers when it is issued and
+// written to its ring slot (widened to FP32) at the next issue, one row later.
+template <int S, bool HALF>
 __global__ void __launch_bounds__(kExtThreads, 5) k_extrema(const Desc *__restrict__ d, int oct) {
   constexpr int WPB = kExtThreads / 32;
   constexpr int SLOT = (S + 3) * 32;
@@ -151,11 +154,19 @@ __global__ void __launch_bounds__(kExtThreads, 5) k_extrema(const Desc *__restri
     const int x = tx * kBmCols - 1 + lane;
     const int y0 = ty * kExtTH, y1 = min(y0 + kExtTH, H);
     const float *lp[S + 3];
+    const __half *lph[S + 3];
     {
-      const float *G = d->pyr + od.lvl + min(max(x, 0), W - 1);
+      const int xc = min(max(x, 0), W - 1);
+      const float *G = d->pyr + od.lvl + xc;
+      const __half *Gh = reinterpret_cast<const __half *>(d->pyr + od.lvl) + xc;
 #pragma unroll
-      for (int l = 0; l < S + 3; l++) lp[l] = G + l * ls;
+      for (int l = 0; l < S + 3; l++) {
+        lp[l] = G + l * ls;
+        lph[l] = Gh + l * ls;
+      }
     }
+    float pend[S + 3];
+    float *pend_slot = nullptr;
     float *mine_ring = my + lane;
     const bool xin = lane >= 1 && lane <= kBmCols && x >= bord && x < W - bord;
     uint32_t *bmw = d->bm + od.bm + (long long)lane * H * od.wpr + tx;
@@ -164,6 +175,20 @@ __global__ void __launch_bounds__(kExtThreads, 5) k_extrema(const Desc *__restri
     // row, empty past the end, so that the number of pending groups is fixed.
     const int n_rows = y1 - y0 + 2;
     auto issue = [&](int k) {
+      if (HALF) {
+        if (pend_slot) {
+#pragma unroll
+          for (int l = 0; l < S + 3; l++) pend_slot[l * 32] = pend[l];
+          pend_slot = nullptr;
+        }
+        if (k < n_rows) {
+          const long long ro = (long long)min(max(y0 - 1 + k, 0), H - 1) * pitch;
+#pragma unroll
+          for (int l = 0; l < S + 3; l++) pend[l] = __half2float(__ldg(lph[l] + ro));
+          pend_slot = mine_ring + (k & (kExtRing - 1)) * SLOT;
+        }
+        return;
+      }
       if (k < n_rows) {
         const int row = min(max(y0 - 1 + k, 0), H - 1);
         ext_issue<S>(mine_ring + (k & (kExtRing - 1)) * SLOT, lp, row * pitch);
@@ -198,6 +223,7 @@ __global__ void __launch_bounds__(kExtThreads, 5) k_extrema(const Desc *__restri
       step(C, A, B, y + 2);
     }
     cp_async_wait<0>();  // no copy of this strip outlives it
+    __syncwarp();
   }
 }
 
@@ -323,6 +349,7 @@ __global__ void __launch_bounds__(kThreads) k_refine(const Desc *__restrict__ d)
     int s = cd.y, y = cd.z, x = cd.w;
     const OctDev od = d->oct[im.oct0 + o];
     const float *G = d->pyr + od.lvl;
+    const bool hf = od.half != 0;
     const long long ls = od.lstride;
     const int pitch = od.pitch;
     int code = RC_NOCONV;
@@ -333,14 +360,13 @@ __global__ void __launch_bounds__(kThreads) k_refine(const Desc *__restrict__ d)
       float v[3][3][3];
 #pragma unroll
       for (int a = 0; a < 3; a++) {
-        const float *g0 = G + (long long)(s + a - 1) * ls;
-        const float *g1 = g0 + ls;
+        const long long l0 = (long long)(s + a - 1) * ls;
 #pragma unroll
         for (int bb = 0; bb < 3; bb++)
 #pragma unroll
           for (int cc = 0; cc < 3; cc++) {
-            const long long off = (long long)(y + bb - 1) * pitch + (x + cc - 1);
-            v[a][bb][cc] = __ldg(g1 + off) - __ldg(g0 + off);
+            const long long off = l0 + (long long)(y + bb - 1) * pitch + (x + cc - 1);
+            v[a][bb][cc] = lvl_ld(G, hf, off + ls) - lvl_ld(G, hf, off);
           }
       }
       c = v[1][1][1];
@@ -399,21 +425,25 @@ int extrema_grid(int n_sm, int n_scales) {
   int nb = 0;
   cudaError_t e = cudaErrorInvalidValue;
   switch (n_scales) {
-    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extrema<2>, kExtThreads, 0); break;
-    case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extrema<3>, kExtThreads, 0); break;
-    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extrema<4>, kExtThreads, 0); break;
-    case 5: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extrema<5>, kExtThreads, 0); break;
-    case 6: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extrema<6>, kExtThreads, 0); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extrema<2, false>, kExtThreads, 0); break;
+    case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extrema<3, false>, kExtThreads, 0); break;
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extrema<4, false>, kExtThreads, 0); break;
+    case 5: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extrema<5, false>, kExtThreads, 0); break;
+    case 6: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extrema<6, false>, kExtThreads, 0); break;
     default: break;
   }
   return n_sm * ((e == cudaSuccess && nb > 0) ? nb : 1);
 }
 
-cudaError_t launch_extrema(const Desc *d, int oct, int n_scales, int grid, cudaStream_t s, bool pdl) {
-#define EXT_CASE(SS)                                                               \
-  case SS:                                                                         \
-    if (pdl) return launch_pdl(k_extrema<SS>, grid, kExtThreads, 0, s, d, oct);     \
-    return launch_plain(k_extrema<SS>, grid, kExtThreads, 0, s, d, oct);
+cudaError_t launch_extrema(const Desc *d, int oct, int n_scales, int grid, cudaStream_t s, bool pdl,
+                           bool half) {
+#define EXT_CASE(SS)                                                                       \
+  case SS:                                                                                 \
+    if (half)                                                                              \
+      return pdl ? launch_pdl(k_extrema<SS, true>, grid, kExtThreads, 0, s, d, oct)          \
+                 : launch_plain(k_extrema<SS, true>, grid, kExtThreads, 0, s, d, oct);       \
+    return pdl ? launch_pdl(k_extrema<SS, false>, grid, kExtThreads, 0, s, d, oct)           \
+               : launch_plain(k_extrema<SS, false>, grid, kExtThreads, 0, s, d, oct);
   switch (n_scales) {
     EXT_CASE(2)
     EXT_CASE(3)

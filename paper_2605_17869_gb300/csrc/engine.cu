@@ -80,6 +80,7 @@ sift_status validate_params(const sift_params &p, std::string *why) {
   if (p.max_kpts < 1) return bad("max_kpts must be >= 1");
   if (p.dsp != 0 && p.dsp != 1) return bad("dsp must be 0 or 1");
   if (p.upsample_max_px < 0) return bad("upsample_max_px must be >= 0");
+  if (p.fp16_pyramid != 0 && p.fp16_pyramid != 1) return bad("fp16_pyramid must be 0 or 1");
   BlurTaps t;
   // Base blur of each mode in use: magnified first octaves when upsampling,
   // the input as is without upsampling or for images above upsample_max_px.
@@ -243,7 +244,7 @@ size_t Engine::workspace_bytes(int n, const int *H, const int *W) const {
     long long px = 0, words = 0;
     for (int o = 0; o < no; o++) {
       const long long pitch = align_up(ws[o], 32);
-      pyr += (size_t)(S_ + 3) * hs[o] * pitch;
+      pyr += (size_t)(S_ + 3) * hs[o] * pitch / (half_octave(o) ? 2 : 1);
       words += (long long)S_ * hs[o] * div_up(ws[o], kBmCols);
       px += (long long)hs[o] * ws[o];
     }
@@ -271,6 +272,7 @@ sift_status Engine::fill_plan(int n, const ImgIn *in, Desc &hd, WsLayout &L, int
   hd.upright = P_.upright ? 1 : 0;
   hd.rootsift = P_.rootsift ? 1 : 0;
   hd.dsp = P_.dsp ? 1 : 0;
+  hd.fp16 = P_.fp16_pyramid ? 1 : 0;
   hd.ori_peak_ratio = P_.ori_peak_ratio;
   size_t pyr = 0, bm = 0, cand = 0, ori = 0, fin = 0;
   int bmc = 0, cc = 0, M = 0;
@@ -299,7 +301,11 @@ sift_status Engine::fill_plan(int n, const ImgIn *in, Desc &hd, WsLayout &L, int
       od.wpr = div_up(ws[o], kBmCols);
       od.lvl = (long long)pyr;
       od.lstride = (long long)od.H * od.pitch;
-      pyr += (size_t)(S_ + 3) * od.lstride;
+      od.half = half_octave(o) ? 1 : 0;
+      od.pad = 0;
+      // Pitches are multiples of 32 elements, so a binary16 octave also starts
+      // and keeps its rows on 64-byte boundaries.
+      pyr += (size_t)(S_ + 3) * od.lstride / (od.half ? 2 : 1);
       od.bm = (long long)bm;
       bm += (size_t)S_ * od.H * od.wpr;
       px += (long long)od.H * od.W;
@@ -464,7 +470,7 @@ cudaError_t Engine::enqueue_pyramid(cudaStream_t s, int M, int modes, std::vecto
       const int kind = o == 0 ? tun_.lvl_kind[l] : TK_BLUR32;  // tuned on octave 0 only
       rec(PC_BLUR, [&] {
         return launch_level_blur(d, o, l, lvl_R_[l], lvl_t_[l], kind, grid_blur(lvl_R_[l], kind, 0), s,
-                                 o > 0 && l == 1);
+                                 o > 0 && l == 1, true, storage(o, l));
       });
     }
   }
@@ -525,19 +531,20 @@ cudaError_t Engine::enqueue_all(cudaStream_t s, int M, int modes, std::vector<Pr
       }
       rec_on(on_side ? side : s, PC_BLUR, [&] {
         return launch_level_blur(d, o, l, lvl_R_[l], lvl_t_[l], kind, grid_blur(lvl_R_[l], kind, 0),
-                                 on_side ? side : s, o > 0 && l == 1, !(on_side && l == S_ + 1));
+                                 on_side ? side : s, o > 0 && l == 1, !(on_side && l == S_ + 1),
+                                 storage(o, l));
       });
     }
     if (branch) {
-      rec_on(side, PC_EXTREMA, [&] { return launch_extrema(d, o, S_, ext_grid_, side); });
+      rec_on(side, PC_EXTREMA, [&] { return launch_extrema(d, o, S_, ext_grid_, side, true, half_octave(o)); });
     } else if (fork) {
       for (int k = 0; k < kSides && k < M - 1; k++) {
         if (e == cudaSuccess) e = cudaEventRecord(join_ev_[k], side_[k]);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, join_ev_[k], 0);
       }
-      rec(PC_EXTREMA, [&] { return launch_extrema(d, o, S_, ext_grid_, s, false); });
+      rec(PC_EXTREMA, [&] { return launch_extrema(d, o, S_, ext_grid_, s, false, half_octave(o)); });
     } else {
-      rec(PC_EXTREMA, [&] { return launch_extrema(d, o, S_, ext_grid_, s); });
+      rec(PC_EXTREMA, [&] { return launch_extrema(d, o, S_, ext_grid_, s, true, half_octave(o)); });
     }
   }
   rec(PC_KEYPOINT, [&] { return launch_bm_compact(d, g4, s); }, 3);

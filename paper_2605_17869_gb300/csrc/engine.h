@@ -49,6 +49,14 @@ class Engine {
   bool magnify(int H, int W) const;
   // Octave sizes for an input; returns the octave count.
   int octave_sizes(int H, int W, int *hs, int *ws) const;
+  // Octave o's levels are stored as binary16 (fp16 storage mode, octaves > 0).
+  bool half_octave(int o) const { return P_.fp16_pyramid && o > 0; }
+  // Storage mode of the launch that writes level l of octave o (see
+  // launch_level_blur): 0 FP32, 1 FP32 source into binary16, 2 binary16.
+  int storage(int o, int l) const {
+    if (!half_octave(o)) return 0;
+    return (l == 1 && !half_octave(o - 1)) ? 1 : 2;
+  }
   // Whether an H x W input's first octave is small enough to address with
   // 32-bit offsets within its level stack (n_scales + 3 levels < 2^32 floats).
   bool addressable(int H, int W) const;

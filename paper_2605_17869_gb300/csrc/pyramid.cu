@@ -221,7 +221,21 @@ __device__ __forceinline__ void col_pass(const float *s_in, float *s_v, const Bl
 //           for i = 1..R-1, out = fma(w0, v[s], a.x) + a.y.
 // The parity of s is that of the output's column, so the order of operations
 // is a fixed function of the pixel, independent of tiling.
-template <int R, int TH>
+// Store four adjacent outputs: FP32, or (DH) rounded to binary16.
+template <bool DH>
+__device__ __forceinline__ void store4(float *out, long long idx, float a, float b, float c, float e) {
+  if (DH) {
+    const __half2 lo = __floats2half2_rn(a, b), hi = __floats2half2_rn(c, e);
+    uint2 u;
+    u.x = *reinterpret_cast<const unsigned *>(&lo);
+    u.y = *reinterpret_cast<const unsigned *>(&hi);
+    *reinterpret_cast<uint2 *>(reinterpret_cast<__half *>(out) + idx) = u;
+  } else {
+    *reinterpret_cast<float4 *>(out + idx) = make_float4(a, b, c, e);
+  }
+}
+
+template <int R, int TH, bool DH = false>
 __device__ __forceinline__ void row_pass_store(const float *s_v, float *out, int pitch, int H,
                                                int x0, int y0, const BlurTaps &tp) {
   constexpr int OFF = RowSpan<R>::OFF;
@@ -230,8 +244,8 @@ __device__ __forceinline__ void row_pass_store(const float *s_v, float *out, int
   const int x = x0 + 4 * lane;
   const bool xok = x < pitch;
   const float *sp = s_v + warp * kSinW + RowSpan<R>::C0 + 4 * lane;
-  float *op = out + (long long)(y0 + warp) * pitch + x;
-  for (int v = warp; v < TH; v += kWarps, sp += kWarps * kSinW, op += (long long)kWarps * pitch) {
+  long long oi = (long long)(y0 + warp) * pitch + x;
+  for (int v = warp; v < TH; v += kWarps, sp += kWarps * kSinW, oi += (long long)kWarps * pitch) {
     const float4 *s4 = reinterpret_cast<const float4 *>(sp);
     float in[NV * 4];
 #pragma unroll
@@ -257,7 +271,7 @@ __device__ __forceinline__ void row_pass_store(const float *s_v, float *out, int
         o[k] = __fadd_rn(fmaf(tp.w[0], in[s], a.x), a.y);
       }
     }
-    if (y0 + v < H && xok) *reinterpret_cast<float4 *>(op) = make_float4(o[0], o[1], o[2], o[3]);
+    if (y0 + v < H && xok) store4<DH>(out, oi, o[0], o[1], o[2], o[3]);
   }
 }
 
@@ -301,7 +315,16 @@ struct TileGeo {
 
 // Geometry of flattened tile t. Image b's octaves sit at fixed slots
 // oct[b * kMaxOct + o], so no ImgDev read is needed for pyramid levels.
-template <int TH, int MODE>
+// Element st of plane p, for planes of 4-byte (half false) or 2-byte elements.
+__device__ __forceinline__ float *elem_ptr(float *p, long long st, bool half) {
+  return half ? reinterpret_cast<float *>(reinterpret_cast<__half *>(p) + st) : p + st;
+}
+
+// ST: storage of the source and the output. 0: FP32 in and out; 1: FP32 source,
+// binary16 output (the first level of octave 1 in the fp16 storage mode);
+// 2: binary16 in and out (octaves above 1, and every level after the first of
+// octave 1).
+template <int TH, int MODE, int ST = 0>
 __device__ __forceinline__ TileGeo tile_geo(const Desc *__restrict__ d, const int *pre, int oct,
                                             int lvl_out, int t) {
   TileGeo g;
@@ -312,16 +335,16 @@ __device__ __forceinline__ TileGeo tile_geo(const Desc *__restrict__ d, const in
   g.W = od.W;
   float *lv = d->pyr + od.lvl;
   g.out0 = lv;
-  g.out = lv + (long long)lvl_out * od.lstride;
+  g.out = elem_ptr(lv, (long long)lvl_out * od.lstride, ST != 0);
   g.sh = 0;
   g.sw = 0;
   if (MODE == 0) {
-    g.src = lv + (long long)(lvl_out - 1) * od.lstride;
+    g.src = elem_ptr(lv, (long long)(lvl_out - 1) * od.lstride, ST == 2);
     g.spitch = od.pitch;
     g.vec = 1;
   } else if (MODE == 3) {
     const OctDev op = d->oct[b * kMaxOct + oct - 1];
-    g.src = d->pyr + op.lvl + (long long)d->n_scales * op.lstride;
+    g.src = elem_ptr(d->pyr + op.lvl, (long long)d->n_scales * op.lstride, ST == 2);
     g.spitch = op.pitch;
     g.vec = 0;
   } else {
@@ -358,15 +381,72 @@ __device__ __forceinline__ void stage_decim_issue(const float *__restrict__ src,
 }
 
 // Store the tile's own rows / columns of the staged (decimated) level 0.
-template <int R, int TH>
+template <int R, int TH, bool DH = false>
 __device__ __forceinline__ void store_level0(const float *s_in, float *out0, int pitch, int H,
                                              int x0, int y0) {
   for (int q = threadIdx.x; q < TH * (kBlurTW / 4); q += kThreads) {
     const int v = q / (kBlurTW / 4), g = q - v * (kBlurTW / 4);
     const int y = y0 + v, x = x0 + 4 * g;
-    if (y < H && x < pitch)
-      *reinterpret_cast<float4 *>(out0 + (long long)y * pitch + x) =
-          *reinterpret_cast<const float4 *>(s_in + (R + v) * kSinW + kBlurHalo + 4 * g);
+    if (y < H && x < pitch) {
+      const float4 f = *reinterpret_cast<const float4 *>(s_in + (R + v) * kSinW + kBlurHalo + 4 * g);
+      store4<DH>(out0, (long long)y * pitch + x, f.x, f.y, f.z, f.w);
+    }
+  }
+}
+
+// Staging by plain loads, for the storage modes that cp.async cannot serve: a
+// binary16 source is widened to FP32 on the way into shared memory, and the
+// decimated base of a binary16 octave (MODE 3, ST 1 or 2) is rounded to
+// binary16 first, so that the level-1 blur reads the values level 0 stores.
+// Rows [y0 - R, y0 + rows - R) x columns [x0 - 16, x0 + 144), reflect-101 in
+// the octave's own domain; MODE 3 samples (2y, 2x) of the previous octave.
+template <int MODE, int ST>
+__device__ __forceinline__ void stage_sync(const TileGeo &g, int R, int rows, float *s_in) {
+  const int xb = g.x0 - kBlurHalo, yb = g.y0 - R;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const __half *src16 = reinterpret_cast<const __half *>(g.src);
+  if (MODE == 0 && ST == 2 && xb >= 0 && xb + kSinW <= g.W && yb >= 0 && yb + rows <= g.H) {
+    // Interior tile of a binary16 level: 16-byte loads of 8 values (rows start
+    // on 64-byte boundaries and xb is a multiple of 16), four in flight per
+    // thread, widened into two float4 stores each.
+    constexpr int NG8 = kSinW / 8;  // 20 groups of 8 columns per row
+    const int n = rows * NG8;
+    for (int i0 = threadIdx.x; i0 < n; i0 += 4 * kThreads) {
+      uint4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const int i = i0 + u * kThreads;
+        if (i < n) {
+          const int r = i / NG8, c8 = i - r * NG8;
+          v[u] = *reinterpret_cast<const uint4 *>(src16 + (long long)(yb + r) * g.spitch + xb + 8 * c8);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const int i = i0 + u * kThreads;
+        if (i < n) {
+          const int r = i / NG8, c8 = i - r * NG8;
+          const __half2 *h = reinterpret_cast<const __half2 *>(&v[u]);
+          const float2 a = __half22float2(h[0]), b = __half22float2(h[1]);
+          const float2 c = __half22float2(h[2]), e = __half22float2(h[3]);
+          float4 *dst = reinterpret_cast<float4 *>(s_in + r * kSinW + 8 * c8);
+          dst[0] = make_float4(a.x, a.y, b.x, b.y);
+          dst[1] = make_float4(c.x, c.y, e.x, e.y);
+        }
+      }
+    }
+    return;
+  }
+  for (int r = warp; r < rows; r += kWarps) {
+    const int gy = refl101(yb + r, g.H);
+    const long long row = (long long)(MODE == 3 ? 2 * gy : gy) * g.spitch;
+    for (int c = lane; c < kSinW; c += 32) {
+      const int gx = refl101(xb + c, g.W);
+      const long long idx = row + (MODE == 3 ? 2 * gx : gx);
+      float v = ST == 2 ? __half2float(src16[idx]) : g.src[idx];
+      if (MODE == 3) v = __half2float(__float2half_rn(v));
+      s_in[r * kSinW + c] = v;
+    }
   }
 }
 
@@ -389,10 +469,12 @@ __device__ __forceinline__ void stage_interior(const float *__restrict__ src, in
     if (i + 1 < NIT || r0 + i * RPP < ROWS) cp_async16_u(d0 + i * RPP * kSinW * 4, p + i * step);
 }
 
-template <int R, int TH, int MODE>
+template <int R, int TH, int MODE, int ST = 0>
 __device__ __forceinline__ void issue_stage(const TileGeo &g, float *dst) {
   constexpr int ROWS = TH + 2 * R;
-  if (MODE == 3) {
+  if (ST != 0) {
+    stage_sync<MODE, ST>(g, R, ROWS, dst);
+  } else if (MODE == 3) {
     stage_decim_issue(g.src, g.spitch, g.H, g.W, g.x0, g.y0, R, ROWS, dst);
   } else {
     const int xb = g.x0 - kBlurHalo, yb = g.y0 - R;
@@ -414,7 +496,7 @@ __device__ __forceinline__ void issue_stage(const TileGeo &g, float *dst) {
 // synchronously). With three or four blocks per SM this measured faster than
 // a second buffer with fewer blocks.
 constexpr int kGeoChunk = 32;
-template <int R, int TH, int MODE>
+template <int R, int TH, int MODE, int ST = 0>
 __global__ void __launch_bounds__(kThreads, TH == 32 ? (MODE == 0 ? 4 : 3) : 1)
     k_blur(const Desc *__restrict__ d, int oct, int lvl_out, BlurTaps tp) {
   constexpr int ROWS = TH + 2 * R;
@@ -432,23 +514,23 @@ __global__ void __launch_bounds__(kThreads, TH == 32 ? (MODE == 0 ? 4 : 3) : 1)
   const int n_mine = (total - t0 + G - 1) / G;  // tiles of this block
   auto fill_chunk = [&](int m) {                // tiles 32 m .. 32 m + 31, by warp 0
     const int k = m * kGeoChunk + (int)threadIdx.x;
-    if (k < n_mine) geo[k & (2 * kGeoChunk - 1)] = tile_geo<TH, MODE>(d, pre, oct, lvl_out, t0 + k * G);
+    if (k < n_mine) geo[k & (2 * kGeoChunk - 1)] = tile_geo<TH, MODE, ST>(d, pre, oct, lvl_out, t0 + k * G);
   };
   if (threadIdx.x < 32) fill_chunk(0);
   __syncthreads();
   pdl_wait();  // the source level is the previous kernel's output
-  issue_stage<R, TH, MODE>(geo[0], s_in);
+  issue_stage<R, TH, MODE, ST>(geo[0], s_in);
   for (int k = 0; k < n_mine; k++) {
     if (k + 1 == n_mine) pdl_trigger();  // successors launch during this block's last tile
     const TileGeo &g = geo[k & (2 * kGeoChunk - 1)];
     const TileGeo &gn = geo[(k + 1) & (2 * kGeoChunk - 1)];
     cp_async_wait_all();
     __syncthreads();
-    if (MODE == 3) store_level0<R, TH>(s_in, g.out0, g.pitch, g.H, g.x0, g.y0);
+    if (MODE == 3) store_level0<R, TH, ST != 0>(s_in, g.out0, g.pitch, g.H, g.x0, g.y0);
     col_pass<R, TH>(s_in, s_v, tp);
     __syncthreads();
-    if (k + 1 < n_mine) issue_stage<R, TH, MODE>(gn, s_in);
-    row_pass_store<R, TH>(s_v, g.out, g.pitch, g.H, g.x0, g.y0, tp);
+    if (k + 1 < n_mine) issue_stage<R, TH, MODE, ST>(gn, s_in);
+    row_pass_store<R, TH, ST != 0>(s_v, g.out, g.pitch, g.H, g.x0, g.y0, tp);
     if (threadIdx.x < 32 && (k & (kGeoChunk - 1)) == kGeoChunk / 2)
       fill_chunk(k / kGeoChunk + 1);
     // No barrier here: the barrier after the next copy-wait orders every
@@ -458,8 +540,9 @@ __global__ void __launch_bounds__(kThreads, TH == 32 ? (MODE == 0 ? 4 : 3) : 1)
 }
 
 // Fallback for radii without a specialised kernel (non-default parameters):
-// same staging and the same per-output order of operations, plain loops.
-template <int MODE>
+// same staging and the same per-output order of operations, plain loops. ST as
+// for k_blur (MODE 0 and 3 only).
+template <int MODE, int ST = 0>
 __global__ void __launch_bounds__(kThreads) k_blur_generic(const Desc *__restrict__ d, int oct,
                                                            int lvl_out, int R, BlurTaps tp) {
   pdl_trigger();
@@ -480,8 +563,23 @@ __global__ void __launch_bounds__(kThreads) k_blur_generic(const Desc *__restric
     const int lt = t - pre[b];
     const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
     const int x0 = tx * kBlurTW, y0 = ty * TH;
-    float *out = d->pyr + od.lvl + (long long)lvl_out * od.lstride;
-    if (MODE == 0) {
+    float *out = elem_ptr(d->pyr + od.lvl, (long long)lvl_out * od.lstride, ST != 0);
+    if (ST != 0) {
+      TileGeo g{};
+      if (MODE == 3) {
+        const OctDev op = d->oct[im.oct0 + oct - 1];
+        g.src = elem_ptr(d->pyr + op.lvl, (long long)d->n_scales * op.lstride, ST == 2);
+        g.spitch = op.pitch;
+      } else {
+        g.src = elem_ptr(d->pyr + od.lvl, (long long)(lvl_out - 1) * od.lstride, ST == 2);
+        g.spitch = od.pitch;
+      }
+      g.H = od.H;
+      g.W = od.W;
+      g.x0 = x0;
+      g.y0 = y0;
+      stage_sync<MODE, ST>(g, R, ROWS, s_in);
+    } else if (MODE == 0) {
       const float *src = d->pyr + od.lvl + (long long)(lvl_out - 1) * od.lstride;
       stage_plain(src, od.pitch, od.H, od.W, true, x0, y0, R, ROWS, s_in);
     } else if (MODE == 1) {
@@ -498,8 +596,12 @@ __global__ void __launch_bounds__(kThreads) k_blur_generic(const Desc *__restric
     if (MODE == 3) {
       for (int q = threadIdx.x; q < TH * kBlurTW; q += kThreads) {
         const int v = q / kBlurTW, k = q - v * kBlurTW;
-        if (y0 + v < od.H && x0 + k < od.pitch)
-          d->pyr[od.lvl + (long long)(y0 + v) * od.pitch + x0 + k] = s_in[(R + v) * kSinW + kBlurHalo + k];
+        if (y0 + v < od.H && x0 + k < od.pitch) {
+          const long long i = (long long)(y0 + v) * od.pitch + x0 + k;
+          const float val = s_in[(R + v) * kSinW + kBlurHalo + k];
+          if (ST != 0) reinterpret_cast<__half *>(d->pyr + od.lvl)[i] = __float2half_rn(val);
+          else d->pyr[od.lvl + i] = val;
+        }
       }
     }
     for (int idx = threadIdx.x; idx < TH * kSinW; idx += kThreads) {
@@ -514,7 +616,10 @@ __global__ void __launch_bounds__(kThreads) k_blur_generic(const Desc *__restric
       const int y = y0 + v, x = x0 + k;
       const int sc = kBlurHalo + k - R;  // first tap column; its parity is that of x - R
       const float acc = row_tap_sum(s_v + v * kSinW + sc, (sc & 1) != 0, R, tp.w);
-      if (y < od.H && x < od.pitch) out[(long long)y * od.pitch + x] = acc;
+      if (y < od.H && x < od.pitch) {
+        if (ST != 0) reinterpret_cast<__half *>(out)[(long long)y * od.pitch + x] = __float2half_rn(acc);
+        else out[(long long)y * od.pitch + x] = acc;
+      }
     }
     __syncthreads();
   }
@@ -672,10 +777,16 @@ cudaError_t blur_set_attributes() {
   SET((k_blur<R, 64, 0>), (smem_bytes<R, 64, 0>()))          \
   SET((k_blur<R, 32, 3>), (smem_bytes<R, 32, 3>()))          \
   SET((k_blur<R, 64, 3>), (smem_bytes<R, 64, 3>()))          \
-  SET((k_blur<R, 32, 1>), (smem_bytes<R, 32, 1>()))
+  SET((k_blur<R, 32, 1>), (smem_bytes<R, 32, 1>()))          \
+  SET((k_blur<R, 32, 0, 2>), (smem_bytes<R, 32, 0>()))       \
+  SET((k_blur<R, 32, 3, 1>), (smem_bytes<R, 32, 3>()))       \
+  SET((k_blur<R, 32, 3, 2>), (smem_bytes<R, 32, 3>()))
   SIFT_FOR_EACH_R(SET_R)
   SET(k_blur_generic<0>, generic_smem_bytes(kMaxR))
   SET(k_blur_generic<3>, generic_smem_bytes(kMaxR))
+  SET((k_blur_generic<0, 2>), generic_smem_bytes(kMaxR))
+  SET((k_blur_generic<3, 1>), generic_smem_bytes(kMaxR))
+  SET((k_blur_generic<3, 2>), generic_smem_bytes(kMaxR))
   SET(k_blur_generic<1>, generic_smem_bytes(kMaxR))
   SET(k_blur_generic<2>, generic_smem_bytes(kMaxR))
 #undef SET_R
@@ -685,8 +796,10 @@ cudaError_t blur_set_attributes() {
 
 cudaError_t launch_level_blur(const Desc *d, int oct, int lvl_out, int R, const BlurTaps &t,
                               int th_kind, int grid, cudaStream_t s, bool from_prev_octave,
-                              bool pdl) {
+                              bool pdl, int storage) {
   const bool m3 = from_prev_octave;
+  if (storage != 0 && (th_kind == TK_BLUR64 || storage > 2 || (storage == 1 && !m3)))
+    return cudaErrorInvalidValue;  // binary16 octaves use 32-row tiles
   // A programmatic dependent of the previous kernel on s, or (pdl false) a plain
   // launch that waits for everything before it (a branch after an event wait).
   auto go = [&](auto kern, size_t smem, auto... args) -> cudaError_t {
@@ -695,6 +808,10 @@ cudaError_t launch_level_blur(const Desc *d, int oct, int lvl_out, int R, const 
   };
 #define CASE_R(RR)                                                                        \
   case RR:                                                                                \
+    if (storage == 1) return go(k_blur<RR, 32, 3, 1>, smem_bytes<RR, 32, 3>(), t);          \
+    if (storage == 2)                                                                     \
+      return m3 ? go(k_blur<RR, 32, 3, 2>, smem_bytes<RR, 32, 3>(), t)                      \
+                : go(k_blur<RR, 32, 0, 2>, smem_bytes<RR, 32, 0>(), t);                     \
     if (th_kind == TK_BLUR64)                                                             \
       return m3 ? go(k_blur<RR, 64, 3>, smem_bytes<RR, 64, 3>(), t)                         \
                 : go(k_blur<RR, 64, 0>, smem_bytes<RR, 64, 0>(), t);                        \
@@ -703,10 +820,33 @@ cudaError_t launch_level_blur(const Desc *d, int oct, int lvl_out, int R, const 
   switch (R) {
     SIFT_FOR_EACH_R(CASE_R)
     default:
+      if (storage == 1) return go(k_blur_generic<3, 1>, generic_smem_bytes(R), R, t);
+      if (storage == 2)
+        return m3 ? go(k_blur_generic<3, 2>, generic_smem_bytes(R), R, t)
+                  : go(k_blur_generic<0, 2>, generic_smem_bytes(R), R, t);
       return m3 ? go(k_blur_generic<3>, generic_smem_bytes(R), R, t)
                 : go(k_blur_generic<0>, generic_smem_bytes(R), R, t);
   }
 #undef CASE_R
+}
+
+namespace {
+// One pyramid level copied out as a dense H x W FP32 plane (binary16 levels
+// widened), for the pyramid export.
+__global__ void k_export_level(const float *__restrict__ src, int half, int pitch, int H, int W,
+                               float *__restrict__ dst) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x >= W || y >= H) return;
+  const long long i = (long long)y * pitch + x;
+  dst[(long long)y * W + x] =
+      half ? __half2float(reinterpret_cast<const __half *>(src)[i]) : src[i];
+}
+}  // namespace
+
+cudaError_t launch_export_level(const float *src, bool half, int pitch, int H, int W, float *dst,
+                                cudaStream_t s) {
+  return launch_plain(k_export_level, dim3((W + 127) / 128, H), 128, 0, s, src, half ? 1 : 0,
+                      pitch, H, W, dst);
 }
 
 cudaError_t launch_base_blur(const Desc *d, int R, const BlurTaps &t, int th_kind, bool upsample,

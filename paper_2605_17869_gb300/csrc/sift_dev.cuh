@@ -2,7 +2,9 @@
 //
 // Data layout in device memory (one "engine" = one workspace + descriptor):
 //  * Pyramid: per image, per octave o, levels 0..S+2 stored back to back, each
-//    H_o rows of `pitch` floats (pitch = W_o rounded up to 32 floats, 128 B).
+//    H_o rows of `pitch` elements (pitch = W_o rounded up to 32). Elements are
+//    FP32, or IEEE binary16 for the octaves above 0 in the fp16 storage mode
+//    (OctDev::half); arithmetic is FP32 throughout.
 //  * Candidate bitmap: per image, per octave, per DoG layer 1..S, H_o rows of
 //    ceil(W_o / 30) 32-bit words; bit k (< 30) of word w in row y marks pixel
 //    x = 30 w + k (one word is the row of one extrema strip). Walking the
@@ -14,6 +16,7 @@
 // launch, so the captured CUDA graphs depend only on the number of octaves.
 #pragma once
 #include <cstdint>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace sift {
@@ -43,10 +46,12 @@ enum RefCode { RC_KEEP = 0, RC_SINGULAR = 1, RC_NOCONV = 2, RC_BOUNDS = 3, RC_CO
 enum { TF_CAND = 1, TF_ORI = 2, TF_TOPK = 4 };
 
 struct OctDev {
-  int H, W, pitch, wpr;        // size, row pitch (floats), bitmap words per row
-  long long lvl;               // float offset of level 0 in the pyramid array
-  long long lstride;           // floats between consecutive levels (H * pitch)
+  int H, W, pitch, wpr;        // size, row pitch (elements), bitmap words per row
+  long long lvl;               // offset of level 0 in the pyramid array, in floats (4-byte units)
+  long long lstride;           // elements between consecutive levels (H * pitch)
   long long bm;                // word offset of layer 1's bitmap
+  int half;                    // 1: this octave's levels are stored as binary16
+  int pad;
 };
 
 struct ImgDev {
@@ -85,7 +90,7 @@ struct Desc {
   float sigma0, contrast_thr, prefilter, edge_ratio;
   int border, max_iter, upright, rootsift;
   float ori_peak_ratio, pad_f[3];
-  int n_bm_chunks, n_cc_chunks, dsp, pad_i;
+  int n_bm_chunks, n_cc_chunks, dsp, fp16;  // fp16: octaves above 0 stored as binary16
   // workspace arrays
   float *pyr;
   uint32_t *bm;
@@ -163,6 +168,13 @@ inline cudaError_t launch_plain(void (*k)(KArgs...), dim3 grid, dim3 block, size
   return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
 }
 
+// Pyramid element access for the per-keypoint stages, which read octaves of
+// either storage type: base = d->pyr + od.lvl, idx in elements of the octave.
+__device__ __forceinline__ float lvl_ld(const float *base, bool half, long long idx) {
+  if (half) return __half2float(__ldg(reinterpret_cast<const __half *>(base) + idx));
+  return __ldg(base + idx);
+}
+
 // Index of the image owning flattened item t, given an exclusive prefix pre[0..n].
 __device__ __forceinline__ int find_owner(const int *pre, int n, int t) {
   int lo = 0, hi = n;
@@ -186,17 +198,25 @@ __device__ __forceinline__ int refl101(int i, int n) {
 cudaError_t launch_base_blur(const Desc *d, int R, const BlurTaps &t, int th_kind, bool upsample,
                              int grid, cudaStream_t s);
 // pdl: launch as a programmatic dependent of the previous kernel on s.
+// storage: 0 FP32 in and out; 1 FP32 source, binary16 output (first level of
+// octave 1 in the fp16 storage mode, from_prev_octave only); 2 binary16 in and
+// out. Binary16 octaves use 32-row tiles.
 cudaError_t launch_level_blur(const Desc *d, int oct, int lvl_out, int R, const BlurTaps &t,
                               int th_kind, int grid, cudaStream_t s, bool from_prev_octave = false,
-                              bool pdl = true);
+                              bool pdl = true, int storage = 0);
+// Copy one pyramid level (src: the level's first element, `half` for binary16)
+// into a dense H x W FP32 plane.
+cudaError_t launch_export_level(const float *src, bool half, int pitch, int H, int W, float *dst,
+                                cudaStream_t s);
 int blur_smem_bytes(int R, int th_kind);
 int blur_blocks_per_sm(int R, int th_kind, int mode);
 cudaError_t blur_set_attributes();
 
 // Detection (detect.cu)
 // pdl: launch as a programmatic dependent of the previous kernel on s.
+// half: the octave's levels are binary16 (fp16 storage mode).
 cudaError_t launch_extrema(const Desc *d, int oct, int n_scales, int grid, cudaStream_t s,
-                           bool pdl = true);
+                           bool pdl = true, bool half = false);
 cudaError_t extrema_set_attributes();
 // Persistent grid of the extrema scan: SMs x resident blocks per SM.
 int extrema_grid(int n_sm, int n_scales);

@@ -138,6 +138,7 @@ def test_parameter_ranges_are_enforced_as_documented(lib):
                              ("ori_peak_ratio", (0.0, 1.01, nan), (1.0, 0.5)), ("border", (0,), (1,)),
                              ("max_refine_iter", (0,), (1,)), ("max_kpts", (0, -5), (1,)),
                              ("dsp", (2, -1), (0, 1)), ("upsample_max_px", (-1,), (0, 1)),
+                             ("fp16_pyramid", (2, -1), (0, 1)),
                              ("min_octave_side", (15, 0), (16, 64))):
         for v in bad:
             assert status(**{field: v}) == _abi.SIFT_E_INVALID, (field, v)

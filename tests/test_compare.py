@@ -1,5 +1,7 @@
 """The parity comparator itself (CPU): an oracle result matched against
 perturbed copies of itself finds exactly the keypoints inside each tolerance."""
+import math
+
 import numpy as np
 import pytest
 
@@ -147,3 +149,26 @@ def test_closest_angle_and_worst_case_over_pairs(ref):
     g["x"][a] += 0.005                                    # only one eligible keypoint moves
     m = compare.match(r, g)
     assert m.worst["pos"] == pytest.approx(0.005, rel=1e-6)
+
+
+def test_tolerance_scale_widens_every_tolerance(ref):
+    """tol_scale (the fp16 storage mode's FP16_TOL_SCALE) multiplies the position,
+    scale and angle tolerances: offsets 3x outside the FP32 tolerances are
+    found at scale 5 and not at scale 1."""
+    r, p = ref
+    assert compare.FP16_TOL_SCALE == math.ceil(2.0 ** -11 / 1e-4)       # 4.88, rounded up
+    for key, delta in (("x", 0.03), ("y", -0.03)):
+        g = _as_gpu(r)
+        g[key] = g[key] + delta
+        assert compare.match(r, g).n_found == 0
+        m = compare.match(r, g, tol_scale=compare.FP16_TOL_SCALE)
+        assert m.n_found == m.n_eligible > 0
+    g = _as_gpu(r)
+    g["sigma"] = g["sigma"] * (1 + 3e-3)
+    assert compare.match(r, g).n_found == 0
+    assert compare.match(r, g, tol_scale=5.0).n_found == compare.match(r, g, tol_scale=5.0).n_eligible
+    g = _as_gpu(r)
+    g["angle"] = (g["angle"] + 1.5) % 360.0
+    assert compare.match(r, g).n_found == 0
+    m = compare.match(r, g, tol_scale=5.0)
+    assert m.n_found == m.n_eligible

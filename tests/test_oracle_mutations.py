@@ -140,6 +140,18 @@ MUTANTS = {
     "response_signed": ("                   abs(contrast), margin)", "                   contrast, margin)"),
     "keypoint_margin_skips_candidate": (
         "            m0 = min(float(mg[ci]), float(me[ci]), r.margin)", "            m0 = r.margin"),
+    "fp16_storage_ignored": ("        return level.astype(np.float16).astype(np.float64)",
+                             "        return level"),
+    "fp16_storage_truncates": ("        return level.astype(np.float16).astype(np.float64)",
+                               "        return np.trunc(level * 2048.0) / 2048.0"),
+    "fp16_storage_octave0_too": ("    if p.fp16_pyramid and o > 0:", "    if p.fp16_pyramid and o >= 0:"),
+    "fp16_storage_after_the_chain": ("            levels.append(store_level(blur(levels[-1], k), o, p))",
+                                     "            levels.append(blur(levels[-1], k))"),
+    "diagonal_votes_downward": ("    bins = np.where(diag, (n * (2 * q + 1) + 4) // 8 % n, bins)",
+                                "    bins = np.where(diag, (n * (2 * q + 1) + 3) // 8 % n, bins)"),
+    "diagonal_quadrants_swapped": ("    q = np.where(dy > 0, np.where(dx > 0, 0, 1), np.where(dx < 0, 2, 3))",
+                                   "    q = np.where(dy > 0, np.where(dx > 0, 1, 0), np.where(dx < 0, 2, 3))"),
+    "vote_margin_counts_diagonals": ("    votes = (wt * mag > 0) & ~diag\n", "    votes = wt * mag > 0\n"),
     "keypoint_margin_skips_votes": (
         "                m1 = min(m1, orientation_vote_margin(L, r.x, r.y, sigma_oct, p))\n", "\n"),
     "vote_margin_from_bin_centre": ("    t = n * th[votes] / (2 * math.pi) + 0.5   # bin",
@@ -148,7 +160,7 @@ MUTANTS = {
                                "    t = th[votes] + 0.5   # bin"),
     "vote_margin_one_sided": ("    return float(np.minimum(f, 1.0 - f).min())",
                               "    return float(f.min())"),
-    "vote_margin_counts_zero_weight": ("    votes = wt * mag > 0\n", "    votes = wt * mag >= 0\n"),
+    "vote_margin_counts_zero_weight": ("    votes = (wt * mag > 0) & ~diag\n", "    votes = (wt * mag >= 0) & ~diag\n"),
     "keypoint_margin_skips_orientation": (
         "                rows.append((o, r, sigma_oct, a, min(m0, m1)))",
         "                rows.append((o, r, sigma_oct, a, m0))"),
@@ -243,6 +255,9 @@ COMPARE_MUTANTS = {
         '            worst["pos"] = max(worst["pos"], float(max(abs(gx[j] - ox[i]), abs(gy[j] - oy[i]))))',
         '            worst["pos"] = float(max(abs(gx[j] - ox[i]), abs(gy[j] - oy[i])))'),
     "compare_pairs_uncounted": ("                pairs += 1", "                pairs += 0"),
+    "compare_scale_ignored_for_angle": ("    pos_tol, sig_tol, ang_tol = POS_TOL * tol_scale, SIGMA_RTOL * tol_scale, ANGLE_TOL * tol_scale",
+                                        "    pos_tol, sig_tol, ang_tol = POS_TOL * tol_scale, SIGMA_RTOL * tol_scale, ANGLE_TOL"),
+    "compare_fp16_scale_four": ("FP16_TOL_SCALE = 5.0", "FP16_TOL_SCALE = 4.0"),
 }
 
 CASES = ([(n, "sift_oracle.py", "test_oracle_pins.py") for n in sorted(MUTANTS)]

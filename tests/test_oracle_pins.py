@@ -107,6 +107,50 @@ def test_upsample_identities():
     np.testing.assert_array_equal(so.decimate(u), img)
 
 
+@pytest.mark.parametrize("v,want", [
+    (1.0 / 3.0, 0.333251953125),            # binary16 0x3555, the nearest to 1/3
+    (1.0 + 2.0 ** -11, 1.0),                # halfway between 1 and 1 + 2^-10: ties to even
+    (1.0 + 3 * 2.0 ** -11, 1.0 + 2.0 ** -9),  # halfway, the even neighbour is above
+    (0.1, 0.0999755859375),                 # binary16 0x2E66
+    (2.0 ** -25, 0.0),                      # below half the smallest subnormal 2^-24
+    (0.75, 0.75),                           # exactly representable
+])
+def test_fp16_storage_rounds_to_nearest_binary16(v, want):
+    """§3.2's fp16 storage: a stored level of an octave above 0 is the nearest
+    IEEE binary16 value, ties to even (values worked out by hand above);
+    octave 0 and the default mode keep the value."""
+    p16 = so.Params(fp16_pyramid=True)
+    a = np.array([[v]])
+    assert so.store_level(a, 1, p16)[0, 0] == want
+    assert so.store_level(a, 0, p16)[0, 0] == v
+    assert so.store_level(a, 3, so.Params())[0, 0] == v
+
+
+@pytest.mark.parametrize("up", [False, True])
+def test_fp16_pyramid_keeps_octave0_and_bounds_the_rest(up):
+    """With fp16 storage, octave 0 equals the full-precision pyramid exactly;
+    every level above it holds binary16 values; and it differs from the
+    full-precision pyramid by at most one half-ulp of [0, 1) values (2^-12)
+    per rounding it went through: the taps are non-negative and sum to one,
+    so a blur does not grow an earlier error. Level i of octave o has gone
+    through (o - 1)(S + 1) + i + 1 roundings."""
+    img = synth.make_image(synth.rng_for(10, 7), 150, 190)
+    p = so.Params(upsample=up)
+    p16 = so.Params(upsample=up, fp16_pyramid=True)
+    a, b = so.build_pyramid(img, p), so.build_pyramid(img, p16)
+    assert len(a) == len(b) >= 3
+    np.testing.assert_array_equal(a[0], b[0])
+    S = p.n_scales
+    for o in range(1, len(a)):
+        assert np.array_equal(b[o].astype(np.float16).astype(np.float64), b[o])
+        for i in range(S + 3):
+            n_round = (o - 1) * (S + 1) + i + 1
+            assert np.abs(b[o][i] - a[o][i]).max() <= n_round * 2.0 ** -12 + 1e-15, (o, i)
+    # Octave 1 starts from octave 0's level S, decimated and then rounded once.
+    want = so.decimate(a[0][S]).astype(np.float16).astype(np.float64)
+    np.testing.assert_array_equal(b[1][0], want)
+
+
 def test_magnify_limit():
     """§5's suppression of the double image above 4 MP: the limit counts input
     pixels, an image of exactly the limit is still magnified, 0 disables it."""
@@ -481,6 +525,21 @@ def test_blob_detected_at_predicted_scale(s):
 
 
 # ------------------------------------------------------------------ orientation
+
+@pytest.mark.parametrize("deg,want_bin", [(45.0, 5), (135.0, 14), (225.0, 23), (315.0, 32)])
+def test_diagonal_gradient_votes_upward(deg, want_bin):
+    """A gradient with |dx| = |dy| sits exactly on a bin boundary (36 theta / 360
+    = 4.5, 13.5, 22.5, 31.5); the nearest-bin rule floor(c + 1/2) sends it to
+    the upper bin, 5, 14, 23 or 32. Such samples are decided exactly, so they
+    do not count as near a boundary in the vote margin."""
+    p = so.Params()
+    c, s = round(math.cos(math.radians(deg))), round(math.sin(math.radians(deg)))
+    Y, X = np.mgrid[0:61, 0:61].astype(float)
+    L = 0.01 * (c * X + s * Y)
+    hist = so.orientation_histogram(L, 30, 30, 2.0, p)
+    assert list(np.nonzero(hist)[0]) == [want_bin]
+    assert so.orientation_vote_margin(L, 30, 30, 2.0, p) == math.inf
+
 
 @pytest.mark.parametrize("deg", [0.0, 30.0, 90.0, 200.0, 313.0, 47.0])
 def test_ramp_orientation(deg):
