@@ -576,6 +576,8 @@ def serving_bench(torch, pkg, rates, n_req, budget=8 << 30):
         srv.release(t)
     out = []
     for lam in rates:
+        prev = srv.steps()
+        t_before = prev[-1][3] if prev else float("-inf")
         trace = synth.serving_trace(lam, n_req, index=int(lam))
         tickets = []
         t0 = time.perf_counter()
@@ -593,10 +595,26 @@ def serving_bench(torch, pkg, rates, n_req, budget=8 << 30):
             srv.release(tk)
         span = time.perf_counter() - t0
         lat.sort()
+        steps = [s for s in srv.steps() if s[2] > t_before]
+        # Device time during which steps of two or more lanes ran at once.
+        ev = sorted([(a, 1) for _, _, a, _ in steps] + [(b, -1) for _, _, _, b in steps])
+        busy = conc = 0.0
+        depth, last = 0, None
+        for t, dlt in ev:
+            if last is not None and depth > 0:
+                busy += t - last
+                if depth > 1:
+                    conc += t - last
+            depth += dlt
+            last = t
         out.append({"rate_per_s": lam, "requests": n_req, "images_per_s": round(n_req / span, 1),
                     "mpix_per_s": round(px / 1e6 / span, 1),
                     "p50_ms": round(lat[len(lat) // 2], 3),
-                    "p99_ms": round(lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)], 3)})
+                    "p99_ms": round(lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)], 3),
+                    "steps": len(steps),
+                    "images_per_step": round(n_req / max(1, len(steps)), 2),
+                    "device_busy_ms": round(busy, 2),
+                    "lanes_concurrent_frac_of_busy": round(conc / busy, 4) if busy > 0 else 0.0})
     srv.close()
     ex.close()
     return {"workload": "Poisson arrivals, 640x480 (50%) / 1920x1080 (35%) / 3840x2160 (15%), "

@@ -339,6 +339,19 @@ sift_status sift_serve_poll(sift_server *s, uint64_t ticket, sift_result *out);
 sift_status sift_serve_wait(sift_server *s, uint64_t ticket, int timeout_ms, sift_result *out);
 /* Free a finished request's result buffers. */
 sift_status sift_serve_release(sift_server *s, uint64_t ticket);
+/* Device-side timing of the server's finished steps (a step is one batched
+ * extraction on one of the server's lanes, each lane a stream of its own),
+ * oldest first: for up to max_steps of the most recent steps, the lane, the number of images, and the times of CUDA events
+ * recorded on the lane's stream before the step's first launch and after its
+ * result read-back, in ms after an event recorded when the server was created.
+ * (The server keeps the last 65536 steps.)
+ * Steps of different lanes whose [start, end] intervals intersect were on the
+ * device at the same time, which is how continuous batching overlaps requests
+ * that arrive while others run. *n_out receives the number written.
+ * SIFT_E_INVALID for a null server or n_out, a negative max_steps, or a null
+ * array with max_steps > 0. Host-only: no synchronisation. */
+sift_status sift_serve_steps(sift_server *s, int max_steps, int *lane, int *n_images,
+                             double *start_ms, double *end_ms, int *n_out);
 /* Stop the scheduler (waits for running steps) and free the server. */
 sift_status sift_serve_destroy(sift_server *s);
 

@@ -25,7 +25,7 @@ __all__ = [
     "sift_last_stats", "sift_pyramid_size", "sift_octave_geometry", "sift_build_pyramid", "sift_set_profiling",
     "sift_kernel_times", "sift_last_launch_count", "sift_autotune", "sift_get_tuning", "sift_set_tuning",
     "sift_serve_create", "sift_serve_submit", "sift_serve_poll", "sift_serve_wait",
-    "sift_serve_release", "sift_serve_destroy", "sift_last_error", "sift_version",
+    "sift_serve_release", "sift_serve_steps", "sift_serve_destroy", "sift_last_error", "sift_version",
     "SIFT_OK", "SIFT_W_TRUNCATED", "SIFT_PENDING", "SIFT_E_INVALID", "SIFT_E_OOM",
     "SIFT_E_CUDA", "SIFT_E_BUDGET", "SIFT_E_TIMEOUT", "SIFT_E_NOTFOUND", "KERNEL_CLASSES",
 ]
@@ -240,6 +240,19 @@ def sift_serve_wait(server, ticket: int, timeout_ms: int = 60000):
 
 def sift_serve_release(server, ticket: int) -> None:
     _check(_lib().sift_serve_release(server, ticket), what="sift_serve_release")
+
+
+def sift_serve_steps(server, max_steps: int = 65536):
+    """Device-side intervals of the server's most recent finished steps, oldest
+    first: a list of (lane, n_images, start_ms, end_ms)."""
+    lane = (c_int * max_steps)()
+    n_img = (c_int * max_steps)()
+    t0 = (c_double * max_steps)()
+    t1 = (c_double * max_steps)()
+    n = c_int()
+    _check(_lib().sift_serve_steps(server, max_steps, lane, n_img, t0, t1, byref(n)),
+           what="sift_serve_steps")
+    return [(lane[i], n_img[i], t0[i], t1[i]) for i in range(n.value)]
 
 
 def sift_serve_destroy(server) -> None:
@@ -580,6 +593,11 @@ class Server:
 
     def release(self, ticket: int):
         sift_serve_release(self.srv, ticket)
+
+    def steps(self, max_steps: int = 65536):
+        """Device intervals of the most recent finished steps: (lane, n_images,
+        start_ms, end_ms) each, oldest first (sift_serve_steps)."""
+        return sift_serve_steps(self.srv, max_steps)
 
     def close(self):
         if getattr(self, "srv", None) is not None:

@@ -76,6 +76,8 @@ SIGNATURES = {
     "sift_serve_poll": (c_int, [c_void_p, c_uint64, POINTER(SiftResult)]),
     "sift_serve_wait": (c_int, [c_void_p, c_uint64, c_int, POINTER(SiftResult)]),
     "sift_serve_release": (c_int, [c_void_p, c_uint64]),
+    "sift_serve_steps": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_int), POINTER(c_double),
+                                 POINTER(c_double), POINTER(c_int)]),
     "sift_serve_destroy": (c_int, [c_void_p]),
     "sift_last_error": (c_char_p, [c_void_p]),
     "sift_version": (c_char_p, []),

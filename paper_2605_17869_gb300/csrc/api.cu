@@ -397,6 +397,7 @@ struct DoneMsg {
 struct Lane {
   Engine *eng = nullptr;
   cudaStream_t stream = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_end = nullptr;  // device bounds of the lane's step
   bool busy = false;
   bool finished = false;
   std::vector<uint64_t> reqs;
@@ -406,8 +407,17 @@ struct Lane {
   DoneMsg msg{};
 };
 
+// Device-side interval of one finished step, in ms after the server's reference event.
+struct StepRec {
+  int lane, n_images;
+  double start_ms, end_ms;
+};
+constexpr size_t kStepLog = 65536;  // most recent steps kept for sift_serve_steps
+
 struct Server {
   sift_handle *h = nullptr;
+  cudaEvent_t ev_ref = nullptr;    // recorded once at creation
+  std::deque<StepRec> steps;
   size_t budget = 0;
   int max_slots = 0;
   std::mutex mu;
@@ -502,21 +512,22 @@ sift_status launch_step(Lane &l, int K, std::vector<Job> &jobs, std::string *err
                        reinterpret_cast<int *>(f + 7 * K + (size_t)K * sift::kDescLen)});
   }
   if (in.empty()) return SIFT_E_OOM;
-  sift_status st = l.eng->run((int)in.size(), in.data(), l.stream);
-  cudaError_t e = cudaSuccess;
+  cudaError_t e = cudaEventRecord(l.ev_start, l.stream);
+  sift_status st = e == cudaSuccess ? l.eng->run((int)in.size(), in.data(), l.stream) : SIFT_E_CUDA;
   if (st == SIFT_OK) {
     for (size_t i = 0; i < in.size() && e == cudaSuccess; i++)
       e = cudaMemcpyAsync(l.h_counts + i, in[i].count, sizeof(int), cudaMemcpyDeviceToHost, l.stream);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(l.h_flags, l.eng->workspace() + l.eng->layout().cnt,
                           in.size() * sizeof(sift::ImgCounters), cudaMemcpyDeviceToHost, l.stream);
+    if (e == cudaSuccess) e = cudaEventRecord(l.ev_end, l.stream);
     if (e == cudaSuccess) e = cudaLaunchHostFunc(l.stream, on_lane_done, &l.msg);
     if (e != cudaSuccess) {
       st = SIFT_E_CUDA;
       *err = cudaGetErrorString(e);
     }
   } else {
-    *err = l.eng->err;
+    *err = e != cudaSuccess ? cudaGetErrorString(e) : l.eng->err;
   }
   return st;
 }
@@ -538,8 +549,24 @@ void scheduler(Server *s) {
   const int K = s->h->eng->params().max_kpts;
   std::unique_lock<std::mutex> lk(s->mu);
   while (true) {
-    for (auto &l : s->lanes)
-      if (l.busy && l.finished) retire(s, l);
+    for (size_t i = 0; i < s->lanes.size(); i++) {
+      Lane &l = s->lanes[i];
+      if (!(l.busy && l.finished)) continue;
+      // The step's events are complete (its completion callback ran). Their
+      // times are read without the lock, like every other CUDA call here;
+      // nothing else touches a finished lane meanwhile.
+      lk.unlock();
+      float t0 = 0.f, t1 = 0.f;
+      const bool timed = cudaEventElapsedTime(&t0, s->ev_ref, l.ev_start) == cudaSuccess &&
+                         cudaEventElapsedTime(&t1, s->ev_ref, l.ev_end) == cudaSuccess;
+      if (!timed) cudaGetLastError();
+      lk.lock();
+      if (timed) {
+        s->steps.push_back(StepRec{(int)i, (int)l.reqs.size(), (double)t0, (double)t1});
+        if (s->steps.size() > kStepLog) s->steps.pop_front();
+      }
+      retire(s, l);
+    }
     if (s->stop) {
       bool any = false;
       for (auto &l : s->lanes) any |= l.busy;
@@ -637,6 +664,10 @@ sift_status sift_serve_create(sift_handle *h, size_t mem_budget_bytes, int max_s
     l.eng->set_tuning(h->eng->tuning());
     sift_status st = l.eng->init();
     cudaError_t e = cudaStreamCreateWithFlags(&l.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&l.ev_start);
+    if (e == cudaSuccess) e = cudaEventCreate(&l.ev_end);
+    if (e == cudaSuccess && i == 0) e = cudaEventCreate(&s.ev_ref);
+    if (e == cudaSuccess && i == 0) e = cudaEventRecord(s.ev_ref, l.stream);
     if (e == cudaSuccess) e = cudaHostAlloc(&l.h_counts, sift::kMaxImg * sizeof(int), 0);
     if (e == cudaSuccess)
       e = cudaHostAlloc(&l.h_flags, sift::kMaxImg * sizeof(sift::ImgCounters), 0);
@@ -645,9 +676,12 @@ sift_status sift_serve_create(sift_handle *h, size_t mem_budget_bytes, int max_s
       for (auto &m : s.lanes) {
         delete m.eng;
         if (m.stream) cudaStreamDestroy(m.stream);
+        if (m.ev_start) cudaEventDestroy(m.ev_start);
+        if (m.ev_end) cudaEventDestroy(m.ev_end);
         if (m.h_counts) cudaFreeHost(m.h_counts);
         if (m.h_flags) cudaFreeHost(m.h_flags);
       }
+      if (s.ev_ref) cudaEventDestroy(s.ev_ref);
       delete sv;
       return fail(h, SIFT_E_CUDA, "server lane initialisation failed");
     }
@@ -745,6 +779,25 @@ sift_status sift_serve_release(sift_server *sv, uint64_t ticket) {
   return SIFT_OK;
 }
 
+sift_status sift_serve_steps(sift_server *sv, int max_steps, int *lane, int *n_images,
+                             double *start_ms, double *end_ms, int *n_out) {
+  if (!sv || !n_out || max_steps < 0 || (max_steps > 0 && (!lane || !n_images || !start_ms || !end_ms)))
+    return SIFT_E_INVALID;
+  Server &s = sv->s;
+  std::lock_guard<std::mutex> lk(s.mu);
+  const int n = (int)std::min<size_t>((size_t)max_steps, s.steps.size());
+  const size_t first = s.steps.size() - (size_t)n;
+  for (int i = 0; i < n; i++) {
+    const StepRec &r = s.steps[first + i];
+    lane[i] = r.lane;
+    n_images[i] = r.n_images;
+    start_ms[i] = r.start_ms;
+    end_ms[i] = r.end_ms;
+  }
+  *n_out = n;
+  return SIFT_OK;
+}
+
 sift_status sift_serve_destroy(sift_server *sv) {
   if (!sv) return SIFT_E_INVALID;
   Server &s = sv->s;
@@ -761,9 +814,12 @@ sift_status sift_serve_destroy(sift_server *sv) {
     cudaStreamSynchronize(l.stream);
     delete l.eng;
     cudaStreamDestroy(l.stream);
+    cudaEventDestroy(l.ev_start);
+    cudaEventDestroy(l.ev_end);
     cudaFreeHost(l.h_counts);
     cudaFreeHost(l.h_flags);
   }
+  cudaEventDestroy(s.ev_ref);
   s.h->serving = false;
   delete sv;
   return SIFT_OK;

@@ -8,8 +8,6 @@
 // conflicts). The columns are then summed bin by bin, warp by warp and lane by
 // lane. No atomics are used anywhere: the sum order is fixed by the code, so
 // outputs are bitwise reproducible.
-#include <type_traits>
-
 #include "scan.cuh"
 #include "sift_dev.cuh"
 
@@ -426,6 +424,139 @@ __device__ __forceinline__ void desc_commit(float *hist, int lane, bool ok, cons
 // DSP-SIFT pooling (§3.2): relative scales of the descriptor's bin width.
 __constant__ float kDspScale[5] = {0.5f, 0.70710678118654752f, 1.0f, 1.41421356237309505f, 2.0f};
 
+// The sample sweeps of one keypoint (plain or DSP), instantiated once per
+// storage type of the level (HF: binary16) so that no load tests it.
+template <bool HF>
+__device__ __forceinline__ void desc_sweep(const Desc *__restrict__ d, const RefRec &r,
+                                           const OctDev &od, const float *L, long long lofs,
+                                           float wbin, float inv_w, float th, float st,
+                                           float ct, int R, float *hist, int lane, int warp,
+                                           int (*s_lo)[32], int (*s_pre)[33]) {
+  const int tid = threadIdx.x;
+    if (!d->dsp) {
+      // Samples: integer offsets (i, jy) in [-R, R]^2 inside the image whose
+      // rotated bin coordinates fall in (-1, 4)^2, i.e. inside a square of half
+      // side h = 2.5 bins around the keypoint. Warp w takes rows jlo + w,
+      // jlo + w + 4, ... (at most 32 of them, one per lane): each lane cuts its
+      // row to an interval, a superset of the square's chord widened by 2
+      // pixels so that rounding can only add candidates, and a warp scan lays
+      // the intervals end to end. The warp then sweeps that list 32 samples at
+      // a time, and the exact test below decides, so the sample set is the
+      // same as a sweep of the whole window.
+      const float h = 2.5f * wbin;
+      const int ilo = max(-R, 1 - r.x), ihi = min(R, od.W - 2 - r.x);
+      const int jlo = max(-R, 1 - r.y), jhi = min(R, od.H - 2 - r.y);
+      const float ica = fabsf(ct) * (float)(R + 1) < 1.0f ? 0.f : 1.0f / ct;
+      const float isa = fabsf(st) * (float)(R + 1) < 1.0f ? 0.f : -1.0f / st;
+      // Rows per warp are at most (2R + 1) / 4 + 1, i.e. 20 for the largest
+      // octave-relative scale of the default parameters; larger windows take
+      // several rounds of 32 rows.
+      for (int rb = 0; jlo + warp + kKpWarps * rb <= jhi; rb += 32) {
+        int len = 0, a0 = 0;
+        {
+          const int jy = jlo + warp + kKpWarps * (rb + lane);
+          if (jy <= jhi) {
+            const float oy = (float)jy - r.dy;
+            float lo = -1e30f, hi = 1e30f;
+            // slab a * ox + b in (-h, h) for (a, b) = (ct, st * oy), (-st, ct * oy)
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+              const float ia = k ? isa : ica, b = k ? ct * oy : st * oy;
+              if (ia == 0.f) {
+                if (fabsf(b) >= h + 2.0f) hi = -1e30f;  // |a * ox| < 1: the row misses the slab
+              } else {
+                const float e0 = (-h - b) * ia, e1 = (h - b) * ia;
+                lo = fmaxf(lo, fminf(e0, e1));
+                hi = fminf(hi, fmaxf(e0, e1));
+              }
+            }
+            int a1 = ihi;
+            a0 = ilo;
+            if (hi < lo) {
+              a1 = a0 - 1;
+            } else {
+              if (lo + r.dx > (float)ilo) a0 = max(ilo, (int)floorf(lo + r.dx) - 2);
+              if (hi + r.dx < (float)ihi) a1 = min(ihi, (int)ceilf(hi + r.dx) + 2);
+            }
+            len = max(0, a1 - a0 + 1);
+          }
+        }
+        // Exclusive scan of the interval lengths over the warp's rows.
+        int pre = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_up_sync(0xffffffffu, pre, o);
+          if (lane >= o) pre += v;
+        }
+        const int tot = __shfl_sync(0xffffffffu, pre, 31);
+        pre -= len;
+        int *wlo = s_lo[warp], *wpre = s_pre[warp];
+        wlo[lane] = a0;
+        wpre[lane] = pre;
+        if (lane == 31) wpre[32] = tot;
+        __syncwarp();
+        int row = 0;
+        // Warp-uniform trip count: every lane reaches the commit's __syncwarp.
+        for (int q0 = 0; q0 < tot; q0 += 32) {
+          const int q = q0 + lane;
+          bool ok = q < tot;
+          Vote vt;
+          if (ok) {
+            while (wpre[row + 1] <= q) row++;
+            const int jy = jlo + warp + kKpWarps * (rb + row);
+            const int i = wlo[row] + (q - wpre[row]);
+            const float ox = (float)i - r.dx, oy = (float)jy - r.dy;
+            const float rx = (ct * ox + st * oy) * inv_w;
+            const float ry = (-st * ox + ct * oy) * inv_w;
+            const float u = rx + 1.5f, v = ry + 1.5f;
+            ok = u > -1.f && u < 4.f && v > -1.f && v < 4.f;
+            if (ok) {
+              const long long q = lofs + (long long)(r.y + jy) * od.pitch + (r.x + i);
+              const float gx = lvl_ld(L, HF, q + 1) - lvl_ld(L, HF, q - 1);
+              const float gy = lvl_ld(L, HF, q + od.pitch) - lvl_ld(L, HF, q - od.pitch);
+              desc_targets(vt, rx, ry, gx, gy, th);
+            }
+          }
+          desc_commit(hist, lane, ok, vt);
+        }
+        __syncwarp();  // the next round rewrites this warp's interval table
+      }
+    } else {
+      for (int f = 0; f < 5; f++) {
+        const float wb = wbin * kDspScale[f];
+        for (int idx = tid; idx < 32 * 32; idx += kKpWarps * 32) {
+          const float rx = ((float)(idx & 31) + 0.5f) * 0.125f - 2.0f;
+          const float ry = ((float)(idx >> 5) + 0.5f) * 0.125f - 2.0f;
+          const float xr = r.dx + wb * (ct * rx - st * ry);  // relative to pixel (r.x, r.y)
+          const float yr = r.dy + wb * (st * rx + ct * ry);
+          const float xf = floorf(xr), yf = floorf(yr);
+          const int x0 = r.x + (int)xf, y0 = r.y + (int)yf;
+          const bool ok = !(x0 < 1 || x0 > od.W - 3 || y0 < 1 || y0 > od.H - 3);
+          Vote vt;
+          if (!ok) {  // (1024 samples per scale: the trip count is warp-uniform)
+            desc_commit(hist, lane, false, vt);
+            continue;
+          }
+          const float fx = xr - xf, fy = yr - yf, gx1 = 1.f - fx, gy1 = 1.f - fy;
+          const long long p = lofs + (long long)y0 * od.pitch + x0;
+          const long long pm = p - od.pitch, pp = p + od.pitch, p2 = pp + od.pitch;
+          auto at = [&](long long i) { return lvl_ld(L, HF, i); };
+          // L(x + 1, y) - L(x - 1, y) and L(x, y + 1) - L(x, y - 1), bilinear
+          const float xp = gy1 * (gx1 * at(p + 1) + fx * at(p + 2)) +
+                           fy * (gx1 * at(pp + 1) + fx * at(pp + 2));
+          const float xm = gy1 * (gx1 * at(p - 1) + fx * at(p)) +
+                           fy * (gx1 * at(pp - 1) + fx * at(pp));
+          const float yp = gy1 * (gx1 * at(pp) + fx * at(pp + 1)) +
+                           fy * (gx1 * at(p2) + fx * at(p2 + 1));
+          const float ym = gy1 * (gx1 * at(pm) + fx * at(pm + 1)) +
+                           fy * (gx1 * at(p) + fx * at(p + 1));
+          desc_targets(vt, rx, ry, xp - xm, yp - ym, th);
+          desc_commit(hist, lane, true, vt);
+        }
+      }
+    }
+}
+
 // One block of kKpWarps warps per output keypoint; same lane-private
 // histogram scheme as the orientation (merge order: warp, then lane).
 // Plain mode samples the pixel grid around the keypoint. DSP mode samples, for
@@ -435,6 +566,10 @@ __constant__ float kDspScale[5] = {0.5f, 0.70710678118654752f, 1.0f, 1.414213562
 // scales vote into the same histogram (pooling before normalisation).
 // Positions are kept relative to the integer keypoint pixel, so the
 // interpolation weights keep full FP32 precision in large octaves.
+// MIXED: the pyramid has binary16 octaves (fp16 storage mode); the kernel then
+// carries both sample sweeps and picks one per keypoint. Without it only the
+// FP32 sweep is compiled in.
+template <bool MIXED>
 __global__ void __launch_bounds__(kKpWarps * 32, 6) k_descriptor(const Desc *__restrict__ d) {
   pdl_wait();
   extern __shared__ __align__(16) float dsm[];
@@ -481,135 +616,10 @@ __global__ void __launch_bounds__(kKpWarps * 32, 6) k_descriptor(const Desc *__r
       for (int k = lane; k < kDescLen * kDescCols / 4; k += 32) h4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncwarp();
-    // The sample sweeps, instantiated once per storage type of the level so
-    // that no load tests it.
-    auto sweep = [&](auto half_tag) {
-      constexpr bool HF = decltype(half_tag)::value;
-      if (!d->dsp) {
-        // Samples: integer offsets (i, jy) in [-R, R]^2 inside the image whose
-        // rotated bin coordinates fall in (-1, 4)^2, i.e. inside a square of half
-        // side h = 2.5 bins around the keypoint. Warp w takes rows jlo + w,
-        // jlo + w + 4, ... (at most 32 of them, one per lane): each lane cuts its
-        // row to an interval, a superset of the square's chord widened by 2
-        // pixels so that rounding can only add candidates, and a warp scan lays
-        // the intervals end to end. The warp then sweeps that list 32 samples at
-        // a time, and the exact test below decides, so the sample set is the
-        // same as a sweep of the whole window.
-        const float h = 2.5f * wbin;
-        const int ilo = max(-R, 1 - r.x), ihi = min(R, od.W - 2 - r.x);
-        const int jlo = max(-R, 1 - r.y), jhi = min(R, od.H - 2 - r.y);
-        const float ica = fabsf(ct) * (float)(R + 1) < 1.0f ? 0.f : 1.0f / ct;
-        const float isa = fabsf(st) * (float)(R + 1) < 1.0f ? 0.f : -1.0f / st;
-        // Rows per warp are at most (2R + 1) / 4 + 1, i.e. 20 for the largest
-        // octave-relative scale of the default parameters; larger windows take
-        // several rounds of 32 rows.
-        for (int rb = 0; jlo + warp + kKpWarps * rb <= jhi; rb += 32) {
-          int len = 0, a0 = 0;
-          {
-            const int jy = jlo + warp + kKpWarps * (rb + lane);
-            if (jy <= jhi) {
-              const float oy = (float)jy - r.dy;
-              float lo = -1e30f, hi = 1e30f;
-              // slab a * ox + b in (-h, h) for (a, b) = (ct, st * oy), (-st, ct * oy)
-  #pragma unroll
-              for (int k = 0; k < 2; k++) {
-                const float ia = k ? isa : ica, b = k ? ct * oy : st * oy;
-                if (ia == 0.f) {
-                  if (fabsf(b) >= h + 2.0f) hi = -1e30f;  // |a * ox| < 1: the row misses the slab
-                } else {
-                  const float e0 = (-h - b) * ia, e1 = (h - b) * ia;
-                  lo = fmaxf(lo, fminf(e0, e1));
-                  hi = fminf(hi, fmaxf(e0, e1));
-                }
-              }
-              int a1 = ihi;
-              a0 = ilo;
-              if (hi < lo) {
-                a1 = a0 - 1;
-              } else {
-                if (lo + r.dx > (float)ilo) a0 = max(ilo, (int)floorf(lo + r.dx) - 2);
-                if (hi + r.dx < (float)ihi) a1 = min(ihi, (int)ceilf(hi + r.dx) + 2);
-              }
-              len = max(0, a1 - a0 + 1);
-            }
-          }
-          // Exclusive scan of the interval lengths over the warp's rows.
-          int pre = len;
-  #pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, pre, o);
-            if (lane >= o) pre += v;
-          }
-          const int tot = __shfl_sync(0xffffffffu, pre, 31);
-          pre -= len;
-          int *wlo = s_lo[warp], *wpre = s_pre[warp];
-          wlo[lane] = a0;
-          wpre[lane] = pre;
-          if (lane == 31) wpre[32] = tot;
-          __syncwarp();
-          int row = 0;
-          // Warp-uniform trip count: every lane reaches the commit's __syncwarp.
-          for (int q0 = 0; q0 < tot; q0 += 32) {
-            const int q = q0 + lane;
-            bool ok = q < tot;
-            Vote vt;
-            if (ok) {
-              while (wpre[row + 1] <= q) row++;
-              const int jy = jlo + warp + kKpWarps * (rb + row);
-              const int i = wlo[row] + (q - wpre[row]);
-              const float ox = (float)i - r.dx, oy = (float)jy - r.dy;
-              const float rx = (ct * ox + st * oy) * inv_w;
-              const float ry = (-st * ox + ct * oy) * inv_w;
-              const float u = rx + 1.5f, v = ry + 1.5f;
-              ok = u > -1.f && u < 4.f && v > -1.f && v < 4.f;
-              if (ok) {
-                const long long q = lofs + (long long)(r.y + jy) * od.pitch + (r.x + i);
-                const float gx = lvl_ld(L, HF, q + 1) - lvl_ld(L, HF, q - 1);
-                const float gy = lvl_ld(L, HF, q + od.pitch) - lvl_ld(L, HF, q - od.pitch);
-                desc_targets(vt, rx, ry, gx, gy, th);
-              }
-            }
-            desc_commit(hist, lane, ok, vt);
-          }
-          __syncwarp();  // the next round rewrites this warp's interval table
-        }
-      } else {
-        for (int f = 0; f < 5; f++) {
-          const float wb = wbin * kDspScale[f];
-          for (int idx = tid; idx < 32 * 32; idx += kKpWarps * 32) {
-            const float rx = ((float)(idx & 31) + 0.5f) * 0.125f - 2.0f;
-            const float ry = ((float)(idx >> 5) + 0.5f) * 0.125f - 2.0f;
-            const float xr = r.dx + wb * (ct * rx - st * ry);  // relative to pixel (r.x, r.y)
-            const float yr = r.dy + wb * (st * rx + ct * ry);
-            const float xf = floorf(xr), yf = floorf(yr);
-            const int x0 = r.x + (int)xf, y0 = r.y + (int)yf;
-            const bool ok = !(x0 < 1 || x0 > od.W - 3 || y0 < 1 || y0 > od.H - 3);
-            Vote vt;
-            if (!ok) {  // (1024 samples per scale: the trip count is warp-uniform)
-              desc_commit(hist, lane, false, vt);
-              continue;
-            }
-            const float fx = xr - xf, fy = yr - yf, gx1 = 1.f - fx, gy1 = 1.f - fy;
-            const long long p = lofs + (long long)y0 * od.pitch + x0;
-            const long long pm = p - od.pitch, pp = p + od.pitch, p2 = pp + od.pitch;
-            auto at = [&](long long i) { return lvl_ld(L, HF, i); };
-            // L(x + 1, y) - L(x - 1, y) and L(x, y + 1) - L(x, y - 1), bilinear
-            const float xp = gy1 * (gx1 * at(p + 1) + fx * at(p + 2)) +
-                             fy * (gx1 * at(pp + 1) + fx * at(pp + 2));
-            const float xm = gy1 * (gx1 * at(p - 1) + fx * at(p)) +
-                             fy * (gx1 * at(pp - 1) + fx * at(pp));
-            const float yp = gy1 * (gx1 * at(pp) + fx * at(pp + 1)) +
-                             fy * (gx1 * at(p2) + fx * at(p2 + 1));
-            const float ym = gy1 * (gx1 * at(pm) + fx * at(pm + 1)) +
-                             fy * (gx1 * at(p) + fx * at(p + 1));
-            desc_targets(vt, rx, ry, xp - xm, yp - ym, th);
-            desc_commit(hist, lane, true, vt);
-          }
-        }
-      }
-    };
-    if (hf) sweep(std::true_type{});
-    else sweep(std::false_type{});
+    if (MIXED && hf)
+      desc_sweep<true>(d, r, od, L, lofs, wbin, inv_w, th, st, ct, R, hist, lane, warp, s_lo, s_pre);
+    else
+      desc_sweep<false>(d, r, od, L, lofs, wbin, inv_w, th, st, ct, R, hist, lane, warp, s_lo, s_pre);
     __syncthreads();
     // Bin tid: per warp, the 16 columns starting at column (tid / 2) % 16 (with
     // the layout [bin][16], the 32 threads of a warp then read 32 distinct
@@ -696,12 +706,18 @@ cudaError_t launch_select(const Desc *d, int grid, cudaStream_t s) {
 int descriptor_smem_bytes() { return kKpWarps * kDescWarpFloats * (int)sizeof(float); }
 
 cudaError_t descriptor_set_attributes() {
-  return cudaFuncSetAttribute(k_descriptor, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              descriptor_smem_bytes());
+  cudaError_t e = cudaFuncSetAttribute(k_descriptor<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       descriptor_smem_bytes());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_descriptor<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             descriptor_smem_bytes());
+  return e;
 }
 
-cudaError_t launch_descriptor(const Desc *d, int grid, cudaStream_t s) {
-  return launch_pdl(k_descriptor, grid, kKpWarps * 32, descriptor_smem_bytes(), s, d);
+cudaError_t launch_descriptor(const Desc *d, int grid, cudaStream_t s, bool mixed) {
+  if (mixed) return launch_pdl(k_descriptor<true>, grid, kKpWarps * 32, descriptor_smem_bytes(), s, d);
+  return launch_pdl(k_descriptor<false>, grid, kKpWarps * 32, descriptor_smem_bytes(), s, d);
 }
 
 }  // namespace sift

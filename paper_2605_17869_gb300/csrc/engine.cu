@@ -552,7 +552,7 @@ cudaError_t Engine::enqueue_all(cudaStream_t s, int M, int modes, std::vector<Pr
   rec(PC_ORIENT, [&] { return launch_orientation(d, n_sm_ * 8, s); });
   rec(PC_KEYPOINT, [&] { return launch_ori_compact(d, g4, s); }, 3);
   rec(PC_KEYPOINT, [&] { return launch_select(d, n_sm_, s); });
-  rec(PC_DESCRIPTOR, [&] { return launch_descriptor(d, n_sm_ * 6, s); });
+  rec(PC_DESCRIPTOR, [&] { return launch_descriptor(d, n_sm_ * 6, s, P_.fp16_pyramid != 0); });
   return e;
 }
 

@@ -227,7 +227,8 @@ cudaError_t launch_refine(const Desc *d, int grid, cudaStream_t s);
 cudaError_t launch_orientation(const Desc *d, int grid, cudaStream_t s);
 cudaError_t launch_ori_compact(const Desc *d, int grid, cudaStream_t s);
 cudaError_t launch_select(const Desc *d, int grid, cudaStream_t s);
-cudaError_t launch_descriptor(const Desc *d, int grid, cudaStream_t s);
+// mixed: the pyramid has binary16 octaves (fp16 storage mode).
+cudaError_t launch_descriptor(const Desc *d, int grid, cudaStream_t s, bool mixed = false);
 
 // Pack the outputs of the batch described by d into one block (describe.cu).
 cudaError_t launch_pack(const Desc *d, void *dst, int n_sm, cudaStream_t s);

@@ -4,6 +4,8 @@ Each served result must be bit-identical to the same image extracted alone:
 requests are batched with whatever else is in flight, and batching never
 changes an image's arithmetic. Autotuned tile shapes change only the work
 distribution, so tuned and default runs must also agree bit for bit."""
+import time
+
 import pytest
 
 from workloads import synth
@@ -43,6 +45,39 @@ def test_served_results_equal_singleton_runs():
         lat.append(ms)
         srv.release(t)
     assert all(v > 0 for v in lat)
+    srv.close()
+
+
+def test_admitted_requests_overlap_on_the_device_and_match_singletons():
+    """Continuous batching: requests that arrive while others are on the GPU
+    are admitted into steps on the other lanes, and those steps run on the
+    device at the same time (their CUDA-event intervals intersect); each result
+    is still bit-identical to the image extracted alone."""
+    shapes = [(1080, 1920), (480, 640), (720, 1280), (1080, 1920), (600, 800), (1080, 1920)] * 4
+    imgs = [torch.from_numpy(synth.make_image(synth.rng_for(42, i), *s)).cuda()
+            for i, s in enumerate(shapes)]
+    ref_ex = pkg.Extractor(max_kpts=2048)
+    refs = [ref_ex.extract(im) for im in imgs]
+    torch.cuda.synchronize()
+    ex = pkg.Extractor(max_kpts=2048)
+    srv = pkg.Server(ex, budget_bytes=4 << 30, max_slots=8)
+    tickets = []
+    for im in imgs:                              # each arrives while earlier ones run
+        tickets.append(srv.submit(im))
+        time.sleep(2e-4)
+    for t, r in zip(tickets, refs):
+        f, _, st = srv.result(t)
+        assert st in (pkg.SIFT_OK, pkg.SIFT_W_TRUNCATED)
+        assert _same(f, r)
+        srv.release(t)
+    steps = srv.steps()
+    assert sum(n for _, n, _, _ in steps) == len(imgs)
+    assert all(t1 > t0 for _, _, t0, t1 in steps)
+    overlaps = [(a, b) for i, a in enumerate(steps) for b in steps[i + 1:]
+                if a[0] != b[0] and a[2] < b[3] and b[2] < a[3]]
+    print(f"{len(steps)} steps on lanes {sorted(set(s[0] for s in steps))}, "
+          f"{len(overlaps)} overlapping pairs on different lanes")
+    assert overlaps, steps
     srv.close()
 
 
