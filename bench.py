@@ -424,14 +424,23 @@ def gpu_arm(args, rank, world, pool, batch):
 
     ext_kw = dict(upsample=0, max_kpts=MAX_KPTS)
     ex = pkg.Extractor(**ext_kw)
-    if args.tuning:
-        ex.set_tuning(args.tuning)
-    else:
-        ex.autotune(max(h for h, _ in shapes), max(w for _, w in shapes))
-    tuning = ex.get_tuning()
 
     def step():
         ex.extract_batch_async(imgs, stream)
+
+    autotune = None
+    if args.tuning:
+        ex.set_tuning(args.tuning)
+    else:
+        # The defaults first (32-row tiles, occupancy-maximum grids), then the
+        # batch autotuner on this very batch; the timed steps use its choice.
+        t_def, _ = timed_steps(torch, step, max(10, args.steps // 4), args.warmup, flush, stream)
+        t0 = time.perf_counter()
+        _, hit = ex.autotune_batch(imgs, stream, cache=args.tuning_cache or None)
+        torch.cuda.synchronize()
+        autotune = {"untuned_ms_per_step": round(statistics.mean(t_def), 4),
+                    "search_s": round(time.perf_counter() - t0, 3), "from_cache": hit}
+    tuning = ex.get_tuning()
 
     if args.minimal:
         times, _ = timed_steps(torch, step, args.steps, args.warmup, flush, stream)
@@ -472,6 +481,8 @@ def gpu_arm(args, rank, world, pool, batch):
     if rank == 0 and not args.no_configs:
         extra["fp16_pyramid"] = fp16_side(torch, pkg, imgs, shapes, mpix, flush, stream, tuning,
                                           max(10, args.steps // 2))
+        extra["keypoint_heavy"] = keypoint_heavy_side(torch, pkg, flush, stream, tuning,
+                                                      max(10, args.steps // 2))
         extra["homography_sequence"] = homography_side(torch, pkg, flush, stream, tuning,
                                                        max(10, args.steps // 2))
         extra["single_and_pair"] = other_configs(torch, pkg, flush, stream, tuning)
@@ -497,6 +508,9 @@ def gpu_arm(args, rank, world, pool, batch):
         "gpu_launches": launches_per_step * args.steps,
         "gpu_launches_per_step": launches_per_step,
         "kernel_ms_per_step": {k: round(v[0], 4) for k, v in acc.items()},
+        "autotune": autotune and {**autotune, "tuned_ms_per_step": round(total_ms / args.steps, 4),
+                                  "untuned_over_tuned": round(autotune["untuned_ms_per_step"] /
+                                                              (total_ms / args.steps), 4)},
         "roofline": roofline,
         "per_class_roofline": per_class,
         "e2e": e2e,
@@ -524,6 +538,41 @@ def fp16_side(torch, pkg, imgs, shapes, mpix, flush, stream, tuning, steps):
             "kernel_ms_per_step": {k: round(v[0], 4) for k, v in cls.items()},
             "pyramid_bytes_per_step": _pyramid_bytes(shapes, False, True),
             "pyramid_bytes_per_step_fp32": _pyramid_bytes(shapes, False, False)}
+
+
+def keypoint_heavy_side(torch, pkg, flush, stream, tuning, steps):
+    """The per-keypoint stages under keypoint-heavy load: 4 images of 1600x1200
+    (the wide-baseline generator with 200 blobs and strong 1/f texture, std
+    0.12), 2x upsampled, cap 8192, one batched call. Reports keypoints per
+    image and, for refinement, orientation and descriptor, their device time
+    and inputs/s: candidates for refinement, refined keypoints for
+    orientation, kept (capped) keypoints for the descriptor."""
+    imgs_np = [synth.make_image(synth.rng_for(2, 700 + i), 1200, 1600, n_blobs=200,
+                                fractal_std=0.12) for i in range(4)]
+    imgs = _device_images(imgs_np, torch)
+    ex = pkg.Extractor(upsample=1, max_kpts=MAX_KPTS)
+    ex.set_tuning(tuning)
+    step = lambda: ex.extract_batch_async(imgs, stream)  # noqa: E731
+    t, _ = timed_steps(torch, step, steps, 3, flush, stream)
+    counts = ex._counts[:len(imgs)].tolist()
+    _, stats = ex.stats(len(imgs))
+    cls = profiled_classes(torch, ex, step, flush, 3)
+    ex.close()
+    n_in = {"refine": sum(s[0] for s in stats),        # candidates after the contrast gate
+            "orientation": sum(s[1] for s in stats),   # refined keypoints
+            "descriptor": sum(counts)}                 # oriented keypoints kept by the cap
+    out = {"workload": "4 x 1600x1200, 200 blobs + 1/f texture (std 0.12), 2x upsampled, cap 8192",
+           "keypoints_per_image": counts,
+           "candidates_per_image": [s[0] for s in stats],
+           "refined_per_image": [s[1] for s in stats],
+           "oriented_per_image": [s[2] for s in stats],
+           "ms_per_step": round(statistics.mean(t), 4),
+           "kernel_ms_per_step": {k: round(v[0], 4) for k, v in cls.items()}}
+    for k, n in n_in.items():
+        ms = cls.get(k, (0.0, 0))[0]
+        if ms > 0 and n:
+            out[k] = {"ms": round(ms, 4), "inputs": n, "inputs_per_s": round(n / (ms / 1e3), 1)}
+    return out
 
 
 def homography_side(torch, pkg, flush, stream, tuning, steps):
@@ -734,10 +783,15 @@ def main():
     ap.add_argument("--pair-only", action="store_true",
                     help="only the single-image and wide-baseline pair runs (extraction, "
                          "matcher, MAGSAC++), e.g. for profiling those kernels")
+    ap.add_argument("--keypoint-heavy", action="store_true",
+                    help="only the keypoint-heavy run (4 x 1600x1200 textured, 2x upsampled), "
+                         "e.g. for profiling the orientation and descriptor kernels")
     ap.add_argument("--images", type=int, default=N_IMAGES,
                     help=f"images per batch (default {N_IMAGES}; the first n of the batch)")
     ap.add_argument("--serving-requests", type=int, default=SERVING_REQUESTS)
     ap.add_argument("--tuning", default="", help='fixed tiles, e.g. {"blur_tile_rows": [32,...]}')
+    ap.add_argument("--tuning-cache", default="",
+                    help="tuning cache file for the batch autotuner (default: none, always search)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank = int(os.environ.get("RANK", 0))
@@ -752,13 +806,17 @@ def main():
             print(json.dumps(reference_arm(args, pool, n_workers, batch)))
         return
 
-    if args.pair_only:
+    if args.pair_only or args.keypoint_heavy:
         import torch
         import paper_2605_17869_gb300 as pkg
         stream = torch.cuda.current_stream()
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
         tuning = args.tuning or '{"blur_tile_rows": [32, 32, 32, 32, 32]}'
-        print(json.dumps({"single_and_pair": other_configs(torch, pkg, flush, stream, tuning)}))
+        if args.keypoint_heavy:
+            print(json.dumps({"keypoint_heavy": keypoint_heavy_side(
+                torch, pkg, flush, stream, tuning, max(1, args.steps))}))
+        else:
+            print(json.dumps({"single_and_pair": other_configs(torch, pkg, flush, stream, tuning)}))
         return
 
     # The worker pool is started (spawn) before any GPU call; it generates the

@@ -296,16 +296,73 @@ sift_status sift_kernel_times(sift_handle *h, double *ms, int *launches, int n_c
  * graph replay). Host-only: no synchronisation. */
 sift_status sift_last_launch_count(sift_handle *h, int *kernels);
 
-/* Autotuner: for each level blur of octave 0, time the two tile heights (32
- * and 64 rows) on a synthetic H x W workload on `stream` and keep the faster;
- * octaves above 0 always use 32-row tiles, which give their few tiles more
- * parallelism. Tile shapes change only how work is distributed, never the
- * arithmetic of any output, so tuned and untuned runs give bit-identical
- * results. The choice can be saved and restored as a short JSON string,
- * {"blur_tile_rows": [r1, ..., rS+2]} with each r 32 or 64. */
+/* Autotuner. The tuning is the set of launch shapes the extraction uses
+ * (tile heights and persistent-grid sizes). Tiles and grids decide only
+ * which CTA computes what, never the arithmetic, so every tuning gives
+ * bit-identical outputs. Its JSON form, every key optional:
+ *   {"blur_tile_rows": [[r_1, ..., r_{S+2}], ...],  per octave, one entry per
+ *                                                   level blur; 32 or 64 rows
+ *                                                   (binary16 levels of the
+ *                                                   fp16 mode always use 32);
+ *                                                   a flat list sets octave 0
+ *    "blur_ctas_per_sm": [c_0, c_1, ...],           level blurs, per octave
+ *    "extrema_ctas_per_sm": c, "orientation_ctas_per_sm": c,
+ *    "descriptor_ctas_per_sm": c}
+ * with c the resident CTAs per SM of that persistent grid, 0 (the default)
+ * meaning the kernel's occupancy maximum and larger values capped by it.
+ * sift_set_tuning changes only the keys given (SIFT_E_INVALID on a malformed
+ * string, an unknown key or a value out of range); sift_get_tuning writes the
+ * full tuning (SIFT_E_INVALID if len is too small).
+ *
+ * sift_autotune: for each level blur of octave 0, time 32- and 64-row tiles
+ * on a synthetic H x W pyramid on `stream` and keep the faster. */
 sift_status sift_autotune(sift_handle *h, int H, int W, void *stream);
 sift_status sift_get_tuning(sift_handle *h, char *json, size_t len);
 sift_status sift_set_tuning(sift_handle *h, const char *json);
+
+/* Autotune on a real batch: the arguments of sift_extract_batch (1 to 128
+ * images), plus from_cache (host, may be NULL) set to 1 when the tuning came
+ * from the cache. Coordinate descent over whole extraction steps of this
+ * batch on `stream`, from the defaults: 64-row tiles per level of the three
+ * largest octaves, then fewer resident CTAs per SM for their level blurs and
+ * for the extrema, orientation and descriptor grids; a change is kept only if
+ * the step gets at least 1% faster, and the result is re-timed against the
+ * defaults at the end. The chosen tuning stays on the handle, and on return
+ * the output buffers hold this batch's results (a run with that tuning;
+ * identical to sift_extract_batch's). Synchronises `stream` while timing.
+ * With a tuning cache set (sift_set_tuning_cache), the batch's signature
+ * (device and sift_batch_signature) is looked up first: a hit applies the
+ * stored tuning and runs the batch once, without timing; a miss tunes and then
+ * stores the result. SIFT_E_INVALID also for an unreadable cache file or an
+ * invalid entry, and when the cache cannot be written. */
+sift_status sift_autotune_batch(sift_handle *h, int n, const float *const *imgs_dev, const int *H,
+                                const int *W, const int *pitch_elems, void *stream,
+                                const sift_kpts_dev *out_kpts, float *const *out_desc,
+                                int *out_counts_dev, int *from_cache);
+
+/* Tuning cache file used by sift_autotune_batch on this handle (path copied;
+ * NULL or "" switches the cache off). The file is JSON,
+ * {"version": 1, "entries": {"<signature>": <tuning JSON>, ...}}, rewritten
+ * through a temporary file and a rename, so readers never see a partial file;
+ * with concurrent writers the last rename wins. */
+sift_status sift_set_tuning_cache(sift_handle *h, const char *path);
+
+/* Host only. The batch part of a tuning-cache signature: every parameter that
+ * changes the work, the image count, total pixels, longest side and a 64-bit
+ * FNV-1a hash of the sorted (H, W) list (a reordered batch has the same
+ * signature). sift_autotune_batch prefixes "sm<major><minor>x<SMs>;".
+ * SIFT_E_INVALID on invalid parameters or sizes, or if len is too small. */
+sift_status sift_batch_signature(const sift_params *p, int n, const int *H, const int *W,
+                                 char *out, size_t len);
+
+/* Host only: read or write one entry of a tuning cache file. get returns
+ * SIFT_E_NOTFOUND when the file or the entry does not exist and SIFT_E_INVALID
+ * for a malformed file or a too-small buffer; put replaces or appends the
+ * entry (json must be one JSON object) and refuses (SIFT_E_INVALID) to
+ * overwrite a file it cannot parse. Signatures may not contain '"', '\\' or
+ * control characters. */
+sift_status sift_tuning_cache_get(const char *path, const char *signature, char *json, size_t len);
+sift_status sift_tuning_cache_put(const char *path, const char *signature, const char *json);
 
 /* ---------------------------------------------------------------- serving
  * Continuous batching: a scheduler thread admits submitted requests while

@@ -24,6 +24,8 @@ __all__ = [
     "sift_extract_noalloc",
     "sift_last_stats", "sift_pyramid_size", "sift_octave_geometry", "sift_build_pyramid", "sift_set_profiling",
     "sift_kernel_times", "sift_last_launch_count", "sift_autotune", "sift_get_tuning", "sift_set_tuning",
+    "sift_autotune_batch", "sift_set_tuning_cache", "sift_batch_signature", "sift_tuning_cache_get",
+    "sift_tuning_cache_put",
     "sift_serve_create", "sift_serve_submit", "sift_serve_poll", "sift_serve_wait",
     "sift_serve_release", "sift_serve_steps", "sift_serve_destroy", "sift_last_error", "sift_version",
     "SIFT_OK", "SIFT_W_TRUNCATED", "SIFT_PENDING", "SIFT_E_INVALID", "SIFT_E_OOM",
@@ -199,13 +201,54 @@ def sift_autotune(handle, H: int, W: int, stream: int) -> None:
 
 
 def sift_get_tuning(handle) -> str:
-    buf = ctypes.create_string_buffer(512)
-    _check(_lib().sift_get_tuning(handle, buf, 512), handle, "sift_get_tuning")
+    buf = ctypes.create_string_buffer(4096)
+    _check(_lib().sift_get_tuning(handle, buf, 4096), handle, "sift_get_tuning")
     return buf.value.decode()
 
 
 def sift_set_tuning(handle, js: str) -> None:
     _check(_lib().sift_set_tuning(handle, js.encode()), handle, "sift_set_tuning")
+
+
+def sift_autotune_batch(handle, img_ptrs, Hs, Ws, pitches, stream: int, kpts_list, desc_ptrs,
+                        counts_ptr: int) -> bool:
+    """Returns True when the tuning came from the handle's tuning cache."""
+    n = len(img_ptrs)
+    hit = c_int(0)
+    _check(_lib().sift_autotune_batch(
+        handle, n, (c_void_p * n)(*img_ptrs), (c_int * n)(*Hs), (c_int * n)(*Ws),
+        (c_int * n)(*pitches), c_void_p(stream), (SiftKptsDev * n)(*kpts_list),
+        (c_void_p * n)(*desc_ptrs), c_void_p(counts_ptr), byref(hit)), handle,
+        "sift_autotune_batch")
+    return bool(hit.value)
+
+
+def sift_set_tuning_cache(handle, path) -> None:
+    _check(_lib().sift_set_tuning_cache(handle, path.encode() if path else None), handle,
+           "sift_set_tuning_cache")
+
+
+def sift_batch_signature(params: SiftParams, Hs, Ws) -> str:
+    n = len(Hs)
+    buf = ctypes.create_string_buffer(1024)
+    _check(_lib().sift_batch_signature(byref(params), n, (c_int * n)(*Hs), (c_int * n)(*Ws), buf,
+                                       1024), None, "sift_batch_signature")
+    return buf.value.decode()
+
+
+def sift_tuning_cache_get(path: str, signature: str):
+    """The stored tuning JSON, or None when the file or the entry is missing."""
+    buf = ctypes.create_string_buffer(4096)
+    st = _lib().sift_tuning_cache_get(path.encode(), signature.encode(), buf, 4096)
+    if st == SIFT_E_NOTFOUND:
+        return None
+    _check(st, None, "sift_tuning_cache_get")
+    return buf.value.decode()
+
+
+def sift_tuning_cache_put(path: str, signature: str, js: str) -> None:
+    _check(_lib().sift_tuning_cache_put(path.encode(), signature.encode(), js.encode()), None,
+           "sift_tuning_cache_put")
 
 
 def sift_serve_create(handle, budget_bytes: int, max_slots: int) -> c_void_p:
@@ -543,6 +586,24 @@ class Extractor:
     def autotune(self, H: int, W: int):
         sift_autotune(self.handle, H, W, _torch().cuda.current_stream().cuda_stream)
         return sift_get_tuning(self.handle)
+
+    def autotune_batch(self, imgs, stream=None, cache=None):
+        """Tune the launch shapes on this batch (sift_autotune_batch) and leave
+        its results in the output buffers, like extract_batch_async. With
+        cache (a file path), the tuning is looked up there first and stored
+        there after a search. Returns (tuning JSON, whether it came from the
+        cache)."""
+        torch = _torch()
+        dims = [self._check_img(im) for im in imgs]
+        s = stream if stream is not None else torch.cuda.current_stream()
+        bufs = self._buffers(len(imgs))
+        sift_set_tuning_cache(self.handle, cache)
+        hit = sift_autotune_batch(self.handle, [im.data_ptr() for im in imgs],
+                                  [d[0] for d in dims], [d[1] for d in dims],
+                                  [d[2] for d in dims], s.cuda_stream, [b.kpts() for b in bufs],
+                                  [b.desc.data_ptr() for b in bufs], self._counts.data_ptr())
+        self._last_batch = len(imgs)
+        return sift_get_tuning(self.handle), hit
 
     def get_tuning(self) -> str:
         return sift_get_tuning(self.handle)

@@ -71,6 +71,15 @@ SIGNATURES = {
     "sift_autotune": (c_int, [c_void_p, c_int, c_int, c_void_p]),
     "sift_get_tuning": (c_int, [c_void_p, c_char_p, c_size_t]),
     "sift_set_tuning": (c_int, [c_void_p, c_char_p]),
+    "sift_autotune_batch": (c_int, [c_void_p, c_int, POINTER(c_void_p), POINTER(c_int),
+                                    POINTER(c_int), POINTER(c_int), c_void_p,
+                                    POINTER(SiftKptsDev), POINTER(c_void_p), c_void_p,
+                                    POINTER(c_int)]),
+    "sift_set_tuning_cache": (c_int, [c_void_p, c_char_p]),
+    "sift_batch_signature": (c_int, [POINTER(SiftParams), c_int, POINTER(c_int), POINTER(c_int),
+                                     c_char_p, c_size_t]),
+    "sift_tuning_cache_get": (c_int, [c_char_p, c_char_p, c_char_p, c_size_t]),
+    "sift_tuning_cache_put": (c_int, [c_char_p, c_char_p, c_char_p]),
     "sift_serve_create": (c_int, [c_void_p, c_size_t, c_int, POINTER(c_void_p)]),
     "sift_serve_submit": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, POINTER(c_uint64)]),
     "sift_serve_poll": (c_int, [c_void_p, c_uint64, POINTER(SiftResult)]),

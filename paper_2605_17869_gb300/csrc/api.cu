@@ -28,6 +28,7 @@ struct sift_handle {
   void *magsac_ws = nullptr;  // MAGSAC++ workspace (stream-ordered allocation)
   size_t magsac_cap = 0;
   cudaStream_t magsac_stream = nullptr;
+  std::string tuning_cache;  // tuning cache file ("" none)
 };
 
 static sift_status fail(sift_handle *h, sift_status st, const std::string &m) {
@@ -328,15 +329,7 @@ sift_status sift_autotune(sift_handle *h, int H, int W, void *stream) {
 
 sift_status sift_get_tuning(sift_handle *h, char *json, size_t len) {
   if (!h || !json || len == 0) return SIFT_E_INVALID;
-  const sift::Tuning t = h->eng->tuning();
-  std::string s = "{\"blur_tile_rows\": [";
-  const int S = h->eng->params().n_scales;
-  for (int l = 1; l <= S + 2; l++) {
-    const int k = t.lvl_kind[l];
-    s += std::to_string(k == sift::TK_BLUR64 ? 64 : 32);
-    if (l < S + 2) s += ", ";
-  }
-  s += "]}";
+  const std::string s = sift::tuning_json(h->eng->tuning(), h->eng->params().n_scales);
   if (s.size() + 1 > len) return fail(h, SIFT_E_INVALID, "buffer too small");
   std::memcpy(json, s.c_str(), s.size() + 1);
   return SIFT_OK;
@@ -344,21 +337,70 @@ sift_status sift_get_tuning(sift_handle *h, char *json, size_t len) {
 
 sift_status sift_set_tuning(sift_handle *h, const char *json) {
   if (!h || !json) return SIFT_E_INVALID;
-  const char *p = std::strchr(json, '[');
-  if (!p) return fail(h, SIFT_E_INVALID, "expected {\"blur_tile_rows\": [...]}");
-  sift::Tuning t = h->eng->tuning();
-  const int S = h->eng->params().n_scales;
-  p++;
-  for (int l = 1; l <= S + 2; l++) {
-    char *end = nullptr;
-    const long v = std::strtol(p, &end, 10);
-    if (end == p || (v != 32 && v != 64))
-      return fail(h, SIFT_E_INVALID, "tile rows must be 32 or 64, one per level");
-    t.lvl_kind[l] = v == 64 ? sift::TK_BLUR64 : sift::TK_BLUR32;
-    p = end;
-    while (*p == ',' || *p == ' ') p++;
-  }
+  sift::Tuning t;
+  std::string why;
+  if (!sift::parse_tuning(json, h->eng->params().n_scales, h->eng->tuning(), &t, &why))
+    return fail(h, SIFT_E_INVALID, why);
   h->eng->set_tuning(t);
+  return SIFT_OK;
+}
+
+sift_status sift_set_tuning_cache(sift_handle *h, const char *path) {
+  if (!h) return SIFT_E_INVALID;
+  h->tuning_cache = path ? path : "";
+  return SIFT_OK;
+}
+
+sift_status sift_autotune_batch(sift_handle *h, int n, const float *const *imgs_dev, const int *H,
+                                const int *W, const int *pitch_elems, void *stream,
+                                const sift_kpts_dev *out_kpts, float *const *out_desc,
+                                int *out_counts_dev, int *from_cache) {
+  if (!h) return SIFT_E_INVALID;
+  if (h->serving) return fail(h, SIFT_E_INVALID, "handle is owned by a server");
+  if (n < 1 || n > sift::kMaxImg || !imgs_dev || !H || !W || !out_kpts || !out_desc ||
+      !out_counts_dev)
+    return fail(h, SIFT_E_INVALID, "null pointer argument or n outside 1..128");
+  if (from_cache) *from_cache = 0;
+  const int ms = h->eng->params().min_octave_side;
+  std::vector<ImgIn> in(n);
+  for (int i = 0; i < n; i++) {
+    const int p = pitch_elems ? pitch_elems[i] : W[i];
+    if (!imgs_dev[i] || !out_desc[i] || !kpts_ok(out_kpts[i]))
+      return fail(h, SIFT_E_INVALID, "null pointer in image " + std::to_string(i));
+    if (H[i] < ms || W[i] < ms || p < W[i])
+      return fail(h, SIFT_E_INVALID, "image " + std::to_string(i) + " smaller than min_octave_side");
+    if (!h->eng->addressable(H[i], W[i]))
+      return fail(h, SIFT_E_INVALID, "image " + std::to_string(i) + " too large");
+    in[i] = ImgIn{imgs_dev[i], H[i], W[i], p, out_kpts[i], out_desc[i], out_counts_dev + i};
+  }
+  h->split_batch = false;
+  const cudaStream_t s = (cudaStream_t)stream;
+  sift_status st = h->eng->init();
+  if (st != SIFT_OK) return pass(h, st);
+  const std::string sig =
+      h->eng->device_key() + ";" + sift::batch_signature(h->eng->params(), n, H, W);
+  if (!h->tuning_cache.empty()) {
+    std::string js;
+    st = sift::cache_get(h->tuning_cache.c_str(), sig.c_str(), &js);
+    if (st == SIFT_OK) {
+      sift::Tuning t;
+      std::string why;
+      if (!sift::parse_tuning(js.c_str(), h->eng->params().n_scales, sift::default_tuning(), &t,
+                              &why))
+        return fail(h, SIFT_E_INVALID, "tuning cache entry: " + why);
+      h->eng->set_tuning(t);
+      if (from_cache) *from_cache = 1;
+      return pass(h, h->eng->run(n, in.data(), s));
+    }
+    if (st != SIFT_E_NOTFOUND) return fail(h, st, "tuning cache unreadable: " + h->tuning_cache);
+  }
+  st = h->eng->autotune_batch(n, in.data(), s);
+  if (st != SIFT_OK) return pass(h, st);
+  if (!h->tuning_cache.empty()) {
+    const std::string js = sift::tuning_json(h->eng->tuning(), h->eng->params().n_scales);
+    st = sift::cache_put(h->tuning_cache.c_str(), sig.c_str(), js.c_str());
+    if (st != SIFT_OK) return fail(h, st, "tuning cache not writable: " + h->tuning_cache);
+  }
   return SIFT_OK;
 }
 

@@ -1,13 +1,12 @@
 // Orientation and descriptor (§3.2), output cap, and the deterministic
 // reduction scheme of §5 ("Bitwise Deterministic GPU Execution").
 //
-// Each keypoint is handled by one block of four warps. Threads sweep the
-// sample window in a fixed interleaved order and accumulate into
-// thread-private histogram columns in shared memory (layout [warp][bin][lane],
-// so no two threads ever touch the same word and there are no bank
-// conflicts). The columns are then summed bin by bin, warp by warp and lane by
-// lane. No atomics are used anywhere: the sum order is fixed by the code, so
-// outputs are bitwise reproducible.
+// Orientation takes one warp per keypoint, the descriptor one block of four
+// warps. Threads sweep the sample window in a fixed order and accumulate
+// into thread-private histogram columns in shared memory (a word is only ever
+// touched by one thread at a time, in an order fixed by the code); the
+// columns are then summed bin by bin in a fixed order. No atomics are used
+// anywhere, so outputs are bitwise reproducible.
 #include "scan.cuh"
 #include "sift_dev.cuh"
 
@@ -34,45 +33,129 @@ __device__ __forceinline__ float block_sum_f(float v, float *red) {
   return s;
 }
 
-// 4-byte global -> shared asynchronous copy; with valid false the destination
-// is zero-filled and no source byte is read.
-__device__ __forceinline__ void cp_async4_zfill(float *dst, const float *src, bool valid) {
-  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src),
-               "r"(valid ? 4 : 0)
-               : "memory");
-}
-
 __device__ __forceinline__ float sigma_of(const Desc *d, const RefRec &r) {
   return d->sigma0 * exp2f(((float)r.s + r.ds) / (float)d->n_scales);
 }
 
+// A pyramid level seen from one pixel: v[off] is the element off places
+// (off = dy * pitch + dx) from it, FP32 or (HF) binary16 widened to FP32.
+// The 64-bit address is formed once per keypoint; sample offsets are 32-bit.
+template <bool HF>
+struct LevelView {
+  const void *p;
+  __device__ __forceinline__ float operator[](int off) const {
+    if (HF) return __half2float(__ldg(static_cast<const __half *>(p) + off));
+    return __ldg(static_cast<const float *>(p) + off);
+  }
+};
+template <bool HF>
+__device__ __forceinline__ LevelView<HF> level_at(const float *L, long long lofs, int pitch, int x,
+                                                  int y) {
+  const long long e = lofs + (long long)y * pitch + x;
+  if (HF) return {reinterpret_cast<const __half *>(L) + e};
+  return {L + e};
+}
+
 // ------------------------------------------------------------ orientation
 
-// One block of kKpWarps warps per candidate slot. Lane l of warp w votes into
-// its private column hist[w][.][l]; bin k is the sum over each warp's lanes,
-// then over the warps, in that fixed order.
-__global__ void __launch_bounds__(kKpWarps * 32) k_orientation(const Desc *__restrict__ d) {
+// One warp per kept candidate; a block holds kOriWarps independent warps.
+// The warp sweeps the (2R + 1)^2 window as one flat list of samples, lane l
+// taking samples l, l + 32, ...; lane l votes into its private column
+// hist[bin][l], and bin k is the sum of the 32 columns in a fixed order, so
+// the histogram is bitwise reproducible. MIXED: the pyramid has binary16
+// octaves (fp16 storage mode) and the level type is chosen per keypoint.
+constexpr int kOriWarps = 8;
+
+// Nearest-bin vote of one gradient: weight wgt into bin floor(36 theta / 2 pi
+// + 1/2) of lane's column.
+__device__ __forceinline__ void ori_vote(float (*hist)[32], int lane, float dx, float dy,
+                                         float wgt) {
+  const float mag = sqrtf(dx * dx + dy * dy);
+  float th = atan2f(dy, dx);
+  if (th < 0.f) th += kTwoPi;
+  int bin = (int)floorf(th * ((float)kOriBins / kTwoPi) + 0.5f);
+  if (bin >= kOriBins) bin -= kOriBins;
+  // |dx| = |dy|: theta is exactly 45 (2q + 1) degrees, a bin boundary the
+  // nearest-bin rule floor(36 theta / 2 pi + 1/2) resolves upward; decided in
+  // integers rather than left to the rounding of atan2f.
+  if (fabsf(dx) == fabsf(dy) && dx != 0.f) {
+    const int qd = dy > 0.f ? (dx > 0.f ? 0 : 1) : (dx < 0.f ? 2 : 3);
+    bin = (kOriBins * (2 * qd + 1) + 4) / 8 % kOriBins;
+  }
+  hist[bin][lane] += wgt * mag;
+}
+
+// The window's samples, lane l taking samples l, l + 32, l + 64, ... in that
+// order, two per step: the eight loads of a pair are issued before either
+// vote, so that more loads are in flight per warp.
+template <bool HF>
+__device__ __forceinline__ void ori_sweep(const float *__restrict__ L, long long lofs, int pitch,
+                                          int H, int W, int x0, int y0, int R, float ninv,
+                                          float (*hist)[32], int lane) {
+  const LevelView<HF> v = level_at<HF>(L, lofs, pitch, x0, y0);
+  const int side = 2 * R + 1, nsamp = side * side;
+  // Sample q = jj * side + c; advancing q by 32 adds dr rows and dc columns.
+  const int dr = 32 / side, dc = 32 - dr * side;
+  int jj = lane / side, c = lane - jj * side;
+  auto advance = [&]() {
+    c += dc;
+    jj += dr;
+    if (c >= side) {
+      c -= side;
+      jj++;
+    }
+  };
+  // Inside the window with a full 3 x 3 neighbourhood in the level.
+  auto inside = [&](int q, int i, int j) {
+    const int px = x0 + i, py = y0 + j;
+    return q < nsamp && px >= 1 && px <= W - 2 && py >= 1 && py <= H - 2;
+  };
+  for (int q = lane; q < nsamp; q += 64) {
+    const int i0 = c - R, j0 = jj - R;
+    advance();
+    const int i1 = c - R, j1 = jj - R;
+    advance();
+    const bool ok0 = inside(q, i0, j0), ok1 = inside(q + 32, i1, j1);
+    float a0 = 0.f, b0 = 0.f, e0 = 0.f, f0 = 0.f, a1 = 0.f, b1 = 0.f, e1 = 0.f, f1 = 0.f;
+    if (ok0) {
+      const int o = j0 * pitch + i0;
+      a0 = v[o + 1];
+      b0 = v[o - 1];
+      e0 = v[o + pitch];
+      f0 = v[o - pitch];
+    }
+    if (ok1) {
+      const int o = j1 * pitch + i1;
+      a1 = v[o + 1];
+      b1 = v[o - 1];
+      e1 = v[o + pitch];
+      f1 = v[o - pitch];
+    }
+    if (ok0) ori_vote(hist, lane, a0 - b0, e0 - f0, expf((float)(i0 * i0 + j0 * j0) * ninv));
+    if (ok1) ori_vote(hist, lane, a1 - b1, e1 - f1, expf((float)(i1 * i1 + j1 * j1) * ninv));
+  }
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(kOriWarps * 32, 4) k_orientation(const Desc *__restrict__ d) {
   pdl_wait();
-  __shared__ float hist[kKpWarps][kOriBins][32];
-  __shared__ float hpart[kKpWarps][kOriBins];
-  __shared__ float hsum[kOriBins];
-  __shared__ float hsm[kOriBins];
-  __shared__ float win[kOriWin];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ float s_hist[kOriWarps][kOriBins][32];
+  __shared__ float s_sum[kOriWarps][kOriBins];
+  __shared__ float s_sm[kOriWarps][kOriBins];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float(*hist)[32] = s_hist[warp];
+  float *hsum = s_sum[warp], *hsm = s_sm[warp];
   const int n = d->n_img;
   const int total = d->cand_flat[n];
   const bool upright = d->upright != 0;
-  // Block k takes the candidate slots k, k + G, k + 2G, ... (G blocks), 32 at
-  // a time: lane l of every warp looks at the l-th of them; warp 0 settles
-  // the rejected slots (no peak) and, in upright mode, the kept ones (one peak
-  // at angle 0); the kept slots are then taken one at a time by the whole
-  // block. Every warp computes the same ballot, so the loop over it is
-  // uniform across the block, and the interleave spreads the kept candidates
-  // evenly over the blocks.
-  const int G = gridDim.x;
-  for (int g0 = blockIdx.x; g0 < total; g0 += 32 * G) {
-    const int tl = g0 + lane * G;
+  // Warp g of NW takes the candidate slots g, g + NW, g + 2 NW, ..., 32 at a
+  // time (lane l looks at the l-th of them): the lanes settle the rejected
+  // slots (no peak) and, in upright mode, the kept ones (one peak at angle
+  // 0); the kept slots are then taken one at a time by the whole warp. The
+  // interleave spreads the kept candidates evenly over the warps.
+  const int NW = gridDim.x * kOriWarps;
+  for (int g0 = blockIdx.x + gridDim.x * warp; g0 < total; g0 += 32 * NW) {
+    const int tl = g0 + lane * NW;
     int bl = 0;
     long long sl = 0;
     bool keep = false;
@@ -80,7 +163,7 @@ __global__ void __launch_bounds__(kKpWarps * 32) k_orientation(const Desc *__res
       bl = find_owner(d->cand_flat, n, tl);
       sl = d->img[bl].cand_off + (tl - d->cand_flat[bl]);
       keep = d->code[sl] == RC_KEEP;
-      if (warp == 0 && (!keep || upright)) {
+      if (!keep || upright) {
         d->npk[sl] = keep ? 1 : 0;
         if (keep) d->angs[sl * kMaxPeaks] = 0.f;
       }
@@ -94,121 +177,62 @@ __global__ void __launch_bounds__(kKpWarps * 32) k_orientation(const Desc *__res
       const ImgDev &im = d->img[b];
       const RefRec r = d->ref[slot];
       const OctDev od = d->oct[im.oct0 + r.o];
-      // Level r.s of the candidate's octave: FP32, or binary16 (od.half).
-      const bool hf = od.half != 0;
       const float *L = d->pyr + od.lvl;
       const long long lofs = (long long)r.s * od.lstride;
       const float sw = 1.5f * sigma_of(d, r);
       const int R = (int)floorf(3.0f * sw + 0.5f);
       const float ninv = -1.0f / (2.0f * sw * sw);
-      for (int k = 0; k < kOriBins; k++) hist[warp][k][lane] = 0.f;
-      // The window's pixels are staged in shared memory in bands of B sample
-      // rows (B + 2 pixel rows of width 2R + 3, coalesced loads).
-      const int side = 2 * R + 1, wd = side + 2;
-      const int B = kOriWin / wd - 2;  // >= 1: the parameter check bounds R
-      for (int jb = -R; jb <= R; jb += B) {
-        const int nb = min(B, R - jb + 1);
-        // Every copy is issued before any is waited for (cp.async, 4 bytes,
-        // zero-filled outside the image, where no byte is read); binary16
-        // levels, which cp.async cannot copy, are loaded and widened.
-        for (int rr = warp; rr < nb + 2; rr += kKpWarps) {
-          const int gy = r.y + jb - 1 + rr;
-          const bool row_ok = gy >= 0 && gy < od.H;
-          const long long rofs = lofs + (long long)(row_ok ? gy : 0) * od.pitch;
-          float *dst = win + rr * wd;
-          for (int c = lane; c < wd; c += 32) {
-            const int gx = r.x - R - 1 + c;
-            const bool ok = row_ok && gx >= 0 && gx < od.W;
-            if (hf) dst[c] = ok ? lvl_ld(L, true, rofs + gx) : 0.f;
-            else cp_async4_zfill(dst + c, L + rofs + (ok ? gx : 0), ok);
-          }
-        }
-        asm volatile("cp.async.wait_all;\n" ::: "memory");
-        __syncthreads();
-        // Warp w takes the band's sample rows w, w + 4, ...; its lanes take the
-        // row's columns 32 at a time.
-        for (int jj = warp; jj < nb; jj += kKpWarps) {
-          const int j = jb + jj, py = r.y + j;
-          if (py < 1 || py > od.H - 2) continue;  // uniform over the warp
-          const float *wrow = win + (jj + 1) * wd + 1;
-          for (int c = lane; c < side; c += 32) {
-            const int i = c - R, px = r.x + i;
-            if (px < 1 || px > od.W - 2) continue;
-            const float *w = wrow + c;
-            const float dx = w[1] - w[-1];
-            const float dy = w[wd] - w[-wd];
-            const float mag = sqrtf(dx * dx + dy * dy);
-            float th = atan2f(dy, dx);
-            if (th < 0.f) th += kTwoPi;
-            int bin = (int)floorf(th * ((float)kOriBins / kTwoPi) + 0.5f);
-            if (bin >= kOriBins) bin -= kOriBins;
-            // |dx| = |dy|: theta is exactly 45 (2q + 1) degrees, a bin boundary
-            // the nearest-bin rule floor(36 theta / 2 pi + 1/2) resolves upward;
-            // decided in integers rather than left to the rounding of atan2f.
-            if (fabsf(dx) == fabsf(dy) && dx != 0.f) {
-              const int q = dy > 0.f ? (dx > 0.f ? 0 : 1) : (dx < 0.f ? 2 : 3);
-              bin = (kOriBins * (2 * q + 1) + 4) / 8 % kOriBins;
-            }
-            hist[warp][bin][lane] += expf((float)(i * i + j * j) * ninv) * mag;
-          }
-        }
-        __syncthreads();
-      }
-      // Bin sums in a fixed order: each warp adds up its own 32 columns of every
-      // bin (lane l: bins l and l + 32, reading the columns from a rotated start
-      // so that the lanes hit distinct banks), then the warp partials in warp
-      // order.
+#pragma unroll 4
+      for (int k = 0; k < kOriBins; k++) hist[k][lane] = 0.f;
+      if (MIXED && od.half != 0)
+        ori_sweep<true>(L, lofs, od.pitch, od.H, od.W, r.x, r.y, R, ninv, hist, lane);
+      else
+        ori_sweep<false>(L, lofs, od.pitch, od.H, od.W, r.x, r.y, R, ninv, hist, lane);
+      __syncwarp();
+      // Bin k: the 32 columns in the order k, k + 1, ... (mod 32); the rotated
+      // start puts the lanes on distinct banks.
       for (int k = lane; k < kOriBins; k += 32) {
         float sacc = 0.f;
 #pragma unroll 8
-        for (int q = 0; q < 32; q++) sacc += hist[warp][k][(q + k) & 31];
-        hpart[warp][k] = sacc;
+        for (int q = 0; q < 32; q++) sacc += hist[k][(q + k) & 31];
+        hsum[k] = sacc;
       }
-      __syncthreads();
-      if (tid < kOriBins) {
-        float sacc = hpart[0][tid];
+      __syncwarp();
+      for (int k = lane; k < kOriBins; k += 32) {
+        const float hm = hsum[(k + kOriBins - 1) % kOriBins];
+        const float hp = hsum[(k + 1) % kOriBins];
+        hsm[k] = 0.25f * hm + 0.5f * hsum[k] + 0.25f * hp;
+      }
+      __syncwarp();
+      float hmax = 0.f;
+      for (int k = lane; k < kOriBins; k += 32) hmax = fmaxf(hmax, hsm[k]);
 #pragma unroll
-        for (int w = 1; w < kKpWarps; w++) sacc += hpart[w][tid];
-        hsum[tid] = sacc;
-      }
-      __syncthreads();
-      if (tid < kOriBins) {
-        const float hm = hsum[(tid + kOriBins - 1) % kOriBins];
-        const float hp = hsum[(tid + 1) % kOriBins];
-        hsm[tid] = 0.25f * hm + 0.5f * hsum[tid] + 0.25f * hp;
-      }
-      __syncthreads();
-      if (warp == 0) {
-        float hmax = 0.f;
-        for (int k = lane; k < kOriBins; k += 32) hmax = fmaxf(hmax, hsm[k]);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) hmax = fmaxf(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
-        const float thr = d->ori_peak_ratio * hmax;
-        int base = 0;
-        for (int k0 = 0; k0 < kOriBins; k0 += 32) {
-          const int k = k0 + lane;
-          bool peak = false;
-          float ang = 0.f;
-          if (k < kOriBins) {
-            const float hk = hsm[k];
-            const float hm = hsm[(k + kOriBins - 1) % kOriBins];
-            const float hp = hsm[(k + 1) % kOriBins];
-            if (hk > hm && hk > hp && hk >= thr) {
-              peak = true;
-              float kf = (float)k + 0.5f * (hm - hp) / (hm - 2.0f * hk + hp);
-              if (kf < 0.f) kf += (float)kOriBins;
-              if (kf >= (float)kOriBins) kf -= (float)kOriBins;
-              ang = kf * (360.0f / (float)kOriBins);
-              if (ang >= 360.0f) ang -= 360.0f;
-            }
+      for (int o = 16; o > 0; o >>= 1) hmax = fmaxf(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
+      const float thr = d->ori_peak_ratio * hmax;
+      int base = 0;
+      for (int k0 = 0; k0 < kOriBins; k0 += 32) {
+        const int k = k0 + lane;
+        bool peak = false;
+        float ang = 0.f;
+        if (k < kOriBins) {
+          const float hk = hsm[k];
+          const float hm = hsm[(k + kOriBins - 1) % kOriBins];
+          const float hp = hsm[(k + 1) % kOriBins];
+          if (hk > hm && hk > hp && hk >= thr) {
+            peak = true;
+            float kf = (float)k + 0.5f * (hm - hp) / (hm - 2.0f * hk + hp);
+            if (kf < 0.f) kf += (float)kOriBins;
+            if (kf >= (float)kOriBins) kf -= (float)kOriBins;
+            ang = kf * (360.0f / (float)kOriBins);
+            if (ang >= 360.0f) ang -= 360.0f;
           }
-          const unsigned m = __ballot_sync(0xffffffffu, peak);
-          if (peak) d->angs[slot * kMaxPeaks + base + __popc(m & ((1u << lane) - 1u))] = ang;
-          base += __popc(m);
         }
-        if (lane == 0) d->npk[slot] = base;
+        const unsigned m = __ballot_sync(0xffffffffu, peak);
+        if (peak) d->angs[slot * kMaxPeaks + base + __popc(m & ((1u << lane) - 1u))] = ang;
+        base += __popc(m);
       }
-      __syncthreads();
+      if (lane == 0) d->npk[slot] = base;
+      __syncwarp();  // the next keypoint rewrites this warp's histogram
     }
   }
 }
@@ -350,8 +374,8 @@ __global__ void __launch_bounds__(1024) k_select(const Desc *__restrict__ d) {
 // different orientation parity), every lane is busy in both passes, and the
 // order in which a word receives its votes is fixed by the code.
 constexpr int kDescCols = 16;
-// Floats of one warp's histogram block: 128 bins x 16 columns + 32 scratch words.
-constexpr int kDescWarpFloats = kDescLen * kDescCols + 32;
+// Floats of one warp's histogram block: 128 bins x 16 columns.
+constexpr int kDescWarpFloats = kDescLen * kDescCols;
 
 // The trilinear targets of one gradient sample at bin coordinates (rx, ry)
 // from the keypoint, (u, v) = (rx, ry) + 3/2: weight m * exp(-(rx^2 + ry^2) /
@@ -381,42 +405,37 @@ __device__ __forceinline__ void desc_targets(Vote &v, float rx, float ry, float 
   v.oo = even0 ? o1 : o0;
   v.fe = even0 ? 1.f - f1 : f1;
   v.fo = even0 ? f1 : 1.f - f1;
+  // u0, v0 lie in [-1, 3] (u, v in (-1, 4)): cell u0 + du exists iff u0 >= 0
+  // (du = 0) or u0 <= 2 (du = 1), and the same for v.
+  const bool uok[2] = {u0 >= 0, u0 <= 2}, vok[2] = {v0 >= 0, v0 <= 2};
+  const int c00 = (v0 * 4 + u0) * 8;
 #pragma unroll
   for (int dv = 0; dv < 2; dv++) {
-    const int vv = v0 + dv;
-    const float wv = dv ? fv : 1.f - fv;
+    const float wv = wt * (dv ? fv : 1.f - fv);
 #pragma unroll
     for (int du = 0; du < 2; du++) {
-      const int uu = u0 + du;
       const float wu = du ? fu : 1.f - fu;
-      const bool in = vv >= 0 && vv <= 3 && uu >= 0 && uu <= 3;
-      v.cell[dv * 2 + du] = in ? (vv * 4 + uu) * 8 : -1;
-      v.w[dv * 2 + du] = wt * wv * wu;
+      v.cell[dv * 2 + du] = (uok[du] && vok[dv]) ? c00 + (dv * 4 + du) * 8 : -1;
+      v.w[dv * 2 + du] = wv * wu;
     }
   }
 }
 
 // Add the votes of the warp's lanes (ok: the lane has a sample) to the warp's
-// columns in the two passes described above. A vote that has no target (a cell
-// outside the grid, or no sample) goes with weight 0 to the lane's own scratch
-// word after the 128 bins, so every lane does the same 8 read-modify-writes
-// without branches; the scratch words are never read. Every lane of the warp
-// must call it.
+// columns in the two passes described above; a vote without a target (a cell
+// outside the grid, or no sample) is skipped. Every lane of the warp must call
+// it.
 __device__ __forceinline__ void desc_commit(float *hist, int lane, bool ok, const Vote &v) {
-  const int col = lane & (kDescCols - 1);
+  float *col = hist + (lane & (kDescCols - 1));
   const bool upper = lane >= 16;
-  float *scratch = hist + kDescLen * kDescCols + lane;
 #pragma unroll
   for (int pass = 0; pass < 2; pass++) {
     const bool even = (pass == 0) != upper;
     const int o = even ? v.oe : v.oo;
     const float f = even ? v.fe : v.fo;
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
-      const bool hit = ok && v.cell[k] >= 0;
-      float *p = hit ? hist + (v.cell[k] + o) * kDescCols + col : scratch;
-      *p += hit ? v.w[k] * f : 0.f;
-    }
+    for (int k = 0; k < 4; k++)
+      if (ok && v.cell[k] >= 0) col[(v.cell[k] + o) * kDescCols] += v.w[k] * f;
     __syncwarp();
   }
 }
@@ -433,6 +452,8 @@ __device__ __forceinline__ void desc_sweep(const Desc *__restrict__ d, const Ref
                                            float ct, int R, float *hist, int lane, int warp,
                                            int (*s_lo)[32], int (*s_pre)[33]) {
   const int tid = threadIdx.x;
+  const int pitch = od.pitch;
+  const LevelView<HF> lv = level_at<HF>(L, lofs, pitch, r.x, r.y);
     if (!d->dsp) {
       // Samples: integer offsets (i, jy) in [-R, R]^2 inside the image whose
       // rotated bin coordinates fall in (-1, 4)^2, i.e. inside a square of half
@@ -511,9 +532,9 @@ __device__ __forceinline__ void desc_sweep(const Desc *__restrict__ d, const Ref
             const float u = rx + 1.5f, v = ry + 1.5f;
             ok = u > -1.f && u < 4.f && v > -1.f && v < 4.f;
             if (ok) {
-              const long long q = lofs + (long long)(r.y + jy) * od.pitch + (r.x + i);
-              const float gx = lvl_ld(L, HF, q + 1) - lvl_ld(L, HF, q - 1);
-              const float gy = lvl_ld(L, HF, q + od.pitch) - lvl_ld(L, HF, q - od.pitch);
+              const int o = jy * pitch + i;
+              const float gx = lv[o + 1] - lv[o - 1];
+              const float gy = lv[o + pitch] - lv[o - pitch];
               desc_targets(vt, rx, ry, gx, gy, th);
             }
           }
@@ -530,7 +551,8 @@ __device__ __forceinline__ void desc_sweep(const Desc *__restrict__ d, const Ref
           const float xr = r.dx + wb * (ct * rx - st * ry);  // relative to pixel (r.x, r.y)
           const float yr = r.dy + wb * (st * rx + ct * ry);
           const float xf = floorf(xr), yf = floorf(yr);
-          const int x0 = r.x + (int)xf, y0 = r.y + (int)yf;
+          const int ix = (int)xf, iy = (int)yf;
+          const int x0 = r.x + ix, y0 = r.y + iy;
           const bool ok = !(x0 < 1 || x0 > od.W - 3 || y0 < 1 || y0 > od.H - 3);
           Vote vt;
           if (!ok) {  // (1024 samples per scale: the trip count is warp-uniform)
@@ -538,9 +560,9 @@ __device__ __forceinline__ void desc_sweep(const Desc *__restrict__ d, const Ref
             continue;
           }
           const float fx = xr - xf, fy = yr - yf, gx1 = 1.f - fx, gy1 = 1.f - fy;
-          const long long p = lofs + (long long)y0 * od.pitch + x0;
-          const long long pm = p - od.pitch, pp = p + od.pitch, p2 = pp + od.pitch;
-          auto at = [&](long long i) { return lvl_ld(L, HF, i); };
+          const int p = iy * pitch + ix;
+          const int pm = p - pitch, pp = p + pitch, p2 = pp + pitch;
+          auto at = [&](int i) { return lv[i]; };
           // L(x + 1, y) - L(x - 1, y) and L(x, y + 1) - L(x, y - 1), bilinear
           const float xp = gy1 * (gx1 * at(p + 1) + fx * at(p + 2)) +
                            fy * (gx1 * at(pp + 1) + fx * at(pp + 2));
@@ -688,8 +710,9 @@ cudaError_t launch_pack(const Desc *d, void *dst, int n_sm, cudaStream_t s) {
   return launch_plain(k_pack, n_sm * 4, kThreads, 0, s, d, static_cast<float4 *>(dst));
 }
 
-cudaError_t launch_orientation(const Desc *d, int grid, cudaStream_t s) {
-  return launch_pdl(k_orientation, grid, kKpWarps * 32, 0, s, d);
+cudaError_t launch_orientation(const Desc *d, int grid, cudaStream_t s, bool mixed) {
+  if (mixed) return launch_pdl(k_orientation<true>, grid, kOriWarps * 32, 0, s, d);
+  return launch_pdl(k_orientation<false>, grid, kOriWarps * 32, 0, s, d);
 }
 
 cudaError_t launch_ori_compact(const Desc *d, int grid, cudaStream_t s) {
@@ -704,6 +727,22 @@ cudaError_t launch_select(const Desc *d, int grid, cudaStream_t s) {
 }
 
 int descriptor_smem_bytes() { return kKpWarps * kDescWarpFloats * (int)sizeof(float); }
+
+int orientation_max_ctas(bool mixed) {
+  int nb = 0;
+  const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &nb, mixed ? k_orientation<true> : k_orientation<false>, kOriWarps * 32, 0);
+  return (e == cudaSuccess && nb > 0) ? nb : 1;
+}
+
+// Needs descriptor_set_attributes() first (the dynamic shared memory opt-in).
+int descriptor_max_ctas(bool mixed) {
+  int nb = 0;
+  const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &nb, mixed ? k_descriptor<true> : k_descriptor<false>, kKpWarps * 32,
+      descriptor_smem_bytes());
+  return (e == cudaSuccess && nb > 0) ? nb : 1;
+}
 
 cudaError_t descriptor_set_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_descriptor<false>,

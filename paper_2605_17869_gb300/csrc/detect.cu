@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(kThreads) k_refine(const Desc *__restrict__ d)
 
 cudaError_t extrema_set_attributes() { return cudaSuccess; }
 
-int extrema_grid(int n_sm, int n_scales) {
+int extrema_max_ctas(int n_scales) {
   int nb = 0;
   cudaError_t e = cudaErrorInvalidValue;
   switch (n_scales) {
@@ -432,7 +432,7 @@ int extrema_grid(int n_sm, int n_scales) {
     case 6: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extrema<6, false>, kExtThreads, 0); break;
     default: break;
   }
-  return n_sm * ((e == cudaSuccess && nb > 0) ? nb : 1);
+  return (e == cudaSuccess && nb > 0) ? nb : 1;
 }
 
 cudaError_t launch_extrema(const Desc *d, int oct, int n_scales, int grid, cudaStream_t s, bool pdl,

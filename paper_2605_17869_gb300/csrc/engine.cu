@@ -96,13 +96,6 @@ sift_status validate_params(const sift_params &p, std::string *why) {
     rmax = r < 0 ? -1 : std::max(rmax, r);
   }
   if (rmax < 0) return bad("sigma0 too large: blur radius above 16");
-  {
-    // The orientation window (radius 4.5 sigma at the largest keypoint scale,
-    // s + ds < S + 1/2) is staged in bands of kOriWin / (2R + 3) - 2 rows.
-    const double smax = (double)p.sigma0 * std::pow(2.0, (p.n_scales + 1.0) / p.n_scales);
-    const int rori = (int)std::floor(4.5 * smax + 0.5);
-    if (kOriWin / (2 * rori + 3) - 2 < 1) return bad("sigma0 too large for the orientation window");
-  }
   if (p.min_octave_side < 16 || p.min_octave_side <= rmax || p.min_octave_side <= 2 * p.border)
     return bad("min_octave_side must be >= 16, above the blur radius and twice the border");
   return SIFT_OK;
@@ -164,10 +157,11 @@ sift_status Engine::init() {
     const double k = std::sqrt(level_sigma(P_, i) * level_sigma(P_, i) -
                                level_sigma(P_, i - 1) * level_sigma(P_, i - 1));
     lvl_R_[i] = gaussian_taps(k, &lvl_t_[i]);
-    tun_.lvl_kind[i] = TK_BLUR32;
   }
-  tun_.grid_mult_blur = 4;
-  ext_grid_ = extrema_grid(n_sm_, S_);
+  tun_ = default_tuning();
+  ext_max_ = extrema_max_ctas(S_);
+  ori_max_ = orientation_max_ctas(P_.fp16_pyramid != 0);
+  desc_max_ = descriptor_max_ctas(P_.fp16_pyramid != 0);
   inited_ = true;
   return SIFT_OK;
 }
@@ -192,10 +186,11 @@ sift_status Engine::init_noalloc() {
     const double k = std::sqrt(level_sigma(P_, i) * level_sigma(P_, i) -
                                level_sigma(P_, i - 1) * level_sigma(P_, i - 1));
     lvl_R_[i] = gaussian_taps(k, &lvl_t_[i]);
-    tun_.lvl_kind[i] = TK_BLUR32;
   }
-  tun_.grid_mult_blur = 4;
-  ext_grid_ = extrema_grid(n_sm_, S_);
+  tun_ = default_tuning();
+  ext_max_ = extrema_max_ctas(S_);
+  ori_max_ = orientation_max_ctas(P_.fp16_pyramid != 0);
+  desc_max_ = descriptor_max_ctas(P_.fp16_pyramid != 0);
   return SIFT_OK;
 }
 
@@ -430,9 +425,8 @@ sift_status Engine::upload(Desc *hd, size_t bytes, cudaStream_t s) {
   return SIFT_OK;
 }
 
-int Engine::grid_blur(int R, int kind, int mode) const {
-  const int per_sm = blur_blocks_per_sm(R, kind, mode);
-  return std::max(1, n_sm_ * per_sm);
+int Engine::grid_blur(int R, int kind, int mode, int ctas) const {
+  return grid_of(blur_blocks_per_sm(R, kind, mode), ctas);
 }
 
 cudaError_t Engine::enqueue_pyramid(cudaStream_t s, int M, int modes, std::vector<ProfRec> *prof) {
@@ -467,9 +461,9 @@ cudaError_t Engine::enqueue_pyramid(cudaStream_t s, int M, int modes, std::vecto
     // Octaves above 0: the level-1 launch also produces level 0 by decimating
     // level S of the previous octave (no separate decimation pass).
     for (int l = 1; l <= S_ + 2; l++) {
-      const int kind = o == 0 ? tun_.lvl_kind[l] : TK_BLUR32;  // tuned on octave 0 only
+      const int kind = storage(o, l) ? TK_BLUR32 : tun_.lvl_kind[o][l];
       rec(PC_BLUR, [&] {
-        return launch_level_blur(d, o, l, lvl_R_[l], lvl_t_[l], kind, grid_blur(lvl_R_[l], kind, 0), s,
+        return launch_level_blur(d, o, l, lvl_R_[l], lvl_t_[l], kind, grid_blur(lvl_R_[l], kind, 0, tun_.blur_ctas[o]), s,
                                  o > 0 && l == 1, true, storage(o, l));
       });
     }
@@ -505,6 +499,7 @@ cudaError_t Engine::enqueue_all(cudaStream_t s, int M, int modes, std::vector<Pr
   fork = fork && side_[0] != nullptr && M > 1;
   const Desc *d = ddesc_;
   const int g4 = n_sm_ * 4;
+  const int ext_grid = grid_of(ext_max_, tun_.ext_ctas);
   for (int o = 0; o < M; o++) {
     if (o == 0) {
       // One base launch per mode present (bit m of modes: images with up = m).
@@ -523,36 +518,37 @@ cudaError_t Engine::enqueue_all(cudaStream_t s, int M, int modes, std::vector<Pr
     const bool branch = fork && o + 1 < M;
     cudaStream_t side = side_[o % kSides];
     for (int l = 1; l <= S_ + 2; l++) {
-      const int kind = o == 0 ? tun_.lvl_kind[l] : TK_BLUR32;  // tuned on octave 0 only
+      const int kind = storage(o, l) ? TK_BLUR32 : tun_.lvl_kind[o][l];
       const bool on_side = branch && l > S_;
       if (on_side && l == S_ + 1) {
         if (e == cudaSuccess) e = cudaEventRecord(fork_ev_[o], s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(side, fork_ev_[o], 0);
       }
       rec_on(on_side ? side : s, PC_BLUR, [&] {
-        return launch_level_blur(d, o, l, lvl_R_[l], lvl_t_[l], kind, grid_blur(lvl_R_[l], kind, 0),
+        return launch_level_blur(d, o, l, lvl_R_[l], lvl_t_[l], kind, grid_blur(lvl_R_[l], kind, 0, tun_.blur_ctas[o]),
                                  on_side ? side : s, o > 0 && l == 1, !(on_side && l == S_ + 1),
                                  storage(o, l));
       });
     }
     if (branch) {
-      rec_on(side, PC_EXTREMA, [&] { return launch_extrema(d, o, S_, ext_grid_, side, true, half_octave(o)); });
+      rec_on(side, PC_EXTREMA, [&] { return launch_extrema(d, o, S_, ext_grid, side, true, half_octave(o)); });
     } else if (fork) {
       for (int k = 0; k < kSides && k < M - 1; k++) {
         if (e == cudaSuccess) e = cudaEventRecord(join_ev_[k], side_[k]);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, join_ev_[k], 0);
       }
-      rec(PC_EXTREMA, [&] { return launch_extrema(d, o, S_, ext_grid_, s, false, half_octave(o)); });
+      rec(PC_EXTREMA, [&] { return launch_extrema(d, o, S_, ext_grid, s, false, half_octave(o)); });
     } else {
-      rec(PC_EXTREMA, [&] { return launch_extrema(d, o, S_, ext_grid_, s, true, half_octave(o)); });
+      rec(PC_EXTREMA, [&] { return launch_extrema(d, o, S_, ext_grid, s, true, half_octave(o)); });
     }
   }
   rec(PC_KEYPOINT, [&] { return launch_bm_compact(d, g4, s); }, 3);
   rec(PC_REFINE, [&] { return launch_refine(d, g4, s); });
-  rec(PC_ORIENT, [&] { return launch_orientation(d, n_sm_ * 8, s); });
+  const bool mixed = P_.fp16_pyramid != 0;
+  rec(PC_ORIENT, [&] { return launch_orientation(d, grid_of(ori_max_, tun_.ori_ctas), s, mixed); });
   rec(PC_KEYPOINT, [&] { return launch_ori_compact(d, g4, s); }, 3);
   rec(PC_KEYPOINT, [&] { return launch_select(d, n_sm_, s); });
-  rec(PC_DESCRIPTOR, [&] { return launch_descriptor(d, n_sm_ * 6, s, P_.fp16_pyramid != 0); });
+  rec(PC_DESCRIPTOR, [&] { return launch_descriptor(d, grid_of(desc_max_, tun_.desc_ctas), s, mixed); });
   return e;
 }
 
@@ -792,8 +788,8 @@ sift_status Engine::autotune(int H, int W, cudaStream_t s) {
   // Time the whole pyramid stage (all octaves, as the pipeline runs it), not
   // one level in isolation: a level's tile height also changes how the level
   // overlaps its neighbours and how warm L2 is for them. Coordinate descent
-  // from 32-row tiles everywhere; a level switches to 64 rows only if the
-  // stage gets at least 1% faster.
+  // from 32-row tiles everywhere in octave 0; a level switches to 64 rows only
+  // if the stage gets at least 1% faster.
   auto time_stage = [&]() -> float {
     for (int w = 0; w < 2; w++) enqueue_pyramid(s, M, modes, nullptr);
     cudaEventRecord(a, s);
@@ -805,13 +801,14 @@ sift_status Engine::autotune(int H, int W, cudaStream_t s) {
     return ms;
   };
   if (st == SIFT_OK) {
-    for (int l = 0; l < kMaxLevels; l++) tun_.lvl_kind[l] = TK_BLUR32;
+    for (int l = 0; l < kMaxLevels; l++) tun_.lvl_kind[0][l] = TK_BLUR32;
     float best = time_stage();
     for (int l = 1; l <= S_ + 2; l++) {
-      tun_.lvl_kind[l] = TK_BLUR64;
+      if (storage(0, l)) continue;
+      tun_.lvl_kind[0][l] = TK_BLUR64;
       const float t = time_stage();
       if (t < 0.99f * best) best = t;
-      else tun_.lvl_kind[l] = TK_BLUR32;
+      else tun_.lvl_kind[0][l] = TK_BLUR32;
     }
   }
   cudaEventDestroy(a);
@@ -825,6 +822,106 @@ sift_status Engine::autotune(int H, int W, cudaStream_t s) {
   }
   drop_graphs();
   return st;
+}
+
+std::string Engine::device_key() const {
+  int ma = 0, mi = 0;
+  cudaDeviceGetAttribute(&ma, cudaDevAttrComputeCapabilityMajor, dev_);
+  cudaDeviceGetAttribute(&mi, cudaDevAttrComputeCapabilityMinor, dev_);
+  return "sm" + std::to_string(ma) + std::to_string(mi) + "x" + std::to_string(n_sm_);
+}
+
+float Engine::time_steps(const Tuning &t, int n, const ImgIn *imgs, cudaStream_t s,
+                         sift_status *st) {
+  set_tuning(t);
+  float best = 1e30f;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+    cudaGetLastError();
+    err = "autotune event creation failed";
+    *st = SIFT_E_CUDA;
+  }
+  // Two untimed steps (the first one captures the graph), then the best of
+  // three runs of five back-to-back steps.
+  for (int w = 0; w < 2 && *st == SIFT_OK; w++) *st = run(n, imgs, s);
+  for (int r = 0; r < 3 && *st == SIFT_OK; r++) {
+    cudaEventRecord(a, s);
+    for (int k = 0; k < 5 && *st == SIFT_OK; k++) *st = run(n, imgs, s);
+    cudaEventRecord(b, s);
+    float ms = 0.f;
+    if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+      err = std::string("autotune timing failed: ") + cudaGetErrorString(cudaGetLastError());
+      *st = SIFT_E_CUDA;
+    }
+    best = std::min(best, ms / 5.0f);
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  return best;
+}
+
+sift_status Engine::autotune_batch(int n, const ImgIn *imgs, cudaStream_t s) {
+  sift_status st = init();
+  if (st != SIFT_OK) return st;
+  if (n < 1 || n > kMaxImg) {
+    err = "autotune batch must hold 1..128 images";
+    return SIFT_E_INVALID;
+  }
+  int M = 0;
+  for (int i = 0; i < n; i++) {
+    int hs[kMaxOct], ws[kMaxOct];
+    M = std::max(M, octave_sizes(imgs[i].H, imgs[i].W, hs, ws));
+  }
+  // Coordinate descent over whole extraction steps of the caller's batch,
+  // starting from the defaults (32-row tiles, occupancy-maximum grids): a
+  // candidate replaces the incumbent only if the step gets at least 1% faster.
+  // Searched, in order: 64-row tiles per FP32 level of the three largest
+  // octaves (smaller octaves have too few tiles to fill the GPU), fewer
+  // resident blur CTAs per SM for those octaves, then fewer extrema,
+  // orientation and descriptor CTAs per SM (down to half the maximum).
+  const Tuning t0 = default_tuning();
+  Tuning best_t = t0;
+  float best = time_steps(best_t, n, imgs, s, &st);
+  auto try_t = [&](const Tuning &c) {
+    if (st != SIFT_OK) return;
+    const float t = time_steps(c, n, imgs, s, &st);
+    if (st == SIFT_OK && t < 0.99f * best) {
+      best = t;
+      best_t = c;
+    }
+  };
+  const int OT = std::min(M, 3);
+  for (int o = 0; o < OT; o++)
+    for (int l = 1; l <= S_ + 2; l++) {
+      if (storage(o, l)) continue;
+      Tuning c = best_t;
+      c.lvl_kind[o][l] = TK_BLUR64;
+      try_t(c);
+    }
+  int blur_max = 1;
+  for (int l = 1; l <= S_ + 2; l++)
+    blur_max = std::max(blur_max, blur_blocks_per_sm(lvl_R_[l], TK_BLUR32, 0));
+  auto fewer = [&](int mx, auto &&field) {
+    for (int c = mx - 1; c >= std::max(1, mx / 2); c--) {
+      Tuning cand = best_t;
+      field(cand) = c;
+      try_t(cand);
+    }
+  };
+  for (int o = 0; o < OT; o++) fewer(blur_max, [o](Tuning &t) -> int & { return t.blur_ctas[o]; });
+  fewer(ext_max_, [](Tuning &t) -> int & { return t.ext_ctas; });
+  fewer(ori_max_, [](Tuning &t) -> int & { return t.ori_ctas; });
+  fewer(desc_max_, [](Tuning &t) -> int & { return t.desc_ctas; });
+  // Confirm against the defaults once more, so that a choice that won by
+  // timing noise early in the search does not stay.
+  if (st == SIFT_OK) {
+    const float tb = time_steps(best_t, n, imgs, s, &st);
+    const float td = st == SIFT_OK ? time_steps(t0, n, imgs, s, &st) : 0.f;
+    if (st == SIFT_OK && !(tb < td)) best_t = t0;
+  }
+  if (st != SIFT_OK) return st;
+  set_tuning(best_t);
+  return run(n, imgs, s);  // the outputs: a run with the chosen tuning
 }
 
 }  // namespace sift

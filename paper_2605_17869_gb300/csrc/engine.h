@@ -5,6 +5,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <map>
 #include <string>
 #include <vector>
@@ -25,10 +26,28 @@ struct ImgIn {
 enum ProfClass { PC_BLUR = 0, PC_BASE = 1, PC_EXTREMA = 2, PC_DECIMATE = 3, PC_KEYPOINT = 4,
                  PC_DESCRIPTOR = 5, PC_REFINE = 6, PC_ORIENT = 7, PC_COUNT = 8 };
 
+// Launch shapes the autotuner chooses. None of them changes an output bit:
+// tiles and grids only decide which CTA computes what.
 struct Tuning {
-  int lvl_kind[kMaxLevels];   // tile-height class per level (TK_BLUR32/64)
-  int grid_mult_blur;         // persistent grid = n_sm * blocks/SM * mult / 4
+  // Tile-height class (TK_BLUR32 / TK_BLUR64) of the blur that writes level l
+  // of octave o; binary16 levels always take 32-row tiles.
+  int lvl_kind[kMaxOct][kMaxLevels];
+  // Resident CTAs per SM of the persistent grids, 0 meaning the occupancy
+  // maximum (larger values are capped by it): the level blurs of octave o, the
+  // extrema scans, orientation, descriptor.
+  int blur_ctas[kMaxOct];
+  int ext_ctas, ori_ctas, desc_ctas;
 };
+
+// Host-only tuning helpers (tuning.cu).
+Tuning default_tuning();
+std::string tuning_json(const Tuning &t, int n_scales);
+bool parse_tuning(const char *json, int n_scales, const Tuning &base, Tuning *out,
+                  std::string *why);
+// Key of the tuning cache for a batch: parameters, image count, shapes.
+std::string batch_signature(const sift_params &p, int n, const int *H, const int *W);
+sift_status cache_get(const char *path, const char *sig, std::string *json);
+sift_status cache_put(const char *path, const char *sig, const char *json);
 
 struct WsLayout {
   size_t pyr, bm, cand, ref, code, npk, angs, ori, okey, fin, bm_cnt, bm_off, cc_cnt, cc_off,
@@ -78,6 +97,12 @@ class Engine {
   Tuning tuning() const { return tun_; }
   void set_tuning(const Tuning &t);
   sift_status autotune(int H, int W, cudaStream_t s);
+  // Search the launch shapes on a real batch (n <= kMaxImg) by timing whole
+  // extraction steps, and keep the fastest; the outputs end up holding the
+  // results of a run with the chosen tuning.
+  sift_status autotune_batch(int n, const ImgIn *imgs, cudaStream_t s);
+  // "sm<major><minor>x<SMs>": the device part of a tuning-cache key.
+  std::string device_key() const;
   int level_radius(int l) const { return lvl_R_[l]; }
 
   const sift_params &params() const { return P_; }
@@ -112,11 +137,18 @@ class Engine {
                           bool fork = false);
   sift_status get_graph(int max_oct, int modes, cudaGraphExec_t *out);
   void drop_graphs();
-  int grid_blur(int R, int kind, int mode) const;
+  int grid_blur(int R, int kind, int mode, int ctas = 0) const;
+  int grid_of(int max_ctas, int ctas) const {
+    return n_sm_ * std::max(1, ctas > 0 ? std::min(ctas, max_ctas) : max_ctas);
+  }
+  // Step time (ms, best of 3 x 5 steps) of a batch under tuning t.
+  float time_steps(const Tuning &t, int n, const ImgIn *imgs, cudaStream_t s, sift_status *st);
 
   sift_params P_;
   int dev_ = 0, n_sm_ = 0;
-  int ext_grid_ = 0;  // extrema scan grid (SMs x resident blocks)
+  // Occupancy maxima (resident CTAs per SM) of the extrema scan, orientation
+  // and descriptor kernels.
+  int ext_max_ = 1, ori_max_ = 1, desc_max_ = 1;
   int S_ = 3;
   int base_R_[2] = {0, 0};  // base blur: [0] input as is, [1] 2x magnified input
   BlurTaps base_t_[2] = {};

@@ -29,7 +29,6 @@ constexpr int kMaxR = 16;          // largest blur radius supported (halo 16)
 constexpr int kOriBins = 36;       // §3.2: 36-bin orientation histogram
 constexpr int kMaxPeaks = kOriBins / 2;  // strict circular maxima of 36 bins
 constexpr int kDescLen = 128;      // 4 x 4 x 8
-constexpr int kOriWin = 1600;      // staged orientation window (floats, one band)
 constexpr int kBlurTW = 128;       // blur tile width (32 lanes x float4)
 constexpr int kBlurHalo = 16;      // staged columns left/right of a blur tile
 constexpr int kBmCols = 30;        // columns per bitmap word = extrema strip width (one warp)
@@ -219,12 +218,15 @@ cudaError_t launch_extrema(const Desc *d, int oct, int n_scales, int grid, cudaS
                            bool pdl = true, bool half = false);
 cudaError_t extrema_set_attributes();
 // Persistent grid of the extrema scan: SMs x resident blocks per SM.
-int extrema_grid(int n_sm, int n_scales);
+// Occupancy maxima (resident CTAs per SM) of the persistent keypoint kernels.
+int extrema_max_ctas(int n_scales);
+int orientation_max_ctas(bool mixed);
+int descriptor_max_ctas(bool mixed);
 cudaError_t launch_bm_compact(const Desc *d, int grid, cudaStream_t s);
 cudaError_t launch_refine(const Desc *d, int grid, cudaStream_t s);
 
 // Description (describe.cu)
-cudaError_t launch_orientation(const Desc *d, int grid, cudaStream_t s);
+cudaError_t launch_orientation(const Desc *d, int grid, cudaStream_t s, bool mixed = false);
 cudaError_t launch_ori_compact(const Desc *d, int grid, cudaStream_t s);
 cudaError_t launch_select(const Desc *d, int grid, cudaStream_t s);
 // mixed: the pyramid has binary16 octaves (fp16 storage mode).

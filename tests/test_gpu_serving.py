@@ -123,3 +123,62 @@ def test_autotuned_tiles_bit_identical():
     for rows in ("[32, 32, 32, 32, 32]", "[64, 64, 64, 64, 64]", "[64, 32, 64, 32, 64]"):
         b.set_tuning('{"blur_tile_rows": %s}' % rows)
         assert _same(fa, b.extract(img))
+
+
+def _batch_feats(ex, n):
+    bufs = ex._buffers(n)
+    counts = ex._counts[:n].tolist()
+    return [pkg.Features(*(t.clone() for t in (f.x, f.y, f.sigma, f.angle, f.response, f.octave,
+                                               f.layer, f.desc)), c)
+            for f, c in ((b.view(c), c) for b, c in zip(bufs, counts))]
+
+
+def test_tuning_json_round_trip_and_validation():
+    ex = pkg.Extractor()
+    js = ('{"blur_tile_rows": [[64, 32, 64, 32, 32], [32, 64, 32, 32, 32]], '
+          '"blur_ctas_per_sm": [2, 3], "extrema_ctas_per_sm": 3, '
+          '"orientation_ctas_per_sm": 5, "descriptor_ctas_per_sm": 4}')
+    ex.set_tuning(js)
+    assert ex.get_tuning() == js
+    ex.set_tuning('{"blur_tile_rows": [32, 32, 32, 32, 64]}')  # flat list: octave 0 only
+    assert ex.get_tuning().startswith('{"blur_tile_rows": [[32, 32, 32, 32, 64], '
+                                      '[32, 64, 32, 32, 32]]')
+    for bad in ('{"blur_tile_rows": [48, 32, 32, 32, 32]}', '{"blur_tile_rows": [32, 32]}',
+                '{"extrema_ctas_per_sm": 65}', '{"extrema_ctas_per_sm": -1}', '{"grid": 1}',
+                '{"descriptor_ctas_per_sm": 2.5}', '[]', '{"blur_ctas_per_sm": [1] } x'):
+        with pytest.raises(pkg.SiftError):
+            ex.set_tuning(bad)
+    ex.close()
+
+
+def test_batch_autotune_bit_identical_and_cached(tmp_path):
+    shapes = [(480, 640), (1200, 1600), (300, 411), (720, 1280), (97, 211), (900, 700)]
+    imgs = [torch.from_numpy(synth.make_image(synth.rng_for(42, i), *s, fractal_std=0.05)).cuda()
+            for i, s in enumerate(shapes)]
+    ref = pkg.Extractor().extract_batch(imgs)  # default tuning
+    cache = str(tmp_path / "tuning.json")
+    ex = pkg.Extractor()
+    js, hit = ex.autotune_batch(imgs, cache=cache)
+    assert not hit
+    torch.cuda.synchronize()
+    tuned = _batch_feats(ex, len(imgs))  # the autotuner leaves the chosen tuning's results
+    assert all(_same(a, b) for a, b in zip(ref, tuned))
+    assert all(_same(a, b) for a, b in zip(ref, ex.extract_batch(imgs)))
+    ex.close()
+    # A second handle finds the tuning in the cache, also for the batch reversed.
+    ex2 = pkg.Extractor()
+    js2, hit2 = ex2.autotune_batch(imgs[::-1], cache=cache)
+    assert hit2 and js2 == js
+    torch.cuda.synchronize()
+    assert all(_same(a, b) for a, b in zip(ref[::-1], _batch_feats(ex2, len(imgs))))
+    ex2.close()
+    # Every corner of the search space gives the same bits.
+    ex3 = pkg.Extractor()
+    for t in ('{"blur_tile_rows": [[64, 64, 64, 64, 64], [64, 64, 64, 64, 64], '
+              '[64, 64, 64, 64, 64]], "blur_ctas_per_sm": [1, 1, 1], "extrema_ctas_per_sm": 1, '
+              '"orientation_ctas_per_sm": 1, "descriptor_ctas_per_sm": 1}',
+              '{"blur_ctas_per_sm": [2, 3, 2, 1], "extrema_ctas_per_sm": 2, '
+              '"orientation_ctas_per_sm": 4, "descriptor_ctas_per_sm": 3}'):
+        ex3.set_tuning(t)
+        assert all(_same(a, b) for a, b in zip(ref, ex3.extract_batch(imgs)))
+    ex3.close()
