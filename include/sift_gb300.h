@@ -250,7 +250,14 @@ sift_status sift_magsac(sift_handle *h, const float *xa, const float *xb, int n,
  *   capacity, bit 2 top-K cap applied).
  * Returns SIFT_W_TRUNCATED if any capacity was exceeded, else SIFT_OK;
  * SIFT_E_INVALID if the last batch had more than 128 images (it ran as several
- * launches, and the statistics cover one launch). */
+ * launches, and the statistics cover one launch); SIFT_E_TIMEOUT if a wait of
+ * the single-pass keypoint compaction gave up (a bounded wait for another
+ * block's published count; it is not expected to happen): that run's counts
+ * and keypoints are then not valid, though every write stayed within its
+ * buffers and the handle remains usable. Tests exercise that path through the
+ * environment variables SIFT_TEST_LOOKBACK_SPINS (poll limit of one wait) and
+ * SIFT_TEST_LOOKBACK_HOLD (index of a compaction block that never publishes
+ * its count), read when a handle is created. */
 sift_status sift_last_stats(sift_handle *h, int *stats, int max_images);
 
 /* Pyramid geometry for an H x W input under the handle's parameters:
@@ -307,7 +314,7 @@ sift_status sift_last_launch_count(sift_handle *h, int *kernels);
  *                                                   a flat list sets octave 0
  *    "blur_ctas_per_sm": [c_0, c_1, ...],           level blurs, per octave
  *    "extrema_ctas_per_sm": c, "orientation_ctas_per_sm": c,
- *    "descriptor_ctas_per_sm": c}
+ *    "descriptor_ctas_per_sm": c, "compaction_ctas_per_sm": c}
  * with c the resident CTAs per SM of that persistent grid, 0 (the default)
  * meaning the kernel's occupancy maximum and larger values capped by it.
  * sift_set_tuning changes only the keys given (SIFT_E_INVALID on a malformed
@@ -325,9 +332,9 @@ sift_status sift_set_tuning(sift_handle *h, const char *json);
  * from the cache. Coordinate descent over whole extraction steps of this
  * batch on `stream`, from the defaults: 64-row tiles per level of the three
  * largest octaves, then fewer resident CTAs per SM for their level blurs and
- * for the extrema, orientation and descriptor grids; a change is kept only if
- * the step gets at least 1% faster, and the result is re-timed against the
- * defaults at the end. The chosen tuning stays on the handle, and on return
+ * for the extrema, orientation, descriptor and compaction grids; a change is
+ * kept only if the step gets at least 1% faster, and the result is re-timed
+ * against the defaults at the end. The chosen tuning stays on the handle, and on return
  * the output buffers hold this batch's results (a run with that tuning;
  * identical to sift_extract_batch's). Synchronises `stream` while timing.
  * With a tuning cache set (sift_set_tuning_cache), the batch's signature

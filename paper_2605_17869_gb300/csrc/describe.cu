@@ -239,84 +239,154 @@ __global__ void __launch_bounds__(kOriWarps * 32, 4) k_orientation(const Desc *_
 
 // --------------------------------------------- oriented keypoint compaction
 
-__global__ void __launch_bounds__(kThreads) k_cc_count(const Desc *__restrict__ d) {
-  pdl_wait();
-  __shared__ int tmp[kThreads / 32 + 1];
+// The oriented keypoints of every image in canonical order (candidate slot,
+// then peak), in one pass over chunks of kChunk candidate slots, organised as
+// k_bm_compact (contiguous chunk ranges per block, counts kept per chunk and
+// warp, one scan over blocks, image starts published right after it). The
+// block with an image's last chunk writes the image's oriented, capped and
+// final counts (and the caller's count output); the last block forms the
+// prefix of the final counts over the images.
+constexpr int kCmpWarps = kThreads / 32;
+constexpr int kMaxCh = 256;
+
+__device__ __forceinline__ int cc_chunk_peaks(const Desc *__restrict__ d, const ImgDev &im, int nc,
+                                              int c, int c0, int (&np)[kChunk / kThreads],
+                                              int *s0_out) {
   constexpr int SPT = kChunk / kThreads;
-  const int n = d->n_img;
-  for (int c = blockIdx.x; c < d->n_cc_chunks; c += gridDim.x) {
-    const int b = find_owner(d->cc_pre, n, c);
-    const ImgDev &im = d->img[b];
-    const int nc = d->cnt[b].n_cand;
-    const int s0 = (c - d->cc_pre[b]) * kChunk + threadIdx.x * SPT;
-    int v = 0;
+  const int s0 = (c - c0) * kChunk + threadIdx.x * SPT;
+  int v = 0;
 #pragma unroll
-    for (int k = 0; k < SPT; k++)
-      if (s0 + k < nc) v += d->npk[im.cand_off + s0 + k];
-    const int tot = block_sum(v, tmp);
-    if (threadIdx.x == 0) d->cc_cnt[c] = tot;
+  for (int k = 0; k < SPT; k++) {
+    np[k] = (s0 + k < nc) ? d->npk[im.cand_off + s0 + k] : 0;
+    v += np[k];
   }
+  *s0_out = s0;
+  return v;
 }
 
-// One block: per image (one warp each), scan of chunk counts, oriented totals,
-// the final (capped) counts and the caller's count output; then the prefix of
-// final counts over images.
-__global__ void __launch_bounds__(512) k_cc_scan(const Desc *__restrict__ d) {
+__global__ void __launch_bounds__(kThreads) k_cc_compact(const Desc *__restrict__ d) {
   pdl_wait();
-  __shared__ int s_nf[kMaxImg];
-  const int n = d->n_img, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int b = warp; b < n; b += 16) {
-    const ImgDev &im = d->img[b];
-    const int carry = warp_excl_scan_array(d->cc_cnt + im.cc0, d->cc_off + im.cc0, im.cc_n);
-    const int no = min(carry, im.ori_cap);
-    const int nf = min(no, im.kcap);
-    if (lane == 0) {
-      ImgCounters &k = d->cnt[b];
-      k.n_ori_raw = carry;
-      k.n_ori = no;
-      k.n_fin = nf;
-      k.flags |= (carry > im.ori_cap ? TF_ORI : 0) | (no > im.kcap ? TF_TOPK : 0);
-      if (im.ocount) *im.ocount = nf;
-      s_nf[b] = nf;
+  __shared__ int tmp[kThreads / 32 + 1];
+  __shared__ int s_w[kMaxCh][kCmpWarps];
+  __shared__ int s_val;
+  constexpr int SPT = kChunk / kThreads;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int n = d->n_img, C = d->n_cc_chunks, G = gridDim.x, g = blockIdx.x;
+  const LookbackCfg cfg{d->lb_epoch, d->lb_spins, d->lb_hold, d->lb_err};
+  const int ca = (int)((long long)C * g / G), cb = (int)((long long)C * (g + 1) / G);
+  const int kept = min(cb - ca, kMaxCh);
+  int np[SPT];
+  int s0;
+  int over = 0;
+  for (int c = ca; c < cb; c++) {
+    const int b = find_owner(d->cc_pre, n, c);
+    const int v = cc_chunk_peaks(d, d->img[b], d->cnt[b].n_cand, c, d->cc_pre[b], np, &s0);
+    if (c - ca < kMaxCh) {
+      int ws = v;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) ws += __shfl_xor_sync(0xffffffffu, ws, o);
+      if (lane == 0) s_w[c - ca][warp] = ws;
+    } else {
+      over += v;
     }
   }
   __syncthreads();
-  if (warp == 0) warp_excl_scan_small(s_nf, d->fin_flat, n);
-}
-
-__global__ void __launch_bounds__(kThreads) k_cc_emit(const Desc *__restrict__ d) {
-  pdl_wait();
-  __shared__ int tmp[kThreads / 32 + 1];
-  constexpr int SPT = kChunk / kThreads;
-  const int n = d->n_img;
-  for (int c = blockIdx.x; c < d->n_cc_chunks; c += gridDim.x) {
+  int part = over;
+  for (int k = threadIdx.x; k < kept; k += kThreads)
+#pragma unroll
+    for (int w = 0; w < kCmpWarps; w++) part += s_w[k][w];
+  const int agg = block_sum(part, tmp);
+  if (threadIdx.x < 32) {
+    const int ex = lb_exclusive(d->lb_cc, 0, g, agg, cfg);
+    if (threadIdx.x == 0) s_val = ex;
+  }
+  __syncthreads();
+  const int base = s_val;
+  __syncthreads();
+  unsigned long long *starts = d->lb_start + kMaxImg;
+  {
+    int acc = base;
+    for (int c = ca; c < cb; c++) {
+      const int b = find_owner(d->cc_pre, n, c);
+      if (c == d->cc_pre[b] && threadIdx.x == 0) lb_store(starts + b, lb_word(kLbInc, cfg.epoch, acc));
+      int t = 0;
+      if (c - ca < kMaxCh) {
+#pragma unroll
+        for (int w = 0; w < kCmpWarps; w++) t += s_w[c - ca][w];
+      } else {  // uniform over the block
+        t = block_sum(cc_chunk_peaks(d, d->img[b], d->cnt[b].n_cand, c, d->cc_pre[b], np, &s0), tmp);
+      }
+      acc += t;
+    }
+  }
+  int carry = base;
+  int cur = -1, start = 0;
+  for (int c = ca; c < cb; c++) {
     const int b = find_owner(d->cc_pre, n, c);
     const ImgDev &im = d->img[b];
-    const int nc = d->cnt[b].n_cand;
-    const int s0 = (c - d->cc_pre[b]) * kChunk + threadIdx.x * SPT;
-    int np[SPT];
-    int v = 0;
+    const int c0 = d->cc_pre[b];
+    const int v = cc_chunk_peaks(d, im, d->cnt[b].n_cand, c, c0, np, &s0);
+    int pre, tot;
+    if (c - ca < kMaxCh) {
+      const int incl = warp_incl_scan(v);
+      int wb = 0;
+      tot = 0;
 #pragma unroll
-    for (int k = 0; k < SPT; k++) {
-      np[k] = (s0 + k < nc) ? d->npk[im.cand_off + s0 + k] : 0;
-      v += np[k];
+      for (int w = 0; w < kCmpWarps; w++) {
+        const int x = s_w[c - ca][w];
+        wb += w < warp ? x : 0;
+        tot += x;
+      }
+      pre = wb + incl - v;
+    } else {  // uniform over the block
+      pre = block_excl_scan(v, tmp, &tot);
     }
-    int tot;
-    int j = d->cc_off[c] + block_excl_scan(v, tmp, &tot);
-    if (tot == 0) continue;
+    if (b != cur) {  // uniform over the block
+      cur = b;
+      if (c == c0) {
+        start = carry;
+      } else {
+        if (threadIdx.x < 32) {
+          unsigned long long w = 0;
+          lb_wait(starts, b, threadIdx.x == 0, cfg, &w);
+          if (threadIdx.x == 0) s_val = lb_current(w, cfg.epoch) ? (int)(unsigned)w : carry;
+        }
+        __syncthreads();
+        start = s_val;
+        __syncthreads();
+      }
+    }
+    const int rel = carry - start;
+    int j = rel + pre;
+    if (v) {
 #pragma unroll
-    for (int k = 0; k < SPT; k++) {
-      if (!np[k]) continue;
-      const long long slot = im.cand_off + s0 + k;
-      const uint32_t key = __float_as_uint(d->ref[slot].resp);
-      for (int p = 0; p < np[k]; p++, j++) {
-        if (j < im.ori_cap) {
-          d->ori[im.ori_off + j] = make_int2(s0 + k, p);
-          d->okey[im.ori_off + j] = key;
+      for (int k = 0; k < SPT; k++) {
+        if (!np[k]) continue;
+        const long long slot = im.cand_off + s0 + k;
+        const uint32_t key = __float_as_uint(d->ref[slot].resp);
+        for (int p = 0; p < np[k]; p++, j++) {
+          if (j >= 0 && j < im.ori_cap) {
+            d->ori[im.ori_off + j] = make_int2(s0 + k, p);
+            d->okey[im.ori_off + j] = key;
+          }
         }
       }
     }
+    if (threadIdx.x == 0 && c == d->cc_pre[b + 1] - 1) {
+      const int total = max(0, rel + tot);
+      const int no = min(total, im.ori_cap);
+      const int nf = min(no, im.kcap);
+      ImgCounters &k = d->cnt[b];
+      k.n_ori_raw = total;
+      k.n_ori = no;
+      k.n_fin = nf;
+      k.flags |= (total > im.ori_cap ? TF_ORI : 0) | (no > im.kcap ? TF_TOPK : 0);
+      if (im.ocount) *im.ocount = nf;
+      lb_store(d->lb_img + kMaxImg + b, lb_word(kLbInc, cfg.epoch, nf));
+    }
+    carry += tot;
   }
+  if (g == G - 1 && threadIdx.x < 32) lb_image_prefix(d->lb_img + kMaxImg, n, cfg, d->fin_flat);
 }
 
 // --------------------------------------------------------- top-K cap
@@ -716,10 +786,7 @@ cudaError_t launch_orientation(const Desc *d, int grid, cudaStream_t s, bool mix
 }
 
 cudaError_t launch_ori_compact(const Desc *d, int grid, cudaStream_t s) {
-  cudaError_t e = launch_pdl(k_cc_count, grid, kThreads, 0, s, d);
-  if (e == cudaSuccess) e = launch_pdl(k_cc_scan, 1, 512, 0, s, d);
-  if (e == cudaSuccess) e = launch_pdl(k_cc_emit, grid, kThreads, 0, s, d);
-  return e;
+  return launch_pdl(k_cc_compact, grid, kThreads, 0, s, d);
 }
 
 cudaError_t launch_select(const Desc *d, int grid, cudaStream_t s) {
@@ -727,6 +794,10 @@ cudaError_t launch_select(const Desc *d, int grid, cudaStream_t s) {
 }
 
 int descriptor_smem_bytes() { return kKpWarps * kDescWarpFloats * (int)sizeof(float); }
+
+cudaError_t cc_compact_occupancy(int *blocks_per_sm) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_cc_compact, kThreads, 0);
+}
 
 int orientation_max_ctas(bool mixed) {
   int nb = 0;

@@ -10,6 +10,8 @@
 // bitmap's memory order is (octave, layer, row, column), so the candidate list
 // comes out in that canonical order independently of tile shapes or batch
 // composition.
+#include <algorithm>
+
 #include "scan.cuh"
 #include "sift_dev.cuh"
 
@@ -229,94 +231,182 @@ __global__ void __launch_bounds__(kExtThreads, 5) k_extrema(const Desc *__restri
 
 // ----------------------------------------------------- bitmap compaction
 
-__global__ void __launch_bounds__(kThreads) k_bm_count(const Desc *__restrict__ d) {
-  pdl_wait();
-  __shared__ int tmp[kThreads / 32 + 1];
-  const int n = d->n_img;
-  for (int c = blockIdx.x; c < d->n_bm_chunks; c += gridDim.x) {
-    const int b = find_owner(d->bmc_pre, n, c);
-    const ImgDev &im = d->img[b];
-    const long long w0 = (long long)(c - d->bmc_pre[b]) * kChunk + threadIdx.x * (kChunk / kThreads);
-    const uint32_t *bm = d->bm + im.bm_begin;
-    int cnt = 0;
+// Candidate list of every image in canonical order (octave, layer, row,
+// column), in one pass. Block g of G takes the contiguous range of bitmap
+// chunks [C g / G, C (g + 1) / G):
+//  1. it counts the set bits of its chunks (per chunk and warp, kept in
+//     shared memory);
+//  2. it takes the count of everything before its range from the
+//     single-pass scan over blocks, so it only ever waits for blocks of lower
+//     index, and at once publishes the global offset of every image that
+//     starts in its range;
+//  3. it writes its candidates chunk by chunk, each image's slots counted
+//     from that image's start (published by the block that holds the image's
+//     first chunk).
+// The block with an image's last chunk writes the image's totals, and the
+// last block forms the prefix of the candidate counts over the images.
+constexpr int kCmpWarps = kThreads / 32;
+constexpr int kMaxCh = 256;  // chunks per block whose counts are kept (more are recounted)
+
+__device__ __forceinline__ int warp_sum_i(int v) {
 #pragma unroll
-    for (int k = 0; k < kChunk / kThreads; k++)
-      if (w0 + k < im.bm_words) cnt += __popc(bm[w0 + k]);
-    const int tot = block_sum(cnt, tmp);
-    if (threadIdx.x == 0) d->bm_cnt[c] = tot;
-  }
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
 }
 
-// One block: per image (one warp each), exclusive scan of chunk counts and the
-// candidate totals; then the prefix of candidate counts over images.
-__global__ void __launch_bounds__(512) k_bm_scan(const Desc *__restrict__ d) {
+__device__ __forceinline__ int bm_chunk_words(const Desc *__restrict__ d, const ImgDev &im, int c,
+                                              int c0, uint32_t (&words)[kChunk / kThreads],
+                                              long long *w0_out) {
+  constexpr int WPT = kChunk / kThreads;
+  const long long w0 = (long long)(c - c0) * kChunk + threadIdx.x * WPT;
+  const uint32_t *bm = d->bm + im.bm_begin;
+  int cnt = 0;
+#pragma unroll
+  for (int k = 0; k < WPT; k++) {
+    words[k] = (w0 + k < im.bm_words) ? bm[w0 + k] : 0u;
+    cnt += __popc(words[k]);
+  }
+  *w0_out = w0;
+  return cnt;
+}
+
+__global__ void __launch_bounds__(kThreads) k_bm_compact(const Desc *__restrict__ d) {
   pdl_wait();
-  __shared__ int s_nc[kMaxImg];
-  const int n = d->n_img, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int b = warp; b < n; b += 16) {
-    const ImgDev &im = d->img[b];
-    const int carry = warp_excl_scan_array(d->bm_cnt + im.bmc0, d->bm_off + im.bmc0, im.bmc_n);
-    const int nc = min(carry, im.cand_cap);
-    if (lane == 0) {
-      ImgCounters &k = d->cnt[b];
-      k.n_cand_raw = carry;
-      k.n_cand = nc;
-      k.flags = carry > im.cand_cap ? TF_CAND : 0;
-      s_nc[b] = nc;
+  __shared__ int tmp[kThreads / 32 + 1];
+  __shared__ int s_w[kMaxCh][kCmpWarps];  // set bits per kept chunk and warp
+  __shared__ int s_val;
+  constexpr int WPT = kChunk / kThreads;  // words per thread
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int n = d->n_img, C = d->n_bm_chunks, G = gridDim.x, g = blockIdx.x;
+  const LookbackCfg cfg{d->lb_epoch, d->lb_spins, d->lb_hold, d->lb_err};
+  const int ca = (int)((long long)C * g / G), cb = (int)((long long)C * (g + 1) / G);
+  const int kept = min(cb - ca, kMaxCh);
+  uint32_t words[WPT];
+  long long w0;
+  // 1. Counts.
+  int over = 0;
+  for (int c = ca; c < cb; c++) {
+    const int b = find_owner(d->bmc_pre, n, c);
+    const int cnt = bm_chunk_words(d, d->img[b], c, d->bmc_pre[b], words, &w0);
+    if (c - ca < kMaxCh) {
+      const int ws = warp_sum_i(cnt);
+      if (lane == 0) s_w[c - ca][warp] = ws;
+    } else {
+      over += cnt;
     }
   }
   __syncthreads();
-  if (warp == 0) warp_excl_scan_small(s_nc, d->cand_flat, n);
-}
-
-__global__ void __launch_bounds__(kThreads) k_bm_emit(const Desc *__restrict__ d) {
-  pdl_wait();
-  __shared__ int tmp[kThreads / 32 + 1];
-  constexpr int WPT = kChunk / kThreads;  // words per thread
-  const int n = d->n_img;
-  for (int c = blockIdx.x; c < d->n_bm_chunks; c += gridDim.x) {
-    const int b = find_owner(d->bmc_pre, n, c);
-    const ImgDev &im = d->img[b];
-    const long long w0 = (long long)(c - d->bmc_pre[b]) * kChunk + threadIdx.x * WPT;
-    const uint32_t *bm = d->bm + im.bm_begin;
-    uint32_t words[WPT];
-    int cnt = 0;
+  int part = over;
+  for (int k = threadIdx.x; k < kept; k += kThreads)
 #pragma unroll
-    for (int k = 0; k < WPT; k++) {
-      words[k] = (w0 + k < im.bm_words) ? bm[w0 + k] : 0u;
-      cnt += __popc(words[k]);
-    }
-    int tot;
-    int slot = d->bm_off[c] + block_excl_scan(cnt, tmp, &tot);
-    if (tot == 0) continue;
-    // Octave of the thread's words: found once and advanced (the words are
-    // contiguous). Offsets within an octave's bitmap fit 32 bits.
-    int o = 0;
-    OctDev od = d->oct[im.oct0];
-    for (int k = 0; k < WPT; k++) {
-      uint32_t wv = words[k];
-      if (!wv) continue;
-      // Locate octave / layer / row / word of this bitmap word.
-      const long long wa = im.bm_begin + w0 + k;
-      while (o + 1 < im.n_oct && wa >= d->oct[im.oct0 + o + 1].bm) {
-        o++;
-        od = d->oct[im.oct0 + o];
+    for (int w = 0; w < kCmpWarps; w++) part += s_w[k][w];
+  const int agg = block_sum(part, tmp);
+  // 2. Offset of the range; starts of the images beginning in it.
+  if (threadIdx.x < 32) {
+    const int ex = lb_exclusive(d->lb_bm, 0, g, agg, cfg);
+    if (threadIdx.x == 0) s_val = ex;
+  }
+  __syncthreads();
+  const int base = s_val;
+  __syncthreads();
+  {
+    int acc = base;
+    for (int c = ca; c < cb; c++) {
+      const int b = find_owner(d->bmc_pre, n, c);
+      if (c == d->bmc_pre[b] && threadIdx.x == 0)
+        lb_store(d->lb_start + b, lb_word(kLbInc, cfg.epoch, acc));
+      int t = 0;
+      if (c - ca < kMaxCh) {
+#pragma unroll
+        for (int w = 0; w < kCmpWarps; w++) t += s_w[c - ca][w];
+      } else {  // uniform over the block
+        t = block_sum(bm_chunk_words(d, d->img[b], c, d->bmc_pre[b], words, &w0), tmp);
       }
-      const unsigned rel = (unsigned)(wa - od.bm);
-      const unsigned lw = (unsigned)od.H * (unsigned)od.wpr;
-      const unsigned li = rel / lw;
-      const unsigned r2 = rel - li * lw;
-      const int layer = (int)li + 1;
-      const int y = (int)(r2 / (unsigned)od.wpr);
-      const int wx = (int)(r2 - (unsigned)y * (unsigned)od.wpr);
-      while (wv) {
-        const int bit = __ffs(wv) - 1;
-        wv &= wv - 1;
-        if (slot < im.cand_cap) d->cand[im.cand_off + slot] = make_int4(o, layer, y, wx * kBmCols + bit);
-        slot++;
-      }
+      acc += t;
     }
   }
+  // 3. Candidates.
+  int carry = base;         // global offset of chunk c
+  int cur = -1, start = 0;  // image of the previous chunk, global offset of its first slot
+  for (int c = ca; c < cb; c++) {
+    const int b = find_owner(d->bmc_pre, n, c);
+    const ImgDev &im = d->img[b];
+    const int c0 = d->bmc_pre[b];
+    const int cnt = bm_chunk_words(d, im, c, c0, words, &w0);
+    int pre, tot;
+    if (c - ca < kMaxCh) {
+      const int incl = warp_incl_scan(cnt);
+      int wb = 0;
+      tot = 0;
+#pragma unroll
+      for (int w = 0; w < kCmpWarps; w++) {
+        const int x = s_w[c - ca][w];
+        wb += w < warp ? x : 0;
+        tot += x;
+      }
+      pre = wb + incl - cnt;
+    } else {  // uniform over the block
+      pre = block_excl_scan(cnt, tmp, &tot);
+    }
+    if (b != cur) {  // uniform over the block
+      cur = b;
+      if (c == c0) {
+        start = carry;
+      } else {  // the image began in a lower block's range (only the range's first image)
+        if (threadIdx.x < 32) {
+          unsigned long long w = 0;
+          lb_wait(d->lb_start, b, threadIdx.x == 0, cfg, &w);
+          if (threadIdx.x == 0) s_val = lb_current(w, cfg.epoch) ? (int)(unsigned)w : carry;
+        }
+        __syncthreads();
+        start = s_val;
+        __syncthreads();
+      }
+    }
+    const int rel = carry - start;  // image-relative offset of chunk c
+    int slot = rel + pre;
+    if (cnt) {
+      // Octave of the thread's words: found once and advanced (the words are
+      // contiguous). Offsets within an octave's bitmap fit 32 bits.
+      int o = 0;
+      OctDev od = d->oct[im.oct0];
+      for (int k = 0; k < WPT; k++) {
+        uint32_t wv = words[k];
+        if (!wv) continue;
+        // Locate octave / layer / row / word of this bitmap word.
+        const long long wa = im.bm_begin + w0 + k;
+        while (o + 1 < im.n_oct && wa >= d->oct[im.oct0 + o + 1].bm) {
+          o++;
+          od = d->oct[im.oct0 + o];
+        }
+        const unsigned rel_w = (unsigned)(wa - od.bm);
+        const unsigned lw = (unsigned)od.H * (unsigned)od.wpr;
+        const unsigned li = rel_w / lw;
+        const unsigned r2 = rel_w - li * lw;
+        const int layer = (int)li + 1;
+        const int y = (int)(r2 / (unsigned)od.wpr);
+        const int wx = (int)(r2 - (unsigned)y * (unsigned)od.wpr);
+        while (wv) {
+          const int bit = __ffs(wv) - 1;
+          wv &= wv - 1;
+          if (slot >= 0 && slot < im.cand_cap)
+            d->cand[im.cand_off + slot] = make_int4(o, layer, y, wx * kBmCols + bit);
+          slot++;
+        }
+      }
+    }
+    if (threadIdx.x == 0 && c == d->bmc_pre[b + 1] - 1) {
+      const int total = max(0, rel + tot);
+      const int nc = min(total, im.cand_cap);
+      ImgCounters &k = d->cnt[b];
+      k.n_cand_raw = total;
+      k.n_cand = nc;
+      k.flags = total > im.cand_cap ? TF_CAND : 0;
+      lb_store(d->lb_img + b, lb_word(kLbInc, cfg.epoch, nc));
+    }
+    carry += tot;
+  }
+  if (g == G - 1 && threadIdx.x < 32) lb_image_prefix(d->lb_img, n, cfg, d->cand_flat);
 }
 
 // ------------------------------------------------------------ refinement
@@ -421,6 +511,13 @@ __global__ void __launch_bounds__(kThreads) k_refine(const Desc *__restrict__ d)
 
 cudaError_t extrema_set_attributes() { return cudaSuccess; }
 
+int compact_max_ctas() {
+  int a = 0, b = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_bm_compact, kThreads, 0);
+  if (e == cudaSuccess) e = cc_compact_occupancy(&b);
+  return (e == cudaSuccess && a > 0 && b > 0) ? std::min(a, b) : 1;
+}
+
 int extrema_max_ctas(int n_scales) {
   int nb = 0;
   cudaError_t e = cudaErrorInvalidValue;
@@ -456,10 +553,7 @@ cudaError_t launch_extrema(const Desc *d, int oct, int n_scales, int grid, cudaS
 }
 
 cudaError_t launch_bm_compact(const Desc *d, int grid, cudaStream_t s) {
-  cudaError_t e = launch_pdl(k_bm_count, grid, kThreads, 0, s, d);
-  if (e == cudaSuccess) e = launch_pdl(k_bm_scan, 1, 512, 0, s, d);
-  if (e == cudaSuccess) e = launch_pdl(k_bm_emit, grid, kThreads, 0, s, d);
-  return e;
+  return launch_pdl(k_bm_compact, grid, kThreads, 0, s, d);
 }
 
 cudaError_t launch_refine(const Desc *d, int grid, cudaStream_t s) {

@@ -12,9 +12,11 @@
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "engine.h"
+#include "scan.cuh"
 
 namespace sift {
 
@@ -103,9 +105,21 @@ sift_status validate_params(const sift_params &p, std::string *why) {
 
 Engine::Engine(const sift_params &p) : P_(p) {}
 
+void lookback_config(int *spins, int *hold) {
+  // A wait polls about every 0.2-1 us, so 2^19 polls give up after a fraction
+  // of a second. Tests of the give-up path (no GPU fault, no hang) shorten
+  // the limit and name a compaction block that never publishes its count
+  // through these variables.
+  *spins = 1 << 19;
+  *hold = -1;
+  if (const char *v = std::getenv("SIFT_TEST_LOOKBACK_SPINS")) *spins = std::max(1, std::atoi(v));
+  if (const char *v = std::getenv("SIFT_TEST_LOOKBACK_HOLD")) *hold = std::atoi(v);
+}
+
 Engine::~Engine() {
   drop_graphs();
   if (ws_) cudaFree(ws_);
+  if (lb_) cudaFree(lb_);
   if (ddesc_) cudaFree(ddesc_);
   for (int i = 0; i < kRing; i++) {
     if (hdesc_[i]) cudaFreeHost(hdesc_[i]);
@@ -159,9 +173,11 @@ sift_status Engine::init() {
     lvl_R_[i] = gaussian_taps(k, &lvl_t_[i]);
   }
   tun_ = default_tuning();
+  lookback_config(&lb_spins_, &lb_hold_);
   ext_max_ = extrema_max_ctas(S_);
   ori_max_ = orientation_max_ctas(P_.fp16_pyramid != 0);
   desc_max_ = descriptor_max_ctas(P_.fp16_pyramid != 0);
+  cmp_max_ = compact_max_ctas();
   inited_ = true;
   return SIFT_OK;
 }
@@ -188,9 +204,11 @@ sift_status Engine::init_noalloc() {
     lvl_R_[i] = gaussian_taps(k, &lvl_t_[i]);
   }
   tun_ = default_tuning();
+  lookback_config(&lb_spins_, &lb_hold_);
   ext_max_ = extrema_max_ctas(S_);
   ori_max_ = orientation_max_ctas(P_.fp16_pyramid != 0);
   desc_max_ = descriptor_max_ctas(P_.fp16_pyramid != 0);
+  cmp_max_ = compact_max_ctas();
   return SIFT_OK;
 }
 
@@ -381,10 +399,6 @@ sift_status Engine::fill_plan(int n, const ImgIn *in, Desc &hd, WsLayout &L, int
   L.ori = put(ori * sizeof(int2));
   L.okey = put(ori * sizeof(uint32_t));
   L.fin = put(fin * sizeof(int));
-  L.bm_cnt = put(bmc * sizeof(int));
-  L.bm_off = put(bmc * sizeof(int));
-  L.cc_cnt = put(cc * sizeof(int));
-  L.cc_off = put(cc * sizeof(int));
   L.cnt = put(kMaxImg * sizeof(ImgCounters));
   L.cand_flat = put((kMaxImg + 1) * sizeof(int));
   L.fin_flat = put((kMaxImg + 1) * sizeof(int));
@@ -412,6 +426,27 @@ sift_status Engine::ensure_workspace(size_t bytes, cudaStream_t s) {
     return SIFT_E_OOM;
   }
   ws_cap_ = want;
+  return SIFT_OK;
+}
+
+sift_status Engine::ensure_lb(size_t words, cudaStream_t s) {
+  if (words <= lb_cap_) return SIFT_OK;
+  if (lb_) {
+    cudaFreeAsync(lb_, s);
+    lb_ = nullptr;
+    lb_cap_ = 0;
+  }
+  const size_t want = align_up(words + words / 4, 4096);
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&lb_), want * sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(lb_, 0, want * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (lb_) cudaFreeAsync(lb_, s);
+    lb_ = nullptr;
+    err = "status array allocation failed";
+    return SIFT_E_OOM;
+  }
+  lb_cap_ = want;
   return SIFT_OK;
 }
 
@@ -446,7 +481,6 @@ cudaError_t Engine::enqueue_pyramid(cudaStream_t s, int M, int modes, std::vecto
     }
   };
   const Desc *d = ddesc_;
-  const int g4 = n_sm_ * 4;
   for (int o = 0; o < M; o++) {
     if (o == 0) {
       // One base launch per mode present (bit m of modes: images with up = m).
@@ -542,11 +576,12 @@ cudaError_t Engine::enqueue_all(cudaStream_t s, int M, int modes, std::vector<Pr
       rec(PC_EXTREMA, [&] { return launch_extrema(d, o, S_, ext_grid, s, true, half_octave(o)); });
     }
   }
-  rec(PC_KEYPOINT, [&] { return launch_bm_compact(d, g4, s); }, 3);
+  const int g2 = compact_grid();
+  rec(PC_KEYPOINT, [&] { return launch_bm_compact(d, g2, s); });
   rec(PC_REFINE, [&] { return launch_refine(d, g4, s); });
   const bool mixed = P_.fp16_pyramid != 0;
   rec(PC_ORIENT, [&] { return launch_orientation(d, grid_of(ori_max_, tun_.ori_ctas), s, mixed); });
-  rec(PC_KEYPOINT, [&] { return launch_ori_compact(d, g4, s); }, 3);
+  rec(PC_KEYPOINT, [&] { return launch_ori_compact(d, g2, s); });
   rec(PC_KEYPOINT, [&] { return launch_select(d, n_sm_, s); });
   rec(PC_DESCRIPTOR, [&] { return launch_descriptor(d, grid_of(desc_max_, tun_.desc_ctas), s, mixed); });
   return e;
@@ -637,13 +672,28 @@ sift_status Engine::run(int n, const ImgIn *imgs, cudaStream_t s) {
   hd->ori = reinterpret_cast<int2 *>(ws_ + lay.ori);
   hd->okey = reinterpret_cast<uint32_t *>(ws_ + lay.okey);
   hd->fin = reinterpret_cast<int *>(ws_ + lay.fin);
-  hd->bm_cnt = reinterpret_cast<int *>(ws_ + lay.bm_cnt);
-  hd->bm_off = reinterpret_cast<int *>(ws_ + lay.bm_off);
-  hd->cc_cnt = reinterpret_cast<int *>(ws_ + lay.cc_cnt);
-  hd->cc_off = reinterpret_cast<int *>(ws_ + lay.cc_off);
   hd->cnt = reinterpret_cast<ImgCounters *>(ws_ + lay.cnt);
   hd->cand_flat = reinterpret_cast<int *>(ws_ + lay.cand_flat);
   hd->fin_flat = reinterpret_cast<int *>(ws_ + lay.fin_flat);
+  const int gc = compact_grid();
+  st = ensure_lb(1 + 4 * kMaxImg + 2 * (size_t)n_sm_ * cmp_max_, s);
+  if (st != SIFT_OK) return st;
+  if (epoch_ >= kLbEpochMask) {  // epochs wrapped: clear every status of earlier runs
+    if (cudaMemsetAsync(lb_, 0, lb_cap_ * sizeof(unsigned long long), s) != cudaSuccess) {
+      err = "status clear failed";
+      return SIFT_E_CUDA;
+    }
+    epoch_ = 0;
+  }
+  epoch_++;
+  hd->lb_err = lb_;
+  hd->lb_img = lb_ + 1;
+  hd->lb_start = hd->lb_img + 2 * kMaxImg;
+  hd->lb_bm = hd->lb_start + 2 * kMaxImg;
+  hd->lb_cc = hd->lb_bm + gc;
+  hd->lb_epoch = epoch_;
+  hd->lb_spins = lb_spins_;
+  hd->lb_hold = lb_hold_;
   const size_t bytes =
       offsetof(Desc, oct) + (size_t)(hd->img[n - 1].oct0 + hd->img[n - 1].n_oct) * sizeof(OctDev);
   cudaGraphExec_t exec = nullptr;
@@ -736,6 +786,8 @@ sift_status Engine::last_stats(int *stats, int max_images) {
   std::vector<ImgCounters> c(last_n);
   if (e == cudaSuccess)
     e = cudaMemcpy(c.data(), ws_ + lay_.cnt, last_n * sizeof(ImgCounters), cudaMemcpyDeviceToHost);
+  unsigned long long gave_up = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&gave_up, lb_, sizeof gave_up, cudaMemcpyDeviceToHost);
   const Desc &hd = *hdesc_[ring_last_];
   bool trunc = false;
   for (int b = 0; b < last_n && b < max_images && e == cudaSuccess; b++) {
@@ -754,6 +806,10 @@ sift_status Engine::last_stats(int *stats, int max_images) {
   if (e != cudaSuccess) {
     err = std::string("stats read failed: ") + cudaGetErrorString(e);
     return SIFT_E_CUDA;
+  }
+  if (gave_up == epoch_) {
+    err = "a compaction wait gave up: the counts of the last run are not valid";
+    return SIFT_E_TIMEOUT;
   }
   return trunc ? SIFT_W_TRUNCATED : SIFT_OK;
 }
@@ -912,6 +968,7 @@ sift_status Engine::autotune_batch(int n, const ImgIn *imgs, cudaStream_t s) {
   fewer(ext_max_, [](Tuning &t) -> int & { return t.ext_ctas; });
   fewer(ori_max_, [](Tuning &t) -> int & { return t.ori_ctas; });
   fewer(desc_max_, [](Tuning &t) -> int & { return t.desc_ctas; });
+  fewer(cmp_max_, [](Tuning &t) -> int & { return t.cmp_ctas; });
   // Confirm against the defaults once more, so that a choice that won by
   // timing noise early in the search does not stay.
   if (st == SIFT_OK) {

@@ -37,7 +37,12 @@ struct Tuning {
   // extrema scans, orientation, descriptor.
   int blur_ctas[kMaxOct];
   int ext_ctas, ori_ctas, desc_ctas;
+  int cmp_ctas;  // the two single-pass keypoint compactions
 };
+
+// Poll limit of a single-pass scan wait and the test hook's held block
+// (environment SIFT_TEST_LOOKBACK_SPINS / SIFT_TEST_LOOKBACK_HOLD).
+void lookback_config(int *spins, int *hold);
 
 // Host-only tuning helpers (tuning.cu).
 Tuning default_tuning();
@@ -50,7 +55,7 @@ sift_status cache_get(const char *path, const char *sig, std::string *json);
 sift_status cache_put(const char *path, const char *sig, const char *json);
 
 struct WsLayout {
-  size_t pyr, bm, cand, ref, code, npk, angs, ori, okey, fin, bm_cnt, bm_off, cc_cnt, cc_off,
+  size_t pyr, bm, cand, ref, code, npk, angs, ori, okey, fin,
       cnt, cand_flat, fin_flat, total;
 };
 
@@ -138,6 +143,12 @@ class Engine {
   sift_status get_graph(int max_oct, int modes, cudaGraphExec_t *out);
   void drop_graphs();
   int grid_blur(int R, int kind, int mode, int ctas = 0) const;
+ public:
+  // Grid of the single-pass compactions (their scan runs over blocks).
+  int compact_grid() const { return grid_of(cmp_max_, tun_.cmp_ctas); }
+ private:
+  // Single-pass scan statuses: make room for `words`, cleared on allocation.
+  sift_status ensure_lb(size_t words, cudaStream_t s);
   int grid_of(int max_ctas, int ctas) const {
     return n_sm_ * std::max(1, ctas > 0 ? std::min(ctas, max_ctas) : max_ctas);
   }
@@ -148,7 +159,7 @@ class Engine {
   int dev_ = 0, n_sm_ = 0;
   // Occupancy maxima (resident CTAs per SM) of the extrema scan, orientation
   // and descriptor kernels.
-  int ext_max_ = 1, ori_max_ = 1, desc_max_ = 1;
+  int ext_max_ = 1, ori_max_ = 1, desc_max_ = 1, cmp_max_ = 1;
   int S_ = 3;
   int base_R_[2] = {0, 0};  // base blur: [0] input as is, [1] 2x magnified input
   BlurTaps base_t_[2] = {};
@@ -158,6 +169,13 @@ class Engine {
 
   char *ws_ = nullptr;
   size_t ws_cap_ = 0;
+  // Scan statuses (scan.cuh), kept apart from the workspace so that no other
+  // data ever lands in them: [0] the gave-up word, then 2 x kMaxImg image
+  // totals, then the chunks of the run. Epochs tell runs apart.
+  unsigned long long *lb_ = nullptr;
+  size_t lb_cap_ = 0;
+  unsigned epoch_ = 0;
+  int lb_spins_ = 0, lb_hold_ = -1;
   WsLayout lay_{};
   Desc *ddesc_ = nullptr;
   static constexpr int kRing = 3;

@@ -15,6 +15,7 @@
 #include <mutex>
 
 #include "engine.h"
+#include "scan.cuh"
 
 namespace sift {
 
@@ -31,6 +32,14 @@ constexpr size_t kDescBytes = (sizeof(Desc) + 255) / 256 * 256;
 // later reads. Calls whose work overlaps on the GPU (different streams, no
 // ordering between them) race on it.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+// Single-pass scan statuses (scan.cuh) of every call on a device, apart from
+// the scratch so that no other data ever lands in them: [0] the gave-up word,
+// 2 x kMaxImg image totals, 2 x kMaxImg image starts, then one word per block
+// of each compaction (up to 16384 blocks each). Zero at load time; calls are
+// told apart by epochs.
+constexpr size_t kLbWords = 1 + 4 * kMaxImg + 2 * 16384;
+static __device__ unsigned long long g_lb[kLbWords];
 
 // The part of a one-image Desc that is not a per-image table.
 struct SetupArgs {
@@ -71,6 +80,8 @@ __global__ void k_noalloc_setup(Desc *d, SetupArgs a) {
 struct DeviceScratch {
   std::mutex mu;
   void *ptr = nullptr;  // device address of g_scratch on this device, once set up
+  unsigned long long *lb = nullptr;  // device address of g_lb
+  unsigned epoch = 0;   // the last call's scan epoch (guarded by g_plan_mu)
 };
 DeviceScratch g_dev[kMaxDevices];
 
@@ -80,8 +91,10 @@ DeviceScratch g_dev[kMaxDevices];
 cudaError_t setup_device(DeviceScratch &ds) {
   std::lock_guard<std::mutex> lk(ds.mu);
   if (ds.ptr) return cudaSuccess;
-  void *ptr = nullptr;
+  void *ptr = nullptr, *lb = nullptr;
   cudaError_t e = cudaGetSymbolAddress(&ptr, g_scratch);
+  if (e == cudaSuccess) e = cudaGetSymbolAddress(&lb, g_lb);
+  if (e == cudaSuccess) ds.lb = static_cast<unsigned long long *>(lb);
   if (e == cudaSuccess) e = blur_set_attributes();
   if (e == cudaSuccess) e = descriptor_set_attributes();
   if (e == cudaSuccess) e = extrema_set_attributes();
@@ -142,13 +155,23 @@ extern "C" sift_status sift_extract_noalloc(const sift_params *p, const float *i
   hd.ori = reinterpret_cast<int2 *>(ws + lay.ori);
   hd.okey = reinterpret_cast<uint32_t *>(ws + lay.okey);
   hd.fin = reinterpret_cast<int *>(ws + lay.fin);
-  hd.bm_cnt = reinterpret_cast<int *>(ws + lay.bm_cnt);
-  hd.bm_off = reinterpret_cast<int *>(ws + lay.bm_off);
-  hd.cc_cnt = reinterpret_cast<int *>(ws + lay.cc_cnt);
-  hd.cc_off = reinterpret_cast<int *>(ws + lay.cc_off);
   hd.cnt = reinterpret_cast<ImgCounters *>(ws + lay.cnt);
   hd.cand_flat = reinterpret_cast<int *>(ws + lay.cand_flat);
   hd.fin_flat = reinterpret_cast<int *>(ws + lay.fin_flat);
+
+  const int gc = eng.compact_grid();
+  if (1 + 4 * kMaxImg + 2 * (size_t)gc > kLbWords) return SIFT_E_BUDGET;
+  if (ds.epoch >= kLbEpochMask) {  // epochs wrapped: clear every earlier status
+    if (cudaMemsetAsync(ds.lb, 0, sizeof(g_lb), s) != cudaSuccess) return SIFT_E_CUDA;
+    ds.epoch = 0;
+  }
+  hd.lb_err = ds.lb;
+  hd.lb_img = ds.lb + 1;
+  hd.lb_start = hd.lb_img + 2 * kMaxImg;
+  hd.lb_bm = hd.lb_start + 2 * kMaxImg;
+  hd.lb_cc = hd.lb_bm + gc;
+  hd.lb_epoch = ++ds.epoch;
+  lookback_config(&hd.lb_spins, &hd.lb_hold);
 
   SetupArgs a;
   std::memcpy(a.head, &hd, sizeof(a.head));

@@ -101,8 +101,15 @@ struct Desc {
   int2 *ori;                   // (candidate slot, peak index)
   uint32_t *okey;              // response bits of oriented keypoints
   int *fin;                    // final indices into the oriented list
-  int *bm_cnt, *bm_off;        // per bitmap chunk: count, image-relative offset
-  int *cc_cnt, *cc_off;        // per candidate chunk
+  // Single-pass scan statuses (scan.cuh): per block of the candidate and of
+  // the oriented compaction, per image (totals: candidates, then final; 2 x
+  // kMaxImg), per image (global offset of its first slot: candidates, then
+  // oriented; 2 x kMaxImg), and the word that records a wait that gave up.
+  unsigned long long *lb_bm, *lb_cc, *lb_img, *lb_start, *lb_err;
+  unsigned lb_epoch;           // this run's epoch, 1 .. 2^30 - 1
+  int lb_spins;                // poll limit of one wait
+  int lb_hold;                 // test hook: a chunk that never publishes (-1: none)
+  int lb_pad;
   ImgCounters *cnt;            // per image
   int *cand_flat;              // [kMaxImg + 1] prefix of n_cand over images
   int *fin_flat;               // [kMaxImg + 1] prefix of n_fin over images
@@ -222,6 +229,8 @@ cudaError_t extrema_set_attributes();
 int extrema_max_ctas(int n_scales);
 int orientation_max_ctas(bool mixed);
 int descriptor_max_ctas(bool mixed);
+int compact_max_ctas();
+cudaError_t cc_compact_occupancy(int *blocks_per_sm);
 cudaError_t launch_bm_compact(const Desc *d, int grid, cudaStream_t s);
 cudaError_t launch_refine(const Desc *d, int grid, cudaStream_t s);
 

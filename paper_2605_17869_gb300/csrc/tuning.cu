@@ -7,7 +7,7 @@
 //                                                    flat list: octave 0)
 //    "blur_ctas_per_sm": [c_0, c_1, ...],            per octave
 //    "extrema_ctas_per_sm": c, "orientation_ctas_per_sm": c,
-//    "descriptor_ctas_per_sm": c}
+//    "descriptor_ctas_per_sm": c, "compaction_ctas_per_sm": c}
 // r is 32 or 64; c is 0 (the occupancy maximum) or 1..64 (capped by the
 // occupancy maximum at launch).
 //
@@ -128,7 +128,7 @@ Tuning default_tuning() {
     for (int l = 0; l < kMaxLevels; l++) t.lvl_kind[o][l] = TK_BLUR32;
     t.blur_ctas[o] = 0;
   }
-  t.ext_ctas = t.ori_ctas = t.desc_ctas = 0;
+  t.ext_ctas = t.ori_ctas = t.desc_ctas = t.cmp_ctas = 0;
   return t;
 }
 
@@ -157,7 +157,8 @@ std::string tuning_json(const Tuning &t, int S) {
   }
   s += "], \"extrema_ctas_per_sm\": " + std::to_string(t.ext_ctas) +
        ", \"orientation_ctas_per_sm\": " + std::to_string(t.ori_ctas) +
-       ", \"descriptor_ctas_per_sm\": " + std::to_string(t.desc_ctas) + "}";
+       ", \"descriptor_ctas_per_sm\": " + std::to_string(t.desc_ctas) +
+       ", \"compaction_ctas_per_sm\": " + std::to_string(t.cmp_ctas) + "}";
   return s;
 }
 
@@ -213,10 +214,13 @@ bool parse_tuning(const char *json, int S, const Tuning &base, Tuning *out, std:
           t.blur_ctas[o] = (int)v[o];
         }
       } else if (key == "extrema_ctas_per_sm" || key == "orientation_ctas_per_sm" ||
-                 key == "descriptor_ctas_per_sm") {
+                 key == "descriptor_ctas_per_sm" || key == "compaction_ctas_per_sm") {
         long v;
         if (!c.integer(&v) || !ctas_ok(v)) return bad("tuning: " + key + " must be 0..64");
-        (key[0] == 'e' ? t.ext_ctas : key[0] == 'o' ? t.ori_ctas : t.desc_ctas) = (int)v;
+        (key[0] == 'e'   ? t.ext_ctas
+         : key[0] == 'o' ? t.ori_ctas
+         : key[0] == 'd' ? t.desc_ctas
+                         : t.cmp_ctas) = (int)v;
       } else {
         return bad("tuning: unknown key \"" + key + "\"");
       }

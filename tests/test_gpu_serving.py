@@ -137,7 +137,8 @@ def test_tuning_json_round_trip_and_validation():
     ex = pkg.Extractor()
     js = ('{"blur_tile_rows": [[64, 32, 64, 32, 32], [32, 64, 32, 32, 32]], '
           '"blur_ctas_per_sm": [2, 3], "extrema_ctas_per_sm": 3, '
-          '"orientation_ctas_per_sm": 5, "descriptor_ctas_per_sm": 4}')
+          '"orientation_ctas_per_sm": 5, "descriptor_ctas_per_sm": 4, '
+          '"compaction_ctas_per_sm": 2}')
     ex.set_tuning(js)
     assert ex.get_tuning() == js
     ex.set_tuning('{"blur_tile_rows": [32, 32, 32, 32, 64]}')  # flat list: octave 0 only
@@ -176,9 +177,11 @@ def test_batch_autotune_bit_identical_and_cached(tmp_path):
     ex3 = pkg.Extractor()
     for t in ('{"blur_tile_rows": [[64, 64, 64, 64, 64], [64, 64, 64, 64, 64], '
               '[64, 64, 64, 64, 64]], "blur_ctas_per_sm": [1, 1, 1], "extrema_ctas_per_sm": 1, '
-              '"orientation_ctas_per_sm": 1, "descriptor_ctas_per_sm": 1}',
+              '"orientation_ctas_per_sm": 1, "descriptor_ctas_per_sm": 1, '
+              '"compaction_ctas_per_sm": 1}',
               '{"blur_ctas_per_sm": [2, 3, 2, 1], "extrema_ctas_per_sm": 2, '
-              '"orientation_ctas_per_sm": 4, "descriptor_ctas_per_sm": 3}'):
+              '"orientation_ctas_per_sm": 4, "descriptor_ctas_per_sm": 3, '
+              '"compaction_ctas_per_sm": 3}'):
         ex3.set_tuning(t)
         assert all(_same(a, b) for a, b in zip(ref, ex3.extract_batch(imgs)))
     ex3.close()
