@@ -584,8 +584,7 @@ def homography_side(torch, pkg, flush, stream, tuning, steps):
     mpix = sum(im.size for im in seq.images) / 1e6
     out = {"workload": HOMOGRAPHY_WORKLOAD}
     for label, kw in (("plain", {}), ("dsp_rootsift", {"dsp": 1, "rootsift": 1})):
-        ex = pkg.Extractor(upsample=1, max_kpts=8000, **kw)
-        ex.set_tuning(tuning)
+        ex = pkg.Extractor(upsample=1, max_kpts=8000, **kw)  # default tuning
         step = lambda: ex.extract_batch_async(imgs, stream)  # noqa: E731
         t, _ = timed_steps(torch, step, steps, 3, flush, stream)
         counts = ex._counts[:len(imgs)].tolist()
@@ -605,6 +604,16 @@ def homography_side(torch, pkg, flush, stream, tuning, steps):
             r["per_image_mpix_s"] = round(mpix * len(ts) / (sum(ts) / 1e3), 1)
             r["accuracy"] = {"what": "image 0 matched to each warped image; MMA against the known "
                                      "homographies (harness: torch mutual NN + ratio 0.8)", **acc}
+            # The batch autotuner on this batch: the steps above used the defaults.
+            t0 = time.perf_counter()
+            js, _ = ex.autotune_batch(imgs, stream)
+            torch.cuda.synchronize()
+            search = time.perf_counter() - t0
+            tt, _ = timed_steps(torch, step, steps, 3, flush, stream)
+            r["autotune"] = {"untuned_ms_per_step": r["ms_per_step"],
+                             "tuned_ms_per_step": round(statistics.mean(tt), 4),
+                             "untuned_over_tuned": round(r["ms_per_step"] / statistics.mean(tt), 4),
+                             "search_s": round(search, 3), "tuning": js}
         out[label] = r
         ex.close()
     return out
@@ -681,6 +690,14 @@ def other_configs(torch, pkg, flush, stream, tuning):
     n0 = int(ex0._counts[0].item())
     out["single_vga"] = {"workload": "one 640x480 image, plain SIFT, no upsampling",
                          "ms_per_image": round(statistics.median(t0), 4), "keypoints": n0}
+    js, _ = ex0.autotune_batch(vga, stream)
+    torch.cuda.synchronize()
+    t0t, _ = timed_steps(torch, lambda: ex0.extract_async(vga[0], stream), 20, 3, flush, stream)
+    out["single_vga"]["autotune"] = {
+        "untuned_ms_per_image": round(statistics.median(t0), 4),
+        "tuned_ms_per_image": round(statistics.median(t0t), 4),
+        "untuned_over_tuned": round(statistics.median(t0) / statistics.median(t0t), 4),
+        "tuning": js}
     ex0.close()
     seq = synth.wide_baseline_pair(0)
     pair = _device_images(seq.images, torch)

@@ -428,9 +428,16 @@ __global__ void __launch_bounds__(kThreads) k_refine(const Desc *__restrict__ d)
   const int total = d->cand_flat[n];
   const int S = d->n_scales, bord = d->border, iters = d->max_iter;
   const float T = d->contrast_thr, er = d->edge_ratio;
-  // Candidate t goes to block t % G, thread (t / G) % blockDim.x: a few
-  // thousand candidates spread over every SM instead of filling the first blocks.
-  for (int t = blockIdx.x + gridDim.x * threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+  // Runs of 32 consecutive candidates go to the warps in turn, block first
+  // (run c to block c % G, warp (c / G) % 8): a few thousand candidates still
+  // spread over every SM, and the lanes of a warp refine neighbouring
+  // candidates (canonical order: same layer, nearby rows), whose 3 x 3 x 3
+  // windows share cache sectors.
+  const int lane = threadIdx.x & 31;
+  const int NW = gridDim.x * (blockDim.x >> 5);
+  for (int run = blockIdx.x + gridDim.x * (threadIdx.x >> 5); run * 32 < total; run += NW) {
+    const int t = run * 32 + lane;
+    if (t >= total) continue;
     const int b = find_owner(d->cand_flat, n, t);
     const ImgDev &im = d->img[b];
     const long long slot = im.cand_off + (t - d->cand_flat[b]);
