@@ -245,6 +245,32 @@ def _alg_blur_bytes(shapes, upsample, S=3, min_side=16):
     return tot, px_tot
 
 
+def _level_radii(S=3, sigma0=1.6):
+    """Blur radius ceil(4 kappa_i) of the incremental level blurs i = 1 .. S + 2,
+    kappa_i = sigma0 sqrt(2^(2i/S) - 2^(2(i-1)/S)) (§3.2)."""
+    return [math.ceil(4.0 * sigma0 * math.sqrt(2.0 ** (2.0 * i / S) - 2.0 ** (2.0 * (i - 1) / S))
+                      - 1e-9) for i in range(1, S + 3)]
+
+
+def _alg_blur_flops(shapes, upsample, S=3, min_side=16):
+    """FP32 operations of all level-blur launches of one step: a separable blur
+    of radius R is 2 (2R + 1) FMAs, 4 (2R + 1) FLOP, per octave pixel."""
+    radii = _level_radii(S)
+    tot = 0
+    for (h, w) in shapes:
+        for (H, W) in _octaves(h, w, upsample, min_side):
+            tot += H * W * sum(4 * (2 * r + 1) for r in radii)
+    return tot
+
+
+def _fp32_peak_tflops(sm_mhz):
+    """FP32 FMA peak from unit counts and the SM clock: 128 FP32 lanes per SM,
+    2 FLOP per FMA."""
+    import torch
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
 def _pyramid_bytes(shapes, upsample, fp16, S=3, min_side=16):
     """Device bytes of one step's Gaussian pyramids: S + 3 levels per octave,
     rows padded to 32 elements; 4-byte elements, or 2-byte ones above octave 0
@@ -330,7 +356,7 @@ def _traffic_per_launch(px_step, blur_n):
     return int(tj["dram_bytes_per_px"] * px_step / blur_n)
 
 
-def rooflines(acc, shapes, upsample, kpts):
+def rooflines(acc, shapes, upsample, kpts, sm_mhz=None):
     peak, peak_kind = _peaks()
     src = "hbm_gbs, " + ("of measured (MEASURED_PEAKS.json)" if peak_kind == "measured"
                          else "of fallback")
@@ -343,6 +369,19 @@ def rooflines(acc, shapes, upsample, kpts):
                 "alg_bytes_per_launch": int(alg_step / max(1, blur_n)),
                 "launch_ms_avg": round(blur_ms / max(1, blur_n), 5),
                 "peak_source": src}
+    if blur_ms > 0 and sm_mhz:
+        # The level blur sits at the ridge of the dual roofline (HBM bytes vs
+        # FP32 FMAs): its attainable time is the larger of the two.
+        flops = _alg_blur_flops(shapes, upsample)
+        fp32_peak = _fp32_peak_tflops(sm_mhz)
+        t_hbm = alg_step / (peak * 1e9)
+        t_fp32 = flops / (fp32_peak * 1e12)
+        roofline["dual"] = {
+            "fp32_tflops_achieved": round(flops / (blur_ms / 1e3) / 1e12, 2),
+            "fp32_peak_tflops": round(fp32_peak, 1),
+            "fp32_peak_source": "SMs x 128 FP32 lanes x 2 FLOP x median SM clock under load",
+            "hbm_time_ms": round(t_hbm * 1e3, 4), "fp32_time_ms": round(t_fp32 * 1e3, 4),
+            "frac_of_attainable": round(max(t_hbm, t_fp32) / (blur_ms / 1e3), 4)}
     cls_bytes = _alg_class_bytes(shapes, upsample)
     cls_bytes["blur"] = alg_step
     per_class = {}
@@ -473,7 +512,7 @@ def gpu_arm(args, rank, world, pool, batch):
 
     reps = max(3, args.steps // 4)
     acc = profiled_classes(torch, ex, step, flush, reps)
-    roofline, per_class = rooflines(acc, shapes, False, kpts)
+    roofline, per_class = rooflines(acc, shapes, False, kpts, clock_info.get("sm_mhz"))
     e2e = e2e_throughput(torch, pkg, ex, imgs_np, tuning, max(3, args.steps // 2), args.warmup,
                          world, ext_kw)
 

@@ -110,29 +110,22 @@ __device__ __forceinline__ void ori_sweep(const float *__restrict__ L, long long
     const int px = x0 + i, py = y0 + j;
     return q < nsamp && px >= 1 && px <= W - 2 && py >= 1 && py <= H - 2;
   };
+  // Without branches: a sample outside the window or the image reads the
+  // keypoint's own pixel neighbourhood (always inside: keypoints keep the
+  // border) and votes with weight 0, which leaves its bin unchanged.
   for (int q = lane; q < nsamp; q += 64) {
     const int i0 = c - R, j0 = jj - R;
     advance();
     const int i1 = c - R, j1 = jj - R;
     advance();
     const bool ok0 = inside(q, i0, j0), ok1 = inside(q + 32, i1, j1);
-    float a0 = 0.f, b0 = 0.f, e0 = 0.f, f0 = 0.f, a1 = 0.f, b1 = 0.f, e1 = 0.f, f1 = 0.f;
-    if (ok0) {
-      const int o = j0 * pitch + i0;
-      a0 = v[o + 1];
-      b0 = v[o - 1];
-      e0 = v[o + pitch];
-      f0 = v[o - pitch];
-    }
-    if (ok1) {
-      const int o = j1 * pitch + i1;
-      a1 = v[o + 1];
-      b1 = v[o - 1];
-      e1 = v[o + pitch];
-      f1 = v[o - pitch];
-    }
-    if (ok0) ori_vote(hist, lane, a0 - b0, e0 - f0, expf((float)(i0 * i0 + j0 * j0) * ninv));
-    if (ok1) ori_vote(hist, lane, a1 - b1, e1 - f1, expf((float)(i1 * i1 + j1 * j1) * ninv));
+    const int o0 = ok0 ? j0 * pitch + i0 : 0, o1 = ok1 ? j1 * pitch + i1 : 0;
+    const float a0 = v[o0 + 1], b0 = v[o0 - 1], e0 = v[o0 + pitch], f0 = v[o0 - pitch];
+    const float a1 = v[o1 + 1], b1 = v[o1 - 1], e1 = v[o1 + pitch], f1 = v[o1 - pitch];
+    const float w0 = expf((float)(i0 * i0 + j0 * j0) * ninv);
+    const float w1 = expf((float)(i1 * i1 + j1 * j1) * ninv);
+    ori_vote(hist, lane, a0 - b0, e0 - f0, ok0 ? w0 : 0.f);
+    ori_vote(hist, lane, a1 - b1, e1 - f1, ok1 ? w1 : 0.f);
   }
 }
 

@@ -102,6 +102,15 @@ template <int S>
 __device__ __forceinline__ void ext_test(const ExtRow<S> &P, const ExtRow<S> &C,
                                          const ExtRow<S> &N, bool inb, float thr, int lane,
                                          uint32_t *word) {
+  // Rows where no pixel of the strip passes the border and pre-gate tests
+  // in any layer have no candidate: skip the neighbour comparisons.
+  bool any = false;
+#pragma unroll
+  for (int s = 1; s <= S; s++) any |= inb && fabsf(C.c[s - 1]) > thr;
+  if (!__any_sync(0xffffffffu, any)) {
+    if (lane < S) *word = 0u;
+    return;
+  }
   float vx[S + 2], vn[S + 2];
 #pragma unroll
   for (int l = 0; l < S + 2; l++) {
