@@ -431,6 +431,20 @@ __device__ __forceinline__ int round_half_away(float v) {
   return (int)(v >= 0.f ? a : -a);
 }
 
+// Levels s - 1 .. s + 2 at rows y - 1 .. y + 1 and columns x - 1 .. x + 1 of
+// an octave's level stack G (FP32, or binary16 widened: HF).
+template <bool HF>
+__device__ __forceinline__ void refine_window(const float *__restrict__ G, int s, int y, int x,
+                                              long long ls, int pitch, float (&g)[4][3][3]) {
+  const long long base = (long long)(s - 1) * ls + (long long)(y - 1) * pitch + (x - 1);
+#pragma unroll
+  for (int a = 0; a < 4; a++)
+#pragma unroll
+    for (int bb = 0; bb < 3; bb++)
+#pragma unroll
+      for (int cc = 0; cc < 3; cc++) g[a][bb][cc] = lvl_ld(G, HF, base + a * ls + bb * pitch + cc);
+}
+
 __global__ void __launch_bounds__(kThreads) k_refine(const Desc *__restrict__ d) {
   pdl_wait();
   const int n = d->n_img;
@@ -463,18 +477,21 @@ __global__ void __launch_bounds__(kThreads) k_refine(const Desc *__restrict__ d)
     float hxx = 0.f, hyy = 0.f, hxy = 0.f;
     bool conv = false;
     for (int it = 0; it < iters; it++) {
+      // The 3 x 3 x 3 DoG neighbourhood of layers s - 1 .. s + 1: the four
+      // Gaussian levels s - 1 .. s + 2 are each loaded once (36 values), and
+      // DoG layer k is level k + 1 minus level k, one FP32 subtraction.
+      float g[4][3][3];
+      if (hf)
+        refine_window<true>(G, s, y, x, ls, pitch, g);
+      else
+        refine_window<false>(G, s, y, x, ls, pitch, g);
       float v[3][3][3];
 #pragma unroll
-      for (int a = 0; a < 3; a++) {
-        const long long l0 = (long long)(s + a - 1) * ls;
+      for (int a = 0; a < 3; a++)
 #pragma unroll
         for (int bb = 0; bb < 3; bb++)
 #pragma unroll
-          for (int cc = 0; cc < 3; cc++) {
-            const long long off = l0 + (long long)(y + bb - 1) * pitch + (x + cc - 1);
-            v[a][bb][cc] = lvl_ld(G, hf, off + ls) - lvl_ld(G, hf, off);
-          }
-      }
+          for (int cc = 0; cc < 3; cc++) v[a][bb][cc] = g[a + 1][bb][cc] - g[a][bb][cc];
       c = v[1][1][1];
       gx = 0.5f * (v[1][1][2] - v[1][1][0]);
       gy = 0.5f * (v[1][2][1] - v[1][0][1]);
