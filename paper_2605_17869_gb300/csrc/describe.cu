@@ -18,21 +18,6 @@ constexpr float kTwoPi = 6.283185307179586f;
 constexpr int kKpWarps = 4;  // warps per keypoint (orientation and descriptor)
 constexpr int kThreads = 256;
 
-// Sum over the kKpWarps * 32 threads of the block in a fixed order: a butterfly
-// within each warp (every lane ends with the same value), then the warp sums
-// in warp order. Every thread returns the same total.
-__device__ __forceinline__ float block_sum_f(float v, float *red) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  float s = 0.f;
-#pragma unroll
-  for (int w = 0; w < kKpWarps; w++) s += red[w];
-  __syncthreads();
-  return s;
-}
-
 __device__ __forceinline__ float sigma_of(const Desc *d, const RefRec &r) {
   return d->sigma0 * exp2f(((float)r.s + r.ds) / (float)d->n_scales);
 }
@@ -658,7 +643,7 @@ template <bool MIXED>
 __global__ void __launch_bounds__(kKpWarps * 32, 6) k_descriptor(const Desc *__restrict__ d) {
   pdl_wait();
   extern __shared__ __align__(16) float dsm[];
-  __shared__ float red[kKpWarps];
+  __shared__ float s_bins[kDescLen];
   __shared__ int s_lo[kKpWarps][32], s_pre[kKpWarps][33];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float *hist = dsm + warp * kDescWarpFloats;
@@ -721,18 +706,44 @@ __global__ void __launch_bounds__(kKpWarps * 32, 6) k_descriptor(const Desc *__r
     float val = pw[0];
 #pragma unroll
     for (int w = 1; w < kKpWarps; w++) val += pw[w];
-    float *out = im.odesc + (long long)j * kDescLen;
-    const float sq = block_sum_f(val * val, red);
-    if (sq > 0.f) {
-      val = fminf(val / sqrtf(sq), 0.2f);
-      const float sq2 = block_sum_f(val * val, red);
-      val = val / sqrtf(sq2);
-      if (d->rootsift) val = sqrtf(val / block_sum_f(val, red));
-    } else {
-      val = 0.f;
-    }
-    out[tid] = val;
+    s_bins[tid] = val;
     __syncthreads();
+    // Normalisation by warp 0 alone (lane l: bins l, l + 32, l + 64, l + 96;
+    // sums in that order, then across lanes by a butterfly), so that the
+    // other warps go on to the next keypoint without waiting. Warp 0 reads
+    // the bins before it reaches the next keypoint's barrier, the only point
+    // after which they are rewritten.
+    if (warp == 0) {
+      float bv[4];
+#pragma unroll
+      for (int k = 0; k < 4; k++) bv[k] = s_bins[lane + 32 * k];
+      auto warp_total = [&](float x) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        return x;
+      };
+      const float sq = warp_total(bv[0] * bv[0] + bv[1] * bv[1] + bv[2] * bv[2] + bv[3] * bv[3]);
+      if (sq > 0.f) {
+        const float n1 = sqrtf(sq);
+#pragma unroll
+        for (int k = 0; k < 4; k++) bv[k] = fminf(bv[k] / n1, 0.2f);
+        const float n2 =
+            sqrtf(warp_total(bv[0] * bv[0] + bv[1] * bv[1] + bv[2] * bv[2] + bv[3] * bv[3]));
+#pragma unroll
+        for (int k = 0; k < 4; k++) bv[k] = bv[k] / n2;
+        if (d->rootsift) {
+          const float l1 = warp_total(bv[0] + bv[1] + bv[2] + bv[3]);
+#pragma unroll
+          for (int k = 0; k < 4; k++) bv[k] = sqrtf(bv[k] / l1);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; k++) bv[k] = 0.f;
+      }
+      float *out = im.odesc + (long long)j * kDescLen;
+#pragma unroll
+      for (int k = 0; k < 4; k++) out[lane + 32 * k] = bv[k];
+    }
   }
 }
 
