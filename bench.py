@@ -547,6 +547,12 @@ def gpu_arm(args, rank, world, pool, batch):
         "gpu_launches": launches_per_step * args.steps,
         "gpu_launches_per_step": launches_per_step,
         "kernel_ms_per_step": {k: round(v[0], 4) for k, v in acc.items()},
+        # Per-class times come from the profiled graph (an event pair around every
+        # launch, all on one stream); their sum against the live step shows how
+        # much the side branches and programmatic dependent launch overlap.
+        "kernel_ms_per_step_note": "profiled graph: each launch timed alone on one stream",
+        "kernel_ms_sum": round(sum(v[0] for v in acc.values()), 4),
+        "live_over_kernel_sum": round((total_ms / args.steps) / max(1e-9, sum(v[0] for v in acc.values())), 4),
         "autotune": autotune and {**autotune, "tuned_ms_per_step": round(total_ms / args.steps, 4),
                                   "untuned_over_tuned": round(autotune["untuned_ms_per_step"] /
                                                               (total_ms / args.steps), 4)},
