@@ -380,7 +380,9 @@ sift_status sift_tuning_cache_put(const char *path, const char *signature, const
  * device (§3.3: results are handed to other frameworks by DLPack, without a
  * copy); results are library-owned until released. */
 typedef struct {
-  sift_status status;   /* SIFT_OK, SIFT_W_TRUNCATED or an error */
+  sift_status status;   /* SIFT_OK, SIFT_W_TRUNCATED or an error (SIFT_E_TIMEOUT:
+                           a compaction wait of the request's step gave up, as in
+                           sift_last_stats; its results are not valid) */
   int count;            /* keypoints in the buffers below */
   sift_kpts_dev kpts;   /* device buffers, valid until sift_serve_release */
   float *desc;          /* device, count x 128 */

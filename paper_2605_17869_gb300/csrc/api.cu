@@ -445,6 +445,8 @@ struct Lane {
   std::vector<uint64_t> reqs;
   int *h_counts = nullptr;                 // pinned
   sift::ImgCounters *h_flags = nullptr;    // pinned
+  unsigned long long *h_gave = nullptr;    // pinned: the engine's gave-up word after the step
+  unsigned epoch = 0;                      // the step's scan epoch
   Clock::time_point t_done;
   DoneMsg msg{};
 };
@@ -504,7 +506,10 @@ void retire(Server *s, Lane &l) {
     Request &r = it->second;
     r.state = 2;
     r.count = l.h_counts[i];
-    r.status = (l.h_flags[i].flags & (sift::TF_CAND | sift::TF_ORI)) ? SIFT_W_TRUNCATED : SIFT_OK;
+    if (*l.h_gave == l.epoch)  // a compaction wait of this step gave up
+      r.status = SIFT_E_TIMEOUT;
+    else
+      r.status = (l.h_flags[i].flags & (sift::TF_CAND | sift::TF_ORI)) ? SIFT_W_TRUNCATED : SIFT_OK;
     r.t_done = l.t_done;
     s->in_flight--;
   }
@@ -562,6 +567,10 @@ sift_status launch_step(Lane &l, int K, std::vector<Job> &jobs, std::string *err
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(l.h_flags, l.eng->workspace() + l.eng->layout().cnt,
                           in.size() * sizeof(sift::ImgCounters), cudaMemcpyDeviceToHost, l.stream);
+    l.epoch = l.eng->last_epoch();
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(l.h_gave, l.eng->gave_up_word(), sizeof(unsigned long long),
+                          cudaMemcpyDeviceToHost, l.stream);
     if (e == cudaSuccess) e = cudaEventRecord(l.ev_end, l.stream);
     if (e == cudaSuccess) e = cudaLaunchHostFunc(l.stream, on_lane_done, &l.msg);
     if (e != cudaSuccess) {
@@ -713,6 +722,7 @@ sift_status sift_serve_create(sift_handle *h, size_t mem_budget_bytes, int max_s
     if (e == cudaSuccess) e = cudaHostAlloc(&l.h_counts, sift::kMaxImg * sizeof(int), 0);
     if (e == cudaSuccess)
       e = cudaHostAlloc(&l.h_flags, sift::kMaxImg * sizeof(sift::ImgCounters), 0);
+    if (e == cudaSuccess) e = cudaHostAlloc(&l.h_gave, sizeof(unsigned long long), 0);
     l.msg = DoneMsg{&s, i};
     if (st != SIFT_OK || e != cudaSuccess) {
       for (auto &m : s.lanes) {
@@ -722,6 +732,7 @@ sift_status sift_serve_create(sift_handle *h, size_t mem_budget_bytes, int max_s
         if (m.ev_end) cudaEventDestroy(m.ev_end);
         if (m.h_counts) cudaFreeHost(m.h_counts);
         if (m.h_flags) cudaFreeHost(m.h_flags);
+        if (m.h_gave) cudaFreeHost(m.h_gave);
       }
       if (s.ev_ref) cudaEventDestroy(s.ev_ref);
       delete sv;
@@ -860,6 +871,7 @@ sift_status sift_serve_destroy(sift_server *sv) {
     cudaEventDestroy(l.ev_end);
     cudaFreeHost(l.h_counts);
     cudaFreeHost(l.h_flags);
+    cudaFreeHost(l.h_gave);
   }
   cudaEventDestroy(s.ev_ref);
   s.h->serving = false;

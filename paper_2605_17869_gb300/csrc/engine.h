@@ -98,6 +98,10 @@ class Engine {
   sift_status kernel_times(double *ms, int *launches, int n_classes);
   sift_status last_stats(int *stats, int max_images);
   int last_launch_count() const { return last_kernels_; }
+  // The single-pass scan's gave-up word (device) and the last run's epoch: the
+  // run's compaction counts are valid unless the word equals the epoch.
+  const unsigned long long *gave_up_word() const { return lb_; }
+  unsigned last_epoch() const { return epoch_; }
 
   Tuning tuning() const { return tun_; }
   void set_tuning(const Tuning &t);

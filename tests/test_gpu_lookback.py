@@ -6,7 +6,8 @@ poll limit; when it runs out the kernel records it and finishes, and the host
 reads SIFT_E_TIMEOUT from sift_last_stats. The test makes a wait run out
 without any fault: in a child process, the test hook names a chunk that never
 publishes and shortens the poll limit. The CUDA context must stay usable and
-a handle made without the hook must extract normally in the same process."""
+a handle made without the hook must extract normally in the same process. A
+served request whose step gave up carries the same status."""
 import json
 import os
 import subprocess
@@ -40,6 +41,15 @@ try:
 except pkg.SiftError as e:
     out["held_status"] = e.status
 ex.close()
+srv = pkg.Server(pkg.Extractor(max_kpts=4096), budget_bytes=1 << 30)  # lanes read the hook too
+tk = srv.submit(img)
+try:
+    srv.result(tk)
+    out["served_status"] = 0
+except pkg.SiftError as e:
+    out["served_status"] = e.status
+srv.release(tk)
+srv.close()
 del os.environ["SIFT_TEST_LOOKBACK_HOLD"]
 del os.environ["SIFT_TEST_LOOKBACK_SPINS"]
 ex2 = pkg.Extractor(max_kpts=4096)         # no hook
@@ -64,6 +74,7 @@ def test_wait_that_never_completes_reports_timeout_and_context_survives():
     out = json.loads(r.stdout.strip().splitlines()[-1])
     import paper_2605_17869_gb300 as pkg
     assert out["held_status"] == pkg.SIFT_E_TIMEOUT
+    assert out["served_status"] == pkg.SIFT_E_TIMEOUT  # the serving result carries it too
     assert out["held_count_in_range"]
     assert out["clean_status"] == pkg.SIFT_OK
     assert out["clean_count"] > 0 and out["clean_repeatable"]
