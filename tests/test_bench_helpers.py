@@ -78,3 +78,23 @@ def test_clock_sampler_parses_the_csv(tmp_path):
 def test_clock_sampler_without_nvidia_smi():
     c = bench.Clocks(0)
     assert c.stop() is None
+
+
+@pytest.mark.parametrize("S,sigma0", [(3, 1.6), (4, 1.6), (2, 1.3)])
+def test_level_radii_follow_the_oracle_taps(S, sigma0):
+    """The dual roofline's FP32 count uses the level blurs' radii: they must be
+    the oracle's ceil(4 kappa_i) for the increments kappa_i of §3.2."""
+    from oracle import sift_oracle as so
+    p = so.Params()
+    p.n_scales, p.sigma0 = S, sigma0
+    assert bench._level_radii(S, sigma0) == [so.gaussian_taps(k)[0] for k in so.increment_sigmas(p)]
+
+
+def test_blur_flops_count_every_level_of_every_octave():
+    """4 (2R + 1) FLOP per octave pixel per level blur (two passes of 2R + 1
+    FMAs), summed over the library's octaves."""
+    shapes = [(480, 640), (97, 211)]
+    radii = bench._level_radii()
+    want = sum(H * W * sum(4 * (2 * r + 1) for r in radii)
+               for h, w in shapes for (H, W) in _geometry(h, w, False))
+    assert bench._alg_blur_flops(shapes, False) == want
