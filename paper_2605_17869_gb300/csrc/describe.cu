@@ -565,28 +565,38 @@ __device__ __forceinline__ void desc_sweep(const Desc *__restrict__ d, const Ref
         if (lane == 31) wpre[32] = tot;
         __syncwarp();
         int row = 0;
-        // Warp-uniform trip count: every lane reaches the commit's __syncwarp.
-        for (int q0 = 0; q0 < tot; q0 += 32) {
-          const int q = q0 + lane;
-          bool ok = q < tot;
+        // Sample q of the list: bin coordinates, whether it lies in the
+        // square, and its offset from the keypoint pixel (0, the keypoint's
+        // own in-image neighbourhood, when it does not).
+        auto locate = [&](int q, float &rx, float &ry, int &off) {
+          if (q >= tot) return false;
+          while (wpre[row + 1] <= q) row++;
+          const int jy = jlo + warp + kKpWarps * (rb + row);
+          const int i = wlo[row] + (q - wpre[row]);
+          const float ox = (float)i - r.dx, oy = (float)jy - r.dy;
+          rx = (ct * ox + st * oy) * inv_w;
+          ry = (-st * ox + ct * oy) * inv_w;
+          const float u = rx + 1.5f, v = ry + 1.5f;
+          const bool in = u > -1.f && u < 4.f && v > -1.f && v < 4.f;
+          off = in ? jy * pitch + i : 0;
+          return in;
+        };
+        // Two samples per lane per step, q and q + 32 (the lane's samples in
+        // increasing order, as one per step would take them): the eight loads
+        // of both are issued before either votes. Warp-uniform trip count:
+        // every lane reaches the commits' __syncwarp.
+        for (int q0 = 0; q0 < tot; q0 += 64) {
+          float rxa = 0.f, rya = 0.f, rxb = 0.f, ryb = 0.f;
+          int oa = 0, ob = 0;
+          const bool oka = locate(q0 + lane, rxa, rya, oa);
+          const bool okb = locate(q0 + 32 + lane, rxb, ryb, ob);
+          const float ga = lv[oa + 1] - lv[oa - 1], ha = lv[oa + pitch] - lv[oa - pitch];
+          const float gb = lv[ob + 1] - lv[ob - 1], hb = lv[ob + pitch] - lv[ob - pitch];
           Vote vt;
-          if (ok) {
-            while (wpre[row + 1] <= q) row++;
-            const int jy = jlo + warp + kKpWarps * (rb + row);
-            const int i = wlo[row] + (q - wpre[row]);
-            const float ox = (float)i - r.dx, oy = (float)jy - r.dy;
-            const float rx = (ct * ox + st * oy) * inv_w;
-            const float ry = (-st * ox + ct * oy) * inv_w;
-            const float u = rx + 1.5f, v = ry + 1.5f;
-            ok = u > -1.f && u < 4.f && v > -1.f && v < 4.f;
-            if (ok) {
-              const int o = jy * pitch + i;
-              const float gx = lv[o + 1] - lv[o - 1];
-              const float gy = lv[o + pitch] - lv[o - pitch];
-              desc_targets(vt, rx, ry, gx, gy, th);
-            }
-          }
-          desc_commit(hist, lane, ok, vt);
+          if (oka) desc_targets(vt, rxa, rya, ga, ha, th);
+          desc_commit(hist, lane, oka, vt);
+          if (okb) desc_targets(vt, rxb, ryb, gb, hb, th);
+          desc_commit(hist, lane, okb, vt);
         }
         __syncwarp();  // the next round rewrites this warp's interval table
       }
