@@ -71,8 +71,8 @@ __device__ __forceinline__ void ori_vote(float (*hist)[32], int lane, float dx, 
 }
 
 // The window's samples, lane l taking samples l, l + 32, l + 64, ... in that
-// order, two per step: the eight loads of a pair are issued before either
-// vote, so that more loads are in flight per warp.
+// order, three per step: the twelve loads of a step are issued before any of
+// its votes, so that more loads are in flight per warp.
 template <bool HF>
 __device__ __forceinline__ void ori_sweep(const float *__restrict__ L, long long lofs, int pitch,
                                           int H, int W, int x0, int y0, int R, float ninv,
@@ -98,19 +98,29 @@ __device__ __forceinline__ void ori_sweep(const float *__restrict__ L, long long
   // Without branches: a sample outside the window or the image reads the
   // keypoint's own pixel neighbourhood (always inside: keypoints keep the
   // border) and votes with weight 0, which leaves its bin unchanged.
-  for (int q = lane; q < nsamp; q += 64) {
-    const int i0 = c - R, j0 = jj - R;
-    advance();
-    const int i1 = c - R, j1 = jj - R;
-    advance();
-    const bool ok0 = inside(q, i0, j0), ok1 = inside(q + 32, i1, j1);
-    const int o0 = ok0 ? j0 * pitch + i0 : 0, o1 = ok1 ? j1 * pitch + i1 : 0;
-    const float a0 = v[o0 + 1], b0 = v[o0 - 1], e0 = v[o0 + pitch], f0 = v[o0 - pitch];
-    const float a1 = v[o1 + 1], b1 = v[o1 - 1], e1 = v[o1 + pitch], f1 = v[o1 - pitch];
-    const float w0 = expf((float)(i0 * i0 + j0 * j0) * ninv);
-    const float w1 = expf((float)(i1 * i1 + j1 * j1) * ninv);
-    ori_vote(hist, lane, a0 - b0, e0 - f0, ok0 ? w0 : 0.f);
-    ori_vote(hist, lane, a1 - b1, e1 - f1, ok1 ? w1 : 0.f);
+  constexpr int NS = 3;
+  for (int q = lane; q < nsamp; q += 32 * NS) {
+    int ii[NS], jv[NS], off[NS];
+    bool ok[NS];
+#pragma unroll
+    for (int k = 0; k < NS; k++) {
+      ii[k] = c - R;
+      jv[k] = jj - R;
+      advance();
+      ok[k] = inside(q + 32 * k, ii[k], jv[k]);
+      off[k] = ok[k] ? jv[k] * pitch + ii[k] : 0;
+    }
+    float gx[NS], gy[NS];
+#pragma unroll
+    for (int k = 0; k < NS; k++) {
+      gx[k] = v[off[k] + 1] - v[off[k] - 1];
+      gy[k] = v[off[k] + pitch] - v[off[k] - pitch];
+    }
+#pragma unroll
+    for (int k = 0; k < NS; k++) {
+      const float w = expf((float)(ii[k] * ii[k] + jv[k] * jv[k]) * ninv);
+      ori_vote(hist, lane, gx[k], gy[k], ok[k] ? w : 0.f);
+    }
   }
 }
 
