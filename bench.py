@@ -356,6 +356,17 @@ def _traffic_per_launch(px_step, blur_n):
     return int(tj["dram_bytes_per_px"] * px_step / blur_n)
 
 
+def _is_default_tuning(js):
+    """Whether a tuning JSON is the defaults (32-row tiles, occupancy-maximum
+    grids): a tuned time then differs from the untuned one by noise only."""
+    t = json.loads(js)
+    rows = t.get("blur_tile_rows", [])
+    rows = rows if rows and isinstance(rows[0], list) else [rows]
+    return (all(r == 32 for oc in rows for r in oc)
+            and all(c == 0 for c in t.get("blur_ctas_per_sm", []))
+            and all(v == 0 for k, v in t.items() if k.endswith("_ctas_per_sm") and not isinstance(v, list)))
+
+
 def rooflines(acc, shapes, upsample, kpts, sm_mhz=None):
     peak, peak_kind = _peaks()
     src = "hbm_gbs, " + ("of measured (MEASURED_PEAKS.json)" if peak_kind == "measured"
@@ -480,6 +491,8 @@ def gpu_arm(args, rank, world, pool, batch):
         autotune = {"untuned_ms_per_step": round(statistics.mean(t_def), 4),
                     "search_s": round(time.perf_counter() - t0, 3), "from_cache": hit}
     tuning = ex.get_tuning()
+    if autotune is not None:
+        autotune["chose_defaults"] = _is_default_tuning(tuning)
 
     if args.minimal:
         times, _ = timed_steps(torch, step, args.steps, args.warmup, flush, stream)
@@ -658,7 +671,8 @@ def homography_side(torch, pkg, flush, stream, tuning, steps):
             r["autotune"] = {"untuned_ms_per_step": r["ms_per_step"],
                              "tuned_ms_per_step": round(statistics.mean(tt), 4),
                              "untuned_over_tuned": round(r["ms_per_step"] / statistics.mean(tt), 4),
-                             "search_s": round(search, 3), "tuning": js}
+                             "search_s": round(search, 3), "tuning": js,
+                             "chose_defaults": _is_default_tuning(js)}
         out[label] = r
         ex.close()
     return out
@@ -742,7 +756,7 @@ def other_configs(torch, pkg, flush, stream, tuning):
         "untuned_ms_per_image": round(statistics.median(t0), 4),
         "tuned_ms_per_image": round(statistics.median(t0t), 4),
         "untuned_over_tuned": round(statistics.median(t0) / statistics.median(t0t), 4),
-        "tuning": js}
+        "tuning": js, "chose_defaults": _is_default_tuning(js)}
     ex0.close()
     seq = synth.wide_baseline_pair(0)
     pair = _device_images(seq.images, torch)

@@ -98,3 +98,15 @@ def test_blur_flops_count_every_level_of_every_octave():
     want = sum(H * W * sum(4 * (2 * r + 1) for r in radii)
                for h, w in shapes for (H, W) in _geometry(h, w, False))
     assert bench._alg_blur_flops(shapes, False) == want
+
+
+def test_default_tuning_is_recognised():
+    d = ('{"blur_tile_rows": [[32, 32, 32, 32, 32]], "blur_ctas_per_sm": [0], '
+         '"extrema_ctas_per_sm": 0, "orientation_ctas_per_sm": 0, "descriptor_ctas_per_sm": 0, '
+         '"compaction_ctas_per_sm": 0}')
+    assert bench._is_default_tuning(d)
+    assert bench._is_default_tuning('{"blur_tile_rows": [32, 32, 32, 32, 32]}')
+    assert not bench._is_default_tuning(d.replace('"extrema_ctas_per_sm": 0', '"extrema_ctas_per_sm": 4'))
+    assert not bench._is_default_tuning(d.replace("[[32, 32, 32, 32, 32]]",
+                                                  "[[32, 32, 32, 32, 32], [32, 64, 32, 32, 32]]"))
+    assert not bench._is_default_tuning(d.replace('"blur_ctas_per_sm": [0]', '"blur_ctas_per_sm": [0, 3]'))
