@@ -263,11 +263,14 @@ __global__ void __launch_bounds__(kThreads) k_cc_compact(const Desc *__restrict_
   const LookbackCfg cfg{d->lb_epoch, d->lb_spins, d->lb_hold, d->lb_err};
   const int ca = (int)((long long)C * g / G), cb = (int)((long long)C * (g + 1) / G);
   const int kept = min(cb - ca, kMaxCh);
+  // Owners of the range's chunks: found once, then advanced (the chunks are
+  // contiguous and images are in order).
+  const int b_lo = ca < cb ? find_owner(d->cc_pre, n, ca) : 0;
   int np[SPT];
   int s0;
   int over = 0;
-  for (int c = ca; c < cb; c++) {
-    const int b = find_owner(d->cc_pre, n, c);
+  for (int c = ca, b = b_lo; c < cb; c++) {
+    while (c >= d->cc_pre[b + 1]) b++;
     const int v = cc_chunk_peaks(d, d->img[b], d->cnt[b].n_cand, c, d->cc_pre[b], np, &s0);
     if (c - ca < kMaxCh) {
       int ws = v;
@@ -294,8 +297,8 @@ __global__ void __launch_bounds__(kThreads) k_cc_compact(const Desc *__restrict_
   unsigned long long *starts = d->lb_start + kMaxImg;
   {
     int acc = base;
-    for (int c = ca; c < cb; c++) {
-      const int b = find_owner(d->cc_pre, n, c);
+    for (int c = ca, b = b_lo; c < cb; c++) {
+      while (c >= d->cc_pre[b + 1]) b++;
       if (c == d->cc_pre[b] && threadIdx.x == 0) lb_store(starts + b, lb_word(kLbInc, cfg.epoch, acc));
       int t = 0;
       if (c - ca < kMaxCh) {
@@ -309,8 +312,8 @@ __global__ void __launch_bounds__(kThreads) k_cc_compact(const Desc *__restrict_
   }
   int carry = base;
   int cur = -1, start = 0;
-  for (int c = ca; c < cb; c++) {
-    const int b = find_owner(d->cc_pre, n, c);
+  for (int c = ca, b = b_lo; c < cb; c++) {
+    while (c >= d->cc_pre[b + 1]) b++;
     const ImgDev &im = d->img[b];
     const int c0 = d->cc_pre[b];
     const int v = cc_chunk_peaks(d, im, d->cnt[b].n_cand, c, c0, np, &s0);

@@ -290,12 +290,15 @@ __global__ void __launch_bounds__(kThreads) k_bm_compact(const Desc *__restrict_
   const LookbackCfg cfg{d->lb_epoch, d->lb_spins, d->lb_hold, d->lb_err};
   const int ca = (int)((long long)C * g / G), cb = (int)((long long)C * (g + 1) / G);
   const int kept = min(cb - ca, kMaxCh);
+  // Owners of the range's chunks: found once, then advanced (the chunks are
+  // contiguous and images are in order).
+  const int b_lo = ca < cb ? find_owner(d->bmc_pre, n, ca) : 0;
   uint32_t words[WPT];
   long long w0;
   // 1. Counts.
   int over = 0;
-  for (int c = ca; c < cb; c++) {
-    const int b = find_owner(d->bmc_pre, n, c);
+  for (int c = ca, b = b_lo; c < cb; c++) {
+    while (c >= d->bmc_pre[b + 1]) b++;
     const int cnt = bm_chunk_words(d, d->img[b], c, d->bmc_pre[b], words, &w0);
     if (c - ca < kMaxCh) {
       const int ws = warp_sum_i(cnt);
@@ -320,8 +323,8 @@ __global__ void __launch_bounds__(kThreads) k_bm_compact(const Desc *__restrict_
   __syncthreads();
   {
     int acc = base;
-    for (int c = ca; c < cb; c++) {
-      const int b = find_owner(d->bmc_pre, n, c);
+    for (int c = ca, b = b_lo; c < cb; c++) {
+      while (c >= d->bmc_pre[b + 1]) b++;
       if (c == d->bmc_pre[b] && threadIdx.x == 0)
         lb_store(d->lb_start + b, lb_word(kLbInc, cfg.epoch, acc));
       int t = 0;
@@ -337,8 +340,8 @@ __global__ void __launch_bounds__(kThreads) k_bm_compact(const Desc *__restrict_
   // 3. Candidates.
   int carry = base;         // global offset of chunk c
   int cur = -1, start = 0;  // image of the previous chunk, global offset of its first slot
-  for (int c = ca; c < cb; c++) {
-    const int b = find_owner(d->bmc_pre, n, c);
+  for (int c = ca, b = b_lo; c < cb; c++) {
+    while (c >= d->bmc_pre[b + 1]) b++;
     const ImgDev &im = d->img[b];
     const int c0 = d->bmc_pre[b];
     const int cnt = bm_chunk_words(d, im, c, c0, words, &w0);
