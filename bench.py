@@ -411,18 +411,25 @@ def rooflines(acc, shapes, upsample, kpts, sm_mhz=None):
     return roofline, per_class
 
 
-def e2e_throughput(torch, pkg, ex, imgs_np, tuning, steps, warmup, world, ext_kw):
+E2E_LANES = 3
+
+
+def e2e_throughput(torch, pkg, ex, imgs_np, tuning, steps, warmup, world, ext_kw,
+                   n_lanes=E2E_LANES):
     """End to end: pinned host images -> device -> extract -> results back in one
-    packed copy. Two handles on two streams take alternate steps: step k + 1's
-    upload and launches are queued before step k's results are read back, so
-    the GPU does not wait for the host. Every step uploads its own inputs and
-    reads back its own results."""
+    packed copy. n_lanes handles on their own streams take the steps in turn:
+    steps k + 1 .. k + n_lanes - 1 are uploaded and queued before step k is read
+    back, so the GPU does not wait for the host and one batch's latency-bound
+    stretches (the small octaves, the keypoint chain) overlap another's work,
+    as in a serving pipeline. Every step uploads its own inputs and reads back
+    its own results."""
     host = [torch.from_numpy(np.ascontiguousarray(im)).pin_memory() for im in imgs_np]
     h2d = sum(h.numel() * 4 for h in host)
-    ex_b = pkg.Extractor(**ext_kw)
-    ex_b.set_tuning(tuning)
+    extra = [pkg.Extractor(**ext_kw) for _ in range(n_lanes - 1)]
+    for e in extra:
+        e.set_tuning(tuning)
     lanes = [(e, torch.cuda.Stream(), [torch.empty_like(h, device="cuda") for h in host])
-             for e in (ex, ex_b)]
+             for e in [ex] + extra]
 
     def submit(lane):
         e, st, din = lane
@@ -437,26 +444,29 @@ def e2e_throughput(torch, pkg, ex, imgs_np, tuning, steps, warmup, world, ext_kw
         return 4 * len(counts_h) + 540 * sum(counts_h)
 
     for it in range(warmup):
-        submit(lanes[it % 2])
-        collect(lanes[it % 2])
+        submit(lanes[it % n_lanes])
+        collect(lanes[it % n_lanes])
     torch.cuda.synchronize()
     d2h_bytes = []
     mpix = sum(im.size for im in imgs_np) / 1e6
     t0 = time.perf_counter()
-    submit(lanes[0])
+    for k in range(min(n_lanes - 1, steps)):
+        submit(lanes[k])
     for it in range(steps):
-        if it + 1 < steps:
-            submit(lanes[(it + 1) % 2])
-        d2h_bytes.append(collect(lanes[it % 2]))
+        if it + n_lanes - 1 < steps:
+            submit(lanes[(it + n_lanes - 1) % n_lanes])
+        d2h_bytes.append(collect(lanes[it % n_lanes]))
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
-    ex_b.close()
+    for e in extra:
+        e.close()
     return {"value": round(world * mpix * steps / t_e2e, 3), "unit": "Mpix/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(np.mean(d2h_bytes)),
-            "steps": steps,
-            "api": "Extractor.extract_batch_async (sift_extract_batch) from pinned host buffers, "
-                   "results by Extractor.download (sift_pack_outputs + one copy); two handles on "
-                   "two streams take alternate steps (step k+1 queued before step k is read back)"}
+            "steps": steps, "lanes": n_lanes,
+            "api": f"Extractor.extract_batch_async (sift_extract_batch) from pinned host buffers, "
+                   f"results by Extractor.download (sift_pack_outputs + one copy); {n_lanes} "
+                   f"handles on {n_lanes} streams take the steps in turn (steps k+1 .. "
+                   f"k+{n_lanes - 1} queued before step k is read back)"}
 
 
 def gpu_arm(args, rank, world, pool, batch):
