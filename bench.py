@@ -358,13 +358,15 @@ def _traffic_per_launch(px_step, blur_n):
 
 def _is_default_tuning(js):
     """Whether a tuning JSON is the defaults (32-row tiles, occupancy-maximum
-    grids): a tuned time then differs from the untuned one by noise only."""
+    grids, a batch split over two lanes): a tuned time then differs from the
+    untuned one by noise only."""
     t = json.loads(js)
     rows = t.get("blur_tile_rows", [])
     rows = rows if rows and isinstance(rows[0], list) else [rows]
     return (all(r == 32 for oc in rows for r in oc)
             and all(c == 0 for c in t.get("blur_ctas_per_sm", []))
-            and all(v == 0 for k, v in t.items() if k.endswith("_ctas_per_sm") and not isinstance(v, list)))
+            and all(v == 0 for k, v in t.items() if k.endswith("_ctas_per_sm") and not isinstance(v, list))
+            and t.get("batch_lanes", 2) == 2)
 
 
 def rooflines(acc, shapes, upsample, kpts, sm_mhz=None):
@@ -411,7 +413,7 @@ def rooflines(acc, shapes, upsample, kpts, sm_mhz=None):
     return roofline, per_class
 
 
-E2E_LANES = 3
+E2E_LANES = 4
 
 
 def e2e_throughput(torch, pkg, ex, imgs_np, tuning, steps, warmup, world, ext_kw,
@@ -422,12 +424,16 @@ def e2e_throughput(torch, pkg, ex, imgs_np, tuning, steps, warmup, world, ext_kw
     back, so the GPU does not wait for the host and one batch's latency-bound
     stretches (the small octaves, the keypoint chain) overlap another's work,
     as in a serving pipeline. Every step uploads its own inputs and reads back
-    its own results."""
+    its own results. The handles run their batches whole (batch_lanes 1): the
+    pipeline already overlaps batches, and a second lane per handle measured
+    slower with three handles and no faster with four."""
     host = [torch.from_numpy(np.ascontiguousarray(im)).pin_memory() for im in imgs_np]
     h2d = sum(h.numel() * 4 for h in host)
     extra = [pkg.Extractor(**ext_kw) for _ in range(n_lanes - 1)]
-    for e in extra:
+    for e in [ex] + extra:
         e.set_tuning(tuning)
+        e.set_tuning('{"batch_lanes": 1}')
+    warmup = max(warmup, n_lanes)  # every handle captures its graph before the timed steps
     lanes = [(e, torch.cuda.Stream(), [torch.empty_like(h, device="cuda") for h in host])
              for e in [ex] + extra]
 
@@ -460,9 +466,10 @@ def e2e_throughput(torch, pkg, ex, imgs_np, tuning, steps, warmup, world, ext_kw
     t_e2e = time.perf_counter() - t0
     for e in extra:
         e.close()
+    ex.set_tuning(tuning)
     return {"value": round(world * mpix * steps / t_e2e, 3), "unit": "Mpix/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(np.mean(d2h_bytes)),
-            "steps": steps, "lanes": n_lanes,
+            "steps": steps, "lanes": n_lanes, "batch_lanes": 1,
             "api": f"Extractor.extract_batch_async (sift_extract_batch) from pinned host buffers, "
                    f"results by Extractor.download (sift_pack_outputs + one copy); {n_lanes} "
                    f"handles on {n_lanes} streams take the steps in turn (steps k+1 .. "

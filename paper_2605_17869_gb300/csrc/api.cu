@@ -1,5 +1,6 @@
 // C ABI of the extractor (declared in include/sift_gb300.h) and the
 // continuous-batching server.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstdint>
@@ -29,6 +30,14 @@ struct sift_handle {
   size_t magsac_cap = 0;
   cudaStream_t magsac_stream = nullptr;
   std::string tuning_cache;  // tuning cache file ("" none)
+  // A batch run as two halves (tuning batch_lanes = 2): images [0, half_m) on
+  // eng and the caller's stream, [half_m, n) on eng2 and s2, forked from and
+  // joined back into the caller's stream by events. half_m = 0: the last
+  // extraction ran on eng alone.
+  Engine *eng2 = nullptr;
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int half_m = 0;
 };
 
 static sift_status fail(sift_handle *h, sift_status st, const std::string &m) {
@@ -43,6 +52,58 @@ static sift_status pass(sift_handle *h, sift_status st) {
 
 static bool kpts_ok(const sift_kpts_dev &k) {
   return k.x && k.y && k.sigma && k.angle && k.response && k.octave && k.layer;
+}
+
+// Run n <= kMaxImg images on stream s: on eng alone, or (batch_lanes = 2, two
+// or more images, not profiling) as two contiguous halves of about equal
+// pixel count on eng and eng2 at once. Every image's output is the same
+// either way (an image's results do not depend on the rest of its batch).
+static sift_status run_batch(sift_handle *h, int n, const ImgIn *in, cudaStream_t s) {
+  const sift::Tuning t = h->eng->tuning();
+  h->half_m = 0;
+  if (t.batch_lanes != 2 || n < 2 || n > sift::kMaxImg || h->eng->profiling())
+    return pass(h, h->eng->run(n, in, s));
+  long long tot = 0, acc = 0;
+  for (int i = 0; i < n; i++) tot += (long long)in[i].H * in[i].W;
+  int m = 1;
+  for (int i = 0; i < n - 1; i++) {
+    acc += (long long)in[i].H * in[i].W;
+    m = i + 1;
+    if (2 * acc >= tot) break;
+  }
+  if (!h->eng2) {
+    Engine *e = new Engine(h->eng->params());
+    const sift_status st = e->init();
+    cudaError_t ce = st == SIFT_OK ? cudaStreamCreateWithFlags(&h->s2, cudaStreamNonBlocking)
+                                   : cudaSuccess;
+    if (st == SIFT_OK && ce == cudaSuccess)
+      ce = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+    if (st == SIFT_OK && ce == cudaSuccess)
+      ce = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+    if (st != SIFT_OK || ce != cudaSuccess) {
+      h->err = st != SIFT_OK ? e->err : std::string("stream set-up failed: ") + cudaGetErrorString(ce);
+      delete e;
+      return st != SIFT_OK ? st : SIFT_E_CUDA;
+    }
+    h->eng2 = e;
+  }
+  const sift::Tuning t2 = h->eng2->tuning();
+  if (std::memcmp(&t, &t2, sizeof t) != 0) h->eng2->set_tuning(t);
+  cudaError_t ce = cudaEventRecord(h->ev_fork, s);
+  if (ce == cudaSuccess) ce = cudaStreamWaitEvent(h->s2, h->ev_fork, 0);
+  if (ce != cudaSuccess) return fail(h, SIFT_E_CUDA, std::string("fork: ") + cudaGetErrorString(ce));
+  sift_status st = h->eng->run(m, in, s);
+  if (st != SIFT_OK) return pass(h, st);
+  st = h->eng2->run(n - m, in + m, h->s2);
+  if (st != SIFT_OK) {
+    h->err = h->eng2->err;
+    return st;
+  }
+  ce = cudaEventRecord(h->ev_join, h->s2);
+  if (ce == cudaSuccess) ce = cudaStreamWaitEvent(s, h->ev_join, 0);
+  if (ce != cudaSuccess) return fail(h, SIFT_E_CUDA, std::string("join: ") + cudaGetErrorString(ce));
+  h->half_m = m;
+  return SIFT_OK;
 }
 
 extern "C" {
@@ -96,6 +157,11 @@ sift_status sift_destroy(sift_handle *h) {
     cudaStreamSynchronize(h->magsac_stream);
     cudaFree(h->magsac_ws);
   }
+  if (h->s2) cudaStreamSynchronize(h->s2);
+  delete h->eng2;
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->s2) cudaStreamDestroy(h->s2);
   delete h->eng;
   delete h;
   return SIFT_OK;
@@ -140,10 +206,14 @@ sift_status sift_pack_outputs(sift_handle *h, void *stream, void *dst_dev, size_
   if (h->split_batch)
     return fail(h, SIFT_E_INVALID, "the last batch had more than 128 images and ran as several launches");
   if (reinterpret_cast<uintptr_t>(dst_dev) & 15) return fail(h, SIFT_E_INVALID, "dst must be 16-byte aligned");
-  const size_t need = (size_t)h->eng->last_n * h->eng->params().max_kpts *
-                      (sift::kDescLen * sizeof(float) + 7 * 4);
+  const Engine *e2 = h->half_m > 0 ? h->eng2 : nullptr;  // the batch's second half
+  if (e2 && (!e2->last_extract || !e2->device_desc()))
+    return fail(h, SIFT_E_INVALID, "the last call on this handle was not an extraction");
+  const size_t n_img = (size_t)h->eng->last_n + (e2 ? e2->last_n : 0);
+  const size_t need = n_img * h->eng->params().max_kpts * (sift::kDescLen * sizeof(float) + 7 * 4);
   if (dst_bytes < need) return fail(h, SIFT_E_INVALID, "dst smaller than last_n * max_kpts * 540 bytes");
-  const cudaError_t e = sift::launch_pack(h->eng->device_desc(), dst_dev, h->eng->sm_count(),
+  const cudaError_t e = sift::launch_pack(h->eng->device_desc(), e2 ? e2->device_desc() : nullptr,
+                                          dst_dev, h->eng->sm_count(),
                                           static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return fail(h, SIFT_E_CUDA, std::string("pack: ") + cudaGetErrorString(e));
   return SIFT_OK;
@@ -200,6 +270,7 @@ sift_status sift_extract(sift_handle *h, const float *img_dev, int H, int W, int
   if (!h->eng->addressable(H, W)) return fail(h, SIFT_E_INVALID, "image too large");
   ImgIn in{img_dev, H, W, pitch_elems, out_kpts, out_desc_dev, out_count_dev};
   h->split_batch = false;
+  h->half_m = 0;
   return pass(h, h->eng->run(1, &in, (cudaStream_t)stream));
 }
 
@@ -224,6 +295,8 @@ sift_status sift_extract_batch(sift_handle *h, int n, const float *const *imgs_d
     in[i] = ImgIn{imgs_dev[i], H[i], W[i], p, out_kpts[i], out_desc[i], out_counts_dev + i};
   }
   h->split_batch = n > sift::kMaxImg;
+  if (!h->split_batch) return run_batch(h, n, in.data(), (cudaStream_t)stream);
+  h->half_m = 0;
   for (int b0 = 0; b0 < n; b0 += sift::kMaxImg) {
     const int m = std::min(sift::kMaxImg, n - b0);
     const sift_status st = h->eng->run(m, in.data() + b0, (cudaStream_t)stream);
@@ -236,6 +309,18 @@ sift_status sift_last_stats(sift_handle *h, int *stats, int max_images) {
   if (!h || !stats || max_images < 1) return SIFT_E_INVALID;
   if (h->split_batch)
     return fail(h, SIFT_E_INVALID, "the last batch had more than 128 images and ran as several launches");
+  if (h->half_m > 0) {  // the two halves, in batch order
+    const int m = h->half_m;
+    const sift_status a = h->eng->last_stats(stats, std::min(max_images, m));
+    if (a < 0) return pass(h, a);
+    if (max_images <= m) return a;
+    const sift_status b = h->eng2->last_stats(stats + 4 * m, max_images - m);
+    if (b < 0) {
+      h->err = h->eng2->err;
+      return b;
+    }
+    return (a == SIFT_W_TRUNCATED || b == SIFT_W_TRUNCATED) ? SIFT_W_TRUNCATED : SIFT_OK;
+  }
   return pass(h, h->eng->last_stats(stats, max_images));
 }
 
@@ -282,6 +367,7 @@ sift_status sift_build_pyramid(sift_handle *h, const float *img_dev, int H, int 
   ImgIn in{img_dev, H, W, pitch_elems, {}, nullptr, nullptr};
   cudaStream_t s = (cudaStream_t)stream;
   h->split_batch = false;
+  h->half_m = 0;
   st = h->eng->run_pyramid(in, s);
   if (st != SIFT_OK) return pass(h, st);
   const sift::Desc &hd = h->eng->host_desc();
@@ -316,7 +402,7 @@ sift_status sift_kernel_times(sift_handle *h, double *ms, int *launches, int n_c
 
 sift_status sift_last_launch_count(sift_handle *h, int *kernels) {
   if (!h || !kernels) return SIFT_E_INVALID;
-  *kernels = h->eng->last_launch_count();
+  *kernels = h->eng->last_launch_count() + (h->half_m > 0 ? h->eng2->last_launch_count() : 0);
   return SIFT_OK;
 }
 
@@ -390,12 +476,47 @@ sift_status sift_autotune_batch(sift_handle *h, int n, const float *const *imgs_
         return fail(h, SIFT_E_INVALID, "tuning cache entry: " + why);
       h->eng->set_tuning(t);
       if (from_cache) *from_cache = 1;
-      return pass(h, h->eng->run(n, in.data(), s));
+      return run_batch(h, n, in.data(), s);
     }
     if (st != SIFT_E_NOTFOUND) return fail(h, st, "tuning cache unreadable: " + h->tuning_cache);
   }
   st = h->eng->autotune_batch(n, in.data(), s);
   if (st != SIFT_OK) return pass(h, st);
+  h->half_m = 0;
+  // One lane or two (the batch as two halves at once) is decided here, at the
+  // handle, by timing whole steps through run_batch each way (best of three
+  // runs of five steps, after two untimed ones).
+  if (n >= 2) {
+    sift::Tuning t = h->eng->tuning();
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+      cudaGetLastError();
+      if (a) cudaEventDestroy(a);
+      return fail(h, SIFT_E_CUDA, "autotune event creation failed");
+    }
+    float best_ms[2] = {1e30f, 1e30f};
+    for (int lanes = 1; lanes <= 2 && st == SIFT_OK; lanes++) {
+      t.batch_lanes = lanes;
+      h->eng->set_tuning(t);
+      for (int w = 0; w < 2 && st == SIFT_OK; w++) st = run_batch(h, n, in.data(), s);
+      for (int r = 0; r < 3 && st == SIFT_OK; r++) {
+        cudaEventRecord(a, s);
+        for (int k = 0; k < 5 && st == SIFT_OK; k++) st = run_batch(h, n, in.data(), s);
+        cudaEventRecord(b, s);
+        float ms = 0.f;
+        if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess)
+          st = fail(h, SIFT_E_CUDA, "autotune timing failed");
+        best_ms[lanes - 1] = std::min(best_ms[lanes - 1], ms / 5.0f);
+      }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st != SIFT_OK) return st;
+    t.batch_lanes = best_ms[1] < best_ms[0] ? 2 : 1;
+    h->eng->set_tuning(t);
+    st = run_batch(h, n, in.data(), s);  // the outputs: a run with the chosen tuning
+    if (st != SIFT_OK) return st;
+  }
   if (!h->tuning_cache.empty()) {
     const std::string js = sift::tuning_json(h->eng->tuning(), h->eng->params().n_scales);
     st = sift::cache_put(h->tuning_cache.c_str(), sig.c_str(), js.c_str());

@@ -774,37 +774,48 @@ __global__ void __launch_bounds__(kKpWarps * 32, 6) k_descriptor(const Desc *__r
 // y, sigma, angle, response, octave, layer (N entries each), N = fin_flat[n],
 // images in batch order. One thread per float4 of descriptor, then one per
 // keypoint for the scalar fields.
-__global__ void __launch_bounds__(kThreads) k_pack(const Desc *__restrict__ d, float4 *__restrict__ dst) {
-  const int n = d->n_img;
-  const int N = d->fin_flat[n];
+__global__ void __launch_bounds__(kThreads) k_pack(const Desc *__restrict__ da,
+                                                   const Desc *__restrict__ db,
+                                                   float4 *__restrict__ dst) {
+  // da's images, then (db non-null: a batch that ran as two halves) db's.
+  const int na = da->n_img, NA = da->fin_flat[na];
+  const int nb = db ? db->n_img : 0, N = NA + (db ? db->fin_flat[nb] : 0);
+  auto locate = [&](int t, const ImgDev *&im, int &j) {
+    const Desc *d = t < NA ? da : db;
+    const int n = t < NA ? na : nb, u = t < NA ? t : t - NA;
+    const int b = find_owner(d->fin_flat, n, u);
+    im = &d->img[b];
+    j = u - d->fin_flat[b];
+  };
   const int stride = gridDim.x * blockDim.x;
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   for (int q = g; q < N * (kDescLen / 4); q += stride) {
     const int t = q / (kDescLen / 4), c = q - t * (kDescLen / 4);
-    const int b = find_owner(d->fin_flat, n, t);
-    const int j = t - d->fin_flat[b];
-    dst[q] = reinterpret_cast<const float4 *>(d->img[b].odesc + (long long)j * kDescLen)[c];
+    const ImgDev *im;
+    int j;
+    locate(t, im, j);
+    dst[q] = reinterpret_cast<const float4 *>(im->odesc + (long long)j * kDescLen)[c];
   }
   float *f = reinterpret_cast<float *>(dst + (long long)N * (kDescLen / 4));
   int *oi = reinterpret_cast<int *>(f + 5LL * N);
   for (int t = g; t < N; t += stride) {
-    const int b = find_owner(d->fin_flat, n, t);
-    const ImgDev &im = d->img[b];
-    const int j = t - d->fin_flat[b];
-    f[t] = im.ox[j];
-    f[N + t] = im.oy[j];
-    f[2LL * N + t] = im.osig[j];
-    f[3LL * N + t] = im.oang[j];
-    f[4LL * N + t] = im.oresp[j];
-    oi[t] = im.ooct[j];
-    oi[N + t] = im.olay[j];
+    const ImgDev *im;
+    int j;
+    locate(t, im, j);
+    f[t] = im->ox[j];
+    f[N + t] = im->oy[j];
+    f[2LL * N + t] = im->osig[j];
+    f[3LL * N + t] = im->oang[j];
+    f[4LL * N + t] = im->oresp[j];
+    oi[t] = im->ooct[j];
+    oi[N + t] = im->olay[j];
   }
 }
 
 }  // namespace
 
-cudaError_t launch_pack(const Desc *d, void *dst, int n_sm, cudaStream_t s) {
-  return launch_plain(k_pack, n_sm * 4, kThreads, 0, s, d, static_cast<float4 *>(dst));
+cudaError_t launch_pack(const Desc *da, const Desc *db, void *dst, int n_sm, cudaStream_t s) {
+  return launch_plain(k_pack, n_sm * 4, kThreads, 0, s, da, db, static_cast<float4 *>(dst));
 }
 
 cudaError_t launch_orientation(const Desc *d, int grid, cudaStream_t s, bool mixed) {

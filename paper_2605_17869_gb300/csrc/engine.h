@@ -38,6 +38,11 @@ struct Tuning {
   int blur_ctas[kMaxOct];
   int ext_ctas, ori_ctas, desc_ctas;
   int cmp_ctas;  // the two single-pass keypoint compactions
+  // sift_extract_batch: 2 runs a batch of two or more images as two
+  // contiguous halves (balanced by pixels) on two engines and streams at once,
+  // so that one half's latency-bound stretches overlap the other's work; 1
+  // runs it on one engine. Outputs are the same either way.
+  int batch_lanes;
 };
 
 // Poll limit of a single-pass scan wait and the test hook's held block
@@ -95,6 +100,7 @@ class Engine {
   char *workspace() const { return ws_; }
 
   void set_profiling(bool on);
+  bool profiling() const { return profiling_; }
   sift_status kernel_times(double *ms, int *launches, int n_classes);
   sift_status last_stats(int *stats, int max_images);
   int last_launch_count() const { return last_kernels_; }

@@ -7,7 +7,7 @@
 //                                                    flat list: octave 0)
 //    "blur_ctas_per_sm": [c_0, c_1, ...],            per octave
 //    "extrema_ctas_per_sm": c, "orientation_ctas_per_sm": c,
-//    "descriptor_ctas_per_sm": c, "compaction_ctas_per_sm": c}
+//    "descriptor_ctas_per_sm": c, "compaction_ctas_per_sm": c, "batch_lanes": 1 | 2}
 // r is 32 or 64; c is 0 (the occupancy maximum) or 1..64 (capped by the
 // occupancy maximum at launch).
 //
@@ -129,6 +129,7 @@ Tuning default_tuning() {
     t.blur_ctas[o] = 0;
   }
   t.ext_ctas = t.ori_ctas = t.desc_ctas = t.cmp_ctas = 0;
+  t.batch_lanes = 2;
   return t;
 }
 
@@ -158,7 +159,8 @@ std::string tuning_json(const Tuning &t, int S) {
   s += "], \"extrema_ctas_per_sm\": " + std::to_string(t.ext_ctas) +
        ", \"orientation_ctas_per_sm\": " + std::to_string(t.ori_ctas) +
        ", \"descriptor_ctas_per_sm\": " + std::to_string(t.desc_ctas) +
-       ", \"compaction_ctas_per_sm\": " + std::to_string(t.cmp_ctas) + "}";
+       ", \"compaction_ctas_per_sm\": " + std::to_string(t.cmp_ctas) +
+       ", \"batch_lanes\": " + std::to_string(t.batch_lanes) + "}";
   return s;
 }
 
@@ -221,6 +223,10 @@ bool parse_tuning(const char *json, int S, const Tuning &base, Tuning *out, std:
          : key[0] == 'o' ? t.ori_ctas
          : key[0] == 'd' ? t.desc_ctas
                          : t.cmp_ctas) = (int)v;
+      } else if (key == "batch_lanes") {
+        long v;
+        if (!c.integer(&v) || (v != 1 && v != 2)) return bad("tuning: batch_lanes must be 1 or 2");
+        t.batch_lanes = (int)v;
       } else {
         return bad("tuning: unknown key \"" + key + "\"");
       }

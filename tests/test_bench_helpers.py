@@ -110,3 +110,5 @@ def test_default_tuning_is_recognised():
     assert not bench._is_default_tuning(d.replace("[[32, 32, 32, 32, 32]]",
                                                   "[[32, 32, 32, 32, 32], [32, 64, 32, 32, 32]]"))
     assert not bench._is_default_tuning(d.replace('"blur_ctas_per_sm": [0]', '"blur_ctas_per_sm": [0, 3]'))
+    assert bench._is_default_tuning(d[:-1] + ', "batch_lanes": 2}')
+    assert not bench._is_default_tuning(d[:-1] + ', "batch_lanes": 1}')

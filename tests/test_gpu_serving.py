@@ -6,6 +6,7 @@ changes an image's arithmetic. Autotuned tile shapes change only the work
 distribution, so tuned and default runs must also agree bit for bit."""
 import time
 
+import numpy as np
 import pytest
 
 from workloads import synth
@@ -138,7 +139,7 @@ def test_tuning_json_round_trip_and_validation():
     js = ('{"blur_tile_rows": [[64, 32, 64, 32, 32], [32, 64, 32, 32, 32]], '
           '"blur_ctas_per_sm": [2, 3], "extrema_ctas_per_sm": 3, '
           '"orientation_ctas_per_sm": 5, "descriptor_ctas_per_sm": 4, '
-          '"compaction_ctas_per_sm": 2}')
+          '"compaction_ctas_per_sm": 2, "batch_lanes": 1}')
     ex.set_tuning(js)
     assert ex.get_tuning() == js
     ex.set_tuning('{"blur_tile_rows": [32, 32, 32, 32, 64]}')  # flat list: octave 0 only
@@ -146,7 +147,8 @@ def test_tuning_json_round_trip_and_validation():
                                       '[32, 64, 32, 32, 32]]')
     for bad in ('{"blur_tile_rows": [48, 32, 32, 32, 32]}', '{"blur_tile_rows": [32, 32]}',
                 '{"extrema_ctas_per_sm": 65}', '{"extrema_ctas_per_sm": -1}', '{"grid": 1}',
-                '{"descriptor_ctas_per_sm": 2.5}', '[]', '{"blur_ctas_per_sm": [1] } x'):
+                '{"descriptor_ctas_per_sm": 2.5}', '[]', '{"blur_ctas_per_sm": [1] } x',
+                '{"batch_lanes": 3}', '{"batch_lanes": 0}'):
         with pytest.raises(pkg.SiftError):
             ex.set_tuning(bad)
     ex.close()
@@ -178,10 +180,45 @@ def test_batch_autotune_bit_identical_and_cached(tmp_path):
     for t in ('{"blur_tile_rows": [[64, 64, 64, 64, 64], [64, 64, 64, 64, 64], '
               '[64, 64, 64, 64, 64]], "blur_ctas_per_sm": [1, 1, 1], "extrema_ctas_per_sm": 1, '
               '"orientation_ctas_per_sm": 1, "descriptor_ctas_per_sm": 1, '
-              '"compaction_ctas_per_sm": 1}',
+              '"compaction_ctas_per_sm": 1, "batch_lanes": 1}',
               '{"blur_ctas_per_sm": [2, 3, 2, 1], "extrema_ctas_per_sm": 2, '
               '"orientation_ctas_per_sm": 4, "descriptor_ctas_per_sm": 3, '
-              '"compaction_ctas_per_sm": 3}'):
+              '"compaction_ctas_per_sm": 3, "batch_lanes": 2}',
+              '{"batch_lanes": 1}'):
         ex3.set_tuning(t)
         assert all(_same(a, b) for a, b in zip(ref, ex3.extract_batch(imgs)))
     ex3.close()
+
+
+def test_batch_lanes_bit_identical_with_pack_and_stats():
+    """Two concurrent halves (batch_lanes 2) against the whole batch in one pass:
+    the same features, the same packed download, the same per-image stats; the
+    caller's stream sees both halves without a device-wide synchronisation."""
+    shapes = [(1200, 1600), (97, 211), (480, 640), (720, 1280), (300, 411)]
+    imgs = [torch.from_numpy(synth.make_image(synth.rng_for(77, i), *s, fractal_std=0.05)).cuda()
+            for i, s in enumerate(shapes)]
+    one, two = pkg.Extractor(), pkg.Extractor()
+    one.set_tuning('{"batch_lanes": 1}')
+    assert '"batch_lanes": 2' in two.get_tuning()
+    side = torch.cuda.Stream()
+    for batch in (imgs, imgs[:2], imgs[1:3], imgs[:1], imgs[::-1]):
+        fa = one.extract_batch(batch)
+        with torch.cuda.stream(side):
+            bufs, cnt = two.extract_batch_async(batch, side)
+            counts = cnt.clone()
+        side.synchronize()  # only the caller's stream: it must have joined the second half
+        fb = [b.view(c) for b, c in zip(bufs, counts.tolist())]
+        assert len(fa) == len(fb)
+        assert all(_same(a, b) for a, b in zip(fa, fb))
+        ca, pa = one.download()
+        cb, pb = two.download(side)
+        assert ca == cb == [f.count for f in fa]
+        for a, b in zip(pa, pb):
+            for k in a:
+                assert np.array_equal(a[k], b[k]), k
+        sa, ra = one.stats(len(batch))
+        sb, rb = two.stats(len(batch))
+        assert sa == sb and ra == rb
+        assert two.launch_count() >= one.launch_count()
+    one.close()
+    two.close()
