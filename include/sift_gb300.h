@@ -152,12 +152,12 @@ sift_status sift_extract(sift_handle *h, const float *img_dev, int H, int W, int
  *   out_counts_dev                           device int[n]
  * A batch of more than 128 images runs as consecutive launches of at most 128
  * (outputs unchanged); sift_pack_outputs and sift_last_stats then refuse.
- * With the tuning's batch_lanes at 2 (the default), a batch of 2 to 128
- * images is cut into two contiguous halves of about equal pixel counts that
- * run concurrently: the first on `stream`, the second on a stream of the
- * handle that waits for `stream` at the call and that `stream` waits for
- * before returning, so work queued on `stream` afterwards sees both halves.
- * Each half has its own graph and scratch buffers; outputs are unchanged.
+ * With the tuning's batch_lanes at k > 1 (default 2), a batch of 2 to 128
+ * images is cut into min(k, n) contiguous parts of about equal pixel counts
+ * that run concurrently: the first on `stream`, each other one on a stream of
+ * the handle that waits for `stream` at the call and that `stream` waits for
+ * before returning, so work queued on `stream` afterwards sees every part.
+ * Each part has its own graph and scratch buffers; outputs are unchanged.
  * Errors as sift_extract. */
 sift_status sift_extract_batch(sift_handle *h, int n, const float *const *imgs_dev,
                                const int *H, const int *W, const int *pitch_elems, void *stream,
@@ -321,9 +321,10 @@ sift_status sift_last_launch_count(sift_handle *h, int *kernels);
  *    "blur_ctas_per_sm": [c_0, c_1, ...],           level blurs, per octave
  *    "extrema_ctas_per_sm": c, "orientation_ctas_per_sm": c,
  *    "descriptor_ctas_per_sm": c, "compaction_ctas_per_sm": c,
- *    "batch_lanes": 1 or 2}                         sift_extract_batch: whole
- *                                                   batch in one pass, or two
- *                                                   concurrent halves (default)
+ *    "batch_lanes": k}                              sift_extract_batch: whole
+ *                                                   batch in one pass (1), or
+ *                                                   up to k concurrent parts
+ *                                                   (2, the default, to 4)
  * with c the resident CTAs per SM of that persistent grid, 0 (the default)
  * meaning the kernel's occupancy maximum and larger values capped by it.
  * sift_set_tuning changes only the keys given (SIFT_E_INVALID on a malformed
@@ -341,9 +342,9 @@ sift_status sift_set_tuning(sift_handle *h, const char *json);
  * from the cache. Coordinate descent over whole extraction steps of this
  * batch on `stream`, from the defaults: 64-row tiles per level of the three
  * largest octaves, then fewer resident CTAs per SM for their level blurs and
- * for the extrema, orientation, descriptor and compaction grids, then one
- * lane against two (batch_lanes); a change is kept only if the step gets at
- * least 1% faster, and the result is re-timed against the defaults at the end. The chosen tuning stays on the handle, and on return
+ * for the extrema, orientation, descriptor and compaction grids, then 1 to 4
+ * lanes (batch_lanes); a change is kept only if the step gets at least 1%
+ * faster, and the result is re-timed against the defaults at the end. The chosen tuning stays on the handle, and on return
  * the output buffers hold this batch's results (a run with that tuning;
  * identical to sift_extract_batch's). Synchronises `stream` while timing.
  * With a tuning cache set (sift_set_tuning_cache), the batch's signature

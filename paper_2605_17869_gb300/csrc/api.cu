@@ -30,14 +30,18 @@ struct sift_handle {
   size_t magsac_cap = 0;
   cudaStream_t magsac_stream = nullptr;
   std::string tuning_cache;  // tuning cache file ("" none)
-  // A batch run as two halves (tuning batch_lanes = 2): images [0, half_m) on
-  // eng and the caller's stream, [half_m, n) on eng2 and s2, forked from and
-  // joined back into the caller's stream by events. half_m = 0: the last
-  // extraction ran on eng alone.
-  Engine *eng2 = nullptr;
-  cudaStream_t s2 = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  int half_m = 0;
+  // A batch run as several parts (tuning batch_lanes > 1): part k holds images
+  // [part_start[k], part_start[k + 1]) and runs on part_eng(k) and stream
+  // lane_s[k] (part 0: eng and the caller's stream), the other streams forked
+  // from and joined back into the caller's stream by events. n_parts = 0: the
+  // last extraction ran on eng alone.
+  Engine *lane_eng[sift::kMaxLanes] = {};  // [0] unused
+  cudaStream_t lane_s[sift::kMaxLanes] = {};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[sift::kMaxLanes] = {};
+  int n_parts = 0;
+  int part_start[sift::kMaxLanes + 1] = {};
+  Engine *part_eng(int k) const { return k == 0 ? eng : lane_eng[k]; }
 };
 
 static sift_status fail(sift_handle *h, sift_status st, const std::string &m) {
@@ -54,55 +58,76 @@ static bool kpts_ok(const sift_kpts_dev &k) {
   return k.x && k.y && k.sigma && k.angle && k.response && k.octave && k.layer;
 }
 
-// Run n <= kMaxImg images on stream s: on eng alone, or (batch_lanes = 2, two
-// or more images, not profiling) as two contiguous halves of about equal
-// pixel count on eng and eng2 at once. Every image's output is the same
-// either way (an image's results do not depend on the rest of its batch).
-static sift_status run_batch(sift_handle *h, int n, const ImgIn *in, cudaStream_t s) {
-  const sift::Tuning t = h->eng->tuning();
-  h->half_m = 0;
-  if (t.batch_lanes != 2 || n < 2 || n > sift::kMaxImg || h->eng->profiling())
-    return pass(h, h->eng->run(n, in, s));
-  long long tot = 0, acc = 0;
-  for (int i = 0; i < n; i++) tot += (long long)in[i].H * in[i].W;
-  int m = 1;
-  for (int i = 0; i < n - 1; i++) {
-    acc += (long long)in[i].H * in[i].W;
-    m = i + 1;
-    if (2 * acc >= tot) break;
-  }
-  if (!h->eng2) {
-    Engine *e = new Engine(h->eng->params());
-    const sift_status st = e->init();
-    cudaError_t ce = st == SIFT_OK ? cudaStreamCreateWithFlags(&h->s2, cudaStreamNonBlocking)
-                                   : cudaSuccess;
-    if (st == SIFT_OK && ce == cudaSuccess)
-      ce = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
-    if (st == SIFT_OK && ce == cudaSuccess)
-      ce = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
-    if (st != SIFT_OK || ce != cudaSuccess) {
-      h->err = st != SIFT_OK ? e->err : std::string("stream set-up failed: ") + cudaGetErrorString(ce);
-      delete e;
-      return st != SIFT_OK ? st : SIFT_E_CUDA;
-    }
-    h->eng2 = e;
-  }
-  const sift::Tuning t2 = h->eng2->tuning();
-  if (std::memcmp(&t, &t2, sizeof t) != 0) h->eng2->set_tuning(t);
-  cudaError_t ce = cudaEventRecord(h->ev_fork, s);
-  if (ce == cudaSuccess) ce = cudaStreamWaitEvent(h->s2, h->ev_fork, 0);
-  if (ce != cudaSuccess) return fail(h, SIFT_E_CUDA, std::string("fork: ") + cudaGetErrorString(ce));
-  sift_status st = h->eng->run(m, in, s);
-  if (st != SIFT_OK) return pass(h, st);
-  st = h->eng2->run(n - m, in + m, h->s2);
+// Set up lane k >= 1 (its engine, stream and join event) on first use.
+static sift_status ensure_lane(sift_handle *h, int k) {
+  if (h->lane_eng[k]) return SIFT_OK;
+  cudaError_t ce = cudaSuccess;
+  if (!h->ev_fork) ce = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+  if (ce == cudaSuccess && !h->lane_s[k])
+    ce = cudaStreamCreateWithFlags(&h->lane_s[k], cudaStreamNonBlocking);
+  if (ce == cudaSuccess && !h->ev_join[k])
+    ce = cudaEventCreateWithFlags(&h->ev_join[k], cudaEventDisableTiming);
+  if (ce != cudaSuccess) return fail(h, SIFT_E_CUDA, std::string("lane set-up failed: ") + cudaGetErrorString(ce));
+  Engine *e = new Engine(h->eng->params());
+  const sift_status st = e->init();
   if (st != SIFT_OK) {
-    h->err = h->eng2->err;
+    h->err = e->err;
+    delete e;
     return st;
   }
-  ce = cudaEventRecord(h->ev_join, h->s2);
-  if (ce == cudaSuccess) ce = cudaStreamWaitEvent(s, h->ev_join, 0);
+  h->lane_eng[k] = e;
+  return SIFT_OK;
+}
+
+// Run n <= kMaxImg images on stream s: on eng alone, or (batch_lanes = k > 1,
+// two or more images, not profiling) as min(k, n) contiguous parts of about
+// equal pixel count on as many engines at once. Every image's output is the
+// same either way (an image's results do not depend on the rest of its batch).
+static sift_status run_batch(sift_handle *h, int n, const ImgIn *in, cudaStream_t s) {
+  const sift::Tuning t = h->eng->tuning();
+  h->n_parts = 0;
+  const int K = std::min(t.batch_lanes, n);
+  if (K < 2 || n > sift::kMaxImg || h->eng->profiling()) return pass(h, h->eng->run(n, in, s));
+  // Part k ends at the first image whose prefix reaches (k + 1) / K of the
+  // pixels, leaving at least one image for each later part.
+  long long tot = 0;
+  for (int i = 0; i < n; i++) tot += (long long)in[i].H * in[i].W;
+  int start[sift::kMaxLanes + 1];
+  start[0] = 0;
+  long long acc = 0;
+  int i = 0;
+  for (int k = 0; k + 1 < K; k++) {
+    do {
+      acc += (long long)in[i].H * in[i].W;
+      i++;
+    } while (i < n - (K - 1 - k) && acc * K < (k + 1) * tot);
+    start[k + 1] = i;
+  }
+  start[K] = n;
+  for (int k = 1; k < K; k++) {
+    const sift_status st = ensure_lane(h, k);
+    if (st != SIFT_OK) return st;
+    const sift::Tuning tk = h->lane_eng[k]->tuning();
+    if (std::memcmp(&t, &tk, sizeof t) != 0) h->lane_eng[k]->set_tuning(t);
+  }
+  cudaError_t ce = cudaEventRecord(h->ev_fork, s);
+  for (int k = 1; k < K && ce == cudaSuccess; k++) ce = cudaStreamWaitEvent(h->lane_s[k], h->ev_fork, 0);
+  if (ce != cudaSuccess) return fail(h, SIFT_E_CUDA, std::string("fork: ") + cudaGetErrorString(ce));
+  for (int k = 0; k < K; k++) {
+    Engine *e = h->part_eng(k);
+    const sift_status st = e->run(start[k + 1] - start[k], in + start[k], k ? h->lane_s[k] : s);
+    if (st != SIFT_OK) {
+      h->err = e->err;
+      return st;
+    }
+  }
+  for (int k = 1; k < K && ce == cudaSuccess; k++) {
+    ce = cudaEventRecord(h->ev_join[k], h->lane_s[k]);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(s, h->ev_join[k], 0);
+  }
   if (ce != cudaSuccess) return fail(h, SIFT_E_CUDA, std::string("join: ") + cudaGetErrorString(ce));
-  h->half_m = m;
+  h->n_parts = K;
+  std::memcpy(h->part_start, start, sizeof(int) * (K + 1));
   return SIFT_OK;
 }
 
@@ -157,11 +182,13 @@ sift_status sift_destroy(sift_handle *h) {
     cudaStreamSynchronize(h->magsac_stream);
     cudaFree(h->magsac_ws);
   }
-  if (h->s2) cudaStreamSynchronize(h->s2);
-  delete h->eng2;
+  for (int k = 1; k < sift::kMaxLanes; k++) {
+    if (h->lane_s[k]) cudaStreamSynchronize(h->lane_s[k]);
+    delete h->lane_eng[k];
+    if (h->ev_join[k]) cudaEventDestroy(h->ev_join[k]);
+    if (h->lane_s[k]) cudaStreamDestroy(h->lane_s[k]);
+  }
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
-  if (h->ev_join) cudaEventDestroy(h->ev_join);
-  if (h->s2) cudaStreamDestroy(h->s2);
   delete h->eng;
   delete h;
   return SIFT_OK;
@@ -206,14 +233,19 @@ sift_status sift_pack_outputs(sift_handle *h, void *stream, void *dst_dev, size_
   if (h->split_batch)
     return fail(h, SIFT_E_INVALID, "the last batch had more than 128 images and ran as several launches");
   if (reinterpret_cast<uintptr_t>(dst_dev) & 15) return fail(h, SIFT_E_INVALID, "dst must be 16-byte aligned");
-  const Engine *e2 = h->half_m > 0 ? h->eng2 : nullptr;  // the batch's second half
-  if (e2 && (!e2->last_extract || !e2->device_desc()))
-    return fail(h, SIFT_E_INVALID, "the last call on this handle was not an extraction");
-  const size_t n_img = (size_t)h->eng->last_n + (e2 ? e2->last_n : 0);
+  sift::PackSrc src{};  // the batch's parts in batch order (one: it ran on eng alone)
+  src.n = std::max(1, h->n_parts);
+  size_t n_img = 0;
+  for (int k = 0; k < src.n; k++) {
+    const Engine *e = h->part_eng(k);
+    if (!e->last_extract || !e->device_desc())
+      return fail(h, SIFT_E_INVALID, "the last call on this handle was not an extraction");
+    src.d[k] = e->device_desc();
+    n_img += (size_t)e->last_n;
+  }
   const size_t need = n_img * h->eng->params().max_kpts * (sift::kDescLen * sizeof(float) + 7 * 4);
   if (dst_bytes < need) return fail(h, SIFT_E_INVALID, "dst smaller than last_n * max_kpts * 540 bytes");
-  const cudaError_t e = sift::launch_pack(h->eng->device_desc(), e2 ? e2->device_desc() : nullptr,
-                                          dst_dev, h->eng->sm_count(),
+  const cudaError_t e = sift::launch_pack(src, dst_dev, h->eng->sm_count(),
                                           static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return fail(h, SIFT_E_CUDA, std::string("pack: ") + cudaGetErrorString(e));
   return SIFT_OK;
@@ -270,7 +302,7 @@ sift_status sift_extract(sift_handle *h, const float *img_dev, int H, int W, int
   if (!h->eng->addressable(H, W)) return fail(h, SIFT_E_INVALID, "image too large");
   ImgIn in{img_dev, H, W, pitch_elems, out_kpts, out_desc_dev, out_count_dev};
   h->split_batch = false;
-  h->half_m = 0;
+  h->n_parts = 0;
   return pass(h, h->eng->run(1, &in, (cudaStream_t)stream));
 }
 
@@ -296,7 +328,7 @@ sift_status sift_extract_batch(sift_handle *h, int n, const float *const *imgs_d
   }
   h->split_batch = n > sift::kMaxImg;
   if (!h->split_batch) return run_batch(h, n, in.data(), (cudaStream_t)stream);
-  h->half_m = 0;
+  h->n_parts = 0;
   for (int b0 = 0; b0 < n; b0 += sift::kMaxImg) {
     const int m = std::min(sift::kMaxImg, n - b0);
     const sift_status st = h->eng->run(m, in.data() + b0, (cudaStream_t)stream);
@@ -309,17 +341,19 @@ sift_status sift_last_stats(sift_handle *h, int *stats, int max_images) {
   if (!h || !stats || max_images < 1) return SIFT_E_INVALID;
   if (h->split_batch)
     return fail(h, SIFT_E_INVALID, "the last batch had more than 128 images and ran as several launches");
-  if (h->half_m > 0) {  // the two halves, in batch order
-    const int m = h->half_m;
-    const sift_status a = h->eng->last_stats(stats, std::min(max_images, m));
-    if (a < 0) return pass(h, a);
-    if (max_images <= m) return a;
-    const sift_status b = h->eng2->last_stats(stats + 4 * m, max_images - m);
-    if (b < 0) {
-      h->err = h->eng2->err;
-      return b;
+  if (h->n_parts > 0) {  // the parts, in batch order
+    bool trunc = false;
+    for (int k = 0; k < h->n_parts && h->part_start[k] < max_images; k++) {
+      Engine *e = h->part_eng(k);
+      const int b0 = h->part_start[k];
+      const sift_status st = e->last_stats(stats + 4 * b0, std::min(max_images, h->part_start[k + 1]) - b0);
+      if (st < 0) {
+        h->err = e->err;
+        return st;
+      }
+      trunc = trunc || st == SIFT_W_TRUNCATED;
     }
-    return (a == SIFT_W_TRUNCATED || b == SIFT_W_TRUNCATED) ? SIFT_W_TRUNCATED : SIFT_OK;
+    return trunc ? SIFT_W_TRUNCATED : SIFT_OK;
   }
   return pass(h, h->eng->last_stats(stats, max_images));
 }
@@ -367,7 +401,7 @@ sift_status sift_build_pyramid(sift_handle *h, const float *img_dev, int H, int 
   ImgIn in{img_dev, H, W, pitch_elems, {}, nullptr, nullptr};
   cudaStream_t s = (cudaStream_t)stream;
   h->split_batch = false;
-  h->half_m = 0;
+  h->n_parts = 0;
   st = h->eng->run_pyramid(in, s);
   if (st != SIFT_OK) return pass(h, st);
   const sift::Desc &hd = h->eng->host_desc();
@@ -402,7 +436,8 @@ sift_status sift_kernel_times(sift_handle *h, double *ms, int *launches, int n_c
 
 sift_status sift_last_launch_count(sift_handle *h, int *kernels) {
   if (!h || !kernels) return SIFT_E_INVALID;
-  *kernels = h->eng->last_launch_count() + (h->half_m > 0 ? h->eng2->last_launch_count() : 0);
+  *kernels = 0;
+  for (int k = 0; k < std::max(1, h->n_parts); k++) *kernels += h->part_eng(k)->last_launch_count();
   return SIFT_OK;
 }
 
@@ -482,10 +517,11 @@ sift_status sift_autotune_batch(sift_handle *h, int n, const float *const *imgs_
   }
   st = h->eng->autotune_batch(n, in.data(), s);
   if (st != SIFT_OK) return pass(h, st);
-  h->half_m = 0;
-  // One lane or two (the batch as two halves at once) is decided here, at the
-  // handle, by timing whole steps through run_batch each way (best of three
-  // runs of five steps, after two untimed ones).
+  h->n_parts = 0;
+  // The number of lanes (the batch as 1 to 4 parts at once) is decided here,
+  // at the handle, by timing whole steps through run_batch each way (best of
+  // three runs of five steps, after two untimed ones); more lanes are kept
+  // only when at least 1% faster.
   if (n >= 2) {
     sift::Tuning t = h->eng->tuning();
     cudaEvent_t a = nullptr, b = nullptr;
@@ -494,8 +530,9 @@ sift_status sift_autotune_batch(sift_handle *h, int n, const float *const *imgs_
       if (a) cudaEventDestroy(a);
       return fail(h, SIFT_E_CUDA, "autotune event creation failed");
     }
-    float best_ms[2] = {1e30f, 1e30f};
-    for (int lanes = 1; lanes <= 2 && st == SIFT_OK; lanes++) {
+    const int max_lanes = std::min(sift::kMaxLanes, n);
+    float best_ms[sift::kMaxLanes] = {1e30f, 1e30f, 1e30f, 1e30f};
+    for (int lanes = 1; lanes <= max_lanes && st == SIFT_OK; lanes++) {
       t.batch_lanes = lanes;
       h->eng->set_tuning(t);
       for (int w = 0; w < 2 && st == SIFT_OK; w++) st = run_batch(h, n, in.data(), s);
@@ -512,7 +549,10 @@ sift_status sift_autotune_batch(sift_handle *h, int n, const float *const *imgs_
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (st != SIFT_OK) return st;
-    t.batch_lanes = best_ms[1] < best_ms[0] ? 2 : 1;
+    int best = 1;
+    for (int lanes = 2; lanes <= max_lanes; lanes++)
+      if (best_ms[lanes - 1] < 0.99f * best_ms[best - 1]) best = lanes;
+    t.batch_lanes = best;
     h->eng->set_tuning(t);
     st = run_batch(h, n, in.data(), s);  // the outputs: a run with the chosen tuning
     if (st != SIFT_OK) return st;

@@ -774,16 +774,19 @@ __global__ void __launch_bounds__(kKpWarps * 32, 6) k_descriptor(const Desc *__r
 // y, sigma, angle, response, octave, layer (N entries each), N = fin_flat[n],
 // images in batch order. One thread per float4 of descriptor, then one per
 // keypoint for the scalar fields.
-__global__ void __launch_bounds__(kThreads) k_pack(const Desc *__restrict__ da,
-                                                   const Desc *__restrict__ db,
-                                                   float4 *__restrict__ dst) {
-  // da's images, then (db non-null: a batch that ran as two halves) db's.
-  const int na = da->n_img, NA = da->fin_flat[na];
-  const int nb = db ? db->n_img : 0, N = NA + (db ? db->fin_flat[nb] : 0);
+__global__ void __launch_bounds__(kThreads) k_pack(PackSrc src, float4 *__restrict__ dst) {
+  // The parts' images in batch order: part p's keypoints start at first[p].
+  int first[5];
+  first[0] = 0;
+  for (int p = 0; p < 4; p++)
+    first[p + 1] = first[p] + (p < src.n ? src.d[p]->fin_flat[src.d[p]->n_img] : 0);
+  const int N = first[4];
   auto locate = [&](int t, const ImgDev *&im, int &j) {
-    const Desc *d = t < NA ? da : db;
-    const int n = t < NA ? na : nb, u = t < NA ? t : t - NA;
-    const int b = find_owner(d->fin_flat, n, u);
+    int p = 0;
+    while (p + 1 < src.n && t >= first[p + 1]) p++;
+    const Desc *d = src.d[p];
+    const int u = t - first[p];
+    const int b = find_owner(d->fin_flat, d->n_img, u);
     im = &d->img[b];
     j = u - d->fin_flat[b];
   };
@@ -814,8 +817,8 @@ __global__ void __launch_bounds__(kThreads) k_pack(const Desc *__restrict__ da,
 
 }  // namespace
 
-cudaError_t launch_pack(const Desc *da, const Desc *db, void *dst, int n_sm, cudaStream_t s) {
-  return launch_plain(k_pack, n_sm * 4, kThreads, 0, s, da, db, static_cast<float4 *>(dst));
+cudaError_t launch_pack(PackSrc src, void *dst, int n_sm, cudaStream_t s) {
+  return launch_plain(k_pack, n_sm * 4, kThreads, 0, s, src, static_cast<float4 *>(dst));
 }
 
 cudaError_t launch_orientation(const Desc *d, int grid, cudaStream_t s, bool mixed) {

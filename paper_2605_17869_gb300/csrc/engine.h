@@ -38,12 +38,13 @@ struct Tuning {
   int blur_ctas[kMaxOct];
   int ext_ctas, ori_ctas, desc_ctas;
   int cmp_ctas;  // the two single-pass keypoint compactions
-  // sift_extract_batch: 2 runs a batch of two or more images as two
-  // contiguous halves (balanced by pixels) on two engines and streams at once,
-  // so that one half's latency-bound stretches overlap the other's work; 1
-  // runs it on one engine. Outputs are the same either way.
+  // sift_extract_batch: k > 1 runs a batch of two or more images as up to k
+  // contiguous parts (balanced by pixels) on as many engines and streams at
+  // once, so that one part's latency-bound stretches overlap the others'
+  // work; 1 runs it on one engine. Outputs are the same either way.
   int batch_lanes;
 };
+constexpr int kMaxLanes = 4;  // largest batch_lanes
 
 // Poll limit of a single-pass scan wait and the test hook's held block
 // (environment SIFT_TEST_LOOKBACK_SPINS / SIFT_TEST_LOOKBACK_HOLD).

@@ -242,7 +242,12 @@ cudaError_t launch_select(const Desc *d, int grid, cudaStream_t s);
 cudaError_t launch_descriptor(const Desc *d, int grid, cudaStream_t s, bool mixed = false);
 
 // Pack the outputs of the batch described by d into one block (describe.cu).
-cudaError_t launch_pack(const Desc *da, const Desc *db, void *dst, int n_sm, cudaStream_t s);
+// The descriptors of the parts of one batch, in batch order (1 to 4).
+struct PackSrc {
+  const Desc *d[4];
+  int n;
+};
+cudaError_t launch_pack(PackSrc src, void *dst, int n_sm, cudaStream_t s);
 
 // MAGSAC++ homography verification (magsac.cu).
 size_t magsac_workspace_bytes(int n_hyp);

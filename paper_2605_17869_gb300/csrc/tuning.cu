@@ -7,7 +7,7 @@
 //                                                    flat list: octave 0)
 //    "blur_ctas_per_sm": [c_0, c_1, ...],            per octave
 //    "extrema_ctas_per_sm": c, "orientation_ctas_per_sm": c,
-//    "descriptor_ctas_per_sm": c, "compaction_ctas_per_sm": c, "batch_lanes": 1 | 2}
+//    "descriptor_ctas_per_sm": c, "compaction_ctas_per_sm": c, "batch_lanes": 1 .. 4}
 // r is 32 or 64; c is 0 (the occupancy maximum) or 1..64 (capped by the
 // occupancy maximum at launch).
 //
@@ -225,7 +225,7 @@ bool parse_tuning(const char *json, int S, const Tuning &base, Tuning *out, std:
                          : t.cmp_ctas) = (int)v;
       } else if (key == "batch_lanes") {
         long v;
-        if (!c.integer(&v) || (v != 1 && v != 2)) return bad("tuning: batch_lanes must be 1 or 2");
+        if (!c.integer(&v) || v < 1 || v > kMaxLanes) return bad("tuning: batch_lanes must be 1 to 4");
         t.batch_lanes = (int)v;
       } else {
         return bad("tuning: unknown key \"" + key + "\"");

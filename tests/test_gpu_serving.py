@@ -148,7 +148,7 @@ def test_tuning_json_round_trip_and_validation():
     for bad in ('{"blur_tile_rows": [48, 32, 32, 32, 32]}', '{"blur_tile_rows": [32, 32]}',
                 '{"extrema_ctas_per_sm": 65}', '{"extrema_ctas_per_sm": -1}', '{"grid": 1}',
                 '{"descriptor_ctas_per_sm": 2.5}', '[]', '{"blur_ctas_per_sm": [1] } x',
-                '{"batch_lanes": 3}', '{"batch_lanes": 0}'):
+                '{"batch_lanes": 5}', '{"batch_lanes": 0}'):
         with pytest.raises(pkg.SiftError):
             ex.set_tuning(bad)
     ex.close()
@@ -191,34 +191,39 @@ def test_batch_autotune_bit_identical_and_cached(tmp_path):
 
 
 def test_batch_lanes_bit_identical_with_pack_and_stats():
-    """Two concurrent halves (batch_lanes 2) against the whole batch in one pass:
-    the same features, the same packed download, the same per-image stats; the
-    caller's stream sees both halves without a device-wide synchronisation."""
+    """A batch in 2, 3 or 4 concurrent parts (batch_lanes) against the whole
+    batch in one pass: the same features, the same packed download, the same
+    per-image stats; the caller's stream sees every part without a
+    device-wide synchronisation."""
     shapes = [(1200, 1600), (97, 211), (480, 640), (720, 1280), (300, 411)]
     imgs = [torch.from_numpy(synth.make_image(synth.rng_for(77, i), *s, fractal_std=0.05)).cuda()
             for i, s in enumerate(shapes)]
-    one, two = pkg.Extractor(), pkg.Extractor()
+    one = pkg.Extractor()
     one.set_tuning('{"batch_lanes": 1}')
-    assert '"batch_lanes": 2' in two.get_tuning()
+    assert '"batch_lanes": 2' in pkg.Extractor().get_tuning()
     side = torch.cuda.Stream()
-    for batch in (imgs, imgs[:2], imgs[1:3], imgs[:1], imgs[::-1]):
-        fa = one.extract_batch(batch)
-        with torch.cuda.stream(side):
-            bufs, cnt = two.extract_batch_async(batch, side)
-            counts = cnt.clone()
-        side.synchronize()  # only the caller's stream: it must have joined the second half
-        fb = [b.view(c) for b, c in zip(bufs, counts.tolist())]
-        assert len(fa) == len(fb)
-        assert all(_same(a, b) for a, b in zip(fa, fb))
-        ca, pa = one.download()
-        cb, pb = two.download(side)
-        assert ca == cb == [f.count for f in fa]
-        for a, b in zip(pa, pb):
-            for k in a:
-                assert np.array_equal(a[k], b[k]), k
-        sa, ra = one.stats(len(batch))
-        sb, rb = two.stats(len(batch))
-        assert sa == sb and ra == rb
-        assert two.launch_count() >= one.launch_count()
+    for lanes in (2, 3, 4):
+        many = pkg.Extractor()
+        many.set_tuning('{"batch_lanes": %d}' % lanes)
+        for batch in (imgs, imgs[:2], imgs[1:4], imgs[:1], imgs[::-1]):
+            fa = one.extract_batch(batch)
+            with torch.cuda.stream(side):
+                bufs, cnt = many.extract_batch_async(batch, side)
+                counts = cnt.clone()
+            side.synchronize()  # only the caller's stream: it must have joined every part
+            fb = [b.view(c) for b, c in zip(bufs, counts.tolist())]
+            assert len(fa) == len(fb)
+            assert all(_same(a, b) for a, b in zip(fa, fb)), (lanes, len(batch))
+            ca, pa = one.download()
+            cb, pb = many.download(side)
+            assert ca == cb == [f.count for f in fa]
+            for a, b in zip(pa, pb):
+                for k in a:
+                    assert np.array_equal(a[k], b[k]), k
+            sa, ra = one.stats(len(batch))
+            sb, rb = many.stats(len(batch))
+            assert sa == sb and ra == rb
+            if len(batch) >= 2:  # every part launches its own graph
+                assert many.launch_count() > one.launch_count()
+        many.close()
     one.close()
-    two.close()
