@@ -88,13 +88,18 @@ def sift_extract(handle, img_ptr: int, H: int, W: int, pitch: int, stream: int,
                   handle, "sift_extract")
 
 
+def _carray(ctype, n, xs):
+    """xs as a ctypes array of n ctype; an array built beforehand passes through."""
+    return xs if isinstance(xs, ctypes.Array) else (ctype * n)(*xs)
+
+
 def sift_extract_batch(handle, img_ptrs, Hs, Ws, pitches, stream: int, kpts_list, desc_ptrs,
                        counts_ptr: int) -> int:
     n = len(img_ptrs)
     return _check(_lib().sift_extract_batch(
         handle, n, (c_void_p * n)(*img_ptrs), (c_int * n)(*Hs), (c_int * n)(*Ws),
-        (c_int * n)(*pitches), c_void_p(stream), (SiftKptsDev * n)(*kpts_list),
-        (c_void_p * n)(*desc_ptrs), c_void_p(counts_ptr)), handle, "sift_extract_batch")
+        (c_int * n)(*pitches), c_void_p(stream), _carray(SiftKptsDev, n, kpts_list),
+        _carray(c_void_p, n, desc_ptrs), c_void_p(counts_ptr)), handle, "sift_extract_batch")
 
 
 def sift_extract_noalloc(params: SiftParams, img_ptr: int, H: int, W: int, pitch: int,
@@ -343,11 +348,12 @@ class OutputBuffers:
         self.octave = torch.empty(max_kpts, **i)
         self.layer = torch.empty(max_kpts, **i)
         self.desc = torch.empty((max_kpts, 128), **f)
+        self._kpts = SiftKptsDev(self.x.data_ptr(), self.y.data_ptr(), self.sigma.data_ptr(),
+                                 self.angle.data_ptr(), self.response.data_ptr(),
+                                 self.octave.data_ptr(), self.layer.data_ptr())
 
     def kpts(self) -> SiftKptsDev:
-        return SiftKptsDev(self.x.data_ptr(), self.y.data_ptr(), self.sigma.data_ptr(),
-                           self.angle.data_ptr(), self.response.data_ptr(),
-                           self.octave.data_ptr(), self.layer.data_ptr())
+        return self._kpts
 
     def view(self, n: int) -> Features:
         return Features(self.x[:n], self.y[:n], self.sigma[:n], self.angle[:n],
@@ -379,6 +385,7 @@ class Extractor:
         self.handle = sift_create(self.params)
         self.device = torch.device("cuda", torch.cuda.current_device())
         self._bufs = []
+        self._out_arrays = {}  # n -> (SiftKptsDev[n], void*[n]) of the first n buffers
         self._counts = None
         self._last_batch = 0
         self._pack_dev = self._pack_host = self._counts_host = None
@@ -403,6 +410,17 @@ class Extractor:
             self._counts = torch.zeros(max(n, 1), dtype=torch.int32, device=self.device)
         return self._bufs[:n]
 
+    def _outputs(self, n: int):
+        """The first n buffers and their pointer arrays, built once per n (the
+        buffers live as long as the Extractor)."""
+        bufs = self._buffers(n)
+        arr = self._out_arrays.get(n)
+        if arr is None:
+            arr = ((SiftKptsDev * n)(*[b.kpts() for b in bufs]),
+                   (c_void_p * n)(*[b.desc.data_ptr() for b in bufs]))
+            self._out_arrays[n] = arr
+        return bufs, arr
+
     @staticmethod
     def _check_img(img):
         torch = _torch()
@@ -411,6 +429,23 @@ class Extractor:
         if img.stride(1) != 1:
             raise SiftError(SIFT_E_INVALID, "image rows must be contiguous")
         return img.shape[0], img.shape[1], img.stride(0)
+
+    @staticmethod
+    def _batch_dims(imgs):
+        """(heights, widths, row pitches) of a batch, with _check_img's checks
+        (one shape and one stride read per image: this runs on every call)."""
+        f32 = _torch().float32
+        Hs, Ws, Ps = [], [], []
+        for img in imgs:
+            sh, st = img.shape, img.stride()
+            if not (img.is_cuda and img.dtype is f32 and len(sh) == 2):
+                raise SiftError(SIFT_E_INVALID, "image must be a 2-D float32 CUDA tensor")
+            if st[1] != 1:
+                raise SiftError(SIFT_E_INVALID, "image rows must be contiguous")
+            Hs.append(sh[0])
+            Ws.append(sh[1])
+            Ps.append(st[0])
+        return Hs, Ws, Ps
 
     def extract_async(self, img, stream=None):
         """Queue one extraction; returns (buffers, counts tensor) without syncing."""
@@ -434,13 +469,11 @@ class Extractor:
 
     def extract_batch_async(self, imgs, stream=None):
         torch = _torch()
-        dims = [self._check_img(im) for im in imgs]
+        Hs, Ws, Ps = self._batch_dims(imgs)
         s = stream if stream is not None else torch.cuda.current_stream()
-        bufs = self._buffers(len(imgs))
-        sift_extract_batch(self.handle, [im.data_ptr() for im in imgs], [d[0] for d in dims],
-                           [d[1] for d in dims], [d[2] for d in dims], s.cuda_stream,
-                           [b.kpts() for b in bufs], [b.desc.data_ptr() for b in bufs],
-                           self._counts.data_ptr())
+        bufs, (k_arr, d_arr) = self._outputs(len(imgs))
+        sift_extract_batch(self.handle, [im.data_ptr() for im in imgs], Hs, Ws, Ps, s.cuda_stream,
+                           k_arr, d_arr, self._counts.data_ptr())
         self._last_batch = len(imgs)
         return bufs, self._counts[:len(imgs)]
 
