@@ -257,21 +257,41 @@ __global__ void __launch_bounds__(kThreads) k_cc_compact(const Desc *__restrict_
   __shared__ int tmp[kThreads / 32 + 1];
   __shared__ int s_w[kMaxCh][kCmpWarps];
   __shared__ int s_val;
+  __shared__ int s_act[kMaxImg + 1];
   constexpr int SPT = kChunk / kThreads;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int n = d->n_img, C = d->n_cc_chunks, G = gridDim.x, g = blockIdx.x;
+  const int n = d->n_img, g = blockIdx.x;
   const LookbackCfg cfg{d->lb_epoch, d->lb_spins, d->lb_hold, d->lb_err};
+  // Only the chunks that hold candidates are scanned: image b's n_cand
+  // candidates fill its first ceil(n_cand / kChunk) chunks (at least one, so
+  // that every image has a chunk whose block writes its totals). s_act is the
+  // prefix of those counts over the images; the blocks beyond the number of
+  // active chunks take no part.
+  if (warp == 0) {
+    int flat = 0;
+    for (int b0 = 0; b0 < n; b0 += 32) {
+      const int b = b0 + lane;
+      const int a = b < n ? max(1, (d->cnt[b].n_cand + kChunk - 1) / kChunk) : 0;
+      const int incl = warp_incl_scan(a);
+      if (b < n) s_act[b + 1] = flat + incl;
+      flat += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (lane == 0) s_act[0] = 0;
+  }
+  __syncthreads();
+  const int C = s_act[n], G = min((int)gridDim.x, C);
+  if (g >= G) return;
   const int ca = (int)((long long)C * g / G), cb = (int)((long long)C * (g + 1) / G);
   const int kept = min(cb - ca, kMaxCh);
   // Owners of the range's chunks: found once, then advanced (the chunks are
   // contiguous and images are in order).
-  const int b_lo = ca < cb ? find_owner(d->cc_pre, n, ca) : 0;
+  const int b_lo = ca < cb ? find_owner(s_act, n, ca) : 0;
   int np[SPT];
   int s0;
   int over = 0;
   for (int c = ca, b = b_lo; c < cb; c++) {
-    while (c >= d->cc_pre[b + 1]) b++;
-    const int v = cc_chunk_peaks(d, d->img[b], d->cnt[b].n_cand, c, d->cc_pre[b], np, &s0);
+    while (c >= s_act[b + 1]) b++;
+    const int v = cc_chunk_peaks(d, d->img[b], d->cnt[b].n_cand, c, s_act[b], np, &s0);
     if (c - ca < kMaxCh) {
       int ws = v;
 #pragma unroll
@@ -298,14 +318,14 @@ __global__ void __launch_bounds__(kThreads) k_cc_compact(const Desc *__restrict_
   {
     int acc = base;
     for (int c = ca, b = b_lo; c < cb; c++) {
-      while (c >= d->cc_pre[b + 1]) b++;
-      if (c == d->cc_pre[b] && threadIdx.x == 0) lb_store(starts + b, lb_word(kLbInc, cfg.epoch, acc));
+      while (c >= s_act[b + 1]) b++;
+      if (c == s_act[b] && threadIdx.x == 0) lb_store(starts + b, lb_word(kLbInc, cfg.epoch, acc));
       int t = 0;
       if (c - ca < kMaxCh) {
 #pragma unroll
         for (int w = 0; w < kCmpWarps; w++) t += s_w[c - ca][w];
       } else {  // uniform over the block
-        t = block_sum(cc_chunk_peaks(d, d->img[b], d->cnt[b].n_cand, c, d->cc_pre[b], np, &s0), tmp);
+        t = block_sum(cc_chunk_peaks(d, d->img[b], d->cnt[b].n_cand, c, s_act[b], np, &s0), tmp);
       }
       acc += t;
     }
@@ -313,9 +333,9 @@ __global__ void __launch_bounds__(kThreads) k_cc_compact(const Desc *__restrict_
   int carry = base;
   int cur = -1, start = 0;
   for (int c = ca, b = b_lo; c < cb; c++) {
-    while (c >= d->cc_pre[b + 1]) b++;
+    while (c >= s_act[b + 1]) b++;
     const ImgDev &im = d->img[b];
-    const int c0 = d->cc_pre[b];
+    const int c0 = s_act[b];
     const int v = cc_chunk_peaks(d, im, d->cnt[b].n_cand, c, c0, np, &s0);
     int pre, tot;
     if (c - ca < kMaxCh) {
@@ -363,7 +383,7 @@ __global__ void __launch_bounds__(kThreads) k_cc_compact(const Desc *__restrict_
         }
       }
     }
-    if (threadIdx.x == 0 && c == d->cc_pre[b + 1] - 1) {
+    if (threadIdx.x == 0 && c == s_act[b + 1] - 1) {
       const int total = max(0, rel + tot);
       const int no = min(total, im.ori_cap);
       const int nf = min(no, im.kcap);
