@@ -629,13 +629,13 @@ def fp16_side(torch, pkg, imgs, shapes, mpix, flush, stream, tuning, steps):
     ex = pkg.Extractor(upsample=0, max_kpts=MAX_KPTS, fp16_pyramid=1)
     ex.set_tuning(tuning)
     step = lambda: ex.extract_batch_async(imgs, stream)  # noqa: E731
-    t, _ = timed_steps(torch, step, steps, 3, flush, stream)
+    ms = queued_steps(torch, step, steps, 3, stream)[0] / steps
     counts = ex._counts[:len(imgs)].tolist()
     cls = profiled_classes(torch, ex, step, flush, 3)
     ex.close()
     return {"workload": "the timed batch with fp16_pyramid=1",
-            "ms_per_step": round(statistics.mean(t), 4),
-            "mpix_s": round(mpix * len(t) / (sum(t) / 1e3), 1),
+            "ms_per_step": round(ms, 4),
+            "mpix_s": round(mpix / (ms / 1e3), 1),
             "keypoints_per_step": sum(counts),
             "kernel_ms_per_step": {k: round(v[0], 4) for k, v in cls.items()},
             "pyramid_bytes_per_step": _pyramid_bytes(shapes, False, True),
@@ -655,7 +655,7 @@ def keypoint_heavy_side(torch, pkg, flush, stream, tuning, steps):
     ex = pkg.Extractor(upsample=1, max_kpts=MAX_KPTS)
     ex.set_tuning(tuning)
     step = lambda: ex.extract_batch_async(imgs, stream)  # noqa: E731
-    t, _ = timed_steps(torch, step, steps, 3, flush, stream)
+    ms_step = queued_steps(torch, step, steps, 3, stream)[0] / steps
     counts = ex._counts[:len(imgs)].tolist()
     _, stats = ex.stats(len(imgs))
     cls = profiled_classes(torch, ex, step, flush, 3)
@@ -668,7 +668,7 @@ def keypoint_heavy_side(torch, pkg, flush, stream, tuning, steps):
            "candidates_per_image": [s[0] for s in stats],
            "refined_per_image": [s[1] for s in stats],
            "oriented_per_image": [s[2] for s in stats],
-           "ms_per_step": round(statistics.mean(t), 4),
+           "ms_per_step": round(ms_step, 4),
            "kernel_ms_per_step": {k: round(v[0], 4) for k, v in cls.items()}}
     for k, n in n_in.items():
         ms = cls.get(k, (0.0, 0))[0]
@@ -688,22 +688,23 @@ def homography_side(torch, pkg, flush, stream, tuning, steps):
     for label, kw in (("plain", {}), ("dsp_rootsift", {"dsp": 1, "rootsift": 1})):
         ex = pkg.Extractor(upsample=1, max_kpts=8000, **kw)  # default tuning
         step = lambda: ex.extract_batch_async(imgs, stream)  # noqa: E731
-        t, _ = timed_steps(torch, step, steps, 3, flush, stream)
+        ms_step = queued_steps(torch, step, steps, 3, stream)[0] / steps
         counts = ex._counts[:len(imgs)].tolist()
         feats = [ex._bufs[i].view(counts[i]) for i in range(len(imgs))]
         acc = matching.sequence_mma(feats, seq.homographies)
         cls = profiled_classes(torch, ex, step, flush, 3)
-        r = {"ms_per_step": round(statistics.mean(t), 4),
-             "mpix_s": round(mpix * len(t) / (sum(t) / 1e3), 1),
-             "keypoints_per_s": round(sum(counts) * len(t) / (sum(t) / 1e3), 1),
+        r = {"ms_per_step": round(ms_step, 4),
+             "mpix_s": round(mpix / (ms_step / 1e3), 1),
+             "keypoints_per_s": round(sum(counts) / (ms_step / 1e3), 1),
              "kernel_ms_per_step": {k: round(v[0], 4) for k, v in cls.items()},
              "matches": acc["matches"], **{k: v for k, v in acc.items() if k.startswith("mma@")}}
         if label == "plain":
             def single():
                 for im in imgs:
                     ex.extract_async(im, stream)
-            ts, _ = timed_steps(torch, single, max(3, steps // 2), 2, flush, stream)
-            r["per_image_mpix_s"] = round(mpix * len(ts) / (sum(ts) / 1e3), 1)
+            n_s = max(3, steps // 2)
+            ts = queued_steps(torch, single, n_s, 2, stream)[0]
+            r["per_image_mpix_s"] = round(mpix * n_s / (ts / 1e3), 1)
             r["accuracy"] = {"what": "image 0 matched to each warped image; MMA against the known "
                                      "homographies (harness: torch mutual NN + ratio 0.8)", **acc}
             # The batch autotuner on this batch: the steps above used the defaults.
@@ -711,10 +712,10 @@ def homography_side(torch, pkg, flush, stream, tuning, steps):
             js, _ = ex.autotune_batch(imgs, stream)
             torch.cuda.synchronize()
             search = time.perf_counter() - t0
-            tt, _ = timed_steps(torch, step, steps, 3, flush, stream)
+            tt = queued_steps(torch, step, steps, 3, stream)[0] / steps
             r["autotune"] = {"untuned_ms_per_step": r["ms_per_step"],
-                             "tuned_ms_per_step": round(statistics.mean(tt), 4),
-                             "untuned_over_tuned": round(r["ms_per_step"] / statistics.mean(tt), 4),
+                             "tuned_ms_per_step": round(tt, 4),
+                             "untuned_over_tuned": round(r["ms_per_step"] / tt, 4),
                              "search_s": round(search, 3), "tuning": js,
                              "chose_defaults": _is_default_tuning(js)}
         out[label] = r
