@@ -723,6 +723,21 @@ def homography_side(torch, pkg, flush, stream, tuning, steps):
     return out
 
 
+def homography_loop(torch, pkg, stream, tuning, steps, warmup):
+    """A timed loop of the homography-sequence batch alone: `warmup` steps,
+    then `steps` steps queued back to back (one graph per lane and step)."""
+    seq = synth.homography_sequence(index=0)
+    imgs = _device_images(seq.images, torch)
+    ex = pkg.Extractor(upsample=1, max_kpts=8000)
+    ex.set_tuning(tuning)
+    ms, _ = queued_steps(torch, lambda: ex.extract_batch_async(imgs, stream), steps, warmup, stream)
+    r = {"workload": HOMOGRAPHY_WORKLOAD, "mode": "timed loop only", "steps": steps,
+         "warmup": warmup, "ms_per_step": round(ms / steps, 4),
+         "gpu_launches_per_step": ex.launch_count(), "tuning": ex.get_tuning()}
+    ex.close()
+    return r
+
+
 def serving_bench(torch, pkg, rates, n_req, budget=8 << 30):
     """Poisson arrivals at each rate: submit on arrival, collect every result,
     report images/s and p50 / p99 latency (from submission to completion)."""
@@ -901,6 +916,9 @@ def main():
                     help="skip the homography-sequence, single-image and image-pair runs")
     ap.add_argument("--minimal", action="store_true",
                     help="only the timed batch loop (for profiler launch lists)")
+    ap.add_argument("--homography-loop", action="store_true",
+                    help="only a timed loop of the homography-sequence batch (6 x 1000x750, "
+                         "2x upsampled, cap 8000) at the given tuning (for profiler captures)")
     ap.add_argument("--pair-only", action="store_true",
                     help="only the single-image and wide-baseline pair runs (extraction, "
                          "matcher, MAGSAC++), e.g. for profiling those kernels")
@@ -927,13 +945,16 @@ def main():
             print(json.dumps(reference_arm(args, pool, n_workers, batch)))
         return
 
-    if args.pair_only or args.keypoint_heavy:
+    if args.pair_only or args.keypoint_heavy or args.homography_loop:
         import torch
         import paper_2605_17869_gb300 as pkg
         stream = torch.cuda.current_stream()
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
         tuning = args.tuning or '{"blur_tile_rows": [32, 32, 32, 32, 32]}'
-        if args.keypoint_heavy:
+        if args.homography_loop:
+            print(json.dumps(homography_loop(torch, pkg, stream, tuning, max(1, args.steps),
+                                             args.warmup)))
+        elif args.keypoint_heavy:
             print(json.dumps({"keypoint_heavy": keypoint_heavy_side(
                 torch, pkg, flush, stream, tuning, max(1, args.steps))}))
         else:
