@@ -679,10 +679,12 @@ __device__ __forceinline__ void desc_sweep(const Desc *__restrict__ d, const Ref
 // scales vote into the same histogram (pooling before normalisation).
 // Positions are kept relative to the integer keypoint pixel, so the
 // interpolation weights keep full FP32 precision in large octaves.
-// MIXED: the pyramid has binary16 octaves (fp16 storage mode); the kernel then
-// carries both sample sweeps and picks one per keypoint. Without it only the
-// FP32 sweep is compiled in.
-template <bool MIXED>
+// PART: which keypoints a launch describes. 0: all of them (every octave
+// FP32); with binary16 octaves (fp16 storage mode) two launches, 1 for the
+// keypoints of FP32 octaves and 2 for those of binary16 octaves, each with
+// only its own sample sweep compiled in (one kernel carrying both sweeps ran
+// a third slower per keypoint).
+template <int PART>
 __global__ void __launch_bounds__(kKpWarps * 32, 6) k_descriptor(const Desc *__restrict__ d) {
   pdl_wait();
   extern __shared__ __align__(16) float dsm[];
@@ -702,6 +704,7 @@ __global__ void __launch_bounds__(kKpWarps * 32, 6) k_descriptor(const Desc *__r
     const RefRec r = d->ref[slot];
     const float angle = d->angs[slot * kMaxPeaks + e.y];
     const OctDev od = d->oct[im.oct0 + r.o];
+    if (PART != 0 && (od.half != 0) != (PART == 2)) continue;  // the other launch's keypoint
     const float sig = sigma_of(d, r);
     if (tid == 0) {
       const float sc = ldexpf(im.up ? 0.5f : 1.0f, r.o);
@@ -713,8 +716,7 @@ __global__ void __launch_bounds__(kKpWarps * 32, 6) k_descriptor(const Desc *__r
       im.ooct[j] = r.o;
       im.olay[j] = r.s;
     }
-    // Level r.s of the keypoint's octave: FP32, or binary16 (od.half).
-    const bool hf = od.half != 0;
+    // Level r.s of the keypoint's octave: FP32, or binary16 (od.half, PART 2).
     const float *L = d->pyr + od.lvl;
     const long long lofs = (long long)r.s * od.lstride;
     const float wbin = 3.0f * sig;
@@ -729,10 +731,7 @@ __global__ void __launch_bounds__(kKpWarps * 32, 6) k_descriptor(const Desc *__r
       for (int k = lane; k < kDescLen * kDescCols / 4; k += 32) h4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncwarp();
-    if (MIXED && hf)
-      desc_sweep<true>(d, r, od, L, lofs, wbin, inv_w, th, st, ct, R, hist, lane, warp, s_lo, s_pre);
-    else
-      desc_sweep<false>(d, r, od, L, lofs, wbin, inv_w, th, st, ct, R, hist, lane, warp, s_lo, s_pre);
+    desc_sweep<PART == 2>(d, r, od, L, lofs, wbin, inv_w, th, st, ct, R, hist, lane, warp, s_lo, s_pre);
     __syncthreads();
     // Bin tid: per warp, the 16 columns starting at column (tid / 2) % 16 (with
     // the layout [bin][16], the 32 threads of a warp then read 32 distinct
@@ -871,24 +870,28 @@ int orientation_max_ctas(bool mixed) {
 int descriptor_max_ctas(bool mixed) {
   int nb = 0;
   const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &nb, mixed ? k_descriptor<true> : k_descriptor<false>, kKpWarps * 32,
+      &nb, mixed ? k_descriptor<2> : k_descriptor<0>, kKpWarps * 32,
       descriptor_smem_bytes());
   return (e == cudaSuccess && nb > 0) ? nb : 1;
 }
 
 cudaError_t descriptor_set_attributes() {
-  cudaError_t e = cudaFuncSetAttribute(k_descriptor<false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       descriptor_smem_bytes());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_descriptor<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             descriptor_smem_bytes());
+  cudaError_t e = cudaSuccess;
+  for (const void *k : {reinterpret_cast<const void *>(k_descriptor<0>),
+                        reinterpret_cast<const void *>(k_descriptor<1>),
+                        reinterpret_cast<const void *>(k_descriptor<2>)})
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, descriptor_smem_bytes());
   return e;
 }
 
+// With binary16 octaves (mixed) two launches: the keypoints of FP32 octaves,
+// then those of binary16 octaves.
 cudaError_t launch_descriptor(const Desc *d, int grid, cudaStream_t s, bool mixed) {
-  if (mixed) return launch_pdl(k_descriptor<true>, grid, kKpWarps * 32, descriptor_smem_bytes(), s, d);
-  return launch_pdl(k_descriptor<false>, grid, kKpWarps * 32, descriptor_smem_bytes(), s, d);
+  if (!mixed) return launch_pdl(k_descriptor<0>, grid, kKpWarps * 32, descriptor_smem_bytes(), s, d);
+  const cudaError_t e = launch_pdl(k_descriptor<1>, grid, kKpWarps * 32, descriptor_smem_bytes(), s, d);
+  if (e != cudaSuccess) return e;
+  return launch_pdl(k_descriptor<2>, grid, kKpWarps * 32, descriptor_smem_bytes(), s, d);
 }
 
 }  // namespace sift

@@ -583,7 +583,8 @@ cudaError_t Engine::enqueue_all(cudaStream_t s, int M, int modes, std::vector<Pr
   rec(PC_ORIENT, [&] { return launch_orientation(d, grid_of(ori_max_, tun_.ori_ctas), s, mixed); });
   rec(PC_KEYPOINT, [&] { return launch_ori_compact(d, g2, s); });
   rec(PC_KEYPOINT, [&] { return launch_select(d, n_sm_, s); });
-  rec(PC_DESCRIPTOR, [&] { return launch_descriptor(d, grid_of(desc_max_, tun_.desc_ctas), s, mixed); });
+  rec(PC_DESCRIPTOR, [&] { return launch_descriptor(d, grid_of(desc_max_, tun_.desc_ctas), s, mixed); },
+      mixed ? 2 : 1);
   return e;
 }
 

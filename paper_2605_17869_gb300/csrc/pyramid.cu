@@ -17,6 +17,8 @@
 // two ascending chains of alternate taps whose grouping depends only on the
 // parity of x - R (row_pass_store). Results therefore do not depend on tiling
 // or on which other images share the launch.
+#include <type_traits>
+
 #include "sift_dev.cuh"
 
 namespace sift {
@@ -147,11 +149,44 @@ template <int R> struct RowSpan {
   static constexpr int G1 = G0 + 31 + NV;
 };
 
+// How the staged window holds its values (binary16 octaves of the fp16 storage
+// mode use 32-row tiles only):
+//   SK_F32  FP32 values;
+//   SK_H16  binary16 values (a binary16 level, MODE 0);
+//   SK_R16  FP32 values still to be rounded to binary16 (the decimated base of
+//           the first binary16 octave, MODE 3 from an FP32 octave);
+//   SK_P16  32-bit words whose low half is the binary16 value (the decimated
+//           base of a later binary16 octave: the word holding sample 2x of a
+//           binary16 row, copied whole by a 4-byte cp.async).
+enum StageKind { SK_F32 = 0, SK_H16 = 1, SK_R16 = 2, SK_P16 = 3 };
+
+template <int MODE, int ST> __host__ __device__ constexpr int stage_kind() {
+  return ST == 0 ? SK_F32 : MODE == 0 ? SK_H16 : ST == 1 ? SK_R16 : SK_P16;
+}
+
+// Staged elements idx, idx + 1 (idx even) as FP32; binary16 values widen
+// exactly, and SK_R16 rounds to binary16 first (what the level stores).
+template <int KIND>
+__device__ __forceinline__ float2 staged_pair(const float *s, int idx) {
+  if constexpr (KIND == SK_H16) {
+    return __half22float2(reinterpret_cast<const __half2 *>(s)[idx >> 1]);
+  } else if constexpr (KIND == SK_P16) {
+    const uint2 w = reinterpret_cast<const uint2 *>(s)[idx >> 1];
+    const unsigned lo = __byte_perm(w.x, w.y, 0x5410);  // the two low halves
+    return __half22float2(*reinterpret_cast<const __half2 *>(&lo));
+  } else {
+    const float2 f = reinterpret_cast<const float2 *>(s)[idx >> 1];
+    if constexpr (KIND == SK_R16) return __half22float2(__float22half2_rn(f));
+    return f;
+  }
+}
+
 // Column pass: s_v[v][c] = sum_j w[j] * s_in[v + j][c], j = 0..2R in order,
 // for the column groups the row pass reads. Thread item = one float4 column
-// group x V = TH/8 rows.
-template <int R, int TH>
+// group x V = TH/8 rows. KIND: how s_in holds the window (StageKind).
+template <int R, int TH, int KIND = SK_F32>
 __device__ __forceinline__ void col_pass(const float *s_in, float *s_v, const BlurTaps &tp) {
+  static_assert(TH == 32 || KIND == SK_F32, "binary16 windows use 32-row tiles");
   if constexpr (TH == 32) {
     // 32-row tiles: items of 8 rows x one column pair (float2), 4 x 72..80
     // items; 8 rows per item halve the staged reads per output compared with
@@ -161,11 +196,11 @@ __device__ __forceinline__ void col_pass(const float *s_in, float *s_v, const Bl
     constexpr int ITEMS = (TH / V) * NP;
     for (int it = threadIdx.x; it < ITEMS; it += kThreads) {
       const int rb = it / NP, c = 4 * RowSpan<R>::G0 + 2 * (it - rb * NP);
-      const float *src = s_in + rb * V * kSinW + c;
+      const int e0 = rb * V * kSinW + c;  // staged element of the item's first tap
       float2 acc[V];
 #pragma unroll
       for (int i = 0; i < V + 2 * R; i++) {
-        const float2 f = *reinterpret_cast<const float2 *>(src + i * kSinW);
+        const float2 f = staged_pair<KIND>(s_in, e0 + i * kSinW);
 #pragma unroll
         for (int v = 0; v < V; v++) {
           const int j = i - v;
@@ -367,6 +402,11 @@ __device__ __forceinline__ TileGeo tile_geo(const Desc *__restrict__ d, const in
 // that level first: sample (y, x) of level 0 is sample (2y, 2x) of level S of
 // octave o - 1, so the window is gathered from there (reflect-101 applied in
 // octave o's own domain), element by element.
+// DEC 2: src holds FP32 samples, spitch in floats. DEC 1: src is a binary16
+// plane seen as 32-bit words (spitch in halves): word gy * spitch + gx holds
+// halves 2 (gy * spitch + gx) and the next, the first of which is sample
+// (2 gy, 2 gx) (SK_P16).
+template <int DEC = 2>
 __device__ __forceinline__ void stage_decim_issue(const float *__restrict__ src, int spitch, int H,
                                                   int W, int x0, int y0, int R, int rows,
                                                   float *s_in) {
@@ -374,30 +414,34 @@ __device__ __forceinline__ void stage_decim_issue(const float *__restrict__ src,
   const bool yin = yb >= 0 && yb + rows <= H;
   constexpr int RPP = kThreads / kSinW;  // rows per pass (2)
   const int c = threadIdx.x % kSinW, r0 = threadIdx.x / kSinW;
-  const float *col = src + 2 * refl101(xb + c, W);
+  const float *col = src + DEC * refl101(xb + c, W);
   float *dst = s_in + r0 * kSinW + c;
   for (int r = r0; r < rows; r += RPP, dst += RPP * kSinW)
-    cp_async4(dst, col + (long long)(2 * (yin ? yb + r : refl101(yb + r, H))) * spitch);
+    cp_async4(dst, col + (long long)(DEC * (yin ? yb + r : refl101(yb + r, H))) * spitch);
 }
 
-// Store the tile's own rows / columns of the staged (decimated) level 0.
-template <int R, int TH, bool DH = false>
+// Store the tile's own rows / columns of the staged (decimated) level 0:
+// FP32, or (DH) rounded to binary16 (exact for SK_P16 words, whose low
+// halves are binary16 values already).
+template <int R, int TH, bool DH = false, int KIND = SK_F32>
 __device__ __forceinline__ void store_level0(const float *s_in, float *out0, int pitch, int H,
                                              int x0, int y0) {
   for (int q = threadIdx.x; q < TH * (kBlurTW / 4); q += kThreads) {
     const int v = q / (kBlurTW / 4), g = q - v * (kBlurTW / 4);
     const int y = y0 + v, x = x0 + 4 * g;
     if (y < H && x < pitch) {
-      const float4 f = *reinterpret_cast<const float4 *>(s_in + (R + v) * kSinW + kBlurHalo + 4 * g);
-      store4<DH>(out0, (long long)y * pitch + x, f.x, f.y, f.z, f.w);
+      const int e = (R + v) * kSinW + kBlurHalo + 4 * g;
+      const float2 a = staged_pair<KIND == SK_P16 ? SK_P16 : SK_F32>(s_in, e);
+      const float2 b = staged_pair<KIND == SK_P16 ? SK_P16 : SK_F32>(s_in, e + 2);
+      store4<DH>(out0, (long long)y * pitch + x, a.x, a.y, b.x, b.y);
     }
   }
 }
 
-// Staging by plain loads, for the storage modes that cp.async cannot serve: a
-// binary16 source is widened to FP32 on the way into shared memory, and the
-// decimated base of a binary16 octave (MODE 3, ST 1 or 2) is rounded to
-// binary16 first, so that the level-1 blur reads the values level 0 stores.
+// Staging by plain loads, for the decimated base of a binary16 octave (MODE 3,
+// ST 1 or 2), which cp.async cannot serve: the samples are rounded to binary16
+// first, so that the level-1 blur reads the values level 0 stores, and a
+// binary16 source (ST 2) is widened to FP32 on the way into shared memory.
 // Rows [y0 - R, y0 + rows - R) x columns [x0 - 16, x0 + 144), reflect-101 in
 // the octave's own domain; MODE 3 samples (2y, 2x) of the previous octave.
 template <int MODE, int ST>
@@ -405,38 +449,6 @@ __device__ __forceinline__ void stage_sync(const TileGeo &g, int R, int rows, fl
   const int xb = g.x0 - kBlurHalo, yb = g.y0 - R;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const __half *src16 = reinterpret_cast<const __half *>(g.src);
-  if (MODE == 0 && ST == 2 && xb >= 0 && xb + kSinW <= g.W && yb >= 0 && yb + rows <= g.H) {
-    // Interior tile of a binary16 level: 16-byte loads of 8 values (rows start
-    // on 64-byte boundaries and xb is a multiple of 16), four in flight per
-    // thread, widened into two float4 stores each.
-    constexpr int NG8 = kSinW / 8;  // 20 groups of 8 columns per row
-    const int n = rows * NG8;
-    for (int i0 = threadIdx.x; i0 < n; i0 += 4 * kThreads) {
-      uint4 v[4];
-#pragma unroll
-      for (int u = 0; u < 4; u++) {
-        const int i = i0 + u * kThreads;
-        if (i < n) {
-          const int r = i / NG8, c8 = i - r * NG8;
-          v[u] = *reinterpret_cast<const uint4 *>(src16 + (long long)(yb + r) * g.spitch + xb + 8 * c8);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 4; u++) {
-        const int i = i0 + u * kThreads;
-        if (i < n) {
-          const int r = i / NG8, c8 = i - r * NG8;
-          const __half2 *h = reinterpret_cast<const __half2 *>(&v[u]);
-          const float2 a = __half22float2(h[0]), b = __half22float2(h[1]);
-          const float2 c = __half22float2(h[2]), e = __half22float2(h[3]);
-          float4 *dst = reinterpret_cast<float4 *>(s_in + r * kSinW + 8 * c8);
-          dst[0] = make_float4(a.x, a.y, b.x, b.y);
-          dst[1] = make_float4(c.x, c.y, e.x, e.y);
-        }
-      }
-    }
-    return;
-  }
   for (int r = warp; r < rows; r += kWarps) {
     const int gy = refl101(yb + r, g.H);
     const long long row = (long long)(MODE == 3 ? 2 * gy : gy) * g.spitch;
@@ -469,13 +481,41 @@ __device__ __forceinline__ void stage_interior(const float *__restrict__ src, in
     if (i + 1 < NIT || r0 + i * RPP < ROWS) cp_async16_u(d0 + i * RPP * kSinW * 4, p + i * step);
 }
 
+// The window of a binary16 level (MODE 0, ST 2), kept as binary16 in shared
+// memory (rows of kSinW halves) and widened by the column pass. Every group of
+// 8 columns that lies inside the image is one 16-byte cp.async copy (rows
+// start on 64-byte boundaries and xb is a multiple of 16; a row outside the
+// image is its reflect-101 row); a group that crosses or lies past a left or
+// right edge is copied element by element through registers with reflect-101
+// (cp.async has no 2-byte copy).
+__device__ __forceinline__ void stage_half_issue(const TileGeo &g, int R, int rows, __half *s_in) {
+  const __half *src = reinterpret_cast<const __half *>(g.src);
+  const int xb = g.x0 - kBlurHalo, yb = g.y0 - R;
+  constexpr int NG8 = kSinW / 8;  // 20 groups of 8 halves per row
+  const bool yin = yb >= 0 && yb + rows <= g.H;
+  for (int i = threadIdx.x; i < rows * NG8; i += kThreads) {
+    const int r = i / NG8, c8 = i - r * NG8;
+    const int gx = xb + 8 * c8;
+    const __half *row = src + (long long)(yin ? yb + r : refl101(yb + r, g.H)) * g.spitch;
+    __half *dst = s_in + r * kSinW + 8 * c8;
+    if (gx >= 0 && gx + 8 <= g.W) {
+      cp_async16(dst, row + gx);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; k++) dst[k] = row[refl101(gx + k, g.W)];
+    }
+  }
+}
+
 template <int R, int TH, int MODE, int ST = 0>
 __device__ __forceinline__ void issue_stage(const TileGeo &g, float *dst) {
   constexpr int ROWS = TH + 2 * R;
-  if (ST != 0) {
+  if (MODE == 0 && ST == 2) {
+    stage_half_issue(g, R, ROWS, reinterpret_cast<__half *>(dst));
+  } else if (MODE == 3) {  // FP32 samples (ST 0, 1) or binary16 words (ST 2)
+    stage_decim_issue<ST == 2 ? 1 : 2>(g.src, g.spitch, g.H, g.W, g.x0, g.y0, R, ROWS, dst);
+  } else if (ST != 0) {
     stage_sync<MODE, ST>(g, R, ROWS, dst);
-  } else if (MODE == 3) {
-    stage_decim_issue(g.src, g.spitch, g.H, g.W, g.x0, g.y0, R, ROWS, dst);
   } else {
     const int xb = g.x0 - kBlurHalo, yb = g.y0 - R;
     if (g.vec && xb >= 0 && xb + kSinW <= g.W && yb >= 0 && yb + ROWS <= g.H)
@@ -503,8 +543,11 @@ __global__ void __launch_bounds__(kThreads, TH == 32 ? (MODE == 0 ? 4 : 3) : 1)
   static_assert(MODE != 2, "the magnified base is k_base_poly");
   extern __shared__ float4 smem4[];
   __shared__ TileGeo geo[2 * kGeoChunk];
+  // A binary16 level (MODE 0, ST 2) is staged as binary16: half the bytes.
+  constexpr int KIND = stage_kind<MODE, ST>();
+  constexpr bool H16 = KIND == SK_H16;
   float *s_in = reinterpret_cast<float *>(smem4);
-  float *s_v = s_in + ROWS * kSinW;
+  float *s_v = s_in + (H16 ? ROWS * kSinW / 2 : ROWS * kSinW);
   // The base blur of images kept at their size (MODE 1) takes the queue of
   // those images only.
   const int *pre = MODE == 1 ? d->base_pre[0] : d->tile_pre[KindOf<TH>::v][oct];
@@ -526,8 +569,8 @@ __global__ void __launch_bounds__(kThreads, TH == 32 ? (MODE == 0 ? 4 : 3) : 1)
     const TileGeo &gn = geo[(k + 1) & (2 * kGeoChunk - 1)];
     cp_async_wait_all();
     __syncthreads();
-    if (MODE == 3) store_level0<R, TH, ST != 0>(s_in, g.out0, g.pitch, g.H, g.x0, g.y0);
-    col_pass<R, TH>(s_in, s_v, tp);
+    if (MODE == 3) store_level0<R, TH, ST != 0, KIND>(s_in, g.out0, g.pitch, g.H, g.x0, g.y0);
+    col_pass<R, TH, KIND>(s_in, s_v, tp);
     __syncthreads();
     if (k + 1 < n_mine) issue_stage<R, TH, MODE, ST>(gn, s_in);
     row_pass_store<R, TH, ST != 0>(s_v, g.out, g.pitch, g.H, g.x0, g.y0, tp);
@@ -625,9 +668,10 @@ __global__ void __launch_bounds__(kThreads) k_blur_generic(const Desc *__restric
   }
 }
 
-// Shared memory: the staging buffer plus the column-pass output.
-template <int R, int TH, int MODE> constexpr int smem_bytes() {
-  return ((TH + 2 * R) + TH) * kSinW * (int)sizeof(float);
+// Shared memory: the staging buffer (binary16 for a binary16 level, ST 2 with
+// MODE 0) plus the column-pass output.
+template <int R, int TH, int MODE, int ST = 0> constexpr int smem_bytes() {
+  return (TH + 2 * R) * kSinW * (MODE == 0 && ST == 2 ? 2 : 4) + TH * kSinW * (int)sizeof(float);
 }
 
 int th_of_kind(int kind) { return kind == TK_BLUR64 ? 64 : 32; }
@@ -778,7 +822,7 @@ cudaError_t blur_set_attributes() {
   SET((k_blur<R, 32, 3>), (smem_bytes<R, 32, 3>()))          \
   SET((k_blur<R, 64, 3>), (smem_bytes<R, 64, 3>()))          \
   SET((k_blur<R, 32, 1>), (smem_bytes<R, 32, 1>()))          \
-  SET((k_blur<R, 32, 0, 2>), (smem_bytes<R, 32, 0>()))       \
+  SET((k_blur<R, 32, 0, 2>), (smem_bytes<R, 32, 0, 2>()))    \
   SET((k_blur<R, 32, 3, 1>), (smem_bytes<R, 32, 3>()))       \
   SET((k_blur<R, 32, 3, 2>), (smem_bytes<R, 32, 3>()))
   SIFT_FOR_EACH_R(SET_R)
@@ -811,7 +855,7 @@ cudaError_t launch_level_blur(const Desc *d, int oct, int lvl_out, int R, const 
     if (storage == 1) return go(k_blur<RR, 32, 3, 1>, smem_bytes<RR, 32, 3>(), t);          \
     if (storage == 2)                                                                     \
       return m3 ? go(k_blur<RR, 32, 3, 2>, smem_bytes<RR, 32, 3>(), t)                      \
-                : go(k_blur<RR, 32, 0, 2>, smem_bytes<RR, 32, 0>(), t);                     \
+                : go(k_blur<RR, 32, 0, 2>, smem_bytes<RR, 32, 0, 2>(), t);                  \
     if (th_kind == TK_BLUR64)                                                             \
       return m3 ? go(k_blur<RR, 64, 3>, smem_bytes<RR, 64, 3>(), t)                         \
                 : go(k_blur<RR, 64, 0>, smem_bytes<RR, 64, 0>(), t);                        \
