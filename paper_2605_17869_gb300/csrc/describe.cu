@@ -406,6 +406,8 @@ __global__ void __launch_bounds__(kThreads) k_cc_compact(const Desc *__restrict_
 // largest responses, ties broken by canonical order, and list the kept indices
 // in canonical order. The threshold is found by a bitwise search on the
 // response bits (responses are non-negative, so bit order = value order).
+// With binary16 octaves (fp16 storage mode) the block also counts the kept
+// keypoints of octave 0 (n_fin0), which the descriptor's two launches split on.
 __global__ void __launch_bounds__(1024) k_select(const Desc *__restrict__ d) {
   pdl_wait();
   __shared__ int tmp[1024 / 32 + 1];
@@ -414,7 +416,21 @@ __global__ void __launch_bounds__(1024) k_select(const Desc *__restrict__ d) {
     const ImgDev &im = d->img[b];
     const int n = d->cnt[b].n_ori;
     const int K = im.kcap;
-    if (n <= K) continue;
+    auto count_octave0 = [&]() {  // uniform over the block
+      if (!d->fp16) return;
+      const int nf = min(n, K);
+      int c = 0;
+      for (int j = threadIdx.x; j < nf; j += blockDim.x) {
+        const int oi = n > K ? d->fin[im.fin_off + j] : j;
+        c += d->ref[im.cand_off + d->ori[im.ori_off + oi].x].o == 0;
+      }
+      const int c0 = block_sum(c, tmp);
+      if (threadIdx.x == 0) d->cnt[b].n_fin0 = c0;
+    };
+    if (n <= K) {
+      count_octave0();
+      continue;
+    }
     const uint32_t *key = d->okey + im.ori_off;
     uint32_t thr = 0;
     for (int bit = 31; bit >= 0; bit--) {
@@ -440,6 +456,8 @@ __global__ void __launch_bounds__(1024) k_select(const Desc *__restrict__ d) {
       out += k_tot;
       eq_seen += eq_tot;
     }
+    __syncthreads();  // the kept list, before it is read back
+    count_octave0();
   }
 }
 
@@ -681,30 +699,54 @@ __device__ __forceinline__ void desc_sweep(const Desc *__restrict__ d, const Ref
 // interpolation weights keep full FP32 precision in large octaves.
 // PART: which keypoints a launch describes. 0: all of them (every octave
 // FP32); with binary16 octaves (fp16 storage mode) two launches, 1 for the
-// keypoints of FP32 octaves and 2 for those of binary16 octaves, each with
-// only its own sample sweep compiled in (one kernel carrying both sweeps ran
-// a third slower per keypoint).
+// keypoints of octave 0 (FP32) and 2 for those of the binary16 octaves, each
+// over its own index ranges (k_select's n_fin0) and with only its own sample
+// sweep compiled in (one kernel carrying both sweeps ran a third slower per
+// keypoint).
 template <int PART>
 __global__ void __launch_bounds__(kKpWarps * 32, 6) k_descriptor(const Desc *__restrict__ d) {
   pdl_wait();
   extern __shared__ __align__(16) float dsm[];
   __shared__ float s_bins[kDescLen];
   __shared__ int s_lo[kKpWarps][32], s_pre[kKpWarps][33];
+  // The prefix over the images of the keypoints this launch describes: all
+  // (PART 0), image b's first n_fin0 (PART 1) or the rest (PART 2); j0 is
+  // where image b's share starts in its list.
+  __shared__ int s_fin[kMaxImg + 1], s_j0[kMaxImg];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float *hist = dsm + warp * kDescWarpFloats;
   const int n = d->n_img;
-  const int total = d->fin_flat[n];
+  if (PART == 0) {
+    for (int i = tid; i <= n; i += kKpWarps * 32) s_fin[i] = d->fin_flat[i];
+    for (int i = tid; i < n; i += kKpWarps * 32) s_j0[i] = 0;
+  } else if (warp == 0) {
+    int flat = 0;
+    for (int b0 = 0; b0 < n; b0 += 32) {
+      const int b = b0 + lane;
+      int c = 0;
+      if (b < n) {
+        const int f = d->fin_flat[b + 1] - d->fin_flat[b], f0 = d->cnt[b].n_fin0;
+        c = PART == 1 ? f0 : f - f0;
+        s_j0[b] = PART == 1 ? 0 : f0;
+      }
+      const int incl = warp_incl_scan(c);
+      if (b < n) s_fin[b] = flat + incl - c;
+      flat += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (lane == 0) s_fin[n] = flat;
+  }
+  __syncthreads();
+  const int total = s_fin[n];
   for (int t = blockIdx.x; t < total; t += gridDim.x) {
-    const int b = find_owner(d->fin_flat, n, t);
+    const int b = find_owner(s_fin, n, t);  // in shared memory: no chain of global loads
     const ImgDev &im = d->img[b];
-    const int j = t - d->fin_flat[b];
+    const int j = s_j0[b] + (t - s_fin[b]);
     const int oi = (d->cnt[b].n_ori > im.kcap) ? d->fin[im.fin_off + j] : j;
     const int2 e = d->ori[im.ori_off + oi];
     const long long slot = im.cand_off + e.x;
     const RefRec r = d->ref[slot];
     const float angle = d->angs[slot * kMaxPeaks + e.y];
     const OctDev od = d->oct[im.oct0 + r.o];
-    if (PART != 0 && (od.half != 0) != (PART == 2)) continue;  // the other launch's keypoint
     const float sig = sigma_of(d, r);
     if (tid == 0) {
       const float sc = ldexpf(im.up ? 0.5f : 1.0f, r.o);

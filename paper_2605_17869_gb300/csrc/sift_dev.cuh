@@ -76,7 +76,11 @@ struct ImgDev {
 
 // Dynamic per-image results written by kernels.
 struct ImgCounters {
-  int n_cand_raw, n_cand, n_ori_raw, n_ori, n_fin, n_ref, flags, pad;
+  int n_cand_raw, n_cand, n_ori_raw, n_ori, n_fin, n_ref, flags;
+  // Kept keypoints of octave 0 (fp16 storage mode only): the list is in
+  // canonical order, so they are its first n_fin0 entries and the keypoints of
+  // the binary16 octaves the rest.
+  int n_fin0;
 };
 
 struct RefRec {               // refined keypoint (octave-local coordinates)
