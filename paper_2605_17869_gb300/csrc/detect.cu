@@ -139,8 +139,9 @@ __device__ __forceinline__ void ext_test(const ExtRow<S> &P, const ExtRow<S> &C,
 // the same FP32 values, so they do not depend on the tiling. Bitmap words are
 // written by ballots; no atomics.
 // HALF: the octave's levels are binary16 (fp16 storage mode). cp.async has no
-// 2-byte copy, so a row is then loaded into registers when it is issued and
-// written to its ring slot (widened to FP32) at the next issue, one row later.
+// 2-byte copy, so each lane copies the 32-bit word that holds its column's
+// value (4-byte aligned: rows start on 64-byte boundaries) and takes the low
+// or the high half of it, widened to FP32, when it reads the row.
 template <int S, bool HALF>
 __global__ void __launch_bounds__(kExtThreads, 5) k_extrema(const Desc *__restrict__ d, int oct) {
   constexpr int WPB = kExtThreads / 32;
@@ -164,20 +165,20 @@ __global__ void __launch_bounds__(kExtThreads, 5) k_extrema(const Desc *__restri
     const int ty = lt / od.wpr, tx = lt - ty * od.wpr;
     const int x = tx * kBmCols - 1 + lane;
     const int y0 = ty * kExtTH, y1 = min(y0 + kExtTH, H);
+    // lp[l]: the 32-bit word of level l, row 0, that holds the lane's column
+    // (binary16 levels: the word of halves xc & ~1 and its neighbour); a row's
+    // words are rstride apart.
     const float *lp[S + 3];
-    const __half *lph[S + 3];
+    const int xc = min(max(x, 0), W - 1);
+    const bool hi_half = HALF && (xc & 1);
+    const long long rstride = HALF ? pitch / 2 : pitch;
     {
-      const int xc = min(max(x, 0), W - 1);
-      const float *G = d->pyr + od.lvl + xc;
-      const __half *Gh = reinterpret_cast<const __half *>(d->pyr + od.lvl) + xc;
+      const float *G = HALF ? reinterpret_cast<const float *>(
+                                  reinterpret_cast<const __half *>(d->pyr + od.lvl) + (xc & ~1))
+                            : d->pyr + od.lvl + xc;
 #pragma unroll
-      for (int l = 0; l < S + 3; l++) {
-        lp[l] = G + l * ls;
-        lph[l] = Gh + l * ls;
-      }
+      for (int l = 0; l < S + 3; l++) lp[l] = G + l * (HALF ? ls / 2 : ls);
     }
-    float pend[S + 3];
-    float *pend_slot = nullptr;
     float *mine_ring = my + lane;
     const bool xin = lane >= 1 && lane <= kBmCols && x >= bord && x < W - bord;
     uint32_t *bmw = d->bm + od.bm + (long long)lane * H * od.wpr + tx;
@@ -186,23 +187,9 @@ __global__ void __launch_bounds__(kExtThreads, 5) k_extrema(const Desc *__restri
     // row, empty past the end, so that the number of pending groups is fixed.
     const int n_rows = y1 - y0 + 2;
     auto issue = [&](int k) {
-      if (HALF) {
-        if (pend_slot) {
-#pragma unroll
-          for (int l = 0; l < S + 3; l++) pend_slot[l * 32] = pend[l];
-          pend_slot = nullptr;
-        }
-        if (k < n_rows) {
-          const long long ro = (long long)min(max(y0 - 1 + k, 0), H - 1) * pitch;
-#pragma unroll
-          for (int l = 0; l < S + 3; l++) pend[l] = __half2float(__ldg(lph[l] + ro));
-          pend_slot = mine_ring + (k & (kExtRing - 1)) * SLOT;
-        }
-        return;
-      }
       if (k < n_rows) {
         const int row = min(max(y0 - 1 + k, 0), H - 1);
-        ext_issue<S>(mine_ring + (k & (kExtRing - 1)) * SLOT, lp, row * pitch);
+        ext_issue<S>(mine_ring + (k & (kExtRing - 1)) * SLOT, lp, row * rstride);
       }
       cp_async_commit();
     };
@@ -211,7 +198,14 @@ __global__ void __launch_bounds__(kExtThreads, 5) k_extrema(const Desc *__restri
       const float *slot = mine_ring + (k & (kExtRing - 1)) * SLOT;
       float g[S + 3];
 #pragma unroll
-      for (int l = 0; l < S + 3; l++) g[l] = slot[l * 32];
+      for (int l = 0; l < S + 3; l++) {
+        if (HALF) {
+          const unsigned w = __float_as_uint(slot[l * 32]);
+          g[l] = __half2float(__ushort_as_half((unsigned short)(hi_half ? w >> 16 : w & 0xffffu)));
+        } else {
+          g[l] = slot[l * 32];
+        }
+      }
       ext_row<S>(R, g);
       issue(k + kExtRing);  // into the slot just read (each lane rewrites only its own words)
     };
