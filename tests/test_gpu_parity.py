@@ -417,3 +417,40 @@ def test_fp16_keypoints_match_oracle(shape, up):
     fb = ex.extract_batch([other, t])
     assert _digest(fb[1]) == _digest(ex.extract(t))
     ex.close()
+
+
+def test_fp16_capped_batch_splits_descriptor_launches_correctly():
+    """In the fp16 storage mode the descriptor runs as two launches, one over
+    each image's octave-0 keypoints (the first n_fin0 of its list, counted by
+    the top-K step) and one over the rest. With a cap that cuts some images
+    and not others, every kept keypoint must carry exactly the descriptor the
+    uncapped run gives it (a keypoint described by the other launch's sweep
+    would read binary16 data as FP32 or the reverse); batches, lanes and
+    singleton runs must agree bit for bit."""
+    shapes = [(480, 640), (300, 411), (720, 560), (97, 211)]
+    imgs = [torch.from_numpy(synth.make_image(synth.rng_for(31, i), *s, n_blobs=60,
+                                              fractal_std=0.05)).cuda()
+            for i, s in enumerate(shapes)]
+    full = pkg.Extractor(max_kpts=8192, fp16_pyramid=1)
+    ref = full.extract_batch(imgs)
+    counts = [f.count for f in ref]
+    assert any(any(o > 0 for o in f.octave.tolist()) for f in ref)
+    cap = max(1, sorted(counts)[len(counts) // 2] // 2)  # cuts at least half the images
+    assert sum(c > cap for c in counts) >= 2
+    for lanes in (1, 2):
+        ex = pkg.Extractor(max_kpts=cap, fp16_pyramid=1)
+        ex.set_tuning('{"batch_lanes": %d}' % lanes)
+        got = ex.extract_batch(imgs)
+        for im, g, r in zip(imgs, got, ref):
+            assert g.count == min(r.count, cap)
+            assert _digest(g) == _digest(ex.extract(im))
+            # Every kept keypoint is one of the uncapped run's, with the same fields.
+            key = {(x, y, s, a): i for i, (x, y, s, a) in enumerate(zip(
+                r.x.tolist(), r.y.tolist(), r.sigma.tolist(), r.angle.tolist()))}
+            for k, tup in enumerate(zip(g.x.tolist(), g.y.tolist(), g.sigma.tolist(),
+                                        g.angle.tolist())):
+                i = key[tup]
+                assert int(g.octave[k]) == int(r.octave[i])
+                assert torch.equal(g.desc[k], r.desc[i])
+        ex.close()
+    full.close()
