@@ -438,10 +438,11 @@ __device__ __forceinline__ void store_level0(const float *s_in, float *out0, int
   }
 }
 
-// Staging by plain loads, for the decimated base of a binary16 octave (MODE 3,
-// ST 1 or 2), which cp.async cannot serve: the samples are rounded to binary16
-// first, so that the level-1 blur reads the values level 0 stores, and a
-// binary16 source (ST 2) is widened to FP32 on the way into shared memory.
+// Staging by plain loads for the binary16 modes of the generic-radius kernel
+// (k_blur uses cp.async for them): a binary16 source (ST 2) is widened to FP32
+// on the way into shared memory, and the decimated base of a binary16 octave
+// (MODE 3, ST 1 or 2) is rounded to binary16 first, so that the level-1 blur
+// reads the values level 0 stores.
 // Rows [y0 - R, y0 + rows - R) x columns [x0 - 16, x0 + 144), reflect-101 in
 // the octave's own domain; MODE 3 samples (2y, 2x) of the previous octave.
 template <int MODE, int ST>
@@ -510,13 +511,12 @@ __device__ __forceinline__ void stage_half_issue(const TileGeo &g, int R, int ro
 template <int R, int TH, int MODE, int ST = 0>
 __device__ __forceinline__ void issue_stage(const TileGeo &g, float *dst) {
   constexpr int ROWS = TH + 2 * R;
-  if (MODE == 0 && ST == 2) {
+  if constexpr (MODE == 0 && ST == 2) {
     stage_half_issue(g, R, ROWS, reinterpret_cast<__half *>(dst));
-  } else if (MODE == 3) {  // FP32 samples (ST 0, 1) or binary16 words (ST 2)
+  } else if constexpr (MODE == 3) {  // FP32 samples (ST 0, 1) or binary16 words (ST 2)
     stage_decim_issue<ST == 2 ? 1 : 2>(g.src, g.spitch, g.H, g.W, g.x0, g.y0, R, ROWS, dst);
-  } else if (ST != 0) {
-    stage_sync<MODE, ST>(g, R, ROWS, dst);
   } else {
+    static_assert(ST == 0, "binary16 output is MODE 3 (ST 1) or MODE 0 / 3 (ST 2)");
     const int xb = g.x0 - kBlurHalo, yb = g.y0 - R;
     if (g.vec && xb >= 0 && xb + kSinW <= g.W && yb >= 0 && yb + ROWS <= g.H)
       stage_interior<ROWS>(g.src, g.spitch, xb, yb, dst);
