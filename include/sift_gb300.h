@@ -340,7 +340,8 @@ sift_status sift_set_tuning(sift_handle *h, const char *json);
 /* Autotune on a real batch: the arguments of sift_extract_batch (1 to 128
  * images), plus from_cache (host, may be NULL) set to 1 when the tuning came
  * from the cache. Coordinate descent over whole extraction steps of this
- * batch on `stream`, from the defaults: 64-row tiles per level of the three
+ * batch on `stream` (each run as sift_extract_batch runs it, lanes included),
+ * from the defaults: 64-row tiles per level of the three
  * largest octaves, then fewer resident CTAs per SM for their level blurs and
  * for the extrema, orientation, descriptor and compaction grids, then 1 to 4
  * lanes (batch_lanes); a change is kept only if the step gets at least 1%

@@ -515,9 +515,9 @@ sift_status sift_autotune_batch(sift_handle *h, int n, const float *const *imgs_
     }
     if (st != SIFT_E_NOTFOUND) return fail(h, st, "tuning cache unreadable: " + h->tuning_cache);
   }
-  st = h->eng->autotune_batch(n, in.data(), s);
+  // Every candidate is timed as the handle runs the batch (lanes included).
+  st = h->eng->autotune_batch(n, in.data(), s, [&] { return run_batch(h, n, in.data(), s); });
   if (st != SIFT_OK) return pass(h, st);
-  h->n_parts = 0;
   // The number of lanes (the batch as 1 to 4 parts at once) is decided here,
   // at the handle, by timing whole steps through run_batch each way (best of
   // three runs of five steps, after two untimed ones); more lanes are kept

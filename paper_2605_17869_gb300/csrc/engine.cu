@@ -888,8 +888,7 @@ std::string Engine::device_key() const {
   return "sm" + std::to_string(ma) + std::to_string(mi) + "x" + std::to_string(n_sm_);
 }
 
-float Engine::time_steps(const Tuning &t, int n, const ImgIn *imgs, cudaStream_t s,
-                         sift_status *st) {
+float Engine::time_steps(const Tuning &t, const StepFn &step, cudaStream_t s, sift_status *st) {
   set_tuning(t);
   float best = 1e30f;
   cudaEvent_t a = nullptr, b = nullptr;
@@ -900,10 +899,10 @@ float Engine::time_steps(const Tuning &t, int n, const ImgIn *imgs, cudaStream_t
   }
   // Two untimed steps (the first one captures the graph), then the best of
   // three runs of five back-to-back steps.
-  for (int w = 0; w < 2 && *st == SIFT_OK; w++) *st = run(n, imgs, s);
+  for (int w = 0; w < 2 && *st == SIFT_OK; w++) *st = step();
   for (int r = 0; r < 3 && *st == SIFT_OK; r++) {
     cudaEventRecord(a, s);
-    for (int k = 0; k < 5 && *st == SIFT_OK; k++) *st = run(n, imgs, s);
+    for (int k = 0; k < 5 && *st == SIFT_OK; k++) *st = step();
     cudaEventRecord(b, s);
     float ms = 0.f;
     if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
@@ -917,7 +916,8 @@ float Engine::time_steps(const Tuning &t, int n, const ImgIn *imgs, cudaStream_t
   return best;
 }
 
-sift_status Engine::autotune_batch(int n, const ImgIn *imgs, cudaStream_t s) {
+sift_status Engine::autotune_batch(int n, const ImgIn *imgs, cudaStream_t s, const StepFn &step_in) {
+  const StepFn step = step_in ? step_in : StepFn([&] { return run(n, imgs, s); });
   sift_status st = init();
   if (st != SIFT_OK) return st;
   if (n < 1 || n > kMaxImg) {
@@ -938,10 +938,10 @@ sift_status Engine::autotune_batch(int n, const ImgIn *imgs, cudaStream_t s) {
   // orientation and descriptor CTAs per SM (down to half the maximum).
   const Tuning t0 = default_tuning();
   Tuning best_t = t0;
-  float best = time_steps(best_t, n, imgs, s, &st);
+  float best = time_steps(best_t, step, s, &st);
   auto try_t = [&](const Tuning &c) {
     if (st != SIFT_OK) return;
-    const float t = time_steps(c, n, imgs, s, &st);
+    const float t = time_steps(c, step, s, &st);
     if (st == SIFT_OK && t < 0.99f * best) {
       best = t;
       best_t = c;
@@ -973,13 +973,13 @@ sift_status Engine::autotune_batch(int n, const ImgIn *imgs, cudaStream_t s) {
   // Confirm against the defaults once more, so that a choice that won by
   // timing noise early in the search does not stay.
   if (st == SIFT_OK) {
-    const float tb = time_steps(best_t, n, imgs, s, &st);
-    const float td = st == SIFT_OK ? time_steps(t0, n, imgs, s, &st) : 0.f;
+    const float tb = time_steps(best_t, step, s, &st);
+    const float td = st == SIFT_OK ? time_steps(t0, step, s, &st) : 0.f;
     if (st == SIFT_OK && !(tb < td)) best_t = t0;
   }
   if (st != SIFT_OK) return st;
   set_tuning(best_t);
-  return run(n, imgs, s);  // the outputs: a run with the chosen tuning
+  return step();  // the outputs: a run with the chosen tuning
 }
 
 }  // namespace sift

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <functional>
 #include <map>
 #include <string>
 #include <vector>
@@ -115,8 +116,12 @@ class Engine {
   sift_status autotune(int H, int W, cudaStream_t s);
   // Search the launch shapes on a real batch (n <= kMaxImg) by timing whole
   // extraction steps, and keep the fastest; the outputs end up holding the
-  // results of a run with the chosen tuning.
-  sift_status autotune_batch(int n, const ImgIn *imgs, cudaStream_t s);
+  // results of a run with the chosen tuning. step, when given, queues one
+  // whole step of the batch on s under this engine's current tuning (the
+  // handle runs it as one or several lanes); by default run(n, imgs, s).
+  using StepFn = std::function<sift_status()>;
+  sift_status autotune_batch(int n, const ImgIn *imgs, cudaStream_t s,
+                             const StepFn &step = StepFn());
   // "sm<major><minor>x<SMs>": the device part of a tuning-cache key.
   std::string device_key() const;
   int level_radius(int l) const { return lvl_R_[l]; }
@@ -164,7 +169,7 @@ class Engine {
     return n_sm_ * std::max(1, ctas > 0 ? std::min(ctas, max_ctas) : max_ctas);
   }
   // Step time (ms, best of 3 x 5 steps) of a batch under tuning t.
-  float time_steps(const Tuning &t, int n, const ImgIn *imgs, cudaStream_t s, sift_status *st);
+  float time_steps(const Tuning &t, const StepFn &step, cudaStream_t s, sift_status *st);
 
   sift_params P_;
   int dev_ = 0, n_sm_ = 0;
