@@ -104,10 +104,10 @@ __device__ __forceinline__ void ext_test(const ExtRow<S> &P, const ExtRow<S> &C,
                                          uint32_t *word) {
   // Rows where no pixel of the strip passes the border and pre-gate tests
   // in any layer have no candidate: skip the neighbour comparisons.
-  bool any = false;
+  float amax = fabsf(C.c[0]);
 #pragma unroll
-  for (int s = 1; s <= S; s++) any |= inb && fabsf(C.c[s - 1]) > thr;
-  if (!__any_sync(0xffffffffu, any)) {
+  for (int s = 2; s <= S; s++) amax = fmaxf(amax, fabsf(C.c[s - 1]));
+  if (!__any_sync(0xffffffffu, inb && amax > thr)) {
     if (lane < S) *word = 0u;
     return;
   }
@@ -123,11 +123,18 @@ __device__ __forceinline__ void ext_test(const ExtRow<S> &P, const ExtRow<S> &C,
     const float c = C.c[s - 1];
     const float mx = max3f(vx[s - 1], vx[s + 1], max3f(P.hx[s], N.hx[s], C.lrx[s - 1]));
     const float mn = min3f(vn[s - 1], vn[s + 1], min3f(P.hn[s], N.hn[s], C.lrn[s - 1]));
-    const bool ok = inb && fabsf(c) > thr && (c > mx || c < mn);
-    const unsigned bits = __ballot_sync(0xffffffffu, ok) >> 1;  // lanes 1 .. 30 -> bits 0 .. 29
+    // |c| > thr and (c > mx or c < mn), as one comparison with zero: the
+    // differences of distinct finite FP32 values are never zero (gradual
+    // underflow) and keep their sign, so each difference is positive exactly
+    // when its comparison holds, and the minimum / maximum combine them. The
+    // subtractions run on the FMA pipe, leaving the ALU pipe (the scan's
+    // bound) three instructions instead of five.
+    const float margin = fminf(fabsf(c) - thr, fmaxf(c - mx, mn - c));
+    const bool ok = inb && margin > 0.f;
+    const unsigned bits = __ballot_sync(0xffffffffu, ok);
     mine = lane == s - 1 ? bits : mine;
   }
-  if (lane < S) *word = mine;
+  if (lane < S) *word = mine >> 1;  // lanes 1 .. 30 -> bits 0 .. 29
 }
 
 // A warp owns a strip of kBmCols = 30 columns x kExtTH rows: lane l holds
