@@ -480,9 +480,9 @@ constexpr int kDescWarpFloats = kDescLen * kDescCols;
 // from the keypoint, (u, v) = (rx, ry) + 3/2: weight m * exp(-(rx^2 + ry^2) /
 // 8), orientation relative to th. Cells outside the 4 x 4 grid get -1.
 struct Vote {
-  int cell[4];    // (v * 4 + u) * 8, or -1
+  int cell[4];    // (v * 4 + u) * 8 * kDescCols (the cell's first histogram word), or -1
   float w[4];     // spatial weights times the magnitude-Gaussian weight
-  int oe, oo;     // the even and the odd orientation bin
+  int oe, oo;     // the even and the odd orientation bin, times kDescCols
   float fe, fo;   // their orientation weights
 };
 
@@ -500,8 +500,8 @@ __device__ __forceinline__ void desc_targets(Vote &v, float rx, float ry, float 
   const float fu = u - u0f, fv = vv0 - v0f, f1 = ob - o0f;
   const int u0 = (int)u0f, v0 = (int)v0f, o0 = (int)o0f & 7, o1 = (o0 + 1) & 7;
   const bool even0 = (o0 & 1) == 0;
-  v.oe = even0 ? o0 : o1;
-  v.oo = even0 ? o1 : o0;
+  v.oe = (even0 ? o0 : o1) * kDescCols;
+  v.oo = (even0 ? o1 : o0) * kDescCols;
   v.fe = even0 ? 1.f - f1 : f1;
   v.fo = even0 ? f1 : 1.f - f1;
   // u0, v0 lie in [-1, 3] (u, v in (-1, 4)): cell u0 + du exists iff u0 >= 0
@@ -514,7 +514,7 @@ __device__ __forceinline__ void desc_targets(Vote &v, float rx, float ry, float 
 #pragma unroll
     for (int du = 0; du < 2; du++) {
       const float wu = du ? fu : 1.f - fu;
-      v.cell[dv * 2 + du] = (uok[du] && vok[dv]) ? c00 + (dv * 4 + du) * 8 : -1;
+      v.cell[dv * 2 + du] = (uok[du] && vok[dv]) ? (c00 + (dv * 4 + du) * 8) * kDescCols : -1;
       v.w[dv * 2 + du] = wv * wu;
     }
   }
@@ -534,7 +534,7 @@ __device__ __forceinline__ void desc_commit(float *hist, int lane, bool ok, cons
     const float f = even ? v.fe : v.fo;
 #pragma unroll
     for (int k = 0; k < 4; k++)
-      if (ok && v.cell[k] >= 0) col[(v.cell[k] + o) * kDescCols] += v.w[k] * f;
+      if (ok && v.cell[k] >= 0) col[v.cell[k] + o] += v.w[k] * f;
     __syncwarp();
   }
 }
