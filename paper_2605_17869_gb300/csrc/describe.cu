@@ -63,10 +63,9 @@ __device__ __forceinline__ void ori_vote(float (*hist)[32], int lane, float dx, 
   // |dx| = |dy|: theta is exactly 45 (2q + 1) degrees, a bin boundary the
   // nearest-bin rule floor(36 theta / 2 pi + 1/2) resolves upward; decided in
   // integers rather than left to the rounding of atan2f.
-  if (fabsf(dx) == fabsf(dy) && dx != 0.f) {
-    const int qd = dy > 0.f ? (dx > 0.f ? 0 : 1) : (dx < 0.f ? 2 : 3);
-    bin = (kOriBins * (2 * qd + 1) + 4) / 8 % kOriBins;
-  }
+  static_assert(kOriBins == 36, "the diagonal bins below are floor(36 (2q + 1) / 8 + 1/2)");
+  if (fabsf(dx) == fabsf(dy) && dx != 0.f)  // quadrant q = 0 .. 3: bins 5, 14, 23, 32
+    bin = dy > 0.f ? (dx > 0.f ? 5 : 14) : (dx < 0.f ? 23 : 32);
   hist[bin][lane] += wgt * mag;
 }
 
@@ -486,8 +485,11 @@ struct Vote {
   float fe, fo;   // their orientation weights
 };
 
+// ok false: the lane has no sample (its coordinates may lie anywhere); all
+// four of its cells are then -1, so that the commit skips it without a
+// branch around this function.
 __device__ __forceinline__ void desc_targets(Vote &v, float rx, float ry, float gx, float gy,
-                                             float th) {
+                                             float th, bool ok = true) {
   const float u = rx + 1.5f, vv0 = ry + 1.5f;
   const float mag = sqrtf(gx * gx + gy * gy);
   float phi = atan2f(gy, gx) - th;
@@ -506,7 +508,7 @@ __device__ __forceinline__ void desc_targets(Vote &v, float rx, float ry, float 
   v.fo = even0 ? f1 : 1.f - f1;
   // u0, v0 lie in [-1, 3] (u, v in (-1, 4)): cell u0 + du exists iff u0 >= 0
   // (du = 0) or u0 <= 2 (du = 1), and the same for v.
-  const bool uok[2] = {u0 >= 0, u0 <= 2}, vok[2] = {v0 >= 0, v0 <= 2};
+  const bool uok[2] = {ok && u0 >= 0, ok && u0 <= 2}, vok[2] = {v0 >= 0, v0 <= 2};
   const int c00 = (v0 * 4 + u0) * 8;
 #pragma unroll
   for (int dv = 0; dv < 2; dv++) {
@@ -520,11 +522,10 @@ __device__ __forceinline__ void desc_targets(Vote &v, float rx, float ry, float 
   }
 }
 
-// Add the votes of the warp's lanes (ok: the lane has a sample) to the warp's
-// columns in the two passes described above; a vote without a target (a cell
-// outside the grid, or no sample) is skipped. Every lane of the warp must call
-// it.
-__device__ __forceinline__ void desc_commit(float *hist, int lane, bool ok, const Vote &v) {
+// Add the votes of the warp's lanes to the warp's columns in the two passes
+// described above; a vote without a target (a cell outside the grid) is
+// skipped. Every lane of the warp must call it.
+__device__ __forceinline__ void desc_commit(float *hist, int lane, const Vote &v) {
   float *col = hist + (lane & (kDescCols - 1));
   const bool upper = lane >= 16;
 #pragma unroll
@@ -534,7 +535,7 @@ __device__ __forceinline__ void desc_commit(float *hist, int lane, bool ok, cons
     const float f = even ? v.fe : v.fo;
 #pragma unroll
     for (int k = 0; k < 4; k++)
-      if (ok && v.cell[k] >= 0) col[v.cell[k] + o] += v.w[k] * f;
+      if (v.cell[k] >= 0) col[v.cell[k] + o] += v.w[k] * f;
     __syncwarp();
   }
 }
@@ -644,10 +645,10 @@ __device__ __forceinline__ void desc_sweep(const Desc *__restrict__ d, const Ref
           const float ga = lv[oa + 1] - lv[oa - 1], ha = lv[oa + pitch] - lv[oa - pitch];
           const float gb = lv[ob + 1] - lv[ob - 1], hb = lv[ob + pitch] - lv[ob - pitch];
           Vote vt;
-          if (oka) desc_targets(vt, rxa, rya, ga, ha, th);
-          desc_commit(hist, lane, oka, vt);
-          if (okb) desc_targets(vt, rxb, ryb, gb, hb, th);
-          desc_commit(hist, lane, okb, vt);
+          desc_targets(vt, rxa, rya, ga, ha, th, oka);
+          desc_commit(hist, lane, vt);
+          desc_targets(vt, rxb, ryb, gb, hb, th, okb);
+          desc_commit(hist, lane, vt);
         }
         __syncwarp();  // the next round rewrites this warp's interval table
       }
@@ -665,7 +666,9 @@ __device__ __forceinline__ void desc_sweep(const Desc *__restrict__ d, const Ref
           const bool ok = !(x0 < 1 || x0 > od.W - 3 || y0 < 1 || y0 > od.H - 3);
           Vote vt;
           if (!ok) {  // (1024 samples per scale: the trip count is warp-uniform)
-            desc_commit(hist, lane, false, vt);
+#pragma unroll
+            for (int k = 0; k < 4; k++) vt.cell[k] = -1;
+            desc_commit(hist, lane, vt);
             continue;
           }
           const float fx = xr - xf, fy = yr - yf, gx1 = 1.f - fx, gy1 = 1.f - fy;
@@ -682,7 +685,7 @@ __device__ __forceinline__ void desc_sweep(const Desc *__restrict__ d, const Ref
           const float ym = gy1 * (gx1 * at(pm) + fx * at(pm + 1)) +
                            fy * (gx1 * at(p) + fx * at(p + 1));
           desc_targets(vt, rx, ry, xp - xm, yp - ym, th);
-          desc_commit(hist, lane, true, vt);
+          desc_commit(hist, lane, vt);
         }
       }
     }
