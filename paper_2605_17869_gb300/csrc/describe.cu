@@ -63,9 +63,10 @@ __device__ __forceinline__ void ori_vote(float (*hist)[32], int lane, float dx, 
   // |dx| = |dy|: theta is exactly 45 (2q + 1) degrees, a bin boundary the
   // nearest-bin rule floor(36 theta / 2 pi + 1/2) resolves upward; decided in
   // integers rather than left to the rounding of atan2f.
-  static_assert(kOriBins == 36, "the diagonal bins below are floor(36 (2q + 1) / 8 + 1/2)");
-  if (fabsf(dx) == fabsf(dy) && dx != 0.f)  // quadrant q = 0 .. 3: bins 5, 14, 23, 32
-    bin = dy > 0.f ? (dx > 0.f ? 5 : 14) : (dx < 0.f ? 23 : 32);
+  if (fabsf(dx) == fabsf(dy) && dx != 0.f) {
+    const int qd = dy > 0.f ? (dx > 0.f ? 0 : 1) : (dx < 0.f ? 2 : 3);
+    bin = (kOriBins * (2 * qd + 1) + 4) / 8 % kOriBins;
+  }
   hist[bin][lane] += wgt * mag;
 }
 
