@@ -222,8 +222,8 @@ def sift_autotune_batch(handle, img_ptrs, Hs, Ws, pitches, stream: int, kpts_lis
     hit = c_int(0)
     _check(_lib().sift_autotune_batch(
         handle, n, (c_void_p * n)(*img_ptrs), (c_int * n)(*Hs), (c_int * n)(*Ws),
-        (c_int * n)(*pitches), c_void_p(stream), (SiftKptsDev * n)(*kpts_list),
-        (c_void_p * n)(*desc_ptrs), c_void_p(counts_ptr), byref(hit)), handle,
+        (c_int * n)(*pitches), c_void_p(stream), _carray(SiftKptsDev, n, kpts_list),
+        _carray(c_void_p, n, desc_ptrs), c_void_p(counts_ptr), byref(hit)), handle,
         "sift_autotune_batch")
     return bool(hit.value)
 
@@ -627,14 +627,12 @@ class Extractor:
         there after a search. Returns (tuning JSON, whether it came from the
         cache)."""
         torch = _torch()
-        dims = [self._check_img(im) for im in imgs]
+        Hs, Ws, Ps = self._batch_dims(imgs)
         s = stream if stream is not None else torch.cuda.current_stream()
-        bufs = self._buffers(len(imgs))
+        _, (k_arr, d_arr) = self._outputs(len(imgs))
         sift_set_tuning_cache(self.handle, cache)
-        hit = sift_autotune_batch(self.handle, [im.data_ptr() for im in imgs],
-                                  [d[0] for d in dims], [d[1] for d in dims],
-                                  [d[2] for d in dims], s.cuda_stream, [b.kpts() for b in bufs],
-                                  [b.desc.data_ptr() for b in bufs], self._counts.data_ptr())
+        hit = sift_autotune_batch(self.handle, [im.data_ptr() for im in imgs], Hs, Ws, Ps,
+                                  s.cuda_stream, k_arr, d_arr, self._counts.data_ptr())
         self._last_batch = len(imgs)
         return sift_get_tuning(self.handle), hit
 
