@@ -300,13 +300,15 @@ sift_status sift_build_pyramid(sift_handle *h, const float *img_dev, int H, int 
  *   2 DoG extrema scan, 3 decimation (no separate launch: it is fused into
  *   the first level blur of each octave), 4 candidate and keypoint
  *   compaction and the top-K cap, 5 descriptor, 6 refinement,
- *   7 orientation. Classes at or above n_classes are left out.
- * Reading synchronises the handle's last run. */
+ *   7 orientation. Classes at or above n_classes are left out. While profiling
+ * is on, sift_extract_batch runs a batch as one lane, so that every kernel is
+ * timed alone. Reading synchronises the handle's last run. */
 sift_status sift_set_profiling(sift_handle *h, int enable);
 sift_status sift_kernel_times(sift_handle *h, double *ms, int *launches, int n_classes);
 
 /* Number of CUDA kernels the last extraction on this handle launched (one
- * graph replay). Host-only: no synchronisation. */
+ * graph replay per lane; a batch run as k lanes counts each lane's kernels).
+ * Host-only: no synchronisation. */
 sift_status sift_last_launch_count(sift_handle *h, int *kernels);
 
 /* Autotuner. The tuning is the set of launch shapes the extraction uses
