@@ -248,3 +248,18 @@ def test_status_codes_match_the_header():
     for name, v in codes.items():
         assert getattr(_abi, name) == v, name
         assert _abi.STATUS_NAMES[v] == name
+
+
+def test_binding_marshalling_on_cpu():
+    """The batch marshalling of the binding: prebuilt ctypes arrays pass
+    through, lists are converted, and images that are not 2-D float32 CUDA
+    tensors with contiguous rows are refused before any library call."""
+    import ctypes
+
+    import paper_2605_17869_gb300 as pkg
+    torch = pytest.importorskip("torch")
+    arr = (ctypes.c_int * 3)(1, 2, 3)
+    assert pkg._carray(ctypes.c_int, 3, arr) is arr
+    assert list(pkg._carray(ctypes.c_int, 3, [4, 5, 6])) == [4, 5, 6]
+    with pytest.raises(pkg.SiftError):
+        pkg.Extractor._batch_dims([torch.zeros(4, 4)])  # on the host, not the device

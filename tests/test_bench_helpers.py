@@ -112,3 +112,56 @@ def test_default_tuning_is_recognised():
     assert not bench._is_default_tuning(d.replace('"blur_ctas_per_sm": [0]', '"blur_ctas_per_sm": [0, 3]'))
     assert bench._is_default_tuning(d[:-1] + ', "batch_lanes": 2}')
     assert not bench._is_default_tuning(d[:-1] + ', "batch_lanes": 1}')
+
+
+class _FakeCuda:
+    """Stand-in for torch.cuda: events read a clock that each step advances,
+    so that the timing helpers can be checked without a device."""
+
+    def __init__(self, clock):
+        self.clock = clock
+
+    def synchronize(self):
+        pass
+
+    def Event(self, enable_timing=False):
+        clock = self.clock
+
+        class Ev:
+            def record(self, stream=None):
+                self.t = clock[0]
+
+            def synchronize(self):
+                pass
+
+            def elapsed_time(self, other):
+                return other.t - self.t
+
+        return Ev()
+
+
+class _FakeTorch:
+    def __init__(self, clock):
+        self.cuda = _FakeCuda(clock)
+
+
+def test_queued_steps_time_exactly_the_queued_steps():
+    clock = [0.0]
+    calls = []
+
+    def step():  # each step costs 2 ms of "device" time
+        clock[0] += 2.0
+        calls.append(1)
+
+    ms, wall = bench.queued_steps(_FakeTorch(clock), step, 7, 3, None)
+    assert len(calls) == 10 and ms == 14.0 and wall >= 0.0
+
+
+def test_best_queued_ms_takes_the_fastest_run():
+    clock = [0.0]
+    costs = iter([5.0] * 4 + [9.0] * 3 + [5.0] * 4 + [2.0] * 3 + [5.0] * 4 + [4.0] * 3)
+
+    def step():  # warm-up steps cost 5 ms; the three timed runs 9, 2 and 4 ms per step
+        clock[0] += next(costs)
+
+    assert bench.best_queued_ms(_FakeTorch(clock), step, 9, 4, None) == 2.0
